@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark: ELBO + gradient source-pixel evaluations per second on one synthetic
+SDSS-shaped field (5 bands x 2048 x 1489 px, 500 sources), FP32 per-pixel arithmetic
+with FP64 accumulation, next to the plain FP64 path, the end-to-end host-pointer call
+and the FP64 CPU oracle.
+
+One step = one ELBO + gradient evaluation of every source of the field (brightness
+moments and mixture tables, per-source E/Var contributions, E/Var maps and
+log-likelihood, adjoint, chain rule + KL, total), i.e. one source-pixel evaluation per
+(source, active pixel) pair.  Inputs are resident on the device; L2 is flushed
+(256 MiB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank evaluates its own field (weak scaling, no collective
+on the data path); timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1801_10277_gb300 import synth  # noqa: E402
+
+FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+FP32_LANES = 128
+KERNELS_PER_STEP = 6     # prep, contrib, gather, adjoint, finalize, total
+
+
+def adjoint_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """Algorithmic FP32 operations (FMA = 2) of the adjoint per source-pixel, counted from
+    the formulas it evaluates: per PSF component the offset and its products (5), the
+    star component (exponent 6, weight 1, P d 6, three sums 5) and each galaxy
+    component (exponent 6, weight 1, P d 6, sums g/gx/gy 5, e_dev 2, nu weight 1, three
+    covariance sums 12); per pixel the likelihood weights and the 12 y-gradients (55)."""
+    nprof = n_exp + n_dev
+    return npsf * (5 + 18 + nprof * 33) + 55
+
+
+def contrib_flops_per_source_pixel(npsf, n_exp, n_dev):
+    nprof = n_exp + n_dev
+    return npsf * (5 + 8 + nprof * 8) + 30
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist.get_rank(), ws, dist
+
+
+def oracle_rate(prob, min_seconds=10.0, max_reps=20):
+    """FP64 CPU oracle ELBO + gradient over the whole field, repeated until
+    min_seconds of work; returns (source-pixel evals/s, cores, reps, seconds)."""
+    from oracle.oracle import Oracle, num_threads
+    orc = Oracle(prob)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        orc.elbo(prob.theta)
+        orc.derivs(prob.theta)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    return prob.source_pixels() * reps / el, num_threads(), reps, el
+
+
+def reference_arm(args, rank, ws):
+    """--impl reference: the oracle as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    prob = synth.config(1)
+    t_steps = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    from oracle.oracle import Oracle, num_threads
+    orc = Oracle(prob)
+    orc.elbo(prob.theta)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.elbo(prob.theta)
+        orc.derivs(prob.theta)
+        t_steps.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(t_steps) / len(t_steps)
+    val = prob.source_pixels() / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": "ELBO+grad source-pixel evals/s", "value": val,
+        "unit": "source-pixel evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "sources": prob.n_src,
+                   "source_pixels": prob.source_pixels()},
+        "cpu_baseline": {"value": val, "unit": "source-pixel evals/s", "cores": num_threads(),
+                         "kind": "oracle",
+                         "sample": "whole field, one ELBO + gradient evaluation per step"},
+        "e2e": {"value": val, "unit": "source-pixel evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    args = ap.parse_args()
+    rank, ws, dist = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, rank, ws)
+        return
+    import torch
+    from paper_1801_10277_gb300 import celeste as cel
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    prob = synth.config(1, seed=2027 + rank)
+    P = cel.Problem(prob)
+    n_sp = P.source_pixels
+    dev = torch.device("cuda", local_rank)
+    theta = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
+    tot = torch.zeros(1, dtype=torch.float64, device=dev)
+    loc = torch.zeros(prob.n_src, dtype=torch.float64, device=dev)
+    grad = torch.zeros(prob.n_src, 44, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        P.elbo_grad_device(theta, tot, loc, grad, precision=prec)
+
+    def timed_loop(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(prec)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    with Clocks(local_rank) as clk:
+        ms32 = timed_loop(cel.FP32, args.steps, args.warmup)
+    if P.device_status() != 0:
+        raise RuntimeError("device-side parameter check failed")
+    value = n_sp * ws / (ms32 / 1000.0)
+    ms64 = timed_loop(cel.FP64, args.fp64_steps, 1)
+    value64 = n_sp * ws / (ms64 / 1000.0)
+
+    # per-kernel durations (CUDA events on the launch stream), FP32 path
+    P.profile(True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step(cel.FP32)
+    torch.cuda.synchronize()
+    prof = P.profile_read()
+    P.profile(False)
+    tot_ms = sum(v[0] for v in prof.values())
+    adj_ms, adj_n = prof.get("adjoint", (0.0, 1))
+    adj_avg = adj_ms / max(1, adj_n)
+    npsf = prob.images[0].psf.shape[0]
+    ne, nd = prob.exp_mix.shape[0], prob.dev_mix.shape[0]
+    flops_adj = adjoint_flops_per_source_pixel(npsf, ne, nd) * n_sp
+    clocks = clk.summary()
+    peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
+    achieved = flops_adj / (adj_avg / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp32, "traffic": None, "kernel": "adjoint (FP32)",
+                "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
+                "kernel_share": {k: v[0] / tot_ms for k, v in prof.items()}}
+
+    # end to end through the host-pointer C ABI (pinned buffers, copies inside)
+    pin_th = torch.tensor(prob.theta, dtype=torch.float64).pin_memory()
+    pin_tot = torch.zeros(1, dtype=torch.float64).pin_memory()
+    pin_loc = torch.zeros(prob.n_src, dtype=torch.float64).pin_memory()
+    pin_g = torch.zeros(prob.n_src, 44, dtype=torch.float64).pin_memory()
+    import ctypes as C
+
+    def host_step():
+        st = P.L.celeste_elbo_grad(P.h, C.c_void_p(pin_th.data_ptr()), cel.FP32,
+                                   C.c_void_p(pin_tot.data_ptr()), C.c_void_p(pin_loc.data_ptr()),
+                                   C.c_void_p(pin_g.data_ptr()))
+        cel._check(st)
+
+    for _ in range(args.warmup):
+        host_step()
+    t_e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        host_step()
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_ms = 1000.0 * sum(t_e2e) / len(t_e2e)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n_sp * ws / (e2e_ms / 1000.0), "unit": "source-pixel evals/s",
+           "h2d_bytes_per_step": int(pin_th.numel() * 8),
+           "d2h_bytes_per_step": int((pin_tot.numel() + pin_loc.numel() + pin_g.numel()) * 8),
+           "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, reps, secs = oracle_rate(prob)
+        cpu = {"value": rate, "unit": "source-pixel evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"whole field ({n_sp} source-pixels) ELBO + gradient x {reps} "
+                         f"({secs:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": "ELBO+grad source-pixel evals/s", "value": value,
+            "unit": "source-pixel evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": prob.name, "sources": prob.n_src, "source_pixels": n_sp,
+                       "bands": 5, "image": "2048x1489", "precision": "fp32 pixels, fp64 accumulation",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replica{ws}" if ws > 1 else "single"},
+            "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
+                          "speedup_fp32_over_fp64": value / value64},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

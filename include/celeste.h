@@ -1,0 +1,225 @@
+/*
+ * celeste.h -- C ABI of the GB300 Celeste hot path: the variational objective (ELBO)
+ * of the Celeste astronomical-catalog model over every active pixel of every
+ * source's patch, its gradient and per-source Hessian, and the per-source
+ * trust-region Newton fit that consumes them.
+ *
+ * Paper: Regier et al., "Cataloging the Visible Universe through Bayesian Inference
+ * at Petascale" (arXiv 1801.10277).
+ *   - Section III: pixels x_nm ~ Poisson(F_nm); per source a star/galaxy indicator,
+ *     log-normal reference-band brightness, Gaussian colours (log ratios of adjacent
+ *     bands), position and galaxy shape; image metadata Lambda_n (PSF, sky,
+ *     calibration, WCS); ELBO  L(theta) = E_q[log p(x, z) - log q(z)]  (Eq. 1).
+ *   - Section IV: 44 parameters per source.
+ *   - Section IV-D: block coordinate ascent, one source's 44 parameters per block;
+ *     Newton steps with exact Hessians inside a trust region.
+ *   - Section VI-B: cost counted per active pixel visit.
+ * The paper defers the exact variational family and the expected log-likelihood to
+ * Regier et al. (ICML 2015).  This library implements the reading:
+ *     E[F]   = sky + iota * sum_s sum_i a_i E[l_si] g_si(pixel)
+ *     Var[F] = sum_s ( sum_i a_i iota^2 E[l_si^2] g_si^2 - (sum_i a_i iota E[l_si] g_si)^2 )
+ *     E_q[log F] ~= log E[F] - Var[F] / (2 E[F]^2)          (second-order delta method)
+ *     ELBO = sum over the union of patches of  x (log E - Var / (2 E^2)) - E
+ *            - sum_s KL(q_s || prior)                      (log x! dropped)
+ * with g the PSF mixture (star) or the PSF convolved with exp/dev Gaussian-mixture
+ * profiles (galaxy), evaluated at integer pixel centres and truncated to the
+ * source's patch.
+ *
+ * PARAMETER LAYOUT (44 doubles per source, row-major [n_src][44], constrained):
+ *   0,1 u (world position)   2 e_dev   3 e_axis (minor/major)   4 e_angle (radians,
+ *   counter-clockwise from +x)   5 e_scale (half-light radius, px)
+ *   6,7 r1[type]  8,9 r2[type] (mean, variance of log r-band brightness, nmgy)
+ *   10..17 c1[type][4]  18..25 c2[type][4] (colour means, variances; colours are
+ *   u-g, g-r, r-i, i-z log ratios)   26,27 a[type] (P(star), P(galaxy))
+ *   28..43 k[type][8] (colour-prior component responsibilities).  type 0 = star.
+ * Bands: 0..4 = u g r i z; the reference band is r (2).
+ *
+ * CONVENTIONS
+ *   - Ownership: every pointer argument is owned by the caller.  celeste_problem_create
+ *     copies what it needs to the current CUDA device; the caller may free its
+ *     arrays afterwards.  The problem owns its device memory until destroy.
+ *   - Host vs device: functions without the _device suffix take HOST pointers and
+ *     synchronise before returning.  _device variants take DEVICE pointers and a
+ *     cudaStream_t (passed as void*), enqueue work on that stream and return
+ *     without synchronising.
+ *   - Errors: every call returns a celeste_status; nothing aborts and no kernel
+ *     traps.  celeste_last_error() returns a thread-local message for the last
+ *     failure of the calling thread.
+ *   - Threading: calls on one problem handle are not thread-safe; different handles
+ *     are independent.
+ *   - Precision: CELESTE_FP64 evaluates every pixel in double; CELESTE_FP32_ACC64
+ *     evaluates per-pixel mixture and likelihood arithmetic in float and keeps
+ *     per-source accumulation (across warps, work items and patches), the chain rule,
+ *     the KL terms and the trust-region solve in double.
+ */
+#ifndef CELESTE_H
+#define CELESTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t celeste_status;
+
+enum {
+    CELESTE_OK = 0,
+    CELESTE_ERR_ARG = -1,        /* invalid argument, size or parameter value */
+    CELESTE_ERR_NOT_PD = -2,     /* a PSF or prior covariance is not positive definite */
+    CELESTE_ERR_NONFINITE = -3,  /* NaN/Inf in inputs, or produced for some source */
+    CELESTE_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+    CELESTE_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+    CELESTE_ERR_NOMEM = -6       /* device allocation failed */
+};
+
+enum { CELESTE_FP64 = 0, CELESTE_FP32_ACC64 = 1 };
+
+enum { CELESTE_NPARAM = 44, CELESTE_NFREE = 41, CELESTE_MAX_PSF = 4, CELESTE_MAX_PROFILE = 16,
+       CELESTE_NPRIOR_COMP = 8 };
+
+/* One image (Section III, metadata Lambda_n). */
+typedef struct {
+    int32_t band;              /* 0..4 = u g r i z */
+    int32_t height, width;     /* pixels */
+    const float* pixels;       /* [height][width] photon counts, row-major */
+    double sky;                /* sky background, counts per pixel (used when sky_map is NULL) */
+    const float* sky_map;      /* optional [height][width] sky counts, or NULL */
+    double nmgy_per_count;     /* calibration; iota = 1 / nmgy_per_count counts per nanomaggy */
+    double wcs[6];             /* affine world->pixel: pixel = A u + t, A = {wcs[0] wcs[1]; wcs[2] wcs[3]}, t = {wcs[4], wcs[5]} */
+    int32_t n_psf;             /* 1..CELESTE_MAX_PSF */
+    const double* psf;         /* [n_psf][6]: weight, offset x, offset y, Sxx, Sxy, Syy (pixels) */
+} celeste_image;
+
+/* Galaxy profiles and priors (Section III: Phi, Upsilon, Xi). */
+typedef struct {
+    int32_t n_exp, n_dev;      /* n_exp + n_dev <= CELESTE_MAX_PROFILE */
+    const double* exp_mix;     /* [n_exp][2]: weight, variance of a circular Gaussian, unit half-light radius */
+    const double* dev_mix;     /* [n_dev][2] */
+    double prior_star;         /* Phi: prior P(star), in (0, 1) */
+    const double* prior_r;     /* [2][2]: mean, variance of log r-band brightness per type */
+    int32_t n_color_comp;      /* must be CELESTE_NPRIOR_COMP (8) */
+    const double* prior_c;     /* [2][n_color_comp][21]: weight, mean[4], covariance[4][4] */
+} celeste_model;
+
+/* One source's active region in one image: a rectangle of pixel centres, inside the image. */
+typedef struct {
+    int32_t image;
+    int32_t x0, y0, w, h;
+} celeste_patch;
+
+typedef struct celeste_problem celeste_problem;   /* opaque; owns device copies */
+
+/*
+ * Copy a problem to the current device and build its work lists.
+ *   imgs[n_img]; model; n_src sources; patch_offsets[n_src + 1] (CSR into patches[]);
+ *   nbr_offsets[n_src + 1] / nbrs: neighbour lists (sources whose patches intersect
+ *   in some image; Section IV-D's conflict graph); every list must be symmetric.
+ * Errors: CELESTE_ERR_ARG (sizes, a patch outside its image, bad band, weights),
+ * CELESTE_ERR_NOT_PD (PSF / prior covariance), CELESTE_ERR_NOMEM, CELESTE_ERR_CUDA.
+ */
+celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
+                                      const celeste_model* model, int32_t n_src,
+                                      const int32_t* patch_offsets, const celeste_patch* patches,
+                                      const int32_t* nbr_offsets, const int32_t* nbrs,
+                                      celeste_problem** out);
+void celeste_problem_destroy(celeste_problem* prob);
+
+/* Number of (source, active pixel) pairs: the unit of the cost accounting (Section VI-B). */
+int64_t celeste_source_pixels(const celeste_problem* prob);
+
+/*
+ * ELBO (Eq. 1, the reading above) at theta[n_src][44] (host).
+ *   elbo_total: sum over the union of patches of the expected log-likelihood minus the
+ *     sum of KL terms.
+ *   elbo_per_source (nullable, [n_src]): local objective of each source, the sum over
+ *     its own patch pixels (neighbours' light included in E and Var) minus its KL.
+ * Errors: CELESTE_ERR_ARG for parameters outside their domain (r2, c2, e_scale <= 0,
+ * a or k outside (0,1), e_axis outside (0,1], e_dev outside [0,1]); CELESTE_ERR_NONFINITE.
+ */
+celeste_status celeste_elbo(celeste_problem* prob, const double* theta, int32_t precision,
+                            double* elbo_total, double* elbo_per_source);
+
+/*
+ * ELBO and its gradient wrt every source's 44 constrained parameters (Section IV-D:
+ * one block per source; d ELBO_total / d theta_s = d ELBO_s / d theta_s because each
+ * source's light is truncated to its patch).  grad[n_src][44] (host).
+ */
+celeste_status celeste_elbo_grad(celeste_problem* prob, const double* theta, int32_t precision,
+                                 double* elbo_total, double* elbo_per_source, double* grad);
+
+/*
+ * Per-source exact Hessians (Section IV-D: 44 x 44, dense symmetric) of ELBO_s wrt
+ * theta_s, with the gradient.  hess[n_src][44][44] full symmetric (host); grad and
+ * elbo_per_source nullable.
+ */
+celeste_status celeste_hess(celeste_problem* prob, const double* theta, int32_t precision,
+                            double* elbo_per_source, double* grad, double* hess);
+
+/* Trust-region Newton options (Section IV-D; Nocedal & Wright, Algorithm 4.1). */
+typedef struct {
+    int32_t max_iter;          /* Newton iterations per source per sweep (default 50) */
+    double grad_tol;           /* stop when max |dELBO_s/dt| <= grad_tol (free coords) */
+    double pred_tol_rel;       /* stop when the model's predicted gain <= pred_tol_rel (1 + |ELBO_s|) */
+    double delta0, delta_max;  /* initial and largest trust radius (free coords) */
+    double eta;                /* accept a step when actual/predicted gain > eta */
+    double f_noise_rel;        /* predicted gains below f_noise_rel (1+|ELBO_s|) skip the ratio test */
+    int32_t precision;         /* CELESTE_FP64 or CELESTE_FP32_ACC64 */
+    int32_t max_sweeps;        /* block-coordinate sweeps over all colour classes */
+    double sweep_tol;          /* stop sweeping when |dELBO_total| / max(1,|ELBO_total|) < sweep_tol */
+} celeste_fit_options;
+
+/* Fill opts with the defaults documented above. */
+void celeste_fit_options_default(celeste_fit_options* opts);
+
+/*
+ * Block-coordinate trust-region Newton fit (Section IV-D).  Sources are greedily
+ * coloured in ascending id over the neighbour graph; the colours are swept in order;
+ * all sources of one colour (which never overlap) take their Newton iterations in
+ * one batch with every other source fixed; E and Var are updated after accepted
+ * steps.  theta_inout[n_src][44] (host) is read and overwritten.  which[n_which]
+ * restricts the moving sources (NULL: all).  iters_out / status_out ([n_src],
+ * nullable) receive Newton iterations and 0 converged / 1 iteration limit /
+ * 2 non-finite.  The fit restarts from theta_inout, so it can be resumed.
+ */
+celeste_status celeste_fit_sources(celeste_problem* prob, double* theta_inout,
+                                   const int32_t* which, int32_t n_which,
+                                   const celeste_fit_options* opts, int32_t* iters_out,
+                                   int32_t* status_out, double* elbo_out);
+
+/* Device-pointer variants: same semantics, pointers on the problem's device, work
+ * enqueued on `stream` (a cudaStream_t; NULL = legacy default stream), no synchronisation.
+ * Parameter-domain checks read theta on the device and report through
+ * celeste_device_status() after the stream completes. */
+celeste_status celeste_elbo_device(celeste_problem* prob, const double* d_theta, int32_t precision,
+                                   double* d_elbo_total, double* d_elbo_per_source, void* stream);
+celeste_status celeste_elbo_grad_device(celeste_problem* prob, const double* d_theta,
+                                        int32_t precision, double* d_elbo_total,
+                                        double* d_elbo_per_source, double* d_grad, void* stream);
+celeste_status celeste_hess_device(celeste_problem* prob, const double* d_theta, int32_t precision,
+                                   double* d_elbo_per_source, double* d_grad, double* d_hess,
+                                   void* stream);
+/* Status word written by the device-side checks of the last _device call (host read;
+ * synchronises the problem's last stream).  CELESTE_OK or a negative status. */
+celeste_status celeste_device_status(celeste_problem* prob);
+
+/*
+ * Per-kernel timing (tracing aid).  With profiling on, every stage launch of the
+ * calls above (prep, contrib, gather, adjoint / ll_sum / hess_adjoint, finalize) is
+ * bracketed by CUDA events on its launch stream.  celeste_profile_read waits for the
+ * recorded events, writes up to max_kernels entries (names[k*32 .. k*32+31]
+ * NUL-terminated, total milliseconds, launch count), resets the accumulators and
+ * returns the number of distinct stages (negative status on error).
+ */
+celeste_status celeste_profile_enable(celeste_problem* prob, int32_t on);
+int32_t celeste_profile_read(celeste_problem* prob, int32_t max_kernels, char* names,
+                             double* ms_total, int32_t* launches);
+
+/* Thread-local message describing the calling thread's last error. */
+const char* celeste_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELESTE_H */

@@ -1,0 +1,272 @@
+"""Thin Python binding of libceleste (the C ABI in include/celeste.h).
+
+Argument marshalling only: every step of the ELBO / gradient / Hessian / fit path
+runs in the library's CUDA kernels.  Host-pointer calls take numpy arrays; the
+``*_device`` calls take CUDA torch tensors and enqueue on torch's current stream.
+There is no CPU fallback: when the shared library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NPARAM = 44
+NFREE = 41
+FP64 = 0
+FP32 = 1          # FP32 per-pixel arithmetic, FP64 accumulation
+
+OK, ERR_ARG, ERR_NOT_PD, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+
+
+class CelesteError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"celeste status {status}: {msg}")
+        self.status = status
+
+
+class celeste_image(C.Structure):
+    _fields_ = [("band", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("pixels", C.c_void_p), ("sky", C.c_double), ("sky_map", C.c_void_p),
+                ("nmgy_per_count", C.c_double), ("wcs", C.c_double * 6),
+                ("n_psf", C.c_int32), ("psf", C.c_void_p)]
+
+
+class celeste_model(C.Structure):
+    _fields_ = [("n_exp", C.c_int32), ("n_dev", C.c_int32), ("exp_mix", C.c_void_p),
+                ("dev_mix", C.c_void_p), ("prior_star", C.c_double), ("prior_r", C.c_void_p),
+                ("n_color_comp", C.c_int32), ("prior_c", C.c_void_p)]
+
+
+class celeste_patch(C.Structure):
+    _fields_ = [("image", C.c_int32), ("x0", C.c_int32), ("y0", C.c_int32), ("w", C.c_int32),
+                ("h", C.c_int32)]
+
+
+class celeste_fit_options(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("grad_tol", C.c_double), ("pred_tol_rel", C.c_double),
+                ("delta0", C.c_double), ("delta_max", C.c_double), ("eta", C.c_double),
+                ("f_noise_rel", C.c_double), ("precision", C.c_int32), ("max_sweeps", C.c_int32),
+                ("sweep_tol", C.c_double)]
+
+
+_lib = None
+
+EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_pixels",
+           "celeste_elbo", "celeste_elbo_grad", "celeste_hess", "celeste_fit_options_default",
+           "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
+           "celeste_hess_device", "celeste_device_status", "celeste_last_error",
+           "celeste_profile_enable", "celeste_profile_read"]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libceleste.  Raises when the library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"libceleste is not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    L.celeste_problem_create.argtypes = [C.POINTER(celeste_image), i32, C.POINTER(celeste_model), i32,
+                                         vp, C.POINTER(celeste_patch), vp, vp, C.POINTER(vp)]
+    L.celeste_problem_create.restype = i32
+    L.celeste_problem_destroy.argtypes = [vp]
+    L.celeste_problem_destroy.restype = None
+    L.celeste_source_pixels.argtypes = [vp]
+    L.celeste_source_pixels.restype = i64
+    L.celeste_elbo.argtypes = [vp, vp, i32, vp, vp]
+    L.celeste_elbo_grad.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.celeste_hess.argtypes = [vp, vp, i32, vp, vp, vp]
+    for f in ("celeste_elbo", "celeste_elbo_grad", "celeste_hess"):
+        getattr(L, f).restype = i32
+    L.celeste_fit_options_default.argtypes = [C.POINTER(celeste_fit_options)]
+    L.celeste_fit_options_default.restype = None
+    L.celeste_fit_sources.argtypes = [vp, vp, vp, i32, C.POINTER(celeste_fit_options), vp, vp, vp]
+    L.celeste_fit_sources.restype = i32
+    L.celeste_elbo_device.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.celeste_elbo_grad_device.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    L.celeste_hess_device.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    for f in ("celeste_elbo_device", "celeste_elbo_grad_device", "celeste_hess_device"):
+        getattr(L, f).restype = i32
+    L.celeste_device_status.argtypes = [vp]
+    L.celeste_device_status.restype = i32
+    L.celeste_profile_enable.argtypes = [vp, i32]
+    L.celeste_profile_enable.restype = i32
+    L.celeste_profile_read.argtypes = [vp, i32, vp, vp, vp]
+    L.celeste_profile_read.restype = i32
+    L.celeste_last_error.argtypes = []
+    L.celeste_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != OK:
+        raise CelesteError(st, _lib.celeste_last_error().decode())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def fit_options(**kw):
+    o = celeste_fit_options()
+    load().celeste_fit_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """A Celeste problem resident on the current CUDA device (owns its device copy)."""
+
+    def __init__(self, prob):
+        L = load()
+        self.n_src = int(prob.theta.shape[0])
+        keep = []
+        imgs = (celeste_image * len(prob.images))()
+        for i, im in enumerate(prob.images):
+            px = np.ascontiguousarray(im.pixels, np.float32)
+            psf = np.ascontiguousarray(im.psf, np.float64)
+            sm = None if im.sky_map is None else np.ascontiguousarray(im.sky_map, np.float32)
+            keep += [px, psf, sm]
+            imgs[i].band, imgs[i].height, imgs[i].width = im.band, px.shape[0], px.shape[1]
+            imgs[i].pixels, imgs[i].sky, imgs[i].sky_map = _p(px), float(im.sky), _p(sm)
+            imgs[i].nmgy_per_count = float(im.calib)
+            for k in range(6):
+                imgs[i].wcs[k] = float(im.wcs[k])
+            imgs[i].n_psf, imgs[i].psf = psf.shape[0], _p(psf)
+        exp_mix = np.ascontiguousarray(prob.exp_mix, np.float64)
+        dev_mix = np.ascontiguousarray(prob.dev_mix, np.float64)
+        prior_r = np.ascontiguousarray(prob.prior_r, np.float64)
+        prior_c = np.ascontiguousarray(prob.prior_c, np.float64)
+        keep += [exp_mix, dev_mix, prior_r, prior_c]
+        m = celeste_model(exp_mix.shape[0], dev_mix.shape[0], _p(exp_mix), _p(dev_mix),
+                          float(prob.prior_star), _p(prior_r), prior_c.shape[1], _p(prior_c))
+        po = np.ascontiguousarray(prob.patch_offsets, np.int32)
+        pa = np.ascontiguousarray(prob.patches, np.int32).reshape(-1, 5)
+        patches = (celeste_patch * max(1, pa.shape[0]))()
+        for i in range(pa.shape[0]):
+            patches[i] = celeste_patch(*(int(v) for v in pa[i]))
+        no = np.ascontiguousarray(prob.nbr_offsets, np.int32)
+        nb = np.ascontiguousarray(prob.nbrs, np.int32)
+        keep += [po, no, nb]
+        h = C.c_void_p()
+        st = L.celeste_problem_create(imgs, len(prob.images), C.byref(m), self.n_src, _p(po),
+                                      patches, _p(no), _p(nb) if nb.size else None, C.byref(h))
+        _check(st)
+        self.h = h
+        self.L = L
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.celeste_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def source_pixels(self):
+        return int(self.L.celeste_source_pixels(self.h))
+
+    def _theta(self, theta):
+        th = np.ascontiguousarray(theta, np.float64)
+        if th.shape != (self.n_src, NPARAM):
+            raise ValueError(f"theta must be [{self.n_src}][{NPARAM}]")
+        return th
+
+    # ---- host-pointer calls
+    def elbo(self, theta, precision=FP64):
+        th = self._theta(theta)
+        tot = C.c_double()
+        loc = np.zeros(self.n_src)
+        _check(self.L.celeste_elbo(self.h, _p(th), precision, C.byref(tot), _p(loc)))
+        return tot.value, loc
+
+    def elbo_grad(self, theta, precision=FP64):
+        th = self._theta(theta)
+        tot = C.c_double()
+        loc = np.zeros(self.n_src)
+        g = np.zeros((self.n_src, NPARAM))
+        _check(self.L.celeste_elbo_grad(self.h, _p(th), precision, C.byref(tot), _p(loc), _p(g)))
+        return tot.value, loc, g
+
+    def hess(self, theta, precision=FP64):
+        th = self._theta(theta)
+        loc = np.zeros(self.n_src)
+        g = np.zeros((self.n_src, NPARAM))
+        h = np.zeros((self.n_src, NPARAM, NPARAM))
+        _check(self.L.celeste_hess(self.h, _p(th), precision, _p(loc), _p(g), _p(h)))
+        return loc, g, h
+
+    def fit(self, theta, which=None, **opts):
+        th = self._theta(theta).copy()
+        w = None if which is None else np.ascontiguousarray(which, np.int32)
+        it = np.zeros(self.n_src, np.int32)
+        st = np.zeros(self.n_src, np.int32)
+        el = C.c_double()
+        o = fit_options(**opts)
+        _check(self.L.celeste_fit_sources(self.h, _p(th), _p(w), 0 if w is None else len(w),
+                                          C.byref(o), _p(it), _p(st), C.byref(el)))
+        return th, it, st, el.value
+
+    # ---- device-pointer calls (torch tensors on the problem's device)
+    @staticmethod
+    def _stream():
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    @staticmethod
+    def _dp(t):
+        if t is None:
+            return None
+        assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous()
+        return C.c_void_p(t.data_ptr())
+
+    def elbo_device(self, d_theta, d_total, d_local=None, precision=FP32):
+        _check(self.L.celeste_elbo_device(self.h, self._dp(d_theta), precision, self._dp(d_total),
+                                          self._dp(d_local), self._stream()))
+
+    def elbo_grad_device(self, d_theta, d_total, d_local, d_grad, precision=FP32):
+        _check(self.L.celeste_elbo_grad_device(self.h, self._dp(d_theta), precision,
+                                               self._dp(d_total), self._dp(d_local),
+                                               self._dp(d_grad), self._stream()))
+
+    def hess_device(self, d_theta, d_local, d_grad, d_hess, precision=FP32):
+        _check(self.L.celeste_hess_device(self.h, self._dp(d_theta), precision, self._dp(d_local),
+                                          self._dp(d_grad), self._dp(d_hess), self._stream()))
+
+    def profile(self, on=True):
+        _check(self.L.celeste_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{stage: (total ms, launches)} since the last read."""
+        mx = 32
+        names = C.create_string_buffer(32 * mx)
+        ms = np.zeros(mx)
+        n_l = np.zeros(mx, np.int32)
+        n = self.L.celeste_profile_read(self.h, mx, names, _p(ms), _p(n_l))
+        if n < 0:
+            _check(n)
+        raw = names.raw
+        return {raw[32 * k:32 * k + 32].split(b"\0")[0].decode(): (float(ms[k]), int(n_l[k]))
+                for k in range(n)}
+
+    def device_status(self):
+        return int(self.L.celeste_device_status(self.h))

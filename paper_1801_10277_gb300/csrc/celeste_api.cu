@@ -1,0 +1,580 @@
+// C ABI of libceleste: problem creation (validation, device copies, work lists) and
+// the ELBO / gradient / Hessian / fit entry points declared in celeste.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace cel;
+
+namespace {
+
+thread_local std::string g_err;
+
+celeste_status fail(celeste_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+celeste_status cuda_fail(cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(CELESTE_ERR_NOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(CELESTE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CEL_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// 2x2 / 4x4 symmetric positive-definiteness and inverse by Cholesky
+bool chol_inverse4(const double* S, double* inv, double* logdet) {
+    double L[4][4] = {{0}};
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = S[4 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    double ld = 0;
+    for (int i = 0; i < 4; ++i) ld += 2.0 * log(L[i][i]);
+    *logdet = ld;
+    // inverse of L, then L^-T L^-1
+    double Li[4][4] = {{0}};
+    for (int i = 0; i < 4; ++i) {
+        Li[i][i] = 1.0 / L[i][i];
+        for (int j = 0; j < i; ++j) {
+            double s = 0;
+            for (int k = j; k < i; ++k) s -= L[i][k] * Li[k][j];
+            Li[i][j] = s / L[i][i];
+        }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double s = 0;
+            for (int k = std::max(i, j); k < 4; ++k) s += Li[k][i] * Li[k][j];
+            inv[4 * i + j] = s;
+        }
+    return true;
+}
+
+template <class T>
+celeste_status upload(T** dst, const T* src, size_t n) {
+    *dst = nullptr;
+    if (n == 0) return CELESTE_OK;
+    CEL_CUDA(cudaMalloc((void**)dst, n * sizeof(T)));
+    CEL_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return CELESTE_OK;
+}
+
+}  // namespace
+
+struct celeste_problem {
+    int device = 0;
+    DevProblem P{};
+    cudaStream_t stream = nullptr;       // stream of the host-pointer entry points
+    cudaStream_t last_stream = nullptr;  // stream of the last enqueued call
+    // host copies used by the fit driver and validation
+    std::vector<int32_t> patch_off, nbr_off, nbrs;
+    std::vector<PatchGeo> geo;
+    std::vector<ImgMeta> imgs;
+    // device buffers owned by the problem
+    std::vector<void*> owned;
+    double* d_theta = nullptr;
+    double* d_out = nullptr;     // total(1) | local(n_src) | grad(n_src*44) | hess(n_src*44*44)
+    size_t out_cap = 0;
+    // per-kernel CUDA-event timing (celeste_profile_*)
+    bool profile = false;
+    struct Rec { std::string name; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int32_t> launches;
+};
+
+namespace {
+
+celeste_status dalloc(celeste_problem* pr, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    pr->owned.push_back(*p);
+    return CELESTE_OK;
+}
+
+template <class T>
+celeste_status dupload(celeste_problem* pr, T** dst, const T* src, size_t n) {
+    void* p;
+    celeste_status st = dalloc(pr, &p, n * sizeof(T));
+    if (st) return st;
+    *dst = (T*)p;
+    if (n) CEL_CUDA(cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return CELESTE_OK;
+}
+
+bool psd2(double xx, double xy, double yy) { return xx > 0 && yy > 0 && xx * yy - xy * xy > 0; }
+
+cudaEvent_t take_event(celeste_problem* pr) {
+    if (!pr->pool.empty()) {
+        cudaEvent_t e = pr->pool.back();
+        pr->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run a launcher; with profiling on, bracket it with events on the launch stream.
+template <class F>
+cudaError_t timed(celeste_problem* pr, const char* name, cudaStream_t st, F&& f) {
+    if (!pr->profile) return f();
+    cudaEvent_t a = take_event(pr), b = take_event(pr);
+    cudaEventRecord(a, st);
+    cudaError_t e = f();
+    cudaEventRecord(b, st);
+    pr->pending.push_back({name, a, b});
+    return e;
+}
+
+celeste_status check_theta_host(const double* theta, int n_src) {
+    for (int s = 0; s < n_src; ++s) {
+        const double* th = theta + (size_t)NP * s;
+        for (int i = 0; i < NP; ++i)
+            if (!isfinite(th[i])) return fail(CELESTE_ERR_NONFINITE, "theta[%d][%d] is not finite", s, i);
+        if (!(th[P_EDEV] >= 0 && th[P_EDEV] <= 1)) return fail(CELESTE_ERR_ARG, "theta[%d]: e_dev outside [0,1]", s);
+        if (!(th[P_AXIS] > 0 && th[P_AXIS] <= 1)) return fail(CELESTE_ERR_ARG, "theta[%d]: e_axis outside (0,1]", s);
+        if (!(th[P_SCALE] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: e_scale <= 0", s);
+        for (int i = 0; i < 2; ++i) {
+            if (!(th[P_R2 + i] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: r2 <= 0", s);
+            if (!(th[P_A + i] > 0 && th[P_A + i] < 1)) return fail(CELESTE_ERR_ARG, "theta[%d]: a outside (0,1)", s);
+            for (int j = 0; j < 4; ++j)
+                if (!(th[P_C2 + 4 * i + j] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: c2 <= 0", s);
+            for (int d = 0; d < NCOMP; ++d)
+                if (!(th[P_K + NCOMP * i + d] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: k <= 0", s);
+        }
+    }
+    return CELESTE_OK;
+}
+
+celeste_status ensure_out(celeste_problem* pr) {
+    size_t need = 1 + (size_t)pr->P.n_src * (1 + NP + NP * NP);
+    if (pr->out_cap >= need) return CELESTE_OK;
+    void* p;
+    celeste_status st = dalloc(pr, &p, need * sizeof(double));
+    if (st) return st;
+    pr->d_out = (double*)p;
+    pr->out_cap = need;
+    return CELESTE_OK;
+}
+
+celeste_status run(celeste_problem* pr, const double* d_theta, int precision, int mode,
+                   double* d_total, double* d_local, double* d_grad, double* d_hess,
+                   cudaStream_t st) {
+    if (precision != CELESTE_FP64 && precision != CELESTE_FP32_ACC64)
+        return fail(CELESTE_ERR_ARG, "precision must be CELESTE_FP64 or CELESTE_FP32_ACC64");
+    CEL_CUDA(cudaSetDevice(pr->device));
+    pr->last_stream = st;
+    const DevProblem& P = pr->P;
+    CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
+    CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st); }));
+    CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
+    if (mode == MODE_HESS)
+        CEL_CUDA(timed(pr, "hess_adjoint", st, [&] { return launch_hess_pixels(P, precision, st); }));
+    else
+        CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
+                       [&] { return launch_adjoint(P, precision, mode, st); }));
+    CEL_CUDA(timed(pr, "finalize", st, [&] {
+        return launch_finalize(P, d_theta, mode, d_total, d_local, d_grad, d_hess, st);
+    }));
+    return CELESTE_OK;
+}
+
+celeste_status run_host(celeste_problem* pr, const double* theta, int precision, int mode,
+                        double* total, double* local, double* grad, double* hess) {
+    if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
+    celeste_status s = check_theta_host(theta, pr->P.n_src);
+    if (s) return s;
+    s = ensure_out(pr);
+    if (s) return s;
+    const int n = pr->P.n_src;
+    double* o_total = pr->d_out;
+    double* o_local = o_total + 1;
+    double* o_grad = o_local + n;
+    double* o_hess = o_grad + (size_t)n * NP;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice,
+                             pr->stream));
+    s = run(pr, pr->d_theta, precision, mode, o_total, o_local,
+            mode >= MODE_GRAD ? o_grad : nullptr, mode >= MODE_HESS ? o_hess : nullptr, pr->stream);
+    if (s) return s;
+    if (total) CEL_CUDA(cudaMemcpyAsync(total, o_total, sizeof(double), cudaMemcpyDeviceToHost, pr->stream));
+    if (local) CEL_CUDA(cudaMemcpyAsync(local, o_local, sizeof(double) * n, cudaMemcpyDeviceToHost, pr->stream));
+    if (grad && mode >= MODE_GRAD)
+        CEL_CUDA(cudaMemcpyAsync(grad, o_grad, sizeof(double) * n * NP, cudaMemcpyDeviceToHost, pr->stream));
+    if (hess && mode >= MODE_HESS)
+        CEL_CUDA(cudaMemcpyAsync(hess, o_hess, sizeof(double) * n * NP * NP, cudaMemcpyDeviceToHost, pr->stream));
+    CEL_CUDA(cudaStreamSynchronize(pr->stream));
+    if (total && !isfinite(*total)) return fail(CELESTE_ERR_NONFINITE, "ELBO is not finite");
+    return CELESTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* celeste_last_error(void) { return g_err.c_str(); }
+
+int64_t celeste_source_pixels(const celeste_problem* pr) { return pr ? pr->P.n_sp : 0; }
+
+void celeste_problem_destroy(celeste_problem* pr) {
+    if (!pr) return;
+    cudaSetDevice(pr->device);
+    if (pr->stream) cudaStreamSynchronize(pr->stream);
+    cudaDeviceSynchronize();
+    for (auto& r : pr->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : pr->pool) cudaEventDestroy(e);
+    for (void* p : pr->owned) cudaFree(p);
+    if (pr->stream) cudaStreamDestroy(pr->stream);
+    delete pr;
+}
+
+celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
+                                      const celeste_model* model, int32_t n_src,
+                                      const int32_t* patch_offsets, const celeste_patch* patches,
+                                      const int32_t* nbr_offsets, const int32_t* nbrs,
+                                      celeste_problem** out) {
+    if (!out) return fail(CELESTE_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (n_img <= 0 || !imgs) return fail(CELESTE_ERR_ARG, "need at least one image");
+    if (n_src < 0 || !model || !patch_offsets || !nbr_offsets)
+        return fail(CELESTE_ERR_ARG, "null model / offsets or negative n_src");
+    // ---- model
+    if (model->n_exp < 1 || model->n_dev < 1 || model->n_exp + model->n_dev > MAXPROF ||
+        !model->exp_mix || !model->dev_mix)
+        return fail(CELESTE_ERR_ARG, "profile mixtures: need 1 <= n_exp, n_dev and n_exp + n_dev <= %d", MAXPROF);
+    if (model->n_color_comp != NCOMP || !model->prior_c || !model->prior_r)
+        return fail(CELESTE_ERR_ARG, "colour prior must have %d components per type", NCOMP);
+    if (!(model->prior_star > 0 && model->prior_star < 1))
+        return fail(CELESTE_ERR_ARG, "prior_star outside (0,1)");
+    ModelDev md{};
+    md.n_exp = model->n_exp;
+    md.n_dev = model->n_dev;
+    for (int j = 0; j < model->n_exp + model->n_dev; ++j) {
+        const double* m = j < model->n_exp ? model->exp_mix + 2 * j : model->dev_mix + 2 * (j - model->n_exp);
+        if (!(m[0] >= 0 && isfinite(m[0]) && m[1] > 0 && isfinite(m[1])))
+            return fail(CELESTE_ERR_ARG, "profile component %d: weight >= 0 and variance > 0 required", j);
+        md.prof_w[j] = m[0];
+        md.prof_nu[j] = m[1];
+    }
+    md.prior_star = model->prior_star;
+    for (int i = 0; i < 2; ++i) {
+        md.prior_r[i][0] = model->prior_r[2 * i];
+        md.prior_r[i][1] = model->prior_r[2 * i + 1];
+        if (!(md.prior_r[i][1] > 0) || !isfinite(md.prior_r[i][0]))
+            return fail(CELESTE_ERR_ARG, "prior_r variance must be > 0");
+        for (int d = 0; d < NCOMP; ++d) {
+            const double* pc = model->prior_c + (size_t)(i * NCOMP + d) * 21;
+            if (!(pc[0] > 0)) return fail(CELESTE_ERR_ARG, "colour prior weight must be > 0");
+            md.prior_w[i][d] = pc[0];
+            for (int j = 0; j < 4; ++j) md.prior_mu[i][d][j] = pc[1 + j];
+            if (!chol_inverse4(pc + 5, md.prior_P[i][d], &md.prior_logdet[i][d]))
+                return fail(CELESTE_ERR_NOT_PD, "colour prior covariance (%d,%d) not positive definite", i, d);
+        }
+    }
+    // ---- images
+    std::vector<ImgMeta> im(n_img);
+    int64_t n_px = 0;
+    bool any_sky_map = false;
+    int npsf_max = 0;
+    for (int n = 0; n < n_img; ++n) {
+        const celeste_image& I = imgs[n];
+        if (I.band < 0 || I.band > 4) return fail(CELESTE_ERR_ARG, "image %d: band must be 0..4", n);
+        if (I.height <= 0 || I.width <= 0 || !I.pixels) return fail(CELESTE_ERR_ARG, "image %d: bad size or pixels", n);
+        if (I.n_psf < 1 || I.n_psf > MAXPSF || !I.psf) return fail(CELESTE_ERR_ARG, "image %d: n_psf must be 1..%d", n, MAXPSF);
+        if (!(I.nmgy_per_count > 0) || !isfinite(I.nmgy_per_count)) return fail(CELESTE_ERR_ARG, "image %d: calibration must be > 0", n);
+        if (!I.sky_map && !(I.sky > 0 && isfinite(I.sky))) return fail(CELESTE_ERR_ARG, "image %d: sky must be > 0", n);
+        const double detA = I.wcs[0] * I.wcs[3] - I.wcs[1] * I.wcs[2];
+        for (int k = 0; k < 6; ++k)
+            if (!isfinite(I.wcs[k])) return fail(CELESTE_ERR_ARG, "image %d: wcs not finite", n);
+        if (detA == 0) return fail(CELESTE_ERR_ARG, "image %d: singular wcs", n);
+        ImgMeta& M = im[n];
+        memset(&M, 0, sizeof M);
+        M.px_off = n_px;
+        M.H = I.height;
+        M.W = I.width;
+        M.band = I.band;
+        M.npsf = I.n_psf;
+        M.has_sky_map = I.sky_map != nullptr;
+        any_sky_map = any_sky_map || M.has_sky_map;
+        M.sky = I.sky;
+        M.iota = 1.0 / I.nmgy_per_count;
+        for (int k = 0; k < 4; ++k) M.A[k] = I.wcs[k];
+        M.t[0] = I.wcs[4];
+        M.t[1] = I.wcs[5];
+        for (int k = 0; k < I.n_psf; ++k) {
+            const double* ps = I.psf + 6 * k;
+            for (int c = 0; c < 6; ++c) {
+                if (!isfinite(ps[c])) return fail(CELESTE_ERR_ARG, "image %d psf %d not finite", n, k);
+                M.psf[k][c] = ps[c];
+            }
+            if (!psd2(ps[3], ps[4], ps[5])) return fail(CELESTE_ERR_NOT_PD, "image %d psf %d covariance not positive definite", n, k);
+        }
+        npsf_max = std::max(npsf_max, (int)I.n_psf);
+        n_px += (int64_t)I.height * I.width;
+    }
+    // ---- patches, work items, tiles
+    if (patch_offsets[0] != 0) return fail(CELESTE_ERR_ARG, "patch_offsets[0] must be 0");
+    for (int s = 0; s < n_src; ++s)
+        if (patch_offsets[s + 1] < patch_offsets[s]) return fail(CELESTE_ERR_ARG, "patch_offsets must be non-decreasing");
+    const int n_patch = patch_offsets[n_src];
+    if (n_patch > 0 && !patches) return fail(CELESTE_ERR_ARG, "patches is null");
+    std::vector<PatchGeo> geo(n_patch);
+    std::vector<WorkItem> items;
+    int64_t n_sp = 0;
+    for (int s = 0; s < n_src; ++s)
+        for (int p = patch_offsets[s]; p < patch_offsets[s + 1]; ++p) {
+            const celeste_patch& c = patches[p];
+            if (c.image < 0 || c.image >= n_img) return fail(CELESTE_ERR_ARG, "patch %d: bad image", p);
+            const ImgMeta& M = im[c.image];
+            if (c.w <= 0 || c.h <= 0 || c.x0 < 0 || c.y0 < 0 || c.x0 + c.w > M.W || c.y0 + c.h > M.H)
+                return fail(CELESTE_ERR_ARG, "patch %d lies outside image %d", p, c.image);
+            PatchGeo& g = geo[p];
+            g.img = c.image; g.x0 = c.x0; g.y0 = c.y0; g.w = c.w; g.h = c.h; g.src = s;
+            g.sp_off = n_sp;
+            g.item0 = (int)items.size();
+            const int npx = c.w * c.h;
+            for (int q0 = 0; q0 < npx; q0 += CHUNK) items.push_back({p, q0, std::min(CHUNK, npx - q0), s});
+            g.nitem = (int)items.size() - g.item0;
+            n_sp += npx;
+        }
+    // tiles: per image a dense grid of TILE x TILE cells, each with its covering patches
+    std::vector<Tile> tiles;
+    std::vector<int32_t> tile_list;
+    {
+        std::vector<std::vector<int32_t>> per_img(n_img);   // patch ids per image in order
+        for (int p = 0; p < n_patch; ++p) per_img[geo[p].img].push_back(p);
+        for (int n = 0; n < n_img; ++n) {
+            if (per_img[n].empty()) continue;
+            const int tw = (im[n].W + TILE - 1) / TILE, th = (im[n].H + TILE - 1) / TILE;
+            std::vector<std::vector<int32_t>> cell((size_t)tw * th);
+            for (int p : per_img[n]) {
+                const PatchGeo& g = geo[p];
+                for (int ty = g.y0 / TILE; ty <= (g.y0 + g.h - 1) / TILE; ++ty)
+                    for (int tx = g.x0 / TILE; tx <= (g.x0 + g.w - 1) / TILE; ++tx)
+                        cell[(size_t)ty * tw + tx].push_back(p);
+            }
+            for (int ty = 0; ty < th; ++ty)
+                for (int tx = 0; tx < tw; ++tx) {
+                    auto& c = cell[(size_t)ty * tw + tx];
+                    if (c.empty()) continue;
+                    Tile t{};
+                    t.img = n; t.x0 = tx * TILE; t.y0 = ty * TILE;
+                    t.list_off = (int)tile_list.size(); t.list_n = (int)c.size();
+                    tile_list.insert(tile_list.end(), c.begin(), c.end());
+                    tiles.push_back(t);
+                }
+        }
+    }
+    // neighbours
+    if (nbr_offsets[0] != 0) return fail(CELESTE_ERR_ARG, "nbr_offsets[0] must be 0");
+    const int n_edge = nbr_offsets[n_src];
+    if (n_edge > 0 && !nbrs) return fail(CELESTE_ERR_ARG, "nbrs is null");
+    for (int s = 0; s < n_src; ++s) {
+        if (nbr_offsets[s + 1] < nbr_offsets[s]) return fail(CELESTE_ERR_ARG, "nbr_offsets must be non-decreasing");
+        for (int e = nbr_offsets[s]; e < nbr_offsets[s + 1]; ++e)
+            if (nbrs[e] < 0 || nbrs[e] >= n_src || nbrs[e] == s) return fail(CELESTE_ERR_ARG, "bad neighbour of source %d", s);
+    }
+
+    celeste_problem* pr = new (std::nothrow) celeste_problem();
+    if (!pr) return fail(CELESTE_ERR_NOMEM, "host allocation failed");
+    auto bail = [&](celeste_status st) { celeste_problem_destroy(pr); return st; };
+    if (cudaGetDevice(&pr->device) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "no CUDA device"));
+    if (cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(CELESTE_ERR_CUDA, "cudaStreamCreate failed"));
+    pr->last_stream = pr->stream;
+    pr->patch_off.assign(patch_offsets, patch_offsets + n_src + 1);
+    pr->nbr_off.assign(nbr_offsets, nbr_offsets + n_src + 1);
+    pr->nbrs.assign(nbrs ? nbrs : nbr_offsets, nbrs ? nbrs + n_edge : nbr_offsets);
+    if (!nbrs) pr->nbrs.clear();
+    pr->geo = geo;
+    pr->imgs = im;
+    DevProblem& P = pr->P;
+    P.n_img = n_img; P.n_src = n_src; P.n_patch = n_patch; P.n_item = (int)items.size();
+    P.n_tile = (int)tiles.size(); P.npsf_max = npsf_max; P.nprof = model->n_exp + model->n_dev;
+    P.n_px = n_px; P.n_sp = n_sp;
+    celeste_status st;
+    // pixels (and optional sky maps) concatenated
+    {
+        void* p;
+        if ((st = dalloc(pr, &p, sizeof(float) * n_px))) return bail(st);
+        P.pixels = (float*)p;
+        void* sm = nullptr;
+        if (any_sky_map) {
+            if ((st = dalloc(pr, &sm, sizeof(float) * n_px))) return bail(st);
+            P.sky_map = (float*)sm;
+        }
+        for (int n = 0; n < n_img; ++n) {
+            const size_t cnt = (size_t)im[n].H * im[n].W;
+            if (cudaMemcpy((float*)p + im[n].px_off, imgs[n].pixels, cnt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(CELESTE_ERR_CUDA, "pixel upload failed"));
+            if (imgs[n].sky_map &&
+                cudaMemcpy((float*)sm + im[n].px_off, imgs[n].sky_map, cnt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(CELESTE_ERR_CUDA, "sky map upload failed"));
+        }
+    }
+    ImgMeta* d_img; PatchGeo* d_geo; WorkItem* d_items; Tile* d_tiles; int32_t* d_tl; int32_t* d_po; ModelDev* d_md;
+    if ((st = dupload(pr, &d_img, im.data(), im.size()))) return bail(st);
+    if ((st = dupload(pr, &d_geo, geo.data(), geo.size()))) return bail(st);
+    if ((st = dupload(pr, &d_items, items.data(), items.size()))) return bail(st);
+    if ((st = dupload(pr, &d_tiles, tiles.data(), tiles.size()))) return bail(st);
+    if ((st = dupload(pr, &d_tl, tile_list.data(), tile_list.size()))) return bail(st);
+    if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
+    if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
+    P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
+    P.patch_off = d_po; P.model = d_md;
+    void* p;
+    if ((st = dalloc(pr, &p, sizeof(double) * TBL_STRIDE * (size_t)n_patch))) return bail(st);
+    P.tbl64 = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(float) * TBL_STRIDE * (size_t)n_patch))) return bail(st);
+    P.tbl32 = (float*)p;
+    if ((st = dalloc(pr, &P.spE, sizeof(double) * (size_t)n_sp))) return bail(st);
+    if ((st = dalloc(pr, &P.spE2, sizeof(double) * (size_t)n_sp))) return bail(st);
+    if ((st = dalloc(pr, &P.emap, sizeof(double) * (size_t)n_px))) return bail(st);
+    if ((st = dalloc(pr, &P.vmap, sizeof(double) * (size_t)n_px))) return bail(st);
+    if ((st = dalloc(pr, &p, sizeof(double) * NPART * (size_t)P.n_item))) return bail(st);
+    P.item_part = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_tile))) return bail(st);
+    P.tile_ll = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
+    P.kl = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
+    P.status = (int32_t*)p;
+    if (cudaMemset(P.status, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
+    if ((st = dalloc(pr, &p, sizeof(double) * NP * (size_t)n_src))) return bail(st);
+    pr->d_theta = (double*)p;
+    if ((st = ensure_out(pr))) return bail(st);
+    *out = pr;
+    return CELESTE_OK;
+}
+
+celeste_status celeste_elbo(celeste_problem* pr, const double* theta, int32_t precision,
+                            double* elbo_total, double* elbo_per_source) {
+    return run_host(pr, theta, precision, MODE_LL, elbo_total, elbo_per_source, nullptr, nullptr);
+}
+
+celeste_status celeste_elbo_grad(celeste_problem* pr, const double* theta, int32_t precision,
+                                 double* elbo_total, double* elbo_per_source, double* grad) {
+    return run_host(pr, theta, precision, MODE_GRAD, elbo_total, elbo_per_source, grad, nullptr);
+}
+
+celeste_status celeste_hess(celeste_problem* pr, const double* theta, int32_t precision,
+                            double* elbo_per_source, double* grad, double* hess) {
+    return run_host(pr, theta, precision, MODE_HESS, nullptr, elbo_per_source, grad, hess);
+}
+
+static celeste_status run_device(celeste_problem* pr, const double* d_theta, int precision,
+                                 int mode, double* d_total, double* d_local, double* d_grad,
+                                 double* d_hess, void* stream) {
+    if (!pr || !d_theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
+    cudaStream_t st = (cudaStream_t)stream;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    CEL_CUDA(cudaMemsetAsync(pr->P.status, 0, sizeof(int32_t), st));
+    CEL_CUDA(launch_check_theta(pr->P, d_theta, st));
+    return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
+}
+
+celeste_status celeste_elbo_device(celeste_problem* pr, const double* d_theta, int32_t precision,
+                                   double* d_total, double* d_local, void* stream) {
+    return run_device(pr, d_theta, precision, MODE_LL, d_total, d_local, nullptr, nullptr, stream);
+}
+
+celeste_status celeste_elbo_grad_device(celeste_problem* pr, const double* d_theta,
+                                        int32_t precision, double* d_total, double* d_local,
+                                        double* d_grad, void* stream) {
+    if (!d_grad) return fail(CELESTE_ERR_ARG, "d_grad is null");
+    return run_device(pr, d_theta, precision, MODE_GRAD, d_total, d_local, d_grad, nullptr, stream);
+}
+
+celeste_status celeste_hess_device(celeste_problem* pr, const double* d_theta, int32_t precision,
+                                   double* d_local, double* d_grad, double* d_hess, void* stream) {
+    if (!d_hess) return fail(CELESTE_ERR_ARG, "d_hess is null");
+    return run_device(pr, d_theta, precision, MODE_HESS, nullptr, d_local, d_grad, d_hess, stream);
+}
+
+celeste_status celeste_profile_enable(celeste_problem* pr, int32_t on) {
+    if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    pr->profile = on != 0;
+    return CELESTE_OK;
+}
+
+int32_t celeste_profile_read(celeste_problem* pr, int32_t max_kernels, char* names,
+                             double* ms_total, int32_t* launches) {
+    if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    cudaSetDevice(pr->device);
+    for (auto& r : pr->pending) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(CELESTE_ERR_CUDA, "event sync");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        size_t k = 0;
+        while (k < pr->names.size() && pr->names[k] != r.name) ++k;
+        if (k == pr->names.size()) {
+            pr->names.push_back(r.name);
+            pr->ms.push_back(0.0);
+            pr->launches.push_back(0);
+        }
+        pr->ms[k] += t;
+        pr->launches[k] += 1;
+        pr->pool.push_back(r.a);
+        pr->pool.push_back(r.b);
+    }
+    pr->pending.clear();
+    const int n = (int)pr->names.size();
+    for (int k = 0; k < n && k < max_kernels; ++k) {
+        if (names) {
+            strncpy(names + 32 * k, pr->names[k].c_str(), 31);
+            names[32 * k + 31] = 0;
+        }
+        if (ms_total) ms_total[k] = pr->ms[k];
+        if (launches) launches[k] = pr->launches[k];
+    }
+    pr->names.clear();
+    pr->ms.clear();
+    pr->launches.clear();
+    return n;
+}
+
+celeste_status celeste_device_status(celeste_problem* pr) {
+    if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    CEL_CUDA(cudaSetDevice(pr->device));
+    CEL_CUDA(cudaStreamSynchronize(pr->last_stream));
+    int32_t v = 0;
+    CEL_CUDA(cudaMemcpy(&v, pr->P.status, sizeof v, cudaMemcpyDeviceToHost));
+    if (v != 0) return fail(v, "device-side check failed with status %d", v);
+    return CELESTE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal layout shared by the CUDA translation units of libceleste (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "celeste.h"
+
+namespace cel {
+
+constexpr int NP = CELESTE_NPARAM;      // 44 constrained parameters per source
+constexpr int NT = CELESTE_NFREE;       // 41 free parameters (trust-region coordinates)
+constexpr int MAXPSF = CELESTE_MAX_PSF;
+constexpr int MAXPROF = CELESTE_MAX_PROFILE;
+constexpr int NCOMP = CELESTE_NPRIOR_COMP;
+
+// constrained parameter indices (see celeste.h)
+enum : int { P_U = 0, P_EDEV = 2, P_AXIS = 3, P_ANGLE = 4, P_SCALE = 5, P_R1 = 6, P_R2 = 8,
+             P_C1 = 10, P_C2 = 18, P_A = 26, P_K = 28 };
+
+// Per (source, image) the pixel terms depend on theta only through twelve
+// intermediate variables y; the kernels differentiate wrt y and a per-source
+// epilogue applies the chain rule dy/dtheta.
+enum : int { Y_A0 = 0, Y_A1, Y_EL0, Y_EL20, Y_EL1, Y_EL21, Y_MX, Y_MY, Y_EDEV, Y_GXX, Y_GXY,
+             Y_GYY, NY };
+constexpr int NYH = NY * (NY + 1) / 2;   // packed upper triangle of the y-Hessian
+
+// Work-item partial record (doubles): [0] sum of ll over the item's pixels,
+// [1..NY] gradient wrt y, [1+NY ..) packed y-Hessian (Hessian mode only).
+constexpr int PART_LL = 0, PART_G = 1, PART_H = 1 + NY;
+constexpr int NPART = 1 + NY + NYH;
+
+// Mixture table of one (source, patch), in units of the pixel precision R:
+//   header [0..7]: a0 a1 E[l|star] E[l^2|star] E[l|gal] E[l^2|gal] iota 0
+//   means  [8..15]: pixel-frame mean of PSF component k (x, y)
+//   star   [16 + 8k]: qa qb qc qd pxx pxy pyy c
+//   galaxy [48 + 12 (k nprof + j)]: qa qb qc qd pxx pxy pyy c dc nu 0 0
+// Component density: c * exp2(qa dx^2 + qb dx dy + qc dy^2 + qd) with
+// (qa, qb, qc) = -log2(e) (Pxx/2, Pxy, Pyy/2) and qd = -log2(2 pi sqrt(det C)).
+constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_GAL = 48, GAL_STRIDE = 12;
+constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 816
+constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
+
+constexpr int CHUNK = 256;   // pixels per work item (one CTA)
+constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
+
+struct ImgMeta {
+    int64_t px_off;          // offset of the image in the concatenated pixel / map buffers
+    int32_t H, W, band, npsf;
+    int32_t has_sky_map, pad;
+    double sky, iota;
+    double A[4], t[2];
+    double psf[MAXPSF][6];
+};
+
+struct PatchGeo {
+    int32_t img, x0, y0, w, h, src;
+    int64_t sp_off;          // offset in the per-(source, pixel) buffers
+    int32_t item0, nitem;    // work items covering this patch
+};
+
+struct WorkItem {
+    int32_t patch, q0, n, src;
+};
+
+struct Tile {
+    int32_t img, x0, y0, list_off, list_n, pad[3];
+};
+
+struct ModelDev {
+    int32_t n_exp, n_dev;
+    double prof_w[MAXPROF], prof_nu[MAXPROF];
+    double prior_star;
+    double prior_r[2][2];
+    double prior_w[2][NCOMP];
+    double prior_mu[2][NCOMP][4];
+    double prior_P[2][NCOMP][16];     // inverse covariances
+    double prior_logdet[2][NCOMP];
+};
+
+// colour coefficient beta_bj: log l_b = log r + sum_j beta_bj c_j, colours c_j the
+// log ratio of band j+1 to band j and r the reference (r, index 2) band brightness.
+__host__ __device__ inline double color_beta(int band, int j) {
+    const int ref = 2;
+    if (band < ref) return (j >= band && j < ref) ? -1.0 : 0.0;
+    if (band > ref) return (j >= ref && j < band) ? 1.0 : 0.0;
+    return 0.0;
+}
+
+__host__ __device__ inline int yh_index(int a, int b) {   // packed upper triangle, a <= b
+    return a * NY - (a * (a - 1)) / 2 + (b - a);
+}
+
+// ---------------------------------------------------------------------------------
+// launchers (pixel_kernels.cu, source_kernels.cu)
+
+enum Mode : int { MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2 };
+
+struct DevProblem {
+    int32_t n_img, n_src, n_patch, n_item, n_tile, npsf_max, nprof;
+    int64_t n_px, n_sp;
+    const ImgMeta* img;
+    const float* pixels;
+    const float* sky_map;
+    const PatchGeo* geo;
+    const WorkItem* items;
+    const Tile* tiles;
+    const int32_t* tile_list;
+    const int32_t* patch_off;
+    const ModelDev* model;
+    double* tbl64;
+    float* tbl32;
+    void* spE;
+    void* spE2;
+    void* emap;
+    void* vmap;
+    double* item_part;
+    double* tile_ll;
+    double* kl;
+    int32_t* status;
+};
+
+cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st);
+cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
+                        cudaStream_t st);
+cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);
+cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st);
+cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st);
+cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int mode,
+                            double* d_total, double* d_local, double* d_grad, double* d_hess,
+                            cudaStream_t st);
+
+}  // namespace cel

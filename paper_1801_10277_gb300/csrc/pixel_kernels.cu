@@ -1,0 +1,427 @@
+// Pixel-level kernels of the Celeste ELBO hot path (Section III model, Section VI-B:
+// the cost is proportional to active pixel visits).
+//
+//   k_prep     per (source, patch): brightness moments and the PSF x profile
+//              mixture table (FP64 arithmetic, stored in the pixel precision)
+//   k_contrib  per work item (<= CHUNK pixels of one patch): each source's own
+//              E_s and Var_s at its patch pixels
+//   k_gather   per 16x16 tile of an image: E and Var summed over the sources
+//              whose patches cover the pixel, in ascending source order (no
+//              atomics, deterministic), and the pixel's expected log-likelihood
+//   k_adjoint  per work item: recomputes the mixture terms (nothing stored from
+//              k_contrib but E_s) and accumulates the gradient of the pixel terms
+//              wrt the twelve intermediate variables y of the (source, patch)
+//
+// R = float: mixture and likelihood arithmetic in FP32, warp sums in FP32, every
+// sum across warps in FP64.  R = double: FP64 throughout.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace cel {
+
+namespace {
+
+constexpr double LOG2E = 1.4426950408889634073599246810019;
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
+__device__ __forceinline__ float lg(float x) { return logf(x); }
+__device__ __forceinline__ double lg(double x) { return log(x); }
+
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV per-thread values over the CTA: FP32/FP64 within a warp, FP64 across warps
+// in warp order.  Thread i < NV returns the CTA total of value i.
+template <class R, int NV>
+__device__ __forceinline__ void cta_sum(const R (&v)[NV], double* out) {
+    __shared__ double red[32][NV > 0 ? NV : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        R s = warp_sum(v[i]);
+        if (lane == 0) red[warp][i] = (double)s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void load_table(R* sT, const R* gT, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sT[i] = gT[i];
+    __syncthreads();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Domain check of theta for the device-pointer entry points: writes
+// CELESTE_ERR_ARG / CELESTE_ERR_NONFINITE into the status word; never traps.
+
+__global__ void k_check_theta(const double* __restrict__ theta, int n_src, int32_t* status) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_src) return;
+    const double* th = theta + (size_t)NP * s;
+    bool fin = true;
+    for (int i = 0; i < NP; ++i) fin = fin && isfinite(th[i]);
+    bool ok = th[P_EDEV] >= 0 && th[P_EDEV] <= 1 && th[P_AXIS] > 0 && th[P_AXIS] <= 1 &&
+              th[P_SCALE] > 0;
+    for (int i = 0; i < 2; ++i) {
+        ok = ok && th[P_R2 + i] > 0 && th[P_A + i] > 0 && th[P_A + i] < 1;
+        for (int j = 0; j < 4; ++j) ok = ok && th[P_C2 + 4 * i + j] > 0;
+        for (int d = 0; d < NCOMP; ++d) ok = ok && th[P_K + NCOMP * i + d] > 0;
+    }
+    if (!fin) atomicExch(status, (int32_t)CELESTE_ERR_NONFINITE);
+    else if (!ok) atomicExch(status, (int32_t)CELESTE_ERR_ARG);
+}
+
+// ---------------------------------------------------------------------------------
+// k_prep: one CTA per patch; thread c builds mixture component c.
+//   star component k:        weight alpha_k, mean mu + xi_k, covariance Sigma_k
+//   galaxy component (k, j): weight alpha_k w_j (1 - e_dev) [exp] or alpha_k w_j e_dev [dev],
+//                            covariance Sigma_k + nu_j G,  G = A W A^T,
+//                            W = sigma^2 R(phi) diag(1, rho^2) R(phi)^T
+// Means are stored relative to the patch origin so FP32 differences stay exact.
+
+__global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
+                       const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
+                       int n_patch, int nprof, double* __restrict__ tbl64,
+                       float* __restrict__ tbl32) {
+    const int p = blockIdx.x;
+    if (p >= n_patch) return;
+    const PatchGeo g = geo[p];
+    const ImgMeta& im = img[g.img];
+    const double* th = theta + (size_t)NP * g.src;
+    const double* A = im.A;
+    const double mux = A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0;
+    const double muy = A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0;
+    // world-frame ellipse W = Ah + Bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi)
+    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE], edev = th[P_EDEV];
+    const double ah = 0.5 * sg * sg * (1.0 + rho * rho), bh = 0.5 * sg * sg * (1.0 - rho * rho);
+    double s2, c2;
+    sincos(2.0 * phi, &s2, &c2);
+    const double wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
+    const double gxx = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+    const double gxy = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+    const double gyy = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
+    double* T64 = tbl64 ? tbl64 + (size_t)p * TBL_STRIDE : nullptr;
+    float* T32 = tbl32 ? tbl32 + (size_t)p * TBL_STRIDE : nullptr;
+    auto put = [&](int i, double v) {
+        if (T64) T64[i] = v;
+        if (T32) T32[i] = (float)v;
+    };
+    const int npsf = im.npsf;
+    if (threadIdx.x == 0) {
+        // brightness moments in this band: log l | type i ~ N(m, v)
+        for (int i = 0; i < 2; ++i) {
+            double m = th[P_R1 + i], v = th[P_R2 + i];
+            for (int j = 0; j < 4; ++j) {
+                double b = color_beta(im.band, j);
+                m += b * th[P_C1 + 4 * i + j];
+                v += b * b * th[P_C2 + 4 * i + j];
+            }
+            put(i == 0 ? H_EL0 : H_EL1, exp(m + 0.5 * v));
+            put(i == 0 ? H_EL20 : H_EL21, exp(2.0 * m + 2.0 * v));
+        }
+        put(H_A0, th[P_A]);
+        put(H_A1, th[P_A + 1]);
+        put(H_IOTA, im.iota);
+        put(7, 0.0);
+        for (int k = 0; k < MAXPSF; ++k) {
+            put(T_MEAN + 2 * k, k < npsf ? mux + im.psf[k][1] : 0.0);
+            put(T_MEAN + 2 * k + 1, k < npsf ? muy + im.psf[k][2] : 0.0);
+        }
+    }
+    const int per_k = 1 + nprof;
+    for (int c = threadIdx.x; c < npsf * per_k; c += blockDim.x) {
+        const int k = c / per_k, j = c % per_k - 1;
+        const double* ps = im.psf[k];
+        double cxx = ps[3], cxy = ps[4], cyy = ps[5], w = ps[0], dw = 0.0, nu = 0.0;
+        if (j >= 0) {
+            nu = md->prof_nu[j];
+            const bool dev = j >= md->n_exp;
+            cxx += nu * gxx;
+            cxy += nu * gxy;
+            cyy += nu * gyy;
+            w = ps[0] * md->prof_w[j] * (dev ? edev : 1.0 - edev);
+            dw = ps[0] * md->prof_w[j] * (dev ? 1.0 : -1.0);
+        }
+        const double det = cxx * cyy - cxy * cxy;
+        const double pxx = cyy / det, pxy = -cxy / det, pyy = cxx / det;
+        const double qd = -log2(TWO_PI * sqrt(det));
+        const int base = (j < 0) ? T_STAR + k * STAR_STRIDE : T_GAL + (k * nprof + j) * GAL_STRIDE;
+        put(base + 0, -0.5 * LOG2E * pxx);
+        put(base + 1, -LOG2E * pxy);
+        put(base + 2, -0.5 * LOG2E * pyy);
+        put(base + 3, qd);
+        put(base + 4, pxx);
+        put(base + 5, pxy);
+        put(base + 6, pyy);
+        put(base + 7, w);
+        if (j >= 0) {
+            put(base + 8, dw);
+            put(base + 9, nu);
+            put(base + 10, 0.0);
+            put(base + 11, 0.0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// k_contrib: E_s and Var_s of the item's source at each of its pixels.
+//   E_s   = a0 f0 + a1 f1,  f_i = iota E[l_i] g_i
+//   Var_s = sum_i a_i iota^2 E[l_i^2] g_i^2 - E_s^2, evaluated as
+//           sum_i a_i f_i^2 (E[l_i^2]/E[l_i]^2 - 1) + a0 (1-a0) f0^2 + a1 (1-a1) f1^2 - 2 a0 a1 f0 f1
+//   (the same polynomial, rearranged so FP32 does not cancel two large squares).
+
+template <class R>
+__global__ void __launch_bounds__(CHUNK) k_contrib(const WorkItem* __restrict__ items,
+                                                   const PatchGeo* __restrict__ geo,
+                                                   const ImgMeta* __restrict__ img, int nprof,
+                                                   const R* __restrict__ tbl, R* __restrict__ spE,
+                                                   R* __restrict__ spV) {
+    __shared__ R sT[TBL_STRIDE];
+    const WorkItem it = items[blockIdx.x];
+    const PatchGeo g = geo[it.patch];
+    const int npsf = img[g.img].npsf;
+    load_table(sT, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
+    const int t = threadIdx.x;
+    if (t >= it.n) return;
+    const int q = it.q0 + t;
+    const int yy = q / g.w, xx = q - yy * g.w;
+    R g0 = 0, g1 = 0;
+    for (int k = 0; k < npsf; ++k) {
+        const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
+        const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+        const R* S = sT + T_STAR + k * STAR_STRIDE;
+        g0 += S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
+        const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+        for (int j = 0; j < nprof; ++j, G += GAL_STRIDE)
+            g1 += G[7] * ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+    }
+    const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+    const R el0 = sT[H_EL0], el1 = sT[H_EL1];
+    const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+    const R e = a0 * f0 + a1 * f1;
+    const R em0 = sT[H_EL20] / (el0 * el0) - (R)1, em1 = sT[H_EL21] / (el1 * el1) - (R)1;
+    const R v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * ((R)1 - a0) * f0 * f0 +
+                a1 * ((R)1 - a1) * f1 * f1 - (R)2 * a0 * a1 * f0 * f1;
+    spE[g.sp_off + q] = e;
+    spV[g.sp_off + q] = v;
+}
+
+// ---------------------------------------------------------------------------------
+// k_gather: E = sky + sum_s E_s, Var = sum_s Var_s over the sources covering each
+// pixel of a tile (ascending source order), and the expected log-likelihood
+//   ll = x (log E - Var / (2 E^2)) - E      (delta-method reading of E_q[log F])
+// at pixels inside at least one patch.  One FP64 ll sum per tile.
+
+template <class R>
+__global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ tiles,
+                                                       const int32_t* __restrict__ tile_list,
+                                                       const PatchGeo* __restrict__ geo,
+                                                       const ImgMeta* __restrict__ img,
+                                                       const float* __restrict__ pixels,
+                                                       const float* __restrict__ sky_map,
+                                                       const R* __restrict__ spE,
+                                                       const R* __restrict__ spV,
+                                                       R* __restrict__ emap, R* __restrict__ vmap,
+                                                       double* __restrict__ tile_ll) {
+    const Tile tl = tiles[blockIdx.x];
+    const ImgMeta& im = img[tl.img];
+    const int gx = tl.x0 + (int)(threadIdx.x % TILE), gy = tl.y0 + (int)(threadIdx.x / TILE);
+    R ll[1] = {0};
+    if (gx < im.W && gy < im.H) {
+        const int64_t m = im.px_off + (int64_t)gy * im.W + gx;
+        R E = im.has_sky_map ? (R)sky_map[m] : (R)im.sky;
+        R V = 0;
+        bool cov = false;
+        for (int e = 0; e < tl.list_n; ++e) {
+            const PatchGeo g = geo[tile_list[tl.list_off + e]];
+            const int xx = gx - g.x0, yy = gy - g.y0;
+            if (xx >= 0 && xx < g.w && yy >= 0 && yy < g.h) {
+                const int64_t q = g.sp_off + (int64_t)yy * g.w + xx;
+                E += spE[q];
+                V += spV[q];
+                cov = true;
+            }
+        }
+        if (cov) {
+            const R x = (R)pixels[m];
+            const R iE = (R)1 / E;
+            ll[0] = x * (lg(E) - (R)0.5 * V * iE * iE) - E;
+            emap[m] = E;
+            vmap[m] = V;
+        }
+    }
+    double tot[1];
+    cta_sum<R, 1>(ll, tot);
+    if (threadIdx.x == 0) tile_ll[blockIdx.x] = tot[0];
+}
+
+// ---------------------------------------------------------------------------------
+// k_adjoint: per work item, sum over its pixels of ll and of d ll / d y.
+//   c_E = d ll/dE = x (1/E + V/E^3) - 1,   c_V = d ll/dV = -x / (2 E^2)
+//   d ll/dy = (c_E - 2 c_V E_s) dE_s/dy + c_V dE2_s/dy,  E2_s = sum_i a_i iota^2 E[l_i^2] g_i^2
+// Mixture derivatives per component N = c exp(-d'Pd/2)/(2 pi sqrt det C), d = p - mean:
+//   dN/dmean = N P d,  dN/dG_xx = nu N ((Pd)_x^2 - Pxx)/2,  dN/dG_xy = nu N ((Pd)_x (Pd)_y - Pxy),
+//   dN/dG_yy = nu N ((Pd)_y^2 - Pyy)/2,  dN/de_dev = dc exp(...)/(...)
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(CHUNK) k_adjoint(const WorkItem* __restrict__ items,
+                                                   const PatchGeo* __restrict__ geo,
+                                                   const ImgMeta* __restrict__ img, int nprof,
+                                                   const float* __restrict__ pixels,
+                                                   const R* __restrict__ tbl,
+                                                   const R* __restrict__ emap,
+                                                   const R* __restrict__ vmap,
+                                                   double* __restrict__ part) {
+    constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
+    __shared__ R sT[TBL_STRIDE];
+    const WorkItem it = items[blockIdx.x];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int npsf = im.npsf;
+    load_table(sT, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
+    R v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = 0;
+    const int t = threadIdx.x;
+    if (t < it.n) {
+        const int q = it.q0 + t;
+        const int yy = q / g.w, xx = q - yy * g.w;
+        const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+        const R x = (R)pixels[m], E = emap[m], V = vmap[m];
+        const R iE = (R)1 / E;
+        v[0] = x * (lg(E) - (R)0.5 * V * iE * iE) - E;
+        if constexpr (MODE >= MODE_GRAD) {
+            const R cE = x * (iE + V * iE * iE * iE) - (R)1;
+            const R cV = (R)-0.5 * x * iE * iE;
+            R g0 = 0, gx0 = 0, gy0 = 0;
+            R g1 = 0, gx1 = 0, gy1 = 0, de1 = 0, sxx = 0, sxy = 0, syy = 0;
+            for (int k = 0; k < npsf; ++k) {
+                const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
+                const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+                {
+                    const R* S = sT + T_STAR + k * STAR_STRIDE;
+                    const R n = S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
+                    const R qx = S[4] * dx + S[5] * dy, qy = S[5] * dx + S[6] * dy;
+                    g0 += n;
+                    gx0 += n * qx;
+                    gy0 += n * qy;
+                }
+                const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+                for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+                    const R e = ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+                    const R n = G[7] * e;
+                    const R qx = G[4] * dx + G[5] * dy, qy = G[5] * dx + G[6] * dy;
+                    g1 += n;
+                    gx1 += n * qx;
+                    gy1 += n * qy;
+                    de1 += G[8] * e;
+                    const R nn = n * G[9];
+                    sxx += nn * (qx * qx - G[4]);
+                    sxy += nn * (qx * qy - G[5]);
+                    syy += nn * (qy * qy - G[6]);
+                }
+            }
+            const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+            const R el0 = sT[H_EL0], el20 = sT[H_EL20], el1 = sT[H_EL1], el21 = sT[H_EL21];
+            const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+            const R Es = a0 * f0 + a1 * f1;
+            const R w1 = cE - (R)2 * cV * Es, w2 = cV;
+            const R i2 = iota * iota;
+            const R s0 = i2 * g0 * g0, s1 = i2 * g1 * g1;
+            v[1 + Y_A0] = w1 * f0 + w2 * el20 * s0;
+            v[1 + Y_A1] = w1 * f1 + w2 * el21 * s1;
+            v[1 + Y_EL0] = w1 * a0 * iota * g0;
+            v[1 + Y_EL20] = w2 * a0 * s0;
+            v[1 + Y_EL1] = w1 * a1 * iota * g1;
+            v[1 + Y_EL21] = w2 * a1 * s1;
+            const R u0 = a0 * iota * (w1 * el0 + (R)2 * w2 * iota * el20 * g0);
+            const R u1 = a1 * iota * (w1 * el1 + (R)2 * w2 * iota * el21 * g1);
+            v[1 + Y_MX] = u0 * gx0 + u1 * gx1;
+            v[1 + Y_MY] = u0 * gy0 + u1 * gy1;
+            v[1 + Y_EDEV] = u1 * de1;
+            v[1 + Y_GXX] = (R)0.5 * u1 * sxx;
+            v[1 + Y_GXY] = u1 * sxy;
+            v[1 + Y_GYY] = (R)0.5 * u1 * syy;
+        }
+    }
+    double tot[NV];
+    cta_sum<R, NV>(v, tot);
+    if (threadIdx.x < NV) part[(size_t)blockIdx.x * NPART + threadIdx.x] = tot[threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------------
+// launchers
+
+cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st) {
+    if (P.n_src > 0) k_check_theta<<<(P.n_src + 127) / 128, 128, 0, st>>>(d_theta, P.n_src, P.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
+                        cudaStream_t st) {
+    if (P.n_patch == 0) return cudaSuccess;
+    k_prep<<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
+                                     precision == CELESTE_FP64 ? P.tbl64 : nullptr,
+                                     precision == CELESTE_FP64 ? nullptr : P.tbl32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) {
+    if (P.n_item == 0) return cudaSuccess;
+    if (precision == CELESTE_FP64)
+        k_contrib<double><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl64,
+                                                      (double*)P.spE, (double*)P.spE2);
+    else
+        k_contrib<float><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
+                                                     (float*)P.spE, (float*)P.spE2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
+    if (P.n_tile == 0) return cudaSuccess;
+    if (precision == CELESTE_FP64)
+        k_gather<double><<<P.n_tile, TILE * TILE, 0, st>>>(
+            P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const double*)P.spE,
+            (const double*)P.spE2, (double*)P.emap, (double*)P.vmap, P.tile_ll);
+    else
+        k_gather<float><<<P.n_tile, TILE * TILE, 0, st>>>(
+            P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const float*)P.spE,
+            (const float*)P.spE2, (float*)P.emap, (float*)P.vmap, P.tile_ll);
+    return cudaGetLastError();
+}
+
+template <class R>
+static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st) {
+    const R* em = (const R*)P.emap;
+    const R* vm = (const R*)P.vmap;
+    if (mode == MODE_LL)
+        k_adjoint<R, MODE_LL><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof,
+                                                          P.pixels, tbl, em, vm, P.item_part);
+    else
+        k_adjoint<R, MODE_GRAD><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof,
+                                                            P.pixels, tbl, em, vm, P.item_part);
+}
+
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st) {
+    if (P.n_item == 0) return cudaSuccess;
+    if (precision == CELESTE_FP64) adjoint_impl<double>(P, P.tbl64, mode, st);
+    else adjoint_impl<float>(P, P.tbl32, mode, st);
+    return cudaGetLastError();
+}
+
+}  // namespace cel

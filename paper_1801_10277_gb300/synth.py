@@ -418,3 +418,29 @@ def many_fields_sample(seed=2030, n_fields_sampled=1, n_src_per_field=3125, brig
     out = one_field(seed, n_src=n_src_per_field * n_fields_sampled, bright_frac=bright_frac)
     out.name = f"sweep_field_{out.n_src}src_bright{bright_frac}"
     return out
+
+
+def subset(prob, idx):
+    """The sub-problem made of sources `idx` (ascending), their patches and the
+    neighbour relations among them; images and priors are shared."""
+    idx = np.asarray(sorted(int(i) for i in idx))
+    remap = -np.ones(prob.n_src, dtype=np.int64)
+    remap[idx] = np.arange(len(idx))
+    offs = [0]
+    rows = []
+    nb_off = [0]
+    nb = []
+    for s in idx:
+        rows.extend(prob.patches[prob.patch_offsets[s]:prob.patch_offsets[s + 1]].tolist())
+        offs.append(len(rows))
+        for o in prob.nbrs[prob.nbr_offsets[s]:prob.nbr_offsets[s + 1]]:
+            if remap[o] >= 0:
+                nb.append(int(remap[o]))
+        nb_off.append(len(nb))
+    return Problem(images=prob.images, exp_mix=prob.exp_mix, dev_mix=prob.dev_mix,
+                   prior_star=prob.prior_star, prior_r=prob.prior_r, prior_c=prob.prior_c,
+                   theta=prob.theta[idx].copy(), truth=prob.truth[idx].copy(),
+                   patch_offsets=np.array(offs, np.int32),
+                   patches=np.array(rows, np.int32).reshape(-1, 5),
+                   nbr_offsets=np.array(nb_off, np.int32), nbrs=np.array(nb, np.int32),
+                   name=f"{prob.name}_subset{len(idx)}", meta=dict(prob.meta))
