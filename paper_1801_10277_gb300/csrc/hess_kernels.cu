@@ -1,31 +1,522 @@
-// Per-source Hessian kernels (placeholder until the Hessian adjoint lands).
+// Per-source exact Hessians (Section IV-D: Newton steps need the exact 44 x 44
+// Hessian of each source's block).
+//
+//   k_hess           per work item: value, gradient and Hessian of the pixel terms
+//                    wrt the twelve intermediate variables y of the (source, patch);
+//                    the mixture terms are recomputed here, nothing is stored.
+//   k_finalize_hess  one CTA per source: sparse chain rule y -> theta over the
+//                    source's patches, plus the KL Hessian; writes the full
+//                    symmetric 44 x 44 matrix, the gradient and the local objective.
+//
+// With e = dE_s/dy, v = dVar_s/dy = dE2_s/dy - 2 E_s e and the second derivatives
+// DE = d2E_s/dy2, DE2 = d2E2_s/dy2 (E2_s = sum_i a_i iota^2 E[l_i^2] g_i^2):
+//   d2 ll/dy2 = (h_EE - 2 c_V) e e' + h_EV (e v' + v e') + (c_E - 2 c_V E_s) DE + c_V DE2
+//   h_EE = -x (1/E^2 + 3 Var/E^4),  h_EV = x / E^3,  h_VV = 0.
+// Per Gaussian component N (log-density derivatives, q = P d, C = Sigma_psf + nu G):
+//   dlogN/dmu = q,  d2logN/dmu2 = -P,
+//   dlogN/dC[E] = (q'Eq - tr PE)/2,   d2logN/dmu dC[F] = -P F q,
+//   d2logN/dC[E]dC[F] = -q'E P F q + tr(P E P F)/2,   d2N = N (dlogN dlogN' + d2logN).
+#include <math.h>
+
 #include "internal.cuh"
+#include "source_math.cuh"
 
 namespace cel {
 
-cudaError_t launch_hess_pixels(const DevProblem&, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_finalize_hess(const DevProblem&, const double*, double*, double*, double*,
-                                 cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+__device__ __forceinline__ float ex2h(float x) { return exp2f(x); }
+__device__ __forceinline__ double ex2h(double x) { return exp2(x); }
+__device__ __forceinline__ float lgh(float x) { return logf(x); }
+__device__ __forceinline__ double lgh(double x) { return log(x); }
+
+template <class R>
+__device__ __forceinline__ R warp_sum_h(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// packed index of the symmetric 12 x 12 (a <= b not required)
+__device__ __forceinline__ int P2(int a, int b) { return a <= b ? yh_index(a, b) : yh_index(b, a); }
+
+}  // namespace
+
+constexpr int HV = 1 + NY + NYH;   // values reduced per work item
+
+template <class R>
+__global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ items,
+                                                const PatchGeo* __restrict__ geo,
+                                                const ImgMeta* __restrict__ img, int nprof,
+                                                const float* __restrict__ pixels,
+                                                const R* __restrict__ tbl,
+                                                const R* __restrict__ emap,
+                                                const R* __restrict__ vmap,
+                                                double* __restrict__ part) {
+    __shared__ R sT[TBL_STRIDE];
+    __shared__ double red[CHUNK / 32][HV];
+    const WorkItem it = items[blockIdx.x];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int npsf = im.npsf;
+    {
+        const R* gT = tbl + (size_t)it.patch * TBL_STRIDE;
+        const int n = T_GAL + npsf * nprof * GAL_STRIDE;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sT[i] = gT[i];
+        __syncthreads();
+    }
+    R out[HV];
+#pragma unroll
+    for (int i = 0; i < HV; ++i) out[i] = 0;
+    const int t = threadIdx.x;
+    if (t < it.n) {
+        const int q = it.q0 + t;
+        const int yy = q / g.w, xx = q - yy * g.w;
+        const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+        const R x = (R)pixels[m], E = emap[m], V = vmap[m];
+        const R iE = (R)1 / E, iE2 = iE * iE;
+        const R cE = x * (iE + V * iE2 * iE) - (R)1;
+        const R cV = (R)-0.5 * x * iE2;
+        const R hEE = -x * iE2 * ((R)1 + (R)3 * V * iE2);
+        const R hEV = x * iE2 * iE;
+        out[0] = x * (lgh(E) - (R)0.5 * V * iE2) - E;
+        // star: value, gradient (mx, my), Hessian (xx, xy, yy)
+        R g0 = 0, d0[2] = {0, 0}, h0[3] = {0, 0, 0};
+        // galaxy: value; gradient over z5 = (mx, my, Gxx, Gxy, Gyy); e_dev derivative;
+        // Hessian over z5 (packed 15); e_dev x z5
+        R g1 = 0, d1[5] = {0, 0, 0, 0, 0}, de = 0, h1[15], he[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 15; ++i) h1[i] = 0;
+        for (int k = 0; k < npsf; ++k) {
+            const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
+            const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+            {
+                const R* S = sT + T_STAR + k * STAR_STRIDE;
+                const R n = S[7] * ex2h(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
+                const R qx = S[4] * dx + S[5] * dy, qy = S[5] * dx + S[6] * dy;
+                g0 += n;
+                d0[0] += n * qx;
+                d0[1] += n * qy;
+                h0[0] += n * (qx * qx - S[4]);
+                h0[1] += n * (qx * qy - S[5]);
+                h0[2] += n * (qy * qy - S[6]);
+            }
+            const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+                const R e = ex2h(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+                const R n = G[7] * e, ne = G[8] * e;
+                const R pxx = G[4], pxy = G[5], pyy = G[6], nu = G[9];
+                const R qx = pxx * dx + pxy * dy, qy = pxy * dx + pyy * dy;
+                R l[5];
+                l[0] = qx;
+                l[1] = qy;
+                l[2] = (R)0.5 * nu * (qx * qx - pxx);
+                l[3] = nu * (qx * qy - pxy);
+                l[4] = (R)0.5 * nu * (qy * qy - pyy);
+                const R nu2 = nu * nu;
+                const R Pqy_x = pxx * qy + pxy * qx;   // (P (qy, qx))_x
+                const R Pqy_y = pxy * qy + pyy * qx;   // (P (qy, qx))_y
+                R L[15];
+                L[0] = -pxx;                  // (mx, mx)
+                L[1] = -pxy;                  // (mx, my)
+                L[2] = -nu * pxx * qx;        // (mx, Gxx)
+                L[3] = -nu * Pqy_x;           // (mx, Gxy)
+                L[4] = -nu * pxy * qy;        // (mx, Gyy)
+                L[5] = -pyy;                  // (my, my)
+                L[6] = -nu * pxy * qx;        // (my, Gxx)
+                L[7] = -nu * Pqy_y;           // (my, Gxy)
+                L[8] = -nu * pyy * qy;        // (my, Gyy)
+                L[9] = nu2 * ((R)0.5 * pxx * pxx - pxx * qx * qx);                           // (Gxx, Gxx)
+                L[10] = nu2 * (pxx * pxy - qx * Pqy_x);                                      // (Gxx, Gxy)
+                L[11] = nu2 * ((R)0.5 * pxy * pxy - pxy * qx * qy);                          // (Gxx, Gyy)
+                L[12] = nu2 * (pxy * pxy + pxx * pyy - (qy * Pqy_x + qx * Pqy_y));            // (Gxy, Gxy)
+                L[13] = nu2 * (pxy * pyy - qy * Pqy_y);                                      // (Gxy, Gyy)
+                L[14] = nu2 * ((R)0.5 * pyy * pyy - pyy * qy * qy);                          // (Gyy, Gyy)
+                g1 += n;
+                de += ne;
+                int c = 0;
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    d1[a] += n * l[a];
+                    he[a] += ne * l[a];
+#pragma unroll
+                    for (int b = a; b < 5; ++b, ++c) h1[c] += n * (l[a] * l[b] + L[c]);
+                }
+            }
+        }
+        // ---- assemble the pixel's y-derivatives
+        const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+        const R el0 = sT[H_EL0], el20 = sT[H_EL20], el1 = sT[H_EL1], el21 = sT[H_EL21];
+        const R i2 = iota * iota;
+        const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+        const R Es = a0 * f0 + a1 * f1;
+        const R w1 = cE - (R)2 * cV * Es, w2 = cV;
+        // gradient of g_i over y (index 6..11), zero elsewhere
+        R dg0[6] = {d0[0], d0[1], 0, 0, 0, 0};
+        R dg1[6] = {d1[0], d1[1], de, d1[2], d1[3], d1[4]};
+        // e = dE_s/dy, v2 = dE2_s/dy
+        R e[NY], v2[NY];
+        e[Y_A0] = f0;
+        e[Y_A1] = f1;
+        e[Y_EL0] = a0 * iota * g0;
+        e[Y_EL20] = 0;
+        e[Y_EL1] = a1 * iota * g1;
+        e[Y_EL21] = 0;
+        v2[Y_A0] = i2 * el20 * g0 * g0;
+        v2[Y_A1] = i2 * el21 * g1 * g1;
+        v2[Y_EL0] = 0;
+        v2[Y_EL20] = a0 * i2 * g0 * g0;
+        v2[Y_EL1] = 0;
+        v2[Y_EL21] = a1 * i2 * g1 * g1;
+        const R k0 = a0 * iota * el0, k1 = a1 * iota * el1;
+        const R m0 = (R)2 * a0 * i2 * el20, m1 = (R)2 * a1 * i2 * el21;
+#pragma unroll
+        for (int z = 0; z < 6; ++z) {
+            e[Y_MX + z] = k0 * dg0[z] + k1 * dg1[z];
+            v2[Y_MX + z] = m0 * g0 * dg0[z] + m1 * g1 * dg1[z];
+        }
+        // gradient
+#pragma unroll
+        for (int y = 0; y < NY; ++y) out[1 + y] = w1 * e[y] + w2 * v2[y];
+        // Hessian: outer-product part
+        R v[NY];
+#pragma unroll
+        for (int y = 0; y < NY; ++y) v[y] = v2[y] - (R)2 * Es * e[y];
+        const R c1 = hEE - (R)2 * cV;
+        R* H = out + 1 + NY;
+#pragma unroll
+        for (int a = 0; a < NY; ++a)
+#pragma unroll
+            for (int b = a; b < NY; ++b)
+                H[yh_index(a, b)] = c1 * e[a] * e[b] + hEV * (e[a] * v[b] + v[a] * e[b]);
+        // second-derivative part  w1 DE + w2 DE2
+        H[P2(Y_A0, Y_EL0)] += w1 * iota * g0;
+        H[P2(Y_A1, Y_EL1)] += w1 * iota * g1;
+        H[P2(Y_A0, Y_EL20)] += w2 * i2 * g0 * g0;
+        H[P2(Y_A1, Y_EL21)] += w2 * i2 * g1 * g1;
+        const R p0 = w1 * iota * el0 + (R)2 * w2 * i2 * el20 * g0;
+        const R p1 = w1 * iota * el1 + (R)2 * w2 * i2 * el21 * g1;
+        const R u0 = a0 * p0, u1 = a1 * p1;
+        const R b0 = w2 * m0, b1 = w2 * m1;
+#pragma unroll
+        for (int z = 0; z < 6; ++z) {
+            const int yz = Y_MX + z;
+            H[P2(Y_A0, yz)] += p0 * dg0[z];
+            H[P2(Y_A1, yz)] += p1 * dg1[z];
+            H[P2(Y_EL0, yz)] += w1 * a0 * iota * dg0[z];
+            H[P2(Y_EL1, yz)] += w1 * a1 * iota * dg1[z];
+            H[P2(Y_EL20, yz)] += w2 * (R)2 * a0 * i2 * g0 * dg0[z];
+            H[P2(Y_EL21, yz)] += w2 * (R)2 * a1 * i2 * g1 * dg1[z];
+        }
+        // z-z block: u0 d2g0 + b0 dg0 dg0' + u1 d2g1 + b1 dg1 dg1'
+        // d2g1 over (mx, my, edev, Gxx, Gxy, Gyy) from h1 (z5 packed) and he (edev x z5)
+        const int zmap[5] = {0, 1, 3, 4, 5};   // z5 position -> position among the six
+        R d2g1[6][6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = 0; b < 6; ++b) d2g1[a][b] = 0;
+        {
+            int c = 0;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                d2g1[zmap[a]][2] = he[a];
+                d2g1[2][zmap[a]] = he[a];
+#pragma unroll
+                for (int b = a; b < 5; ++b, ++c) {
+                    d2g1[zmap[a]][zmap[b]] = h1[c];
+                    d2g1[zmap[b]][zmap[a]] = h1[c];
+                }
+            }
+        }
+        const R d2g0[3] = {h0[0], h0[1], h0[2]};
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b) {
+                R s = u1 * d2g1[a][b] + b1 * dg1[a] * dg1[b] + b0 * dg0[a] * dg0[b];
+                if (a < 2 && b < 2) s += u0 * d2g0[a + b];
+                H[yh_index(Y_MX + a, Y_MX + b)] += s;
+            }
+    }
+    // ---- CTA reduction: FP32 or FP64 within a warp, FP64 across warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < HV; ++i) {
+        const R s = warp_sum_h(out[i]);
+        if (lane == 0) red[warp][i] = (double)s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < HV; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][i];
+        part[(size_t)blockIdx.x * NPART + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// per-source chain rule and KL Hessian
+
+
+// d2(Gxx, Gxy, Gyy)/d(s_a) d(s_b), s = (e_axis, e_angle, e_scale)
+__device__ void shape_hessian(const double* A, const double* th, double d2G[3][3][3]) {
+    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
+    const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
+    double s2, c2;
+    sincos(2.0 * phi, &s2, &c2);
+    const double bh_r = -sg * sg * rho, bh_s = sg * (1.0 - rho * rho);
+    // second derivatives of ah, bh over (rho, sigma)
+    const double ah_rr = sg * sg, ah_ss = 1.0 + rho * rho, ah_rs = 2.0 * sg * rho;
+    const double bh_rr = -sg * sg, bh_ss = 1.0 - rho * rho, bh_rs = -2.0 * sg * rho;
+    // W = (ah + bh c2, bh s2, ah - bh c2); index order (rho=0, phi=1, sigma=2)
+    double d2W[3][3][3];
+    auto set = [&](int a, int b, double xx, double xy, double yy) {
+        d2W[a][b][0] = d2W[b][a][0] = xx;
+        d2W[a][b][1] = d2W[b][a][1] = xy;
+        d2W[a][b][2] = d2W[b][a][2] = yy;
+    };
+    set(0, 0, ah_rr + bh_rr * c2, bh_rr * s2, ah_rr - bh_rr * c2);
+    set(2, 2, ah_ss + bh_ss * c2, bh_ss * s2, ah_ss - bh_ss * c2);
+    set(0, 2, ah_rs + bh_rs * c2, bh_rs * s2, ah_rs - bh_rs * c2);
+    set(0, 1, -2.0 * bh_r * s2, 2.0 * bh_r * c2, 2.0 * bh_r * s2);
+    set(2, 1, -2.0 * bh_s * s2, 2.0 * bh_s * c2, 2.0 * bh_s * s2);
+    set(1, 1, -4.0 * bh * c2, -4.0 * bh * s2, 4.0 * bh * c2);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double wxx = d2W[a][b][0], wxy = d2W[a][b][1], wyy = d2W[a][b][2];
+            d2G[a][b][0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+            d2G[a][b][1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+            d2G[a][b][2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
+        }
+}
+
+// full KL Hessian (44 x 44, row-major) into H (zeroed by the caller); one thread
+__device__ void kl_hessian(const ModelDev& md, const double* th, double* H) {
+    for (int i = 0; i < 2; ++i) {
+        const double a = th[P_A + i];
+        const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
+        const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
+        const int ia = P_A + i, ir1 = P_R1 + i, ir2 = P_R2 + i;
+        auto add = [&](int p, int q, double v) {
+            H[p * NP + q] += v;
+            if (p != q) H[q * NP + p] += v;
+        };
+        add(ia, ia, 1.0 / a);
+        add(ia, ir1, (r1 - pm) / pv);
+        add(ia, ir2, 0.5 * (1.0 / pv - 1.0 / r2));
+        add(ir1, ir1, a / pv);
+        add(ir2, ir2, a * 0.5 / (r2 * r2));
+        double c1[4], c2[4], slog = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            c1[j] = th[P_C1 + 4 * i + j];
+            c2[j] = th[P_C2 + 4 * i + j];
+            slog += log(c2[j]);
+        }
+        double dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
+        double Pk[16];
+        for (int j = 0; j < 16; ++j) Pk[j] = 0.0;
+        double ksum = 0.0;
+        for (int d = 0; d < NCOMP; ++d) {
+            const double k = th[P_K + NCOMP * i + d];
+            const double* Pm = md.prior_P[i][d];
+            const double* mu = md.prior_mu[i][d];
+            double diff[4], Pd[4], quad = 0.0, tr = 0.0;
+            for (int j = 0; j < 4; ++j) diff[j] = c1[j] - mu[j];
+            for (int j = 0; j < 4; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
+                Pd[j] = s;
+                quad += diff[j] * s;
+                tr += Pm[5 * j] * c2[j];
+            }
+            const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
+            const int ik = P_K + NCOMP * i + d;
+            add(ia, ik, log(k / md.prior_w[i][d]) + 1.0 + klc);
+            add(ik, ik, a / k);
+            for (int j = 0; j < 4; ++j) {
+                add(ik, P_C1 + 4 * i + j, a * Pd[j]);
+                add(ik, P_C2 + 4 * i + j, a * 0.5 * (Pm[5 * j] - 1.0 / c2[j]));
+                dc1[j] += k * Pd[j];
+                dc2[j] += 0.5 * k * (Pm[5 * j] - 1.0 / c2[j]);
+            }
+            for (int j = 0; j < 16; ++j) Pk[j] += k * Pm[j];
+            ksum += k;
+        }
+        for (int j = 0; j < 4; ++j) {
+            add(ia, P_C1 + 4 * i + j, dc1[j]);
+            add(ia, P_C2 + 4 * i + j, dc2[j]);
+            add(P_C2 + 4 * i + j, P_C2 + 4 * i + j, a * 0.5 * ksum / (c2[j] * c2[j]));
+            for (int l = j; l < 4; ++l) add(P_C1 + 4 * i + j, P_C1 + 4 * i + l, a * Pk[4 * j + l]);
+        }
+    }
+}
+
+constexpr int FH_THREADS = 256;
+constexpr int FH_PER = (NP * NP + FH_THREADS - 1) / FH_THREADS;
+
+__global__ void __launch_bounds__(FH_THREADS)
+k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
+                const int32_t* __restrict__ patch_off, const ImgMeta* __restrict__ img,
+                const ModelDev* __restrict__ md, const double* __restrict__ part,
+                double* __restrict__ kl_out, double* __restrict__ local_out,
+                double* __restrict__ grad_out, double* __restrict__ hess_out) {
+    const int s = blockIdx.x;
+    if (s >= n_src) return;
+    const double* th = theta + (size_t)NP * s;
+    __shared__ double Hy[NY][NY];
+    __shared__ double Gy[NY + 1];
+    __shared__ int nzn[NP];
+    __shared__ int nzy[NP][3];
+    __shared__ double nzv[NP][3];
+    __shared__ double dvec[2][NP], evec[2][NP];   // d(m + v/2), d(2m + 2v) per type
+    __shared__ double wd[2], we[2];
+    __shared__ double S2[3][3];
+    __shared__ double klH[NP * NP];
+    __shared__ double klg[NP];
+    __shared__ double klv;
+    const int t = threadIdx.x;
+    for (int i = t; i < NP * NP; i += blockDim.x) klH[i] = 0.0;
+    __syncthreads();
+    if (t == 0) {
+        klv = kl_value_grad(*md, th, klg);
+        kl_hessian(*md, th, klH);
+    }
+    double acc[FH_PER];
+#pragma unroll
+    for (int k = 0; k < FH_PER; ++k) acc[k] = 0.0;
+    double gacc = 0.0, lacc = 0.0;
+    for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
+        __syncthreads();
+        const PatchGeo g = geo[p];
+        const ImgMeta& im = img[g.img];
+        if (t < 1 + NY + NYH) {
+            double v = 0.0;
+            for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
+            if (t == 0) lacc += v;
+            else if (t < 1 + NY) Gy[t - 1] = v;
+            else {
+                // unpack the packed upper triangle
+                int idx = t - 1 - NY, a = 0;
+                while (idx >= NY - a) { idx -= NY - a; ++a; }
+                const int b = a + idx;
+                Hy[a][b] = v;
+                Hy[b][a] = v;
+            }
+        }
+        if (t == 0) {
+            // sparse Jacobian dy/dtheta, column by column (theta index)
+            for (int i = 0; i < NP; ++i) nzn[i] = 0;
+            auto put = [&](int i, int y, double val) {
+                const int n = nzn[i]++;
+                nzy[i][n] = y;
+                nzv[i][n] = val;
+            };
+            put(P_A, Y_A0, 1.0);
+            put(P_A + 1, Y_A1, 1.0);
+            const double* A = im.A;
+            put(0, Y_MX, A[0]);
+            put(0, Y_MY, A[2]);
+            put(1, Y_MX, A[1]);
+            put(1, Y_MY, A[3]);
+            put(P_EDEV, Y_EDEV, 1.0);
+            double dG[3][3];
+            shape_jacobian(A, th, dG);
+            for (int q = 0; q < 3; ++q) {
+                put(P_AXIS + q, Y_GXX, dG[q][0]);
+                put(P_AXIS + q, Y_GXY, dG[q][1]);
+                put(P_AXIS + q, Y_GYY, dG[q][2]);
+            }
+            for (int i = 0; i < 2; ++i) {
+                double el, el2;
+                band_moments(th, im.band, i, el, el2);
+                const int yl = i == 0 ? Y_EL0 : Y_EL1, yl2 = i == 0 ? Y_EL20 : Y_EL21;
+                for (int j = 0; j < NP; ++j) dvec[i][j] = evec[i][j] = 0.0;
+                dvec[i][P_R1 + i] = 1.0;
+                dvec[i][P_R2 + i] = 0.5;
+                evec[i][P_R1 + i] = 2.0;
+                evec[i][P_R2 + i] = 2.0;
+                for (int j = 0; j < 4; ++j) {
+                    const double b = color_beta(im.band, j);
+                    dvec[i][P_C1 + 4 * i + j] = b;
+                    dvec[i][P_C2 + 4 * i + j] = 0.5 * b * b;
+                    evec[i][P_C1 + 4 * i + j] = 2.0 * b;
+                    evec[i][P_C2 + 4 * i + j] = 2.0 * b * b;
+                }
+                for (int j = 0; j < NP; ++j) {
+                    if (dvec[i][j] != 0.0) put(j, yl, el * dvec[i][j]);
+                    if (evec[i][j] != 0.0) put(j, yl2, el2 * evec[i][j]);
+                }
+                wd[i] = el;
+                we[i] = el2;
+            }
+        }
+        __syncthreads();
+        if (t == 0) {
+            // weights of the second-derivative terms sum_y Gy d2y
+            double d2G[3][3][3];
+            shape_hessian(im.A, th, d2G);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    S2[a][b] = Gy[Y_GXX] * d2G[a][b][0] + Gy[Y_GXY] * d2G[a][b][1] +
+                               Gy[Y_GYY] * d2G[a][b][2];
+            wd[0] *= Gy[Y_EL0];
+            wd[1] *= Gy[Y_EL1];
+            we[0] *= Gy[Y_EL20];
+            we[1] *= Gy[Y_EL21];
+        }
+        __syncthreads();
+        if (t < NP)
+            for (int n = 0; n < nzn[t]; ++n) gacc += nzv[t][n] * Gy[nzy[t][n]];
+#pragma unroll
+        for (int k = 0; k < FH_PER; ++k) {
+            const int idx = t + k * FH_THREADS;
+            if (idx >= NP * NP) break;
+            const int i = idx / NP, j = idx - i * NP;
+            double h = 0.0;
+            for (int a = 0; a < nzn[i]; ++a)
+                for (int b = 0; b < nzn[j]; ++b)
+                    h += nzv[i][a] * Hy[nzy[i][a]][nzy[j][b]] * nzv[j][b];
+            for (int ty = 0; ty < 2; ++ty)
+                h += wd[ty] * dvec[ty][i] * dvec[ty][j] + we[ty] * evec[ty][i] * evec[ty][j];
+            if (i >= P_AXIS && i <= P_SCALE && j >= P_AXIS && j <= P_SCALE)
+                h += S2[i - P_AXIS][j - P_AXIS];
+            acc[k] += h;
+        }
+    }
+    __syncthreads();
+    double* Ho = hess_out + (size_t)NP * NP * s;
+#pragma unroll
+    for (int k = 0; k < FH_PER; ++k) {
+        const int idx = t + k * FH_THREADS;
+        if (idx < NP * NP) Ho[idx] = acc[k] - klH[idx];
+    }
+    if (t < NP && grad_out) grad_out[(size_t)NP * s + t] = gacc - klg[t];
+    if (t == 0) {
+        kl_out[s] = klv;
+        if (local_out) local_out[s] = lacc - klv;
+    }
+}
+
+cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st) {
+    if (P.n_item == 0) return cudaSuccess;
+    if (precision == CELESTE_FP64)
+        k_hess<double><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
+                                                   P.tbl64, (const double*)P.emap,
+                                                   (const double*)P.vmap, P.item_part);
+    else
+        k_hess<float><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
+                                                  P.tbl32, (const float*)P.emap,
+                                                  (const float*)P.vmap, P.item_part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
+                                 double* d_grad, double* d_hess, cudaStream_t st) {
+    if (P.n_src == 0) return cudaSuccess;
+    k_finalize_hess<<<P.n_src, FH_THREADS, 0, st>>>(P.n_src, d_theta, P.geo, P.patch_off, P.img,
+                                                    P.model, P.item_part, P.kl, d_local, d_grad,
+                                                    d_hess);
+    return cudaGetLastError();
 }
 
 }  // namespace cel
-
-extern "C" {
-void celeste_fit_options_default(celeste_fit_options* o) {
-    o->max_iter = 50;
-    o->grad_tol = 1e-8;
-    o->pred_tol_rel = 1e-12;
-    o->delta0 = 1.0;
-    o->delta_max = 1e3;
-    o->eta = 1e-4;
-    o->f_noise_rel = 1e-13;
-    o->precision = CELESTE_FP64;
-    o->max_sweeps = 20;
-    o->sweep_tol = 1e-8;
-}
-celeste_status celeste_fit_sources(celeste_problem*, double*, const int32_t*, int32_t,
-                                   const celeste_fit_options*, int32_t*, int32_t*, double*) {
-    return CELESTE_ERR_ARG;
-}
-}

@@ -1,0 +1,111 @@
+// Per-source FP64 helpers shared by the gradient and Hessian epilogues: KL terms,
+// band brightness moments and the galaxy-shape Jacobian.
+#pragma once
+
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace cel {
+
+// KL(q_s || prior) and its gradient (Section III priors Phi, Upsilon, Xi; Eq. 1):
+//   KL = sum_i a_i [ log(a_i / Phi_i) + KL_r,i + sum_d k_id ( log(k_id / w_id) + KL_c,id ) ]
+//   KL_r,i  = (log(pv/r2) + (r2 + (r1 - pm)^2)/pv - 1) / 2
+//   KL_c,id = (tr(P_d diag c2) + (c1 - mu_d)' P_d (c1 - mu_d) - 4 + log det Sigma_d
+//              - sum_j log c2_j) / 2
+// g (nullable) receives all 44 entries; position and shape entries are zero.
+__device__ inline double kl_value_grad(const ModelDev& md, const double* th, double* g) {
+    double kl = 0.0;
+    if (g)
+        for (int i = 0; i < NP; ++i) g[i] = 0.0;
+    for (int i = 0; i < 2; ++i) {
+        const double a = th[P_A + i];
+        const double phi = (i == 0) ? md.prior_star : 1.0 - md.prior_star;
+        const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
+        const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
+        double K = 0.5 * (log(pv / r2) + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0);
+        const double dr1 = (r1 - pm) / pv, dr2 = 0.5 * (1.0 / pv - 1.0 / r2);
+        double dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
+        double c1[4], c2[4], slog = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            c1[j] = th[P_C1 + 4 * i + j];
+            c2[j] = th[P_C2 + 4 * i + j];
+            slog += log(c2[j]);
+        }
+        for (int d = 0; d < NCOMP; ++d) {
+            const double k = th[P_K + NCOMP * i + d];
+            const double* Pm = md.prior_P[i][d];
+            const double* mu = md.prior_mu[i][d];
+            double diff[4], Pd[4];
+            for (int j = 0; j < 4; ++j) diff[j] = c1[j] - mu[j];
+            double quad = 0.0, tr = 0.0;
+            for (int j = 0; j < 4; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
+                Pd[j] = s;
+                quad += diff[j] * s;
+                tr += Pm[5 * j] * c2[j];
+            }
+            const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
+            const double lk = log(k / md.prior_w[i][d]);
+            K += k * (lk + klc);
+            if (g) g[P_K + NCOMP * i + d] = a * (lk + 1.0 + klc);
+            for (int j = 0; j < 4; ++j) {
+                dc1[j] += k * Pd[j];
+                dc2[j] += 0.5 * k * (Pm[5 * j] - 1.0 / c2[j]);
+            }
+        }
+        const double la = log(a / phi);
+        kl += a * (la + K);
+        if (g) {
+            g[P_A + i] = la + 1.0 + K;
+            g[P_R1 + i] = a * dr1;
+            g[P_R2 + i] = a * dr2;
+            for (int j = 0; j < 4; ++j) {
+                g[P_C1 + 4 * i + j] = a * dc1[j];
+                g[P_C2 + 4 * i + j] = a * dc2[j];
+            }
+        }
+    }
+    return kl;
+}
+
+// d(Gxx, Gxy, Gyy)/d(e_axis, e_angle, e_scale), G = A W A^T in the image's pixel frame.
+__device__ inline void shape_jacobian(const double* A, const double* th, double dG[3][3]) {
+    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
+    const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
+    double s2, c2;
+    sincos(2.0 * phi, &s2, &c2);
+    double dW[3][3];
+    // d/d rho: d ah = sg^2 rho, d bh = -sg^2 rho
+    {
+        const double da = sg * sg * rho, db = -sg * sg * rho;
+        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+    }
+    // d/d phi
+    dW[1][0] = -2.0 * bh * s2; dW[1][1] = 2.0 * bh * c2; dW[1][2] = 2.0 * bh * s2;
+    // d/d sigma: d ah = sg (1 + rho^2), d bh = sg (1 - rho^2)
+    {
+        const double da = sg * (1.0 + rho * rho), db = sg * (1.0 - rho * rho);
+        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
+    }
+    for (int q = 0; q < 3; ++q) {
+        const double wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
+        dG[q][0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+        dG[q][1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+        dG[q][2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
+    }
+}
+
+__device__ inline void band_moments(const double* th, int band, int i, double& el, double& el2) {
+    double m = th[P_R1 + i], v = th[P_R2 + i];
+    for (int j = 0; j < 4; ++j) {
+        const double b = color_beta(band, j);
+        m += b * th[P_C1 + 4 * i + j];
+        v += b * b * th[P_C2 + 4 * i + j];
+    }
+    el = exp(m + 0.5 * v);
+    el2 = exp(2.0 * m + 2.0 * v);
+}
+
+}  // namespace cel

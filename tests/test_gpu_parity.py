@@ -144,3 +144,41 @@ def test_bad_problem_inputs_rejected(cel):
     with pytest.raises(cel.CelesteError) as e:
         cel.Problem(prob)
     assert e.value.status == cel.ERR_ARG
+
+
+HTOL = {0: 1e-8, 1: 1e-4}
+
+
+def _check_hessian(cel, prob, which=None):
+    orc = Oracle(prob)
+    o_loc, o_g, o_h = orc.derivs(prob.theta, which=which, hess=True)
+    P = cel.Problem(prob)
+    for prec in (cel.FP64, cel.FP32):
+        loc, g, h = P.hess(prob.theta, precision=prec)
+        if which is not None:
+            loc, g, h = loc[which], g[which], h[which]
+        te, tl, tg = TOL[prec]
+        assert np.max(np.abs(loc - o_loc) / np.abs(o_loc)) <= tl
+        assert rel_l2(g, o_g) <= tg
+        for k in range(h.shape[0]):
+            assert np.abs(h[k] - h[k].T).max() <= 1e-12 * np.abs(h[k]).max()
+            assert rel_l2(h[k], o_h[k]) <= HTOL[prec], (prec, k, rel_l2(h[k], o_h[k]))
+    P.close()
+
+
+def test_hessian_tiny(cel):
+    _check_hessian(cel, synth.config(0))
+
+
+def test_hessian_crowded(cel):
+    _check_hessian(cel, synth.config(2), which=np.arange(0, 64, 4).astype(np.int32))
+
+
+def test_hessian_edge_cases(cel):
+    th = np.stack([H.star_theta(1.0, 2.0), H.star_theta(20.0, 21.0, a_star=0.3)])
+    th[1, synth.I_AXIS] = 0.35
+    patches = (np.array([0, 3, 6], np.int32),
+               np.array([(0, 0, 0, 9, 11), (1, 0, 0, 17, 5), (4, 0, 0, 3, 1),
+                         (0, 10, 12, 23, 20), (2, 5, 5, 27, 27), (4, 13, 13, 19, 19)], np.int32))
+    prob = H.problem(th, H=33, W=35, patches=patches, wcs=[0.98, -0.05, 0.05, 0.98, 0.7, -0.4])
+    _check_hessian(cel, prob)
