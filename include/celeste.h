@@ -215,6 +215,41 @@ celeste_status celeste_profile_enable(celeste_problem* prob, int32_t on);
 int32_t celeste_profile_read(celeste_problem* prob, int32_t max_kernels, char* names,
                              double* ms_total, int32_t* launches);
 
+/*
+ * Allocation-free variant (no counterpart in the paper): the ELBO, local objective
+ * and gradient of ONE source whose light falls in ONE patch, for callers that cannot
+ * call cudaMalloc -- a program whose device memory is owned by another allocator, or
+ * code that must not allocate on a latency-critical path.  celeste_problem_create
+ * allocates the problem's device copies; this call allocates nothing.  It takes:
+ *   im, model, patch: host structs as for celeste_problem_create (im->pixels and
+ *     im->sky_map are ignored; the patch rectangle is in im's pixel frame);
+ *   d_pixels: DEVICE [patch->h][patch->w] counts of the patch's pixels (row-major);
+ *   d_sky_map: DEVICE [patch->h][patch->w] sky counts, or NULL for the scalar im->sky;
+ *   d_theta: DEVICE [44] parameters of the source (domain as in celeste_elbo; not
+ *     checked here);
+ *   outputs (DEVICE): d_elbo_total (nullable, [1]: the patch's expected
+ *     log-likelihood minus the KL), d_elbo_local (nullable, [1]: the same here, since
+ *     the patch is the source's only one), d_grad ([44]);
+ *   stream: cudaStream_t for the launches (NULL = legacy default stream); the call
+ *     returns without synchronising.
+ * Every intermediate buffer lives in one file-scope device array of
+ * CELESTE_NOALLOC_SCRATCH_BYTES, which each GPU that loads the library holds until the
+ * process exits; the largest patch it serves is 101 x 101 pixels (larger sides return
+ * CELESTE_ERR_ARG with a message).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls on a device share the array and it keeps
+ * the last call's contents (every value a call reads is written by the same call
+ * first): calls whose work overlaps on the GPU race on it, so order them on one
+ * stream or synchronise between them.  Errors: CELESTE_ERR_ARG, CELESTE_ERR_NOT_PD,
+ * CELESTE_ERR_CUDA; message via celeste_last_error().
+ */
+enum { CELESTE_NOALLOC_SCRATCH_BYTES = 393216 };
+celeste_status celeste_patch_elbo_grad_noalloc(const celeste_image* im, const celeste_model* model,
+                                               const celeste_patch* patch, const float* d_pixels,
+                                               const float* d_sky_map, const double* d_theta,
+                                               int32_t precision, double* d_elbo_total,
+                                               double* d_elbo_local, double* d_grad, void* stream);
+
 /* Thread-local message describing the calling thread's last error. */
 const char* celeste_last_error(void);
 

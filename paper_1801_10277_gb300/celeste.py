@@ -59,7 +59,8 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_elbo", "celeste_elbo_grad", "celeste_hess", "celeste_fit_options_default",
            "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
-           "celeste_profile_enable", "celeste_profile_read"]
+           "celeste_profile_enable", "celeste_profile_read",
+           "celeste_patch_elbo_grad_noalloc"]
 
 
 def lib_path():
@@ -106,6 +107,10 @@ def load(build_if_missing=False):
     L.celeste_profile_enable.restype = i32
     L.celeste_profile_read.argtypes = [vp, i32, vp, vp, vp]
     L.celeste_profile_read.restype = i32
+    L.celeste_patch_elbo_grad_noalloc.argtypes = [C.POINTER(celeste_image), C.POINTER(celeste_model),
+                                                  C.POINTER(celeste_patch), vp, vp, vp, i32, vp,
+                                                  vp, vp, vp]
+    L.celeste_patch_elbo_grad_noalloc.restype = i32
     L.celeste_last_error.argtypes = []
     L.celeste_last_error.restype = C.c_char_p
     _lib = L
@@ -270,3 +275,43 @@ class Problem:
 
     def device_status(self):
         return int(self.L.celeste_device_status(self.h))
+
+
+def patch_elbo_grad_noalloc(image, exp_mix, dev_mix, prior_star, prior_r, prior_c, patch,
+                            d_pixels, d_theta, d_total, d_local, d_grad, d_sky_map=None,
+                            precision=FP64):
+    """Allocation-free ELBO + gradient of one source confined to one patch.
+
+    For callers that cannot call cudaMalloc (device memory owned by another
+    allocator, or no allocation allowed on the calling path): every intermediate
+    buffer lives in a fixed device array inside the library.  ``image`` is a
+    ``synth.Image`` (its pixels are not read); ``patch`` is (x0, y0, w, h) in that
+    image's pixel frame; the ``d_*`` arguments are CUDA torch tensors: the patch's
+    pixels [h][w] float32, theta [44], and float64 outputs total [1], local [1],
+    grad [44].  Work is enqueued on torch's current stream."""
+    L = load()
+    psf = np.ascontiguousarray(image.psf, np.float64)
+    im = celeste_image()
+    im.band, im.height, im.width = image.band, image.height, image.width
+    im.pixels, im.sky, im.sky_map = None, float(image.sky), None
+    im.nmgy_per_count = float(image.calib)
+    for k in range(6):
+        im.wcs[k] = float(image.wcs[k])
+    im.n_psf, im.psf = psf.shape[0], _p(psf)
+    em = np.ascontiguousarray(exp_mix, np.float64)
+    dm = np.ascontiguousarray(dev_mix, np.float64)
+    pr = np.ascontiguousarray(prior_r, np.float64)
+    pc = np.ascontiguousarray(prior_c, np.float64)
+    m = celeste_model(em.shape[0], dm.shape[0], _p(em), _p(dm), float(prior_star), _p(pr),
+                      pc.shape[1], _p(pc))
+    p = celeste_patch(0, *(int(v) for v in patch))
+    import torch
+
+    def ptr(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+
+    st = L.celeste_patch_elbo_grad_noalloc(C.byref(im), C.byref(m), C.byref(p), ptr(d_pixels),
+                                           ptr(d_sky_map), ptr(d_theta), precision, ptr(d_total),
+                                           ptr(d_local), ptr(d_grad),
+                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(st)

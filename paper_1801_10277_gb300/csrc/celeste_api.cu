@@ -87,6 +87,11 @@ celeste_status upload(T** dst, const T* src, size_t n) {
 
 }  // namespace
 
+namespace cel {
+// lets other translation units report through celeste_last_error()
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace cel
+
 struct celeste_problem {
     int device = 0;
     DevProblem P{};

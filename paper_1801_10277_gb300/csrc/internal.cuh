@@ -120,6 +120,8 @@ struct DevProblem {
     int32_t* status;
 };
 
+void set_last_error(const char* msg);
+
 cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st);
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st);
