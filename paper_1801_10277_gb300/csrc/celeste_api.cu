@@ -92,29 +92,7 @@ namespace cel {
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace cel
 
-struct celeste_problem {
-    int device = 0;
-    DevProblem P{};
-    cudaStream_t stream = nullptr;       // stream of the host-pointer entry points
-    cudaStream_t last_stream = nullptr;  // stream of the last enqueued call
-    // host copies used by the fit driver and validation
-    std::vector<int32_t> patch_off, nbr_off, nbrs;
-    std::vector<PatchGeo> geo;
-    std::vector<ImgMeta> imgs;
-    // device buffers owned by the problem
-    std::vector<void*> owned;
-    double* d_theta = nullptr;
-    double* d_out = nullptr;     // total(1) | local(n_src) | grad(n_src*44) | hess(n_src*44*44)
-    size_t out_cap = 0;
-    // per-kernel CUDA-event timing (celeste_profile_*)
-    bool profile = false;
-    struct Rec { std::string name; cudaEvent_t a, b; };
-    std::vector<Rec> pending;
-    std::vector<cudaEvent_t> pool;
-    std::vector<std::string> names;
-    std::vector<double> ms;
-    std::vector<int32_t> launches;
-};
+#include "problem.cuh"
 
 namespace {
 
@@ -379,12 +357,16 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     // tiles: per image a dense grid of TILE x TILE cells, each with its covering patches
     std::vector<Tile> tiles;
     std::vector<int32_t> tile_list;
+    std::vector<int32_t> tile_grid;
     {
         std::vector<std::vector<int32_t>> per_img(n_img);   // patch ids per image in order
         for (int p = 0; p < n_patch; ++p) per_img[geo[p].img].push_back(p);
         for (int n = 0; n < n_img; ++n) {
             if (per_img[n].empty()) continue;
             const int tw = (im[n].W + TILE - 1) / TILE, th = (im[n].H + TILE - 1) / TILE;
+            im[n].tg_off = (int64_t)tile_grid.size();
+            im[n].tgw = tw;
+            tile_grid.resize(tile_grid.size() + (size_t)tw * th, -1);
             std::vector<std::vector<int32_t>> cell((size_t)tw * th);
             for (int p : per_img[n]) {
                 const PatchGeo& g = geo[p];
@@ -397,6 +379,7 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                     auto& c = cell[(size_t)ty * tw + tx];
                     if (c.empty()) continue;
                     Tile t{};
+                    tile_grid[im[n].tg_off + (size_t)ty * tw + tx] = (int32_t)tiles.size();
                     t.img = n; t.x0 = tx * TILE; t.y0 = ty * TILE;
                     t.list_off = (int)tile_list.size(); t.list_n = (int)c.size();
                     tile_list.insert(tile_list.end(), c.begin(), c.end());
@@ -452,14 +435,17 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
         }
     }
     ImgMeta* d_img; PatchGeo* d_geo; WorkItem* d_items; Tile* d_tiles; int32_t* d_tl; int32_t* d_po; ModelDev* d_md;
+    int32_t* d_tg;
     if ((st = dupload(pr, &d_img, im.data(), im.size()))) return bail(st);
     if ((st = dupload(pr, &d_geo, geo.data(), geo.size()))) return bail(st);
     if ((st = dupload(pr, &d_items, items.data(), items.size()))) return bail(st);
     if ((st = dupload(pr, &d_tiles, tiles.data(), tiles.size()))) return bail(st);
     if ((st = dupload(pr, &d_tl, tile_list.data(), tile_list.size()))) return bail(st);
+    if ((st = dupload(pr, &d_tg, tile_grid.data(), tile_grid.size()))) return bail(st);
     if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
     if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
+    P.tile_grid = d_tg;
     P.patch_off = d_po; P.model = d_md;
     void* p;
     if ((st = dalloc(pr, &p, sizeof(double) * TBL_STRIDE * (size_t)n_patch))) return bail(st);
@@ -528,6 +514,34 @@ celeste_status celeste_hess_device(celeste_problem* pr, const double* d_theta, i
                                    double* d_local, double* d_grad, double* d_hess, void* stream) {
     if (!d_hess) return fail(CELESTE_ERR_ARG, "d_hess is null");
     return run_device(pr, d_theta, precision, MODE_HESS, nullptr, d_local, d_grad, d_hess, stream);
+}
+
+celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, const int32_t* which,
+                                   int32_t n_which, const celeste_fit_options* opts,
+                                   int32_t* iters_out, int32_t* status_out, double* elbo_out) {
+    if (!pr || !theta_inout) return fail(CELESTE_ERR_ARG, "null problem or theta");
+    celeste_fit_options o;
+    if (opts) o = *opts;
+    else celeste_fit_options_default(&o);
+    if (o.precision != CELESTE_FP64 && o.precision != CELESTE_FP32_ACC64)
+        return fail(CELESTE_ERR_ARG, "precision must be CELESTE_FP64 or CELESTE_FP32_ACC64");
+    if (o.max_iter < 1 || o.max_sweeps < 1 || !(o.delta0 > 0) || !(o.delta_max >= o.delta0))
+        return fail(CELESTE_ERR_ARG, "bad fit options");
+    if (which && n_which < 0) return fail(CELESTE_ERR_ARG, "n_which < 0");
+    celeste_status s = check_theta_host(theta_inout, pr->P.n_src);
+    if (s) return s;
+    for (int i = 0; i < pr->P.n_src; ++i) {
+        const double* th = theta_inout + (size_t)NP * i;
+        if (!(th[P_EDEV] > 0.01 && th[P_EDEV] < 0.99 && th[P_AXIS] > 0.01 && th[P_AXIS] < 0.99 &&
+              th[P_A] > 0.005 && th[P_A] < 0.995))
+            return fail(CELESTE_ERR_ARG,
+                        "theta[%d]: the fit needs e_dev, e_axis in (0.01, 0.99) and a_star in (0.005, 0.995)", i);
+    }
+    CEL_CUDA(cudaSetDevice(pr->device));
+    s = ensure_out(pr);
+    if (s) return s;
+    return fit_sources_impl(pr, theta_inout, which, n_which, &o, iters_out, status_out, elbo_out,
+                            celeste_elbo);
 }
 
 celeste_status celeste_profile_enable(celeste_problem* pr, int32_t on) {

@@ -1,5 +1,884 @@
-// Block-coordinate trust-region Newton fit driver (Section IV-D).
+// Block-coordinate trust-region Newton fit (Section IV-D): each source's 44 parameters
+// form a block; sources whose patches never intersect (one colour of a greedy colouring
+// of the neighbour graph) are optimised together, each with the others fixed; a
+// source's step is a Newton step with its exact Hessian inside a trust region
+// (Nocedal & Wright, Chapter 4).
+//
+// Per colour the batch runs in lock step; one iteration is
+//   k_prep / k_contrib   E_s, Var_s of every batch source at theta
+//   k_batch_maps         E = E_other + E_s and Var at the batch pixels (patches of one
+//                        colour are disjoint, so every pixel has one writer)
+//   k_hess / k_finalize_hess   ELBO_s, gradient and Hessian (44 x 44)
+//   k_tr_step            one CTA per source: free coordinates (41), the trust-region
+//                        subproblem (More-Sorensen with Cholesky factorisations), the
+//                        candidate point
+//   k_prep / k_contrib   E_s, Var_s at the candidate
+//   k_batch_dll          per-pixel change of the log-likelihood (stable difference form)
+//   k_tr_accept          actual / predicted gain, radius update, accept or reject
+// The iteration is captured once per colour as a CUDA graph and replayed; the host
+// reads one counter (sources still iterating) per replay.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
+#include "problem.cuh"
+#include "source_math.cuh"
+
+namespace cel {
+
+cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
+                                 double* d_grad, double* d_hess, cudaStream_t st);
+
+namespace {
+
+constexpr double BOX_LO = 0.01, BOX_HI = 0.99, A_LO = 0.005, A_HI = 0.995;
+enum : int { ST_ACTIVE = -1, ST_CONVERGED = 0, ST_MAXITER = 1, ST_NONFINITE = 2 };
+
+__device__ __forceinline__ double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+// theta(t): identity for u, angle, r1, c1; exp for scale, r2, c2; box sigmoids for
+// e_dev, e_axis and the star probability; softmax (last logit 0) for k.
+__device__ void free_to_theta(const double* t, double* th) {
+    th[0] = t[0];
+    th[1] = t[1];
+    th[P_EDEV] = BOX_LO + (BOX_HI - BOX_LO) * sigm(t[2]);
+    th[P_AXIS] = BOX_LO + (BOX_HI - BOX_LO) * sigm(t[3]);
+    th[P_ANGLE] = t[4];
+    th[P_SCALE] = exp(t[5]);
+    th[P_R1] = t[6];
+    th[P_R1 + 1] = t[7];
+    th[P_R2] = exp(t[8]);
+    th[P_R2 + 1] = exp(t[9]);
+    for (int j = 0; j < 8; ++j) {
+        th[P_C1 + j] = t[10 + j];
+        th[P_C2 + j] = exp(t[18 + j]);
+    }
+    th[P_A] = A_LO + (A_HI - A_LO) * sigm(t[26]);
+    th[P_A + 1] = 1.0 - th[P_A];
+    for (int i = 0; i < 2; ++i) {
+        double m = 0.0;
+        for (int e = 0; e < 7; ++e) m = fmax(m, t[27 + 7 * i + e]);
+        double ex[8], den = 0.0;
+        for (int e = 0; e < 7; ++e) den += (ex[e] = exp(t[27 + 7 * i + e] - m));
+        den += (ex[7] = exp(-m));
+        for (int d = 0; d < 8; ++d) th[P_K + 8 * i + d] = ex[d] / den;
+    }
+}
+
+__device__ void theta_to_free(const double* th, double* t) {
+    auto logit = [](double p) { return log(p / (1.0 - p)); };
+    t[0] = th[0];
+    t[1] = th[1];
+    t[2] = logit((th[P_EDEV] - BOX_LO) / (BOX_HI - BOX_LO));
+    t[3] = logit((th[P_AXIS] - BOX_LO) / (BOX_HI - BOX_LO));
+    t[4] = th[P_ANGLE];
+    t[5] = log(th[P_SCALE]);
+    t[6] = th[P_R1];
+    t[7] = th[P_R1 + 1];
+    t[8] = log(th[P_R2]);
+    t[9] = log(th[P_R2 + 1]);
+    for (int j = 0; j < 8; ++j) {
+        t[10 + j] = th[P_C1 + j];
+        t[18 + j] = log(th[P_C2 + j]);
+    }
+    t[26] = logit((th[P_A] - A_LO) / (A_HI - A_LO));
+    for (int i = 0; i < 2; ++i)
+        for (int e = 0; e < 7; ++e) t[27 + 7 * i + e] = log(th[P_K + 8 * i + e] / th[P_K + 8 * i + 7]);
+}
+
+// ------------------------------------------------------------------------------------
+// batch kernels
+
+// E_other, Var_other at every batch pixel: sky plus every other source covering it
+// (tile lists, ascending source order), from the current global E_s / Var_s buffers.
+template <class R>
+__global__ void k_other(const WorkItem* __restrict__ bitems, const PatchGeo* __restrict__ bgeo,
+                        const PatchGeo* __restrict__ geo, const ImgMeta* __restrict__ img,
+                        const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_list,
+                        const int32_t* __restrict__ tile_grid, const float* __restrict__ sky_map,
+                        const R* __restrict__ spE, const R* __restrict__ spV, R* __restrict__ eo,
+                        R* __restrict__ vo) {
+    const WorkItem it = bitems[blockIdx.x];
+    const int t = threadIdx.x;
+    if (t >= it.n) return;
+    const PatchGeo g = bgeo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int q = it.q0 + t;
+    const int yy = q / g.w, xx = q - yy * g.w;
+    const int gx = g.x0 + xx, gy = g.y0 + yy;
+    const int64_t m = im.px_off + (int64_t)gy * im.W + gx;
+    R E = im.has_sky_map ? (R)sky_map[m] : (R)im.sky;
+    R V = 0;
+    const int tid = tile_grid[im.tg_off + (int64_t)(gy / TILE) * im.tgw + gx / TILE];
+    if (tid >= 0) {
+        const Tile tl = tiles[tid];
+        for (int e = 0; e < tl.list_n; ++e) {
+            const PatchGeo o = geo[tile_list[tl.list_off + e]];
+            if (o.src == it.src) continue;
+            const int ox = gx - o.x0, oy = gy - o.y0;
+            if (ox >= 0 && ox < o.w && oy >= 0 && oy < o.h) {
+                const int64_t qq = o.sp_off + (int64_t)oy * o.w + ox;
+                E += spE[qq];
+                V += spV[qq];
+            }
+        }
+    }
+    eo[g.sp_off + q] = E;
+    vo[g.sp_off + q] = V;
+}
+
+// E, Var maps at the batch pixels from E_other and the batch sources' own terms
+template <class R>
+__global__ void k_batch_maps(const WorkItem* __restrict__ bitems, const PatchGeo* __restrict__ bgeo,
+                             const ImgMeta* __restrict__ img, const R* __restrict__ eo,
+                             const R* __restrict__ vo, const R* __restrict__ se,
+                             const R* __restrict__ sv, R* __restrict__ emap, R* __restrict__ vmap) {
+    const WorkItem it = bitems[blockIdx.x];
+    const int t = threadIdx.x;
+    if (t >= it.n) return;
+    const PatchGeo g = bgeo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int q = it.q0 + t;
+    const int yy = q / g.w, xx = q - yy * g.w;
+    const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+    const int64_t b = g.sp_off + q;
+    emap[m] = eo[b] + se[b];
+    vmap[m] = vo[b] + sv[b];
+}
+
+// per-item sum of ll(E', V') - ll(E, V) at the candidate, in a difference form that
+// does not cancel:  x (log1p(dE/E) - (dV E^2 - V dE (E + E')) / (2 E^2 E'^2)) - dE
+template <class R>
+__global__ void k_batch_dll(const WorkItem* __restrict__ bitems, const PatchGeo* __restrict__ bgeo,
+                            const ImgMeta* __restrict__ img, const float* __restrict__ pixels,
+                            const R* __restrict__ eo, const R* __restrict__ vo,
+                            const R* __restrict__ se, const R* __restrict__ sv,
+                            const R* __restrict__ ce, const R* __restrict__ cv,
+                            double* __restrict__ dll) {
+    __shared__ double red[CHUNK / 32];
+    const WorkItem it = bitems[blockIdx.x];
+    const int t = threadIdx.x;
+    R v = 0;
+    if (t < it.n) {
+        const PatchGeo g = bgeo[it.patch];
+        const ImgMeta& im = img[g.img];
+        const int q = it.q0 + t;
+        const int yy = q / g.w, xx = q - yy * g.w;
+        const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+        const int64_t b = g.sp_off + q;
+        const R x = (R)pixels[m];
+        const R E = eo[b] + se[b], V = vo[b] + sv[b];
+        const R dE = ce[b] - se[b], dV = cv[b] - sv[b];
+        const R E1 = E + dE;
+        const R num = dV * E * E - V * dE * (E + E1);
+        v = x * (log1p(dE / E) - num / ((R)2 * E * E * E1 * E1)) - dE;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) red[t >> 5] = (double)v;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        dll[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_to_free(int nb, const double* __restrict__ th, double* __restrict__ t) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) theta_to_free(th + (size_t)NP * b, t + (size_t)NT * b);
+}
+
+// ------------------------------------------------------------------------------------
+// trust-region step: one CTA per batch source
+
+constexpr int TR_THREADS = 128;
+constexpr int TRN = NT;   // 41
+
+struct TrState {
+    double delta;   // trust radius (free coordinates)
+    double pred;    // predicted gain of the candidate
+    double pnorm;   // |p|
+    double f;       // ELBO_s at theta
+    double kl;      // KL at theta
+    int32_t status; // ST_*
+    int32_t iters;
+    int32_t cand;   // a candidate was produced this iteration
+    int32_t pad;
+};
+
+// Cholesky of (B + lam I) into L (lower, row-major n x n); returns success to all threads
+__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < n * n; i += nt) {
+        const int r = i / n, c = i - r * n;
+        L[i] = (c <= r) ? B[i] + (r == c ? lam : 0.0) : 0.0;
+    }
+    if (tid == 0) *flag = 1;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            const double d = L[k * n + k];
+            if (!(d > 0.0) || !isfinite(d)) *flag = 0;
+            else L[k * n + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (!*flag) return false;
+        const double dk = L[k * n + k];
+        for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int idx = tid; idx < m * m; idx += nt) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+            if (j <= i) L[i * n + j] -= L[i * n + k] * L[j * n + k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// forward (L y = b) and backward (L^T x = y) substitution by one thread
+__device__ void chol_solve(const double* L, const double* b, double* x, int n) {
+    double y[TRN];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+__device__ void fwd_solve(const double* L, const double* b, double* y, int n) {
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s / L[i * n + i];
+    }
+}
+
+__global__ void __launch_bounds__(TR_THREADS)
+k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ tfree,
+          const double* __restrict__ f_in, const double* __restrict__ g_in,
+          const double* __restrict__ h_in, const double* __restrict__ kl_in,
+          double* __restrict__ theta_c, double* __restrict__ tfree_c, TrState* __restrict__ st,
+          celeste_fit_options o, int32_t* __restrict__ active) {
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    __shared__ TrState S;
+    __shared__ double gt[TRN], Ht[TRN * TRN], L[TRN * TRN], cvec[TRN], p[TRN], w[TRN];
+    __shared__ double th[NP], tt[TRN], g44[NP];
+    __shared__ int tn[TRN], tj[TRN][8];
+    __shared__ double tv[TRN][8];
+    __shared__ int flag, done;
+    __shared__ double lam_s, pn_s;
+    const int tid = threadIdx.x;
+    if (tid == 0) S = st[b];
+    __syncthreads();
+    if (S.status != ST_ACTIVE) {
+        if (tid == 0) st[b].cand = 0;
+        return;
+    }
+    for (int i = tid; i < NP; i += blockDim.x) {
+        th[i] = theta[(size_t)NP * b + i];
+        g44[i] = g_in[(size_t)NP * b + i];
+    }
+    for (int i = tid; i < TRN; i += blockDim.x) tt[i] = tfree[(size_t)NT * b + i];
+    __syncthreads();
+    // columns of T = d theta / d t
+    if (tid < TRN) {
+        const int a = tid;
+        int n = 0;
+        auto put = [&](int j, double v) {
+            tj[a][n] = j;
+            tv[a][n] = v;
+            ++n;
+        };
+        if (a == 2 || a == 3) {
+            const double s = sigm(tt[a]);
+            put(a, (BOX_HI - BOX_LO) * s * (1.0 - s));
+        } else if (a == 5 || a == 8 || a == 9 || (a >= 18 && a < 26)) {
+            put(a, th[a]);
+        } else if (a == 26) {
+            const double s = sigm(tt[26]);
+            const double d = (A_HI - A_LO) * s * (1.0 - s);
+            put(P_A, d);
+            put(P_A + 1, -d);
+        } else if (a >= 27) {
+            const int i = (a - 27) / 7, e = (a - 27) % 7;
+            const double pe = th[P_K + 8 * i + e];
+            for (int d = 0; d < 8; ++d) {
+                const double pd = th[P_K + 8 * i + d];
+                put(P_K + 8 * i + d, pd * ((d == e ? 1.0 : 0.0) - pe));
+            }
+        } else {
+            put(a, 1.0);
+        }
+        tn[a] = n;
+        double s = 0.0;
+        for (int u = 0; u < n; ++u) s += tv[a][u] * g44[tj[a][u]];
+        gt[a] = s;
+    }
+    __syncthreads();
+    // Ht = T' H T + sum_j g_j d2 theta_j / dt dt
+    const double* H44 = h_in + (size_t)NP * NP * b;
+    for (int idx = tid; idx < TRN * TRN; idx += blockDim.x) {
+        const int a = idx / TRN, c = idx % TRN;
+        double s = 0.0;
+        for (int u = 0; u < tn[a]; ++u)
+            for (int v = 0; v < tn[c]; ++v) s += tv[a][u] * H44[tj[a][u] * NP + tj[c][v]] * tv[c][v];
+        if (a == c) {
+            if (a == 2 || a == 3) {
+                const double sg = sigm(tt[a]);
+                s += g44[a] * (BOX_HI - BOX_LO) * sg * (1.0 - sg) * (1.0 - 2.0 * sg);
+            } else if (a == 5 || a == 8 || a == 9 || (a >= 18 && a < 26)) {
+                s += g44[a] * th[a];
+            } else if (a == 26) {
+                const double sg = sigm(tt[26]);
+                s += (g44[P_A] - g44[P_A + 1]) * (A_HI - A_LO) * sg * (1.0 - sg) * (1.0 - 2.0 * sg);
+            }
+        }
+        if (a >= 27 && c >= 27 && (a - 27) / 7 == (c - 27) / 7) {
+            const int i = (a - 27) / 7, e = (a - 27) % 7, f = (c - 27) % 7;
+            const double pe = th[P_K + 8 * i + e], pf = th[P_K + 8 * i + f];
+            for (int d = 0; d < 8; ++d) {
+                const double pd = th[P_K + 8 * i + d];
+                const double de = (d == e) ? 1.0 : 0.0, df = (d == f) ? 1.0 : 0.0;
+                const double ef = (e == f) ? 1.0 : 0.0;
+                s += g44[P_K + 8 * i + d] * pd * ((de - pe) * (df - pf) - pe * (ef - pf));
+            }
+        }
+        Ht[idx] = s;
+    }
+    __syncthreads();
+    // convergence checks
+    if (tid == 0) {
+        double gmax = 0.0;
+        bool fin = isfinite(f_in[b]);
+        for (int a = 0; a < TRN; ++a) {
+            gmax = fmax(gmax, fabs(gt[a]));
+            fin = fin && isfinite(gt[a]);
+        }
+        for (int a = 0; a < TRN * TRN && fin; ++a) fin = isfinite(Ht[a]);
+        done = 0;
+        if (!fin) {
+            S.status = ST_NONFINITE;
+            done = 1;
+        } else if (gmax <= o.grad_tol) {
+            S.status = ST_CONVERGED;
+            done = 1;
+        }
+        S.f = f_in[b];
+        S.kl = kl_in[b];
+    }
+    __syncthreads();
+    if (done) {
+        if (tid == 0) {
+            S.cand = 0;
+            st[b] = S;
+        }
+        return;
+    }
+    // minimise m(p) = c.p + p.B p / 2, |p| <= Delta with c = -gt, B = -Ht
+    for (int i = tid; i < TRN * TRN; i += blockDim.x) Ht[i] = -Ht[i];   // Ht now holds B
+    for (int i = tid; i < TRN; i += blockDim.x) cvec[i] = -gt[i];
+    __syncthreads();
+    const double Delta = S.delta;
+    double cn = 0.0, bnorm = 0.0, bdmin = 1e300;
+    for (int i = 0; i < TRN; ++i) {
+        cn += cvec[i] * cvec[i];
+        double r = 0.0;
+        for (int j = 0; j < TRN; ++j) r += fabs(Ht[i * TRN + j]);
+        bnorm = fmax(bnorm, r);
+        bdmin = fmin(bdmin, Ht[i * TRN + i]);
+    }
+    cn = sqrt(cn);
+    double lamL = fmax(0.0, fmax(-bdmin, cn / Delta - bnorm));
+    double lamU = cn / Delta + bnorm;
+    double lam = 0.0;
+    for (int i = tid; i < TRN; i += blockDim.x) p[i] = 0.0;   // a zero step if nothing factors
+    if (tid == 0) pn_s = 0.0;
+    __syncthreads();
+    bool ok = block_chol(Ht, 0.0, L, TRN, &flag);
+    bool solved = false;
+    if (ok) {
+        if (tid == 0) {
+            chol_solve(L, cvec, p, TRN);
+            double s = 0.0;
+            for (int i = 0; i < TRN; ++i) {
+                p[i] = -p[i];
+                s += p[i] * p[i];
+            }
+            pn_s = sqrt(s);
+        }
+        __syncthreads();
+        if (pn_s <= Delta) solved = true;
+        else lam = fmax(lamL, 0.0);
+    }
+    if (!solved) {
+        lam = fmax(lamL, fmax(1e-3 * lamU, sqrt(fmax(lamL, 1e-300) * lamU)));
+        if (ok) lamL = fmax(lamL, 0.0);
+        for (int it = 0; it < 200; ++it) {
+            const bool pd = block_chol(Ht, lam, L, TRN, &flag);
+            if (tid == 0) {
+                double nl;
+                if (!pd) {
+                    lamL = fmax(lamL, lam);
+                    nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
+                    done = 0;
+                } else {
+                    chol_solve(L, cvec, p, TRN);
+                    double s = 0.0;
+                    for (int i = 0; i < TRN; ++i) {
+                        p[i] = -p[i];
+                        s += p[i] * p[i];
+                    }
+                    const double pn = sqrt(s);
+                    pn_s = pn;
+                    if (fabs(pn - Delta) <= 1e-12 * Delta) {
+                        done = 1;
+                    } else {
+                        if (pn < Delta) lamU = lam;
+                        else lamL = lam;
+                        fwd_solve(L, p, w, TRN);
+                        double wn = 0.0;
+                        for (int i = 0; i < TRN; ++i) wn += w[i] * w[i];
+                        nl = lam + (pn * pn / wn) * (pn - Delta) / Delta;
+                        if (!(nl > lamL && nl < lamU))
+                            nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
+                        done = (lamU - lamL <= 1e-15 * fmax(1.0, lamU)) ? 2 : 0;
+                    }
+                }
+                if (!done) lam_s = nl;
+            }
+            __syncthreads();
+            if (done) break;
+            lam = lam_s;
+        }
+        // hard case: |p| < Delta with lambda pinned at -lambda_min: add tau z, z from
+        // inverse iteration with the last factorisation
+        if (done == 2 && pn_s < Delta) {
+            if (tid == 0) {
+                double z[TRN], zn = 0.0;
+                for (int i = 0; i < TRN; ++i) z[i] = 1.0 + 0.01 * i;
+                for (int r = 0; r < 6; ++r) {
+                    chol_solve(L, z, w, TRN);
+                    zn = 0.0;
+                    for (int i = 0; i < TRN; ++i) zn += w[i] * w[i];
+                    zn = sqrt(zn);
+                    for (int i = 0; i < TRN; ++i) z[i] = w[i] / zn;
+                }
+                double pz = 0.0, pp = 0.0;
+                for (int i = 0; i < TRN; ++i) {
+                    pz += p[i] * z[i];
+                    pp += p[i] * p[i];
+                }
+                const double disc = sqrt(fmax(0.0, pz * pz + Delta * Delta - pp));
+                const double t1 = -pz + disc, t2 = -pz - disc;
+                // pick the root with the lower model value: m(p + t z) - m(p) = -lam t p.z + t^2 z'Bz/2
+                double zbz = 0.0;
+                for (int i = 0; i < TRN; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < TRN; ++j) s += Ht[i * TRN + j] * z[j];
+                    zbz += z[i] * s;
+                }
+                const double m1 = -lam * t1 * pz + 0.5 * t1 * t1 * zbz;
+                const double m2 = -lam * t2 * pz + 0.5 * t2 * t2 * zbz;
+                const double tau = (m1 <= m2) ? t1 : t2;
+                for (int i = 0; i < TRN; ++i) p[i] += tau * z[i];
+                pn_s = Delta;
+            }
+            __syncthreads();
+        }
+    }
+    // predicted gain of the maximisation: g.p + p.H p / 2 = -(c.p + p.B p / 2)
+    if (tid == 0) {
+        double pred = 0.0;
+        for (int i = 0; i < TRN; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < TRN; ++j) s += Ht[i * TRN + j] * p[j];
+            pred -= cvec[i] * p[i] + 0.5 * p[i] * s;
+        }
+        S.pred = pred;
+        S.pnorm = pn_s;
+        if (pred <= o.pred_tol_rel * (1.0 + fabs(S.f))) {
+            S.status = ST_CONVERGED;
+            S.cand = 0;
+            done = 1;
+        } else {
+            S.cand = 1;
+            done = 0;
+        }
+        st[b] = S;
+    }
+    __syncthreads();
+    if (done) return;
+    if (tid < TRN) tfree_c[(size_t)NT * b + tid] = tt[tid] + p[tid];
+    __syncthreads();
+    if (tid == 0) {
+        double tc[TRN], thc[NP];
+        for (int i = 0; i < TRN; ++i) tc[i] = tt[i] + p[i];
+        free_to_theta(tc, thc);
+        for (int i = 0; i < NP; ++i) theta_c[(size_t)NP * b + i] = thc[i];
+        atomicAdd(active, 1);
+    }
+}
+
+// ratio of actual to predicted gain, radius update, acceptance (one thread per source)
+__global__ void k_tr_accept(int nb, const int32_t* __restrict__ bpatch_off,
+                            const PatchGeo* __restrict__ bgeo, const double* __restrict__ dll,
+                            const ModelDev* __restrict__ md, double* __restrict__ theta,
+                            double* __restrict__ tfree, const double* __restrict__ theta_c,
+                            const double* __restrict__ tfree_c, TrState* __restrict__ st,
+                            celeste_fit_options o) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    TrState S = st[b];
+    if (S.status != ST_ACTIVE || !S.cand) return;
+    const double* thc = theta_c + (size_t)NP * b;
+    double d = 0.0;
+    for (int p = bpatch_off[b]; p < bpatch_off[b + 1]; ++p) {
+        const PatchGeo g = bgeo[p];
+        for (int it = g.item0; it < g.item0 + g.nitem; ++it) d += dll[it];
+    }
+    const double klc = kl_value_grad(*md, thc, nullptr);
+    const double df = d - (klc - S.kl);
+    const double scale = 1.0 + fabs(S.f);
+    double rho = (S.pred <= o.f_noise_rel * scale) ? 1.0 : df / S.pred;
+    if (!isfinite(df)) rho = -1.0;
+    if (rho < 0.25) S.delta = 0.25 * S.delta;
+    else if (rho > 0.75 && S.pnorm >= (1.0 - 1e-9) * S.delta) S.delta = fmin(2.0 * S.delta, o.delta_max);
+    if (rho > o.eta) {
+        for (int i = 0; i < NP; ++i) theta[(size_t)NP * b + i] = thc[i];
+        for (int i = 0; i < NT; ++i) tfree[(size_t)NT * b + i] = tfree_c[(size_t)NT * b + i];
+    }
+    S.iters += 1;
+    if (S.iters >= o.max_iter) S.status = ST_MAXITER;
+    S.cand = 0;
+    st[b] = S;
+}
+
+__global__ void k_gather_theta(int nb, const int32_t* __restrict__ bsrc,
+                               const double* __restrict__ theta, double* __restrict__ bth) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb * NP) bth[i] = theta[(size_t)NP * bsrc[i / NP] + i % NP];
+}
+
+__global__ void k_scatter_theta(int nb, const int32_t* __restrict__ bsrc,
+                                const double* __restrict__ bth, double* __restrict__ theta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb * NP) theta[(size_t)NP * bsrc[i / NP] + i % NP] = bth[i];
+}
+
+__global__ void k_init_state(int nb, TrState* st, double delta0) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    TrState S{};
+    S.delta = delta0;
+    S.status = ST_ACTIVE;
+    st[b] = S;
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    ~DevBuf() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t alloc(T** p, size_t n) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = (T*)q;
+        return e;
+    }
+};
+
+struct Batch {
+    std::vector<int32_t> src;        // global ids
+    std::vector<int32_t> patch_off;  // batch CSR
+    std::vector<PatchGeo> geo;       // batch patches (src = batch index, sp_off batch-local)
+    std::vector<WorkItem> items;     // patch = batch patch, src = GLOBAL id
+    int64_t n_sp = 0;
+};
+
+Batch make_batch(const celeste_problem* pr, const std::vector<int32_t>& members) {
+    Batch B;
+    B.src = members;
+    B.patch_off.push_back(0);
+    for (int bi = 0; bi < (int)members.size(); ++bi) {
+        const int s = members[bi];
+        for (int p = pr->patch_off[s]; p < pr->patch_off[s + 1]; ++p) {
+            PatchGeo g = pr->geo[p];
+            g.src = bi;
+            g.sp_off = B.n_sp;
+            g.item0 = (int)B.items.size();
+            const int npx = g.w * g.h;
+            for (int q0 = 0; q0 < npx; q0 += CHUNK)
+                B.items.push_back({(int)B.geo.size(), q0, std::min(CHUNK, npx - q0), s});
+            g.nitem = (int)B.items.size() - g.item0;
+            B.n_sp += npx;
+            B.geo.push_back(g);
+        }
+        B.patch_off.push_back((int)B.geo.size());
+    }
+    return B;
+}
+
+}  // namespace
+
+}  // namespace cel
+
+using namespace cel;
+
+celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const int32_t* which,
+                                     int32_t n_which, const celeste_fit_options* opts,
+                                     int32_t* iters_out, int32_t* status_out, double* elbo_out,
+                                     celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t, double*, double*)) {
+    const DevProblem& P = pr->P;
+    const int n = P.n_src;
+    const int prec = opts->precision;
+    cudaStream_t st = pr->stream;
+    auto cuda_err = [&](cudaError_t e, const char* w) -> celeste_status {
+        char buf[256];
+        snprintf(buf, sizeof buf, "%s: %s", w, cudaGetErrorString(e));
+        set_last_error(buf);
+        return e == cudaErrorMemoryAllocation ? CELESTE_ERR_NOMEM : CELESTE_ERR_CUDA;
+    };
+#define FIT_CUDA(x)                                          \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) return cuda_err(e_, #x);      \
+    } while (0)
+    // greedy colouring in ascending id over the neighbour graph
+    std::vector<int32_t> colour(n, 0);
+    int ncol = 0;
+    for (int s = 0; s < n; ++s) {
+        std::vector<char> used(ncol + 2, 0);
+        for (int e = pr->nbr_off[s]; e < pr->nbr_off[s + 1]; ++e) {
+            const int o = pr->nbrs[e];
+            if (o < s && colour[o] <= ncol) used[colour[o]] = 1;
+        }
+        int c = 0;
+        while (used[c]) ++c;
+        colour[s] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    std::vector<char> moves(n, which ? 0 : 1);
+    if (which)
+        for (int k = 0; k < n_which; ++k) {
+            if (which[k] < 0 || which[k] >= n) {
+                set_last_error("which[] holds an invalid source index");
+                return CELESTE_ERR_ARG;
+            }
+            moves[which[k]] = 1;
+        }
+    std::vector<Batch> batches(ncol);
+    size_t maxB = 1, maxP = 1, maxI = 1;
+    int64_t maxSp = 1;
+    for (int c = 0; c < ncol; ++c) {
+        std::vector<int32_t> mem;
+        for (int s = 0; s < n; ++s)
+            if (colour[s] == c && moves[s]) mem.push_back(s);
+        batches[c] = make_batch(pr, mem);
+        maxB = std::max(maxB, mem.size());
+        maxP = std::max(maxP, batches[c].geo.size());
+        maxI = std::max(maxI, batches[c].items.size());
+        maxSp = std::max(maxSp, batches[c].n_sp);
+    }
+    // device buffers for the largest batch
+    DevBuf mem;
+    const size_t rs = (prec == CELESTE_FP64) ? sizeof(double) : sizeof(float);
+    int32_t *d_bsrc, *d_bpo, *d_active;
+    PatchGeo* d_bgeo;
+    WorkItem* d_bitems;
+    double *d_bth, *d_bthc, *d_bt, *d_btc, *d_f, *d_g, *d_h, *d_kl, *d_part, *d_dll, *d_tbl64;
+    float* d_tbl32;
+    TrState* d_st;
+    unsigned char *d_eo, *d_vo, *d_se, *d_sv, *d_ce, *d_cv;
+    FIT_CUDA(mem.alloc(&d_bsrc, maxB));
+    FIT_CUDA(mem.alloc(&d_bpo, maxB + 1));
+    FIT_CUDA(mem.alloc(&d_active, 1));
+    FIT_CUDA(mem.alloc(&d_bgeo, maxP));
+    FIT_CUDA(mem.alloc(&d_bitems, maxI));
+    FIT_CUDA(mem.alloc(&d_bth, maxB * NP));
+    FIT_CUDA(mem.alloc(&d_bthc, maxB * NP));
+    FIT_CUDA(mem.alloc(&d_bt, maxB * NT));
+    FIT_CUDA(mem.alloc(&d_btc, maxB * NT));
+    FIT_CUDA(mem.alloc(&d_f, maxB));
+    FIT_CUDA(mem.alloc(&d_g, maxB * NP));
+    FIT_CUDA(mem.alloc(&d_h, maxB * NP * NP));
+    FIT_CUDA(mem.alloc(&d_kl, maxB));
+    FIT_CUDA(mem.alloc(&d_part, maxI * NPART));
+    FIT_CUDA(mem.alloc(&d_dll, maxI));
+    FIT_CUDA(mem.alloc(&d_tbl64, maxP * TBL_STRIDE));
+    FIT_CUDA(mem.alloc(&d_tbl32, maxP * TBL_STRIDE));
+    FIT_CUDA(mem.alloc(&d_st, maxB));
+    FIT_CUDA(mem.alloc(&d_eo, maxSp * rs));
+    FIT_CUDA(mem.alloc(&d_vo, maxSp * rs));
+    FIT_CUDA(mem.alloc(&d_se, maxSp * rs));
+    FIT_CUDA(mem.alloc(&d_sv, maxSp * rs));
+    FIT_CUDA(mem.alloc(&d_ce, maxSp * rs));
+    FIT_CUDA(mem.alloc(&d_cv, maxSp * rs));
+    int32_t* h_active = nullptr;
+    FIT_CUDA(cudaMallocHost((void**)&h_active, sizeof(int32_t)));
+    struct HostFree {
+        int32_t* p;
+        ~HostFree() { cudaFreeHost(p); }
+    } hf{h_active};
+
+    FIT_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> iters(n, 0), status(n, ST_CONVERGED);
+    double prev = 0.0;
+    {
+        celeste_status s0 = elbo_fn(pr, theta, prec, &prev, nullptr);
+        if (s0) return s0;
+    }
+    int sw = 0;
+    std::vector<TrState> hst(maxB);
+    for (; sw < opts->max_sweeps; ++sw) {
+        for (int c = 0; c < ncol; ++c) {
+            const Batch& B = batches[c];
+            const int nb = (int)B.src.size();
+            if (nb == 0) continue;
+            // current E_s / Var_s of every source (global buffers)
+            FIT_CUDA(launch_prep(P, pr->d_theta, prec, st));
+            FIT_CUDA(launch_contrib(P, prec, st));
+            FIT_CUDA(cudaMemcpyAsync(d_bsrc, B.src.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
+            FIT_CUDA(cudaMemcpyAsync(d_bpo, B.patch_off.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, st));
+            FIT_CUDA(cudaMemcpyAsync(d_bgeo, B.geo.data(), sizeof(PatchGeo) * B.geo.size(), cudaMemcpyHostToDevice, st));
+            FIT_CUDA(cudaMemcpyAsync(d_bitems, B.items.data(), sizeof(WorkItem) * B.items.size(), cudaMemcpyHostToDevice, st));
+            const int nI = (int)B.items.size();
+            if (nI > 0) {
+                if (prec == CELESTE_FP64)
+                    k_other<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
+                                                         P.tile_grid, P.sky_map, (const double*)P.spE,
+                                                         (const double*)P.spE2, (double*)d_eo, (double*)d_vo);
+                else
+                    k_other<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
+                                                        P.tile_grid, P.sky_map, (const float*)P.spE,
+                                                        (const float*)P.spE2, (float*)d_eo, (float*)d_vo);
+            }
+            k_gather_theta<<<(nb * NP + 255) / 256, 256, 0, st>>>(nb, d_bsrc, pr->d_theta, d_bth);
+            k_to_free<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bth, d_bt);
+            k_init_state<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, opts->delta0);
+            FIT_CUDA(cudaGetLastError());
+            // batch views of the problem
+            DevProblem Pb = P;
+            Pb.n_src = nb;
+            Pb.n_patch = (int)B.geo.size();
+            Pb.n_item = nI;
+            Pb.n_sp = B.n_sp;
+            Pb.geo = d_bgeo;
+            Pb.items = d_bitems;
+            Pb.patch_off = d_bpo;
+            Pb.tbl64 = d_tbl64;
+            Pb.tbl32 = d_tbl32;
+            Pb.spE = d_se;
+            Pb.spE2 = d_sv;
+            Pb.item_part = d_part;
+            Pb.kl = d_kl;
+            DevProblem Pc = Pb;
+            Pc.spE = d_ce;
+            Pc.spE2 = d_cv;
+            // one Newton iteration, captured as a graph
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            FIT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaSuccess;
+            auto chk = [&](cudaError_t e) {
+                if (ce == cudaSuccess && e != cudaSuccess) ce = e;
+            };
+            chk(cudaMemsetAsync(d_active, 0, sizeof(int32_t), st));
+            chk(launch_prep(Pb, d_bth, prec, st));
+            chk(launch_contrib(Pb, prec, st));
+            if (nI > 0) {
+                if (prec == CELESTE_FP64)
+                    k_batch_maps<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, (const double*)d_eo,
+                                                               (const double*)d_vo, (const double*)d_se,
+                                                               (const double*)d_sv, (double*)P.emap, (double*)P.vmap);
+                else
+                    k_batch_maps<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, (const float*)d_eo,
+                                                              (const float*)d_vo, (const float*)d_se,
+                                                              (const float*)d_sv, (float*)P.emap, (float*)P.vmap);
+            }
+            chk(launch_hess_pixels(Pb, prec, st));
+            chk(launch_finalize_hess(Pb, d_bth, d_f, d_g, d_h, st));
+            k_tr_step<<<nb, TR_THREADS, 0, st>>>(nb, d_bth, d_bt, d_f, d_g, d_h, d_kl, d_bthc, d_btc,
+                                                 d_st, *opts, d_active);
+            chk(launch_prep(Pc, d_bthc, prec, st));
+            chk(launch_contrib(Pc, prec, st));
+            if (nI > 0) {
+                if (prec == CELESTE_FP64)
+                    k_batch_dll<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, P.pixels,
+                                                              (const double*)d_eo, (const double*)d_vo,
+                                                              (const double*)d_se, (const double*)d_sv,
+                                                              (const double*)d_ce, (const double*)d_cv, d_dll);
+                else
+                    k_batch_dll<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, P.pixels,
+                                                             (const float*)d_eo, (const float*)d_vo,
+                                                             (const float*)d_se, (const float*)d_sv,
+                                                             (const float*)d_ce, (const float*)d_cv, d_dll);
+            }
+            k_tr_accept<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bpo, d_bgeo, d_dll, P.model, d_bth, d_bt,
+                                                          d_bthc, d_btc, d_st, *opts);
+            chk(cudaGetLastError());
+            chk(cudaMemcpyAsync(h_active, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            cudaError_t ee = cudaStreamEndCapture(st, &graph);
+            if (ce != cudaSuccess || ee != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_err(ce != cudaSuccess ? ce : ee, "fit iteration capture");
+            }
+            ee = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ee != cudaSuccess) return cuda_err(ee, "cudaGraphInstantiate");
+            int it = 0;
+            for (; it < opts->max_iter + 1; ++it) {
+                ee = cudaGraphLaunch(exec, st);
+                if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+                if (ee != cudaSuccess) {
+                    cudaGraphExecDestroy(exec);
+                    return cuda_err(ee, "fit iteration");
+                }
+                if (*h_active == 0) break;
+            }
+            cudaGraphExecDestroy(exec);
+            // results of this colour
+            k_scatter_theta<<<(nb * NP + 255) / 256, 256, 0, st>>>(nb, d_bsrc, d_bth, pr->d_theta);
+            FIT_CUDA(cudaGetLastError());
+            FIT_CUDA(cudaMemcpyAsync(hst.data(), d_st, sizeof(TrState) * nb, cudaMemcpyDeviceToHost, st));
+            FIT_CUDA(cudaStreamSynchronize(st));
+            for (int bi = 0; bi < nb; ++bi) {
+                iters[B.src[bi]] += hst[bi].iters;
+                status[B.src[bi]] = hst[bi].status == ST_ACTIVE ? ST_MAXITER : hst[bi].status;
+            }
+        }
+        FIT_CUDA(cudaMemcpyAsync(theta, pr->d_theta, sizeof(double) * NP * n, cudaMemcpyDeviceToHost, st));
+        FIT_CUDA(cudaStreamSynchronize(st));
+        double cur = 0.0;
+        celeste_status s1 = elbo_fn(pr, theta, prec, &cur, nullptr);
+        if (s1) return s1;
+        const double rel = fabs(cur - prev) / fmax(1.0, fabs(cur));
+        prev = cur;
+        if (rel < opts->sweep_tol) {
+            ++sw;
+            break;
+        }
+    }
+    if (iters_out) memcpy(iters_out, iters.data(), sizeof(int32_t) * n);
+    if (status_out) memcpy(status_out, status.data(), sizeof(int32_t) * n);
+    if (elbo_out) *elbo_out = prev;
+    return CELESTE_OK;
+#undef FIT_CUDA
+}
 
 extern "C" {
 
@@ -14,11 +893,6 @@ void celeste_fit_options_default(celeste_fit_options* o) {
     o->precision = CELESTE_FP64;
     o->max_sweeps = 20;
     o->sweep_tol = 1e-8;
-}
-
-celeste_status celeste_fit_sources(celeste_problem*, double*, const int32_t*, int32_t,
-                                   const celeste_fit_options*, int32_t*, int32_t*, double*) {
-    return CELESTE_ERR_ARG;
 }
 
 }  // extern "C"

@@ -46,8 +46,9 @@ constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
 
 struct ImgMeta {
     int64_t px_off;          // offset of the image in the concatenated pixel / map buffers
+    int64_t tg_off;          // offset of the image's tile grid (tile id per cell, -1 = none)
     int32_t H, W, band, npsf;
-    int32_t has_sky_map, pad;
+    int32_t has_sky_map, tgw; // tgw: tile-grid cells per row
     double sky, iota;
     double A[4], t[2];
     double psf[MAXPSF][6];
@@ -106,6 +107,7 @@ struct DevProblem {
     const WorkItem* items;
     const Tile* tiles;
     const int32_t* tile_list;
+    const int32_t* tile_grid;
     const int32_t* patch_off;
     const ModelDev* model;
     double* tbl64;
@@ -121,6 +123,12 @@ struct DevProblem {
 };
 
 void set_last_error(const char* msg);
+
+celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const int32_t* which,
+                                int32_t n_which, const celeste_fit_options* opts,
+                                int32_t* iters_out, int32_t* status_out, double* elbo_out,
+                                celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t,
+                                                          double*, double*));
 
 cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st);
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,

@@ -1,0 +1,34 @@
+// Host-side problem object shared by the C-ABI translation units (not installed).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct celeste_problem {
+    using PatchGeo = cel::PatchGeo;
+    using ImgMeta = cel::ImgMeta;
+    using DevProblem = cel::DevProblem;
+    int device = 0;
+    DevProblem P{};
+    cudaStream_t stream = nullptr;       // stream of the host-pointer entry points
+    cudaStream_t last_stream = nullptr;  // stream of the last enqueued call
+    // host copies used by the fit driver and validation
+    std::vector<int32_t> patch_off, nbr_off, nbrs;
+    std::vector<PatchGeo> geo;
+    std::vector<ImgMeta> imgs;
+    // device buffers owned by the problem
+    std::vector<void*> owned;
+    double* d_theta = nullptr;
+    double* d_out = nullptr;     // total(1) | local(n_src) | grad(n_src*44) | hess(n_src*44*44)
+    size_t out_cap = 0;
+    // per-kernel CUDA-event timing (celeste_profile_*)
+    bool profile = false;
+    struct Rec { std::string name; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int32_t> launches;
+};
