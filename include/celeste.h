@@ -167,6 +167,9 @@ typedef struct {
     int32_t precision;         /* CELESTE_FP64 or CELESTE_FP32_ACC64 */
     int32_t max_sweeps;        /* block-coordinate sweeps over all colour classes */
     double sweep_tol;          /* stop sweeping when |dELBO_total| / max(1,|ELBO_total|) < sweep_tol */
+    int32_t refine_fp64;       /* with CELESTE_FP32_ACC64: after the FP32 sweeps converge, polish with
+                                  FP64 sweeps (Newton needs one or two steps from there), so poorly
+                                  constrained parameters are not left at FP32 rounding noise */
 } celeste_fit_options;
 
 /* Fill opts with the defaults documented above. */

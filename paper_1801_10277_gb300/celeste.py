@@ -50,7 +50,7 @@ class celeste_fit_options(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("grad_tol", C.c_double), ("pred_tol_rel", C.c_double),
                 ("delta0", C.c_double), ("delta_max", C.c_double), ("eta", C.c_double),
                 ("f_noise_rel", C.c_double), ("precision", C.c_int32), ("max_sweeps", C.c_int32),
-                ("sweep_tol", C.c_double)]
+                ("sweep_tol", C.c_double), ("refine_fp64", C.c_int32)]
 
 
 _lib = None

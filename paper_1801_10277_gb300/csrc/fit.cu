@@ -645,7 +645,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                                      celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t, double*, double*)) {
     const DevProblem& P = pr->P;
     const int n = P.n_src;
-    const int prec = opts->precision;
+    int prec = opts->precision;
     cudaStream_t st = pr->stream;
     auto cuda_err = [&](cudaError_t e, const char* w) -> celeste_status {
         char buf[256];
@@ -696,7 +696,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
     }
     // device buffers for the largest batch
     DevBuf mem;
-    const size_t rs = (prec == CELESTE_FP64) ? sizeof(double) : sizeof(float);
+    const size_t rs = sizeof(double);   // per-pixel batch buffers serve both precisions
     int32_t *d_bsrc, *d_bpo, *d_active;
     PatchGeo* d_bgeo;
     WorkItem* d_bitems;
@@ -742,8 +742,16 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
         celeste_status s0 = elbo_fn(pr, theta, prec, &prev, nullptr);
         if (s0) return s0;
     }
-    int sw = 0;
     std::vector<TrState> hst(maxB);
+    // phase 0 in the requested precision; with FP32 and refine_fp64, phase 1 polishes in FP64
+    const int nphase = (opts->precision == CELESTE_FP32_ACC64 && opts->refine_fp64) ? 2 : 1;
+    for (int phase = 0; phase < nphase; ++phase) {
+    prec = (phase == 0) ? opts->precision : CELESTE_FP64;
+    if (phase == 1) {
+        celeste_status s2 = elbo_fn(pr, theta, prec, &prev, nullptr);
+        if (s2) return s2;
+    }
+    int sw = 0;
     for (; sw < opts->max_sweeps; ++sw) {
         for (int c = 0; c < ncol; ++c) {
             const Batch& B = batches[c];
@@ -873,6 +881,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             break;
         }
     }
+    }
     if (iters_out) memcpy(iters_out, iters.data(), sizeof(int32_t) * n);
     if (status_out) memcpy(status_out, status.data(), sizeof(int32_t) * n);
     if (elbo_out) *elbo_out = prev;
@@ -893,6 +902,7 @@ void celeste_fit_options_default(celeste_fit_options* o) {
     o->precision = CELESTE_FP64;
     o->max_sweeps = 20;
     o->sweep_tol = 1e-8;
+    o->refine_fp64 = 1;
 }
 
 }  // extern "C"

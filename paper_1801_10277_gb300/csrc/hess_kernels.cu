@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                                                 const R* __restrict__ vmap,
                                                 double* __restrict__ part) {
     __shared__ R sT[TBL_STRIDE];
-    __shared__ double red[CHUNK / 32][HV];
+    __shared__ R red[CHUNK / 32][HV];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
@@ -244,12 +244,12 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
 #pragma unroll
     for (int i = 0; i < HV; ++i) {
         const R s = warp_sum_h(out[i]);
-        if (lane == 0) red[warp][i] = (double)s;
+        if (lane == 0) red[warp][i] = s;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < HV; i += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][i];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)red[w][i];
         part[(size_t)blockIdx.x * NPART + i] = s;
     }
 }

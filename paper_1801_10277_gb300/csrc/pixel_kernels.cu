@@ -41,18 +41,19 @@ __device__ __forceinline__ R warp_sum(R v) {
 // in warp order.  Thread i < NV returns the CTA total of value i.
 template <class R, int NV>
 __device__ __forceinline__ void cta_sum(const R (&v)[NV], double* out) {
-    __shared__ double red[32][NV > 0 ? NV : 1];
+    // warp sums stay in R; only the NV cross-warp sums convert (the FP64 pipe is narrow)
+    __shared__ R red[32][NV > 0 ? NV : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         R s = warp_sum(v[i]);
-        if (lane == 0) red[warp][i] = (double)s;
+        if (lane == 0) red[warp][i] = s;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
 }
@@ -92,88 +93,94 @@ __global__ void k_check_theta(const double* __restrict__ theta, int n_src, int32
 //   galaxy component (k, j): weight alpha_k w_j (1 - e_dev) [exp] or alpha_k w_j e_dev [dev],
 //                            covariance Sigma_k + nu_j G,  G = A W A^T,
 //                            W = sigma^2 R(phi) diag(1, rho^2) R(phi)^T
-// Means are stored relative to the patch origin so FP32 differences stay exact.
+// Positions, the galaxy covariance and the brightness moments are formed in FP64 by
+// thread 0; the per-component algebra runs in the table's precision R.  Means are
+// stored relative to the patch origin so FP32 differences stay exact.
 
+__device__ __forceinline__ float lg2(float x) { return log2f(x); }
+__device__ __forceinline__ double lg2(double x) { return log2(x); }
+
+template <class R>
 __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
                        const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
-                       int n_patch, int nprof, double* __restrict__ tbl64,
-                       float* __restrict__ tbl32) {
+                       int n_patch, int nprof, R* __restrict__ tbl) {
     const int p = blockIdx.x;
     if (p >= n_patch) return;
+    __shared__ double sh[8];   // gxx gxy gyy edev
     const PatchGeo g = geo[p];
     const ImgMeta& im = img[g.img];
     const double* th = theta + (size_t)NP * g.src;
-    const double* A = im.A;
-    const double mux = A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0;
-    const double muy = A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0;
-    // world-frame ellipse W = Ah + Bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi)
-    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE], edev = th[P_EDEV];
-    const double ah = 0.5 * sg * sg * (1.0 + rho * rho), bh = 0.5 * sg * sg * (1.0 - rho * rho);
-    double s2, c2;
-    sincos(2.0 * phi, &s2, &c2);
-    const double wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
-    const double gxx = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
-    const double gxy = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
-    const double gyy = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
-    double* T64 = tbl64 ? tbl64 + (size_t)p * TBL_STRIDE : nullptr;
-    float* T32 = tbl32 ? tbl32 + (size_t)p * TBL_STRIDE : nullptr;
-    auto put = [&](int i, double v) {
-        if (T64) T64[i] = v;
-        if (T32) T32[i] = (float)v;
-    };
+    R* T = tbl + (size_t)p * TBL_STRIDE;
     const int npsf = im.npsf;
     if (threadIdx.x == 0) {
+        const double* A = im.A;
+        const double mux = A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0;
+        const double muy = A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0;
+        // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi)
+        const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
+        const double ah = 0.5 * sg * sg * (1.0 + rho * rho), bh = 0.5 * sg * sg * (1.0 - rho * rho);
+        double s2, c2;
+        sincos(2.0 * phi, &s2, &c2);
+        const double wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
+        sh[0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+        sh[1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+        sh[2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
+        sh[3] = th[P_EDEV];
         // brightness moments in this band: log l | type i ~ N(m, v)
         for (int i = 0; i < 2; ++i) {
             double m = th[P_R1 + i], v = th[P_R2 + i];
             for (int j = 0; j < 4; ++j) {
-                double b = color_beta(im.band, j);
+                const double b = color_beta(im.band, j);
                 m += b * th[P_C1 + 4 * i + j];
                 v += b * b * th[P_C2 + 4 * i + j];
             }
-            put(i == 0 ? H_EL0 : H_EL1, exp(m + 0.5 * v));
-            put(i == 0 ? H_EL20 : H_EL21, exp(2.0 * m + 2.0 * v));
+            T[i == 0 ? H_EL0 : H_EL1] = (R)exp(m + 0.5 * v);
+            T[i == 0 ? H_EL20 : H_EL21] = (R)exp(2.0 * m + 2.0 * v);
         }
-        put(H_A0, th[P_A]);
-        put(H_A1, th[P_A + 1]);
-        put(H_IOTA, im.iota);
-        put(7, 0.0);
+        T[H_A0] = (R)th[P_A];
+        T[H_A1] = (R)th[P_A + 1];
+        T[H_IOTA] = (R)im.iota;
+        T[7] = (R)0;
         for (int k = 0; k < MAXPSF; ++k) {
-            put(T_MEAN + 2 * k, k < npsf ? mux + im.psf[k][1] : 0.0);
-            put(T_MEAN + 2 * k + 1, k < npsf ? muy + im.psf[k][2] : 0.0);
+            T[T_MEAN + 2 * k] = (R)(k < npsf ? mux + im.psf[k][1] : 0.0);
+            T[T_MEAN + 2 * k + 1] = (R)(k < npsf ? muy + im.psf[k][2] : 0.0);
         }
     }
+    __syncthreads();
+    const R gxx = (R)sh[0], gxy = (R)sh[1], gyy = (R)sh[2], edev = (R)sh[3];
+    const R log2e = (R)LOG2E, log2_2pi = (R)2.6514961294723187;   // log2(2 pi)
     const int per_k = 1 + nprof;
     for (int c = threadIdx.x; c < npsf * per_k; c += blockDim.x) {
         const int k = c / per_k, j = c % per_k - 1;
         const double* ps = im.psf[k];
-        double cxx = ps[3], cxy = ps[4], cyy = ps[5], w = ps[0], dw = 0.0, nu = 0.0;
+        R cxx = (R)ps[3], cxy = (R)ps[4], cyy = (R)ps[5], w = (R)ps[0], dw = 0, nu = 0;
         if (j >= 0) {
-            nu = md->prof_nu[j];
+            nu = (R)md->prof_nu[j];
             const bool dev = j >= md->n_exp;
             cxx += nu * gxx;
             cxy += nu * gxy;
             cyy += nu * gyy;
-            w = ps[0] * md->prof_w[j] * (dev ? edev : 1.0 - edev);
-            dw = ps[0] * md->prof_w[j] * (dev ? 1.0 : -1.0);
+            const R aw = (R)ps[0] * (R)md->prof_w[j];
+            w = aw * (dev ? edev : (R)1 - edev);
+            dw = dev ? aw : -aw;
         }
-        const double det = cxx * cyy - cxy * cxy;
-        const double pxx = cyy / det, pxy = -cxy / det, pyy = cxx / det;
-        const double qd = -log2(TWO_PI * sqrt(det));
+        const R det = cxx * cyy - cxy * cxy;
+        const R idet = (R)1 / det;
+        const R pxx = cyy * idet, pxy = -cxy * idet, pyy = cxx * idet;
         const int base = (j < 0) ? T_STAR + k * STAR_STRIDE : T_GAL + (k * nprof + j) * GAL_STRIDE;
-        put(base + 0, -0.5 * LOG2E * pxx);
-        put(base + 1, -LOG2E * pxy);
-        put(base + 2, -0.5 * LOG2E * pyy);
-        put(base + 3, qd);
-        put(base + 4, pxx);
-        put(base + 5, pxy);
-        put(base + 6, pyy);
-        put(base + 7, w);
+        T[base + 0] = (R)-0.5 * log2e * pxx;
+        T[base + 1] = -log2e * pxy;
+        T[base + 2] = (R)-0.5 * log2e * pyy;
+        T[base + 3] = -log2_2pi - (R)0.5 * lg2(det);
+        T[base + 4] = pxx;
+        T[base + 5] = pxy;
+        T[base + 6] = pyy;
+        T[base + 7] = w;
         if (j >= 0) {
-            put(base + 8, dw);
-            put(base + 9, nu);
-            put(base + 10, 0.0);
-            put(base + 11, 0.0);
+            T[base + 8] = dw;
+            T[base + 9] = nu;
+            T[base + 10] = 0;
+            T[base + 11] = 0;
         }
     }
 }
@@ -375,9 +382,12 @@ cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaS
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st) {
     if (P.n_patch == 0) return cudaSuccess;
-    k_prep<<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
-                                     precision == CELESTE_FP64 ? P.tbl64 : nullptr,
-                                     precision == CELESTE_FP64 ? nullptr : P.tbl32);
+    if (precision == CELESTE_FP64)
+        k_prep<double><<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
+                                                 P.tbl64);
+    else
+        k_prep<float><<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
+                                                P.tbl32);
     return cudaGetLastError();
 }
 

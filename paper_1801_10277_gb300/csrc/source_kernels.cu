@@ -9,69 +9,82 @@
 
 namespace cel {
 
-// grad += J^T Gy for one patch
-__device__ void chain_grad(const ImgMeta& im, const double* th, const double* Gy, double* grad) {
-    grad[P_A] += Gy[Y_A0];
-    grad[P_A + 1] += Gy[Y_A1];
-    for (int i = 0; i < 2; ++i) {
-        double el, el2;
-        band_moments(th, im.band, i, el, el2);
-        const double gl = Gy[i == 0 ? Y_EL0 : Y_EL1] * el;
-        const double gl2 = Gy[i == 0 ? Y_EL20 : Y_EL21] * el2;
-        // d El = El d(m + v/2),  d El2 = El2 d(2m + 2v)
-        const double dm = gl + 2.0 * gl2, dv = 0.5 * gl + 2.0 * gl2;
-        grad[P_R1 + i] += dm;
-        grad[P_R2 + i] += dv;
-        for (int j = 0; j < 4; ++j) {
-            const double b = color_beta(im.band, j);
-            grad[P_C1 + 4 * i + j] += b * dm;
-            grad[P_C2 + 4 * i + j] += b * b * dv;
-        }
+// d ELBO / d theta_j contributed by one patch through the intermediate variables y:
+// sum_y Gy[y] dy/dtheta_j (El = E[l|i] = exp(m + v/2), El2 = E[l^2|i] = exp(2m + 2v)).
+__device__ __forceinline__ double chain_entry(int j, int band, const double* A, const double* Gy,
+                                              const double* el, const double* el2,
+                                              const double (*dG)[3]) {
+    if (j == 0) return Gy[Y_MX] * A[0] + Gy[Y_MY] * A[2];
+    if (j == 1) return Gy[Y_MX] * A[1] + Gy[Y_MY] * A[3];
+    if (j == P_EDEV) return Gy[Y_EDEV];
+    if (j >= P_AXIS && j <= P_SCALE) {
+        const int q = j - P_AXIS;
+        return Gy[Y_GXX] * dG[q][0] + Gy[Y_GXY] * dG[q][1] + Gy[Y_GYY] * dG[q][2];
     }
-    const double* A = im.A;
-    grad[0] += Gy[Y_MX] * A[0] + Gy[Y_MY] * A[2];
-    grad[1] += Gy[Y_MX] * A[1] + Gy[Y_MY] * A[3];
-    grad[P_EDEV] += Gy[Y_EDEV];
-    double dG[3][3];
-    shape_jacobian(A, th, dG);
-    for (int q = 0; q < 3; ++q)
-        grad[P_AXIS + q] += Gy[Y_GXX] * dG[q][0] + Gy[Y_GXY] * dG[q][1] + Gy[Y_GYY] * dG[q][2];
+    if (j >= P_A) return (j < P_K) ? Gy[j == P_A ? Y_A0 : Y_A1] : 0.0;
+    int i, kind, c = 0;   // kind: 0 r1, 1 r2, 2 c1, 3 c2
+    if (j < P_R2) { i = j - P_R1; kind = 0; }
+    else if (j < P_C1) { i = j - P_R2; kind = 1; }
+    else if (j < P_C2) { i = (j - P_C1) / 4; c = (j - P_C1) % 4; kind = 2; }
+    else { i = (j - P_C2) / 4; c = (j - P_C2) % 4; kind = 3; }
+    const double gl = Gy[i == 0 ? Y_EL0 : Y_EL1] * el[i];
+    const double gl2 = Gy[i == 0 ? Y_EL20 : Y_EL21] * el2[i];
+    const double dm = gl + 2.0 * gl2, dv = 0.5 * gl + 2.0 * gl2;
+    if (kind == 0) return dm;
+    if (kind == 1) return dv;
+    const double b = color_beta(band, c);
+    return kind == 2 ? b * dm : b * b * dv;
 }
 
-// one thread per source: local objective, KL, gradient
-__global__ void k_finalize(int n_src, int mode, const double* __restrict__ theta,
-                           const PatchGeo* __restrict__ geo, const int32_t* __restrict__ patch_off,
-                           const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
-                           const double* __restrict__ part, double* __restrict__ kl_out,
-                           double* __restrict__ local_out, double* __restrict__ grad_out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// one CTA per source: KL (two threads, one per type, while the others sum the first
+// patch's work items), then per patch the item sums and the chain rule, one thread
+// per parameter.  FP64.
+constexpr int FZ_THREADS = 64;
+
+__global__ void __launch_bounds__(FZ_THREADS)
+k_finalize(int n_src, int mode, const double* __restrict__ theta,
+           const PatchGeo* __restrict__ geo, const int32_t* __restrict__ patch_off,
+           const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
+           const double* __restrict__ part, double* __restrict__ kl_out,
+           double* __restrict__ local_out, double* __restrict__ grad_out) {
+    const int s = blockIdx.x;
     if (s >= n_src) return;
-    const double* th = theta + (size_t)NP * s;
-    double grad[NP];
-    double kl;
-    if (mode >= MODE_GRAD) {
-        kl = kl_value_grad(*md, th, grad);
-        for (int i = 0; i < NP; ++i) grad[i] = -grad[i];
-    } else {
-        kl = kl_value_grad(*md, th, nullptr);
-    }
-    double loc = -kl;
+    const int t = threadIdx.x;
+    __shared__ double th[NP], klg[NP], Gy[NY + 1];
+    __shared__ double el[2], el2[2], dG[3][3], klv;
+    for (int i = t; i < NP; i += blockDim.x) th[i] = theta[(size_t)NP * s + i];
+    __syncthreads();
+    if (t == 0) klv = kl_value_grad(*md, th, mode >= MODE_GRAD ? klg : nullptr);
+    double gacc = 0.0, lacc = 0.0;
+    const int nv = (mode >= MODE_GRAD) ? 1 + NY : 1;
     for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
         const PatchGeo g = geo[p];
-        double Gy[NY];
-        for (int y = 0; y < NY; ++y) Gy[y] = 0.0;
-        for (int it = g.item0; it < g.item0 + g.nitem; ++it) {
-            const double* pr = part + (size_t)it * NPART;
-            loc += pr[PART_LL];
-            if (mode >= MODE_GRAD)
-                for (int y = 0; y < NY; ++y) Gy[y] += pr[PART_G + y];
+        if (t < nv) {
+            double v = 0.0;
+            for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
+            Gy[t] = v;
         }
-        if (mode >= MODE_GRAD) chain_grad(img[g.img], th, Gy, grad);
+        const ImgMeta& im = img[g.img];
+        if (mode >= MODE_GRAD) {
+            if (t == 32) {
+                for (int i = 0; i < 2; ++i) band_moments(th, im.band, i, el[i], el2[i]);
+                double d[3][3];
+                shape_jacobian(im.A, th, d);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) dG[a][b] = d[a][b];
+            }
+        }
+        __syncthreads();
+        if (t == 0) lacc += Gy[0];
+        if (mode >= MODE_GRAD && t < NP) gacc += chain_entry(t, im.band, im.A, Gy + 1, el, el2, dG);
+        __syncthreads();
     }
-    kl_out[s] = kl;
-    if (local_out) local_out[s] = loc;
-    if (grad_out && mode >= MODE_GRAD)
-        for (int i = 0; i < NP; ++i) grad_out[(size_t)NP * s + i] = grad[i];
+    __syncthreads();   // klv / klg from thread 0 (sources without patches skip the loop)
+    if (t == 0) {
+        kl_out[s] = klv;
+        if (local_out) local_out[s] = lacc - klv;
+    }
+    if (mode >= MODE_GRAD && grad_out && t < NP) grad_out[(size_t)NP * s + t] = gacc - klg[t];
 }
 
 // total = sum of tile ll sums - sum of KL, one CTA, fixed order
@@ -100,9 +113,9 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int mode
         cudaError_t e = launch_finalize_hess(P, d_theta, d_local, d_grad, d_hess, st);
         if (e != cudaSuccess) return e;
     } else if (P.n_src > 0) {
-        k_finalize<<<(P.n_src + 127) / 128, 128, 0, st>>>(P.n_src, mode, d_theta, P.geo,
-                                                          P.patch_off, P.img, P.model,
-                                                          P.item_part, P.kl, d_local, d_grad);
+        k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo, P.patch_off,
+                                                   P.img, P.model, P.item_part, P.kl, d_local,
+                                                   d_grad);
     }
     if (d_total) k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.kl, P.n_src, d_total);
     return cudaGetLastError();

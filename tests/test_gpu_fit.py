@@ -36,7 +36,7 @@ def _compare(cel, prob, which=None, max_sweeps=20):
     moving = np.arange(prob.n_src) if which is None else np.asarray(which)
     for prec in (cel.FP64, cel.FP32):
         th, it, st, el = P.fit(prob.theta, which=which, precision=prec, max_sweeps=max_sweeps)
-        assert np.all(it[moving] <= 50 * max_sweeps)
+        assert np.all(it[moving] <= 50 * max_sweeps * (2 if prec == cel.FP32 else 1))
         both = [s for s in moving if st[s] == 0 and o_st[s] == 0]
         assert len(both) >= 0.75 * len(moving), (prec, st[moving], o_st[moving])
         for s in both:
