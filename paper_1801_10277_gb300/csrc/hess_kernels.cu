@@ -248,9 +248,9 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
     }
     __syncthreads();
     for (int i = threadIdx.x; i < HV; i += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)red[w][i];
-        part[(size_t)blockIdx.x * NPART + i] = s;
+        R s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][i];
+        part[(size_t)blockIdx.x * NPART + i] = (double)s;
     }
 }
 

@@ -41,7 +41,8 @@ __device__ __forceinline__ R warp_sum(R v) {
 // in warp order.  Thread i < NV returns the CTA total of value i.
 template <class R, int NV>
 __device__ __forceinline__ void cta_sum(const R (&v)[NV], double* out) {
-    // warp sums stay in R; only the NV cross-warp sums convert (the FP64 pipe is narrow)
+    // sums within the CTA stay in R (a fixed tree over <= 256 pixels); one conversion
+    // per value: an FP64 warp instruction costs the narrow FP64 pipe ~16 cycles
     __shared__ R red[32][NV > 0 ? NV : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
@@ -52,9 +53,9 @@ __device__ __forceinline__ void cta_sum(const R (&v)[NV], double* out) {
     }
     __syncthreads();
     if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
-        out[threadIdx.x] = s;
+        R s = 0;
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = (double)s;
     }
 }
 
@@ -93,12 +94,17 @@ __global__ void k_check_theta(const double* __restrict__ theta, int n_src, int32
 //   galaxy component (k, j): weight alpha_k w_j (1 - e_dev) [exp] or alpha_k w_j e_dev [dev],
 //                            covariance Sigma_k + nu_j G,  G = A W A^T,
 //                            W = sigma^2 R(phi) diag(1, rho^2) R(phi)^T
-// Positions, the galaxy covariance and the brightness moments are formed in FP64 by
-// thread 0; the per-component algebra runs in the table's precision R.  Means are
-// stored relative to the patch origin so FP32 differences stay exact.
+// Positions are formed in FP64 and stored relative to the patch origin (so FP32
+// differences stay exact); the galaxy covariance, the brightness moments and the
+// per-component algebra run in the table's precision R, spread over lanes (a lone
+// FP64 lane costs a whole warp slot of the narrow FP64 pipe).
 
 __device__ __forceinline__ float lg2(float x) { return log2f(x); }
 __device__ __forceinline__ double lg2(double x) { return log2(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
+__device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <class R>
 __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
@@ -112,39 +118,44 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
     const double* th = theta + (size_t)NP * g.src;
     R* T = tbl + (size_t)p * TBL_STRIDE;
     const int npsf = im.npsf;
-    if (threadIdx.x == 0) {
+    const int t0 = threadIdx.x;
+    if (t0 == 0) {
+        // position relative to the patch origin in FP64 (the pixel frame spans 2048 px)
         const double* A = im.A;
         const double mux = A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0;
         const double muy = A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0;
-        // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi)
-        const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
-        const double ah = 0.5 * sg * sg * (1.0 + rho * rho), bh = 0.5 * sg * sg * (1.0 - rho * rho);
-        double s2, c2;
-        sincos(2.0 * phi, &s2, &c2);
-        const double wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
-        sh[0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
-        sh[1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
-        sh[2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
-        sh[3] = th[P_EDEV];
-        // brightness moments in this band: log l | type i ~ N(m, v)
-        for (int i = 0; i < 2; ++i) {
-            double m = th[P_R1 + i], v = th[P_R2 + i];
-            for (int j = 0; j < 4; ++j) {
-                const double b = color_beta(im.band, j);
-                m += b * th[P_C1 + 4 * i + j];
-                v += b * b * th[P_C2 + 4 * i + j];
-            }
-            T[i == 0 ? H_EL0 : H_EL1] = (R)exp(m + 0.5 * v);
-            T[i == 0 ? H_EL20 : H_EL21] = (R)exp(2.0 * m + 2.0 * v);
-        }
-        T[H_A0] = (R)th[P_A];
-        T[H_A1] = (R)th[P_A + 1];
-        T[H_IOTA] = (R)im.iota;
-        T[7] = (R)0;
         for (int k = 0; k < MAXPSF; ++k) {
             T[T_MEAN + 2 * k] = (R)(k < npsf ? mux + im.psf[k][1] : 0.0);
             T[T_MEAN + 2 * k + 1] = (R)(k < npsf ? muy + im.psf[k][2] : 0.0);
         }
+    } else if (t0 == 1) {
+        // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi), G = A W A^T
+        const R rho = (R)th[P_AXIS], phi = (R)th[P_ANGLE], sg = (R)th[P_SCALE];
+        const R ah = (R)0.5 * sg * sg * ((R)1 + rho * rho), bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
+        R s2, c2;
+        sc(2 * phi, &s2, &c2);
+        const R wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
+        const R a0 = (R)im.A[0], a1 = (R)im.A[1], a2 = (R)im.A[2], a3 = (R)im.A[3];
+        sh[0] = (double)(a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy);
+        sh[1] = (double)(a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy);
+        sh[2] = (double)(a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy);
+        sh[3] = th[P_EDEV];
+    } else if (t0 >= 2 && t0 < 6) {
+        // brightness moments in this band: log l | type i ~ N(m, v); E[l] = e^{m+v/2}, E[l^2] = e^{2m+2v}
+        const int i = (t0 - 2) >> 1, second = (t0 - 2) & 1;
+        double m = th[P_R1 + i], v = th[P_R2 + i];
+        for (int j = 0; j < 4; ++j) {
+            const double b = color_beta(im.band, j);
+            m += b * th[P_C1 + 4 * i + j];
+            v += b * b * th[P_C2 + 4 * i + j];
+        }
+        const R arg = second ? (R)(2.0 * m + 2.0 * v) : (R)(m + 0.5 * v);
+        T[(i == 0) ? (second ? H_EL20 : H_EL0) : (second ? H_EL21 : H_EL1)] = ex(arg);
+    } else if (t0 == 6) {
+        T[H_A0] = (R)th[P_A];
+        T[H_A1] = (R)th[P_A + 1];
+        T[H_IOTA] = (R)im.iota;
+        T[7] = (R)0;
     }
     __syncthreads();
     const R gxx = (R)sh[0], gxy = (R)sh[1], gyy = (R)sh[2], edev = (R)sh[3];

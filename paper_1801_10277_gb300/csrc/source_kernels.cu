@@ -36,9 +36,11 @@ __device__ __forceinline__ double chain_entry(int j, int band, const double* A, 
     return kind == 2 ? b * dm : b * b * dv;
 }
 
-// one CTA per source: KL (two threads, one per type, while the others sum the first
-// patch's work items), then per patch the item sums and the chain rule, one thread
-// per parameter.  FP64.
+// one CTA per source: the KL in warp 0 (16 lanes), the shape derivative in lane 32,
+// then per patch the item sums (lanes 0..12), the band's brightness moments (lanes
+// 32..35) and the image-frame shape Jacobian (lanes 40..48), and the chain rule with
+// one lane per parameter.  FP64 throughout, spread over lanes: a lone FP64 lane costs
+// a whole warp slot of the narrow FP64 pipe.
 constexpr int FZ_THREADS = 64;
 
 __global__ void __launch_bounds__(FZ_THREADS)
@@ -51,35 +53,44 @@ k_finalize(int n_src, int mode, const double* __restrict__ theta,
     if (s >= n_src) return;
     const int t = threadIdx.x;
     __shared__ double th[NP], klg[NP], Gy[NY + 1];
-    __shared__ double el[2], el2[2], dG[3][3], klv;
+    __shared__ double el[2], el2[2], dW[3][3], dG[3][3], klv;
     for (int i = t; i < NP; i += blockDim.x) th[i] = theta[(size_t)NP * s + i];
     __syncthreads();
-    if (t == 0) klv = kl_value_grad(*md, th, mode >= MODE_GRAD ? klg : nullptr);
+    if (t < 32) {
+        const double v = kl_warp(*md, th, klg);
+        if (t == 0) klv = v;
+    } else if (t == 32 && mode >= MODE_GRAD) {
+        shape_dW(th, dW);
+    }
+    __syncthreads();
     double gacc = 0.0, lacc = 0.0;
     const int nv = (mode >= MODE_GRAD) ? 1 + NY : 1;
     for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
         const PatchGeo g = geo[p];
+        const ImgMeta& im = img[g.img];
         if (t < nv) {
             double v = 0.0;
             for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
             Gy[t] = v;
-        }
-        const ImgMeta& im = img[g.img];
-        if (mode >= MODE_GRAD) {
-            if (t == 32) {
-                for (int i = 0; i < 2; ++i) band_moments(th, im.band, i, el[i], el2[i]);
-                double d[3][3];
-                shape_jacobian(im.A, th, d);
-                for (int a = 0; a < 3; ++a)
-                    for (int b = 0; b < 3; ++b) dG[a][b] = d[a][b];
+        } else if (mode >= MODE_GRAD && t >= 32 && t < 36) {
+            const int i = (t - 32) >> 1, second = (t - 32) & 1;
+            double m = th[P_R1 + i], v = th[P_R2 + i];
+            for (int j = 0; j < 4; ++j) {
+                const double b = color_beta(im.band, j);
+                m += b * th[P_C1 + 4 * i + j];
+                v += b * b * th[P_C2 + 4 * i + j];
             }
+            if (second) el2[i] = exp(2.0 * m + 2.0 * v);
+            else el[i] = exp(m + 0.5 * v);
+        } else if (mode >= MODE_GRAD && t >= 40 && t < 49) {
+            const int q = (t - 40) / 3, c = (t - 40) % 3;
+            dG[q][c] = shape_dG_entry(im.A, dW, q, c);
         }
         __syncthreads();
         if (t == 0) lacc += Gy[0];
         if (mode >= MODE_GRAD && t < NP) gacc += chain_entry(t, im.band, im.A, Gy + 1, el, el2, dG);
         __syncthreads();
     }
-    __syncthreads();   // klv / klg from thread 0 (sources without patches skip the loop)
     if (t == 0) {
         kl_out[s] = klv;
         if (local_out) local_out[s] = lacc - klv;

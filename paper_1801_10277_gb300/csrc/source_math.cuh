@@ -108,4 +108,87 @@ __device__ inline void band_moments(const double* th, int band, int i, double& e
     el2 = exp(2.0 * m + 2.0 * v);
 }
 
+// The same KL and gradient computed by the 16 lanes 0..15 of one warp, lane = 8 i + d
+// (type i, colour-prior component d); every lane of the warp must call it.  Writes the
+// gradient (all 44 entries, zero for position and shape) into g (shared) and returns
+// the KL on every lane.  FP64, but one warp instruction per step instead of sixteen.
+__device__ inline double kl_warp(const ModelDev& md, const double* th, double* g) {
+    const int lane = threadIdx.x & 31;
+    const int i = (lane >> 3) & 1, d = lane & 7;
+    const bool act = lane < 16;
+    double term = 0.0, dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
+    const double a = th[P_A + i];
+    double c2[4];
+    for (int j = 0; j < 4; ++j) c2[j] = th[P_C2 + 4 * i + j];
+    if (act) {
+        double slog = 0.0;
+        for (int j = 0; j < 4; ++j) slog += log(c2[j]);
+        const double k = th[P_K + NCOMP * i + d];
+        const double* Pm = md.prior_P[i][d];
+        const double* mu = md.prior_mu[i][d];
+        double diff[4], quad = 0.0, tr = 0.0;
+        for (int j = 0; j < 4; ++j) diff[j] = th[P_C1 + 4 * i + j] - mu[j];
+        for (int j = 0; j < 4; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
+            quad += diff[j] * s;
+            tr += Pm[5 * j] * c2[j];
+            dc1[j] = k * s;
+            dc2[j] = 0.5 * k * (Pm[5 * j] - 1.0 / c2[j]);
+        }
+        const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
+        const double lk = log(k / md.prior_w[i][d]);
+        term = k * (lk + klc);
+        g[P_K + NCOMP * i + d] = a * (lk + 1.0 + klc);
+    }
+    // sums over the eight components of each type
+    for (int o = 1; o < 8; o <<= 1) {
+        term += __shfl_xor_sync(0xffffffffu, term, o);
+        for (int j = 0; j < 4; ++j) {
+            dc1[j] += __shfl_xor_sync(0xffffffffu, dc1[j], o);
+            dc2[j] += __shfl_xor_sync(0xffffffffu, dc2[j], o);
+        }
+    }
+    double klv = 0.0;
+    if (act && d == 0) {
+        const double phi = (i == 0) ? md.prior_star : 1.0 - md.prior_star;
+        const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
+        const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
+        const double K = 0.5 * (log(pv / r2) + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
+        const double la = log(a / phi);
+        klv = a * (la + K);
+        g[P_A + i] = la + 1.0 + K;
+        g[P_R1 + i] = a * (r1 - pm) / pv;
+        g[P_R2 + i] = a * 0.5 * (1.0 / pv - 1.0 / r2);
+        for (int j = 0; j < 4; ++j) {
+            g[P_C1 + 4 * i + j] = a * dc1[j];
+            g[P_C2 + 4 * i + j] = a * dc2[j];
+        }
+    }
+    if (lane < 6) g[lane] = 0.0;   // position and shape carry no prior
+    klv += __shfl_xor_sync(0xffffffffu, klv, 8);
+    return __shfl_sync(0xffffffffu, klv, 0);
+}
+
+// world-frame d(Wxx, Wxy, Wyy)/d(e_axis, e_angle, e_scale)
+__device__ inline void shape_dW(const double* th, double dW[3][3]) {
+    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
+    const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
+    double s2, c2;
+    sincos(2.0 * phi, &s2, &c2);
+    double da = sg * sg * rho, db = -sg * sg * rho;
+    dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+    dW[1][0] = -2.0 * bh * s2; dW[1][1] = 2.0 * bh * c2; dW[1][2] = 2.0 * bh * s2;
+    da = sg * (1.0 + rho * rho); db = sg * (1.0 - rho * rho);
+    dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
+}
+
+// one entry (q, c) of dG = A dW A^T, c = 0 xx, 1 xy, 2 yy
+__device__ inline double shape_dG_entry(const double* A, const double dW[3][3], int q, int c) {
+    const double wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
+    if (c == 0) return A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+    if (c == 1) return A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+    return A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
+}
+
 }  // namespace cel
