@@ -354,6 +354,30 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
             g.nitem = (int)items.size() - g.item0;
             n_sp += npx;
         }
+    // per-(source, pixel) flag: 1 when no other patch covers the pixel (those pixels are
+    // finished by k_contrib; k_gather visits only cells that two or more patches touch)
+    std::vector<uint8_t> single((size_t)n_sp, 0);
+    {
+        std::vector<std::vector<uint8_t>> cover(n_img);
+        for (int p = 0; p < n_patch; ++p) {
+            const PatchGeo& g = geo[p];
+            auto& c = cover[g.img];
+            if (c.empty()) c.assign((size_t)im[g.img].H * im[g.img].W, 0);
+            for (int yy = 0; yy < g.h; ++yy)
+                for (int xx = 0; xx < g.w; ++xx) {
+                    uint8_t& v = c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx];
+                    if (v < 255) ++v;
+                }
+        }
+        for (int p = 0; p < n_patch; ++p) {
+            const PatchGeo& g = geo[p];
+            const auto& c = cover[g.img];
+            for (int yy = 0; yy < g.h; ++yy)
+                for (int xx = 0; xx < g.w; ++xx)
+                    single[(size_t)g.sp_off + (size_t)yy * g.w + xx] =
+                        c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx] == 1;
+        }
+    }
     // tiles: per image a dense grid of TILE x TILE cells, each with its covering patches
     std::vector<Tile> tiles;
     std::vector<int32_t> tile_list;
@@ -377,7 +401,7 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
             for (int ty = 0; ty < th; ++ty)
                 for (int tx = 0; tx < tw; ++tx) {
                     auto& c = cell[(size_t)ty * tw + tx];
-                    if (c.empty()) continue;
+                    if (c.size() < 2) continue;   // a lone patch's pixels are done in k_contrib
                     Tile t{};
                     tile_grid[im[n].tg_off + (size_t)ty * tw + tx] = (int32_t)tiles.size();
                     t.img = n; t.x0 = tx * TILE; t.y0 = ty * TILE;
@@ -442,6 +466,9 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     if ((st = dupload(pr, &d_tiles, tiles.data(), tiles.size()))) return bail(st);
     if ((st = dupload(pr, &d_tl, tile_list.data(), tile_list.size()))) return bail(st);
     if ((st = dupload(pr, &d_tg, tile_grid.data(), tile_grid.size()))) return bail(st);
+    uint8_t* d_single;
+    if ((st = dupload(pr, &d_single, single.data(), single.size()))) return bail(st);
+    P.single = d_single;
     if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
     if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
@@ -460,6 +487,8 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.item_part = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_tile))) return bail(st);
     P.tile_ll = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
+    P.item_ll = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
@@ -493,8 +522,7 @@ static celeste_status run_device(celeste_problem* pr, const double* d_theta, int
     if (!pr || !d_theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
     cudaStream_t st = (cudaStream_t)stream;
     CEL_CUDA(cudaSetDevice(pr->device));
-    CEL_CUDA(cudaMemsetAsync(pr->P.status, 0, sizeof(int32_t), st));
-    CEL_CUDA(launch_check_theta(pr->P, d_theta, st));
+    CEL_CUDA(cudaMemsetAsync(pr->P.status, 0, sizeof(int32_t), st));   // checked in the epilogue
     return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
 }
 

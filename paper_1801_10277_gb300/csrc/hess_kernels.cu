@@ -359,10 +359,12 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 const int32_t* __restrict__ patch_off, const ImgMeta* __restrict__ img,
                 const ModelDev* __restrict__ md, const double* __restrict__ part,
                 double* __restrict__ kl_out, double* __restrict__ local_out,
-                double* __restrict__ grad_out, double* __restrict__ hess_out) {
+                double* __restrict__ grad_out, double* __restrict__ hess_out,
+                int32_t* __restrict__ status) {
     const int s = blockIdx.x;
     if (s >= n_src) return;
     const double* th = theta + (size_t)NP * s;
+    if (status && (int)threadIdx.x < NP) theta_domain_check(threadIdx.x, th[threadIdx.x], status);
     __shared__ double Hy[NY][NY];
     __shared__ double Gy[NY + 1];
     __shared__ int nzn[NP];
@@ -515,7 +517,7 @@ cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, dou
     if (P.n_src == 0) return cudaSuccess;
     k_finalize_hess<<<P.n_src, FH_THREADS, 0, st>>>(P.n_src, d_theta, P.geo, P.patch_off, P.img,
                                                     P.model, P.item_part, P.kl, d_local, d_grad,
-                                                    d_hess);
+                                                    d_hess, P.status);
     return cudaGetLastError();
 }
 

@@ -116,6 +116,8 @@ struct DevProblem {
     void* spE2;
     void* emap;
     void* vmap;
+    const uint8_t* single;   // per (source, pixel): 1 when no other patch covers the pixel (nullable)
+    double* item_ll;         // per work item: ll summed over its singly covered pixels
     double* item_part;
     double* tile_ll;
     double* kl;
@@ -130,7 +132,6 @@ celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const 
                                 celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t,
                                                           double*, double*));
 
-cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st);
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st);
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);

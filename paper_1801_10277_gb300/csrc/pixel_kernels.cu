@@ -25,7 +25,12 @@ namespace {
 constexpr double LOG2E = 1.4426950408889634073599246810019;
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
-__device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+// 2^x on the SFU in one instruction (flush-to-zero: results below 2^-126 become 0)
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double ex2(double x) { return exp2(x); }
 __device__ __forceinline__ float lg(float x) { return logf(x); }
 __device__ __forceinline__ double lg(double x) { return log(x); }
@@ -66,27 +71,6 @@ __device__ __forceinline__ void load_table(R* sT, const R* gT, int n) {
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------------
-// Domain check of theta for the device-pointer entry points: writes
-// CELESTE_ERR_ARG / CELESTE_ERR_NONFINITE into the status word; never traps.
-
-__global__ void k_check_theta(const double* __restrict__ theta, int n_src, int32_t* status) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_src) return;
-    const double* th = theta + (size_t)NP * s;
-    bool fin = true;
-    for (int i = 0; i < NP; ++i) fin = fin && isfinite(th[i]);
-    bool ok = th[P_EDEV] >= 0 && th[P_EDEV] <= 1 && th[P_AXIS] > 0 && th[P_AXIS] <= 1 &&
-              th[P_SCALE] > 0;
-    for (int i = 0; i < 2; ++i) {
-        ok = ok && th[P_R2 + i] > 0 && th[P_A + i] > 0 && th[P_A + i] < 1;
-        for (int j = 0; j < 4; ++j) ok = ok && th[P_C2 + 4 * i + j] > 0;
-        for (int d = 0; d < NCOMP; ++d) ok = ok && th[P_K + NCOMP * i + d] > 0;
-    }
-    if (!fin) atomicExch(status, (int32_t)CELESTE_ERR_NONFINITE);
-    else if (!ok) atomicExch(status, (int32_t)CELESTE_ERR_ARG);
-}
 
 // ---------------------------------------------------------------------------------
 // k_prep: one CTA per patch; thread c builds mixture component c.
@@ -202,48 +186,76 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
 //   Var_s = sum_i a_i iota^2 E[l_i^2] g_i^2 - E_s^2, evaluated as
 //           sum_i a_i f_i^2 (E[l_i^2]/E[l_i]^2 - 1) + a0 (1-a0) f0^2 + a1 (1-a1) f1^2 - 2 a0 a1 f0 f1
 //   (the same polynomial, rearranged so FP32 does not cancel two large squares).
+// A pixel no other patch covers is finished here: E = sky + E_s, Var = Var_s and its
+// expected log-likelihood go straight to the maps and to the item's ll sum; only
+// pixels covered by several patches keep E_s / Var_s for k_gather.
 
 template <class R>
 __global__ void __launch_bounds__(CHUNK) k_contrib(const WorkItem* __restrict__ items,
                                                    const PatchGeo* __restrict__ geo,
                                                    const ImgMeta* __restrict__ img, int nprof,
                                                    const R* __restrict__ tbl, R* __restrict__ spE,
-                                                   R* __restrict__ spV) {
+                                                   R* __restrict__ spV,
+                                                   const uint8_t* __restrict__ single,
+                                                   const float* __restrict__ pixels,
+                                                   const float* __restrict__ sky_map,
+                                                   R* __restrict__ emap, R* __restrict__ vmap,
+                                                   double* __restrict__ item_ll) {
     __shared__ R sT[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
-    const int npsf = img[g.img].npsf;
+    const ImgMeta& im = img[g.img];
+    const int npsf = im.npsf;
     load_table(sT, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
     const int t = threadIdx.x;
-    if (t >= it.n) return;
-    const int q = it.q0 + t;
-    const int yy = q / g.w, xx = q - yy * g.w;
-    R g0 = 0, g1 = 0;
-    for (int k = 0; k < npsf; ++k) {
-        const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
-        const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
-        const R* S = sT + T_STAR + k * STAR_STRIDE;
-        g0 += S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
-        const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
-        for (int j = 0; j < nprof; ++j, G += GAL_STRIDE)
-            g1 += G[7] * ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+    R ll[1] = {0};
+    if (t < it.n) {
+        const int q = it.q0 + t;
+        const int yy = q / g.w, xx = q - yy * g.w;
+        R g0 = 0, g1 = 0;
+        for (int k = 0; k < npsf; ++k) {
+            const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
+            const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+            const R* S = sT + T_STAR + k * STAR_STRIDE;
+            g0 += S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
+            const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE)
+                g1 += G[7] * ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+        }
+        const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+        const R el0 = sT[H_EL0], el1 = sT[H_EL1];
+        const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+        const R e = a0 * f0 + a1 * f1;
+        const R em0 = sT[H_EL20] / (el0 * el0) - (R)1, em1 = sT[H_EL21] / (el1 * el1) - (R)1;
+        const R v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * ((R)1 - a0) * f0 * f0 +
+                    a1 * ((R)1 - a1) * f1 * f1 - (R)2 * a0 * a1 * f0 * f1;
+        const int64_t sp = g.sp_off + q;
+        if (single && single[sp]) {
+            const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+            const R E = (im.has_sky_map ? (R)sky_map[m] : (R)im.sky) + e;
+            const R x = (R)pixels[m];
+            const R iE = (R)1 / E;
+            ll[0] = x * (lg(E) - (R)0.5 * v * iE * iE) - E;
+            emap[m] = E;
+            vmap[m] = v;
+        } else {
+            spE[sp] = e;
+            spV[sp] = v;
+        }
     }
-    const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
-    const R el0 = sT[H_EL0], el1 = sT[H_EL1];
-    const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
-    const R e = a0 * f0 + a1 * f1;
-    const R em0 = sT[H_EL20] / (el0 * el0) - (R)1, em1 = sT[H_EL21] / (el1 * el1) - (R)1;
-    const R v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * ((R)1 - a0) * f0 * f0 +
-                a1 * ((R)1 - a1) * f1 * f1 - (R)2 * a0 * a1 * f0 * f1;
-    spE[g.sp_off + q] = e;
-    spV[g.sp_off + q] = v;
+    if (single) {
+        double tot[1];
+        cta_sum<R, 1>(ll, tot);
+        if (threadIdx.x == 0) item_ll[blockIdx.x] = tot[0];
+    }
 }
 
 // ---------------------------------------------------------------------------------
 // k_gather: E = sky + sum_s E_s, Var = sum_s Var_s over the sources covering each
 // pixel of a tile (ascending source order), and the expected log-likelihood
 //   ll = x (log E - Var / (2 E^2)) - E      (delta-method reading of E_q[log F])
-// at pixels inside at least one patch.  One FP64 ll sum per tile.
+// at pixels covered by at least min_cover patches (2 when k_contrib finished the
+// singly covered ones, else 1).  One ll sum per tile.
 
 template <class R>
 __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ tiles,
@@ -255,7 +267,8 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
                                                        const R* __restrict__ spE,
                                                        const R* __restrict__ spV,
                                                        R* __restrict__ emap, R* __restrict__ vmap,
-                                                       double* __restrict__ tile_ll) {
+                                                       double* __restrict__ tile_ll,
+                                                       int min_cover) {
     const Tile tl = tiles[blockIdx.x];
     const ImgMeta& im = img[tl.img];
     const int gx = tl.x0 + (int)(threadIdx.x % TILE), gy = tl.y0 + (int)(threadIdx.x / TILE);
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
         const int64_t m = im.px_off + (int64_t)gy * im.W + gx;
         R E = im.has_sky_map ? (R)sky_map[m] : (R)im.sky;
         R V = 0;
-        bool cov = false;
+        int cov = 0;
         for (int e = 0; e < tl.list_n; ++e) {
             const PatchGeo g = geo[tile_list[tl.list_off + e]];
             const int xx = gx - g.x0, yy = gy - g.y0;
@@ -272,10 +285,10 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
                 const int64_t q = g.sp_off + (int64_t)yy * g.w + xx;
                 E += spE[q];
                 V += spV[q];
-                cov = true;
+                ++cov;
             }
         }
-        if (cov) {
+        if (cov >= min_cover) {
             const R x = (R)pixels[m];
             const R iE = (R)1 / E;
             ll[0] = x * (lg(E) - (R)0.5 * V * iE * iE) - E;
@@ -385,11 +398,6 @@ __global__ void __launch_bounds__(CHUNK) k_adjoint(const WorkItem* __restrict__ 
 // ---------------------------------------------------------------------------------
 // launchers
 
-cudaError_t launch_check_theta(const DevProblem& P, const double* d_theta, cudaStream_t st) {
-    if (P.n_src > 0) k_check_theta<<<(P.n_src + 127) / 128, 128, 0, st>>>(d_theta, P.n_src, P.status);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st) {
     if (P.n_patch == 0) return cudaSuccess;
@@ -406,10 +414,14 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) 
     if (P.n_item == 0) return cudaSuccess;
     if (precision == CELESTE_FP64)
         k_contrib<double><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl64,
-                                                      (double*)P.spE, (double*)P.spE2);
+                                                      (double*)P.spE, (double*)P.spE2, P.single,
+                                                      P.pixels, P.sky_map, (double*)P.emap,
+                                                      (double*)P.vmap, P.item_ll);
     else
         k_contrib<float><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
-                                                     (float*)P.spE, (float*)P.spE2);
+                                                     (float*)P.spE, (float*)P.spE2, P.single,
+                                                     P.pixels, P.sky_map, (float*)P.emap,
+                                                     (float*)P.vmap, P.item_ll);
     return cudaGetLastError();
 }
 
@@ -418,11 +430,11 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
     if (precision == CELESTE_FP64)
         k_gather<double><<<P.n_tile, TILE * TILE, 0, st>>>(
             P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const double*)P.spE,
-            (const double*)P.spE2, (double*)P.emap, (double*)P.vmap, P.tile_ll);
+            (const double*)P.spE2, (double*)P.emap, (double*)P.vmap, P.tile_ll, P.single ? 2 : 1);
     else
         k_gather<float><<<P.n_tile, TILE * TILE, 0, st>>>(
             P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const float*)P.spE,
-            (const float*)P.spE2, (float*)P.emap, (float*)P.vmap, P.tile_ll);
+            (const float*)P.spE2, (float*)P.emap, (float*)P.vmap, P.tile_ll, P.single ? 2 : 1);
     return cudaGetLastError();
 }
 

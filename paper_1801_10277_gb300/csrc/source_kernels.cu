@@ -48,13 +48,15 @@ k_finalize(int n_src, int mode, const double* __restrict__ theta,
            const PatchGeo* __restrict__ geo, const int32_t* __restrict__ patch_off,
            const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
            const double* __restrict__ part, double* __restrict__ kl_out,
-           double* __restrict__ local_out, double* __restrict__ grad_out) {
+           double* __restrict__ local_out, double* __restrict__ grad_out,
+           int32_t* __restrict__ status) {
     const int s = blockIdx.x;
     if (s >= n_src) return;
     const int t = threadIdx.x;
     __shared__ double th[NP], klg[NP], Gy[NY + 1];
     __shared__ double el[2], el2[2], dW[3][3], dG[3][3], klv;
     for (int i = t; i < NP; i += blockDim.x) th[i] = theta[(size_t)NP * s + i];
+    if (status && t < NP) theta_domain_check(t, theta[(size_t)NP * s + t], status);
     __syncthreads();
     if (t < 32) {
         const double v = kl_warp(*md, th, klg);
@@ -98,12 +100,14 @@ k_finalize(int n_src, int mode, const double* __restrict__ theta,
     if (mode >= MODE_GRAD && grad_out && t < NP) grad_out[(size_t)NP * s + t] = gacc - klg[t];
 }
 
-// total = sum of tile ll sums - sum of KL, one CTA, fixed order
+// total = sum of tile and item ll sums - sum of KL, one CTA, fixed order
 __global__ void k_total(const double* __restrict__ tile_ll, int n_tile,
+                        const double* __restrict__ item_ll, int n_item,
                         const double* __restrict__ kl, int n_src, double* __restrict__ out) {
     __shared__ double red[512];
     double s = 0.0;
     for (int i = threadIdx.x; i < n_tile; i += blockDim.x) s += tile_ll[i];
+    for (int i = threadIdx.x; i < n_item; i += blockDim.x) s += item_ll[i];
     for (int i = threadIdx.x; i < n_src; i += blockDim.x) s -= kl[i];
     red[threadIdx.x] = s;
     __syncthreads();
@@ -126,9 +130,11 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int mode
     } else if (P.n_src > 0) {
         k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo, P.patch_off,
                                                    P.img, P.model, P.item_part, P.kl, d_local,
-                                                   d_grad);
+                                                   d_grad, P.status);
     }
-    if (d_total) k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.kl, P.n_src, d_total);
+    if (d_total)
+        k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl,
+                                   P.n_src, d_total);
     return cudaGetLastError();
 }
 

@@ -170,6 +170,23 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g
     return __shfl_sync(0xffffffffu, klv, 0);
 }
 
+// Domain of parameter j (celeste.h): every entry finite; e_dev in [0,1]; e_axis in
+// (0,1]; e_scale, r2, c2, k > 0; a in (0,1).  A violation sets the status word
+// (CELESTE_ERR_NONFINITE or CELESTE_ERR_ARG); nothing traps.
+__device__ inline void theta_domain_check(int j, double x, int32_t* status) {
+    bool ok;
+    if (!isfinite(x)) {
+        atomicExch(status, (int32_t)CELESTE_ERR_NONFINITE);
+        return;
+    }
+    if (j == P_EDEV) ok = x >= 0.0 && x <= 1.0;
+    else if (j == P_AXIS) ok = x > 0.0 && x <= 1.0;
+    else if (j == P_SCALE || (j >= P_R2 && j < P_C1) || (j >= P_C2 && j < P_A) || j >= P_K) ok = x > 0.0;
+    else if (j == P_A || j == P_A + 1) ok = x > 0.0 && x < 1.0;
+    else ok = true;
+    if (!ok) atomicExch(status, (int32_t)CELESTE_ERR_ARG);
+}
+
 // world-frame d(Wxx, Wxy, Wyy)/d(e_axis, e_angle, e_scale)
 __device__ inline void shape_dW(const double* th, double dW[3][3]) {
     const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
