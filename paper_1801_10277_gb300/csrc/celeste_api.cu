@@ -188,7 +188,7 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
         CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
                        [&] { return launch_adjoint(P, precision, mode, st); }));
     CEL_CUDA(timed(pr, "finalize", st, [&] {
-        return launch_finalize(P, d_theta, mode, d_total, d_local, d_grad, d_hess, st);
+        return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
     }));
     return CELESTE_OK;
 }
@@ -288,6 +288,7 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                 return fail(CELESTE_ERR_NOT_PD, "colour prior covariance (%d,%d) not positive definite", i, d);
         }
     }
+    fill_float_copies(md);
     // ---- images
     std::vector<ImgMeta> im(n_img);
     int64_t n_px = 0;
@@ -326,6 +327,7 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
             }
             if (!psd2(ps[3], ps[4], ps[5])) return fail(CELESTE_ERR_NOT_PD, "image %d psf %d covariance not positive definite", n, k);
         }
+        fill_float_copies(M);
         npsf_max = std::max(npsf_max, (int)I.n_psf);
         n_px += (int64_t)I.height * I.width;
     }

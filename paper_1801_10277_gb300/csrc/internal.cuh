@@ -52,6 +52,7 @@ struct ImgMeta {
     double sky, iota;
     double A[4], t[2];
     double psf[MAXPSF][6];
+    float psf_f[MAXPSF][6];  // the same in FP32 (conversions run on the narrow FP64 pipe)
 };
 
 struct PatchGeo {
@@ -77,7 +78,45 @@ struct ModelDev {
     double prior_mu[2][NCOMP][4];
     double prior_P[2][NCOMP][16];     // inverse covariances
     double prior_logdet[2][NCOMP];
+    // FP32 copies for the FP32 path
+    float prof_w_f[MAXPROF], prof_nu_f[MAXPROF];
+    float prior_star_f;
+    float prior_r_f[2][2];
+    float prior_w_f[2][NCOMP];
+    float prior_mu_f[2][NCOMP][4];
+    float prior_P_f[2][NCOMP][16];
+    float prior_logdet_f[2][NCOMP];
 };
+
+// FP32 copies of the model / image constants, filled once on the host
+inline void fill_float_copies(ModelDev& m) {
+    for (int j = 0; j < MAXPROF; ++j) {
+        m.prof_w_f[j] = (float)m.prof_w[j];
+        m.prof_nu_f[j] = (float)m.prof_nu[j];
+    }
+    m.prior_star_f = (float)m.prior_star;
+    for (int i = 0; i < 2; ++i) {
+        for (int c = 0; c < 2; ++c) m.prior_r_f[i][c] = (float)m.prior_r[i][c];
+        for (int d = 0; d < NCOMP; ++d) {
+            m.prior_w_f[i][d] = (float)m.prior_w[i][d];
+            m.prior_logdet_f[i][d] = (float)m.prior_logdet[i][d];
+            for (int j = 0; j < 4; ++j) m.prior_mu_f[i][d][j] = (float)m.prior_mu[i][d][j];
+            for (int j = 0; j < 16; ++j) m.prior_P_f[i][d][j] = (float)m.prior_P[i][d][j];
+        }
+    }
+}
+inline void fill_float_copies(ImgMeta& im) {
+    for (int k = 0; k < MAXPSF; ++k)
+        for (int c = 0; c < 6; ++c) im.psf_f[k][c] = (float)im.psf[k][c];
+}
+
+// precision-selected views of those constants
+__device__ inline const double* psf_row(const ImgMeta& im, int k, double) { return im.psf[k]; }
+__device__ inline const float* psf_row(const ImgMeta& im, int k, float) { return im.psf_f[k]; }
+__device__ inline double prof_w_of(const ModelDev& m, int j, double) { return m.prof_w[j]; }
+__device__ inline float prof_w_of(const ModelDev& m, int j, float) { return m.prof_w_f[j]; }
+__device__ inline double prof_nu_of(const ModelDev& m, int j, double) { return m.prof_nu[j]; }
+__device__ inline float prof_nu_of(const ModelDev& m, int j, float) { return m.prof_nu_f[j]; }
 
 // colour coefficient beta_bj: log l_b = log r + sum_j beta_bj c_j, colours c_j the
 // log ratio of band j+1 to band j and r the reference (r, index 2) band brightness.
@@ -138,7 +177,7 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st);
 cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st);
-cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int mode,
+cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,
                             cudaStream_t st);
 

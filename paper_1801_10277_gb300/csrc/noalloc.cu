@@ -177,6 +177,7 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
             return na_fail(CELESTE_ERR_NOT_PD, "PSF covariance not positive definite");
         for (int c = 0; c < 6; ++c) M.psf[k][c] = ps[c];
     }
+    fill_float_copies(M);
     ModelDev md;
     memset(&md, 0, sizeof md);
     md.n_exp = model->n_exp;
@@ -200,6 +201,7 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
                 return na_fail(CELESTE_ERR_NOT_PD, "colour prior covariance not positive definite");
         }
     }
+    fill_float_copies(md);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
         return na_fail(CELESTE_ERR_CUDA, "no current CUDA device");
@@ -250,7 +252,7 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
     if (e == cudaSuccess) e = launch_gather(P, precision, st);
     if (e == cudaSuccess) e = launch_adjoint(P, precision, MODE_GRAD, st);
     if (e == cudaSuccess)
-        e = launch_finalize(P, d_theta, MODE_GRAD, d_elbo_total, d_elbo_local, d_grad, nullptr, st);
+        e = launch_finalize(P, d_theta, precision, MODE_GRAD, d_elbo_total, d_elbo_local, d_grad, nullptr, st);
     if (e != cudaSuccess) return na_fail(CELESTE_ERR_CUDA, cudaGetErrorString(e));
     return CELESTE_OK;
 }

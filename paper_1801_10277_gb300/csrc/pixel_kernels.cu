@@ -106,11 +106,12 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
     if (t0 == 0) {
         // position relative to the patch origin in FP64 (the pixel frame spans 2048 px)
         const double* A = im.A;
-        const double mux = A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0;
-        const double muy = A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0;
+        const R mux = (R)(A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0);
+        const R muy = (R)(A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0);
         for (int k = 0; k < MAXPSF; ++k) {
-            T[T_MEAN + 2 * k] = (R)(k < npsf ? mux + im.psf[k][1] : 0.0);
-            T[T_MEAN + 2 * k + 1] = (R)(k < npsf ? muy + im.psf[k][2] : 0.0);
+            const R* ps = psf_row(im, k, R());
+            T[T_MEAN + 2 * k] = k < npsf ? mux + ps[1] : (R)0;
+            T[T_MEAN + 2 * k + 1] = k < npsf ? muy + ps[2] : (R)0;
         }
     } else if (t0 == 1) {
         // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi), G = A W A^T
@@ -147,15 +148,15 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
     const int per_k = 1 + nprof;
     for (int c = threadIdx.x; c < npsf * per_k; c += blockDim.x) {
         const int k = c / per_k, j = c % per_k - 1;
-        const double* ps = im.psf[k];
-        R cxx = (R)ps[3], cxy = (R)ps[4], cyy = (R)ps[5], w = (R)ps[0], dw = 0, nu = 0;
+        const R* ps = psf_row(im, k, R());
+        R cxx = ps[3], cxy = ps[4], cyy = ps[5], w = ps[0], dw = 0, nu = 0;
         if (j >= 0) {
-            nu = (R)md->prof_nu[j];
+            nu = prof_nu_of(*md, j, R());
             const bool dev = j >= md->n_exp;
             cxx += nu * gxx;
             cxy += nu * gxy;
             cyy += nu * gyy;
-            const R aw = (R)ps[0] * (R)md->prof_w[j];
+            const R aw = ps[0] * prof_w_of(*md, j, R());
             w = aw * (dev ? edev : (R)1 - edev);
             dw = dev ? aw : -aw;
         }
@@ -190,17 +191,17 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
 // expected log-likelihood go straight to the maps and to the item's ll sum; only
 // pixels covered by several patches keep E_s / Var_s for k_gather.
 
-template <class R>
-__global__ void __launch_bounds__(CHUNK) k_contrib(const WorkItem* __restrict__ items,
-                                                   const PatchGeo* __restrict__ geo,
-                                                   const ImgMeta* __restrict__ img, int nprof,
-                                                   const R* __restrict__ tbl, R* __restrict__ spE,
-                                                   R* __restrict__ spV,
-                                                   const uint8_t* __restrict__ single,
-                                                   const float* __restrict__ pixels,
-                                                   const float* __restrict__ sky_map,
-                                                   R* __restrict__ emap, R* __restrict__ vmap,
-                                                   double* __restrict__ item_ll) {
+template <class R, int PPT>
+__global__ void __launch_bounds__(CHUNK / PPT) k_contrib(const WorkItem* __restrict__ items,
+                                                         const PatchGeo* __restrict__ geo,
+                                                         const ImgMeta* __restrict__ img, int nprof,
+                                                         const R* __restrict__ tbl, R* __restrict__ spE,
+                                                         R* __restrict__ spV,
+                                                         const uint8_t* __restrict__ single,
+                                                         const float* __restrict__ pixels,
+                                                         const float* __restrict__ sky_map,
+                                                         R* __restrict__ emap, R* __restrict__ vmap,
+                                                         double* __restrict__ item_ll) {
     __shared__ R sT[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
@@ -208,34 +209,60 @@ __global__ void __launch_bounds__(CHUNK) k_contrib(const WorkItem* __restrict__ 
     const int npsf = im.npsf;
     load_table(sT, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
     const int t = threadIdx.x;
-    R ll[1] = {0};
-    if (t < it.n) {
-        const int q = it.q0 + t;
-        const int yy = q / g.w, xx = q - yy * g.w;
-        R g0 = 0, g1 = 0;
-        for (int k = 0; k < npsf; ++k) {
-            const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
-            const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
-            const R* S = sT + T_STAR + k * STAR_STRIDE;
-            g0 += S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
-            const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
-            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE)
-                g1 += G[7] * ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
+    // each thread evaluates PPT pixels with every component load shared between them
+    int xs[PPT], ys[PPT];
+    bool ok[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int l = t + p * (CHUNK / PPT);
+        ok[p] = l < it.n;
+        const int q = it.q0 + (ok[p] ? l : 0);
+        ys[p] = q / g.w;
+        xs[p] = q - ys[p] * g.w;
+    }
+    R g0[PPT], g1[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) g0[p] = g1[p] = 0;
+    for (int k = 0; k < npsf; ++k) {
+        const R mx = sT[T_MEAN + 2 * k], my = sT[T_MEAN + 2 * k + 1];
+        R dxx[PPT], dxy[PPT], dyy[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const R dx = (R)xs[p] - mx, dy = (R)ys[p] - my;
+            dxx[p] = dx * dx;
+            dxy[p] = dx * dy;
+            dyy[p] = dy * dy;
         }
-        const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
-        const R el0 = sT[H_EL0], el1 = sT[H_EL1];
-        const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+        const R* S = sT + T_STAR + k * STAR_STRIDE;
+        const R s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3], s7 = S[7];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) g0[p] += s7 * ex2(s0 * dxx[p] + s1 * dxy[p] + s2 * dyy[p] + s3);
+        const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+        for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+            const R c0 = G[0], c1 = G[1], c2 = G[2], c3 = G[3], c7 = G[7];
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) g1[p] += c7 * ex2(c0 * dxx[p] + c1 * dxy[p] + c2 * dyy[p] + c3);
+        }
+    }
+    const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+    const R el0 = sT[H_EL0], el1 = sT[H_EL1];
+    const R em0 = sT[H_EL20] / (el0 * el0) - (R)1, em1 = sT[H_EL21] / (el1 * el1) - (R)1;
+    R ll[1] = {0};
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if (!ok[p]) continue;
+        const R f0 = iota * el0 * g0[p], f1 = iota * el1 * g1[p];
         const R e = a0 * f0 + a1 * f1;
-        const R em0 = sT[H_EL20] / (el0 * el0) - (R)1, em1 = sT[H_EL21] / (el1 * el1) - (R)1;
         const R v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * ((R)1 - a0) * f0 * f0 +
                     a1 * ((R)1 - a1) * f1 * f1 - (R)2 * a0 * a1 * f0 * f1;
+        const int q = it.q0 + t + p * (CHUNK / PPT);
         const int64_t sp = g.sp_off + q;
         if (single && single[sp]) {
-            const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
+            const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
             const R E = (im.has_sky_map ? (R)sky_map[m] : (R)im.sky) + e;
             const R x = (R)pixels[m];
             const R iE = (R)1 / E;
-            ll[0] = x * (lg(E) - (R)0.5 * v * iE * iE) - E;
+            ll[0] += x * (lg(E) - (R)0.5 * v * iE * iE) - E;
             emap[m] = E;
             vmap[m] = v;
         } else {
@@ -309,15 +336,15 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
 //   dN/dmean = N P d,  dN/dG_xx = nu N ((Pd)_x^2 - Pxx)/2,  dN/dG_xy = nu N ((Pd)_x (Pd)_y - Pxy),
 //   dN/dG_yy = nu N ((Pd)_y^2 - Pyy)/2,  dN/de_dev = dc exp(...)/(...)
 
-template <class R, int MODE>
-__global__ void __launch_bounds__(CHUNK) k_adjoint(const WorkItem* __restrict__ items,
-                                                   const PatchGeo* __restrict__ geo,
-                                                   const ImgMeta* __restrict__ img, int nprof,
-                                                   const float* __restrict__ pixels,
-                                                   const R* __restrict__ tbl,
-                                                   const R* __restrict__ emap,
-                                                   const R* __restrict__ vmap,
-                                                   double* __restrict__ part) {
+template <class R, int MODE, int PPT>
+__global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restrict__ items,
+                                                         const PatchGeo* __restrict__ geo,
+                                                         const ImgMeta* __restrict__ img, int nprof,
+                                                         const float* __restrict__ pixels,
+                                                         const R* __restrict__ tbl,
+                                                         const R* __restrict__ emap,
+                                                         const R* __restrict__ vmap,
+                                                         double* __restrict__ part) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     __shared__ R sT[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
@@ -329,65 +356,97 @@ __global__ void __launch_bounds__(CHUNK) k_adjoint(const WorkItem* __restrict__ 
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = 0;
     const int t = threadIdx.x;
-    if (t < it.n) {
-        const int q = it.q0 + t;
-        const int yy = q / g.w, xx = q - yy * g.w;
-        const int64_t m = im.px_off + (int64_t)(g.y0 + yy) * im.W + (g.x0 + xx);
-        const R x = (R)pixels[m], E = emap[m], V = vmap[m];
+    int xs[PPT], ys[PPT];
+    bool ok[PPT];
+    R x[PPT], cE[PPT], cV[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int l = t + p * (CHUNK / PPT);
+        ok[p] = l < it.n;
+        const int q = it.q0 + (ok[p] ? l : 0);
+        ys[p] = q / g.w;
+        xs[p] = q - ys[p] * g.w;
+        const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
+        x[p] = (R)pixels[m];
+        const R E = emap[m], V = vmap[m];
         const R iE = (R)1 / E;
-        v[0] = x * (lg(E) - (R)0.5 * V * iE * iE) - E;
-        if constexpr (MODE >= MODE_GRAD) {
-            const R cE = x * (iE + V * iE * iE * iE) - (R)1;
-            const R cV = (R)-0.5 * x * iE * iE;
-            R g0 = 0, gx0 = 0, gy0 = 0;
-            R g1 = 0, gx1 = 0, gy1 = 0, de1 = 0, sxx = 0, sxy = 0, syy = 0;
-            for (int k = 0; k < npsf; ++k) {
-                const R dx = (R)xx - sT[T_MEAN + 2 * k], dy = (R)yy - sT[T_MEAN + 2 * k + 1];
-                const R dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
-                {
-                    const R* S = sT + T_STAR + k * STAR_STRIDE;
-                    const R n = S[7] * ex2(S[0] * dxx + S[1] * dxy + S[2] * dyy + S[3]);
-                    const R qx = S[4] * dx + S[5] * dy, qy = S[5] * dx + S[6] * dy;
-                    g0 += n;
-                    gx0 += n * qx;
-                    gy0 += n * qy;
-                }
-                const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
-                for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
-                    const R e = ex2(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
-                    const R n = G[7] * e;
-                    const R qx = G[4] * dx + G[5] * dy, qy = G[5] * dx + G[6] * dy;
-                    g1 += n;
-                    gx1 += n * qx;
-                    gy1 += n * qy;
-                    de1 += G[8] * e;
-                    const R nn = n * G[9];
-                    sxx += nn * (qx * qx - G[4]);
-                    sxy += nn * (qx * qy - G[5]);
-                    syy += nn * (qy * qy - G[6]);
+        if (ok[p]) v[0] += x[p] * (lg(E) - (R)0.5 * V * iE * iE) - E;
+        cE[p] = x[p] * (iE + V * iE * iE * iE) - (R)1;
+        cV[p] = (R)-0.5 * x[p] * iE * iE;
+    }
+    if constexpr (MODE >= MODE_GRAD) {
+        R g0[PPT], gx0[PPT], gy0[PPT], g1[PPT], gx1[PPT], gy1[PPT], de1[PPT], sxx[PPT], sxy[PPT], syy[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p)
+            g0[p] = gx0[p] = gy0[p] = g1[p] = gx1[p] = gy1[p] = de1[p] = sxx[p] = sxy[p] = syy[p] = 0;
+        for (int k = 0; k < npsf; ++k) {
+            const R mx = sT[T_MEAN + 2 * k], my = sT[T_MEAN + 2 * k + 1];
+            R dx[PPT], dy[PPT], dxx[PPT], dxy[PPT], dyy[PPT];
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                dx[p] = (R)xs[p] - mx;
+                dy[p] = (R)ys[p] - my;
+                dxx[p] = dx[p] * dx[p];
+                dxy[p] = dx[p] * dy[p];
+                dyy[p] = dy[p] * dy[p];
+            }
+            {
+                const R* S = sT + T_STAR + k * STAR_STRIDE;
+                const R s0 = S[0], s1 = S[1], s2 = S[2], s3 = S[3];
+                const R pxx = S[4], pxy = S[5], pyy = S[6], c = S[7];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const R n = c * ex2(s0 * dxx[p] + s1 * dxy[p] + s2 * dyy[p] + s3);
+                    const R qx = pxx * dx[p] + pxy * dy[p], qy = pxy * dx[p] + pyy * dy[p];
+                    g0[p] += n;
+                    gx0[p] += n * qx;
+                    gy0[p] += n * qy;
                 }
             }
-            const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
-            const R el0 = sT[H_EL0], el20 = sT[H_EL20], el1 = sT[H_EL1], el21 = sT[H_EL21];
-            const R f0 = iota * el0 * g0, f1 = iota * el1 * g1;
+            const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
+            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+                const R c0 = G[0], c1 = G[1], c2 = G[2], c3 = G[3];
+                const R pxx = G[4], pxy = G[5], pyy = G[6], c = G[7], dc = G[8], nu = G[9];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const R e = ex2(c0 * dxx[p] + c1 * dxy[p] + c2 * dyy[p] + c3);
+                    const R n = c * e;
+                    const R qx = pxx * dx[p] + pxy * dy[p], qy = pxy * dx[p] + pyy * dy[p];
+                    g1[p] += n;
+                    gx1[p] += n * qx;
+                    gy1[p] += n * qy;
+                    de1[p] += dc * e;
+                    const R nn = n * nu;
+                    sxx[p] += nn * (qx * qx - pxx);
+                    sxy[p] += nn * (qx * qy - pxy);
+                    syy[p] += nn * (qy * qy - pyy);
+                }
+            }
+        }
+        const R iota = sT[H_IOTA], a0 = sT[H_A0], a1 = sT[H_A1];
+        const R el0 = sT[H_EL0], el20 = sT[H_EL20], el1 = sT[H_EL1], el21 = sT[H_EL21];
+        const R i2 = iota * iota;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (!ok[p]) continue;
+            const R f0 = iota * el0 * g0[p], f1 = iota * el1 * g1[p];
             const R Es = a0 * f0 + a1 * f1;
-            const R w1 = cE - (R)2 * cV * Es, w2 = cV;
-            const R i2 = iota * iota;
-            const R s0 = i2 * g0 * g0, s1 = i2 * g1 * g1;
-            v[1 + Y_A0] = w1 * f0 + w2 * el20 * s0;
-            v[1 + Y_A1] = w1 * f1 + w2 * el21 * s1;
-            v[1 + Y_EL0] = w1 * a0 * iota * g0;
-            v[1 + Y_EL20] = w2 * a0 * s0;
-            v[1 + Y_EL1] = w1 * a1 * iota * g1;
-            v[1 + Y_EL21] = w2 * a1 * s1;
-            const R u0 = a0 * iota * (w1 * el0 + (R)2 * w2 * iota * el20 * g0);
-            const R u1 = a1 * iota * (w1 * el1 + (R)2 * w2 * iota * el21 * g1);
-            v[1 + Y_MX] = u0 * gx0 + u1 * gx1;
-            v[1 + Y_MY] = u0 * gy0 + u1 * gy1;
-            v[1 + Y_EDEV] = u1 * de1;
-            v[1 + Y_GXX] = (R)0.5 * u1 * sxx;
-            v[1 + Y_GXY] = u1 * sxy;
-            v[1 + Y_GYY] = (R)0.5 * u1 * syy;
+            const R w1 = cE[p] - (R)2 * cV[p] * Es, w2 = cV[p];
+            const R s0 = i2 * g0[p] * g0[p], s1 = i2 * g1[p] * g1[p];
+            v[1 + Y_A0] += w1 * f0 + w2 * el20 * s0;
+            v[1 + Y_A1] += w1 * f1 + w2 * el21 * s1;
+            v[1 + Y_EL0] += w1 * a0 * iota * g0[p];
+            v[1 + Y_EL20] += w2 * a0 * s0;
+            v[1 + Y_EL1] += w1 * a1 * iota * g1[p];
+            v[1 + Y_EL21] += w2 * a1 * s1;
+            const R u0 = a0 * iota * (w1 * el0 + (R)2 * w2 * iota * el20 * g0[p]);
+            const R u1 = a1 * iota * (w1 * el1 + (R)2 * w2 * iota * el21 * g1[p]);
+            v[1 + Y_MX] += u0 * gx0[p] + u1 * gx1[p];
+            v[1 + Y_MY] += u0 * gy0[p] + u1 * gy1[p];
+            v[1 + Y_EDEV] += u1 * de1[p];
+            v[1 + Y_GXX] += (R)0.5 * u1 * sxx[p];
+            v[1 + Y_GXY] += u1 * sxy[p];
+            v[1 + Y_GYY] += (R)0.5 * u1 * syy[p];
         }
     }
     double tot[NV];
@@ -397,6 +456,8 @@ __global__ void __launch_bounds__(CHUNK) k_adjoint(const WorkItem* __restrict__ 
 
 // ---------------------------------------------------------------------------------
 // launchers
+
+constexpr int PPT32 = 2;   // pixels per thread on the FP32 path
 
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st) {
@@ -413,12 +474,12 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) {
     if (P.n_item == 0) return cudaSuccess;
     if (precision == CELESTE_FP64)
-        k_contrib<double><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl64,
+        k_contrib<double, 1><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl64,
                                                       (double*)P.spE, (double*)P.spE2, P.single,
                                                       P.pixels, P.sky_map, (double*)P.emap,
                                                       (double*)P.vmap, P.item_ll);
     else
-        k_contrib<float><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
+        k_contrib<float, PPT32><<<P.n_item, CHUNK / PPT32, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
                                                      (float*)P.spE, (float*)P.spE2, P.single,
                                                      P.pixels, P.sky_map, (float*)P.emap,
                                                      (float*)P.vmap, P.item_ll);
@@ -438,22 +499,22 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <class R>
+template <class R, int PPT>
 static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st) {
     const R* em = (const R*)P.emap;
     const R* vm = (const R*)P.vmap;
     if (mode == MODE_LL)
-        k_adjoint<R, MODE_LL><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof,
-                                                          P.pixels, tbl, em, vm, P.item_part);
+        k_adjoint<R, MODE_LL, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
     else
-        k_adjoint<R, MODE_GRAD><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof,
-                                                            P.pixels, tbl, em, vm, P.item_part);
+        k_adjoint<R, MODE_GRAD, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
 }
 
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st) {
     if (P.n_item == 0) return cudaSuccess;
-    if (precision == CELESTE_FP64) adjoint_impl<double>(P, P.tbl64, mode, st);
-    else adjoint_impl<float>(P, P.tbl32, mode, st);
+    if (precision == CELESTE_FP64) adjoint_impl<double, 1>(P, P.tbl64, mode, st);
+    else adjoint_impl<float, PPT32>(P, P.tbl32, mode, st);
     return cudaGetLastError();
 }
 

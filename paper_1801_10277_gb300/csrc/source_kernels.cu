@@ -36,13 +36,20 @@ __device__ __forceinline__ double chain_entry(int j, int band, const double* A, 
     return kind == 2 ? b * dm : b * b * dv;
 }
 
-// one CTA per source: the KL in warp 0 (16 lanes), the shape derivative in lane 32,
+// one CTA per source: the KL in warp 0 (kl_warp), the shape derivative in lane 32,
 // then per patch the item sums (lanes 0..12), the band's brightness moments (lanes
 // 32..35) and the image-frame shape Jacobian (lanes 40..48), and the chain rule with
-// one lane per parameter.  FP64 throughout, spread over lanes: a lone FP64 lane costs
-// a whole warp slot of the narrow FP64 pipe.
+// one lane per parameter.  Transcendentals and the small per-source algebra run in the
+// path precision R; every sum is FP64.  (A lone FP64 lane costs a whole warp slot of
+// the narrow FP64 pipe, so no FP64 work is left to a single thread.)
 constexpr int FZ_THREADS = 64;
 
+__device__ __forceinline__ float exr(float x) { return expf(x); }
+__device__ __forceinline__ double exr(double x) { return exp(x); }
+__device__ __forceinline__ void scr(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void scr(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <class R>
 __global__ void __launch_bounds__(FZ_THREADS)
 k_finalize(int n_src, int mode, const double* __restrict__ theta,
            const PatchGeo* __restrict__ geo, const int32_t* __restrict__ patch_off,
@@ -54,15 +61,25 @@ k_finalize(int n_src, int mode, const double* __restrict__ theta,
     if (s >= n_src) return;
     const int t = threadIdx.x;
     __shared__ double th[NP], klg[NP], Gy[NY + 1];
-    __shared__ double el[2], el2[2], dW[3][3], dG[3][3], klv;
+    __shared__ double el[2], el2[2], dG[3][3], klv;
+    __shared__ R dW[3][3];
     for (int i = t; i < NP; i += blockDim.x) th[i] = theta[(size_t)NP * s + i];
     if (status && t < NP) theta_domain_check(t, theta[(size_t)NP * s + t], status);
     __syncthreads();
     if (t < 32) {
-        const double v = kl_warp(*md, th, klg);
+        const double v = kl_warp<R>(*md, th, klg);
         if (t == 0) klv = v;
     } else if (t == 32 && mode >= MODE_GRAD) {
-        shape_dW(th, dW);
+        // world-frame d(Wxx, Wxy, Wyy)/d(e_axis, e_angle, e_scale)
+        const R rho = (R)th[P_AXIS], phi = (R)th[P_ANGLE], sg = (R)th[P_SCALE];
+        const R bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
+        R s2, c2;
+        scr((R)2 * phi, &s2, &c2);
+        R da = sg * sg * rho, db = -sg * sg * rho;
+        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+        dW[1][0] = (R)-2 * bh * s2; dW[1][1] = (R)2 * bh * c2; dW[1][2] = (R)2 * bh * s2;
+        da = sg * ((R)1 + rho * rho); db = sg * ((R)1 - rho * rho);
+        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
     }
     __syncthreads();
     double gacc = 0.0, lacc = 0.0;
@@ -76,17 +93,23 @@ k_finalize(int n_src, int mode, const double* __restrict__ theta,
             Gy[t] = v;
         } else if (mode >= MODE_GRAD && t >= 32 && t < 36) {
             const int i = (t - 32) >> 1, second = (t - 32) & 1;
-            double m = th[P_R1 + i], v = th[P_R2 + i];
+            R m = (R)th[P_R1 + i], v = (R)th[P_R2 + i];
             for (int j = 0; j < 4; ++j) {
-                const double b = color_beta(im.band, j);
-                m += b * th[P_C1 + 4 * i + j];
-                v += b * b * th[P_C2 + 4 * i + j];
+                const R b = (R)color_beta(im.band, j);
+                m += b * (R)th[P_C1 + 4 * i + j];
+                v += b * b * (R)th[P_C2 + 4 * i + j];
             }
-            if (second) el2[i] = exp(2.0 * m + 2.0 * v);
-            else el[i] = exp(m + 0.5 * v);
+            if (second) el2[i] = (double)exr((R)2 * m + (R)2 * v);
+            else el[i] = (double)exr(m + (R)0.5 * v);
         } else if (mode >= MODE_GRAD && t >= 40 && t < 49) {
             const int q = (t - 40) / 3, c = (t - 40) % 3;
-            dG[q][c] = shape_dG_entry(im.A, dW, q, c);
+            const R a0 = (R)im.A[0], a1 = (R)im.A[1], a2 = (R)im.A[2], a3 = (R)im.A[3];
+            const R wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
+            R v;
+            if (c == 0) v = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
+            else if (c == 1) v = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
+            else v = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
+            dG[q][c] = (double)v;
         }
         __syncthreads();
         if (t == 0) lacc += Gy[0];
@@ -121,16 +144,23 @@ __global__ void k_total(const double* __restrict__ tile_ll, int n_tile,
 cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
                                  double* d_grad, double* d_hess, cudaStream_t st);
 
-cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int mode,
+cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,
                             cudaStream_t st) {
     if (mode == MODE_HESS) {
         cudaError_t e = launch_finalize_hess(P, d_theta, d_local, d_grad, d_hess, st);
         if (e != cudaSuccess) return e;
     } else if (P.n_src > 0) {
-        k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo, P.patch_off,
-                                                   P.img, P.model, P.item_part, P.kl, d_local,
-                                                   d_grad, P.status);
+        if (precision == CELESTE_FP64)
+            k_finalize<double><<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo,
+                                                               P.patch_off, P.img, P.model,
+                                                               P.item_part, P.kl, d_local, d_grad,
+                                                               P.status);
+        else
+            k_finalize<float><<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo,
+                                                              P.patch_off, P.img, P.model,
+                                                              P.item_part, P.kl, d_local, d_grad,
+                                                              P.status);
     }
     if (d_total)
         k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl,

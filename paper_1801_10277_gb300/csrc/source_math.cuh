@@ -109,65 +109,103 @@ __device__ inline void band_moments(const double* th, int band, int i, double& e
 }
 
 // The same KL and gradient computed by the 16 lanes 0..15 of one warp, lane = 8 i + d
-// (type i, colour-prior component d); every lane of the warp must call it.  Writes the
-// gradient (all 44 entries, zero for position and shape) into g (shared) and returns
-// the KL on every lane.  FP64, but one warp instruction per step instead of sixteen.
+// (type i, colour-prior component d); every lane of the warp must call it.  The
+// per-component algebra and the logarithms run in R (each lane takes one logarithm of
+// the shared ones in a single round); the sums over components and the outputs are
+// FP64.  Writes the gradient (all 44 entries, zero for position and shape) into g
+// (shared) and returns the KL on every lane.
+__device__ inline const double* prior_P_of(const ModelDev& m, int i, int d, double) { return m.prior_P[i][d]; }
+__device__ inline const float* prior_P_of(const ModelDev& m, int i, int d, float) { return m.prior_P_f[i][d]; }
+__device__ inline const double* prior_mu_of(const ModelDev& m, int i, int d, double) { return m.prior_mu[i][d]; }
+__device__ inline const float* prior_mu_of(const ModelDev& m, int i, int d, float) { return m.prior_mu_f[i][d]; }
+__device__ inline double prior_ld_of(const ModelDev& m, int i, int d, double) { return m.prior_logdet[i][d]; }
+__device__ inline float prior_ld_of(const ModelDev& m, int i, int d, float) { return m.prior_logdet_f[i][d]; }
+__device__ inline double prior_w_of(const ModelDev& m, int i, int d, double) { return m.prior_w[i][d]; }
+__device__ inline float prior_w_of(const ModelDev& m, int i, int d, float) { return m.prior_w_f[i][d]; }
+__device__ __forceinline__ float lgr(float x) { return logf(x); }
+__device__ __forceinline__ double lgr(double x) { return log(x); }
+
+template <class R>
 __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g) {
     const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    // round 1: one logarithm / reciprocal per lane
+    //   lanes 0..15 log(k_id / w_id); 16..23 log c2 and 1/c2; 24,25 log(a_i/Phi_i);
+    //   26,27 log(pv_i / r2_i) and 1/r2_i
+    R lv = 0, rv = 0;
+    if (lane < 16) {
+        const int i = lane >> 3, d = lane & 7;
+        lv = lgr((R)th[P_K + NCOMP * i + d] / prior_w_of(md, i, d, R()));
+    } else if (lane < 24) {
+        const R c = (R)th[P_C2 + (lane - 16)];
+        lv = lgr(c);
+        rv = (R)1 / c;
+    } else if (lane < 26) {
+        const int i = lane - 24;
+        const R phi = (i == 0) ? (R)md.prior_star : (R)1 - (R)md.prior_star;
+        lv = lgr((R)th[P_A + i] / phi);
+    } else if (lane < 28) {
+        const int i = lane - 26;
+        const R r2 = (R)th[P_R2 + i];
+        lv = lgr((R)md.prior_r[i][1] / r2);
+        rv = (R)1 / r2;
+    }
     const int i = (lane >> 3) & 1, d = lane & 7;
-    const bool act = lane < 16;
+    R ic2[4], slog = 0;
+    for (int j = 0; j < 4; ++j) {
+        slog += __shfl_sync(full, lv, 16 + 4 * i + j);
+        ic2[j] = __shfl_sync(full, rv, 16 + 4 * i + j);
+    }
+    const R la = __shfl_sync(full, lv, 24 + i);
+    const R lpr = __shfl_sync(full, lv, 26 + i);
+    const R ir2 = __shfl_sync(full, rv, 26 + i);
+    // round 2: per-component terms (lanes 0..15)
     double term = 0.0, dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
-    const double a = th[P_A + i];
-    double c2[4];
-    for (int j = 0; j < 4; ++j) c2[j] = th[P_C2 + 4 * i + j];
-    if (act) {
-        double slog = 0.0;
-        for (int j = 0; j < 4; ++j) slog += log(c2[j]);
-        const double k = th[P_K + NCOMP * i + d];
-        const double* Pm = md.prior_P[i][d];
-        const double* mu = md.prior_mu[i][d];
-        double diff[4], quad = 0.0, tr = 0.0;
-        for (int j = 0; j < 4; ++j) diff[j] = th[P_C1 + 4 * i + j] - mu[j];
+    const R a = (R)th[P_A + i];
+    if (lane < 16) {
+        const R k = (R)th[P_K + NCOMP * i + d];
+        const R* Pm = prior_P_of(md, i, d, R());
+        const R* mu = prior_mu_of(md, i, d, R());
+        R diff[4], quad = 0, tr = 0;
+        for (int j = 0; j < 4; ++j) diff[j] = (R)th[P_C1 + 4 * i + j] - mu[j];
         for (int j = 0; j < 4; ++j) {
-            double s = 0.0;
+            R s = 0;
             for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
             quad += diff[j] * s;
-            tr += Pm[5 * j] * c2[j];
-            dc1[j] = k * s;
-            dc2[j] = 0.5 * k * (Pm[5 * j] - 1.0 / c2[j]);
+            tr += Pm[5 * j] * (R)th[P_C2 + 4 * i + j];
+            dc1[j] = (double)(k * s);
+            dc2[j] = (double)((R)0.5 * k * (Pm[5 * j] - ic2[j]));
         }
-        const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
-        const double lk = log(k / md.prior_w[i][d]);
-        term = k * (lk + klc);
-        g[P_K + NCOMP * i + d] = a * (lk + 1.0 + klc);
+        const R klc = (R)0.5 * (tr + quad - (R)4 + prior_ld_of(md, i, d, R()) - slog);
+        term = (double)(k * (lv + klc));
+        g[P_K + NCOMP * i + d] = (double)(a * (lv + (R)1 + klc));
     }
-    // sums over the eight components of each type
+    // FP64 sums over the eight components of each type
     for (int o = 1; o < 8; o <<= 1) {
-        term += __shfl_xor_sync(0xffffffffu, term, o);
+        term += __shfl_xor_sync(full, term, o);
         for (int j = 0; j < 4; ++j) {
-            dc1[j] += __shfl_xor_sync(0xffffffffu, dc1[j], o);
-            dc2[j] += __shfl_xor_sync(0xffffffffu, dc2[j], o);
+            dc1[j] += __shfl_xor_sync(full, dc1[j], o);
+            dc2[j] += __shfl_xor_sync(full, dc2[j], o);
         }
     }
     double klv = 0.0;
-    if (act && d == 0) {
-        const double phi = (i == 0) ? md.prior_star : 1.0 - md.prior_star;
+    if (lane < 16 && d == 0) {
         const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
         const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
-        const double K = 0.5 * (log(pv / r2) + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
-        const double la = log(a / phi);
-        klv = a * (la + K);
-        g[P_A + i] = la + 1.0 + K;
-        g[P_R1 + i] = a * (r1 - pm) / pv;
-        g[P_R2 + i] = a * 0.5 * (1.0 / pv - 1.0 / r2);
+        const double K = 0.5 * ((double)lpr + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
+        const double ad = th[P_A + i];
+        klv = ad * ((double)la + K);
+        g[P_A + i] = (double)la + 1.0 + K;
+        g[P_R1 + i] = ad * (r1 - pm) / pv;
+        g[P_R2 + i] = ad * 0.5 * (1.0 / pv - (double)ir2);
         for (int j = 0; j < 4; ++j) {
-            g[P_C1 + 4 * i + j] = a * dc1[j];
-            g[P_C2 + 4 * i + j] = a * dc2[j];
+            g[P_C1 + 4 * i + j] = ad * dc1[j];
+            g[P_C2 + 4 * i + j] = ad * dc2[j];
         }
     }
     if (lane < 6) g[lane] = 0.0;   // position and shape carry no prior
-    klv += __shfl_xor_sync(0xffffffffu, klv, 8);
-    return __shfl_sync(0xffffffffu, klv, 0);
+    klv += __shfl_xor_sync(full, klv, 8);
+    return __shfl_sync(full, klv, 0);
 }
 
 // Domain of parameter j (celeste.h): every entry finite; e_dev in [0,1]; e_axis in
