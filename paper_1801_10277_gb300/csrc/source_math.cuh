@@ -110,9 +110,8 @@ __device__ inline void band_moments(const double* th, int band, int i, double& e
 
 // The same KL and gradient computed by the 16 lanes 0..15 of one warp, lane = 8 i + d
 // (type i, colour-prior component d); every lane of the warp must call it.  The
-// per-component algebra and the logarithms run in R (each lane takes one logarithm of
-// the shared ones in a single round); the sums over components and the outputs are
-// FP64.  Writes the gradient (all 44 entries, zero for position and shape) into g
+// logarithms and reciprocals are FP64, one per lane in a single round; the 4 x 4
+// per-component algebra runs in R; the sums over components and the outputs are FP64.  Writes the gradient (all 44 entries, zero for position and shape) into g
 // (shared) and returns the KL on every lane.
 __device__ inline const double* prior_P_of(const ModelDev& m, int i, int d, double) { return m.prior_P[i][d]; }
 __device__ inline const float* prior_P_of(const ModelDev& m, int i, int d, float) { return m.prior_P_f[i][d]; }
@@ -129,56 +128,60 @@ template <class R>
 __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    // round 1: one logarithm / reciprocal per lane
+    // round 1, FP64 (responsibilities and variances can be far below FP32's range):
+    // one logarithm / reciprocal per lane
     //   lanes 0..15 log(k_id / w_id); 16..23 log c2 and 1/c2; 24,25 log(a_i/Phi_i);
     //   26,27 log(pv_i / r2_i) and 1/r2_i
-    R lv = 0, rv = 0;
+    double lv = 0.0, rv = 0.0;
     if (lane < 16) {
         const int i = lane >> 3, d = lane & 7;
-        lv = lgr((R)th[P_K + NCOMP * i + d] / prior_w_of(md, i, d, R()));
+        lv = log(th[P_K + NCOMP * i + d] / md.prior_w[i][d]);
     } else if (lane < 24) {
-        const R c = (R)th[P_C2 + (lane - 16)];
-        lv = lgr(c);
-        rv = (R)1 / c;
+        const double c = th[P_C2 + (lane - 16)];
+        lv = log(c);
+        rv = 1.0 / c;
     } else if (lane < 26) {
         const int i = lane - 24;
-        const R phi = (i == 0) ? (R)md.prior_star : (R)1 - (R)md.prior_star;
-        lv = lgr((R)th[P_A + i] / phi);
+        const double phi = (i == 0) ? md.prior_star : 1.0 - md.prior_star;
+        lv = log(th[P_A + i] / phi);
     } else if (lane < 28) {
         const int i = lane - 26;
-        const R r2 = (R)th[P_R2 + i];
-        lv = lgr((R)md.prior_r[i][1] / r2);
-        rv = (R)1 / r2;
+        lv = log(md.prior_r[i][1] / th[P_R2 + i]);
+        rv = 1.0 / th[P_R2 + i];
     }
     const int i = (lane >> 3) & 1, d = lane & 7;
-    R ic2[4], slog = 0;
+    double ic2[4], slog = 0.0;
     for (int j = 0; j < 4; ++j) {
         slog += __shfl_sync(full, lv, 16 + 4 * i + j);
         ic2[j] = __shfl_sync(full, rv, 16 + 4 * i + j);
     }
-    const R la = __shfl_sync(full, lv, 24 + i);
-    const R lpr = __shfl_sync(full, lv, 26 + i);
-    const R ir2 = __shfl_sync(full, rv, 26 + i);
-    // round 2: per-component terms (lanes 0..15)
+    const double la = __shfl_sync(full, lv, 24 + i);
+    const double lpr = __shfl_sync(full, lv, 26 + i);
+    const double ir2 = __shfl_sync(full, rv, 26 + i);
+    // round 2: per-component terms (lanes 0..15); the 4 x 4 algebra in R
     double term = 0.0, dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
-    const R a = (R)th[P_A + i];
     if (lane < 16) {
-        const R k = (R)th[P_K + NCOMP * i + d];
+        const double k = th[P_K + NCOMP * i + d];
+        const double a = th[P_A + i];
         const R* Pm = prior_P_of(md, i, d, R());
         const R* mu = prior_mu_of(md, i, d, R());
         R diff[4], quad = 0, tr = 0;
         for (int j = 0; j < 4; ++j) diff[j] = (R)th[P_C1 + 4 * i + j] - mu[j];
+        R Pd[4];
         for (int j = 0; j < 4; ++j) {
             R s = 0;
             for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
+            Pd[j] = s;
             quad += diff[j] * s;
             tr += Pm[5 * j] * (R)th[P_C2 + 4 * i + j];
-            dc1[j] = (double)(k * s);
-            dc2[j] = (double)((R)0.5 * k * (Pm[5 * j] - ic2[j]));
         }
-        const R klc = (R)0.5 * (tr + quad - (R)4 + prior_ld_of(md, i, d, R()) - slog);
-        term = (double)(k * (lv + klc));
-        g[P_K + NCOMP * i + d] = (double)(a * (lv + (R)1 + klc));
+        const double klc = 0.5 * ((double)(tr + quad) - 4.0 + md.prior_logdet[i][d] - slog);
+        term = k * (lv + klc);
+        g[P_K + NCOMP * i + d] = a * (lv + 1.0 + klc);
+        for (int j = 0; j < 4; ++j) {
+            dc1[j] = k * (double)Pd[j];
+            dc2[j] = 0.5 * k * ((double)Pm[5 * j] - ic2[j]);
+        }
     }
     // FP64 sums over the eight components of each type
     for (int o = 1; o < 8; o <<= 1) {
@@ -192,12 +195,12 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g
     if (lane < 16 && d == 0) {
         const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
         const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
-        const double K = 0.5 * ((double)lpr + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
+        const double K = 0.5 * (lpr + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
         const double ad = th[P_A + i];
-        klv = ad * ((double)la + K);
-        g[P_A + i] = (double)la + 1.0 + K;
+        klv = ad * (la + K);
+        g[P_A + i] = la + 1.0 + K;
         g[P_R1 + i] = ad * (r1 - pm) / pv;
-        g[P_R2 + i] = ad * 0.5 * (1.0 / pv - (double)ir2);
+        g[P_R2 + i] = ad * 0.5 * (1.0 / pv - ir2);
         for (int j = 0; j < 4; ++j) {
             g[P_C1 + 4 * i + j] = ad * dc1[j];
             g[P_C2 + 4 * i + j] = ad * dc2[j];
