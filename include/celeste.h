@@ -202,6 +202,16 @@ celeste_status celeste_elbo_grad_device(celeste_problem* prob, const double* d_t
 celeste_status celeste_hess_device(celeste_problem* prob, const double* d_theta, int32_t precision,
                                    double* d_elbo_per_source, double* d_grad, double* d_hess,
                                    void* stream);
+/*
+ * Backward half of an ELBO evaluation (the adjoint, Section IV-D's gradient): the
+ * gradient wrt every source's 44 parameters, reusing the mixture tables and the
+ * E / Var maps that the immediately preceding celeste_elbo_device call on this problem
+ * left behind, which must have used the same d_theta contents and precision.  The
+ * per-pixel mixture terms are recomputed, never stored.  elbo_per_source nullable.
+ */
+celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta, int32_t precision,
+                                   double* d_elbo_per_source, double* d_grad, void* stream);
+
 /* Status word written by the device-side checks of the last _device call (host read;
  * synchronises the problem's last stream).  CELESTE_OK or a negative status. */
 celeste_status celeste_device_status(celeste_problem* prob);

@@ -60,7 +60,7 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
            "celeste_profile_enable", "celeste_profile_read",
-           "celeste_patch_elbo_grad_noalloc"]
+           "celeste_patch_elbo_grad_noalloc", "celeste_grad_device"]
 
 
 def lib_path():
@@ -101,6 +101,8 @@ def load(build_if_missing=False):
     L.celeste_hess_device.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     for f in ("celeste_elbo_device", "celeste_elbo_grad_device", "celeste_hess_device"):
         getattr(L, f).restype = i32
+    L.celeste_grad_device.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.celeste_grad_device.restype = i32
     L.celeste_device_status.argtypes = [vp]
     L.celeste_device_status.restype = i32
     L.celeste_profile_enable.argtypes = [vp, i32]
@@ -252,6 +254,11 @@ class Problem:
         _check(self.L.celeste_elbo_grad_device(self.h, self._dp(d_theta), precision,
                                                self._dp(d_total), self._dp(d_local),
                                                self._dp(d_grad), self._stream()))
+
+    def grad_device(self, d_theta, d_grad, d_local=None, precision=FP32):
+        """Adjoint only; needs the preceding elbo_device call on the same theta."""
+        _check(self.L.celeste_grad_device(self.h, self._dp(d_theta), precision, self._dp(d_local),
+                                          self._dp(d_grad), self._stream()))
 
     def hess_device(self, d_theta, d_local, d_grad, d_hess, precision=FP32):
         _check(self.L.celeste_hess_device(self.h, self._dp(d_theta), precision, self._dp(d_local),

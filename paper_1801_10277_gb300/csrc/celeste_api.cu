@@ -616,6 +616,26 @@ int32_t celeste_profile_read(celeste_problem* pr, int32_t max_kernels, char* nam
     return n;
 }
 
+celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, int32_t precision,
+                                  double* d_elbo_per_source, double* d_grad, void* stream) {
+    if (!pr || !d_theta || !d_grad) return fail(CELESTE_ERR_ARG, "null problem, theta or grad");
+    if (precision != CELESTE_FP64 && precision != CELESTE_FP32_ACC64)
+        return fail(CELESTE_ERR_ARG, "precision must be CELESTE_FP64 or CELESTE_FP32_ACC64");
+    cudaStream_t st = (cudaStream_t)stream;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    pr->last_stream = st;
+    const DevProblem& P = pr->P;
+    CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
+    // the mixture tables and the E / Var maps of the preceding celeste_elbo_device call
+    // are reused; the mixture terms themselves are recomputed by the adjoint
+    CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
+    CEL_CUDA(timed(pr, "finalize", st, [&] {
+        return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
+                               nullptr, st);
+    }));
+    return CELESTE_OK;
+}
+
 celeste_status celeste_device_status(celeste_problem* pr) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
     CEL_CUDA(cudaSetDevice(pr->device));
