@@ -19,9 +19,8 @@ class ELBO(torch.autograd.Function):
         th = theta.detach().contiguous()
         total = torch.zeros(1, dtype=torch.float64, device=theta.device)
         problem.elbo_device(th, total, None, precision=precision)
-        problem._forward_generation = getattr(problem, "_forward_generation", 0) + 1
         ctx.problem, ctx.precision = problem, precision
-        ctx.generation = problem._forward_generation
+        ctx.generation = problem.generation
         ctx.save_for_backward(th)
         return total[0]
 
@@ -29,12 +28,10 @@ class ELBO(torch.autograd.Function):
     def backward(ctx, grad_out):
         (th,) = ctx.saved_tensors
         pr = ctx.problem
-        if pr._forward_generation != ctx.generation:
+        if pr.generation != ctx.generation:
             # another evaluation replaced the maps: rebuild this theta's maps first
             total = torch.zeros(1, dtype=torch.float64, device=th.device)
             pr.elbo_device(th, total, None, precision=ctx.precision)
-            pr._forward_generation += 1
-            ctx.generation = pr._forward_generation
         g = torch.empty_like(th)
         pr.grad_device(th, g, precision=ctx.precision)
         return grad_out * g, None, None

@@ -176,6 +176,7 @@ class Problem:
         _check(st)
         self.h = h
         self.L = L
+        self.generation = 0    # bumped by every call that rebuilds the E / Var maps
 
     def close(self):
         if getattr(self, "h", None):
@@ -200,6 +201,7 @@ class Problem:
 
     # ---- host-pointer calls
     def elbo(self, theta, precision=FP64):
+        self.generation += 1   # the problem's maps now belong to this call
         th = self._theta(theta)
         tot = C.c_double()
         loc = np.zeros(self.n_src)
@@ -207,6 +209,7 @@ class Problem:
         return tot.value, loc
 
     def elbo_grad(self, theta, precision=FP64):
+        self.generation += 1   # the problem's maps now belong to this call
         th = self._theta(theta)
         tot = C.c_double()
         loc = np.zeros(self.n_src)
@@ -215,6 +218,7 @@ class Problem:
         return tot.value, loc, g
 
     def hess(self, theta, precision=FP64):
+        self.generation += 1   # the problem's maps now belong to this call
         th = self._theta(theta)
         loc = np.zeros(self.n_src)
         g = np.zeros((self.n_src, NPARAM))
@@ -223,6 +227,7 @@ class Problem:
         return loc, g, h
 
     def fit(self, theta, which=None, **opts):
+        self.generation += 1   # the problem's maps now belong to this call
         th = self._theta(theta).copy()
         w = None if which is None else np.ascontiguousarray(which, np.int32)
         it = np.zeros(self.n_src, np.int32)
@@ -247,10 +252,12 @@ class Problem:
         return C.c_void_p(t.data_ptr())
 
     def elbo_device(self, d_theta, d_total, d_local=None, precision=FP32):
+        self.generation += 1   # the problem's maps now belong to this call
         _check(self.L.celeste_elbo_device(self.h, self._dp(d_theta), precision, self._dp(d_total),
                                           self._dp(d_local), self._stream()))
 
     def elbo_grad_device(self, d_theta, d_total, d_local, d_grad, precision=FP32):
+        self.generation += 1   # the problem's maps now belong to this call
         _check(self.L.celeste_elbo_grad_device(self.h, self._dp(d_theta), precision,
                                                self._dp(d_total), self._dp(d_local),
                                                self._dp(d_grad), self._stream()))
@@ -261,6 +268,7 @@ class Problem:
                                           self._dp(d_grad), self._stream()))
 
     def hess_device(self, d_theta, d_local, d_grad, d_hess, precision=FP32):
+        self.generation += 1   # the problem's maps now belong to this call
         _check(self.L.celeste_hess_device(self.h, self._dp(d_theta), precision, self._dp(d_local),
                                           self._dp(d_grad), self._dp(d_hess), self._stream()))
 
