@@ -212,6 +212,17 @@ celeste_status celeste_hess_device(celeste_problem* prob, const double* d_theta,
 celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta, int32_t precision,
                                    double* d_elbo_per_source, double* d_grad, void* stream);
 
+/*
+ * Autotuner: times the FP32 contrib and adjoint kernels of this problem with 1, 2 and 4
+ * pixels per thread (CTAs of 256, 128, 64 threads over the same 256-pixel work items),
+ * reps launches each with CUDA events on the problem's stream, at theta (host), and keeps
+ * the fastest for later FP32 calls.  The choice is returned (nullable outputs) and can be
+ * stored by the caller and restored with celeste_set_tuning (0 = built-in default 2).
+ */
+celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint);
+celeste_status celeste_set_tuning(celeste_problem* prob, int32_t ppt_contrib, int32_t ppt_adjoint);
+
 /* Status word written by the device-side checks of the last _device call (host read;
  * synchronises the problem's last stream).  CELESTE_OK or a negative status. */
 celeste_status celeste_device_status(celeste_problem* prob);

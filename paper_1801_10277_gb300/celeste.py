@@ -60,7 +60,8 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
            "celeste_profile_enable", "celeste_profile_read",
-           "celeste_patch_elbo_grad_noalloc", "celeste_grad_device"]
+           "celeste_patch_elbo_grad_noalloc", "celeste_grad_device", "celeste_autotune",
+           "celeste_set_tuning"]
 
 
 def lib_path():
@@ -103,6 +104,10 @@ def load(build_if_missing=False):
         getattr(L, f).restype = i32
     L.celeste_grad_device.argtypes = [vp, vp, i32, vp, vp, vp]
     L.celeste_grad_device.restype = i32
+    L.celeste_autotune.argtypes = [vp, vp, i32, vp, vp]
+    L.celeste_autotune.restype = i32
+    L.celeste_set_tuning.argtypes = [vp, i32, i32]
+    L.celeste_set_tuning.restype = i32
     L.celeste_device_status.argtypes = [vp]
     L.celeste_device_status.restype = i32
     L.celeste_profile_enable.argtypes = [vp, i32]
@@ -271,6 +276,17 @@ class Problem:
         self.generation += 1   # the problem's maps now belong to this call
         _check(self.L.celeste_hess_device(self.h, self._dp(d_theta), precision, self._dp(d_local),
                                           self._dp(d_grad), self._dp(d_hess), self._stream()))
+
+    def autotune(self, theta, reps=5):
+        """Pick the fastest FP32 pixels-per-thread variants; returns (contrib, adjoint)."""
+        self.generation += 1
+        a = C.c_int32()
+        b = C.c_int32()
+        _check(self.L.celeste_autotune(self.h, _p(self._theta(theta)), reps, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_tuning(self, ppt_contrib, ppt_adjoint):
+        _check(self.L.celeste_set_tuning(self.h, ppt_contrib, ppt_adjoint))
 
     def profile(self, on=True):
         _check(self.L.celeste_profile_enable(self.h, 1 if on else 0))

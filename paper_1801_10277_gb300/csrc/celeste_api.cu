@@ -182,14 +182,21 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
     CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st); }));
     CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
+    // with work items, the LL / GRAD epilogue runs in the adjoint's tail
+    const bool fused = mode != MODE_HESS && P.src_count && P.n_item > 0;
     if (mode == MODE_HESS)
         CEL_CUDA(timed(pr, "hess_adjoint", st, [&] { return launch_hess_pixels(P, precision, st); }));
+    else if (fused)
+        CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st, [&] {
+            return launch_adjoint(P, precision, mode, st, d_theta, d_total, d_local, d_grad);
+        }));
     else
         CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
                        [&] { return launch_adjoint(P, precision, mode, st); }));
-    CEL_CUDA(timed(pr, "finalize", st, [&] {
-        return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
-    }));
+    if (!fused)
+        CEL_CUDA(timed(pr, "finalize", st, [&] {
+            return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
+        }));
     return CELESTE_OK;
 }
 
@@ -491,6 +498,27 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.tile_ll = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
     P.item_ll = (double*)p;
+    {
+        // fused epilogue bookkeeping: items per source, sources without items
+        std::vector<int32_t> nitems(n_src, 0), idle;
+        for (const WorkItem& w : items) ++nitems[w.src];
+        for (int s = 0; s < n_src; ++s)
+            if (nitems[s] == 0) idle.push_back(s);
+        int32_t *d_cnt, *d_nit, *d_done, *d_idle;
+        if ((st = dalloc(pr, (void**)&d_cnt, sizeof(int32_t) * (size_t)n_src))) return bail(st);
+        if ((st = dupload(pr, &d_nit, nitems.data(), nitems.size()))) return bail(st);
+        if ((st = dalloc(pr, (void**)&d_done, sizeof(int32_t)))) return bail(st);
+        if ((st = dupload(pr, &d_idle, idle.data(), idle.size()))) return bail(st);
+        if (cudaMemset(d_cnt, 0, sizeof(int32_t) * (size_t)std::max(n_src, 1)) != cudaSuccess ||
+            cudaMemset(d_done, 0, sizeof(int32_t)) != cudaSuccess)
+            return bail(fail(CELESTE_ERR_CUDA, "memset"));
+        P.src_count = d_cnt;
+        P.src_nitems = d_nit;
+        P.done = d_done;
+        P.idle_src = d_idle;
+        P.n_idle = (int32_t)idle.size();
+        P.n_with_items = n_src - (int32_t)idle.size();
+    }
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
@@ -628,11 +656,76 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
     // the mixture tables and the E / Var maps of the preceding celeste_elbo_device call
     // are reused; the mixture terms themselves are recomputed by the adjoint
-    CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
-    CEL_CUDA(timed(pr, "finalize", st, [&] {
-        return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
-                               nullptr, st);
+    const bool fused = P.src_count && P.n_item > 0;
+    CEL_CUDA(timed(pr, "adjoint", st, [&] {
+        return fused ? launch_adjoint(P, precision, MODE_GRAD, st, d_theta, nullptr, d_elbo_per_source, d_grad)
+                     : launch_adjoint(P, precision, MODE_GRAD, st);
     }));
+    if (!fused)
+        CEL_CUDA(timed(pr, "finalize", st, [&] {
+            return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source,
+                                   d_grad, nullptr, st);
+        }));
+    return CELESTE_OK;
+}
+
+celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_t reps,
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint) {
+    if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
+    celeste_status s = check_theta_host(theta, pr->P.n_src);
+    if (s) return s;
+    if (reps < 1) reps = 5;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    cudaStream_t st = pr->stream;
+    DevProblem& P = pr->P;
+    CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * P.n_src,
+                             cudaMemcpyHostToDevice, st));
+    CEL_CUDA(launch_prep(P, pr->d_theta, CELESTE_FP32_ACC64, st));
+    cudaEvent_t a, b;
+    CEL_CUDA(cudaEventCreate(&a));
+    CEL_CUDA(cudaEventCreate(&b));
+    const int cands[3] = {1, 2, 4};
+    float best_c = 1e30f, best_a = 1e30f;
+    int pick_c = 2, pick_a = 2;
+    cudaError_t e = cudaSuccess;
+    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+        P.tune_contrib = P.tune_adjoint = cands[ci];
+        // warm once, then time reps launches of each kernel
+        e = launch_contrib(P, CELESTE_FP32_ACC64, st);
+        if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
+        if (e == cudaSuccess) e = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
+        float tc = 0.f, ta = 0.f;
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_contrib(P, CELESTE_FP32_ACC64, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&tc, a, b);
+        if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ta, a, b);
+        if (e == cudaSuccess && tc < best_c) { best_c = tc; pick_c = cands[ci]; }
+        if (e == cudaSuccess && ta < best_a) { best_a = ta; pick_a = cands[ci]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    P.tune_contrib = pick_c;
+    P.tune_adjoint = pick_a;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (ppt_contrib) *ppt_contrib = pick_c;
+    if (ppt_adjoint) *ppt_adjoint = pick_a;
+    return CELESTE_OK;
+}
+
+celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint) {
+    if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    auto okp = [](int v) { return v == 0 || v == 1 || v == 2 || v == 4; };
+    if (!okp(ppt_contrib) || !okp(ppt_adjoint)) return fail(CELESTE_ERR_ARG, "pixels per thread must be 0, 1, 2 or 4");
+    pr->P.tune_contrib = ppt_contrib;
+    pr->P.tune_adjoint = ppt_adjoint;
     return CELESTE_OK;
 }
 

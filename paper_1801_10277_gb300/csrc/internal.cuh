@@ -138,6 +138,7 @@ enum Mode : int { MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
 struct DevProblem {
     int32_t n_img, n_src, n_patch, n_item, n_tile, npsf_max, nprof;
+    int32_t tune_contrib, tune_adjoint;   // FP32 pixels per thread (0 = default)
     int64_t n_px, n_sp;
     const ImgMeta* img;
     const float* pixels;
@@ -158,6 +159,12 @@ struct DevProblem {
     const uint8_t* single;   // per (source, pixel): 1 when no other patch covers the pixel (nullable)
     double* item_ll;         // per work item: ll summed over its singly covered pixels
     double* item_part;
+    // epilogue fused into the adjoint's tail (null src_count: separate finalize kernel)
+    int32_t* src_count;
+    const int32_t* src_nitems;
+    int32_t* done;
+    const int32_t* idle_src;
+    int32_t n_idle, n_with_items;
     double* tile_ll;
     double* kl;
     int32_t* status;
@@ -175,7 +182,9 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
                         cudaStream_t st);
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st);
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
+                           const double* d_theta = nullptr, double* d_total = nullptr,
+                           double* d_local = nullptr, double* d_grad = nullptr);
 cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,

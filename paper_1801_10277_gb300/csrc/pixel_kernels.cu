@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "epilogue.cuh"
 
 namespace cel {
 
@@ -336,15 +337,19 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
 //   dN/dmean = N P d,  dN/dG_xx = nu N ((Pd)_x^2 - Pxx)/2,  dN/dG_xy = nu N ((Pd)_x (Pd)_y - Pxy),
 //   dN/dG_yy = nu N ((Pd)_y^2 - Pyy)/2,  dN/de_dev = dc exp(...)/(...)
 
+// at most 64 registers a thread for FP32 (the rarely taken epilogue tail may spill;
+// the pixel loop must not)
 template <class R, int MODE, int PPT>
-__global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(CHUNK / PPT, (sizeof(R) == 4 ? 65536 / (64 * (CHUNK / PPT)) : 1))
+k_adjoint(const WorkItem* __restrict__ items,
                                                          const PatchGeo* __restrict__ geo,
                                                          const ImgMeta* __restrict__ img, int nprof,
                                                          const float* __restrict__ pixels,
                                                          const R* __restrict__ tbl,
                                                          const R* __restrict__ emap,
                                                          const R* __restrict__ vmap,
-                                                         double* __restrict__ part) {
+                                                         double* __restrict__ part,
+                                                         const EpilogueArgs ep) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     __shared__ R sT[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
@@ -452,12 +457,16 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
     double tot[NV];
     cta_sum<R, NV>(v, tot);
     if (threadIdx.x < NV) part[(size_t)blockIdx.x * NPART + threadIdx.x] = tot[threadIdx.x];
+    if (ep.src_count) adjoint_tail<R>(ep, it.src, geo, img, part);
 }
 
 // ---------------------------------------------------------------------------------
 // launchers
 
-constexpr int PPT32 = 2;   // pixels per thread on the FP32 path
+// pixels per thread of the FP32 contrib / adjoint kernels: P.tune (autotuned per
+// problem, celeste_autotune), 2 when untuned
+static inline int ppt_contrib(const DevProblem& P) { return P.tune_contrib > 0 ? P.tune_contrib : 2; }
+static inline int ppt_adjoint(const DevProblem& P) { return P.tune_adjoint > 0 ? P.tune_adjoint : 2; }
 
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st) {
@@ -479,10 +488,21 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) 
                                                       P.pixels, P.sky_map, (double*)P.emap,
                                                       (double*)P.vmap, P.item_ll);
     else
-        k_contrib<float, PPT32><<<P.n_item, CHUNK / PPT32, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
-                                                     (float*)P.spE, (float*)P.spE2, P.single,
-                                                     P.pixels, P.sky_map, (float*)P.emap,
-                                                     (float*)P.vmap, P.item_ll);
+        switch (ppt_contrib(P)) {
+#define CEL_CONTRIB32(N)                                                                         \
+    case N:                                                                                      \
+        k_contrib<float, N><<<P.n_item, CHUNK / N, 0, st>>>(P.items, P.geo, P.img, P.nprof,        \
+                                                            P.tbl32, (float*)P.spE, (float*)P.spE2, \
+                                                            P.single, P.pixels, P.sky_map,         \
+                                                            (float*)P.emap, (float*)P.vmap,        \
+                                                            P.item_ll);                            \
+        break;
+            CEL_CONTRIB32(1)
+            CEL_CONTRIB32(2)
+            CEL_CONTRIB32(4)
+#undef CEL_CONTRIB32
+            default: return cudaErrorInvalidValue;
+        }
     return cudaGetLastError();
 }
 
@@ -500,21 +520,55 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
 }
 
 template <class R, int PPT>
-static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st) {
+static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st,
+                         const EpilogueArgs& ep) {
     const R* em = (const R*)P.emap;
     const R* vm = (const R*)P.vmap;
     if (mode == MODE_LL)
         k_adjoint<R, MODE_LL, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part, ep);
     else
         k_adjoint<R, MODE_GRAD, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part, ep);
 }
 
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st) {
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
+                           const double* d_theta, double* d_total, double* d_local,
+                           double* d_grad) {
     if (P.n_item == 0) return cudaSuccess;
-    if (precision == CELESTE_FP64) adjoint_impl<double, 1>(P, P.tbl64, mode, st);
-    else adjoint_impl<float, PPT32>(P, P.tbl32, mode, st);
+    EpilogueArgs ep{};
+    if (P.src_count && d_theta) {
+        ep.src_count = P.src_count;
+        ep.src_nitems = P.src_nitems;
+        ep.done = P.done;
+        ep.n_with_items = P.n_with_items;
+        ep.idle_src = P.idle_src;
+        ep.n_idle = P.n_idle;
+        ep.n_src = P.n_src;
+        ep.mode = mode;
+        ep.theta = d_theta;
+        ep.patch_off = P.patch_off;
+        ep.md = P.model;
+        ep.kl = P.kl;
+        ep.local_out = d_local;
+        ep.grad_out = d_grad;
+        ep.total_out = d_total;
+        ep.status = P.status;
+        ep.tile_ll = P.tile_ll;
+        ep.n_tile = P.n_tile;
+        ep.item_ll = P.item_ll;
+        ep.n_item_ll = P.single ? P.n_item : 0;
+    }
+    if (precision == CELESTE_FP64) {
+        adjoint_impl<double, 1>(P, P.tbl64, mode, st, ep);
+    } else {
+        switch (ppt_adjoint(P)) {
+            case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st, ep); break;
+            case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st, ep); break;
+            case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st, ep); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
     return cudaGetLastError();
 }
 

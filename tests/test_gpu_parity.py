@@ -85,6 +85,23 @@ def test_edge_cases(cel):
     _check_problem(cel, prob)
 
 
+def test_autotuned_variants_agree(cel):
+    """Every pixels-per-thread variant the autotuner may pick gives the oracle's answer
+    within the FP32 tolerances, and the tuner returns one of them."""
+    prob = synth.config(2)
+    orc = Oracle(prob)
+    o_tot, _ = orc.elbo(prob.theta)
+    _, o_g, _ = orc.derivs(prob.theta)
+    P = cel.Problem(prob)
+    for ppt in (1, 2, 4):
+        P.set_tuning(ppt, ppt)
+        tot, loc, g = P.elbo_grad(prob.theta, precision=cel.FP32)
+        assert rel(tot, o_tot) <= 1e-5 and rel_l2(g, o_g) <= 1e-4, ppt
+    c, a = P.autotune(prob.theta)
+    assert c in (1, 2, 4) and a in (1, 2, 4)
+    P.close()
+
+
 def test_device_entry_points_match_host(cel):
     import torch
     prob = synth.config(2)
