@@ -32,7 +32,7 @@ from paper_1801_10277_gb300 import synth  # noqa: E402
 FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
 FP32_LANES = 128
-KERNELS_PER_STEP = 4     # prep, contrib, gather, adjoint (+ fused per-source epilogue and total)
+KERNELS_PER_STEP = 6     # prep, contrib, gather, adjoint, finalize, total
 
 
 def adjoint_flops_per_source_pixel(npsf, n_exp, n_dev):
@@ -228,7 +228,7 @@ def main():
     prof = P.profile_read()
     P.profile(False)
     tot_ms = sum(v[0] for v in prof.values())
-    adj_ms, adj_n = prof.get("adjoint", (0.0, 1))   # includes the fused per-source epilogue
+    adj_ms, adj_n = prof.get("adjoint", (0.0, 1))
     adj_avg = adj_ms / max(1, adj_n)
     npsf = prob.images[0].psf.shape[0]
     ne, nd = prob.exp_mix.shape[0], prob.dev_mix.shape[0]

@@ -182,21 +182,14 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
     CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st); }));
     CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
-    // with work items, the LL / GRAD epilogue runs in the adjoint's tail
-    const bool fused = mode != MODE_HESS && P.src_count && P.n_item > 0;
     if (mode == MODE_HESS)
         CEL_CUDA(timed(pr, "hess_adjoint", st, [&] { return launch_hess_pixels(P, precision, st); }));
-    else if (fused)
-        CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st, [&] {
-            return launch_adjoint(P, precision, mode, st, d_theta, d_total, d_local, d_grad);
-        }));
     else
         CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
                        [&] { return launch_adjoint(P, precision, mode, st); }));
-    if (!fused)
-        CEL_CUDA(timed(pr, "finalize", st, [&] {
-            return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
-        }));
+    CEL_CUDA(timed(pr, "finalize", st, [&] {
+        return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
+    }));
     return CELESTE_OK;
 }
 
@@ -498,27 +491,7 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.tile_ll = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
     P.item_ll = (double*)p;
-    {
-        // fused epilogue bookkeeping: items per source, sources without items
-        std::vector<int32_t> nitems(n_src, 0), idle;
-        for (const WorkItem& w : items) ++nitems[w.src];
-        for (int s = 0; s < n_src; ++s)
-            if (nitems[s] == 0) idle.push_back(s);
-        int32_t *d_cnt, *d_nit, *d_done, *d_idle;
-        if ((st = dalloc(pr, (void**)&d_cnt, sizeof(int32_t) * (size_t)n_src))) return bail(st);
-        if ((st = dupload(pr, &d_nit, nitems.data(), nitems.size()))) return bail(st);
-        if ((st = dalloc(pr, (void**)&d_done, sizeof(int32_t)))) return bail(st);
-        if ((st = dupload(pr, &d_idle, idle.data(), idle.size()))) return bail(st);
-        if (cudaMemset(d_cnt, 0, sizeof(int32_t) * (size_t)std::max(n_src, 1)) != cudaSuccess ||
-            cudaMemset(d_done, 0, sizeof(int32_t)) != cudaSuccess)
-            return bail(fail(CELESTE_ERR_CUDA, "memset"));
-        P.src_count = d_cnt;
-        P.src_nitems = d_nit;
-        P.done = d_done;
-        P.idle_src = d_idle;
-        P.n_idle = (int32_t)idle.size();
-        P.n_with_items = n_src - (int32_t)idle.size();
-    }
+
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
@@ -656,16 +629,11 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
     // the mixture tables and the E / Var maps of the preceding celeste_elbo_device call
     // are reused; the mixture terms themselves are recomputed by the adjoint
-    const bool fused = P.src_count && P.n_item > 0;
-    CEL_CUDA(timed(pr, "adjoint", st, [&] {
-        return fused ? launch_adjoint(P, precision, MODE_GRAD, st, d_theta, nullptr, d_elbo_per_source, d_grad)
-                     : launch_adjoint(P, precision, MODE_GRAD, st);
+    CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
+    CEL_CUDA(timed(pr, "finalize", st, [&] {
+        return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
+                               nullptr, st);
     }));
-    if (!fused)
-        CEL_CUDA(timed(pr, "finalize", st, [&] {
-            return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source,
-                                   d_grad, nullptr, st);
-        }));
     return CELESTE_OK;
 }
 

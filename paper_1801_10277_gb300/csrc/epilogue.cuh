@@ -1,6 +1,5 @@
-// Per-source epilogue shared by the standalone finalize kernel and the tail of the
-// adjoint kernel: item sums -> chain rule -> KL -> local objective and gradient; and
-// the total.  FP64 sums; transcendentals of the FP32 path in FP32 where the range allows.
+// Per-source epilogue: item sums -> chain rule -> KL -> local objective and gradient;
+// and the total.  FP64 sums; transcendentals of the FP32 path in FP32 where the range allows.
 #pragma once
 
 #include <math.h>
@@ -10,31 +9,51 @@
 
 namespace cel {
 
-// d ELBO / d theta_j contributed by one patch through the intermediate variables y:
-// sum_y Gy[y] dy/dtheta_j (El = E[l|i] = exp(m + v/2), El2 = E[l^2|i] = exp(2m + 2v)).
-__device__ __forceinline__ double chain_entry(int j, int band, const double* A, const double* Gy,
-                                              const double* el, const double* el2,
-                                              const double (*dG)[3]) {
-    if (j == 0) return Gy[Y_MX] * A[0] + Gy[Y_MY] * A[2];
-    if (j == 1) return Gy[Y_MX] * A[1] + Gy[Y_MY] * A[3];
-    if (j == P_EDEV) return Gy[Y_EDEV];
-    if (j >= P_AXIS && j <= P_SCALE) {
+template <class R> __device__ __forceinline__ R band_beta(int band, int j) { return (R)color_beta(band, j); }
+template <> __device__ __forceinline__ float band_beta<float>(int band, int j) {
+    const int ref = 2;   // the same rule as color_beta, in FP32
+    if (band < ref) return (j >= band && j < ref) ? -1.f : 0.f;
+    if (band > ref) return (j >= ref && j < band) ? 1.f : 0.f;
+    return 0.f;
+}
+template <class R> __device__ __forceinline__ const R* wcs_row(const ImgMeta& im);
+template <> __device__ __forceinline__ const double* wcs_row<double>(const ImgMeta& im) { return im.A; }
+template <> __device__ __forceinline__ const float* wcs_row<float>(const ImgMeta& im) { return im.A_f; }
+
+// Column j of dy/dtheta for one patch as up to three (y, coefficient) pairs (unused
+// pairs point at y = 0 with coefficient 0), El = E[l|i] = exp(m + v/2),
+// El2 = E[l^2|i] = exp(2m + 2v):
+//   u -> mean via A;  e_dev -> e_dev;  (e_axis, e_angle, e_scale) -> G via dG;
+//   r1 -> (El, 2 El2);  r2 -> (El/2, 2 El2);  c1_j -> beta_j (El, 2 El2);
+//   c2_j -> beta_j^2 (El/2, 2 El2);  a_i -> a_i;  k -> nothing.
+template <class R>
+__device__ __forceinline__ void chain_column(int j, int band, const R* A, const R* el,
+                                             const R* el2, const R (*dG)[3], int* y0, R* c0,
+                                             int* y1, R* c1, int* y2, R* c2) {
+    *y0 = *y1 = *y2 = 0;
+    *c0 = *c1 = *c2 = (R)0;
+    if (j < 2) {
+        *y0 = Y_MX; *c0 = A[j];
+        *y1 = Y_MY; *c1 = A[2 + j];
+    } else if (j == P_EDEV) {
+        *y0 = Y_EDEV; *c0 = (R)1;
+    } else if (j <= P_SCALE) {
         const int q = j - P_AXIS;
-        return Gy[Y_GXX] * dG[q][0] + Gy[Y_GXY] * dG[q][1] + Gy[Y_GYY] * dG[q][2];
+        *y0 = Y_GXX; *c0 = dG[q][0];
+        *y1 = Y_GXY; *c1 = dG[q][1];
+        *y2 = Y_GYY; *c2 = dG[q][2];
+    } else if (j < P_A) {
+        int i, c = 0;
+        R fm, fv;   // weights of El and El2
+        if (j < P_R2) { i = j - P_R1; fm = (R)1; fv = (R)2; }
+        else if (j < P_C1) { i = j - P_R2; fm = (R)0.5; fv = (R)2; }
+        else if (j < P_C2) { i = (j - P_C1) / 4; c = (j - P_C1) % 4; const R b = band_beta<R>(band, c); fm = b; fv = (R)2 * b; }
+        else { i = (j - P_C2) / 4; c = (j - P_C2) % 4; const R b = band_beta<R>(band, c); fm = (R)0.5 * b * b; fv = (R)2 * b * b; }
+        *y0 = (i == 0) ? Y_EL0 : Y_EL1; *c0 = fm * el[i];
+        *y1 = (i == 0) ? Y_EL20 : Y_EL21; *c1 = fv * el2[i];
+    } else if (j < P_K) {
+        *y0 = (j == P_A) ? Y_A0 : Y_A1; *c0 = (R)1;
     }
-    if (j >= P_A) return (j < P_K) ? Gy[j == P_A ? Y_A0 : Y_A1] : 0.0;
-    int i, kind, c = 0;   // kind: 0 r1, 1 r2, 2 c1, 3 c2
-    if (j < P_R2) { i = j - P_R1; kind = 0; }
-    else if (j < P_C1) { i = j - P_R2; kind = 1; }
-    else if (j < P_C2) { i = (j - P_C1) / 4; c = (j - P_C1) % 4; kind = 2; }
-    else { i = (j - P_C2) / 4; c = (j - P_C2) % 4; kind = 3; }
-    const double gl = Gy[i == 0 ? Y_EL0 : Y_EL1] * el[i];
-    const double gl2 = Gy[i == 0 ? Y_EL20 : Y_EL21] * el2[i];
-    const double dm = gl + 2.0 * gl2, dv = 0.5 * gl + 2.0 * gl2;
-    if (kind == 0) return dm;
-    if (kind == 1) return dv;
-    const double b = color_beta(band, c);
-    return kind == 2 ? b * dm : b * b * dv;
 }
 
 // one CTA per source: the KL in warp 0 (kl_warp), the shape derivative in lane 32,
@@ -65,9 +84,13 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
                                                 int32_t* __restrict__ status) {
     const int t = threadIdx.x;
     __shared__ double th[NP], klg[NP], Gy[NY + 1];
-    __shared__ double el[2], el2[2], dG[3][3], klv;
-    __shared__ R dW[3][3];
-    for (int i = t; i < NP; i += blockDim.x) th[i] = theta[(size_t)NP * s + i];
+    __shared__ double klv;
+    __shared__ R el[2], el2[2], dG[3][3], dW[3][3], thr[NP];
+    for (int i = t; i < NP; i += blockDim.x) {
+        const double v = theta[(size_t)NP * s + i];
+        th[i] = v;
+        thr[i] = (R)v;   // one conversion per parameter
+    }
     if (status && t < NP) theta_domain_check(t, theta[(size_t)NP * s + t], status);
     __syncthreads();
     if (t < 32) {
@@ -75,7 +98,7 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
         if (t == 0) klv = v;
     } else if (t == 32 && mode >= MODE_GRAD) {
         // world-frame d(Wxx, Wxy, Wyy)/d(e_axis, e_angle, e_scale)
-        const R rho = (R)th[P_AXIS], phi = (R)th[P_ANGLE], sg = (R)th[P_SCALE];
+        const R rho = thr[P_AXIS], phi = thr[P_ANGLE], sg = thr[P_SCALE];
         const R bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
         R s2, c2;
         scr((R)2 * phi, &s2, &c2);
@@ -97,27 +120,34 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
             Gy[t] = v;
         } else if (mode >= MODE_GRAD && t >= 32 && t < 36) {
             const int i = (t - 32) >> 1, second = (t - 32) & 1;
-            R m = (R)th[P_R1 + i], v = (R)th[P_R2 + i];
+            R m = thr[P_R1 + i], v = thr[P_R2 + i];
             for (int j = 0; j < 4; ++j) {
-                const R b = (R)color_beta(im.band, j);
-                m += b * (R)th[P_C1 + 4 * i + j];
-                v += b * b * (R)th[P_C2 + 4 * i + j];
+                const R b = band_beta<R>(im.band, j);
+                m += b * thr[P_C1 + 4 * i + j];
+                v += b * b * thr[P_C2 + 4 * i + j];
             }
-            if (second) el2[i] = (double)exr((R)2 * m + (R)2 * v);
-            else el[i] = (double)exr(m + (R)0.5 * v);
+            if (second) el2[i] = exr((R)2 * m + (R)2 * v);
+            else el[i] = exr(m + (R)0.5 * v);
         } else if (mode >= MODE_GRAD && t >= 40 && t < 49) {
             const int q = (t - 40) / 3, c = (t - 40) % 3;
-            const R a0 = (R)im.A[0], a1 = (R)im.A[1], a2 = (R)im.A[2], a3 = (R)im.A[3];
+            const R* Aa = wcs_row<R>(im);
+            const R a0 = Aa[0], a1 = Aa[1], a2 = Aa[2], a3 = Aa[3];
             const R wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
             R v;
             if (c == 0) v = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
             else if (c == 1) v = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
             else v = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
-            dG[q][c] = (double)v;
+            dG[q][c] = v;
         }
         __syncthreads();
         if (t == 0) lacc += Gy[0];
-        if (mode >= MODE_GRAD && t < NP) gacc += chain_entry(t, im.band, im.A, Gy + 1, el, el2, dG);
+        if (mode >= MODE_GRAD && t < NP) {
+            // column t of dy/dtheta in R (branchy, cheap pipes), then FP64 accumulation
+            int y0, y1, y2;
+            R c0, c1, c2;
+            chain_column<R>(t, im.band, wcs_row<R>(im), el, el2, dG, &y0, &c0, &y1, &c1, &y2, &c2);
+            gacc += (double)c0 * Gy[1 + y0] + (double)c1 * Gy[1 + y1] + (double)c2 * Gy[1 + y2];
+        }
         __syncthreads();
     }
     if (t == 0) {
@@ -150,60 +180,6 @@ __device__ __forceinline__ void total_reduce(const double* __restrict__ tile_ll,
     }
     if (threadIdx.x == 0) *out = red[0];
     __syncthreads();
-}
-
-// Arguments of the epilogue fused into the adjoint's tail (the last CTA of a source
-// finalises it; the last source also forms the total).
-struct EpilogueArgs {
-    int32_t* src_count;           // per source: work items done (reset to 0 by its finaliser)
-    const int32_t* src_nitems;    // per source: work items in total
-    int32_t* done;                // sources finalised (reset by the last one)
-    int32_t n_with_items;         // sources owning at least one work item
-    const int32_t* idle_src;      // sources without work items (finalised by the last one)
-    int32_t n_idle;
-    int32_t n_src, mode;
-    const double* theta;
-    const int32_t* patch_off;
-    const ModelDev* md;
-    double* kl;
-    double* local_out;
-    double* grad_out;
-    double* total_out;
-    int32_t* status;
-    const double* tile_ll;
-    int32_t n_tile;
-    const double* item_ll;
-    int32_t n_item_ll;
-};
-
-// The fused tail: call from every thread after the CTA wrote its item partials.
-template <class R>
-__device__ __forceinline__ void adjoint_tail(const EpilogueArgs& ep, int src,
-                                             const PatchGeo* __restrict__ geo,
-                                             const ImgMeta* __restrict__ img,
-                                             const double* __restrict__ part) {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&ep.src_count[src], 1) == ep.src_nitems[src] - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    finalize_source<R>(src, ep.mode, ep.theta, geo, ep.patch_off, img, ep.md, part, ep.kl,
-                       ep.local_out, ep.grad_out, ep.status);
-    if (threadIdx.x == 0) ep.src_count[src] = 0;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ep.done, 1) == ep.n_with_items - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int k = 0; k < ep.n_idle; ++k)
-        finalize_source<R>(ep.idle_src[k], ep.mode, ep.theta, geo, ep.patch_off, img, ep.md, part,
-                           ep.kl, ep.local_out, ep.grad_out, ep.status);
-    if (ep.total_out)
-        total_reduce(ep.tile_ll, ep.n_tile, ep.item_ll, ep.n_item_ll, ep.kl, ep.n_src, ep.total_out);
-    if (threadIdx.x == 0) *ep.done = 0;
 }
 
 }  // namespace cel

@@ -795,7 +795,6 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             Pb.item_part = d_part;
             Pb.kl = d_kl;
             Pb.single = nullptr;    // batch buffers keep every E_s / Var_s
-            Pb.src_count = nullptr; // no fused epilogue on batch views
             Pb.item_ll = nullptr;
             Pb.status = nullptr;
             DevProblem Pc = Pb;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "celeste.h"
 
 namespace cel {
@@ -53,6 +55,7 @@ struct ImgMeta {
     double A[4], t[2];
     double psf[MAXPSF][6];
     float psf_f[MAXPSF][6];  // the same in FP32 (conversions run on the narrow FP64 pipe)
+    float A_f[4];
 };
 
 struct PatchGeo {
@@ -78,6 +81,9 @@ struct ModelDev {
     double prior_mu[2][NCOMP][4];
     double prior_P[2][NCOMP][16];     // inverse covariances
     double prior_logdet[2][NCOMP];
+    double prior_logw[2][NCOMP];      // log w_id, log Phi_i, log pv_i
+    double prior_logphi[2];
+    double prior_logpv[2];
     // FP32 copies for the FP32 path
     float prof_w_f[MAXPROF], prof_nu_f[MAXPROF];
     float prior_star_f;
@@ -90,6 +96,11 @@ struct ModelDev {
 
 // FP32 copies of the model / image constants, filled once on the host
 inline void fill_float_copies(ModelDev& m) {
+    for (int i = 0; i < 2; ++i) {
+        for (int d = 0; d < NCOMP; ++d) m.prior_logw[i][d] = std::log(m.prior_w[i][d]);
+        m.prior_logphi[i] = std::log(i == 0 ? m.prior_star : 1.0 - m.prior_star);
+        m.prior_logpv[i] = std::log(m.prior_r[i][1]);
+    }
     for (int j = 0; j < MAXPROF; ++j) {
         m.prof_w_f[j] = (float)m.prof_w[j];
         m.prof_nu_f[j] = (float)m.prof_nu[j];
@@ -108,11 +119,14 @@ inline void fill_float_copies(ModelDev& m) {
 inline void fill_float_copies(ImgMeta& im) {
     for (int k = 0; k < MAXPSF; ++k)
         for (int c = 0; c < 6; ++c) im.psf_f[k][c] = (float)im.psf[k][c];
+    for (int k = 0; k < 4; ++k) im.A_f[k] = (float)im.A[k];
 }
 
 // precision-selected views of those constants
 __device__ inline const double* psf_row(const ImgMeta& im, int k, double) { return im.psf[k]; }
 __device__ inline const float* psf_row(const ImgMeta& im, int k, float) { return im.psf_f[k]; }
+__device__ inline double wcs_of(const ImgMeta& im, int k, double) { return im.A[k]; }
+__device__ inline float wcs_of(const ImgMeta& im, int k, float) { return im.A_f[k]; }
 __device__ inline double prof_w_of(const ModelDev& m, int j, double) { return m.prof_w[j]; }
 __device__ inline float prof_w_of(const ModelDev& m, int j, float) { return m.prof_w_f[j]; }
 __device__ inline double prof_nu_of(const ModelDev& m, int j, double) { return m.prof_nu[j]; }
@@ -159,12 +173,6 @@ struct DevProblem {
     const uint8_t* single;   // per (source, pixel): 1 when no other patch covers the pixel (nullable)
     double* item_ll;         // per work item: ll summed over its singly covered pixels
     double* item_part;
-    // epilogue fused into the adjoint's tail (null src_count: separate finalize kernel)
-    int32_t* src_count;
-    const int32_t* src_nitems;
-    int32_t* done;
-    const int32_t* idle_src;
-    int32_t n_idle, n_with_items;
     double* tile_ll;
     double* kl;
     int32_t* status;
@@ -182,9 +190,7 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
                         cudaStream_t st);
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
-                           const double* d_theta = nullptr, double* d_total = nullptr,
-                           double* d_local = nullptr, double* d_grad = nullptr);
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st);
 cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,

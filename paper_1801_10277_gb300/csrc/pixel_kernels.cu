@@ -17,7 +17,6 @@
 #include <math.h>
 
 #include "internal.cuh"
-#include "epilogue.cuh"
 
 namespace cel {
 
@@ -97,7 +96,7 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
                        int n_patch, int nprof, R* __restrict__ tbl) {
     const int p = blockIdx.x;
     if (p >= n_patch) return;
-    __shared__ double sh[8];   // gxx gxy gyy edev
+    __shared__ R sh[4];   // gxx gxy gyy edev
     const PatchGeo g = geo[p];
     const ImgMeta& im = img[g.img];
     const double* th = theta + (size_t)NP * g.src;
@@ -121,21 +120,24 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
         R s2, c2;
         sc(2 * phi, &s2, &c2);
         const R wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
-        const R a0 = (R)im.A[0], a1 = (R)im.A[1], a2 = (R)im.A[2], a3 = (R)im.A[3];
-        sh[0] = (double)(a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy);
-        sh[1] = (double)(a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy);
-        sh[2] = (double)(a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy);
-        sh[3] = th[P_EDEV];
+        const R a0 = wcs_of(im, 0, R()), a1 = wcs_of(im, 1, R()), a2 = wcs_of(im, 2, R()),
+                a3 = wcs_of(im, 3, R());
+        sh[0] = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
+        sh[1] = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
+        sh[2] = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
+        sh[3] = (R)th[P_EDEV];
     } else if (t0 >= 2 && t0 < 6) {
         // brightness moments in this band: log l | type i ~ N(m, v); E[l] = e^{m+v/2}, E[l^2] = e^{2m+2v}
         const int i = (t0 - 2) >> 1, second = (t0 - 2) & 1;
-        double m = th[P_R1 + i], v = th[P_R2 + i];
+        R m = (R)th[P_R1 + i], v = (R)th[P_R2 + i];
         for (int j = 0; j < 4; ++j) {
-            const double b = color_beta(im.band, j);
-            m += b * th[P_C1 + 4 * i + j];
-            v += b * b * th[P_C2 + 4 * i + j];
+            if (color_beta(im.band, j) != 0.0) {
+                const R b = (R)color_beta(im.band, j);
+                m += b * (R)th[P_C1 + 4 * i + j];
+                v += b * b * (R)th[P_C2 + 4 * i + j];
+            }
         }
-        const R arg = second ? (R)(2.0 * m + 2.0 * v) : (R)(m + 0.5 * v);
+        const R arg = second ? (R)2 * m + (R)2 * v : m + (R)0.5 * v;
         T[(i == 0) ? (second ? H_EL20 : H_EL0) : (second ? H_EL21 : H_EL1)] = ex(arg);
     } else if (t0 == 6) {
         T[H_A0] = (R)th[P_A];
@@ -144,7 +146,7 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
         T[7] = (R)0;
     }
     __syncthreads();
-    const R gxx = (R)sh[0], gxy = (R)sh[1], gyy = (R)sh[2], edev = (R)sh[3];
+    const R gxx = sh[0], gxy = sh[1], gyy = sh[2], edev = sh[3];
     const R log2e = (R)LOG2E, log2_2pi = (R)2.6514961294723187;   // log2(2 pi)
     const int per_k = 1 + nprof;
     for (int c = threadIdx.x; c < npsf * per_k; c += blockDim.x) {
@@ -337,19 +339,15 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
 //   dN/dmean = N P d,  dN/dG_xx = nu N ((Pd)_x^2 - Pxx)/2,  dN/dG_xy = nu N ((Pd)_x (Pd)_y - Pxy),
 //   dN/dG_yy = nu N ((Pd)_y^2 - Pyy)/2,  dN/de_dev = dc exp(...)/(...)
 
-// at most 64 registers a thread for FP32 (the rarely taken epilogue tail may spill;
-// the pixel loop must not)
 template <class R, int MODE, int PPT>
-__global__ void __launch_bounds__(CHUNK / PPT, (sizeof(R) == 4 ? 65536 / (64 * (CHUNK / PPT)) : 1))
-k_adjoint(const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restrict__ items,
                                                          const PatchGeo* __restrict__ geo,
                                                          const ImgMeta* __restrict__ img, int nprof,
                                                          const float* __restrict__ pixels,
                                                          const R* __restrict__ tbl,
                                                          const R* __restrict__ emap,
                                                          const R* __restrict__ vmap,
-                                                         double* __restrict__ part,
-                                                         const EpilogueArgs ep) {
+                                                         double* __restrict__ part) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     __shared__ R sT[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
@@ -457,7 +455,6 @@ k_adjoint(const WorkItem* __restrict__ items,
     double tot[NV];
     cta_sum<R, NV>(v, tot);
     if (threadIdx.x < NV) part[(size_t)blockIdx.x * NPART + threadIdx.x] = tot[threadIdx.x];
-    if (ep.src_count) adjoint_tail<R>(ep, it.src, geo, img, part);
 }
 
 // ---------------------------------------------------------------------------------
@@ -520,52 +517,26 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
 }
 
 template <class R, int PPT>
-static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st,
-                         const EpilogueArgs& ep) {
+static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st) {
     const R* em = (const R*)P.emap;
     const R* vm = (const R*)P.vmap;
     if (mode == MODE_LL)
         k_adjoint<R, MODE_LL, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part, ep);
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
     else
         k_adjoint<R, MODE_GRAD, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part, ep);
+            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
 }
 
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
-                           const double* d_theta, double* d_total, double* d_local,
-                           double* d_grad) {
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st) {
     if (P.n_item == 0) return cudaSuccess;
-    EpilogueArgs ep{};
-    if (P.src_count && d_theta) {
-        ep.src_count = P.src_count;
-        ep.src_nitems = P.src_nitems;
-        ep.done = P.done;
-        ep.n_with_items = P.n_with_items;
-        ep.idle_src = P.idle_src;
-        ep.n_idle = P.n_idle;
-        ep.n_src = P.n_src;
-        ep.mode = mode;
-        ep.theta = d_theta;
-        ep.patch_off = P.patch_off;
-        ep.md = P.model;
-        ep.kl = P.kl;
-        ep.local_out = d_local;
-        ep.grad_out = d_grad;
-        ep.total_out = d_total;
-        ep.status = P.status;
-        ep.tile_ll = P.tile_ll;
-        ep.n_tile = P.n_tile;
-        ep.item_ll = P.item_ll;
-        ep.n_item_ll = P.single ? P.n_item : 0;
-    }
     if (precision == CELESTE_FP64) {
-        adjoint_impl<double, 1>(P, P.tbl64, mode, st, ep);
+        adjoint_impl<double, 1>(P, P.tbl64, mode, st);
     } else {
         switch (ppt_adjoint(P)) {
-            case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st, ep); break;
-            case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st, ep); break;
-            case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st, ep); break;
+            case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st); break;
+            case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st); break;
+            case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st); break;
             default: return cudaErrorInvalidValue;
         }
     }

@@ -124,6 +124,32 @@ __device__ inline float prior_w_of(const ModelDev& m, int i, int d, float) { ret
 __device__ __forceinline__ float lgr(float x) { return logf(x); }
 __device__ __forceinline__ double lgr(double x) { return log(x); }
 
+// log and reciprocal of a positive normal double for the FP32 path: x = m 2^e split
+// with integer operations, the mantissa's log / reciprocal in FP32 (relative error
+// ~1e-7), the exponent applied in FP64 -- three FP64-pipe instructions instead of the
+// ~40 of a full FP64 log, with FP64's range (k or c2 can fall below FP32's).
+__device__ __forceinline__ void split_pos(double x, float* mant, int* ex) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    *ex = (int)((b >> 52) & 0x7FF) - 1023;                    // x = 1.f * 2^ex
+    *mant = __uint_as_float(0x3F800000u | (unsigned)((b >> 29) & 0x7FFFFFu));   // 1.f in [1, 2)
+}
+__device__ __forceinline__ double log_fast(double x) {
+    float m;
+    int e;
+    split_pos(x, &m, &e);
+    return (double)logf(m) + (double)e * 0.69314718055994530942;
+}
+__device__ __forceinline__ double rcp_fast(double x) {
+    float m;
+    int e;
+    split_pos(x, &m, &e);
+    return (double)(1.0f / m) * __longlong_as_double((long long)(1023 - e) << 52);
+}
+template <class R> __device__ __forceinline__ double logp(double x) { return log_fast(x); }
+template <> __device__ __forceinline__ double logp<double>(double x) { return log(x); }
+template <class R> __device__ __forceinline__ double rcpp(double x) { return rcp_fast(x); }
+template <> __device__ __forceinline__ double rcpp<double>(double x) { return 1.0 / x; }
+
 template <class R>
 __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g) {
     const int lane = threadIdx.x & 31;
@@ -133,21 +159,22 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g
     //   lanes 0..15 log(k_id / w_id); 16..23 log c2 and 1/c2; 24,25 log(a_i/Phi_i);
     //   26,27 log(pv_i / r2_i) and 1/r2_i
     double lv = 0.0, rv = 0.0;
+    // the arguments: lanes 0..15 k/w (log), 16..23 c2 (log, rcp), 24..25 a/Phi (log),
+    // 26..27 r2 (log pv - log r2, rcp); divisions by the constants folded into logs
     if (lane < 16) {
         const int i = lane >> 3, d = lane & 7;
-        lv = log(th[P_K + NCOMP * i + d] / md.prior_w[i][d]);
+        lv = logp<R>(th[P_K + NCOMP * i + d]) - md.prior_logw[i][d];
     } else if (lane < 24) {
         const double c = th[P_C2 + (lane - 16)];
-        lv = log(c);
-        rv = 1.0 / c;
+        lv = logp<R>(c);
+        rv = rcpp<R>(c);
     } else if (lane < 26) {
         const int i = lane - 24;
-        const double phi = (i == 0) ? md.prior_star : 1.0 - md.prior_star;
-        lv = log(th[P_A + i] / phi);
+        lv = logp<R>(th[P_A + i]) - md.prior_logphi[i];
     } else if (lane < 28) {
         const int i = lane - 26;
-        lv = log(md.prior_r[i][1] / th[P_R2 + i]);
-        rv = 1.0 / th[P_R2 + i];
+        lv = md.prior_logpv[i] - logp<R>(th[P_R2 + i]);
+        rv = rcpp<R>(th[P_R2 + i]);
     }
     const int i = (lane >> 3) & 1, d = lane & 7;
     double ic2[4], slog = 0.0;
