@@ -83,9 +83,9 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
                                                 double* __restrict__ grad_out,
                                                 int32_t* __restrict__ status) {
     const int t = threadIdx.x;
-    __shared__ double th[NP], klg[NP], Gy[NY + 1];
+    __shared__ double th[NP], klg[NP];
     __shared__ double klv;
-    __shared__ R el[2], el2[2], dG[3][3], dW[3][3], thr[NP];
+    __shared__ R thr[NP];
     for (int i = t; i < NP; i += blockDim.x) {
         const double v = theta[(size_t)NP * s + i];
         th[i] = v;
@@ -96,63 +96,25 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
     if (t < 32) {
         const double v = kl_warp<R>(*md, th, klg);
         if (t == 0) klv = v;
-    } else if (t == 32 && mode >= MODE_GRAD) {
-        // world-frame d(Wxx, Wxy, Wyy)/d(e_axis, e_angle, e_scale)
-        const R rho = thr[P_AXIS], phi = thr[P_ANGLE], sg = thr[P_SCALE];
-        const R bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
-        R s2, c2;
-        scr((R)2 * phi, &s2, &c2);
-        R da = sg * sg * rho, db = -sg * sg * rho;
-        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
-        dW[1][0] = (R)-2 * bh * s2; dW[1][1] = (R)2 * bh * c2; dW[1][2] = (R)2 * bh * s2;
-        da = sg * ((R)1 + rho * rho); db = sg * ((R)1 - rho * rho);
-        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
     }
-    __syncthreads();
+    // item partials: the source's items are contiguous
+    const int pa = patch_off[s], pb = patch_off[s + 1];
     double gacc = 0.0, lacc = 0.0;
-    const int nv = (mode >= MODE_GRAD) ? 1 + NY : 1;
-    for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
-        const PatchGeo g = geo[p];
-        const ImgMeta& im = img[g.img];
-        if (t < nv) {
-            double v = 0.0;
-            for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
-            Gy[t] = v;
-        } else if (mode >= MODE_GRAD && t >= 32 && t < 36) {
-            const int i = (t - 32) >> 1, second = (t - 32) & 1;
-            R m = thr[P_R1 + i], v = thr[P_R2 + i];
-            for (int j = 0; j < 4; ++j) {
-                const R b = band_beta<R>(im.band, j);
-                m += b * thr[P_C1 + 4 * i + j];
-                v += b * b * thr[P_C2 + 4 * i + j];
-            }
-            if (second) el2[i] = exr((R)2 * m + (R)2 * v);
-            else el[i] = exr(m + (R)0.5 * v);
-        } else if (mode >= MODE_GRAD && t >= 40 && t < 49) {
-            const int q = (t - 40) / 3, c = (t - 40) % 3;
-            const R* Aa = wcs_row<R>(im);
-            const R a0 = Aa[0], a1 = Aa[1], a2 = Aa[2], a3 = Aa[3];
-            const R wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
-            R v;
-            if (c == 0) v = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
-            else if (c == 1) v = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
-            else v = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
-            dG[q][c] = v;
-        }
-        __syncthreads();
-        if (t == 0) lacc += Gy[0];
-        if (mode >= MODE_GRAD && t < NP) {
-            // column t of dy/dtheta in R (branchy, cheap pipes), then FP64 accumulation
-            int y0, y1, y2;
-            R c0, c1, c2;
-            chain_column<R>(t, im.band, wcs_row<R>(im), el, el2, dG, &y0, &c0, &y1, &c1, &y2, &c2);
-            gacc += (double)c0 * Gy[1 + y0] + (double)c1 * Gy[1 + y1] + (double)c2 * Gy[1 + y2];
-        }
-        __syncthreads();
+    if (pb > pa) {
+        const int i0 = geo[pa].item0;
+        const PatchGeo gl = geo[pb - 1];
+        const int i1 = gl.item0 + gl.nitem;
+        if (mode >= MODE_GRAD && t < NP)
+            for (int it = i0; it < i1; ++it) gacc += part[(size_t)it * NPART + PART_TH + t];
+        else if (t == 48)
+            for (int it = i0; it < i1; ++it) lacc += part[(size_t)it * NPART + PART_LL];
     }
+    __shared__ double lsum;
+    if (t == 48) lsum = lacc;
+    __syncthreads();
     if (t == 0) {
         kl_out[s] = klv;
-        if (local_out) local_out[s] = lacc - klv;
+        if (local_out) local_out[s] = lsum - klv;
     }
     if (mode >= MODE_GRAD && grad_out && t < NP) grad_out[(size_t)NP * s + t] = gacc - klg[t];
     __syncthreads();   // shared scratch is reused by the caller

@@ -27,20 +27,23 @@ enum : int { Y_A0 = 0, Y_A1, Y_EL0, Y_EL20, Y_EL1, Y_EL21, Y_MX, Y_MY, Y_EDEV, Y
              Y_GYY, NY };
 constexpr int NYH = NY * (NY + 1) / 2;   // packed upper triangle of the y-Hessian
 
-// Work-item partial record (doubles): [0] sum of ll over the item's pixels,
-// [1..NY] gradient wrt y, [1+NY ..) packed y-Hessian (Hessian mode only).
-constexpr int PART_LL = 0, PART_G = 1, PART_H = 1 + NY;
+// Work-item partial record (doubles): [0] sum of ll over the item's pixels; gradient
+// mode: [1..44] gradient wrt theta (the chain rule applied per item); Hessian mode:
+// [1..NY] gradient wrt y, [1+NY ..) packed y-Hessian.
+constexpr int PART_LL = 0, PART_G = 1, PART_H = 1 + NY, PART_TH = 1;
 constexpr int NPART = 1 + NY + NYH;
 
 // Mixture table of one (source, patch), in units of the pixel precision R:
 //   header [0..7]: a0 a1 E[l|star] E[l^2|star] E[l|gal] E[l^2|gal] iota 0
 //   means  [8..15]: pixel-frame mean of PSF component k (x, y)
 //   star   [16 + 8k]: qa qb qc qd pxx pxy pyy c
-//   galaxy [48 + 12 (k nprof + j)]: qa qb qc qd pxx pxy pyy c dc nu 0 0
+//   dG     [48 + 3q + c]: d(Gxx, Gxy, Gyy)[c] / d(e_axis, e_angle, e_scale)[q] (chain rule)
+//   galaxy [64 + 12 (k nprof + j)]: qa qb qc qd pxx pxy pyy c dc nu 0 0
 // Component density: c * exp2(qa dx^2 + qb dx dy + qc dy^2 + qd) with
 // (qa, qb, qc) = -log2(e) (Pxx/2, Pxy, Pyy/2) and qd = -log2(2 pi sqrt(det C)).
-constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_GAL = 48, GAL_STRIDE = 12;
-constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 816
+constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_GAL = 64,
+              GAL_STRIDE = 12;
+constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
 
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)

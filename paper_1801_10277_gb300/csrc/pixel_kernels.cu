@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "epilogue.cuh"
 
 namespace cel {
 
@@ -126,6 +127,19 @@ __global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restr
         sh[1] = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
         sh[2] = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
         sh[3] = (R)th[P_EDEV];
+        // chain-rule block for the shape: dG = A dW A^T, W over (e_axis, e_angle, e_scale)
+        R dW[3][3];
+        R da = sg * sg * rho, db = -sg * sg * rho;
+        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+        dW[1][0] = (R)-2 * bh * s2; dW[1][1] = (R)2 * bh * c2; dW[1][2] = (R)2 * bh * s2;
+        da = sg * ((R)1 + rho * rho); db = sg * ((R)1 - rho * rho);
+        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
+        for (int q = 0; q < 3; ++q) {
+            const R ux = dW[q][0], uxy = dW[q][1], uy = dW[q][2];
+            T[T_DG + 3 * q + 0] = a0 * a0 * ux + (R)2 * a0 * a1 * uxy + a1 * a1 * uy;
+            T[T_DG + 3 * q + 1] = a0 * a2 * ux + (a0 * a3 + a1 * a2) * uxy + a1 * a3 * uy;
+            T[T_DG + 3 * q + 2] = a2 * a2 * ux + (R)2 * a2 * a3 * uxy + a3 * a3 * uy;
+        }
     } else if (t0 >= 2 && t0 < 6) {
         // brightness moments in this band: log l | type i ~ N(m, v); E[l] = e^{m+v/2}, E[l^2] = e^{2m+2v}
         const int i = (t0 - 2) >> 1, second = (t0 - 2) & 1;
@@ -452,9 +466,24 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
             v[1 + Y_GYY] += (R)0.5 * u1 * syy[p];
         }
     }
-    double tot[NV];
+    __shared__ double tot[NV];
     cta_sum<R, NV>(v, tot);
-    if (threadIdx.x < NV) part[(size_t)blockIdx.x * NPART + threadIdx.x] = tot[threadIdx.x];
+    __syncthreads();
+    double* out = part + (size_t)blockIdx.x * NPART;
+    if (threadIdx.x == 0) out[PART_LL] = tot[0];
+    if constexpr (MODE >= MODE_GRAD) {
+        // chain rule of this item's y-gradient: d/dtheta_j = sum_y dy/dtheta_j d/dy
+        // (coefficients in R, sums in FP64), one thread per parameter
+        for (int j = threadIdx.x; j < NP; j += blockDim.x) {
+            const R el[2] = {sT[H_EL0], sT[H_EL1]}, el2[2] = {sT[H_EL20], sT[H_EL21]};
+            int y0, y1, y2;
+            R c0, c1, c2;
+            chain_column<R>(j, im.band, wcs_row<R>(im), el, el2, (const R(*)[3])(sT + T_DG), &y0,
+                            &c0, &y1, &c1, &y2, &c2);
+            out[PART_TH + j] = (double)c0 * tot[1 + y0] + (double)c1 * tot[1 + y1] +
+                               (double)c2 * tot[1 + y2];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------

@@ -29,13 +29,18 @@ def rflux(th):
     return np.exp(th[synth.I_R1 + i] + 0.5 * th[synth.I_R2 + i])
 
 
-def _compare(cel, prob, which=None, max_sweeps=20):
+def _compare(cel, prob, which=None, max_sweeps=20, sweep_tol=1e-12):
+    """Both sides sweep until the total ELBO stops moving (relative 1e-12): a looser
+    sweep tolerance leaves overlapping sources short of the joint optimum by amounts
+    that depend on the path."""
     orc = Oracle(prob)
-    o_th, o_it, o_st, o_el, _ = orc.fit(prob.theta, which=which, max_sweeps=max_sweeps)
+    o_th, o_it, o_st, o_el, _ = orc.fit(prob.theta, which=which, max_sweeps=max_sweeps,
+                                        sweep_tol=sweep_tol)
     P = cel.Problem(prob)
     moving = np.arange(prob.n_src) if which is None else np.asarray(which)
     for prec in (cel.FP64, cel.FP32):
-        th, it, st, el = P.fit(prob.theta, which=which, precision=prec, max_sweeps=max_sweeps)
+        th, it, st, el = P.fit(prob.theta, which=which, precision=prec, max_sweeps=max_sweeps,
+                               sweep_tol=sweep_tol)
         assert np.all(it[moving] <= 50 * max_sweeps * (2 if prec == cel.FP32 else 1))
         both = [s for s in moving if st[s] == 0 and o_st[s] == 0]
         assert len(both) >= 0.75 * len(moving), (prec, st[moving], o_st[moving])
