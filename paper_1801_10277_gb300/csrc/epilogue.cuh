@@ -104,10 +104,22 @@ __device__ __forceinline__ void finalize_source(int s, int mode, const double* _
         const int i0 = geo[pa].item0;
         const PatchGeo gl = geo[pb - 1];
         const int i1 = gl.item0 + gl.nitem;
-        if (mode >= MODE_GRAD && t < NP)
-            for (int it = i0; it < i1; ++it) gacc += part[(size_t)it * NPART + PART_TH + t];
-        else if (t == 48)
-            for (int it = i0; it < i1; ++it) lacc += part[(size_t)it * NPART + PART_LL];
+        // four independent FP64 accumulators so the loads overlap; fixed order
+        const int col = (mode >= MODE_GRAD && t < NP) ? PART_TH + t : (t == 48 ? PART_LL : -1);
+        if (col >= 0) {
+            double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+            int it = i0;
+            for (; it + 4 <= i1; it += 4) {
+                q0 += part[(size_t)it * NPART + col];
+                q1 += part[(size_t)(it + 1) * NPART + col];
+                q2 += part[(size_t)(it + 2) * NPART + col];
+                q3 += part[(size_t)(it + 3) * NPART + col];
+            }
+            for (; it < i1; ++it) q0 += part[(size_t)it * NPART + col];
+            const double sum = (q0 + q1) + (q2 + q3);
+            if (t == 48) lacc = sum;
+            else gacc = sum;
+        }
     }
     __shared__ double lsum;
     if (t == 48) lsum = lacc;

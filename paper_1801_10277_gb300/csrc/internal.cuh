@@ -87,6 +87,7 @@ struct ModelDev {
     double prior_logw[2][NCOMP];      // log w_id, log Phi_i, log pv_i
     double prior_logphi[2];
     double prior_logpv[2];
+    double prior_inv_pv[2];
     // FP32 copies for the FP32 path
     float prof_w_f[MAXPROF], prof_nu_f[MAXPROF];
     float prior_star_f;
@@ -103,6 +104,7 @@ inline void fill_float_copies(ModelDev& m) {
         for (int d = 0; d < NCOMP; ++d) m.prior_logw[i][d] = std::log(m.prior_w[i][d]);
         m.prior_logphi[i] = std::log(i == 0 ? m.prior_star : 1.0 - m.prior_star);
         m.prior_logpv[i] = std::log(m.prior_r[i][1]);
+        m.prior_inv_pv[i] = 1.0 / m.prior_r[i][1];
     }
     for (int j = 0; j < MAXPROF; ++j) {
         m.prof_w_f[j] = (float)m.prof_w[j];

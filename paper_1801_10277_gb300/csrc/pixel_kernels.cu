@@ -74,7 +74,8 @@ __device__ __forceinline__ void load_table(R* sT, const R* gT, int n) {
 }  // namespace
 
 // ---------------------------------------------------------------------------------
-// k_prep: one CTA per patch; thread c builds mixture component c.
+// k_prep: one CTA per source; groups of 8 lanes build the patch headers, then the
+// threads build the mixture components of all its patches.
 //   star component k:        weight alpha_k, mean mu + xi_k, covariance Sigma_k
 //   galaxy component (k, j): weight alpha_k w_j (1 - e_dev) [exp] or alpha_k w_j e_dev [dev],
 //                            covariance Sigma_k + nu_j G,  G = A W A^T,
@@ -91,110 +92,147 @@ __device__ __forceinline__ double ex(double x) { return exp(x); }
 __device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
 
+constexpr int PREP_THREADS = 256;
+constexpr int PREP_HDR = 8;   // lanes per patch header
+
 template <class R>
-__global__ void k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
-                       const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
-                       int n_patch, int nprof, R* __restrict__ tbl) {
-    const int p = blockIdx.x;
-    if (p >= n_patch) return;
-    __shared__ R sh[4];   // gxx gxy gyy edev
-    const PatchGeo g = geo[p];
-    const ImgMeta& im = img[g.img];
-    const double* th = theta + (size_t)NP * g.src;
-    R* T = tbl + (size_t)p * TBL_STRIDE;
-    const int npsf = im.npsf;
-    const int t0 = threadIdx.x;
-    if (t0 == 0) {
-        // position relative to the patch origin in FP64 (the pixel frame spans 2048 px)
-        const double* A = im.A;
-        const R mux = (R)(A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0);
-        const R muy = (R)(A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0);
-        for (int k = 0; k < MAXPSF; ++k) {
-            const R* ps = psf_row(im, k, R());
-            T[T_MEAN + 2 * k] = k < npsf ? mux + ps[1] : (R)0;
-            T[T_MEAN + 2 * k + 1] = k < npsf ? muy + ps[2] : (R)0;
-        }
-    } else if (t0 == 1) {
-        // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi), G = A W A^T
-        const R rho = (R)th[P_AXIS], phi = (R)th[P_ANGLE], sg = (R)th[P_SCALE];
-        const R ah = (R)0.5 * sg * sg * ((R)1 + rho * rho), bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
-        R s2, c2;
-        sc(2 * phi, &s2, &c2);
-        const R wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
-        const R a0 = wcs_of(im, 0, R()), a1 = wcs_of(im, 1, R()), a2 = wcs_of(im, 2, R()),
-                a3 = wcs_of(im, 3, R());
-        sh[0] = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
-        sh[1] = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
-        sh[2] = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
-        sh[3] = (R)th[P_EDEV];
-        // chain-rule block for the shape: dG = A dW A^T, W over (e_axis, e_angle, e_scale)
-        R dW[3][3];
-        R da = sg * sg * rho, db = -sg * sg * rho;
-        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
-        dW[1][0] = (R)-2 * bh * s2; dW[1][1] = (R)2 * bh * c2; dW[1][2] = (R)2 * bh * s2;
-        da = sg * ((R)1 + rho * rho); db = sg * ((R)1 - rho * rho);
-        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
-        for (int q = 0; q < 3; ++q) {
-            const R ux = dW[q][0], uxy = dW[q][1], uy = dW[q][2];
-            T[T_DG + 3 * q + 0] = a0 * a0 * ux + (R)2 * a0 * a1 * uxy + a1 * a1 * uy;
-            T[T_DG + 3 * q + 1] = a0 * a2 * ux + (a0 * a3 + a1 * a2) * uxy + a1 * a3 * uy;
-            T[T_DG + 3 * q + 2] = a2 * a2 * ux + (R)2 * a2 * a3 * uxy + a3 * a3 * uy;
-        }
-    } else if (t0 >= 2 && t0 < 6) {
-        // brightness moments in this band: log l | type i ~ N(m, v); E[l] = e^{m+v/2}, E[l^2] = e^{2m+2v}
-        const int i = (t0 - 2) >> 1, second = (t0 - 2) & 1;
-        R m = (R)th[P_R1 + i], v = (R)th[P_R2 + i];
-        for (int j = 0; j < 4; ++j) {
-            if (color_beta(im.band, j) != 0.0) {
-                const R b = (R)color_beta(im.band, j);
-                m += b * (R)th[P_C1 + 4 * i + j];
-                v += b * b * (R)th[P_C2 + 4 * i + j];
-            }
-        }
-        const R arg = second ? (R)2 * m + (R)2 * v : m + (R)0.5 * v;
-        T[(i == 0) ? (second ? H_EL20 : H_EL0) : (second ? H_EL21 : H_EL1)] = ex(arg);
-    } else if (t0 == 6) {
-        T[H_A0] = (R)th[P_A];
-        T[H_A1] = (R)th[P_A + 1];
-        T[H_IOTA] = (R)im.iota;
-        T[7] = (R)0;
+__global__ void __launch_bounds__(PREP_THREADS)
+k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
+       const int32_t* __restrict__ patch_off, const ImgMeta* __restrict__ img,
+       const ModelDev* __restrict__ md, int n_src, int nprof, R* __restrict__ tbl) {
+    const int s = blockIdx.x;
+    if (s >= n_src) return;
+    const int p0 = patch_off[s], np = patch_off[s + 1] - p0;
+    if (np == 0) return;
+    __shared__ double th[NP];
+    __shared__ R thr[NP];
+    __shared__ R gsh[PREP_THREADS / PREP_HDR][4];   // gxx gxy gyy e_dev per patch of a round
+    const int t = threadIdx.x;
+    if (t < NP) {
+        const double v = theta[(size_t)NP * s + t];
+        th[t] = v;
+        thr[t] = (R)v;   // the parameters converted once per source
     }
     __syncthreads();
-    const R gxx = sh[0], gxy = sh[1], gyy = sh[2], edev = sh[3];
-    const R log2e = (R)LOG2E, log2_2pi = (R)2.6514961294723187;   // log2(2 pi)
     const int per_k = 1 + nprof;
-    for (int c = threadIdx.x; c < npsf * per_k; c += blockDim.x) {
-        const int k = c / per_k, j = c % per_k - 1;
-        const R* ps = psf_row(im, k, R());
-        R cxx = ps[3], cxy = ps[4], cyy = ps[5], w = ps[0], dw = 0, nu = 0;
-        if (j >= 0) {
-            nu = prof_nu_of(*md, j, R());
-            const bool dev = j >= md->n_exp;
-            cxx += nu * gxx;
-            cxy += nu * gxy;
-            cyy += nu * gyy;
-            const R aw = ps[0] * prof_w_of(*md, j, R());
-            w = aw * (dev ? edev : (R)1 - edev);
-            dw = dev ? aw : -aw;
+    // patches in rounds of PREP_THREADS / PREP_HDR
+    for (int r0 = 0; r0 < np; r0 += PREP_THREADS / PREP_HDR) {
+        const int pi = r0 + t / PREP_HDR, role = t % PREP_HDR;
+        if (pi < np) {
+            const PatchGeo g = geo[p0 + pi];
+            const ImgMeta& im = img[g.img];
+            R* T = tbl + (size_t)(p0 + pi) * TBL_STRIDE;
+            const int npsf = im.npsf;
+            if (role == 0) {
+                // position relative to the patch origin in FP64 (the pixel frame spans 2048 px)
+                const double* A = im.A;
+                const R mux = (R)(A[0] * th[0] + A[1] * th[1] + im.t[0] - g.x0);
+                const R muy = (R)(A[2] * th[0] + A[3] * th[1] + im.t[1] - g.y0);
+                for (int k = 0; k < MAXPSF; ++k) {
+                    const R* ps = psf_row(im, k, R());
+                    T[T_MEAN + 2 * k] = k < npsf ? mux + ps[1] : (R)0;
+                    T[T_MEAN + 2 * k + 1] = k < npsf ? muy + ps[2] : (R)0;
+                }
+            } else if (role == 1) {
+                // world-frame ellipse W = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi),
+                // G = A W A^T, and the chain-rule block dG = A dW A^T over (axis, angle, scale)
+                const R rho = thr[P_AXIS], phi = thr[P_ANGLE], sg = thr[P_SCALE];
+                const R ah = (R)0.5 * sg * sg * ((R)1 + rho * rho), bh = (R)0.5 * sg * sg * ((R)1 - rho * rho);
+                R s2, c2;
+                sc(2 * phi, &s2, &c2);
+                const R wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
+                const R a0 = wcs_of(im, 0, R()), a1 = wcs_of(im, 1, R()), a2 = wcs_of(im, 2, R()),
+                        a3 = wcs_of(im, 3, R());
+                R* G = gsh[t / PREP_HDR];
+                G[0] = a0 * a0 * wxx + (R)2 * a0 * a1 * wxy + a1 * a1 * wyy;
+                G[1] = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
+                G[2] = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
+                G[3] = thr[P_EDEV];
+                R dW[3][3];
+                R da = sg * sg * rho, db = -sg * sg * rho;
+                dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+                dW[1][0] = (R)-2 * bh * s2; dW[1][1] = (R)2 * bh * c2; dW[1][2] = (R)2 * bh * s2;
+                da = sg * ((R)1 + rho * rho); db = sg * ((R)1 - rho * rho);
+                dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
+                for (int q = 0; q < 3; ++q) {
+                    const R ux = dW[q][0], uxy = dW[q][1], uy = dW[q][2];
+                    T[T_DG + 3 * q + 0] = a0 * a0 * ux + (R)2 * a0 * a1 * uxy + a1 * a1 * uy;
+                    T[T_DG + 3 * q + 1] = a0 * a2 * ux + (a0 * a3 + a1 * a2) * uxy + a1 * a3 * uy;
+                    T[T_DG + 3 * q + 2] = a2 * a2 * ux + (R)2 * a2 * a3 * uxy + a3 * a3 * uy;
+                }
+            } else if (role < 6) {
+                // brightness moments in this band: log l | type i ~ N(m, v);
+                // E[l] = e^{m+v/2}, E[l^2] = e^{2m+2v}
+                const int i = (role - 2) >> 1, second = (role - 2) & 1;
+                R m = thr[P_R1 + i], v = thr[P_R2 + i];
+                for (int j = 0; j < 4; ++j) {
+                    const R b = band_beta<R>(im.band, j);
+                    m += b * thr[P_C1 + 4 * i + j];
+                    v += b * b * thr[P_C2 + 4 * i + j];
+                }
+                const R arg = second ? (R)2 * m + (R)2 * v : m + (R)0.5 * v;
+                T[(i == 0) ? (second ? H_EL20 : H_EL0) : (second ? H_EL21 : H_EL1)] = ex(arg);
+            } else if (role == 6) {
+                T[H_A0] = thr[P_A];
+                T[H_A1] = thr[P_A + 1];
+                T[H_IOTA] = (R)im.iota;
+                T[7] = (R)0;
+            }
         }
-        const R det = cxx * cyy - cxy * cxy;
-        const R idet = (R)1 / det;
-        const R pxx = cyy * idet, pxy = -cxy * idet, pyy = cxx * idet;
-        const int base = (j < 0) ? T_STAR + k * STAR_STRIDE : T_GAL + (k * nprof + j) * GAL_STRIDE;
-        T[base + 0] = (R)-0.5 * log2e * pxx;
-        T[base + 1] = -log2e * pxy;
-        T[base + 2] = (R)-0.5 * log2e * pyy;
-        T[base + 3] = -log2_2pi - (R)0.5 * lg2(det);
-        T[base + 4] = pxx;
-        T[base + 5] = pxy;
-        T[base + 6] = pyy;
-        T[base + 7] = w;
-        if (j >= 0) {
-            T[base + 8] = dw;
-            T[base + 9] = nu;
-            T[base + 10] = 0;
-            T[base + 11] = 0;
+        __syncthreads();
+        // components of the patches of this round
+        const int nr = min(np - r0, PREP_THREADS / PREP_HDR);
+        const R log2e = (R)LOG2E, log2_2pi = (R)2.6514961294723187;   // log2(2 pi)
+        for (int idx = t; ; idx += blockDim.x) {
+            // component idx of the round: patch pj = first patch whose running count exceeds idx
+            int pj = 0, base_c = idx;
+            int npsf_j = 0;
+            const ImgMeta* imj = nullptr;
+            while (pj < nr) {
+                imj = &img[geo[p0 + r0 + pj].img];
+                npsf_j = imj->npsf;
+                if (base_c < npsf_j * per_k) break;
+                base_c -= npsf_j * per_k;
+                ++pj;
+            }
+            if (pj >= nr) break;
+            const ImgMeta& im = *imj;
+            R* T = tbl + (size_t)(p0 + r0 + pj) * TBL_STRIDE;
+            const R* Gp = gsh[pj];
+            const R gxx = Gp[0], gxy = Gp[1], gyy = Gp[2], edev = Gp[3];
+            const int k = base_c / per_k, j = base_c % per_k - 1;
+            const R* ps = psf_row(im, k, R());
+            R cxx = ps[3], cxy = ps[4], cyy = ps[5], w = ps[0], dw = 0, nu = 0;
+            if (j >= 0) {
+                nu = prof_nu_of(*md, j, R());
+                const bool dev = j >= md->n_exp;
+                cxx += nu * gxx;
+                cxy += nu * gxy;
+                cyy += nu * gyy;
+                const R aw = ps[0] * prof_w_of(*md, j, R());
+                w = aw * (dev ? edev : (R)1 - edev);
+                dw = dev ? aw : -aw;
+            }
+            const R det = cxx * cyy - cxy * cxy;
+            const R idet = (R)1 / det;
+            const R pxx = cyy * idet, pxy = -cxy * idet, pyy = cxx * idet;
+            const int base = (j < 0) ? T_STAR + k * STAR_STRIDE : T_GAL + (k * nprof + j) * GAL_STRIDE;
+            T[base + 0] = (R)-0.5 * log2e * pxx;
+            T[base + 1] = -log2e * pxy;
+            T[base + 2] = (R)-0.5 * log2e * pyy;
+            T[base + 3] = -log2_2pi - (R)0.5 * lg2(det);
+            T[base + 4] = pxx;
+            T[base + 5] = pxy;
+            T[base + 6] = pyy;
+            T[base + 7] = w;
+            if (j >= 0) {
+                T[base + 8] = dw;
+                T[base + 9] = nu;
+                T[base + 10] = 0;
+                T[base + 11] = 0;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -498,10 +536,12 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
                         cudaStream_t st) {
     if (P.n_patch == 0) return cudaSuccess;
     if (precision == CELESTE_FP64)
-        k_prep<double><<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
+        k_prep<double><<<P.n_src, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
+                                                         P.n_src, P.nprof,
                                                  P.tbl64);
     else
-        k_prep<float><<<P.n_patch, 64, 0, st>>>(d_theta, P.geo, P.img, P.model, P.n_patch, P.nprof,
+        k_prep<float><<<P.n_src, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
+                                                        P.n_src, P.nprof,
                                                 P.tbl32);
     return cudaGetLastError();
 }

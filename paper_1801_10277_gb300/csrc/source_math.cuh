@@ -221,13 +221,14 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g
     double klv = 0.0;
     if (lane < 16 && d == 0) {
         const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
-        const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
-        const double K = 0.5 * (lpr + (r2 + (r1 - pm) * (r1 - pm)) / pv - 1.0) + term;
+        const double pm = md.prior_r[i][0];
+        const double ipv = md.prior_inv_pv[i];
+        const double K = 0.5 * (lpr + (r2 + (r1 - pm) * (r1 - pm)) * ipv - 1.0) + term;
         const double ad = th[P_A + i];
         klv = ad * (la + K);
         g[P_A + i] = la + 1.0 + K;
-        g[P_R1 + i] = ad * (r1 - pm) / pv;
-        g[P_R2 + i] = ad * 0.5 * (1.0 / pv - ir2);
+        g[P_R1 + i] = ad * (r1 - pm) * ipv;
+        g[P_R2 + i] = ad * 0.5 * (ipv - ir2);
         for (int j = 0; j < 4; ++j) {
             g[P_C1 + 4 * i + j] = ad * dc1[j];
             g[P_C2 + 4 * i + j] = ad * dc2[j];
