@@ -652,11 +652,11 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     cudaEvent_t a, b;
     CEL_CUDA(cudaEventCreate(&a));
     CEL_CUDA(cudaEventCreate(&b));
-    const int cands[3] = {1, 2, 4};
+    const int cands[4] = {1, 2, 4, 3};   // 3: two pixels per thread in packed FP32x2
     float best_c = 1e30f, best_a = 1e30f;
     int pick_c = 2, pick_a = 2;
     cudaError_t e = cudaSuccess;
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
         P.tune_contrib = P.tune_adjoint = cands[ci];
         // warm once, then time reps launches of each kernel
         e = launch_contrib(P, CELESTE_FP32_ACC64, st);
@@ -690,8 +690,9 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
 
 celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
-    auto okp = [](int v) { return v == 0 || v == 1 || v == 2 || v == 4; };
-    if (!okp(ppt_contrib) || !okp(ppt_adjoint)) return fail(CELESTE_ERR_ARG, "pixels per thread must be 0, 1, 2 or 4");
+    auto okp = [](int v) { return v >= 0 && v <= 4; };
+    if (!okp(ppt_contrib) || !okp(ppt_adjoint))
+        return fail(CELESTE_ERR_ARG, "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 packed FP32x2 pairs");
     pr->P.tune_contrib = ppt_contrib;
     pr->P.tune_adjoint = ppt_adjoint;
     return CELESTE_OK;

@@ -525,6 +525,252 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
 }
 
 // ---------------------------------------------------------------------------------
+// Packed FP32x2 variants (tuning code 3): two pixels per thread carried in float2
+// registers, every per-component operation one fma/mul/add.rn.f32x2 instruction (half
+// the issue slots of the scalar pair).  The table is staged in shared memory with each
+// coefficient duplicated, so a coefficient pair is one 64-bit load.
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ex2x2(float2 a) { return make_float2(ex2(a.x), ex2(a.y)); }
+
+// The PSF-shifted means and the precision entries (Pxx, Pxy, Pyy) are staged negated, so
+// d = p - mean is one add and (Pd)_x^2 - Pxx one fma; the kernels then carry -(Pd) and
+// flip the sign of its sums once per pixel.
+__device__ __forceinline__ bool staged_negated(int i) {
+    if (i >= T_MEAN && i < T_STAR) return true;
+    if (i >= T_STAR && i < T_STAR + MAXPSF * STAR_STRIDE) {
+        const int r = (i - T_STAR) % STAR_STRIDE;
+        return r >= 4 && r <= 6;
+    }
+    if (i >= T_GAL) {
+        const int r = (i - T_GAL) % GAL_STRIDE;
+        return r >= 4 && r <= 6;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void load_table_x2(float2* sT2, const float* gT, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float v = gT[i];
+        sT2[i] = f2(staged_negated(i) ? -v : v);
+    }
+    __syncthreads();
+}
+
+constexpr int PX2_THREADS = CHUNK / 2;
+
+__global__ void __launch_bounds__(PX2_THREADS) k_contrib_x2(const WorkItem* __restrict__ items,
+                                                          const PatchGeo* __restrict__ geo,
+                                                          const ImgMeta* __restrict__ img, int nprof,
+                                                          const float* __restrict__ tbl,
+                                                          float* __restrict__ spE,
+                                                          float* __restrict__ spV,
+                                                          const uint8_t* __restrict__ single,
+                                                          const float* __restrict__ pixels,
+                                                          const float* __restrict__ sky_map,
+                                                          float* __restrict__ emap,
+                                                          float* __restrict__ vmap,
+                                                          double* __restrict__ item_ll) {
+    __shared__ float2 sT2[TBL_STRIDE];
+    const WorkItem it = items[blockIdx.x];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int npsf = im.npsf;
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
+    const int t = threadIdx.x;
+    int xs[2], ys[2];
+    bool ok[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int l = t + p * PX2_THREADS;
+        ok[p] = l < it.n;
+        const int q = it.q0 + (ok[p] ? l : 0);
+        ys[p] = q / g.w;
+        xs[p] = q - ys[p] * g.w;
+    }
+    const float2 X = make_float2((float)xs[0], (float)xs[1]), Y = make_float2((float)ys[0], (float)ys[1]);
+    float2 g0 = f2(0.f), g1 = f2(0.f);
+    for (int k = 0; k < npsf; ++k) {
+        const float2 dx = __fadd2_rn(X, sT2[T_MEAN + 2 * k]);
+        const float2 dy = __fadd2_rn(Y, sT2[T_MEAN + 2 * k + 1]);
+        const float2 dxx = __fmul2_rn(dx, dx), dxy = __fmul2_rn(dx, dy), dyy = __fmul2_rn(dy, dy);
+        const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
+        float2 a = __ffma2_rn(S[2], dyy, S[3]);
+        a = __ffma2_rn(S[1], dxy, a);
+        a = __ffma2_rn(S[0], dxx, a);
+        g0 = __ffma2_rn(S[7], ex2x2(a), g0);
+        const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
+        for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+            float2 b = __ffma2_rn(G[2], dyy, G[3]);
+            b = __ffma2_rn(G[1], dxy, b);
+            b = __ffma2_rn(G[0], dxx, b);
+            g1 = __ffma2_rn(G[7], ex2x2(b), g1);
+        }
+    }
+    const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
+    const float el0 = sT2[H_EL0].x, el1 = sT2[H_EL1].x;
+    const float em0 = sT2[H_EL20].x / (el0 * el0) - 1.f, em1 = sT2[H_EL21].x / (el1 * el1) - 1.f;
+    float ll[1] = {0.f};
+    const float gg0[2] = {g0.x, g0.y}, gg1[2] = {g1.x, g1.y};
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        if (!ok[p]) continue;
+        const float f0 = iota * el0 * gg0[p], f1 = iota * el1 * gg1[p];
+        const float e = a0 * f0 + a1 * f1;
+        const float v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
+                        a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
+        const int q = it.q0 + t + p * PX2_THREADS;
+        const int64_t sp = g.sp_off + q;
+        if (single && single[sp]) {
+            const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
+            const float E = (im.has_sky_map ? sky_map[m] : (float)im.sky) + e;
+            const float x = pixels[m];
+            const float iE = 1.f / E;
+            ll[0] += x * (lg(E) - 0.5f * v * iE * iE) - E;
+            emap[m] = E;
+            vmap[m] = v;
+        } else {
+            spE[sp] = e;
+            spV[sp] = v;
+        }
+    }
+    if (single) {
+        double tot[1];
+        cta_sum<float, 1>(ll, tot);
+        if (threadIdx.x == 0) item_ll[blockIdx.x] = tot[0];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(PX2_THREADS) k_adjoint_x2(const WorkItem* __restrict__ items,
+                                                          const PatchGeo* __restrict__ geo,
+                                                          const ImgMeta* __restrict__ img, int nprof,
+                                                          const float* __restrict__ pixels,
+                                                          const float* __restrict__ tbl,
+                                                          const float* __restrict__ emap,
+                                                          const float* __restrict__ vmap,
+                                                          double* __restrict__ part) {
+    constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
+    __shared__ float2 sT2[TBL_STRIDE];
+    const WorkItem it = items[blockIdx.x];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    const int npsf = im.npsf;
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
+    float v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = 0.f;
+    const int t = threadIdx.x;
+    int xs[2], ys[2];
+    bool ok[2];
+    float x[2], cE[2], cV[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int l = t + p * PX2_THREADS;
+        ok[p] = l < it.n;
+        const int q = it.q0 + (ok[p] ? l : 0);
+        ys[p] = q / g.w;
+        xs[p] = q - ys[p] * g.w;
+        const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
+        x[p] = pixels[m];
+        const float E = emap[m], V = vmap[m];
+        const float iE = 1.f / E;
+        if (ok[p]) v[0] += x[p] * (lg(E) - 0.5f * V * iE * iE) - E;
+        cE[p] = x[p] * (iE + V * iE * iE * iE) - 1.f;
+        cV[p] = -0.5f * x[p] * iE * iE;
+    }
+    if constexpr (MODE >= MODE_GRAD) {
+        const float2 X = make_float2((float)xs[0], (float)xs[1]), Y = make_float2((float)ys[0], (float)ys[1]);
+        float2 g0 = f2(0.f), gx0 = f2(0.f), gy0 = f2(0.f);
+        float2 g1 = f2(0.f), gx1 = f2(0.f), gy1 = f2(0.f), de1 = f2(0.f);
+        float2 sxx = f2(0.f), sxy = f2(0.f), syy = f2(0.f);
+        for (int k = 0; k < npsf; ++k) {
+            const float2 dx = __fadd2_rn(X, sT2[T_MEAN + 2 * k]);
+            const float2 dy = __fadd2_rn(Y, sT2[T_MEAN + 2 * k + 1]);
+            const float2 dxx = __fmul2_rn(dx, dx), dxy = __fmul2_rn(dx, dy), dyy = __fmul2_rn(dy, dy);
+            {
+                const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
+                float2 a = __ffma2_rn(S[2], dyy, S[3]);
+                a = __ffma2_rn(S[1], dxy, a);
+                a = __ffma2_rn(S[0], dxx, a);
+                const float2 n = __fmul2_rn(S[7], ex2x2(a));
+                const float2 qx = __ffma2_rn(S[4], dx, __fmul2_rn(S[5], dy));
+                const float2 qy = __ffma2_rn(S[5], dx, __fmul2_rn(S[6], dy));
+                g0 = __fadd2_rn(g0, n);
+                gx0 = __ffma2_rn(n, qx, gx0);
+                gy0 = __ffma2_rn(n, qy, gy0);
+            }
+            const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
+            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+                float2 b = __ffma2_rn(G[2], dyy, G[3]);
+                b = __ffma2_rn(G[1], dxy, b);
+                b = __ffma2_rn(G[0], dxx, b);
+                const float2 e = ex2x2(b);
+                const float2 n = __fmul2_rn(G[7], e);
+                const float2 npxx = G[4], npxy = G[5], npyy = G[6];   // negated
+                const float2 qx = __ffma2_rn(npxx, dx, __fmul2_rn(npxy, dy));   // -(Pd)_x
+                const float2 qy = __ffma2_rn(npxy, dx, __fmul2_rn(npyy, dy));   // -(Pd)_y
+                g1 = __fadd2_rn(g1, n);
+                gx1 = __ffma2_rn(n, qx, gx1);
+                gy1 = __ffma2_rn(n, qy, gy1);
+                de1 = __ffma2_rn(G[8], e, de1);
+                const float2 nn = __fmul2_rn(n, G[9]);
+                sxx = __ffma2_rn(nn, __ffma2_rn(qx, qx, npxx), sxx);
+                sxy = __ffma2_rn(nn, __ffma2_rn(qx, qy, npxy), sxy);
+                syy = __ffma2_rn(nn, __ffma2_rn(qy, qy, npyy), syy);
+            }
+        }
+        const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
+        const float el0 = sT2[H_EL0].x, el20 = sT2[H_EL20].x, el1 = sT2[H_EL1].x, el21 = sT2[H_EL21].x;
+        const float i2 = iota * iota;
+        // gx, gy were accumulated with -(Pd): flip them here
+        const float G0[2] = {g0.x, g0.y}, GX0[2] = {-gx0.x, -gx0.y}, GY0[2] = {-gy0.x, -gy0.y};
+        const float G1[2] = {g1.x, g1.y}, GX1[2] = {-gx1.x, -gx1.y}, GY1[2] = {-gy1.x, -gy1.y};
+        const float DE[2] = {de1.x, de1.y}, SXX[2] = {sxx.x, sxx.y}, SXY[2] = {sxy.x, sxy.y},
+                    SYY[2] = {syy.x, syy.y};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            if (!ok[p]) continue;
+            const float f0 = iota * el0 * G0[p], f1 = iota * el1 * G1[p];
+            const float Es = a0 * f0 + a1 * f1;
+            const float w1 = cE[p] - 2.f * cV[p] * Es, w2 = cV[p];
+            const float s0 = i2 * G0[p] * G0[p], s1 = i2 * G1[p] * G1[p];
+            v[1 + Y_A0] += w1 * f0 + w2 * el20 * s0;
+            v[1 + Y_A1] += w1 * f1 + w2 * el21 * s1;
+            v[1 + Y_EL0] += w1 * a0 * iota * G0[p];
+            v[1 + Y_EL20] += w2 * a0 * s0;
+            v[1 + Y_EL1] += w1 * a1 * iota * G1[p];
+            v[1 + Y_EL21] += w2 * a1 * s1;
+            const float u0 = a0 * iota * (w1 * el0 + 2.f * w2 * iota * el20 * G0[p]);
+            const float u1 = a1 * iota * (w1 * el1 + 2.f * w2 * iota * el21 * G1[p]);
+            v[1 + Y_MX] += u0 * GX0[p] + u1 * GX1[p];
+            v[1 + Y_MY] += u0 * GY0[p] + u1 * GY1[p];
+            v[1 + Y_EDEV] += u1 * DE[p];
+            v[1 + Y_GXX] += 0.5f * u1 * SXX[p];
+            v[1 + Y_GXY] += u1 * SXY[p];
+            v[1 + Y_GYY] += 0.5f * u1 * SYY[p];
+        }
+    }
+    __shared__ double tot[NV];
+    cta_sum<float, NV>(v, tot);
+    __syncthreads();
+    double* out = part + (size_t)blockIdx.x * NPART;
+    if (threadIdx.x == 0) out[PART_LL] = tot[0];
+    if constexpr (MODE >= MODE_GRAD) {
+        for (int j = threadIdx.x; j < NP; j += blockDim.x) {
+            const float el[2] = {sT2[H_EL0].x, sT2[H_EL1].x}, el2[2] = {sT2[H_EL20].x, sT2[H_EL21].x};
+            float dG[3][3];
+            for (int q = 0; q < 9; ++q) dG[q / 3][q % 3] = sT2[T_DG + q].x;
+            int y0, y1, y2;
+            float c0, c1, c2;
+            chain_column<float>(j, im.band, wcs_row<float>(im), el, el2, dG, &y0, &c0, &y1, &c1, &y2, &c2);
+            out[PART_TH + j] = (double)c0 * tot[1 + y0] + (double)c1 * tot[1 + y1] +
+                               (double)c2 * tot[1 + y2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // launchers
 
 // pixels per thread of the FP32 contrib / adjoint kernels: P.tune (autotuned per
@@ -567,6 +813,12 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) 
             CEL_CONTRIB32(2)
             CEL_CONTRIB32(4)
 #undef CEL_CONTRIB32
+            case 3:
+                k_contrib_x2<<<P.n_item, PX2_THREADS, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
+                                                               (float*)P.spE, (float*)P.spE2, P.single,
+                                                               P.pixels, P.sky_map, (float*)P.emap,
+                                                               (float*)P.vmap, P.item_ll);
+                break;
             default: return cudaErrorInvalidValue;
         }
     return cudaGetLastError();
@@ -606,6 +858,16 @@ cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStr
             case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st); break;
             case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st); break;
             case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st); break;
+            case 3:
+                if (mode == MODE_LL)
+                    k_adjoint_x2<MODE_LL><<<P.n_item, PX2_THREADS, 0, st>>>(
+                        P.items, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
+                        (const float*)P.vmap, P.item_part);
+                else
+                    k_adjoint_x2<MODE_GRAD><<<P.n_item, PX2_THREADS, 0, st>>>(
+                        P.items, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
+                        (const float*)P.vmap, P.item_part);
+                break;
             default: return cudaErrorInvalidValue;
         }
     }
