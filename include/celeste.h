@@ -215,11 +215,11 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
 /*
  * Autotuner: times the FP32 contrib and adjoint kernels of this problem with 1, 2 and 4
  * pixels per thread (CTAs of 256, 128, 64 threads over the same 256-pixel work items)
- * and with two pixels per thread in packed FP32x2 instructions (code 3),
+ * and with two or four pixels per thread in packed FP32x2 instructions (codes 3, 5),
  * reps launches each with CUDA events on the problem's stream, at theta (host), and keeps
  * the fastest for later FP32 calls.  The choice is returned (nullable outputs) and can be
- * stored by the caller and restored with celeste_set_tuning (codes 1, 2, 3, 4; 0 =
- * built-in default 2).
+ * stored by the caller and restored with celeste_set_tuning (codes 1, 2, 3, 4, 5;
+ * 0 = built-in default 2; anything else is CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
                                 int32_t* ppt_contrib, int32_t* ppt_adjoint);

@@ -494,6 +494,13 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
 
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * NP * (size_t)n_src))) return bail(st);
+    P.kl_grad = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
+    P.src_total = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
+    P.done = (int32_t*)p;
+    if (cudaMemset(P.done, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.status = (int32_t*)p;
     if (cudaMemset(P.status, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
@@ -652,11 +659,12 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     cudaEvent_t a, b;
     CEL_CUDA(cudaEventCreate(&a));
     CEL_CUDA(cudaEventCreate(&b));
-    const int cands[4] = {1, 2, 4, 3};   // 3: two pixels per thread in packed FP32x2
+    // 1, 2, 4 pixels per thread; 3, 5: two and four pixels per thread in packed FP32x2
+    const int cands[5] = {1, 2, 4, 3, 5};
     float best_c = 1e30f, best_a = 1e30f;
     int pick_c = 2, pick_a = 2;
     cudaError_t e = cudaSuccess;
-    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+    for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
         P.tune_contrib = P.tune_adjoint = cands[ci];
         // warm once, then time reps launches of each kernel
         e = launch_contrib(P, CELESTE_FP32_ACC64, st);
@@ -690,9 +698,10 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
 
 celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
-    auto okp = [](int v) { return v >= 0 && v <= 4; };
+    auto okp = [](int v) { return v >= 0 && v <= 5; };
     if (!okp(ppt_contrib) || !okp(ppt_adjoint))
-        return fail(CELESTE_ERR_ARG, "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 packed FP32x2 pairs");
+        return fail(CELESTE_ERR_ARG,
+                    "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 pixels)");
     pr->P.tune_contrib = ppt_contrib;
     pr->P.tune_adjoint = ppt_adjoint;
     return CELESTE_OK;

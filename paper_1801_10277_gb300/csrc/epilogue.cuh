@@ -56,103 +56,117 @@ __device__ __forceinline__ void chain_column(int j, int band, const R* A, const 
     }
 }
 
-// one CTA per source: the KL in warp 0 (kl_warp), the shape derivative in lane 32,
-// then per patch the item sums (lanes 0..12), the band's brightness moments (lanes
-// 32..35) and the image-frame shape Jacobian (lanes 40..48), and the chain rule with
-// one lane per parameter.  Transcendentals and the small per-source algebra run in the
-// path precision R; every sum is FP64.  (A lone FP64 lane costs a whole warp slot of
-// the narrow FP64 pipe, so no FP64 work is left to a single thread.)
-constexpr int FZ_THREADS = 64;
+// One CTA per source: FZ_SLICES slices of FZ_LANES column lanes (lanes 0..43 one
+// parameter each, 48 the ll column, 49 the ll of the singly covered pixels, 50 the
+// tiles) each sum every FZ_SLICES-th item of the source (items are contiguous per
+// source), so a source with hundreds of items is not one long chain of loads; the
+// slices are then added in slice order (FP64 throughout, fixed order).  The KL value
+// and gradient come from k_prep.  The total's share of the source (ll of its singly
+// covered pixels + a strided slice of the tile sums - its KL) goes to src_total; the
+// last CTA to finish adds the shares in index order and resets the counter.
+constexpr int FZ_LANES = 64;
+constexpr int FZ_SLICES = 8;
+constexpr int FZ_THREADS = FZ_LANES * FZ_SLICES;
 
-__device__ __forceinline__ float exr(float x) { return expf(x); }
-__device__ __forceinline__ double exr(double x) { return exp(x); }
-__device__ __forceinline__ void scr(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void scr(double x, double* s, double* c) { sincos(x, s, c); }
+// sum of a[i * stride] for i = i0, i0 + step, ... < i1; four independent accumulators
+// so the loads overlap; fixed order
+__device__ __forceinline__ double sum_strided4(const double* __restrict__ a, int i0, int i1, int step,
+                                               int stride = 1) {
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+    int i = i0;
+    for (; i + 3 * step < i1; i += 4 * step) {
+        q0 += a[(size_t)i * stride];
+        q1 += a[(size_t)(i + step) * stride];
+        q2 += a[(size_t)(i + 2 * step) * stride];
+        q3 += a[(size_t)(i + 3 * step) * stride];
+    }
+    for (; i < i1; i += step) q0 += a[(size_t)i * stride];
+    return (q0 + q1) + (q2 + q3);
+}
 
-// Called by every thread of a CTA of >= FZ_THREADS threads (it holds barriers); the
-// first 64 threads do the work.
-template <class R>
-__device__ __forceinline__ void finalize_source(int s, int mode, const double* __restrict__ theta,
+__device__ __forceinline__ void finalize_source(int s, int n_src, int mode,
                                                 const PatchGeo* __restrict__ geo,
                                                 const int32_t* __restrict__ patch_off,
-                                                const ImgMeta* __restrict__ img,
-                                                const ModelDev* __restrict__ md,
                                                 const double* __restrict__ part,
-                                                double* __restrict__ kl_out,
+                                                const double* __restrict__ item_ll,
+                                                const double* __restrict__ tile_ll, int n_tile,
+                                                const double* __restrict__ kl,
+                                                const double* __restrict__ kl_grad,
                                                 double* __restrict__ local_out,
                                                 double* __restrict__ grad_out,
-                                                int32_t* __restrict__ status) {
-    const int t = threadIdx.x;
-    __shared__ double th[NP], klg[NP];
-    __shared__ double klv;
-    __shared__ R thr[NP];
-    for (int i = t; i < NP; i += blockDim.x) {
-        const double v = theta[(size_t)NP * s + i];
-        th[i] = v;
-        thr[i] = (R)v;   // one conversion per parameter
-    }
-    if (status && t < NP) theta_domain_check(t, theta[(size_t)NP * s + t], status);
-    __syncthreads();
-    if (t < 32) {
-        const double v = kl_warp<R>(*md, th, klg);
-        if (t == 0) klv = v;
-    }
-    // item partials: the source's items are contiguous
+                                                double* __restrict__ src_total,
+                                                int32_t* __restrict__ done,
+                                                double* __restrict__ total_out) {
+    const int t = threadIdx.x, c = t % FZ_LANES, sl = t / FZ_LANES;
+    __shared__ double red[FZ_SLICES][FZ_LANES];
     const int pa = patch_off[s], pb = patch_off[s + 1];
-    double gacc = 0.0, lacc = 0.0;
+    double acc = 0.0;
     if (pb > pa) {
         const int i0 = geo[pa].item0;
         const PatchGeo gl = geo[pb - 1];
         const int i1 = gl.item0 + gl.nitem;
-        // four independent FP64 accumulators so the loads overlap; fixed order
-        const int col = (mode >= MODE_GRAD && t < NP) ? PART_TH + t : (t == 48 ? PART_LL : -1);
-        if (col >= 0) {
-            double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
-            int it = i0;
-            for (; it + 4 <= i1; it += 4) {
-                q0 += part[(size_t)it * NPART + col];
-                q1 += part[(size_t)(it + 1) * NPART + col];
-                q2 += part[(size_t)(it + 2) * NPART + col];
-                q3 += part[(size_t)(it + 3) * NPART + col];
-            }
-            for (; it < i1; ++it) q0 += part[(size_t)it * NPART + col];
-            const double sum = (q0 + q1) + (q2 + q3);
-            if (t == 48) lacc = sum;
-            else gacc = sum;
-        }
+        const int col = (mode >= MODE_GRAD && c < NP) ? PART_TH + c : (c == 48 ? PART_LL : -1);
+        if (col >= 0) acc = sum_strided4(part + col, i0 + sl, i1, FZ_SLICES, NPART);
+        else if (c == 49 && total_out && item_ll) acc = sum_strided4(item_ll, i0 + sl, i1, FZ_SLICES);
     }
-    __shared__ double lsum;
-    if (t == 48) lsum = lacc;
+    if (c == 50 && total_out) acc = sum_strided4(tile_ll, s + n_src * sl, n_tile, n_src * FZ_SLICES);
+    red[sl][c] = acc;
     __syncthreads();
-    if (t == 0) {
-        kl_out[s] = klv;
-        if (local_out) local_out[s] = lsum - klv;
+    if (sl == 0) {
+        double v = red[0][c];
+        for (int q = 1; q < FZ_SLICES; ++q) v += red[q][c];
+        red[0][c] = v;
     }
-    if (mode >= MODE_GRAD && grad_out && t < NP) grad_out[(size_t)NP * s + t] = gacc - klg[t];
-    __syncthreads();   // shared scratch is reused by the caller
+    __syncthreads();
+    const double klv = kl[s];
+    if (t == 0 && local_out) local_out[s] = red[0][48] - klv;
+    if (mode >= MODE_GRAD && grad_out && t < NP) grad_out[(size_t)NP * s + t] = red[0][t] - kl_grad[(size_t)NP * s + t];
+    if (!total_out) return;
+    __shared__ int last;
+    if (t == 0) {
+        src_total[s] = (red[0][49] + red[0][50]) - klv;
+        __threadfence();
+        last = atomicAdd(done, 1) == n_src - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int i = t; i < n_src; i += FZ_THREADS) v += __ldcg(src_total + i);
+    double* r = &red[0][0];   // FZ_THREADS doubles
+    r[t] = v;
+    __syncthreads();
+    for (int h = FZ_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) r[t] += r[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        *total_out = r[0];
+        *done = 0;
+    }
 }
 
 // total = sum of tile and item ll sums - sum of KL, fixed order; every thread of a CTA
-// of <= 512 threads calls it
+// of <= 512 threads calls it (used where k_finalize does not fold the total in)
 __device__ __forceinline__ void total_reduce(const double* __restrict__ tile_ll, int n_tile,
                                              const double* __restrict__ item_ll, int n_item,
                                              const double* __restrict__ kl, int n_src,
                                              double* __restrict__ out) {
     __shared__ double red[512];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n_tile; i += blockDim.x) s += tile_ll[i];
-    for (int i = threadIdx.x; i < n_item; i += blockDim.x) s += item_ll[i];
-    for (int i = threadIdx.x; i < n_src; i += blockDim.x) s -= kl[i];
-    red[threadIdx.x] = s;
+    const int t = threadIdx.x, nt = blockDim.x;
+    double s = sum_strided4(tile_ll, t, n_tile, nt);
+    s += sum_strided4(item_ll, t, n_item, nt);
+    s -= sum_strided4(kl, t, n_src, nt);
+    red[t] = s;
     __syncthreads();
-    int n = blockDim.x;
+    int n = nt;
     while (n > 1) {
         const int h = (n + 1) / 2;
-        if ((int)threadIdx.x < n - h) red[threadIdx.x] += red[threadIdx.x + h];
+        if (t < n - h) red[t] += red[t + h];
         __syncthreads();
         n = h;
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (t == 0) *out = red[0];
     __syncthreads();
 }
 

@@ -794,6 +794,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             Pb.spE2 = d_sv;
             Pb.item_part = d_part;
             Pb.kl = d_kl;
+            Pb.kl_grad = nullptr;   // k_finalize_hess and k_tr_accept take the KL themselves
             Pb.single = nullptr;    // batch buffers keep every E_s / Var_s
             Pb.item_ll = nullptr;
             Pb.status = nullptr;

@@ -180,6 +180,9 @@ struct DevProblem {
     double* item_part;
     double* tile_ll;
     double* kl;
+    double* kl_grad;         // [n_src][44] KL gradient, written by k_prep (nullable: no KL in prep)
+    double* src_total;       // [n_src] each source's share of the total ELBO (k_finalize)
+    int32_t* done;           // k_finalize completion counter, 0 between launches
     int32_t* status;
 };
 

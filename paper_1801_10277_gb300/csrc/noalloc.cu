@@ -49,7 +49,10 @@ constexpr size_t OFF_VMAP = OFF_EMAP + al(sizeof(double) * NA_MAX_PX);
 constexpr size_t OFF_PART = OFF_VMAP + al(sizeof(double) * NA_MAX_PX);
 constexpr size_t OFF_TILELL = OFF_PART + al(sizeof(double) * NPART * NA_MAX_ITEMS);
 constexpr size_t OFF_KL = OFF_TILELL + al(sizeof(double) * NA_MAX_TILES);
-constexpr size_t OFF_STATUS = OFF_KL + al(sizeof(double));
+constexpr size_t OFF_KLG = OFF_KL + al(sizeof(double));
+constexpr size_t OFF_SRCTOT = OFF_KLG + al(sizeof(double) * NP);
+constexpr size_t OFF_DONE = OFF_SRCTOT + al(sizeof(double));
+constexpr size_t OFF_STATUS = OFF_DONE + al(sizeof(int32_t));
 constexpr size_t NA_BYTES = OFF_STATUS + al(sizeof(int32_t));
 
 }  // namespace
@@ -92,6 +95,7 @@ __global__ void k_noalloc_setup(unsigned char* base, ImgMeta im, ModelDev md, in
         d_poff[0] = 0;
         d_poff[1] = 1;
         *(int32_t*)(base + OFF_STATUS) = 0;
+        *(int32_t*)(base + OFF_DONE) = 0;
     }
     for (int i = threadIdx.x; i < nitem; i += blockDim.x)
         d_items[i] = WorkItem{0, i * CHUNK, min(CHUNK, npx - i * CHUNK), 0};
@@ -245,6 +249,9 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
     P.item_part = (double*)(base + OFF_PART);
     P.tile_ll = (double*)(base + OFF_TILELL);
     P.kl = (double*)(base + OFF_KL);
+    P.kl_grad = (double*)(base + OFF_KLG);
+    P.src_total = (double*)(base + OFF_SRCTOT);
+    P.done = (int32_t*)(base + OFF_DONE);
     P.status = (int32_t*)(base + OFF_STATUS);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_prep(P, d_theta, precision, st);

@@ -24,7 +24,7 @@ namespace cel {
 namespace {
 
 constexpr double LOG2E = 1.4426950408889634073599246810019;
-constexpr double TWO_PI = 6.283185307179586476925286766559;
+
 
 // 2^x on the SFU in one instruction (flush-to-zero: results below 2^-126 become 0)
 __device__ __forceinline__ float ex2(float x) {
@@ -95,15 +95,34 @@ __device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_HDR = 8;   // lanes per patch header
 
+// The KL of source s (value, gradient; Section III priors) and the domain check of its
+// parameters, by warp PREP_KL_WARP of the source's block while the other warps build
+// the patch headers: the KL depends on theta alone, so it costs no step of its own.
+constexpr int PREP_KL_WARP = PREP_THREADS / 32 - 1;
+
+template <class R>
+__device__ __forceinline__ void prep_kl(int s, const double* th, const R* thr,
+                                        const ModelDev* __restrict__ md, double* __restrict__ kl_out,
+                                        double* __restrict__ klg_out, int32_t* __restrict__ status) {
+    __shared__ double kg[NP];
+    const int lane = threadIdx.x & 31;
+    if (status)
+        for (int i = lane; i < NP; i += 32) theta_domain_check(i, th[i], status);
+    const double v = kl_warp<R>(*md, th, thr, kg);
+    __syncwarp();
+    if (lane == 0) kl_out[s] = v;
+    for (int i = lane; i < NP; i += 32) klg_out[(size_t)NP * s + i] = kg[i];
+}
+
 template <class R>
 __global__ void __launch_bounds__(PREP_THREADS)
 k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
        const int32_t* __restrict__ patch_off, const ImgMeta* __restrict__ img,
-       const ModelDev* __restrict__ md, int n_src, int nprof, R* __restrict__ tbl) {
+       const ModelDev* __restrict__ md, int n_src, int nprof, R* __restrict__ tbl,
+       double* __restrict__ kl_out, double* __restrict__ klg_out, int32_t* __restrict__ status) {
     const int s = blockIdx.x;
     if (s >= n_src) return;
     const int p0 = patch_off[s], np = patch_off[s + 1] - p0;
-    if (np == 0) return;
     __shared__ double th[NP];
     __shared__ R thr[NP];
     __shared__ R gsh[PREP_THREADS / PREP_HDR][4];   // gxx gxy gyy e_dev per patch of a round
@@ -114,6 +133,11 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
         thr[t] = (R)v;   // the parameters converted once per source
     }
     __syncthreads();
+    const bool kl_here = klg_out && (t >> 5) == PREP_KL_WARP;
+    if (np == 0) {
+        if (kl_here) prep_kl<R>(s, th, thr, md, kl_out, klg_out, status);
+        return;
+    }
     const int per_k = 1 + nprof;
     // patches in rounds of PREP_THREADS / PREP_HDR
     for (int r0 = 0; r0 < np; r0 += PREP_THREADS / PREP_HDR) {
@@ -178,6 +202,10 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
                 T[H_IOTA] = (R)im.iota;
                 T[7] = (R)0;
             }
+        }
+        if (r0 == 0 && kl_here) {
+            __syncwarp();
+            prep_kl<R>(s, th, thr, md, kl_out, klg_out, status);
         }
         __syncthreads();
         // components of the patches of this round
@@ -557,69 +585,105 @@ __device__ __forceinline__ void load_table_x2(float2* sT2, const float* gT, int 
     __syncthreads();
 }
 
-constexpr int PX2_THREADS = CHUNK / 2;
+// two coefficient pairs in one 128-bit shared load (p at an even index of the table)
+__device__ __forceinline__ void ld2(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
 
-__global__ void __launch_bounds__(PX2_THREADS) k_contrib_x2(const WorkItem* __restrict__ items,
-                                                          const PatchGeo* __restrict__ geo,
-                                                          const ImgMeta* __restrict__ img, int nprof,
-                                                          const float* __restrict__ tbl,
-                                                          float* __restrict__ spE,
-                                                          float* __restrict__ spV,
-                                                          const uint8_t* __restrict__ single,
-                                                          const float* __restrict__ pixels,
-                                                          const float* __restrict__ sky_map,
-                                                          float* __restrict__ emap,
-                                                          float* __restrict__ vmap,
-                                                          double* __restrict__ item_ll) {
-    __shared__ float2 sT2[TBL_STRIDE];
+// NPAIR pixel pairs per thread (tuning code 3: one pair, code 5: two pairs)
+template <int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_x2(const WorkItem* __restrict__ items,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img, int nprof,
+                                                                  const float* __restrict__ tbl,
+                                                                  float* __restrict__ spE,
+                                                                  float* __restrict__ spV,
+                                                                  const uint8_t* __restrict__ single,
+                                                                  const float* __restrict__ pixels,
+                                                                  const float* __restrict__ sky_map,
+                                                                  float* __restrict__ emap,
+                                                                  float* __restrict__ vmap,
+                                                                  double* __restrict__ item_ll) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    constexpr int PPT = 2 * NPAIR;
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
     const int t = threadIdx.x;
-    int xs[2], ys[2];
-    bool ok[2];
+    int xs[PPT], ys[PPT];
+    bool ok[PPT];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int l = t + p * PX2_THREADS;
+    for (int p = 0; p < PPT; ++p) {
+        const int l = t + p * NT;
         ok[p] = l < it.n;
         const int q = it.q0 + (ok[p] ? l : 0);
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
     }
-    const float2 X = make_float2((float)xs[0], (float)xs[1]), Y = make_float2((float)ys[0], (float)ys[1]);
-    float2 g0 = f2(0.f), g1 = f2(0.f);
+    float2 X[NPAIR], Y[NPAIR], g0[NPAIR], g1[NPAIR];
+#pragma unroll
+    for (int r = 0; r < NPAIR; ++r) {
+        X[r] = make_float2((float)xs[2 * r], (float)xs[2 * r + 1]);
+        Y[r] = make_float2((float)ys[2 * r], (float)ys[2 * r + 1]);
+        g0[r] = g1[r] = f2(0.f);
+    }
     for (int k = 0; k < npsf; ++k) {
-        const float2 dx = __fadd2_rn(X, sT2[T_MEAN + 2 * k]);
-        const float2 dy = __fadd2_rn(Y, sT2[T_MEAN + 2 * k + 1]);
-        const float2 dxx = __fmul2_rn(dx, dx), dxy = __fmul2_rn(dx, dy), dyy = __fmul2_rn(dy, dy);
+        float2 nmx, nmy;
+        ld2(sT2 + T_MEAN + 2 * k, nmx, nmy);
+        float2 dxx[NPAIR], dxy[NPAIR], dyy[NPAIR];
+#pragma unroll
+        for (int r = 0; r < NPAIR; ++r) {
+            const float2 dx = __fadd2_rn(X[r], nmx), dy = __fadd2_rn(Y[r], nmy);
+            dxx[r] = __fmul2_rn(dx, dx);
+            dxy[r] = __fmul2_rn(dx, dy);
+            dyy[r] = __fmul2_rn(dy, dy);
+        }
         const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
-        float2 a = __ffma2_rn(S[2], dyy, S[3]);
-        a = __ffma2_rn(S[1], dxy, a);
-        a = __ffma2_rn(S[0], dxx, a);
-        g0 = __ffma2_rn(S[7], ex2x2(a), g0);
+        float2 s0, s1, s2, s3;
+        ld2(S, s0, s1);
+        ld2(S + 2, s2, s3);
+        const float2 s7 = S[7];
+#pragma unroll
+        for (int r = 0; r < NPAIR; ++r) {
+            float2 a = __ffma2_rn(s2, dyy[r], s3);
+            a = __ffma2_rn(s1, dxy[r], a);
+            a = __ffma2_rn(s0, dxx[r], a);
+            g0[r] = __ffma2_rn(s7, ex2x2(a), g0[r]);
+        }
         const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
         for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
-            float2 b = __ffma2_rn(G[2], dyy, G[3]);
-            b = __ffma2_rn(G[1], dxy, b);
-            b = __ffma2_rn(G[0], dxx, b);
-            g1 = __ffma2_rn(G[7], ex2x2(b), g1);
+            float2 c0, c1, c2, c3;
+            ld2(G, c0, c1);
+            ld2(G + 2, c2, c3);
+            const float2 c7 = G[7];
+#pragma unroll
+            for (int r = 0; r < NPAIR; ++r) {
+                float2 b = __ffma2_rn(c2, dyy[r], c3);
+                b = __ffma2_rn(c1, dxy[r], b);
+                b = __ffma2_rn(c0, dxx[r], b);
+                g1[r] = __ffma2_rn(c7, ex2x2(b), g1[r]);
+            }
         }
     }
     const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
     const float el0 = sT2[H_EL0].x, el1 = sT2[H_EL1].x;
     const float em0 = sT2[H_EL20].x / (el0 * el0) - 1.f, em1 = sT2[H_EL21].x / (el1 * el1) - 1.f;
     float ll[1] = {0.f};
-    const float gg0[2] = {g0.x, g0.y}, gg1[2] = {g1.x, g1.y};
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < PPT; ++p) {
         if (!ok[p]) continue;
-        const float f0 = iota * el0 * gg0[p], f1 = iota * el1 * gg1[p];
+        const int r = p >> 1;
+        const float G0 = (p & 1) ? g0[r].y : g0[r].x, G1 = (p & 1) ? g1[r].y : g1[r].x;
+        const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
         const float e = a0 * f0 + a1 * f1;
         const float v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
                         a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
-        const int q = it.q0 + t + p * PX2_THREADS;
+        const int q = it.q0 + t + p * NT;
         const int64_t sp = g.sp_off + q;
         if (single && single[sp]) {
             const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
@@ -641,17 +705,27 @@ __global__ void __launch_bounds__(PX2_THREADS) k_contrib_x2(const WorkItem* __re
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(PX2_THREADS) k_adjoint_x2(const WorkItem* __restrict__ items,
-                                                          const PatchGeo* __restrict__ geo,
-                                                          const ImgMeta* __restrict__ img, int nprof,
-                                                          const float* __restrict__ pixels,
-                                                          const float* __restrict__ tbl,
-                                                          const float* __restrict__ emap,
-                                                          const float* __restrict__ vmap,
-                                                          double* __restrict__ part) {
+template <int NPAIR>
+static void contrib_x2(const DevProblem& P, cudaStream_t st) {
+    k_contrib_x2<NPAIR><<<P.n_item, CHUNK / (2 * NPAIR), 0, st>>>(
+        P.items, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2, P.single, P.pixels,
+        P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll);
+}
+
+// NPAIR pixel pairs per thread, as in k_contrib_x2
+template <int MODE, int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkItem* __restrict__ items,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img, int nprof,
+                                                                  const float* __restrict__ pixels,
+                                                                  const float* __restrict__ tbl,
+                                                                  const float* __restrict__ emap,
+                                                                  const float* __restrict__ vmap,
+                                                                  double* __restrict__ part) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
-    __shared__ float2 sT2[TBL_STRIDE];
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    constexpr int PPT = 2 * NPAIR;
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
@@ -661,94 +735,128 @@ __global__ void __launch_bounds__(PX2_THREADS) k_adjoint_x2(const WorkItem* __re
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = 0.f;
     const int t = threadIdx.x;
-    int xs[2], ys[2];
-    bool ok[2];
-    float x[2], cE[2], cV[2];
+    // pixel p of this thread: t + p * NT; pair r holds pixels 2r, 2r + 1
+    int xs[PPT], ys[PPT];
+    bool ok[PPT];
+    float cE[PPT], cV[PPT];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const int l = t + p * PX2_THREADS;
+    for (int p = 0; p < PPT; ++p) {
+        const int l = t + p * NT;
         ok[p] = l < it.n;
         const int q = it.q0 + (ok[p] ? l : 0);
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
         const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
-        x[p] = pixels[m];
+        const float x = pixels[m];
         const float E = emap[m], V = vmap[m];
         const float iE = 1.f / E;
-        if (ok[p]) v[0] += x[p] * (lg(E) - 0.5f * V * iE * iE) - E;
-        cE[p] = x[p] * (iE + V * iE * iE * iE) - 1.f;
-        cV[p] = -0.5f * x[p] * iE * iE;
+        if (ok[p]) v[0] += x * (lg(E) - 0.5f * V * iE * iE) - E;
+        cE[p] = x * (iE + V * iE * iE * iE) - 1.f;
+        cV[p] = -0.5f * x * iE * iE;
     }
     if constexpr (MODE >= MODE_GRAD) {
-        const float2 X = make_float2((float)xs[0], (float)xs[1]), Y = make_float2((float)ys[0], (float)ys[1]);
-        float2 g0 = f2(0.f), gx0 = f2(0.f), gy0 = f2(0.f);
-        float2 g1 = f2(0.f), gx1 = f2(0.f), gy1 = f2(0.f), de1 = f2(0.f);
-        float2 sxx = f2(0.f), sxy = f2(0.f), syy = f2(0.f);
+        float2 X[NPAIR], Y[NPAIR];
+        float2 g0[NPAIR], gx0[NPAIR], gy0[NPAIR], g1[NPAIR], gx1[NPAIR], gy1[NPAIR], de1[NPAIR],
+            sxx[NPAIR], sxy[NPAIR], syy[NPAIR];
+#pragma unroll
+        for (int r = 0; r < NPAIR; ++r) {
+            X[r] = make_float2((float)xs[2 * r], (float)xs[2 * r + 1]);
+            Y[r] = make_float2((float)ys[2 * r], (float)ys[2 * r + 1]);
+            g0[r] = gx0[r] = gy0[r] = g1[r] = gx1[r] = gy1[r] = de1[r] = sxx[r] = sxy[r] = syy[r] = f2(0.f);
+        }
         for (int k = 0; k < npsf; ++k) {
-            const float2 dx = __fadd2_rn(X, sT2[T_MEAN + 2 * k]);
-            const float2 dy = __fadd2_rn(Y, sT2[T_MEAN + 2 * k + 1]);
-            const float2 dxx = __fmul2_rn(dx, dx), dxy = __fmul2_rn(dx, dy), dyy = __fmul2_rn(dy, dy);
+            float2 nmx, nmy;
+            ld2(sT2 + T_MEAN + 2 * k, nmx, nmy);
+            float2 dx[NPAIR], dy[NPAIR], dxx[NPAIR], dxy[NPAIR], dyy[NPAIR];
+#pragma unroll
+            for (int r = 0; r < NPAIR; ++r) {
+                dx[r] = __fadd2_rn(X[r], nmx);
+                dy[r] = __fadd2_rn(Y[r], nmy);
+                dxx[r] = __fmul2_rn(dx[r], dx[r]);
+                dxy[r] = __fmul2_rn(dx[r], dy[r]);
+                dyy[r] = __fmul2_rn(dy[r], dy[r]);
+            }
             {
                 const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
-                float2 a = __ffma2_rn(S[2], dyy, S[3]);
-                a = __ffma2_rn(S[1], dxy, a);
-                a = __ffma2_rn(S[0], dxx, a);
-                const float2 n = __fmul2_rn(S[7], ex2x2(a));
-                const float2 qx = __ffma2_rn(S[4], dx, __fmul2_rn(S[5], dy));
-                const float2 qy = __ffma2_rn(S[5], dx, __fmul2_rn(S[6], dy));
-                g0 = __fadd2_rn(g0, n);
-                gx0 = __ffma2_rn(n, qx, gx0);
-                gy0 = __ffma2_rn(n, qy, gy0);
+                float2 s0, s1, s2, s3, npxx, npxy, npyy, c;
+                ld2(S, s0, s1);
+                ld2(S + 2, s2, s3);
+                ld2(S + 4, npxx, npxy);
+                ld2(S + 6, npyy, c);
+#pragma unroll
+                for (int r = 0; r < NPAIR; ++r) {
+                    float2 a = __ffma2_rn(s2, dyy[r], s3);
+                    a = __ffma2_rn(s1, dxy[r], a);
+                    a = __ffma2_rn(s0, dxx[r], a);
+                    const float2 n = __fmul2_rn(c, ex2x2(a));
+                    const float2 qx = __ffma2_rn(npxx, dx[r], __fmul2_rn(npxy, dy[r]));   // -(Pd)_x
+                    const float2 qy = __ffma2_rn(npxy, dx[r], __fmul2_rn(npyy, dy[r]));   // -(Pd)_y
+                    g0[r] = __fadd2_rn(g0[r], n);
+                    gx0[r] = __ffma2_rn(n, qx, gx0[r]);
+                    gy0[r] = __ffma2_rn(n, qy, gy0[r]);
+                }
             }
             const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
             for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
-                float2 b = __ffma2_rn(G[2], dyy, G[3]);
-                b = __ffma2_rn(G[1], dxy, b);
-                b = __ffma2_rn(G[0], dxx, b);
-                const float2 e = ex2x2(b);
-                const float2 n = __fmul2_rn(G[7], e);
-                const float2 npxx = G[4], npxy = G[5], npyy = G[6];   // negated
-                const float2 qx = __ffma2_rn(npxx, dx, __fmul2_rn(npxy, dy));   // -(Pd)_x
-                const float2 qy = __ffma2_rn(npxy, dx, __fmul2_rn(npyy, dy));   // -(Pd)_y
-                g1 = __fadd2_rn(g1, n);
-                gx1 = __ffma2_rn(n, qx, gx1);
-                gy1 = __ffma2_rn(n, qy, gy1);
-                de1 = __ffma2_rn(G[8], e, de1);
-                const float2 nn = __fmul2_rn(n, G[9]);
-                sxx = __ffma2_rn(nn, __ffma2_rn(qx, qx, npxx), sxx);
-                sxy = __ffma2_rn(nn, __ffma2_rn(qx, qy, npxy), sxy);
-                syy = __ffma2_rn(nn, __ffma2_rn(qy, qy, npyy), syy);
+                float2 c0, c1, c2, c3, npxx, npxy, npyy, c, dc, nu;
+                ld2(G, c0, c1);
+                ld2(G + 2, c2, c3);
+                ld2(G + 4, npxx, npxy);
+                ld2(G + 6, npyy, c);
+                ld2(G + 8, dc, nu);
+#pragma unroll
+                for (int r = 0; r < NPAIR; ++r) {
+                    float2 b = __ffma2_rn(c2, dyy[r], c3);
+                    b = __ffma2_rn(c1, dxy[r], b);
+                    b = __ffma2_rn(c0, dxx[r], b);
+                    const float2 e = ex2x2(b);
+                    const float2 n = __fmul2_rn(c, e);
+                    const float2 qx = __ffma2_rn(npxx, dx[r], __fmul2_rn(npxy, dy[r]));
+                    const float2 qy = __ffma2_rn(npxy, dx[r], __fmul2_rn(npyy, dy[r]));
+                    g1[r] = __fadd2_rn(g1[r], n);
+                    gx1[r] = __ffma2_rn(n, qx, gx1[r]);
+                    gy1[r] = __ffma2_rn(n, qy, gy1[r]);
+                    de1[r] = __ffma2_rn(dc, e, de1[r]);
+                    const float2 nn = __fmul2_rn(n, nu);
+                    sxx[r] = __ffma2_rn(nn, __ffma2_rn(qx, qx, npxx), sxx[r]);
+                    sxy[r] = __ffma2_rn(nn, __ffma2_rn(qx, qy, npxy), sxy[r]);
+                    syy[r] = __ffma2_rn(nn, __ffma2_rn(qy, qy, npyy), syy[r]);
+                }
             }
         }
         const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
         const float el0 = sT2[H_EL0].x, el20 = sT2[H_EL20].x, el1 = sT2[H_EL1].x, el21 = sT2[H_EL21].x;
         const float i2 = iota * iota;
-        // gx, gy were accumulated with -(Pd): flip them here
-        const float G0[2] = {g0.x, g0.y}, GX0[2] = {-gx0.x, -gx0.y}, GY0[2] = {-gy0.x, -gy0.y};
-        const float G1[2] = {g1.x, g1.y}, GX1[2] = {-gx1.x, -gx1.y}, GY1[2] = {-gy1.x, -gy1.y};
-        const float DE[2] = {de1.x, de1.y}, SXX[2] = {sxx.x, sxx.y}, SXY[2] = {sxy.x, sxy.y},
-                    SYY[2] = {syy.x, syy.y};
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
+        for (int p = 0; p < PPT; ++p) {
             if (!ok[p]) continue;
-            const float f0 = iota * el0 * G0[p], f1 = iota * el1 * G1[p];
+            const int r = p >> 1;
+            const bool hi = p & 1;
+            // gx, gy were accumulated with -(Pd): flip them here
+            const float G0 = hi ? g0[r].y : g0[r].x, G1 = hi ? g1[r].y : g1[r].x;
+            const float GX0 = -(hi ? gx0[r].y : gx0[r].x), GY0 = -(hi ? gy0[r].y : gy0[r].x);
+            const float GX1 = -(hi ? gx1[r].y : gx1[r].x), GY1 = -(hi ? gy1[r].y : gy1[r].x);
+            const float DE = hi ? de1[r].y : de1[r].x;
+            const float SXX = hi ? sxx[r].y : sxx[r].x, SXY = hi ? sxy[r].y : sxy[r].x,
+                        SYY = hi ? syy[r].y : syy[r].x;
+            const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
             const float Es = a0 * f0 + a1 * f1;
             const float w1 = cE[p] - 2.f * cV[p] * Es, w2 = cV[p];
-            const float s0 = i2 * G0[p] * G0[p], s1 = i2 * G1[p] * G1[p];
+            const float s0 = i2 * G0 * G0, s1 = i2 * G1 * G1;
             v[1 + Y_A0] += w1 * f0 + w2 * el20 * s0;
             v[1 + Y_A1] += w1 * f1 + w2 * el21 * s1;
-            v[1 + Y_EL0] += w1 * a0 * iota * G0[p];
+            v[1 + Y_EL0] += w1 * a0 * iota * G0;
             v[1 + Y_EL20] += w2 * a0 * s0;
-            v[1 + Y_EL1] += w1 * a1 * iota * G1[p];
+            v[1 + Y_EL1] += w1 * a1 * iota * G1;
             v[1 + Y_EL21] += w2 * a1 * s1;
-            const float u0 = a0 * iota * (w1 * el0 + 2.f * w2 * iota * el20 * G0[p]);
-            const float u1 = a1 * iota * (w1 * el1 + 2.f * w2 * iota * el21 * G1[p]);
-            v[1 + Y_MX] += u0 * GX0[p] + u1 * GX1[p];
-            v[1 + Y_MY] += u0 * GY0[p] + u1 * GY1[p];
-            v[1 + Y_EDEV] += u1 * DE[p];
-            v[1 + Y_GXX] += 0.5f * u1 * SXX[p];
-            v[1 + Y_GXY] += u1 * SXY[p];
-            v[1 + Y_GYY] += 0.5f * u1 * SYY[p];
+            const float u0 = a0 * iota * (w1 * el0 + 2.f * w2 * iota * el20 * G0);
+            const float u1 = a1 * iota * (w1 * el1 + 2.f * w2 * iota * el21 * G1);
+            v[1 + Y_MX] += u0 * GX0 + u1 * GX1;
+            v[1 + Y_MY] += u0 * GY0 + u1 * GY1;
+            v[1 + Y_EDEV] += u1 * DE;
+            v[1 + Y_GXX] += 0.5f * u1 * SXX;
+            v[1 + Y_GXY] += u1 * SXY;
+            v[1 + Y_GYY] += 0.5f * u1 * SYY;
         }
     }
     __shared__ double tot[NV];
@@ -770,6 +878,19 @@ __global__ void __launch_bounds__(PX2_THREADS) k_adjoint_x2(const WorkItem* __re
     }
 }
 
+template <int NPAIR>
+static void adjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    if (mode == MODE_LL)
+        k_adjoint_x2<MODE_LL, NPAIR><<<P.n_item, NT, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
+                                                             P.tbl32, (const float*)P.emap,
+                                                             (const float*)P.vmap, P.item_part);
+    else
+        k_adjoint_x2<MODE_GRAD, NPAIR><<<P.n_item, NT, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
+                                                               P.tbl32, (const float*)P.emap,
+                                                               (const float*)P.vmap, P.item_part);
+}
+
 // ---------------------------------------------------------------------------------
 // launchers
 
@@ -780,15 +901,16 @@ static inline int ppt_adjoint(const DevProblem& P) { return P.tune_adjoint > 0 ?
 
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st) {
-    if (P.n_patch == 0) return cudaSuccess;
+    if (P.n_src == 0 || (P.n_patch == 0 && !P.kl_grad)) return cudaSuccess;
+    const int grid = P.n_src;
     if (precision == CELESTE_FP64)
-        k_prep<double><<<P.n_src, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                         P.n_src, P.nprof,
-                                                 P.tbl64);
+        k_prep<double><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
+                                                      P.n_src, P.nprof, P.tbl64, P.kl, P.kl_grad,
+                                                      P.status);
     else
-        k_prep<float><<<P.n_src, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                        P.n_src, P.nprof,
-                                                P.tbl32);
+        k_prep<float><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
+                                                     P.n_src, P.nprof, P.tbl32, P.kl, P.kl_grad,
+                                                     P.status);
     return cudaGetLastError();
 }
 
@@ -813,12 +935,8 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) 
             CEL_CONTRIB32(2)
             CEL_CONTRIB32(4)
 #undef CEL_CONTRIB32
-            case 3:
-                k_contrib_x2<<<P.n_item, PX2_THREADS, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl32,
-                                                               (float*)P.spE, (float*)P.spE2, P.single,
-                                                               P.pixels, P.sky_map, (float*)P.emap,
-                                                               (float*)P.vmap, P.item_ll);
-                break;
+            case 3: contrib_x2<1>(P, st); break;
+            case 5: contrib_x2<2>(P, st); break;
             default: return cudaErrorInvalidValue;
         }
     return cudaGetLastError();
@@ -858,16 +976,8 @@ cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStr
             case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st); break;
             case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st); break;
             case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st); break;
-            case 3:
-                if (mode == MODE_LL)
-                    k_adjoint_x2<MODE_LL><<<P.n_item, PX2_THREADS, 0, st>>>(
-                        P.items, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
-                        (const float*)P.vmap, P.item_part);
-                else
-                    k_adjoint_x2<MODE_GRAD><<<P.n_item, PX2_THREADS, 0, st>>>(
-                        P.items, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
-                        (const float*)P.vmap, P.item_part);
-                break;
+            case 3: adjoint_x2<1>(P, mode, st); break;
+            case 5: adjoint_x2<2>(P, mode, st); break;
             default: return cudaErrorInvalidValue;
         }
     }

@@ -1,7 +1,7 @@
-// Per-source kernels: KL terms (value, gradient) and the chain rule from the twelve
-// intermediate pixel variables y of each (source, patch) to the source's 44
-// constrained parameters (Section IV: 44 parameters per source; Section IV-D: the
-// block of one source).  FP64 throughout.
+// Per-source epilogue of the ELBO and gradient (Section IV: 44 parameters per source;
+// Section IV-D: the block of one source): item partials (already mapped to the 44
+// constrained parameters by k_adjoint) summed per source, the KL terms from k_prep
+// subtracted, and the total folded in by the last CTA.  FP64 sums.
 #include <math.h>
 
 #include "internal.cuh"
@@ -10,17 +10,17 @@
 
 namespace cel {
 
-template <class R>
 __global__ void __launch_bounds__(FZ_THREADS)
-k_finalize(int n_src, int mode, const double* __restrict__ theta,
-           const PatchGeo* __restrict__ geo, const int32_t* __restrict__ patch_off,
-           const ImgMeta* __restrict__ img, const ModelDev* __restrict__ md,
-           const double* __restrict__ part, double* __restrict__ kl_out,
+k_finalize(int n_src, int mode, const PatchGeo* __restrict__ geo,
+           const int32_t* __restrict__ patch_off, const double* __restrict__ part,
+           const double* __restrict__ item_ll, const double* __restrict__ tile_ll, int n_tile,
+           const double* __restrict__ kl, const double* __restrict__ kl_grad,
            double* __restrict__ local_out, double* __restrict__ grad_out,
-           int32_t* __restrict__ status) {
+           double* __restrict__ src_total, int32_t* __restrict__ done,
+           double* __restrict__ total_out) {
     if ((int)blockIdx.x >= n_src) return;
-    finalize_source<R>(blockIdx.x, mode, theta, geo, patch_off, img, md, part, kl_out, local_out,
-                       grad_out, status);
+    finalize_source(blockIdx.x, n_src, mode, geo, patch_off, part, item_ll, tile_ll, n_tile, kl,
+                    kl_grad, local_out, grad_out, src_total, done, total_out);
 }
 
 __global__ void k_total(const double* __restrict__ tile_ll, int n_tile,
@@ -39,16 +39,14 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int prec
         cudaError_t e = launch_finalize_hess(P, d_theta, d_local, d_grad, d_hess, st);
         if (e != cudaSuccess) return e;
     } else if (P.n_src > 0) {
-        if (precision == CELESTE_FP64)
-            k_finalize<double><<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo,
-                                                               P.patch_off, P.img, P.model,
-                                                               P.item_part, P.kl, d_local, d_grad,
-                                                               P.status);
-        else
-            k_finalize<float><<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, d_theta, P.geo,
-                                                              P.patch_off, P.img, P.model,
-                                                              P.item_part, P.kl, d_local, d_grad,
-                                                              P.status);
+        // the KL value and gradient come from k_prep of the same theta
+        (void)precision;
+        (void)d_theta;
+        k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, P.geo, P.patch_off, P.item_part,
+                                                   P.single ? P.item_ll : nullptr, P.tile_ll,
+                                                   P.n_tile, P.kl, P.kl_grad, d_local, d_grad,
+                                                   P.src_total, P.done, d_total);
+        return cudaGetLastError();
     }
     if (d_total)
         k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl,

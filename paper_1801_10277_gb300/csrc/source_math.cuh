@@ -108,11 +108,6 @@ __device__ inline void band_moments(const double* th, int band, int i, double& e
     el2 = exp(2.0 * m + 2.0 * v);
 }
 
-// The same KL and gradient computed by the 16 lanes 0..15 of one warp, lane = 8 i + d
-// (type i, colour-prior component d); every lane of the warp must call it.  The
-// logarithms and reciprocals are FP64, one per lane in a single round; the 4 x 4
-// per-component algebra runs in R; the sums over components and the outputs are FP64.  Writes the gradient (all 44 entries, zero for position and shape) into g
-// (shared) and returns the KL on every lane.
 __device__ inline const double* prior_P_of(const ModelDev& m, int i, int d, double) { return m.prior_P[i][d]; }
 __device__ inline const float* prior_P_of(const ModelDev& m, int i, int d, float) { return m.prior_P_f[i][d]; }
 __device__ inline const double* prior_mu_of(const ModelDev& m, int i, int d, double) { return m.prior_mu[i][d]; }
@@ -150,17 +145,24 @@ template <> __device__ __forceinline__ double logp<double>(double x) { return lo
 template <class R> __device__ __forceinline__ double rcpp(double x) { return rcp_fast(x); }
 template <> __device__ __forceinline__ double rcpp<double>(double x) { return 1.0 / x; }
 
+// The KL and its gradient (closed forms of kl_value_grad) computed by one warp; every
+// lane must call it.  th: the 44 parameters (FP64), thr: the same in R (shared).
+//   round 1 (FP64 range, one logarithm / reciprocal per lane): lanes 0..15 log(k_id /
+//     w_id), 16..23 log c2 and 1/c2, 24..25 log(a_i / Phi_i), 26..27 log(pv_i / r2_i) and
+//     1/r2_i;
+//   round 2 (lanes 0..15, lane = 8 i + d: type i, colour-prior component d): the 4 x 4
+//     algebra of component d in R, then sums over the eight components in R of
+//     k_d (log k_d/w_d + KL_d), k_d P_d (c1 - mu_d), k_d diag P_d and k_d;
+//   outputs: lanes 8 i + j (j < 4) the c1 / c2 entries of colour j, lanes 8 i + 4..6 the
+//     a, r1, r2 entries, in FP64 where a reciprocal can exceed FP32's range.
+// The c2 derivative is (sum_d k_d diag P_d - (sum_d k_d) / c2) / 2, the 1/c2 term taken
+// out of the component sum.  Writes all 44 entries of g (shared; zero for position and
+// shape) and returns the KL on every lane.
 template <class R>
-__device__ inline double kl_warp(const ModelDev& md, const double* th, double* g) {
+__device__ inline double kl_warp(const ModelDev& md, const double* th, const R* thr, double* g) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    // round 1, FP64 (responsibilities and variances can be far below FP32's range):
-    // one logarithm / reciprocal per lane
-    //   lanes 0..15 log(k_id / w_id); 16..23 log c2 and 1/c2; 24,25 log(a_i/Phi_i);
-    //   26,27 log(pv_i / r2_i) and 1/r2_i
     double lv = 0.0, rv = 0.0;
-    // the arguments: lanes 0..15 k/w (log), 16..23 c2 (log, rcp), 24..25 a/Phi (log),
-    // 26..27 r2 (log pv - log r2, rcp); divisions by the constants folded into logs
     if (lane < 16) {
         const int i = lane >> 3, d = lane & 7;
         lv = logp<R>(th[P_K + NCOMP * i + d]) - md.prior_logw[i][d];
@@ -177,66 +179,70 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, double* g
         rv = rcpp<R>(th[P_R2 + i]);
     }
     const int i = (lane >> 3) & 1, d = lane & 7;
-    double ic2[4], slog = 0.0;
-    for (int j = 0; j < 4; ++j) {
-        slog += __shfl_sync(full, lv, 16 + 4 * i + j);
-        ic2[j] = __shfl_sync(full, rv, 16 + 4 * i + j);
-    }
-    const double la = __shfl_sync(full, lv, 24 + i);
-    const double lpr = __shfl_sync(full, lv, 26 + i);
-    const double ir2 = __shfl_sync(full, rv, 26 + i);
-    // round 2: per-component terms (lanes 0..15); the 4 x 4 algebra in R
-    double term = 0.0, dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
+    // log det of q's colour covariance: sum of the four log c2 of type i
+    R slog = 0;
+    for (int j = 0; j < 4; ++j) slog += (R)__shfl_sync(full, lv, 16 + 4 * i + j);
+    // round 2
+    R term = 0, ks = 0, kP[4] = {0, 0, 0, 0}, kD[4] = {0, 0, 0, 0};
     if (lane < 16) {
-        const double k = th[P_K + NCOMP * i + d];
-        const double a = th[P_A + i];
+        const R k = thr[P_K + NCOMP * i + d];
         const R* Pm = prior_P_of(md, i, d, R());
         const R* mu = prior_mu_of(md, i, d, R());
         R diff[4], quad = 0, tr = 0;
-        for (int j = 0; j < 4; ++j) diff[j] = (R)th[P_C1 + 4 * i + j] - mu[j];
-        R Pd[4];
+        for (int j = 0; j < 4; ++j) diff[j] = thr[P_C1 + 4 * i + j] - mu[j];
         for (int j = 0; j < 4; ++j) {
-            R s = 0;
-            for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
-            Pd[j] = s;
-            quad += diff[j] * s;
-            tr += Pm[5 * j] * (R)th[P_C2 + 4 * i + j];
+            R sj = 0;
+            for (int l = 0; l < 4; ++l) sj += Pm[4 * j + l] * diff[l];
+            kP[j] = k * sj;
+            kD[j] = k * Pm[5 * j];
+            quad += diff[j] * sj;
+            tr += Pm[5 * j] * thr[P_C2 + 4 * i + j];
         }
-        const double klc = 0.5 * ((double)(tr + quad) - 4.0 + md.prior_logdet[i][d] - slog);
-        term = k * (lv + klc);
-        g[P_K + NCOMP * i + d] = a * (lv + 1.0 + klc);
-        for (int j = 0; j < 4; ++j) {
-            dc1[j] = k * (double)Pd[j];
-            dc2[j] = 0.5 * k * ((double)Pm[5 * j] - ic2[j]);
-        }
+        const R klc = (R)0.5 * (tr + quad - (R)4 + prior_ld_of(md, i, d, R()) - slog);
+        term = k * ((R)lv + klc);
+        ks = k;
+        g[P_K + NCOMP * i + d] = th[P_A + i] * (lv + 1.0 + (double)klc);
     }
-    // FP64 sums over the eight components of each type
     for (int o = 1; o < 8; o <<= 1) {
         term += __shfl_xor_sync(full, term, o);
+        ks += __shfl_xor_sync(full, ks, o);
         for (int j = 0; j < 4; ++j) {
-            dc1[j] += __shfl_xor_sync(full, dc1[j], o);
-            dc2[j] += __shfl_xor_sync(full, dc2[j], o);
+            kP[j] += __shfl_xor_sync(full, kP[j], o);
+            kD[j] += __shfl_xor_sync(full, kD[j], o);
         }
     }
+    // every lane of the group 8 i .. 8 i + 7 holds the type's sums
+    const double la = __shfl_sync(full, lv, 24 + i);
+    const double lpr = __shfl_sync(full, lv, 26 + i);
+    const double ir2 = __shfl_sync(full, rv, 26 + i);
+    const double icd = __shfl_sync(full, rv, 16 + 4 * i + (d & 3));   // 1 / c2 of colour d (d < 4)
     double klv = 0.0;
-    if (lane < 16 && d == 0) {
-        const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
-        const double pm = md.prior_r[i][0];
-        const double ipv = md.prior_inv_pv[i];
-        const double K = 0.5 * (lpr + (r2 + (r1 - pm) * (r1 - pm)) * ipv - 1.0) + term;
+    if (lane < 16) {
         const double ad = th[P_A + i];
-        klv = ad * (la + K);
-        g[P_A + i] = la + 1.0 + K;
-        g[P_R1 + i] = ad * (r1 - pm) * ipv;
-        g[P_R2 + i] = ad * 0.5 * (ipv - ir2);
-        for (int j = 0; j < 4; ++j) {
-            g[P_C1 + 4 * i + j] = ad * dc1[j];
-            g[P_C2 + 4 * i + j] = ad * dc2[j];
+        if (d < 4) {
+            R kp = kP[0], kd = kD[0];
+            for (int j = 1; j < 4; ++j)
+                if (j == d) { kp = kP[j]; kd = kD[j]; }
+            g[P_C1 + 4 * i + d] = (double)((R)ad * kp);
+            g[P_C2 + 4 * i + d] = 0.5 * ad * ((double)kd - icd * (double)ks);
+        } else {
+            const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
+            const double pm = md.prior_r[i][0];
+            const double ipv = md.prior_inv_pv[i];
+            if (d == 4) {
+                const double K = 0.5 * (lpr + (r2 + (r1 - pm) * (r1 - pm)) * ipv - 1.0) + (double)term;
+                klv = ad * (la + K);
+                g[P_A + i] = la + 1.0 + K;
+            } else if (d == 5) {
+                g[P_R1 + i] = ad * (r1 - pm) * ipv;
+            } else if (d == 6) {
+                g[P_R2 + i] = ad * 0.5 * (ipv - ir2);
+            }
         }
     }
     if (lane < 6) g[lane] = 0.0;   // position and shape carry no prior
     klv += __shfl_xor_sync(full, klv, 8);
-    return __shfl_sync(full, klv, 0);
+    return __shfl_sync(full, klv, 4);
 }
 
 // Domain of parameter j (celeste.h): every entry finite; e_dev in [0,1]; e_axis in

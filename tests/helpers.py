@@ -56,3 +56,12 @@ def problem(thetas, H=32, W=32, psfs=None, bands=(0, 1, 2, 3, 4), pixels=None, s
                          prior_r=prior_r, prior_c=prior_c, theta=thetas.copy(),
                          truth=thetas.copy(), patch_offsets=po, patches=pa, nbr_offsets=no,
                          nbrs=nb, name="test")
+
+
+def neighbour_closure(prob, sample):
+    """The sample and every neighbour of a sampled source (ascending ids): the
+    sub-problem on which the sampled sources' local objectives are exact."""
+    keep = set(int(s) for s in sample)
+    for s in sample:
+        keep.update(int(o) for o in prob.nbrs[prob.nbr_offsets[s]:prob.nbr_offsets[s + 1]])
+    return np.array(sorted(keep), np.int64)

@@ -596,3 +596,20 @@ def test_fit_recovers_truth_on_noiseless_image():
     f, g, h = o.derivs(th, hess=True)
     gt, _ = free_derivs(to_free(th[0]), g[0], h[0])
     assert np.abs(gt).max() < 1e-7 * abs(f[0])
+
+
+def test_oracle_matches_its_stored_values():
+    """Regression guard: the oracle reproduces the values make_oracle_golden.py stored
+    (to summation-order rounding), so a change of its arithmetic is deliberate."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tiny_two_source_oracle.json")
+    with open(path) as f:
+        ref = json.load(f)
+    prob = synth.config(0)
+    orc = Oracle(prob)
+    tot, loc = orc.elbo(prob.theta)
+    _, g, _ = orc.derivs(prob.theta)
+    assert abs(tot - ref["elbo_total"]) <= 1e-12 * abs(ref["elbo_total"])
+    assert np.allclose(loc, ref["elbo_local"], rtol=1e-12, atol=0)
+    assert np.allclose(g, ref["grad"], rtol=1e-10, atol=1e-10)
