@@ -129,6 +129,16 @@ void celeste_problem_destroy(celeste_problem* prob);
 int64_t celeste_source_pixels(const celeste_problem* prob);
 
 /*
+ * Work decomposition of a problem (host read, no GPU work), for cost accounting:
+ * out[0] sources, [1] patches, [2] work items (<= 256 pixels of one patch each),
+ * [3] items whose every pixel only their own patch covers (they take the fused FP32 map +
+ * adjoint pass), [4] source-pixels in those items, [5] 16 x 16 tiles covered by two or
+ * more patches (the gather's cells), [6] source-pixels in all.  Writes min(n, 7) entries;
+ * returns the number written, or CELESTE_ERR_ARG for a null problem / out.
+ */
+int32_t celeste_problem_stats(const celeste_problem* prob, int64_t* out, int32_t n);
+
+/*
  * ELBO (Eq. 1, the reading above) at theta[n_src][44] (host).
  *   elbo_total: sum over the union of patches of the expected log-likelihood minus the
  *     sum of KL terms.
@@ -215,10 +225,12 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
 /*
  * Autotuner: times the FP32 contrib and adjoint kernels of this problem with 1, 2 and 4
  * pixels per thread (CTAs of 256, 128, 64 threads over the same 256-pixel work items)
- * and with two or four pixels per thread in packed FP32x2 instructions (codes 3, 5),
+ * and with two or four pixels per thread in packed FP32x2 instructions (codes 3, 5;
+ * codes 6, 7: the same as persistent CTAs taking items from a work queue, with the
+ * next item's table prefetched by bulk asynchronous copy),
  * reps launches each with CUDA events on the problem's stream, at theta (host), and keeps
  * the fastest for later FP32 calls.  The choice is returned (nullable outputs) and can be
- * stored by the caller and restored with celeste_set_tuning (codes 1, 2, 3, 4, 5;
+ * stored by the caller and restored with celeste_set_tuning (codes 1 .. 7;
  * 0 = built-in default 2; anything else is CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,

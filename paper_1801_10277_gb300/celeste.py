@@ -56,6 +56,7 @@ class celeste_fit_options(C.Structure):
 _lib = None
 
 EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_pixels",
+           "celeste_problem_stats",
            "celeste_elbo", "celeste_elbo_grad", "celeste_hess", "celeste_fit_options_default",
            "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
@@ -88,6 +89,8 @@ def load(build_if_missing=False):
     L.celeste_problem_destroy.restype = None
     L.celeste_source_pixels.argtypes = [vp]
     L.celeste_source_pixels.restype = i64
+    L.celeste_problem_stats.argtypes = [vp, vp, C.c_int32]
+    L.celeste_problem_stats.restype = C.c_int32
     L.celeste_elbo.argtypes = [vp, vp, i32, vp, vp]
     L.celeste_elbo_grad.argtypes = [vp, vp, i32, vp, vp, vp]
     L.celeste_hess.argtypes = [vp, vp, i32, vp, vp, vp]
@@ -197,6 +200,18 @@ class Problem:
     @property
     def source_pixels(self):
         return int(self.L.celeste_source_pixels(self.h))
+
+    STAT_KEYS = ("sources", "patches", "items", "fused_items", "fused_source_pixels", "tiles",
+                 "source_pixels")
+
+    def stats(self):
+        """Work decomposition: {sources, patches, items, fused_items, fused_source_pixels,
+        tiles, source_pixels}."""
+        out = np.zeros(len(self.STAT_KEYS), np.int64)
+        n = self.L.celeste_problem_stats(self.h, _p(out), len(out))
+        if n < 0:
+            _check(n)
+        return {k: int(v) for k, v in zip(self.STAT_KEYS, out[:n])}
 
     def _theta(self, theta):
         th = np.ascontiguousarray(theta, np.float64)

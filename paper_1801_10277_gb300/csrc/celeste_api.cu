@@ -179,7 +179,33 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     CEL_CUDA(cudaSetDevice(pr->device));
     pr->last_stream = st;
     const DevProblem& P = pr->P;
+    // FP32 value / gradient: items whose pixels only their own patch covers take the fused
+    // map + adjoint pass on the side stream, concurrently with the critical path on st
+    // (map pass over the other items -> gather -> their adjoint -> per-source epilogue);
+    // the total (tile and item ll sums - KL) follows the gather on the side stream.  The
+    // two streams write disjoint pixels and items, so the results do not depend on how
+    // the kernels interleave.
+    const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.idx_single;
     CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
+    if (fused) {
+        cudaStream_t sd = pr->side;
+        CEL_CUDA(cudaEventRecord(pr->ev_fork, st));
+        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_fork, 0));
+        CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd); }));
+        CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st, P.idx_mixed, P.n_mixed); }));
+        CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
+        CEL_CUDA(cudaEventRecord(pr->ev_gather, st));
+        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_gather, 0));
+        if (d_total) CEL_CUDA(timed(pr, "total", sd, [&] { return launch_total(P, d_total, sd); }));
+        CEL_CUDA(cudaEventRecord(pr->ev_join, sd));
+        CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
+                       [&] { return launch_adjoint(P, precision, mode, st, P.idx_mixed, P.n_mixed); }));
+        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_join, 0));
+        CEL_CUDA(timed(pr, "finalize", st, [&] {
+            return launch_finalize(P, d_theta, precision, mode, nullptr, d_local, d_grad, d_hess, st);
+        }));
+        return CELESTE_OK;
+    }
     CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st); }));
     CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
     if (mode == MODE_HESS)
@@ -230,6 +256,15 @@ const char* celeste_last_error(void) { return g_err.c_str(); }
 
 int64_t celeste_source_pixels(const celeste_problem* pr) { return pr ? pr->P.n_sp : 0; }
 
+int32_t celeste_problem_stats(const celeste_problem* pr, int64_t* out, int32_t n) {
+    if (!pr || !out) return fail(CELESTE_ERR_ARG, "null problem or output");
+    const DevProblem& P = pr->P;
+    const int64_t v[7] = {P.n_src, P.n_patch, P.n_item, P.n_single, pr->sp_single, P.n_tile, P.n_sp};
+    const int m = n < 7 ? (n > 0 ? n : 0) : 7;
+    for (int i = 0; i < m; ++i) out[i] = v[i];
+    return m;
+}
+
 void celeste_problem_destroy(celeste_problem* pr) {
     if (!pr) return;
     cudaSetDevice(pr->device);
@@ -241,6 +276,9 @@ void celeste_problem_destroy(celeste_problem* pr) {
     }
     for (cudaEvent_t e : pr->pool) cudaEventDestroy(e);
     for (void* p : pr->owned) cudaFree(p);
+    if (pr->side) cudaStreamDestroy(pr->side);
+    for (cudaEvent_t e : {pr->ev_fork, pr->ev_gather, pr->ev_join})
+        if (e) cudaEventDestroy(e);
     if (pr->stream) cudaStreamDestroy(pr->stream);
     delete pr;
 }
@@ -380,6 +418,15 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                         c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx] == 1;
         }
     }
+    // items whose every pixel is singly covered take the fused map + adjoint pass
+    std::vector<int32_t> idx_single, idx_mixed;
+    for (int i = 0; i < (int)items.size(); ++i) {
+        const WorkItem& w = items[i];
+        const uint8_t* f = single.data() + geo[w.patch].sp_off + w.q0;
+        bool all = true;
+        for (int q = 0; q < w.n && all; ++q) all = f[q] != 0;
+        (all ? idx_single : idx_mixed).push_back(i);
+    }
     // tiles: per image a dense grid of TILE x TILE cells, each with its covering patches
     std::vector<Tile> tiles;
     std::vector<int32_t> tile_list;
@@ -429,6 +476,15 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     if (cudaGetDevice(&pr->device) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "no CUDA device"));
     if (cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(CELESTE_ERR_CUDA, "cudaStreamCreate failed"));
+    {
+        int least = 0, greatest = 0;   // numerically greatest = lowest priority
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&pr->side, cudaStreamNonBlocking, least) != cudaSuccess)
+            return bail(fail(CELESTE_ERR_CUDA, "cudaStreamCreate failed"));
+        for (cudaEvent_t* e : {&pr->ev_fork, &pr->ev_gather, &pr->ev_join})
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+                return bail(fail(CELESTE_ERR_CUDA, "cudaEventCreate failed"));
+    }
     pr->last_stream = pr->stream;
     pr->patch_off.assign(patch_offsets, patch_offsets + n_src + 1);
     pr->nbr_off.assign(nbr_offsets, nbr_offsets + n_src + 1);
@@ -471,6 +527,15 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     uint8_t* d_single;
     if ((st = dupload(pr, &d_single, single.data(), single.size()))) return bail(st);
     P.single = d_single;
+    int32_t *d_is = nullptr, *d_im = nullptr;
+    if ((st = dupload(pr, &d_is, idx_single.data(), idx_single.size()))) return bail(st);
+    if ((st = dupload(pr, &d_im, idx_mixed.data(), idx_mixed.size()))) return bail(st);
+    P.idx_single = d_is;
+    P.idx_mixed = d_im;
+    P.n_single = (int)idx_single.size();
+    P.n_mixed = (int)idx_mixed.size();
+    pr->sp_single = 0;
+    for (int32_t i : idx_single) pr->sp_single += items[i].n;
     if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
     if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
@@ -501,6 +566,10 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.done = (int32_t*)p;
     if (cudaMemset(P.done, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
+    if ((st = dalloc(pr, &p, 2 * sizeof(int32_t)))) return bail(st);
+    P.queue = (int32_t*)p;
+    prime_persistent_grids();
+    if (cudaMemset(P.queue, 0, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.status = (int32_t*)p;
     if (cudaMemset(P.status, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
@@ -635,8 +704,16 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     const DevProblem& P = pr->P;
     CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
     // the mixture tables and the E / Var maps of the preceding celeste_elbo_device call
-    // are reused; the mixture terms themselves are recomputed by the adjoint
-    CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
+    // are reused; the mixture terms themselves are recomputed by the adjoint.  In FP32 the
+    // same kernels as celeste_elbo_grad run (the fused pass over the singly covered items,
+    // whose maps it rewrites with the same values, and the adjoint over the others), so
+    // the gradient is bit-identical to the one-call gradient.
+    const bool fused = precision == CELESTE_FP32_ACC64 && P.idx_single;
+    if (fused) CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
+    CEL_CUDA(timed(pr, "adjoint", st, [&] {
+        return fused ? launch_adjoint(P, precision, MODE_GRAD, st, P.idx_mixed, P.n_mixed)
+                     : launch_adjoint(P, precision, MODE_GRAD, st);
+    }));
     CEL_CUDA(timed(pr, "finalize", st, [&] {
         return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
                                nullptr, st);
@@ -659,27 +736,38 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     cudaEvent_t a, b;
     CEL_CUDA(cudaEventCreate(&a));
     CEL_CUDA(cudaEventCreate(&b));
-    // 1, 2, 4 pixels per thread; 3, 5: two and four pixels per thread in packed FP32x2
-    const int cands[5] = {1, 2, 4, 3, 5};
+    // 1, 2, 4 pixels per thread; 3, 5: two and four pixels per thread in packed FP32x2;
+    // 6, 7: the packed kernels as persistent CTAs on a work queue
+    const int cands[7] = {1, 2, 4, 3, 5, 6, 7};
     float best_c = 1e30f, best_a = 1e30f;
     int pick_c = 2, pick_a = 2;
     cudaError_t e = cudaSuccess;
-    for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
+    // with the fused pass (FP32 value + gradient) contrib runs over the mixed items and
+    // the adjoint stage is the fused kernel plus the adjoint over the mixed items
+    const bool fused = P.idx_single != nullptr;
+    const int32_t* rest = fused ? P.idx_mixed : nullptr;
+    const int n_rest = fused ? P.n_mixed : -1;
+    auto adjoint_stage = [&]() {
+        cudaError_t r = fused ? launch_fused(P, MODE_GRAD, st) : cudaSuccess;
+        if (r == cudaSuccess) r = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st, rest, n_rest);
+        return r;
+    };
+    for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
         P.tune_contrib = P.tune_adjoint = cands[ci];
-        // warm once, then time reps launches of each kernel
-        e = launch_contrib(P, CELESTE_FP32_ACC64, st);
+        // warm once, then time reps launches of each stage
+        if (fused) e = launch_fused(P, MODE_GRAD, st);
+        if (e == cudaSuccess) e = launch_contrib(P, CELESTE_FP32_ACC64, st, rest, n_rest);
         if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
-        if (e == cudaSuccess) e = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
+        if (e == cudaSuccess) e = adjoint_stage();
         float tc = 0.f, ta = 0.f;
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_contrib(P, CELESTE_FP32_ACC64, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_contrib(P, CELESTE_FP32_ACC64, st, rest, n_rest);
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&tc, a, b);
         if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = adjoint_stage();
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ta, a, b);
@@ -698,10 +786,11 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
 
 celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
-    auto okp = [](int v) { return v >= 0 && v <= 5; };
+    auto okp = [](int v) { return v >= 0 && v <= 7; };
     if (!okp(ppt_contrib) || !okp(ppt_adjoint))
         return fail(CELESTE_ERR_ARG,
-                    "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 pixels)");
+                    "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 "
+                    "pixels), 6 / 7 the same as persistent CTAs on a work queue");
     pr->P.tune_contrib = ppt_contrib;
     pr->P.tune_adjoint = ppt_adjoint;
     return CELESTE_OK;

@@ -183,6 +183,11 @@ struct DevProblem {
     double* kl_grad;         // [n_src][44] KL gradient, written by k_prep (nullable: no KL in prep)
     double* src_total;       // [n_src] each source's share of the total ELBO (k_finalize)
     int32_t* done;           // k_finalize completion counter, 0 between launches
+    const int32_t* idx_single;   // items whose every pixel only their own patch covers (nullable)
+    const int32_t* idx_mixed;    // the other items
+    int n_single, n_mixed;
+    int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
+                             // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;
 };
 
@@ -194,11 +199,19 @@ celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const 
                                 celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t,
                                                           double*, double*));
 
+void prime_persistent_grids();
+// total = tile ll sums + item ll sums - KL (after the gather and every item ll)
+cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st);
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
                         cudaStream_t st);
-cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st);
+// contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
+cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
+                           const int32_t* idx = nullptr, int n = -1);
+// FP32 map pass + adjoint in one kernel over P.idx_single (mode MODE_LL or MODE_GRAD)
+cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st);
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
+                           const int32_t* idx = nullptr, int n = -1);
 cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,

@@ -16,7 +16,11 @@
 // sum across warps in FP64.  R = double: FP64 throughout.
 #include <math.h>
 
+#include <map>
+#include <mutex>
+
 #include "internal.cuh"
+#include "async_copy.cuh"
 #include "epilogue.cuh"
 
 namespace cel {
@@ -276,6 +280,7 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
 
 template <class R, int PPT>
 __global__ void __launch_bounds__(CHUNK / PPT) k_contrib(const WorkItem* __restrict__ items,
+                                                         const int32_t* __restrict__ idx,
                                                          const PatchGeo* __restrict__ geo,
                                                          const ImgMeta* __restrict__ img, int nprof,
                                                          const R* __restrict__ tbl, R* __restrict__ spE,
@@ -286,7 +291,8 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_contrib(const WorkItem* __restr
                                                          R* __restrict__ emap, R* __restrict__ vmap,
                                                          double* __restrict__ item_ll) {
     __shared__ R sT[TBL_STRIDE];
-    const WorkItem it = items[blockIdx.x];
+    const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+    const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_contrib(const WorkItem* __restr
     if (single) {
         double tot[1];
         cta_sum<R, 1>(ll, tot);
-        if (threadIdx.x == 0) item_ll[blockIdx.x] = tot[0];
+        if (threadIdx.x == 0) item_ll[item] = tot[0];
     }
 }
 
@@ -421,6 +427,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
 
 template <class R, int MODE, int PPT>
 __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restrict__ items,
+                                                         const int32_t* __restrict__ idx,
                                                          const PatchGeo* __restrict__ geo,
                                                          const ImgMeta* __restrict__ img, int nprof,
                                                          const float* __restrict__ pixels,
@@ -430,7 +437,8 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
                                                          double* __restrict__ part) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     __shared__ R sT[TBL_STRIDE];
-    const WorkItem it = items[blockIdx.x];
+    const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+    const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
     __shared__ double tot[NV];
     cta_sum<R, NV>(v, tot);
     __syncthreads();
-    double* out = part + (size_t)blockIdx.x * NPART;
+    double* out = part + (size_t)item * NPART;
     if (threadIdx.x == 0) out[PART_LL] = tot[0];
     if constexpr (MODE >= MODE_GRAD) {
         // chain rule of this item's y-gradient: d/dtheta_j = sum_y dy/dtheta_j d/dy
@@ -592,28 +600,21 @@ __device__ __forceinline__ void ld2(const float2* p, float2& a, float2& b) {
     b = make_float2(v.z, v.w);
 }
 
-// NPAIR pixel pairs per thread (tuning code 3: one pair, code 5: two pairs)
+// Work of one item on a staged table, NPAIR pixel pairs per thread (CHUNK / (2 NPAIR)
+// threads; every thread of the CTA calls it, it holds barriers).
+
 template <int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_x2(const WorkItem* __restrict__ items,
-                                                                  const PatchGeo* __restrict__ geo,
-                                                                  const ImgMeta* __restrict__ img, int nprof,
-                                                                  const float* __restrict__ tbl,
-                                                                  float* __restrict__ spE,
-                                                                  float* __restrict__ spV,
-                                                                  const uint8_t* __restrict__ single,
-                                                                  const float* __restrict__ pixels,
-                                                                  const float* __restrict__ sky_map,
-                                                                  float* __restrict__ emap,
-                                                                  float* __restrict__ vmap,
-                                                                  double* __restrict__ item_ll) {
+__device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, const PatchGeo& g,
+                                                const ImgMeta& im, int nprof, const float2* sT2,
+                                                float* __restrict__ spE, float* __restrict__ spV,
+                                                const uint8_t* __restrict__ single,
+                                                const float* __restrict__ pixels,
+                                                const float* __restrict__ sky_map,
+                                                float* __restrict__ emap, float* __restrict__ vmap,
+                                                double* __restrict__ item_ll) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
-    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    const WorkItem it = items[blockIdx.x];
-    const PatchGeo g = geo[it.patch];
-    const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
-    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
     const int t = threadIdx.x;
     int xs[PPT], ys[PPT];
     bool ok[PPT];
@@ -701,36 +702,31 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_x2(const WorkIt
     if (single) {
         double tot[1];
         cta_sum<float, 1>(ll, tot);
-        if (threadIdx.x == 0) item_ll[blockIdx.x] = tot[0];
+        if (threadIdx.x == 0) item_ll[item] = tot[0];
     }
 }
 
-template <int NPAIR>
-static void contrib_x2(const DevProblem& P, cudaStream_t st) {
-    k_contrib_x2<NPAIR><<<P.n_item, CHUNK / (2 * NPAIR), 0, st>>>(
-        P.items, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2, P.single, P.pixels,
-        P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll);
-}
-
-// NPAIR pixel pairs per thread, as in k_contrib_x2
-template <int MODE, int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkItem* __restrict__ items,
-                                                                  const PatchGeo* __restrict__ geo,
-                                                                  const ImgMeta* __restrict__ img, int nprof,
-                                                                  const float* __restrict__ pixels,
-                                                                  const float* __restrict__ tbl,
-                                                                  const float* __restrict__ emap,
-                                                                  const float* __restrict__ vmap,
-                                                                  double* __restrict__ part) {
+// FUSED: an item whose every pixel only its own patch covers.  E = sky + E_s and
+// Var = Var_s are then known from the item's own mixture sums, so the map pass and the
+// adjoint pass become one: the mixture is evaluated once, E and Var are formed after
+// the component loop (and written to the maps, which a later backward-only call reads),
+// and the item's ll goes to item_ll as well as to its partials.  Otherwise E and Var
+// come from the maps k_contrib / k_gather wrote.
+template <int MODE, int NPAIR, bool FUSED = false>
+__device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, const PatchGeo& g,
+                                                const ImgMeta& im, int nprof, const float2* sT2,
+                                                const float* __restrict__ pixels,
+                                                const float* __restrict__ emap,
+                                                const float* __restrict__ vmap,
+                                                double* __restrict__ part,
+                                                const float* __restrict__ sky_map = nullptr,
+                                                float* __restrict__ emap_out = nullptr,
+                                                float* __restrict__ vmap_out = nullptr,
+                                                double* __restrict__ item_ll = nullptr) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
-    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    const WorkItem it = items[blockIdx.x];
-    const PatchGeo g = geo[it.patch];
-    const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
-    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
     float v[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = 0.f;
@@ -738,7 +734,8 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
     // pixel p of this thread: t + p * NT; pair r holds pixels 2r, 2r + 1
     int xs[PPT], ys[PPT];
     bool ok[PPT];
-    float cE[PPT], cV[PPT];
+    float cE[PPT], cV[PPT], xv[PPT], sky[PPT];
+    int64_t mm[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
@@ -748,11 +745,83 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
         xs[p] = q - ys[p] * g.w;
         const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
         const float x = pixels[m];
-        const float E = emap[m], V = vmap[m];
-        const float iE = 1.f / E;
-        if (ok[p]) v[0] += x * (lg(E) - 0.5f * V * iE * iE) - E;
-        cE[p] = x * (iE + V * iE * iE * iE) - 1.f;
-        cV[p] = -0.5f * x * iE * iE;
+        if constexpr (FUSED) {
+            mm[p] = m;
+            xv[p] = x;
+            sky[p] = im.has_sky_map ? sky_map[m] : (float)im.sky;
+        } else {
+            const float E = emap[m], V = vmap[m];
+            const float iE = 1.f / E;
+            if (ok[p]) v[0] += x * (lg(E) - 0.5f * V * iE * iE) - E;
+            cE[p] = x * (iE + V * iE * iE * iE) - 1.f;
+            cV[p] = -0.5f * x * iE * iE;
+        }
+    }
+    if constexpr (FUSED && MODE == MODE_LL) {
+        // value only: the mixture sums, then E, Var and ll per pixel
+        float2 X[NPAIR], Y[NPAIR], g0[NPAIR], g1[NPAIR];
+#pragma unroll
+        for (int r = 0; r < NPAIR; ++r) {
+            X[r] = make_float2((float)xs[2 * r], (float)xs[2 * r + 1]);
+            Y[r] = make_float2((float)ys[2 * r], (float)ys[2 * r + 1]);
+            g0[r] = g1[r] = f2(0.f);
+        }
+        for (int k = 0; k < npsf; ++k) {
+            float2 nmx, nmy;
+            ld2(sT2 + T_MEAN + 2 * k, nmx, nmy);
+            float2 dxx[NPAIR], dxy[NPAIR], dyy[NPAIR];
+#pragma unroll
+            for (int r = 0; r < NPAIR; ++r) {
+                const float2 dx = __fadd2_rn(X[r], nmx), dy = __fadd2_rn(Y[r], nmy);
+                dxx[r] = __fmul2_rn(dx, dx);
+                dxy[r] = __fmul2_rn(dx, dy);
+                dyy[r] = __fmul2_rn(dy, dy);
+            }
+            const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
+            float2 s0, s1, s2, s3;
+            ld2(S, s0, s1);
+            ld2(S + 2, s2, s3);
+            const float2 s7 = S[7];
+#pragma unroll
+            for (int r = 0; r < NPAIR; ++r) {   // the gradient pass's rounding: n = c e, g += n
+                float2 a = __ffma2_rn(s2, dyy[r], s3);
+                a = __ffma2_rn(s1, dxy[r], a);
+                a = __ffma2_rn(s0, dxx[r], a);
+                g0[r] = __fadd2_rn(g0[r], __fmul2_rn(s7, ex2x2(a)));
+            }
+            const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
+            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
+                float2 c0, c1, c2, c3;
+                ld2(G, c0, c1);
+                ld2(G + 2, c2, c3);
+                const float2 c7 = G[7];
+#pragma unroll
+                for (int r = 0; r < NPAIR; ++r) {
+                    float2 b = __ffma2_rn(c2, dyy[r], c3);
+                    b = __ffma2_rn(c1, dxy[r], b);
+                    b = __ffma2_rn(c0, dxx[r], b);
+                    g1[r] = __fadd2_rn(g1[r], __fmul2_rn(c7, ex2x2(b)));
+                }
+            }
+        }
+        const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
+        const float el0 = sT2[H_EL0].x, el1 = sT2[H_EL1].x;
+        const float em0 = sT2[H_EL20].x / (el0 * el0) - 1.f, em1 = sT2[H_EL21].x / (el1 * el1) - 1.f;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (!ok[p]) continue;
+            const int r = p >> 1;
+            const float G0 = (p & 1) ? g0[r].y : g0[r].x, G1 = (p & 1) ? g1[r].y : g1[r].x;
+            const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
+            const float e = a0 * f0 + a1 * f1;
+            const float V = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
+                            a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
+            const float E = sky[p] + e;
+            const float iE = 1.f / E;
+            v[0] += xv[p] * (lg(E) - 0.5f * V * iE * iE) - E;
+            emap_out[mm[p]] = E;
+            vmap_out[mm[p]] = V;
+        }
     }
     if constexpr (MODE >= MODE_GRAD) {
         float2 X[NPAIR], Y[NPAIR];
@@ -841,6 +910,19 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
                         SYY = hi ? syy[r].y : syy[r].x;
             const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
             const float Es = a0 * f0 + a1 * f1;
+            if constexpr (FUSED) {
+                // this pixel's E and Var are the item's own: form them, the ll and its weights
+                const float em0 = el20 / (el0 * el0) - 1.f, em1 = el21 / (el1 * el1) - 1.f;
+                const float V = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
+                                a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
+                const float E = sky[p] + Es;
+                const float iE = 1.f / E;
+                v[0] += xv[p] * (lg(E) - 0.5f * V * iE * iE) - E;
+                cE[p] = xv[p] * (iE + V * iE * iE * iE) - 1.f;
+                cV[p] = -0.5f * xv[p] * iE * iE;
+                emap_out[mm[p]] = E;
+                vmap_out[mm[p]] = V;
+            }
             const float w1 = cE[p] - 2.f * cV[p] * Es, w2 = cV[p];
             const float s0 = i2 * G0 * G0, s1 = i2 * G1 * G1;
             v[1 + Y_A0] += w1 * f0 + w2 * el20 * s0;
@@ -862,8 +944,11 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
     __shared__ double tot[NV];
     cta_sum<float, NV>(v, tot);
     __syncthreads();
-    double* out = part + (size_t)blockIdx.x * NPART;
-    if (threadIdx.x == 0) out[PART_LL] = tot[0];
+    double* out = part + (size_t)item * NPART;
+    if (threadIdx.x == 0) {
+        out[PART_LL] = tot[0];
+        if constexpr (FUSED) item_ll[item] = tot[0];
+    }
     if constexpr (MODE >= MODE_GRAD) {
         for (int j = threadIdx.x; j < NP; j += blockDim.x) {
             const float el[2] = {sT2[H_EL0].x, sT2[H_EL1].x}, el2[2] = {sT2[H_EL20].x, sT2[H_EL21].x};
@@ -878,17 +963,345 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
     }
 }
 
+// ---- one CTA per item (tuning codes 3, 5): the table staged with plain loads
+
 template <int NPAIR>
-static void adjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_x2(const WorkItem* __restrict__ items,
+                                                                  const int32_t* __restrict__ idx,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img, int nprof,
+                                                                  const float* __restrict__ tbl,
+                                                                  float* __restrict__ spE,
+                                                                  float* __restrict__ spV,
+                                                                  const uint8_t* __restrict__ single,
+                                                                  const float* __restrict__ pixels,
+                                                                  const float* __restrict__ sky_map,
+                                                                  float* __restrict__ emap,
+                                                                  float* __restrict__ vmap,
+                                                                  double* __restrict__ item_ll) {
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+    const WorkItem it = items[item];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
+    contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, single, pixels, sky_map, emap,
+                           vmap, item_ll);
+}
+
+template <int MODE, int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkItem* __restrict__ items,
+                                                                  const int32_t* __restrict__ idx,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img, int nprof,
+                                                                  const float* __restrict__ pixels,
+                                                                  const float* __restrict__ tbl,
+                                                                  const float* __restrict__ emap,
+                                                                  const float* __restrict__ vmap,
+                                                                  double* __restrict__ part) {
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
+    const WorkItem it = items[item];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
+    adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part);
+}
+
+// map pass + adjoint in one, for the items listed in idx (every pixel singly covered)
+template <int MODE, int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_fused_x2(const WorkItem* __restrict__ items,
+                                                                const int32_t* __restrict__ idx,
+                                                                const PatchGeo* __restrict__ geo,
+                                                                const ImgMeta* __restrict__ img, int nprof,
+                                                                const float* __restrict__ pixels,
+                                                                const float* __restrict__ sky_map,
+                                                                const float* __restrict__ tbl,
+                                                                float* __restrict__ emap,
+                                                                float* __restrict__ vmap,
+                                                                double* __restrict__ part,
+                                                                double* __restrict__ item_ll) {
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    const int item = idx[blockIdx.x];
+    const WorkItem it = items[item];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
+    adjoint_x2_item<MODE, NPAIR, true>(item, it, g, im, nprof, sT2, pixels, nullptr, nullptr, part,
+                                       sky_map, emap, vmap, item_ll);
+}
+
+// ---- persistent CTAs with a work queue (tuning codes 6, 7)
+//
+// A grid of (resident CTAs per SM) x (SMs) CTAs takes items from a global counter.
+// Thread 0 runs the queue ahead of the CTA so that no global latency sits on an item's
+// critical path: the queue slot of item i + 2 is taken during item i - 1... i, its
+// WorkItem is loaded during item i, and at the top of item i + 1's predecessor the
+// bulk asynchronous copy of its mixture table is issued (landing in shared memory and
+// completing an mbarrier while the current item is computed) together with the load of
+// its PatchGeo.  The raw table is double-buffered; each CTA expands it into the
+// duplicated / negated FP32x2 layout before use.  The last CTA to finish resets the
+// counters for the next launch.
+
+struct PersistentQueue {
+    int32_t* queue;    // [0] next item, [1] finished CTAs
+    int32_t* status;   // CELESTE_ERR_TIMEOUT when a bounded wait gives up (nullable)
+};
+
+// queue slot q -> item index (through the optional list)
+__device__ __forceinline__ int queue_item(const int32_t* __restrict__ idx, int q) { return idx ? idx[q] : q; }
+
+template <class Body>
+__device__ __forceinline__ void run_items_persistent(const WorkItem* __restrict__ items,
+                                                     const int32_t* __restrict__ idx,
+                                                     const PatchGeo* __restrict__ geo,
+                                                     const ImgMeta* __restrict__ img, int n_item,
+                                                     const float* __restrict__ tbl, int tbl_floats,
+                                                     PersistentQueue Q, Body& body) {
+    __shared__ __align__(16) float raw[2][TBL_STRIDE];
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_item[2];
+    __shared__ WorkItem s_it[2];
+    __shared__ PatchGeo s_g[2];
+    const int t = threadIdx.x;
+    const unsigned bytes = (unsigned)tbl_floats * 4u;
+    // thread 0's look-ahead: n1 / w1 = the item after the current one and its WorkItem,
+    // n2 = the one after that (queue slot taken), g_next = the PatchGeo of the item whose
+    // table was issued last (stored to shared memory at the top of the next item)
+    int n1 = 0, n2 = 0;
+    WorkItem w1{};
+    PatchGeo g_next{};
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        fence_proxy_async_smem();
+        const int n0 = atomicAdd(Q.queue, 1);
+        s_item[0] = n0;
+        if (n0 < n_item) {
+            const WorkItem w0 = items[queue_item(idx, n0)];
+            s_it[0] = w0;
+            s_g[0] = geo[w0.patch];
+            bulk_copy_g2s(raw[0], tbl + (size_t)w0.patch * TBL_STRIDE, bytes, &bar[0]);
+        }
+        n1 = atomicAdd(Q.queue, 1);
+        if (n1 < n_item) w1 = items[queue_item(idx, n1)];
+        n2 = atomicAdd(Q.queue, 1);
+    }
+    __syncthreads();
+    unsigned parity[2] = {0u, 0u};
+    int b = 0;
+    bool failed = false, first = true;
+    for (;;) {
+        if (t == 0) {
+            if (!first) s_g[b] = g_next;
+            first = false;
+        }
+        const int cur = s_item[b];
+        if (cur >= n_item) break;
+        if (t == 0) {
+            s_item[b ^ 1] = n1;
+            if (n1 < n_item) {
+                s_it[b ^ 1] = w1;
+                g_next = geo[w1.patch];
+                fence_proxy_async_smem();   // raw[b ^ 1] was last read by the generic proxy
+                bulk_copy_g2s(raw[b ^ 1], tbl + (size_t)w1.patch * TBL_STRIDE, bytes, &bar[b ^ 1]);
+            }
+            n1 = n2;
+            if (n1 < n_item) w1 = items[queue_item(idx, n1)];
+            n2 = atomicAdd(Q.queue, 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[b], parity[b]);
+        parity[b] ^= 1u;
+        if (__syncthreads_or(!ok)) {   // also publishes s_g[b]
+            failed = true;
+            break;
+        }
+        for (int i = t; i < tbl_floats; i += blockDim.x) {
+            const float v = raw[b][i];
+            sT2[i] = f2(staged_negated(i) ? -v : v);
+        }
+        const WorkItem it = s_it[b];
+        const PatchGeo g = s_g[b];
+        const ImgMeta& im = img[g.img];
+        const int item = queue_item(idx, cur);
+        __syncthreads();
+        body(item, it, g, im, sT2);
+        __syncthreads();   // sT2 and the shared item records are rewritten by the next item
+        b ^= 1;
+    }
+    if (failed && t == 0) {
+        if (Q.status) atomicExch(Q.status, (int32_t)CELESTE_ERR_TIMEOUT);
+        // a copy into the other buffer may still be in flight: let it land (bounded)
+        if (s_item[b ^ 1] < n_item) mbar_wait_bounded(&bar[b ^ 1], parity[b ^ 1]);
+    }
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(Q.queue + 1, 1) == (int)gridDim.x - 1) {
+            Q.queue[0] = 0;
+            Q.queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int NPAIR>
+struct ContribBody {
+    int nprof;
+    float* spE;
+    float* spV;
+    const uint8_t* single;
+    const float* pixels;
+    const float* sky_map;
+    float* emap;
+    float* vmap;
+    double* item_ll;
+    __device__ void operator()(int item, const WorkItem& it, const PatchGeo& g, const ImgMeta& im,
+                               const float2* sT2) const {
+        contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, single, pixels, sky_map, emap,
+                               vmap, item_ll);
+    }
+};
+
+template <int MODE, int NPAIR>
+struct AdjointBody {
+    int nprof;
+    const float* pixels;
+    const float* emap;
+    const float* vmap;
+    double* part;
+    __device__ void operator()(int item, const WorkItem& it, const PatchGeo& g, const ImgMeta& im,
+                               const float2* sT2) const {
+        adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part);
+    }
+};
+
+// at most 64 registers for one pixel pair per thread, so that 8 CTAs fit on an SM
+template <int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR), 8 / NPAIR) k_contrib_pq(const WorkItem* __restrict__ items,
+                                                                  const int32_t* __restrict__ idx,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img,
+                                                                  int n_item, const float* __restrict__ tbl,
+                                                                  int tbl_floats, PersistentQueue Q,
+                                                                  ContribBody<NPAIR> body) {
+    run_items_persistent(items, idx, geo, img, n_item, tbl, tbl_floats, Q, body);
+}
+
+template <int MODE, int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR), 8 / NPAIR) k_adjoint_pq(const WorkItem* __restrict__ items,
+                                                                  const int32_t* __restrict__ idx,
+                                                                  const PatchGeo* __restrict__ geo,
+                                                                  const ImgMeta* __restrict__ img,
+                                                                  int n_item, const float* __restrict__ tbl,
+                                                                  int tbl_floats, PersistentQueue Q,
+                                                                  AdjointBody<MODE, NPAIR> body) {
+    run_items_persistent(items, idx, geo, img, n_item, tbl, tbl_floats, Q, body);
+}
+
+// table floats a persistent CTA copies per item: header .. galaxy components of the
+// problem's largest PSF (a multiple of 4 floats, so the copy is a multiple of 16 bytes)
+static inline int table_floats(const DevProblem& P) { return T_GAL + P.npsf_max * P.nprof * GAL_STRIDE; }
+
+// resident CTAs of a kernel x SMs of the current device, cached per (kernel, device)
+static int persistent_grid(const void* kernel, int threads, int n_item) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto f = cache.find({kernel, dev});
+        if (f != cache.end()) grid = f->second;
+    }
+    if (grid == 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+        grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        std::lock_guard<std::mutex> lk(mu);
+        cache[{kernel, dev}] = grid;
+    }
+    return grid < n_item ? grid : n_item;
+}
+
+// The item set of one launch: the items listed in idx[0 .. n) (idx null: items 0 .. n).
+struct ItemSet {
+    const int32_t* idx;
+    int n;
+};
+
+template <int NPAIR>
+static void contrib_x2(const DevProblem& P, ItemSet S, cudaStream_t st) {
+    k_contrib_x2<NPAIR><<<S.n, CHUNK / (2 * NPAIR), 0, st>>>(
+        P.items, S.idx, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2, P.single,
+        P.pixels, P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll);
+}
+
+template <int NPAIR>
+static void contrib_pq(const DevProblem& P, ItemSet S, cudaStream_t st) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    const ContribBody<NPAIR> body{P.nprof, (float*)P.spE, (float*)P.spE2, P.single, P.pixels,
+                                  P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll};
+    const int grid = persistent_grid((const void*)k_contrib_pq<NPAIR>, NT, S.n);
+    k_contrib_pq<NPAIR><<<grid, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, S.n, P.tbl32,
+                                             table_floats(P), PersistentQueue{P.queue, P.status}, body);
+}
+
+template <int NPAIR>
+static void adjoint_x2(const DevProblem& P, int mode, ItemSet S, cudaStream_t st) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     if (mode == MODE_LL)
-        k_adjoint_x2<MODE_LL, NPAIR><<<P.n_item, NT, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
-                                                             P.tbl32, (const float*)P.emap,
-                                                             (const float*)P.vmap, P.item_part);
+        k_adjoint_x2<MODE_LL, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
+                                                        P.tbl32, (const float*)P.emap,
+                                                        (const float*)P.vmap, P.item_part);
     else
-        k_adjoint_x2<MODE_GRAD, NPAIR><<<P.n_item, NT, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
-                                                               P.tbl32, (const float*)P.emap,
-                                                               (const float*)P.vmap, P.item_part);
+        k_adjoint_x2<MODE_GRAD, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
+                                                          P.tbl32, (const float*)P.emap,
+                                                          (const float*)P.vmap, P.item_part);
+}
+
+template <int MODE, int NPAIR>
+static void adjoint_pq_mode(const DevProblem& P, ItemSet S, cudaStream_t st) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    const AdjointBody<MODE, NPAIR> body{P.nprof, P.pixels, (const float*)P.emap, (const float*)P.vmap,
+                                        P.item_part};
+    const int grid = persistent_grid((const void*)k_adjoint_pq<MODE, NPAIR>, NT, S.n);
+    k_adjoint_pq<MODE, NPAIR><<<grid, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, S.n, P.tbl32,
+                                                   table_floats(P), PersistentQueue{P.queue, P.status},
+                                                   body);
+}
+
+template <int NPAIR>
+static void adjoint_pq(const DevProblem& P, int mode, ItemSet S, cudaStream_t st) {
+    if (mode == MODE_LL) adjoint_pq_mode<MODE_LL, NPAIR>(P, S, st);
+    else adjoint_pq_mode<MODE_GRAD, NPAIR>(P, S, st);
+}
+
+template <int NPAIR>
+static void fused_x2(const DevProblem& P, int mode, cudaStream_t st) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    if (mode == MODE_LL)
+        k_fused_x2<MODE_LL, NPAIR><<<P.n_single, NT, 0, st>>>(
+            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+    else
+        k_fused_x2<MODE_GRAD, NPAIR><<<P.n_single, NT, 0, st>>>(
+            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+}
+
+// Occupancy queries of the persistent kernels, made once on the current device outside
+// any stream capture (a CUDA graph of the fit may launch them later).
+void prime_persistent_grids() {
+    persistent_grid((const void*)k_contrib_pq<1>, CHUNK / 2, 1);
+    persistent_grid((const void*)k_contrib_pq<2>, CHUNK / 4, 1);
+    persistent_grid((const void*)k_adjoint_pq<MODE_LL, 1>, CHUNK / 2, 1);
+    persistent_grid((const void*)k_adjoint_pq<MODE_GRAD, 1>, CHUNK / 2, 1);
+    persistent_grid((const void*)k_adjoint_pq<MODE_LL, 2>, CHUNK / 4, 1);
+    persistent_grid((const void*)k_adjoint_pq<MODE_GRAD, 2>, CHUNK / 4, 1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -914,31 +1327,48 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
     return cudaGetLastError();
 }
 
-cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st) {
-    if (P.n_item == 0) return cudaSuccess;
+static ItemSet item_set(const DevProblem& P, const int32_t* idx, int n) {
+    return ItemSet{idx, n < 0 ? P.n_item : n};
+}
+
+cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st, const int32_t* idx, int n) {
+    const ItemSet S = item_set(P, idx, n);
+    if (S.n == 0) return cudaSuccess;
     if (precision == CELESTE_FP64)
-        k_contrib<double, 1><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.tbl64,
-                                                      (double*)P.spE, (double*)P.spE2, P.single,
-                                                      P.pixels, P.sky_map, (double*)P.emap,
-                                                      (double*)P.vmap, P.item_ll);
+        k_contrib<double, 1><<<S.n, CHUNK, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.tbl64,
+                                                    (double*)P.spE, (double*)P.spE2, P.single,
+                                                    P.pixels, P.sky_map, (double*)P.emap,
+                                                    (double*)P.vmap, P.item_ll);
     else
         switch (ppt_contrib(P)) {
-#define CEL_CONTRIB32(N)                                                                         \
-    case N:                                                                                      \
-        k_contrib<float, N><<<P.n_item, CHUNK / N, 0, st>>>(P.items, P.geo, P.img, P.nprof,        \
-                                                            P.tbl32, (float*)P.spE, (float*)P.spE2, \
-                                                            P.single, P.pixels, P.sky_map,         \
-                                                            (float*)P.emap, (float*)P.vmap,        \
-                                                            P.item_ll);                            \
+#define CEL_CONTRIB32(N)                                                                          \
+    case N:                                                                                       \
+        k_contrib<float, N><<<S.n, CHUNK / N, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof,       \
+                                                       P.tbl32, (float*)P.spE, (float*)P.spE2,      \
+                                                       P.single, P.pixels, P.sky_map,              \
+                                                       (float*)P.emap, (float*)P.vmap, P.item_ll); \
         break;
             CEL_CONTRIB32(1)
             CEL_CONTRIB32(2)
             CEL_CONTRIB32(4)
 #undef CEL_CONTRIB32
-            case 3: contrib_x2<1>(P, st); break;
-            case 5: contrib_x2<2>(P, st); break;
+            case 3: contrib_x2<1>(P, S, st); break;
+            case 5: contrib_x2<2>(P, S, st); break;
+            case 6: if (P.queue) contrib_pq<1>(P, S, st); else contrib_x2<1>(P, S, st); break;
+            case 7: if (P.queue) contrib_pq<2>(P, S, st); else contrib_x2<2>(P, S, st); break;
             default: return cudaErrorInvalidValue;
         }
+    return cudaGetLastError();
+}
+
+// The fused map + adjoint pass over the items whose pixels only their own patch covers
+// (FP32; the packed kernel with the adjoint's pair count: two pixels per thread unless
+// the adjoint is tuned to four).
+cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st) {
+    if (P.n_single == 0) return cudaSuccess;
+    const int code = ppt_adjoint(P);
+    if (code == 5 || code == 7) fused_x2<2>(P, mode, st);
+    else fused_x2<1>(P, mode, st);
     return cudaGetLastError();
 }
 
@@ -956,28 +1386,32 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
 }
 
 template <class R, int PPT>
-static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, cudaStream_t st) {
+static void adjoint_impl(const DevProblem& P, const R* tbl, int mode, ItemSet S, cudaStream_t st) {
     const R* em = (const R*)P.emap;
     const R* vm = (const R*)P.vmap;
     if (mode == MODE_LL)
-        k_adjoint<R, MODE_LL, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
+        k_adjoint<R, MODE_LL, PPT><<<S.n, CHUNK / PPT, 0, st>>>(
+            P.items, S.idx, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
     else
-        k_adjoint<R, MODE_GRAD, PPT><<<P.n_item, CHUNK / PPT, 0, st>>>(
-            P.items, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
+        k_adjoint<R, MODE_GRAD, PPT><<<S.n, CHUNK / PPT, 0, st>>>(
+            P.items, S.idx, P.geo, P.img, P.nprof, P.pixels, tbl, em, vm, P.item_part);
 }
 
-cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st) {
-    if (P.n_item == 0) return cudaSuccess;
+cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
+                           const int32_t* idx, int n) {
+    const ItemSet S = item_set(P, idx, n);
+    if (S.n == 0) return cudaSuccess;
     if (precision == CELESTE_FP64) {
-        adjoint_impl<double, 1>(P, P.tbl64, mode, st);
+        adjoint_impl<double, 1>(P, P.tbl64, mode, S, st);
     } else {
         switch (ppt_adjoint(P)) {
-            case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, st); break;
-            case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, st); break;
-            case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, st); break;
-            case 3: adjoint_x2<1>(P, mode, st); break;
-            case 5: adjoint_x2<2>(P, mode, st); break;
+            case 1: adjoint_impl<float, 1>(P, P.tbl32, mode, S, st); break;
+            case 2: adjoint_impl<float, 2>(P, P.tbl32, mode, S, st); break;
+            case 4: adjoint_impl<float, 4>(P, P.tbl32, mode, S, st); break;
+            case 3: adjoint_x2<1>(P, mode, S, st); break;
+            case 5: adjoint_x2<2>(P, mode, S, st); break;
+            case 6: if (P.queue) adjoint_pq<1>(P, mode, S, st); else adjoint_x2<1>(P, mode, S, st); break;
+            case 7: if (P.queue) adjoint_pq<2>(P, mode, S, st); else adjoint_x2<2>(P, mode, S, st); break;
             default: return cudaErrorInvalidValue;
         }
     }

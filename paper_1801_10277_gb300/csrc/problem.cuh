@@ -14,10 +14,15 @@ struct celeste_problem {
     DevProblem P{};
     cudaStream_t stream = nullptr;       // stream of the host-pointer entry points
     cudaStream_t last_stream = nullptr;  // stream of the last enqueued call
+    // the fused FP32 pass and the total run on a low-priority side stream, forked from and
+    // joined back into the caller's stream by these events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_gather = nullptr, ev_join = nullptr;
     // host copies used by the fit driver and validation
     std::vector<int32_t> patch_off, nbr_off, nbrs;
     std::vector<PatchGeo> geo;
     std::vector<ImgMeta> imgs;
+    int64_t sp_single = 0;               // source-pixels of the fused-pass items
     // device buffers owned by the problem
     std::vector<void*> owned;
     double* d_theta = nullptr;

@@ -32,6 +32,13 @@ __global__ void k_total(const double* __restrict__ tile_ll, int n_tile,
 cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
                                  double* d_grad, double* d_hess, cudaStream_t st);
 
+// total = tile ll sums + item ll sums - KL, one CTA (fixed order)
+cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st) {
+    k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl, P.n_src,
+                               d_total);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int precision, int mode,
                             double* d_total, double* d_local, double* d_grad, double* d_hess,
                             cudaStream_t st) {
