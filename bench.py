@@ -384,7 +384,7 @@ def main():
             "config": {"workload": prob.name, "sources": prob.n_src, "source_pixels": n_sp,
                        "bands": 5, "image": "2048x1489", "precision": "fp32 pixels, fp64 accumulation",
                        "l2": "flushed between steps (256 MiB write)",
-                       "pixels_per_thread": {"contrib": tuning[0], "adjoint": tuning[1]},
+                       "tuning": {"contrib": tuning[0], "adjoint": tuning[1], "fused_cap": tuning[2]},
                        "parallelism": f"replica{ws}" if ws > 1 else "single"},
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},

@@ -227,15 +227,20 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
  * pixels per thread (CTAs of 256, 128, 64 threads over the same 256-pixel work items)
  * and with two or four pixels per thread in packed FP32x2 instructions (codes 3, 5;
  * codes 6, 7: the same as persistent CTAs taking items from a work queue, with the
- * next item's table prefetched by bulk asynchronous copy),
- * reps launches each with CUDA events on the problem's stream, at theta (host), and keeps
- * the fastest for later FP32 calls.  The choice is returned (nullable outputs) and can be
- * stored by the caller and restored with celeste_set_tuning (codes 1 .. 7;
- * 0 = built-in default 2; anything else is CELESTE_ERR_ARG).
+ * next item's table prefetched by bulk asynchronous copy), reps launches each with CUDA
+ * events on the problem's stream, at theta (host).  The adjoint's code also picks the
+ * pair count of the fused map + adjoint pass (four pixels per thread for codes 5, 7).
+ * Then, with those kernels, it times whole FP32 value + gradient evaluations for caps
+ * of 0 (none), 8, 7, .., 3 resident CTAs per SM on the fused pass, which runs beside the
+ * map / gather / adjoint chain of the other items and must leave it room.  The choices
+ * are kept for later FP32 calls and returned (nullable outputs); celeste_set_tuning
+ * restores them (codes 1 .. 7, 0 = built-in default 2; cap 0 .. 8; anything else is
+ * CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint);
-celeste_status celeste_set_tuning(celeste_problem* prob, int32_t ppt_contrib, int32_t ppt_adjoint);
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap);
+celeste_status celeste_set_tuning(celeste_problem* prob, int32_t ppt_contrib, int32_t ppt_adjoint,
+                                  int32_t fused_cap);
 
 /* Status word written by the device-side checks of the last _device call (host read;
  * synchronises the problem's last stream).  CELESTE_OK or a negative status. */

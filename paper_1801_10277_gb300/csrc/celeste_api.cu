@@ -181,31 +181,38 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     const DevProblem& P = pr->P;
     // FP32 value / gradient: items whose pixels only their own patch covers take the fused
     // map + adjoint pass on the side stream, concurrently with the critical path on st
-    // (map pass over the other items -> gather -> their adjoint -> per-source epilogue);
-    // the total (tile and item ll sums - KL) follows the gather on the side stream.  The
-    // two streams write disjoint pixels and items, so the results do not depend on how
-    // the kernels interleave.
+    // (map pass over the other items -> their gather + adjoint -> per-source epilogue);
+    // the total (per-item ll sums - KL) follows on the side stream.  The two streams write
+    // disjoint pixels and items, so the results do not depend on how the kernels
+    // interleave.
     const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.idx_single;
-    CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
     if (fused) {
+        // st:   prep (tables, KL) -> map pass (other items) -> gather + adjoint (other items)
+        //       -> finalize (after the fused pass)
+        // side: fused pass (after prep) -> total (after the gather + adjoint pass)
         cudaStream_t sd = pr->side;
-        CEL_CUDA(cudaEventRecord(pr->ev_fork, st));
-        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_fork, 0));
+        CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
+        CEL_CUDA(cudaEventRecord(pr->ev_prep, st));
+        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_prep, 0));
         CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd); }));
+        CEL_CUDA(cudaEventRecord(pr->ev_fused, sd));
         CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st, P.idx_mixed, P.n_mixed); }));
-        CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
-        CEL_CUDA(cudaEventRecord(pr->ev_gather, st));
-        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_gather, 0));
-        if (d_total) CEL_CUDA(timed(pr, "total", sd, [&] { return launch_total(P, d_total, sd); }));
+        CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,
+                       [&] { return launch_gather_adjoint(P, mode, st); }));
+        if (d_total) {
+            CEL_CUDA(cudaEventRecord(pr->ev_gather, st));
+            CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_gather, 0));
+            CEL_CUDA(timed(pr, "total", sd, [&] { return launch_total_items(P, d_total, sd); }));
+        }
         CEL_CUDA(cudaEventRecord(pr->ev_join, sd));
-        CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
-                       [&] { return launch_adjoint(P, precision, mode, st, P.idx_mixed, P.n_mixed); }));
-        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_join, 0));
+        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_fused, 0));
         CEL_CUDA(timed(pr, "finalize", st, [&] {
             return launch_finalize(P, d_theta, precision, mode, nullptr, d_local, d_grad, d_hess, st);
         }));
+        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_join, 0));
         return CELESTE_OK;
     }
+    CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
     CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st); }));
     CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
     if (mode == MODE_HESS)
@@ -216,6 +223,59 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     CEL_CUDA(timed(pr, "finalize", st, [&] {
         return launch_finalize(P, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
     }));
+    return CELESTE_OK;
+}
+
+// run() through the graph cache: the first call with an argument set captures the
+// evaluation (with the status reset when reset_status) on the private capture stream and
+// instantiates it; every call launches the graph on st.  With profiling on, run() is
+// called directly (its per-kernel events are recorded at launch time).
+constexpr size_t MAX_GRAPHS = 8;
+
+void drop_graphs(celeste_problem* pr) {
+    for (auto& g : pr->graphs) cudaGraphExecDestroy(g.second);
+    pr->graphs.clear();
+}
+
+celeste_status run_cached(celeste_problem* pr, const double* d_theta, int precision, int mode,
+                          double* d_total, double* d_local, double* d_grad, double* d_hess,
+                          cudaStream_t st, bool reset_status) {
+    const DevProblem& P = pr->P;
+    if (pr->profile || !pr->capture) {
+        if (reset_status) CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
+        return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
+    }
+    celeste_problem::GraphKey key{precision, mode, P.tune_contrib, P.tune_adjoint, P.fused_cap,
+                                  {d_theta, d_total, d_local, d_grad, d_hess}};
+    if (!reset_status) key.mode |= 0x100;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : pr->graphs)
+        if (g.first == key) exec = g.second;
+    if (!exec) {
+        cudaStream_t cs = pr->capture;
+        CEL_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = reset_status ? cudaMemsetAsync(P.status, 0, sizeof(int32_t), cs) : cudaSuccess;
+        celeste_status rs = ce == cudaSuccess
+                                ? run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, cs)
+                                : CELESTE_ERR_CUDA;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (rs != CELESTE_OK || ce != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (rs != CELESTE_OK) return rs;
+            return cuda_fail(ce != cudaSuccess ? ce : ee, "evaluation capture");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+        if (pr->graphs.size() >= MAX_GRAPHS) {
+            cudaGraphExecDestroy(pr->graphs.front().second);
+            pr->graphs.erase(pr->graphs.begin());
+        }
+        pr->graphs.push_back({key, exec});
+    }
+    CEL_CUDA(cudaGraphLaunch(exec, st));
+    pr->last_stream = st;
     return CELESTE_OK;
 }
 
@@ -234,8 +294,9 @@ celeste_status run_host(celeste_problem* pr, const double* theta, int precision,
     CEL_CUDA(cudaSetDevice(pr->device));
     CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice,
                              pr->stream));
-    s = run(pr, pr->d_theta, precision, mode, o_total, o_local,
-            mode >= MODE_GRAD ? o_grad : nullptr, mode >= MODE_HESS ? o_hess : nullptr, pr->stream);
+    s = run_cached(pr, pr->d_theta, precision, mode, o_total, o_local,
+                   mode >= MODE_GRAD ? o_grad : nullptr, mode >= MODE_HESS ? o_hess : nullptr,
+                   pr->stream, false);
     if (s) return s;
     if (total) CEL_CUDA(cudaMemcpyAsync(total, o_total, sizeof(double), cudaMemcpyDeviceToHost, pr->stream));
     if (local) CEL_CUDA(cudaMemcpyAsync(local, o_local, sizeof(double) * n, cudaMemcpyDeviceToHost, pr->stream));
@@ -275,9 +336,11 @@ void celeste_problem_destroy(celeste_problem* pr) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : pr->pool) cudaEventDestroy(e);
+    drop_graphs(pr);
     for (void* p : pr->owned) cudaFree(p);
     if (pr->side) cudaStreamDestroy(pr->side);
-    for (cudaEvent_t e : {pr->ev_fork, pr->ev_gather, pr->ev_join})
+    if (pr->capture) cudaStreamDestroy(pr->capture);
+    for (cudaEvent_t e : {pr->ev_prep, pr->ev_fused, pr->ev_gather, pr->ev_join})
         if (e) cudaEventDestroy(e);
     if (pr->stream) cudaStreamDestroy(pr->stream);
     delete pr;
@@ -479,9 +542,10 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     {
         int least = 0, greatest = 0;   // numerically greatest = lowest priority
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        if (cudaStreamCreateWithPriority(&pr->side, cudaStreamNonBlocking, least) != cudaSuccess)
+        if (cudaStreamCreateWithPriority(&pr->side, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&pr->capture, cudaStreamNonBlocking) != cudaSuccess)
             return bail(fail(CELESTE_ERR_CUDA, "cudaStreamCreate failed"));
-        for (cudaEvent_t* e : {&pr->ev_fork, &pr->ev_gather, &pr->ev_join})
+        for (cudaEvent_t* e : {&pr->ev_prep, &pr->ev_fused, &pr->ev_gather, &pr->ev_join})
             if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
                 return bail(fail(CELESTE_ERR_CUDA, "cudaEventCreate failed"));
     }
@@ -556,6 +620,10 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.tile_ll = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
     P.item_ll = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
+    P.item_own = (double*)p;
+    if (P.n_item && cudaMemset(P.item_own, 0, sizeof(double) * P.n_item) != cudaSuccess)
+        return bail(fail(CELESTE_ERR_CUDA, "memset"));
 
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
@@ -566,9 +634,15 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.done = (int32_t*)p;
     if (cudaMemset(P.done, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
+    if ((st = dalloc(pr, &p, sizeof(double) * 64))) return bail(st);
+    P.tot_part = (double*)p;
+    if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
+    P.tot_done = (int32_t*)p;
+    if (cudaMemset(P.tot_done, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, 2 * sizeof(int32_t)))) return bail(st);
     P.queue = (int32_t*)p;
     prime_persistent_grids();
+    prime_fused_caps();
     if (cudaMemset(P.queue, 0, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.status = (int32_t*)p;
@@ -601,8 +675,8 @@ static celeste_status run_device(celeste_problem* pr, const double* d_theta, int
     if (!pr || !d_theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
     cudaStream_t st = (cudaStream_t)stream;
     CEL_CUDA(cudaSetDevice(pr->device));
-    CEL_CUDA(cudaMemsetAsync(pr->P.status, 0, sizeof(int32_t), st));   // checked in the epilogue
-    return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
+    // the status word (checked on the device) is reset first
+    return run_cached(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st, true);
 }
 
 celeste_status celeste_elbo_device(celeste_problem* pr, const double* d_theta, int32_t precision,
@@ -711,8 +785,7 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     const bool fused = precision == CELESTE_FP32_ACC64 && P.idx_single;
     if (fused) CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
     CEL_CUDA(timed(pr, "adjoint", st, [&] {
-        return fused ? launch_adjoint(P, precision, MODE_GRAD, st, P.idx_mixed, P.n_mixed)
-                     : launch_adjoint(P, precision, MODE_GRAD, st);
+        return fused ? launch_adjoint_mixed_maps(P, st) : launch_adjoint(P, precision, MODE_GRAD, st);
     }));
     CEL_CUDA(timed(pr, "finalize", st, [&] {
         return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
@@ -722,7 +795,7 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
 }
 
 celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint) {
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap) {
     if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
     celeste_status s = check_theta_host(theta, pr->P.n_src);
     if (s) return s;
@@ -748,8 +821,9 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     const int32_t* rest = fused ? P.idx_mixed : nullptr;
     const int n_rest = fused ? P.n_mixed : -1;
     auto adjoint_stage = [&]() {
-        cudaError_t r = fused ? launch_fused(P, MODE_GRAD, st) : cudaSuccess;
-        if (r == cudaSuccess) r = launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st, rest, n_rest);
+        if (!fused) return launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
+        cudaError_t r = launch_fused(P, MODE_GRAD, st);
+        if (r == cudaSuccess) r = launch_gather_adjoint(P, MODE_GRAD, st);
         return r;
     };
     for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
@@ -774,18 +848,45 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
         if (e == cudaSuccess && tc < best_c) { best_c = tc; pick_c = cands[ci]; }
         if (e == cudaSuccess && ta < best_a) { best_a = ta; pick_a = cands[ci]; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     P.tune_contrib = pick_c;
     P.tune_adjoint = pick_a;
+    // the fused pass's CTA cap per SM, timed on whole value + gradient evaluations (it
+    // trades the fused pass's own speed against room for the concurrent chain)
+    int pick_cap = 0;
+    if (e == cudaSuccess && fused && ensure_out(pr) == CELESTE_OK) {
+        const int caps[7] = {0, 8, 7, 6, 5, 4, 3};
+        float best = 1e30f;
+        double* o = pr->d_out;
+        for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
+            P.fused_cap = caps[ci];
+            celeste_status rs = run(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1,
+                                    o + 1 + P.n_src, nullptr, st);
+            float t = 0.f;
+            if (rs == CELESTE_OK) e = cudaEventRecord(a, st);
+            for (int r = 0; r < 2 * reps && rs == CELESTE_OK && e == cudaSuccess; ++r)
+                rs = run(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1, o + 1 + P.n_src,
+                         nullptr, st);
+            if (rs != CELESTE_OK) e = cudaErrorUnknown;
+            if (e == cudaSuccess) e = cudaEventRecord(b, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+            if (e == cudaSuccess && t < best) { best = t; pick_cap = caps[ci]; }
+        }
+    }
+    P.fused_cap = pick_cap;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     if (ppt_contrib) *ppt_contrib = pick_c;
     if (ppt_adjoint) *ppt_adjoint = pick_a;
+    if (fused_cap) *fused_cap = pick_cap;
     return CELESTE_OK;
 }
 
-celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint) {
+celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint,
+                                  int32_t fused_cap) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    if (fused_cap < 0 || fused_cap > 8) return fail(CELESTE_ERR_ARG, "fused_cap must be 0 .. 8");
     auto okp = [](int v) { return v >= 0 && v <= 7; };
     if (!okp(ppt_contrib) || !okp(ppt_adjoint))
         return fail(CELESTE_ERR_ARG,
@@ -793,6 +894,7 @@ celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int3
                     "pixels), 6 / 7 the same as persistent CTAs on a work queue");
     pr->P.tune_contrib = ppt_contrib;
     pr->P.tune_adjoint = ppt_adjoint;
+    pr->P.fused_cap = fused_cap;
     return CELESTE_OK;
 }
 

@@ -146,28 +146,60 @@ __device__ __forceinline__ void finalize_source(int s, int n_src, int mode,
     }
 }
 
-// total = sum of tile and item ll sums - sum of KL, fixed order; every thread of a CTA
-// of <= 512 threads calls it (used where k_finalize does not fold the total in)
+// total = sum of tile and item ll sums - sum of KL, over the concatenated index space
+// [tile_ll | item_ll | kl], split into gridDim.x contiguous slices: each CTA of
+// TOTAL_THREADS sums its slice (fixed order), the last CTA to finish adds the slice sums
+// in order and resets the counter.  Spread over many SMs because GB300's FP64 adds are
+// slow on any one SM.
+constexpr int TOTAL_THREADS = 256;
+constexpr int TOTAL_CTAS = 64;
+
+__device__ __forceinline__ double total_term(const double* __restrict__ tile_ll, int n_tile,
+                                             const double* __restrict__ item_ll, int n_item,
+                                             const double* __restrict__ kl, int i) {
+    if (i < n_tile) return tile_ll[i];
+    i -= n_tile;
+    if (i < n_item) return item_ll[i];
+    return -kl[i - n_item];
+}
+
 __device__ __forceinline__ void total_reduce(const double* __restrict__ tile_ll, int n_tile,
                                              const double* __restrict__ item_ll, int n_item,
                                              const double* __restrict__ kl, int n_src,
+                                             double* __restrict__ part, int32_t* __restrict__ done,
                                              double* __restrict__ out) {
-    __shared__ double red[512];
-    const int t = threadIdx.x, nt = blockDim.x;
-    double s = sum_strided4(tile_ll, t, n_tile, nt);
-    s += sum_strided4(item_ll, t, n_item, nt);
-    s -= sum_strided4(kl, t, n_src, nt);
-    red[t] = s;
+    __shared__ double red[TOTAL_THREADS];
+    __shared__ int last;
+    const int t = threadIdx.x;
+    const int n = n_tile + n_item + n_src;
+    const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int i0 = (int)blockIdx.x * per, i1 = min(n, i0 + per);
+    double v = 0.0;
+    for (int i = i0 + t; i < i1; i += TOTAL_THREADS) v += total_term(tile_ll, n_tile, item_ll, n_item, kl, i);
+    red[t] = v;
     __syncthreads();
-    int n = nt;
-    while (n > 1) {
-        const int h = (n + 1) / 2;
-        if (t < n - h) red[t] += red[t + h];
+    for (int h = TOTAL_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) red[t] += red[t + h];
         __syncthreads();
-        n = h;
     }
-    if (t == 0) *out = red[0];
+    if (t == 0) {
+        part[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(done, 1) == (int)gridDim.x - 1;
+    }
     __syncthreads();
+    if (!last) return;
+    __threadfence();
+    red[t] = t < (int)gridDim.x ? __ldcg(part + t) : 0.0;
+    __syncthreads();
+    for (int h = TOTAL_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) red[t] += red[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        *out = red[0];
+        *done = 0;
+    }
 }
 
 }  // namespace cel

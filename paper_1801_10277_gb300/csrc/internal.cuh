@@ -158,6 +158,7 @@ enum Mode : int { MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 struct DevProblem {
     int32_t n_img, n_src, n_patch, n_item, n_tile, npsf_max, nprof;
     int32_t tune_contrib, tune_adjoint;   // FP32 pixels per thread (0 = default)
+    int32_t fused_cap;                    // resident CTAs per SM of the fused pass (0 = no cap)
     int64_t n_px, n_sp;
     const ImgMeta* img;
     const float* pixels;
@@ -177,12 +178,16 @@ struct DevProblem {
     void* vmap;
     const uint8_t* single;   // per (source, pixel): 1 when no other patch covers the pixel (nullable)
     double* item_ll;         // per work item: ll summed over its singly covered pixels
+    double* item_own;        // per work item: ll of the multiply covered pixels it owns (gather +
+                             // adjoint pass; the first covering patch owns a pixel)
     double* item_part;
     double* tile_ll;
     double* kl;
     double* kl_grad;         // [n_src][44] KL gradient, written by k_prep (nullable: no KL in prep)
     double* src_total;       // [n_src] each source's share of the total ELBO (k_finalize)
     int32_t* done;           // k_finalize completion counter, 0 between launches
+    double* tot_part;        // [64] k_total slice sums
+    int32_t* tot_done;       // k_total completion counter, 0 between launches
     const int32_t* idx_single;   // items whose every pixel only their own patch covers (nullable)
     const int32_t* idx_mixed;    // the other items
     int n_single, n_mixed;
@@ -200,15 +205,23 @@ celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const 
                                                           double*, double*));
 
 void prime_persistent_grids();
+void prime_fused_caps();
 // total = tile ll sums + item ll sums - KL (after the gather and every item ll)
 cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st);
+// tables (and, with_kl, the KL value / gradient and the domain check) of every source
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
-                        cudaStream_t st);
+                        cudaStream_t st, bool with_kl = true);
 // contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);
 // FP32 map pass + adjoint in one kernel over P.idx_single (mode MODE_LL or MODE_GRAD)
 cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st);
+// FP32 gather + adjoint in one kernel over P.idx_mixed (after the map pass over them)
+cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st);
+// FP32 adjoint over P.idx_mixed from the maps (same kernel as the gather + adjoint pass)
+cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st);
+// total over the fused path's per-item sums: item_own + item_ll - KL
+cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);

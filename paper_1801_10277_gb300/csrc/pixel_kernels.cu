@@ -18,6 +18,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "internal.cuh"
 #include "async_copy.cuh"
@@ -107,8 +108,8 @@ constexpr int PREP_KL_WARP = PREP_THREADS / 32 - 1;
 template <class R>
 __device__ __forceinline__ void prep_kl(int s, const double* th, const R* thr,
                                         const ModelDev* __restrict__ md, double* __restrict__ kl_out,
-                                        double* __restrict__ klg_out, int32_t* __restrict__ status) {
-    __shared__ double kg[NP];
+                                        double* __restrict__ klg_out, int32_t* __restrict__ status,
+                                        double* kg /* shared, NP */) {
     const int lane = threadIdx.x & 31;
     if (status)
         for (int i = lane; i < NP; i += 32) theta_domain_check(i, th[i], status);
@@ -138,8 +139,9 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
     }
     __syncthreads();
     const bool kl_here = klg_out && (t >> 5) == PREP_KL_WARP;
+    __shared__ double kg[NP];
     if (np == 0) {
-        if (kl_here) prep_kl<R>(s, th, thr, md, kl_out, klg_out, status);
+        if (kl_here) prep_kl<R>(s, th, thr, md, kl_out, klg_out, status, kg);
         return;
     }
     const int per_k = 1 + nprof;
@@ -209,7 +211,7 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
         }
         if (r0 == 0 && kl_here) {
             __syncwarp();
-            prep_kl<R>(s, th, thr, md, kl_out, klg_out, status);
+            prep_kl<R>(s, th, thr, md, kl_out, klg_out, status, kg);
         }
         __syncthreads();
         // components of the patches of this round
@@ -566,6 +568,15 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_adjoint(const WorkItem* __restr
 // the issue slots of the scalar pair).  The table is staged in shared memory with each
 // coefficient duplicated, so a coefficient pair is one 64-bit load.
 
+// compile-time knobs of the packed kernels (defaults measured best on GB300)
+#ifndef CEL_GAL_UNROLL
+#define CEL_GAL_UNROLL 1
+#endif
+#ifndef CEL_FUSED_MINB
+#define CEL_FUSED_MINB 8
+#endif
+constexpr int GAL_UNROLL = CEL_GAL_UNROLL;
+
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 ex2x2(float2 a) { return make_float2(ex2(a.x), ex2(a.y)); }
 
@@ -712,7 +723,31 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
 // the component loop (and written to the maps, which a later backward-only call reads),
 // and the item's ll goes to item_ll as well as to its partials.  Otherwise E and Var
 // come from the maps k_contrib / k_gather wrote.
-template <int MODE, int NPAIR, bool FUSED = false>
+// Where an item's E and Var come from:
+//   SRC_MAPS   the maps (k_contrib / k_gather wrote them);
+//   SRC_OWN    the item's own mixture sums (every pixel singly covered; see FUSED);
+//   SRC_GATHER singly covered pixels from the maps (k_contrib wrote them), the others
+//              gathered here from the E_s, Var_s of the patches covering the pixel's 16 x 16
+//              cell, in the cell list's (ascending source) order -- the same sums k_gather
+//              forms.  The first covering patch owns the pixel: its item writes the maps and
+//              counts the pixel's ll for the total (item_own).
+constexpr int SRC_MAPS = 0, SRC_OWN = 1, SRC_GATHER = 2;
+
+struct GatherArgs {
+    const uint8_t* single;
+    const int32_t* tile_grid;
+    const Tile* tiles;
+    const int32_t* tile_list;
+    const PatchGeo* geo;
+    const float* spE;
+    const float* spV;
+    const float* sky_map;
+    float* emap;
+    float* vmap;
+    double* item_own;
+};
+
+template <int MODE, int NPAIR, int SRC = SRC_MAPS>
 __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, const PatchGeo& g,
                                                 const ImgMeta& im, int nprof, const float2* sT2,
                                                 const float* __restrict__ pixels,
@@ -722,7 +757,9 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                                                 const float* __restrict__ sky_map = nullptr,
                                                 float* __restrict__ emap_out = nullptr,
                                                 float* __restrict__ vmap_out = nullptr,
-                                                double* __restrict__ item_ll = nullptr) {
+                                                double* __restrict__ item_ll = nullptr,
+                                                const GatherArgs* ga = nullptr) {
+    constexpr bool FUSED = SRC == SRC_OWN;
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
@@ -736,6 +773,7 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
     bool ok[PPT];
     float cE[PPT], cV[PPT], xv[PPT], sky[PPT];
     int64_t mm[PPT];
+    float vown = 0.f;   // SRC_GATHER: ll of the multiply covered pixels this item owns
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
@@ -750,9 +788,43 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
             xv[p] = x;
             sky[p] = im.has_sky_map ? sky_map[m] : (float)im.sky;
         } else {
-            const float E = emap[m], V = vmap[m];
+            float E, V;
+            bool own = false;
+            if constexpr (SRC == SRC_GATHER) {
+                if (ga->single[g.sp_off + q]) {
+                    E = emap[m];
+                    V = vmap[m];
+                } else {
+                    const int gx = g.x0 + xs[p], gy = g.y0 + ys[p];
+                    const Tile tl = ga->tiles[ga->tile_grid[im.tg_off + (int64_t)(gy / TILE) * im.tgw + gx / TILE]];
+                    E = im.has_sky_map ? ga->sky_map[m] : (float)im.sky;
+                    V = 0.f;
+                    int first = -1;
+                    for (int e = 0; e < tl.list_n; ++e) {
+                        const int pe = ga->tile_list[tl.list_off + e];
+                        const PatchGeo G = ga->geo[pe];
+                        const int xx = gx - G.x0, yy = gy - G.y0;
+                        if (xx >= 0 && xx < G.w && yy >= 0 && yy < G.h) {
+                            const int64_t qq = G.sp_off + (int64_t)yy * G.w + xx;
+                            E += ga->spE[qq];
+                            V += ga->spV[qq];
+                            if (first < 0) first = pe;
+                        }
+                    }
+                    own = ok[p] && first == it.patch;
+                    if (own) {
+                        ga->emap[m] = E;
+                        ga->vmap[m] = V;
+                    }
+                }
+            } else {
+                E = emap[m];
+                V = vmap[m];
+            }
             const float iE = 1.f / E;
-            if (ok[p]) v[0] += x * (lg(E) - 0.5f * V * iE * iE) - E;
+            const float ll = x * (lg(E) - 0.5f * V * iE * iE) - E;
+            if (ok[p]) v[0] += ll;
+            if (own) vown += ll;
             cE[p] = x * (iE + V * iE * iE * iE) - 1.f;
             cV[p] = -0.5f * x * iE * iE;
         }
@@ -866,6 +938,7 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                 }
             }
             const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
+#pragma unroll (GAL_UNROLL)
             for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
                 float2 c0, c1, c2, c3, npxx, npxy, npyy, c, dc, nu;
                 ld2(G, c0, c1);
@@ -943,6 +1016,12 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
     }
     __shared__ double tot[NV];
     cta_sum<float, NV>(v, tot);
+    if constexpr (SRC == SRC_GATHER) {
+        float vo[1] = {vown};
+        double to[1];
+        cta_sum<float, 1>(vo, to);
+        if (threadIdx.x == 0) ga->item_own[item] = to[0];
+    }
     __syncthreads();
     double* out = part + (size_t)item * NPART;
     if (threadIdx.x == 0) {
@@ -1008,9 +1087,28 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
     adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part);
 }
 
+// gather + adjoint in one, for the items listed in idx (some pixel covered twice or more)
+template <int MODE, int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_gadjoint_x2(const WorkItem* __restrict__ items,
+                                                                   const int32_t* __restrict__ idx,
+                                                                   const ImgMeta* __restrict__ img, int nprof,
+                                                                   const float* __restrict__ pixels,
+                                                                   const float* __restrict__ tbl,
+                                                                   double* __restrict__ part,
+                                                                   GatherArgs ga) {
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    const int item = idx[blockIdx.x];
+    const WorkItem it = items[item];
+    const PatchGeo g = ga.geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
+    adjoint_x2_item<MODE, NPAIR, SRC_GATHER>(item, it, g, im, nprof, sT2, pixels, ga.emap, ga.vmap, part,
+                                             nullptr, nullptr, nullptr, nullptr, &ga);
+}
+
 // map pass + adjoint in one, for the items listed in idx (every pixel singly covered)
 template <int MODE, int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_fused_x2(const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x2(const WorkItem* __restrict__ items,
                                                                 const int32_t* __restrict__ idx,
                                                                 const PatchGeo* __restrict__ geo,
                                                                 const ImgMeta* __restrict__ img, int nprof,
@@ -1027,8 +1125,8 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_fused_x2(const WorkItem
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR, true>(item, it, g, im, nprof, sT2, pixels, nullptr, nullptr, part,
-                                       sky_map, emap, vmap, item_ll);
+    adjoint_x2_item<MODE, NPAIR, SRC_OWN>(item, it, g, im, nprof, sT2, pixels, nullptr, nullptr, part,
+                                          sky_map, emap, vmap, item_ll);
 }
 
 // ---- persistent CTAs with a work queue (tuning codes 6, 7)
@@ -1280,17 +1378,78 @@ static void adjoint_pq(const DevProblem& P, int mode, ItemSet S, cudaStream_t st
     else adjoint_pq_mode<MODE_GRAD, NPAIR>(P, S, st);
 }
 
+// Dynamic shared memory (unused by the kernel) that holds a kernel to at most `cap`
+// resident CTAs per SM, so that the fused pass running beside the map / gather / adjoint
+// chain leaves SM slots for that chain; 0 = no cap.  Found with the occupancy API and
+// cached per (kernel, cap, device).
+static int cap_padding(const void* kernel, int threads, int cap) {
+    if (cap <= 0) return 0;
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto f = cache.find({kernel, cap, dev});
+        if (f != cache.end()) return f->second;
+    }
+    int smem_blk = 0;
+    cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    const int room = smem_blk - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, room > 0 ? room : 0);
+    int pad = 0;
+    for (int bytes = 0; bytes <= room; bytes += 1024) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, bytes) != cudaSuccess) break;
+        if (per_sm <= cap) {
+            pad = bytes;
+            break;
+        }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[{kernel, cap, dev}] = pad;
+    return pad;
+}
+
 template <int NPAIR>
 static void fused_x2(const DevProblem& P, int mode, cudaStream_t st) {
     constexpr int NT = CHUNK / (2 * NPAIR);
+    if (mode == MODE_LL) {
+        const int pad = cap_padding((const void*)k_fused_x2<MODE_LL, NPAIR>, NT, P.fused_cap);
+        k_fused_x2<MODE_LL, NPAIR><<<P.n_single, NT, pad, st>>>(
+            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+    } else {
+        const int pad = cap_padding((const void*)k_fused_x2<MODE_GRAD, NPAIR>, NT, P.fused_cap);
+        k_fused_x2<MODE_GRAD, NPAIR><<<P.n_single, NT, pad, st>>>(
+            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+    }
+}
+
+// the padding of every fused kernel for caps 1 .. 8, found outside any stream capture
+void prime_fused_caps() {
+    for (int cap = 1; cap <= 8; ++cap) {
+        cap_padding((const void*)k_fused_x2<MODE_LL, 1>, CHUNK / 2, cap);
+        cap_padding((const void*)k_fused_x2<MODE_GRAD, 1>, CHUNK / 2, cap);
+        cap_padding((const void*)k_fused_x2<MODE_LL, 2>, CHUNK / 4, cap);
+        cap_padding((const void*)k_fused_x2<MODE_GRAD, 2>, CHUNK / 4, cap);
+    }
+}
+
+template <int NPAIR>
+static void gadjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
+    constexpr int NT = CHUNK / (2 * NPAIR);
+    const GatherArgs ga{P.single, P.tile_grid, P.tiles, P.tile_list, P.geo, (const float*)P.spE,
+                        (const float*)P.spE2, P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_own};
     if (mode == MODE_LL)
-        k_fused_x2<MODE_LL, NPAIR><<<P.n_single, NT, 0, st>>>(
-            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+        k_gadjoint_x2<MODE_LL, NPAIR><<<P.n_mixed, NT, 0, st>>>(P.items, P.idx_mixed, P.img, P.nprof,
+                                                               P.pixels, P.tbl32, P.item_part, ga);
     else
-        k_fused_x2<MODE_GRAD, NPAIR><<<P.n_single, NT, 0, st>>>(
-            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+        k_gadjoint_x2<MODE_GRAD, NPAIR><<<P.n_mixed, NT, 0, st>>>(P.items, P.idx_mixed, P.img, P.nprof,
+                                                                 P.pixels, P.tbl32, P.item_part, ga);
 }
 
 // Occupancy queries of the persistent kernels, made once on the current device outside
@@ -1313,17 +1472,16 @@ static inline int ppt_contrib(const DevProblem& P) { return P.tune_contrib > 0 ?
 static inline int ppt_adjoint(const DevProblem& P) { return P.tune_adjoint > 0 ? P.tune_adjoint : 2; }
 
 cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precision,
-                        cudaStream_t st) {
-    if (P.n_src == 0 || (P.n_patch == 0 && !P.kl_grad)) return cudaSuccess;
+                        cudaStream_t st, bool with_kl) {
+    double* klg = with_kl ? P.kl_grad : nullptr;
+    if (P.n_src == 0 || (P.n_patch == 0 && !klg)) return cudaSuccess;
     const int grid = P.n_src;
     if (precision == CELESTE_FP64)
         k_prep<double><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                      P.n_src, P.nprof, P.tbl64, P.kl, P.kl_grad,
-                                                      P.status);
+                                                      P.n_src, P.nprof, P.tbl64, P.kl, klg, P.status);
     else
         k_prep<float><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                     P.n_src, P.nprof, P.tbl32, P.kl, P.kl_grad,
-                                                     P.status);
+                                                     P.n_src, P.nprof, P.tbl32, P.kl, klg, P.status);
     return cudaGetLastError();
 }
 
@@ -1369,6 +1527,26 @@ cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st) {
     const int code = ppt_adjoint(P);
     if (code == 5 || code == 7) fused_x2<2>(P, mode, st);
     else fused_x2<1>(P, mode, st);
+    return cudaGetLastError();
+}
+
+// gather + adjoint over P.idx_mixed (FP32, packed pairs as launch_fused picks them)
+cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st) {
+    if (P.n_mixed == 0) return cudaSuccess;
+    const int code = ppt_adjoint(P);
+    if (code == 5 || code == 7) gadjoint_x2<2>(P, mode, st);
+    else gadjoint_x2<1>(P, mode, st);
+    return cudaGetLastError();
+}
+
+// the adjoint over P.idx_mixed from the maps, with the kernel launch_gather_adjoint uses
+// (a backward-only call then reproduces the one-call gradient bit for bit)
+cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st) {
+    if (P.n_mixed == 0) return cudaSuccess;
+    const ItemSet S{P.idx_mixed, P.n_mixed};
+    const int code = ppt_adjoint(P);
+    if (code == 5 || code == 7) adjoint_x2<2>(P, MODE_GRAD, S, st);
+    else adjoint_x2<1>(P, MODE_GRAD, S, st);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,23 @@ struct celeste_problem {
     // the fused FP32 pass and the total run on a low-priority side stream, forked from and
     // joined back into the caller's stream by these events
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_gather = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_prep = nullptr, ev_fused = nullptr, ev_gather = nullptr, ev_join = nullptr;
+    // one evaluation (status reset + every launch of both streams) captured as a CUDA graph
+    // per argument set, replayed by later calls with the same arguments
+    struct GraphKey {
+        int precision, mode, tune_c, tune_a, cap;
+        const void* ptr[5];   // theta, total, local, grad, hess
+        bool operator==(const GraphKey& o) const {
+            if (precision != o.precision || mode != o.mode || tune_c != o.tune_c || tune_a != o.tune_a ||
+                cap != o.cap)
+                return false;
+            for (int i = 0; i < 5; ++i)
+                if (ptr[i] != o.ptr[i]) return false;
+            return true;
+        }
+    };
+    std::vector<std::pair<GraphKey, cudaGraphExec_t>> graphs;
+    cudaStream_t capture = nullptr;       // private stream the graphs are captured on
     // host copies used by the fit driver and validation
     std::vector<int32_t> patch_off, nbr_off, nbrs;
     std::vector<PatchGeo> geo;

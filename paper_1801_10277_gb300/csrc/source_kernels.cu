@@ -23,19 +23,28 @@ k_finalize(int n_src, int mode, const PatchGeo* __restrict__ geo,
                     kl_grad, local_out, grad_out, src_total, done, total_out);
 }
 
-__global__ void k_total(const double* __restrict__ tile_ll, int n_tile,
-                        const double* __restrict__ item_ll, int n_item,
-                        const double* __restrict__ kl, int n_src, double* __restrict__ out) {
-    total_reduce(tile_ll, n_tile, item_ll, n_item, kl, n_src, out);
+__global__ void __launch_bounds__(TOTAL_THREADS)
+k_total(const double* __restrict__ tile_ll, int n_tile, const double* __restrict__ item_ll, int n_item,
+        const double* __restrict__ kl, int n_src, double* __restrict__ part, int32_t* __restrict__ done,
+        double* __restrict__ out) {
+    total_reduce(tile_ll, n_tile, item_ll, n_item, kl, n_src, part, done, out);
 }
 
 cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
                                  double* d_grad, double* d_hess, cudaStream_t st);
 
-// total = tile ll sums + item ll sums - KL, one CTA (fixed order)
+// total = item_own + item_ll - KL: the fused path's per-item sums (fixed order)
+cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st) {
+    k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.item_own, P.n_item, P.item_ll, P.n_item, P.kl,
+                                                  P.n_src, P.tot_part, P.tot_done, d_total);
+    return cudaGetLastError();
+}
+
+// total = tile ll sums + item ll sums - KL (fixed order, TOTAL_CTAS slices)
 cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st) {
-    k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl, P.n_src,
-                               d_total);
+    k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll,
+                                                  P.single ? P.n_item : 0, P.kl, P.n_src, P.tot_part,
+                                                  P.tot_done, d_total);
     return cudaGetLastError();
 }
 
@@ -56,8 +65,9 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int prec
         return cudaGetLastError();
     }
     if (d_total)
-        k_total<<<1, 512, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll, P.single ? P.n_item : 0, P.kl,
-                                   P.n_src, d_total);
+        k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll,
+                                                      P.single ? P.n_item : 0, P.kl, P.n_src,
+                                                      P.tot_part, P.tot_done, d_total);
     return cudaGetLastError();
 }
 
