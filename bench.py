@@ -31,6 +31,10 @@ from paper_1801_10277_gb300 import synth  # noqa: E402
 
 FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
+# DRAM bytes (read + write) per launch of each pixel kernel on the one-field workload, from
+# one ncu capture (profiles/k_fused_x2_field_500src.md, profiles/step_kernels_field_500src.md);
+# an entry is removed whenever its kernel changes after the capture.
+DRAM_BYTES_PER_LAUNCH = {"fused": 13.95e6, "gather_adjoint": 7.05e6, "contrib": 3.03e6}
 FP32_LANES = 128
 
 
@@ -212,6 +216,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--hess-steps", type=int, default=20)
     ap.add_argument("--no-fit", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="contrib,adjoint,fused_cap codes to use instead of autotuning (e.g. 2,1,0)")
     args = ap.parse_args()
     rank, ws, dist = dist_init()
     if args.impl == "reference":
@@ -224,7 +230,11 @@ def main():
     prob = synth.config(1, seed=rank_field_seed(rank))
     P = cel.Problem(prob)
     n_sp = P.source_pixels
-    tuning = P.autotune(prob.theta)
+    if args.tuning:
+        tuning = tuple(int(v) for v in args.tuning.split(","))
+        P.set_tuning(*tuning)
+    else:
+        tuning = P.autotune(prob.theta)
     dev = torch.device("cuda", local_rank)
     theta = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
     tot = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -280,10 +290,12 @@ def main():
     ne, nd = prob.exp_mix.shape[0], prob.dev_mix.shape[0]
     split = P.stats()
     sp_fused = split["fused_source_pixels"] if "fused" in prof else 0
-    work = {   # algorithmic FP32 FLOP per launch of each pixel kernel
+    rest = n_sp - sp_fused
+    work = {   # algorithmic FP32 FLOP per launch of each pixel kernel (stage names)
         "fused": fused_flops_per_source_pixel(npsf, ne, nd) * sp_fused,
-        "adjoint": adjoint_flops_per_source_pixel(npsf, ne, nd) * (n_sp - sp_fused),
-        "contrib": contrib_flops_per_source_pixel(npsf, ne, nd) * (n_sp - sp_fused),
+        "gather_adjoint": adjoint_flops_per_source_pixel(npsf, ne, nd) * rest,
+        "adjoint": adjoint_flops_per_source_pixel(npsf, ne, nd) * rest,
+        "contrib": contrib_flops_per_source_pixel(npsf, ne, nd) * rest,
     }
     achieved_k = {k: work[k] / (kernel_us[k] * 1e-6) / 1e12
                   for k in work if kernel_us.get(k, 0) > 0 and work[k] > 0}
@@ -291,8 +303,9 @@ def main():
     clocks = clk.summary()
     peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
     achieved = achieved_k[dom]
+    traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if prob.name.startswith("field_500src") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32, "traffic": None, "kernel": f"{dom} (FP32)",
+                "frac": achieved / peak_fp32, "traffic": traffic, "kernel": f"{dom} (FP32)",
                 "flop_per_launch": work[dom],
                 "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
                 "kernel_us": kernel_us, "kernel_tflops": achieved_k,
