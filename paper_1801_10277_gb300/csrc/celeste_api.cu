@@ -187,14 +187,14 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     // interleave.
     const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.idx_single;
     if (fused) {
-        // st:   prep (tables, KL) -> map pass (other items) -> gather + adjoint (other items)
+        // st:   prep (tables) -> map pass (other items) -> gather + adjoint (other items)
         //       -> finalize (after the fused pass)
-        // side: fused pass (after prep) -> total (after the gather + adjoint pass)
+        // side: fused pass + KL (after prep) -> total (after the gather + adjoint pass)
         cudaStream_t sd = pr->side;
-        CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
+        CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st, false); }));
         CEL_CUDA(cudaEventRecord(pr->ev_prep, st));
         CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_prep, 0));
-        CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd); }));
+        CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd, d_theta); }));
         CEL_CUDA(cudaEventRecord(pr->ev_fused, sd));
         CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st, P.idx_mixed, P.n_mixed); }));
         CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,

@@ -214,8 +214,9 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
 // contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);
-// FP32 map pass + adjoint in one kernel over P.idx_single (mode MODE_LL or MODE_GRAD)
-cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st);
+// FP32 map pass + adjoint in one kernel over P.idx_single (mode MODE_LL or MODE_GRAD);
+// with d_theta, the same launch also computes the KL (value, gradient, domain check)
+cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta = nullptr);
 // FP32 gather + adjoint in one kernel over P.idx_mixed (after the map pass over them)
 cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st);
 // FP32 adjoint over P.idx_mixed from the maps (same kernel as the gather + adjoint pass)

@@ -1106,7 +1106,19 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_gadjoint_x2(const WorkI
                                              nullptr, nullptr, nullptr, nullptr, &ga);
 }
 
-// map pass + adjoint in one, for the items listed in idx (every pixel singly covered)
+// map pass + adjoint in one, for the items listed in idx (every pixel singly covered).
+// With kl.klg set, the first kl.blocks CTAs instead compute the KL (one warp per source,
+// value, gradient, domain check): the KL is needed only by the epilogue and the total,
+// which follow this kernel on the side stream, so it leaves k_prep's critical path.
+struct KlArgs {
+    const double* theta;
+    const ModelDev* md;
+    int n_src, blocks;
+    double* kl;
+    double* klg;
+    int32_t* status;
+};
+
 template <int MODE, int NPAIR>
 __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x2(const WorkItem* __restrict__ items,
                                                                 const int32_t* __restrict__ idx,
@@ -1118,9 +1130,26 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x
                                                                 float* __restrict__ emap,
                                                                 float* __restrict__ vmap,
                                                                 double* __restrict__ part,
-                                                                double* __restrict__ item_ll) {
+                                                                double* __restrict__ item_ll,
+                                                                KlArgs kl) {
+    constexpr int WARPS = CHUNK / (2 * NPAIR) / 32;
+    if ((int)blockIdx.x < kl.blocks) {
+        __shared__ double kth[WARPS][NP], kg[WARPS][NP];
+        __shared__ float kthr[WARPS][NP];
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int s = (int)blockIdx.x * WARPS + w;
+        if (s >= kl.n_src) return;   // whole warps leave; no block barrier in this branch
+        for (int i = lane; i < NP; i += 32) {
+            const double v = kl.theta[(size_t)NP * s + i];
+            kth[w][i] = v;
+            kthr[w][i] = (float)v;
+        }
+        __syncwarp();
+        prep_kl<float>(s, kth[w], kthr[w], kl.md, kl.kl, kl.klg, kl.status, kg[w]);
+        return;
+    }
     __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    const int item = idx[blockIdx.x];
+    const int item = idx[blockIdx.x - kl.blocks];
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
@@ -1414,18 +1443,23 @@ static int cap_padding(const void* kernel, int threads, int cap) {
 }
 
 template <int NPAIR>
-static void fused_x2(const DevProblem& P, int mode, cudaStream_t st) {
+static void fused_x2(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta) {
     constexpr int NT = CHUNK / (2 * NPAIR);
+    constexpr int WARPS = NT / 32;
+    KlArgs kl{d_theta, P.model, P.n_src, 0, P.kl, P.kl_grad, P.status};
+    if (d_theta && P.kl_grad) kl.blocks = (P.n_src + WARPS - 1) / WARPS;
+    const int grid = P.n_single + kl.blocks;
+    if (grid == 0) return;
     if (mode == MODE_LL) {
         const int pad = cap_padding((const void*)k_fused_x2<MODE_LL, NPAIR>, NT, P.fused_cap);
-        k_fused_x2<MODE_LL, NPAIR><<<P.n_single, NT, pad, st>>>(
+        k_fused_x2<MODE_LL, NPAIR><<<grid, NT, pad, st>>>(
             P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll, kl);
     } else {
         const int pad = cap_padding((const void*)k_fused_x2<MODE_GRAD, NPAIR>, NT, P.fused_cap);
-        k_fused_x2<MODE_GRAD, NPAIR><<<P.n_single, NT, pad, st>>>(
+        k_fused_x2<MODE_GRAD, NPAIR><<<grid, NT, pad, st>>>(
             P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll);
+            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll, kl);
     }
 }
 
@@ -1522,11 +1556,10 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st, 
 // The fused map + adjoint pass over the items whose pixels only their own patch covers
 // (FP32; the packed kernel with the adjoint's pair count: two pixels per thread unless
 // the adjoint is tuned to four).
-cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st) {
-    if (P.n_single == 0) return cudaSuccess;
+cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta) {
     const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7) fused_x2<2>(P, mode, st);
-    else fused_x2<1>(P, mode, st);
+    if (code == 5 || code == 7) fused_x2<2>(P, mode, st, d_theta);
+    else fused_x2<1>(P, mode, st, d_theta);
     return cudaGetLastError();
 }
 
