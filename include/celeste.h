@@ -131,8 +131,9 @@ int64_t celeste_source_pixels(const celeste_problem* prob);
 /*
  * Work decomposition of a problem (host read, no GPU work), for cost accounting:
  * out[0] sources, [1] patches, [2] work items (<= 256 pixels of one patch each),
- * [3] items whose every pixel only their own patch covers (they take the fused FP32 map +
- * adjoint pass), [4] source-pixels in those items, [5] 16 x 16 tiles covered by two or
+ * [3] work items of singly covered pixels in the FP32 value / gradient path (each patch's
+ * pixels that no other patch covers, in items of <= 256; they take the fused map +
+ * adjoint pass), [4] singly covered source-pixels, [5] 16 x 16 tiles covered by two or
  * more patches (the gather's cells), [6] source-pixels in all.  Writes min(n, 7) entries;
  * returns the number written, or CELESTE_ERR_ARG for a null problem / out.
  */

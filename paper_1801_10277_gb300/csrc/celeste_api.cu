@@ -185,7 +185,7 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     // the total (per-item ll sums - KL) follows on the side stream.  The two streams write
     // disjoint pixels and items, so the results do not depend on how the kernels
     // interleave.
-    const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.idx_single;
+    const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.sitems;
     if (fused) {
         // st:   prep (tables) -> map pass (other items) -> gather + adjoint (other items)
         //       -> finalize (after the fused pass)
@@ -196,7 +196,7 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
         CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_prep, 0));
         CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd, d_theta); }));
         CEL_CUDA(cudaEventRecord(pr->ev_fused, sd));
-        CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib(P, precision, st, P.idx_mixed, P.n_mixed); }));
+        CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib_split(P, st); }));
         CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,
                        [&] { return launch_gather_adjoint(P, mode, st); }));
         if (d_total) {
@@ -206,9 +206,7 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
         }
         CEL_CUDA(cudaEventRecord(pr->ev_join, sd));
         CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_fused, 0));
-        CEL_CUDA(timed(pr, "finalize", st, [&] {
-            return launch_finalize(P, d_theta, precision, mode, nullptr, d_local, d_grad, d_hess, st);
-        }));
+        CEL_CUDA(timed(pr, "finalize", st, [&] { return launch_finalize_split(P, mode, d_local, d_grad, st); }));
         CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_join, 0));
         return CELESTE_OK;
     }
@@ -320,7 +318,7 @@ int64_t celeste_source_pixels(const celeste_problem* pr) { return pr ? pr->P.n_s
 int32_t celeste_problem_stats(const celeste_problem* pr, int64_t* out, int32_t n) {
     if (!pr || !out) return fail(CELESTE_ERR_ARG, "null problem or output");
     const DevProblem& P = pr->P;
-    const int64_t v[7] = {P.n_src, P.n_patch, P.n_item, P.n_single, pr->sp_single, P.n_tile, P.n_sp};
+    const int64_t v[7] = {P.n_src, P.n_patch, P.n_item, P.n_ssingle, pr->sp_single, P.n_tile, P.n_sp};
     const int m = n < 7 ? (n > 0 ? n : 0) : 7;
     for (int i = 0; i < m; ++i) out[i] = v[i];
     return m;
@@ -481,14 +479,29 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                         c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx] == 1;
         }
     }
-    // items whose every pixel is singly covered take the fused map + adjoint pass
-    std::vector<int32_t> idx_single, idx_mixed;
-    for (int i = 0; i < (int)items.size(); ++i) {
-        const WorkItem& w = items[i];
-        const uint8_t* f = single.data() + geo[w.patch].sp_off + w.q0;
-        bool all = true;
-        for (int q = 0; q < w.n && all; ++q) all = f[q] != 0;
-        (all ? idx_single : idx_mixed).push_back(i);
+    // the split item set: per source, per patch, the singly covered pixels (fused pass)
+    // then the multiply covered ones, each list cut into items of <= CHUNK pixels
+    std::vector<WorkItem> sitems;
+    std::vector<int32_t> spix, sitem_off(1, 0), sidx_single, sidx_multi;
+    spix.reserve((size_t)n_sp);
+    int64_t sp_single = 0;
+    for (int s = 0; s < n_src; ++s) {
+        for (int p = patch_offsets[s]; p < patch_offsets[s + 1]; ++p) {
+            const PatchGeo& g = geo[p];
+            const uint8_t* f = single.data() + g.sp_off;
+            for (int pass = 0; pass < 2; ++pass) {
+                const int first = (int)spix.size();
+                for (int q = 0; q < g.w * g.h; ++q)
+                    if ((f[q] != 0) == (pass == 0)) spix.push_back(q);
+                const int cnt = (int)spix.size() - first;
+                for (int o = 0; o < cnt; o += CHUNK) {
+                    (pass == 0 ? sidx_single : sidx_multi).push_back((int32_t)sitems.size());
+                    sitems.push_back({p, first + o, std::min(CHUNK, cnt - o), s});
+                }
+                if (pass == 0) sp_single += cnt;
+            }
+        }
+        sitem_off.push_back((int32_t)sitems.size());
     }
     // tiles: per image a dense grid of TILE x TILE cells, each with its covering patches
     std::vector<Tile> tiles;
@@ -591,15 +604,31 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     uint8_t* d_single;
     if ((st = dupload(pr, &d_single, single.data(), single.size()))) return bail(st);
     P.single = d_single;
-    int32_t *d_is = nullptr, *d_im = nullptr;
-    if ((st = dupload(pr, &d_is, idx_single.data(), idx_single.size()))) return bail(st);
-    if ((st = dupload(pr, &d_im, idx_mixed.data(), idx_mixed.size()))) return bail(st);
-    P.idx_single = d_is;
-    P.idx_mixed = d_im;
-    P.n_single = (int)idx_single.size();
-    P.n_mixed = (int)idx_mixed.size();
-    pr->sp_single = 0;
-    for (int32_t i : idx_single) pr->sp_single += items[i].n;
+    if (!sitems.empty()) {
+        WorkItem* d_sit = nullptr;
+        int32_t *d_spix = nullptr, *d_soff = nullptr, *d_ss = nullptr, *d_sm = nullptr;
+        if ((st = dupload(pr, &d_sit, sitems.data(), sitems.size()))) return bail(st);
+        if ((st = dupload(pr, &d_spix, spix.data(), spix.size()))) return bail(st);
+        if ((st = dupload(pr, &d_soff, sitem_off.data(), sitem_off.size()))) return bail(st);
+        if ((st = dupload(pr, &d_ss, sidx_single.data(), sidx_single.size()))) return bail(st);
+        if ((st = dupload(pr, &d_sm, sidx_multi.data(), sidx_multi.size()))) return bail(st);
+        P.sitems = d_sit; P.spix = d_spix; P.sitem_off = d_soff;
+        P.sidx_single = d_ss; P.sidx_multi = d_sm;
+        P.n_sitem = (int)sitems.size();
+        P.n_ssingle = (int)sidx_single.size();
+        P.n_smulti = (int)sidx_multi.size();
+        void* q;
+        if ((st = dalloc(pr, &q, sizeof(double) * NPART * (size_t)P.n_sitem))) return bail(st);
+        P.spart = (double*)q;
+        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
+        P.sitem_ll = (double*)q;
+        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
+        P.sitem_own = (double*)q;
+        if (cudaMemset(P.sitem_ll, 0, sizeof(double) * P.n_sitem) != cudaSuccess ||
+            cudaMemset(P.sitem_own, 0, sizeof(double) * P.n_sitem) != cudaSuccess)
+            return bail(fail(CELESTE_ERR_CUDA, "memset"));
+    }
+    pr->sp_single = sp_single;
     if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
     if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
@@ -620,10 +649,6 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.tile_ll = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
     P.item_ll = (double*)p;
-    if ((st = dalloc(pr, &p, sizeof(double) * (size_t)P.n_item))) return bail(st);
-    P.item_own = (double*)p;
-    if (P.n_item && cudaMemset(P.item_own, 0, sizeof(double) * P.n_item) != cudaSuccess)
-        return bail(fail(CELESTE_ERR_CUDA, "memset"));
 
     if ((st = dalloc(pr, &p, sizeof(double) * (size_t)n_src))) return bail(st);
     P.kl = (double*)p;
@@ -782,11 +807,16 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     // same kernels as celeste_elbo_grad run (the fused pass over the singly covered items,
     // whose maps it rewrites with the same values, and the adjoint over the others), so
     // the gradient is bit-identical to the one-call gradient.
-    const bool fused = precision == CELESTE_FP32_ACC64 && P.idx_single;
-    if (fused) CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
-    CEL_CUDA(timed(pr, "adjoint", st, [&] {
-        return fused ? launch_adjoint_mixed_maps(P, st) : launch_adjoint(P, precision, MODE_GRAD, st);
-    }));
+    const bool fused = precision == CELESTE_FP32_ACC64 && P.sitems;
+    if (fused) {
+        CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
+        CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint_mixed_maps(P, st); }));
+        CEL_CUDA(timed(pr, "finalize", st, [&] {
+            return launch_finalize_split(P, MODE_GRAD, d_elbo_per_source, d_grad, st);
+        }));
+        return CELESTE_OK;
+    }
+    CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
     CEL_CUDA(timed(pr, "finalize", st, [&] {
         return launch_finalize(P, d_theta, precision, MODE_GRAD, nullptr, d_elbo_per_source, d_grad,
                                nullptr, st);
@@ -817,12 +847,14 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     cudaError_t e = cudaSuccess;
     // with the fused pass (FP32 value + gradient) contrib runs over the mixed items and
     // the adjoint stage is the fused kernel plus the adjoint over the mixed items
-    const bool fused = P.idx_single != nullptr;
-    const int32_t* rest = fused ? P.idx_mixed : nullptr;
-    const int n_rest = fused ? P.n_mixed : -1;
+    // (the split item set's kernels follow the adjoint code's pair count)
+    const bool fused = P.sitems != nullptr;
+    const int32_t* rest = nullptr;
+    const int n_rest = -1;
     auto adjoint_stage = [&]() {
         if (!fused) return launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
         cudaError_t r = launch_fused(P, MODE_GRAD, st);
+        if (r == cudaSuccess) r = launch_contrib_split(P, st);
         if (r == cudaSuccess) r = launch_gather_adjoint(P, MODE_GRAD, st);
         return r;
     };

@@ -87,6 +87,7 @@ __device__ __forceinline__ double sum_strided4(const double* __restrict__ a, int
 __device__ __forceinline__ void finalize_source(int s, int n_src, int mode,
                                                 const PatchGeo* __restrict__ geo,
                                                 const int32_t* __restrict__ patch_off,
+                                                const int32_t* __restrict__ item_off,
                                                 const double* __restrict__ part,
                                                 const double* __restrict__ item_ll,
                                                 const double* __restrict__ tile_ll, int n_tile,
@@ -99,12 +100,21 @@ __device__ __forceinline__ void finalize_source(int s, int n_src, int mode,
                                                 double* __restrict__ total_out) {
     const int t = threadIdx.x, c = t % FZ_LANES, sl = t / FZ_LANES;
     __shared__ double red[FZ_SLICES][FZ_LANES];
-    const int pa = patch_off[s], pb = patch_off[s + 1];
+    // the source's items: item_off (the split item set) or its patches' items
+    int i0 = 0, i1 = 0;
+    if (item_off) {
+        i0 = item_off[s];
+        i1 = item_off[s + 1];
+    } else {
+        const int pa = patch_off[s], pb = patch_off[s + 1];
+        if (pb > pa) {
+            i0 = geo[pa].item0;
+            const PatchGeo gl = geo[pb - 1];
+            i1 = gl.item0 + gl.nitem;
+        }
+    }
     double acc = 0.0;
-    if (pb > pa) {
-        const int i0 = geo[pa].item0;
-        const PatchGeo gl = geo[pb - 1];
-        const int i1 = gl.item0 + gl.nitem;
+    if (i1 > i0) {
         const int col = (mode >= MODE_GRAD && c < NP) ? PART_TH + c : (c == 48 ? PART_LL : -1);
         if (col >= 0) acc = sum_strided4(part + col, i0 + sl, i1, FZ_SLICES, NPART);
         else if (c == 49 && total_out && item_ll) acc = sum_strided4(item_ll, i0 + sl, i1, FZ_SLICES);

@@ -178,8 +178,6 @@ struct DevProblem {
     void* vmap;
     const uint8_t* single;   // per (source, pixel): 1 when no other patch covers the pixel (nullable)
     double* item_ll;         // per work item: ll summed over its singly covered pixels
-    double* item_own;        // per work item: ll of the multiply covered pixels it owns (gather +
-                             // adjoint pass; the first covering patch owns a pixel)
     double* item_part;
     double* tile_ll;
     double* kl;
@@ -188,9 +186,20 @@ struct DevProblem {
     int32_t* done;           // k_finalize completion counter, 0 between launches
     double* tot_part;        // [64] k_total slice sums
     int32_t* tot_done;       // k_total completion counter, 0 between launches
-    const int32_t* idx_single;   // items whose every pixel only their own patch covers (nullable)
-    const int32_t* idx_mixed;    // the other items
-    int n_single, n_mixed;
+    // The split item set of the FP32 value / gradient path: each patch's pixels split into
+    // the singly covered ones and the others, each list cut into items of <= CHUNK pixels
+    // (WorkItem.q0 indexes spix, which holds patch-relative pixel indices); a source's
+    // split items are contiguous (sitem_off).  Nullable (no split set: sitems null).
+    const WorkItem* sitems;
+    const int32_t* spix;
+    const int32_t* sitem_off;    // [n_src + 1]
+    const int32_t* sidx_single;  // split items of singly covered pixels (fused pass)
+    const int32_t* sidx_multi;   // split items of multiply covered pixels (map pass, gather + adjoint)
+    int n_sitem, n_ssingle, n_smulti;
+    double* spart;               // [n_sitem][NPART] partials of the split items
+    double* sitem_ll;            // ll of a singly covered item (0 for the others)
+    double* sitem_own;           // ll of the multiply covered pixels an item owns (the first
+                                 // covering patch owns a pixel; 0 for singly covered items)
     int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
                              // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;
@@ -214,14 +223,20 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
 // contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);
-// FP32 map pass + adjoint in one kernel over P.idx_single (mode MODE_LL or MODE_GRAD);
+// FP32 map pass + adjoint in one kernel over the split items of singly covered pixels
+// (mode MODE_LL or MODE_GRAD);
 // with d_theta, the same launch also computes the KL (value, gradient, domain check)
 cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta = nullptr);
-// FP32 gather + adjoint in one kernel over P.idx_mixed (after the map pass over them)
+// FP32 map pass over the split items of multiply covered pixels (E_s, Var_s)
+cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st);
+// FP32 gather + adjoint in one kernel over the same items (after their map pass)
 cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st);
-// FP32 adjoint over P.idx_mixed from the maps (same kernel as the gather + adjoint pass)
+// FP32 adjoint over the same items from the maps (same kernel body as the gather + adjoint)
 cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st);
-// total over the fused path's per-item sums: item_own + item_ll - KL
+// per-source epilogue over the split item set (FP32 value / gradient path)
+cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local, double* d_grad,
+                                  cudaStream_t st);
+// total over the split items' sums: sitem_own + sitem_ll - KL
 cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,

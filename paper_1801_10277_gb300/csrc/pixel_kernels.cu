@@ -622,18 +622,21 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
                                                 const float* __restrict__ pixels,
                                                 const float* __restrict__ sky_map,
                                                 float* __restrict__ emap, float* __restrict__ vmap,
-                                                double* __restrict__ item_ll) {
+                                                double* __restrict__ item_ll,
+                                                const int32_t* __restrict__ pix = nullptr) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
     const int npsf = im.npsf;
     const int t = threadIdx.x;
-    int xs[PPT], ys[PPT];
+    int xs[PPT], ys[PPT], qs[PPT];
     bool ok[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
         ok[p] = l < it.n;
-        const int q = it.q0 + (ok[p] ? l : 0);
+        const int qi = it.q0 + (ok[p] ? l : 0);
+        const int q = pix ? pix[qi] : qi;   // patch-relative pixel (split items list them)
+        qs[p] = q;
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
     }
@@ -695,8 +698,7 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
         const float e = a0 * f0 + a1 * f1;
         const float v = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
                         a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
-        const int q = it.q0 + t + p * NT;
-        const int64_t sp = g.sp_off + q;
+        const int64_t sp = g.sp_off + qs[p];
         if (single && single[sp]) {
             const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
             const float E = (im.has_sky_map ? sky_map[m] : (float)im.sky) + e;
@@ -745,6 +747,7 @@ struct GatherArgs {
     float* emap;
     float* vmap;
     double* item_own;
+    const int32_t* pix;
 };
 
 template <int MODE, int NPAIR, int SRC = SRC_MAPS>
@@ -758,7 +761,8 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                                                 float* __restrict__ emap_out = nullptr,
                                                 float* __restrict__ vmap_out = nullptr,
                                                 double* __restrict__ item_ll = nullptr,
-                                                const GatherArgs* ga = nullptr) {
+                                                const GatherArgs* ga = nullptr,
+                                                const int32_t* __restrict__ pix = nullptr) {
     constexpr bool FUSED = SRC == SRC_OWN;
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
     constexpr int NT = CHUNK / (2 * NPAIR);
@@ -778,7 +782,8 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
         ok[p] = l < it.n;
-        const int q = it.q0 + (ok[p] ? l : 0);
+        const int qi = it.q0 + (ok[p] ? l : 0);
+        const int q = pix ? pix[qi] : qi;   // patch-relative pixel (split items list them)
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
         const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
@@ -1077,14 +1082,36 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
                                                                   const float* __restrict__ tbl,
                                                                   const float* __restrict__ emap,
                                                                   const float* __restrict__ vmap,
-                                                                  double* __restrict__ part) {
+                                                                  double* __restrict__ part,
+                                                                  const int32_t* __restrict__ pix) {
     __shared__ __align__(16) float2 sT2[TBL_STRIDE];
     const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part);
+    adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, pix);
+}
+
+// map pass over split items of multiply covered pixels: E_s, Var_s for the gather
+template <int NPAIR>
+__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_split(const WorkItem* __restrict__ items,
+                                                                     const int32_t* __restrict__ idx,
+                                                                     const int32_t* __restrict__ pix,
+                                                                     const PatchGeo* __restrict__ geo,
+                                                                     const ImgMeta* __restrict__ img, int nprof,
+                                                                     const float* __restrict__ tbl,
+                                                                     float* __restrict__ spE,
+                                                                     float* __restrict__ spV) {
+    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    const int item = idx[blockIdx.x];
+    const WorkItem it = items[item];
+    const PatchGeo g = geo[it.patch];
+    const ImgMeta& im = img[g.img];
+    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
+    contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, pix);
 }
 
 // gather + adjoint in one, for the items listed in idx (some pixel covered twice or more)
@@ -1103,7 +1130,7 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_gadjoint_x2(const WorkI
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
     adjoint_x2_item<MODE, NPAIR, SRC_GATHER>(item, it, g, im, nprof, sT2, pixels, ga.emap, ga.vmap, part,
-                                             nullptr, nullptr, nullptr, nullptr, &ga);
+                                             nullptr, nullptr, nullptr, nullptr, &ga, ga.pix);
 }
 
 // map pass + adjoint in one, for the items listed in idx (every pixel singly covered).
@@ -1131,6 +1158,7 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x
                                                                 float* __restrict__ vmap,
                                                                 double* __restrict__ part,
                                                                 double* __restrict__ item_ll,
+                                                                const int32_t* __restrict__ pix,
                                                                 KlArgs kl) {
     constexpr int WARPS = CHUNK / (2 * NPAIR) / 32;
     if ((int)blockIdx.x < kl.blocks) {
@@ -1155,7 +1183,7 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
     adjoint_x2_item<MODE, NPAIR, SRC_OWN>(item, it, g, im, nprof, sT2, pixels, nullptr, nullptr, part,
-                                          sky_map, emap, vmap, item_ll);
+                                          sky_map, emap, vmap, item_ll, nullptr, pix);
 }
 
 // ---- persistent CTAs with a work queue (tuning codes 6, 7)
@@ -1383,11 +1411,11 @@ static void adjoint_x2(const DevProblem& P, int mode, ItemSet S, cudaStream_t st
     if (mode == MODE_LL)
         k_adjoint_x2<MODE_LL, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
                                                         P.tbl32, (const float*)P.emap,
-                                                        (const float*)P.vmap, P.item_part);
+                                                        (const float*)P.vmap, P.item_part, nullptr);
     else
         k_adjoint_x2<MODE_GRAD, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
                                                           P.tbl32, (const float*)P.emap,
-                                                          (const float*)P.vmap, P.item_part);
+                                                          (const float*)P.vmap, P.item_part, nullptr);
 }
 
 template <int MODE, int NPAIR>
@@ -1448,18 +1476,18 @@ static void fused_x2(const DevProblem& P, int mode, cudaStream_t st, const doubl
     constexpr int WARPS = NT / 32;
     KlArgs kl{d_theta, P.model, P.n_src, 0, P.kl, P.kl_grad, P.status};
     if (d_theta && P.kl_grad) kl.blocks = (P.n_src + WARPS - 1) / WARPS;
-    const int grid = P.n_single + kl.blocks;
+    const int grid = P.n_ssingle + kl.blocks;
     if (grid == 0) return;
     if (mode == MODE_LL) {
         const int pad = cap_padding((const void*)k_fused_x2<MODE_LL, NPAIR>, NT, P.fused_cap);
         k_fused_x2<MODE_LL, NPAIR><<<grid, NT, pad, st>>>(
-            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll, kl);
+            P.sitems, P.sidx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.spart, P.sitem_ll, P.spix, kl);
     } else {
         const int pad = cap_padding((const void*)k_fused_x2<MODE_GRAD, NPAIR>, NT, P.fused_cap);
         k_fused_x2<MODE_GRAD, NPAIR><<<grid, NT, pad, st>>>(
-            P.items, P.idx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.item_part, P.item_ll, kl);
+            P.sitems, P.sidx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
+            (float*)P.emap, (float*)P.vmap, P.spart, P.sitem_ll, P.spix, kl);
     }
 }
 
@@ -1477,13 +1505,20 @@ template <int NPAIR>
 static void gadjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     const GatherArgs ga{P.single, P.tile_grid, P.tiles, P.tile_list, P.geo, (const float*)P.spE,
-                        (const float*)P.spE2, P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_own};
+                        (const float*)P.spE2, P.sky_map, (float*)P.emap, (float*)P.vmap, P.sitem_own,
+                        P.spix};
     if (mode == MODE_LL)
-        k_gadjoint_x2<MODE_LL, NPAIR><<<P.n_mixed, NT, 0, st>>>(P.items, P.idx_mixed, P.img, P.nprof,
-                                                               P.pixels, P.tbl32, P.item_part, ga);
+        k_gadjoint_x2<MODE_LL, NPAIR><<<P.n_smulti, NT, 0, st>>>(P.sitems, P.sidx_multi, P.img, P.nprof,
+                                                                P.pixels, P.tbl32, P.spart, ga);
     else
-        k_gadjoint_x2<MODE_GRAD, NPAIR><<<P.n_mixed, NT, 0, st>>>(P.items, P.idx_mixed, P.img, P.nprof,
-                                                                 P.pixels, P.tbl32, P.item_part, ga);
+        k_gadjoint_x2<MODE_GRAD, NPAIR><<<P.n_smulti, NT, 0, st>>>(P.sitems, P.sidx_multi, P.img, P.nprof,
+                                                                  P.pixels, P.tbl32, P.spart, ga);
+}
+
+template <int NPAIR>
+static void contrib_split(const DevProblem& P, cudaStream_t st) {
+    k_contrib_split<NPAIR><<<P.n_smulti, CHUNK / (2 * NPAIR), 0, st>>>(
+        P.sitems, P.sidx_multi, P.spix, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2);
 }
 
 // Occupancy queries of the persistent kernels, made once on the current device outside
@@ -1563,9 +1598,19 @@ cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const d
     return cudaGetLastError();
 }
 
-// gather + adjoint over P.idx_mixed (FP32, packed pairs as launch_fused picks them)
+// map pass over the split items of multiply covered pixels (FP32, packed pairs as
+// launch_fused picks them)
+cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st) {
+    if (P.n_smulti == 0) return cudaSuccess;
+    const int code = ppt_adjoint(P);
+    if (code == 5 || code == 7) contrib_split<2>(P, st);
+    else contrib_split<1>(P, st);
+    return cudaGetLastError();
+}
+
+// gather + adjoint over the split items of multiply covered pixels
 cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st) {
-    if (P.n_mixed == 0) return cudaSuccess;
+    if (P.n_smulti == 0) return cudaSuccess;
     const int code = ppt_adjoint(P);
     if (code == 5 || code == 7) gadjoint_x2<2>(P, mode, st);
     else gadjoint_x2<1>(P, mode, st);
@@ -1575,11 +1620,16 @@ cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st
 // the adjoint over P.idx_mixed from the maps, with the kernel launch_gather_adjoint uses
 // (a backward-only call then reproduces the one-call gradient bit for bit)
 cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st) {
-    if (P.n_mixed == 0) return cudaSuccess;
-    const ItemSet S{P.idx_mixed, P.n_mixed};
+    if (P.n_smulti == 0) return cudaSuccess;
     const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7) adjoint_x2<2>(P, MODE_GRAD, S, st);
-    else adjoint_x2<1>(P, MODE_GRAD, S, st);
+    if (code == 5 || code == 7)
+        k_adjoint_x2<MODE_GRAD, 2><<<P.n_smulti, CHUNK / 4, 0, st>>>(
+            P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
+            (const float*)P.vmap, P.spart, P.spix);
+    else
+        k_adjoint_x2<MODE_GRAD, 1><<<P.n_smulti, CHUNK / 2, 0, st>>>(
+            P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
+            (const float*)P.vmap, P.spart, P.spix);
     return cudaGetLastError();
 }
 

@@ -12,14 +12,15 @@ namespace cel {
 
 __global__ void __launch_bounds__(FZ_THREADS)
 k_finalize(int n_src, int mode, const PatchGeo* __restrict__ geo,
-           const int32_t* __restrict__ patch_off, const double* __restrict__ part,
+           const int32_t* __restrict__ patch_off, const int32_t* __restrict__ item_off,
+           const double* __restrict__ part,
            const double* __restrict__ item_ll, const double* __restrict__ tile_ll, int n_tile,
            const double* __restrict__ kl, const double* __restrict__ kl_grad,
            double* __restrict__ local_out, double* __restrict__ grad_out,
            double* __restrict__ src_total, int32_t* __restrict__ done,
            double* __restrict__ total_out) {
     if ((int)blockIdx.x >= n_src) return;
-    finalize_source(blockIdx.x, n_src, mode, geo, patch_off, part, item_ll, tile_ll, n_tile, kl,
+    finalize_source(blockIdx.x, n_src, mode, geo, patch_off, item_off, part, item_ll, tile_ll, n_tile, kl,
                     kl_grad, local_out, grad_out, src_total, done, total_out);
 }
 
@@ -33,9 +34,19 @@ k_total(const double* __restrict__ tile_ll, int n_tile, const double* __restrict
 cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
                                  double* d_grad, double* d_hess, cudaStream_t st);
 
-// total = item_own + item_ll - KL: the fused path's per-item sums (fixed order)
+// per-source epilogue over the split item set (no total: launch_total_items gives it)
+cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local, double* d_grad,
+                                  cudaStream_t st) {
+    if (P.n_src == 0) return cudaSuccess;
+    k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, P.geo, P.patch_off, P.sitem_off, P.spart,
+                                               nullptr, nullptr, 0, P.kl, P.kl_grad, d_local, d_grad,
+                                               P.src_total, P.done, nullptr);
+    return cudaGetLastError();
+}
+
+// total = sitem_own + sitem_ll - KL: the split items' sums (fixed order)
 cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st) {
-    k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.item_own, P.n_item, P.item_ll, P.n_item, P.kl,
+    k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.sitem_own, P.n_sitem, P.sitem_ll, P.n_sitem, P.kl,
                                                   P.n_src, P.tot_part, P.tot_done, d_total);
     return cudaGetLastError();
 }
@@ -58,7 +69,7 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int prec
         // the KL value and gradient come from k_prep of the same theta
         (void)precision;
         (void)d_theta;
-        k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, P.geo, P.patch_off, P.item_part,
+        k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, P.geo, P.patch_off, nullptr, P.item_part,
                                                    P.single ? P.item_ll : nullptr, P.tile_ll,
                                                    P.n_tile, P.kl, P.kl_grad, d_local, d_grad,
                                                    P.src_total, P.done, d_total);
