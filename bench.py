@@ -34,7 +34,7 @@ SM_COUNT = 152
 # DRAM bytes (read + write) per launch of each pixel kernel on the one-field workload, from
 # one ncu capture (profiles/k_fused_x2_field_500src.md, profiles/step_kernels_field_500src.md);
 # an entry is removed whenever its kernel changes after the capture.
-DRAM_BYTES_PER_LAUNCH = {"fused": 13.95e6, "gather_adjoint": 7.05e6, "contrib": 3.03e6}
+DRAM_BYTES_PER_LAUNCH = {}
 FP32_LANES = 128
 
 
@@ -216,8 +216,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--hess-steps", type=int, default=20)
     ap.add_argument("--no-fit", action="store_true")
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4],
+                    help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
+                         "4 sweep field; the JSON line names it")
     ap.add_argument("--tuning", default=None,
-                    help="contrib,adjoint,fused_cap codes to use instead of autotuning (e.g. 2,1,0)")
+                    help="contrib,adjoint,fused_cap,gather_sep codes to use instead of autotuning (e.g. 2,1,0,0)")
     args = ap.parse_args()
     rank, ws, dist = dist_init()
     if args.impl == "reference":
@@ -227,7 +230,10 @@ def main():
     from paper_1801_10277_gb300 import celeste as cel
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local_rank)
-    prob = synth.config(1, seed=rank_field_seed(rank))
+    if args.workload == 1:
+        prob = synth.config(1, seed=rank_field_seed(rank))
+    else:
+        prob = synth.config(args.workload)
     P = cel.Problem(prob)
     n_sp = P.source_pixels
     if args.tuning:
@@ -303,7 +309,7 @@ def main():
     clocks = clk.summary()
     peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
     achieved = achieved_k[dom]
-    traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if prob.name.startswith("field_500src") else None
+    traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if args.workload == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                 "frac": achieved / peak_fp32, "traffic": traffic, "kernel": f"{dom} (FP32)",
                 "flop_per_launch": work[dom],
@@ -395,9 +401,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": prob.name, "sources": prob.n_src, "source_pixels": n_sp,
-                       "bands": 5, "image": "2048x1489", "precision": "fp32 pixels, fp64 accumulation",
+                       "images": len(prob.images),
+                       "image": "x".join(str(v) for v in prob.images[0].pixels.shape[::-1]),
+                       "precision": "fp32 pixels, fp64 accumulation",
                        "l2": "flushed between steps (256 MiB write)",
-                       "tuning": {"contrib": tuning[0], "adjoint": tuning[1], "fused_cap": tuning[2]},
+                       "tuning": dict(zip(("contrib", "adjoint", "fused_cap", "gather_sep"), tuning)),
                        "parallelism": f"replica{ws}" if ws > 1 else "single"},
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},

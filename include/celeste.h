@@ -231,17 +231,20 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
  * next item's table prefetched by bulk asynchronous copy), reps launches each with CUDA
  * events on the problem's stream, at theta (host).  The adjoint's code also picks the
  * pair count of the fused map + adjoint pass (four pixels per thread for codes 5, 7).
- * Then, with those kernels, it times whole FP32 value + gradient evaluations for caps
- * of 0 (none), 8, 7, .., 3 resident CTAs per SM on the fused pass, which runs beside the
- * map / gather / adjoint chain of the other items and must leave it room.  The choices
- * are kept for later FP32 calls and returned (nullable outputs); celeste_set_tuning
- * restores them (codes 1 .. 7, 0 = built-in default 2; cap 0 .. 8; anything else is
- * CELESTE_ERR_ARG).
+ * Then, with those kernels, it times whole FP32 value + gradient evaluations for the
+ * schedule of the multiply covered pixels (gather_sep 0: each covering patch's adjoint
+ * gathers E and Var itself; 1: one tile-major gather, then the adjoint from the maps --
+ * better when many patches overlap) and for caps of 0 (none), 8, 7, .., 3 resident CTAs
+ * per SM on the fused pass, which runs beside that chain and must leave it room.  The
+ * choices are kept for later FP32 calls and returned (nullable outputs);
+ * celeste_set_tuning restores them (codes 1 .. 7, 0 = built-in default 2; cap 0 .. 8;
+ * gather_sep 0 or 1; anything else is CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap);
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap,
+                                int32_t* gather_sep);
 celeste_status celeste_set_tuning(celeste_problem* prob, int32_t ppt_contrib, int32_t ppt_adjoint,
-                                  int32_t fused_cap);
+                                  int32_t fused_cap, int32_t gather_sep);
 
 /* Status word written by the device-side checks of the last _device call (host read;
  * synchronises the problem's last stream).  CELESTE_OK or a negative status. */

@@ -107,9 +107,9 @@ def load(build_if_missing=False):
         getattr(L, f).restype = i32
     L.celeste_grad_device.argtypes = [vp, vp, i32, vp, vp, vp]
     L.celeste_grad_device.restype = i32
-    L.celeste_autotune.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.celeste_autotune.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     L.celeste_autotune.restype = i32
-    L.celeste_set_tuning.argtypes = [vp, i32, i32, i32]
+    L.celeste_set_tuning.argtypes = [vp, i32, i32, i32, i32]
     L.celeste_set_tuning.restype = i32
     L.celeste_device_status.argtypes = [vp]
     L.celeste_device_status.restype = i32
@@ -293,18 +293,16 @@ class Problem:
                                           self._dp(d_grad), self._dp(d_hess), self._stream()))
 
     def autotune(self, theta, reps=5):
-        """Pick the fastest FP32 kernel variants and the fused pass's CTA cap; returns
-        (contrib code, adjoint code, fused cap)."""
+        """Pick the fastest FP32 kernel variants and schedule; returns (contrib code,
+        adjoint code, fused-pass CTA cap, gather_sep)."""
         self.generation += 1
-        a = C.c_int32()
-        b = C.c_int32()
-        c = C.c_int32()
-        _check(self.L.celeste_autotune(self.h, _p(self._theta(theta)), reps, C.byref(a), C.byref(b),
-                                       C.byref(c)))
-        return a.value, b.value, c.value
+        out = [C.c_int32() for _ in range(4)]
+        _check(self.L.celeste_autotune(self.h, _p(self._theta(theta)), reps,
+                                       *(C.byref(o) for o in out)))
+        return tuple(o.value for o in out)
 
-    def set_tuning(self, ppt_contrib, ppt_adjoint, fused_cap=0):
-        _check(self.L.celeste_set_tuning(self.h, ppt_contrib, ppt_adjoint, fused_cap))
+    def set_tuning(self, ppt_contrib, ppt_adjoint, fused_cap=0, gather_sep=0):
+        _check(self.L.celeste_set_tuning(self.h, ppt_contrib, ppt_adjoint, fused_cap, gather_sep))
 
     def profile(self, on=True):
         _check(self.L.celeste_profile_enable(self.h, 1 if on else 0))

@@ -197,8 +197,14 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
         CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd, d_theta); }));
         CEL_CUDA(cudaEventRecord(pr->ev_fused, sd));
         CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib_split(P, st); }));
-        CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,
-                       [&] { return launch_gather_adjoint(P, mode, st); }));
+        if (P.gather_sep) {
+            CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
+            CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
+                           [&] { return launch_adjoint_mixed_maps(P, mode, st); }));
+        } else {
+            CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,
+                           [&] { return launch_gather_adjoint(P, mode, st); }));
+        }
         if (d_total) {
             CEL_CUDA(cudaEventRecord(pr->ev_gather, st));
             CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_gather, 0));
@@ -243,7 +249,7 @@ celeste_status run_cached(celeste_problem* pr, const double* d_theta, int precis
         if (reset_status) CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
         return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
     }
-    celeste_problem::GraphKey key{precision, mode, P.tune_contrib, P.tune_adjoint, P.fused_cap,
+    celeste_problem::GraphKey key{precision, mode, P.tune_contrib, P.tune_adjoint, P.fused_cap | (P.gather_sep << 8),
                                   {d_theta, d_total, d_local, d_grad, d_hess}};
     if (!reset_status) key.mode |= 0x100;
     cudaGraphExec_t exec = nullptr;
@@ -810,7 +816,7 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     const bool fused = precision == CELESTE_FP32_ACC64 && P.sitems;
     if (fused) {
         CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
-        CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint_mixed_maps(P, st); }));
+        CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint_mixed_maps(P, MODE_GRAD, st); }));
         CEL_CUDA(timed(pr, "finalize", st, [&] {
             return launch_finalize_split(P, MODE_GRAD, d_elbo_per_source, d_grad, st);
         }));
@@ -825,7 +831,8 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
 }
 
 celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap) {
+                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap,
+                                int32_t* gather_sep) {
     if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
     celeste_status s = check_theta_host(theta, pr->P.n_src);
     if (s) return s;
@@ -884,13 +891,15 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     P.tune_adjoint = pick_a;
     // the fused pass's CTA cap per SM, timed on whole value + gradient evaluations (it
     // trades the fused pass's own speed against room for the concurrent chain)
-    int pick_cap = 0;
+    int pick_cap = 0, pick_sep = 0;
     if (e == cudaSuccess && fused && ensure_out(pr) == CELESTE_OK) {
-        const int caps[7] = {0, 8, 7, 6, 5, 4, 3};
+        // (sep, cap) pairs: the gather inside the adjoint or tile-major, then the cap
+        const int combos[9][2] = {{0, 0}, {1, 0}, {0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {1, 6}};
         float best = 1e30f;
         double* o = pr->d_out;
-        for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
-            P.fused_cap = caps[ci];
+        for (int ci = 0; ci < 9 && e == cudaSuccess; ++ci) {
+            P.gather_sep = combos[ci][0];
+            P.fused_cap = combos[ci][1];
             celeste_status rs = run(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1,
                                     o + 1 + P.n_src, nullptr, st);
             float t = 0.f;
@@ -902,23 +911,30 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
             if (e == cudaSuccess) e = cudaEventRecord(b, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(b);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-            if (e == cudaSuccess && t < best) { best = t; pick_cap = caps[ci]; }
+            if (e == cudaSuccess && t < best) {
+                best = t;
+                pick_sep = combos[ci][0];
+                pick_cap = combos[ci][1];
+            }
         }
     }
     P.fused_cap = pick_cap;
+    P.gather_sep = pick_sep;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     if (ppt_contrib) *ppt_contrib = pick_c;
     if (ppt_adjoint) *ppt_adjoint = pick_a;
     if (fused_cap) *fused_cap = pick_cap;
+    if (gather_sep) *gather_sep = pick_sep;
     return CELESTE_OK;
 }
 
 celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint,
-                                  int32_t fused_cap) {
+                                  int32_t fused_cap, int32_t gather_sep) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
     if (fused_cap < 0 || fused_cap > 8) return fail(CELESTE_ERR_ARG, "fused_cap must be 0 .. 8");
+    if (gather_sep != 0 && gather_sep != 1) return fail(CELESTE_ERR_ARG, "gather_sep must be 0 or 1");
     auto okp = [](int v) { return v >= 0 && v <= 7; };
     if (!okp(ppt_contrib) || !okp(ppt_adjoint))
         return fail(CELESTE_ERR_ARG,
@@ -927,6 +943,7 @@ celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int3
     pr->P.tune_contrib = ppt_contrib;
     pr->P.tune_adjoint = ppt_adjoint;
     pr->P.fused_cap = fused_cap;
+    pr->P.gather_sep = gather_sep;
     return CELESTE_OK;
 }
 

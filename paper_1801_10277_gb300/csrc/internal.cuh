@@ -159,6 +159,8 @@ struct DevProblem {
     int32_t n_img, n_src, n_patch, n_item, n_tile, npsf_max, nprof;
     int32_t tune_contrib, tune_adjoint;   // FP32 pixels per thread (0 = default)
     int32_t fused_cap;                    // resident CTAs per SM of the fused pass (0 = no cap)
+    int32_t gather_sep;                   // split path: 0 gather inside the adjoint of the multiply
+                                          // covered items, 1 tile-major k_gather then the adjoint
     int64_t n_px, n_sp;
     const ImgMeta* img;
     const float* pixels;
@@ -232,11 +234,12 @@ cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st);
 // FP32 gather + adjoint in one kernel over the same items (after their map pass)
 cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st);
 // FP32 adjoint over the same items from the maps (same kernel body as the gather + adjoint)
-cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st);
+cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, int mode, cudaStream_t st);
 // per-source epilogue over the split item set (FP32 value / gradient path)
 cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local, double* d_grad,
                                   cudaStream_t st);
-// total over the split items' sums: sitem_own + sitem_ll - KL
+// total over the split items' sums: sitem_own + sitem_ll - KL (gather_sep: the tile sums
+// of k_gather instead of sitem_own)
 cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,

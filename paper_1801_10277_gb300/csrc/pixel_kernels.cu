@@ -1619,17 +1619,24 @@ cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st
 
 // the adjoint over P.idx_mixed from the maps, with the kernel launch_gather_adjoint uses
 // (a backward-only call then reproduces the one-call gradient bit for bit)
-cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, cudaStream_t st) {
+template <int MODE, int NPAIR>
+static void adjoint_split_maps(const DevProblem& P, cudaStream_t st) {
+    k_adjoint_x2<MODE, NPAIR><<<P.n_smulti, CHUNK / (2 * NPAIR), 0, st>>>(
+        P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
+        (const float*)P.vmap, P.spart, P.spix);
+}
+
+cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, int mode, cudaStream_t st) {
     if (P.n_smulti == 0) return cudaSuccess;
     const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7)
-        k_adjoint_x2<MODE_GRAD, 2><<<P.n_smulti, CHUNK / 4, 0, st>>>(
-            P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
-            (const float*)P.vmap, P.spart, P.spix);
-    else
-        k_adjoint_x2<MODE_GRAD, 1><<<P.n_smulti, CHUNK / 2, 0, st>>>(
-            P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
-            (const float*)P.vmap, P.spart, P.spix);
+    const bool two = code == 5 || code == 7;
+    if (mode == MODE_LL) {
+        if (two) adjoint_split_maps<MODE_LL, 2>(P, st);
+        else adjoint_split_maps<MODE_LL, 1>(P, st);
+    } else {
+        if (two) adjoint_split_maps<MODE_GRAD, 2>(P, st);
+        else adjoint_split_maps<MODE_GRAD, 1>(P, st);
+    }
     return cudaGetLastError();
 }
 

@@ -46,8 +46,12 @@ cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local
 
 // total = sitem_own + sitem_ll - KL: the split items' sums (fixed order)
 cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st) {
-    k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.sitem_own, P.n_sitem, P.sitem_ll, P.n_sitem, P.kl,
-                                                  P.n_src, P.tot_part, P.tot_done, d_total);
+    if (P.gather_sep)
+        k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.tile_ll, P.n_tile, P.sitem_ll, P.n_sitem, P.kl,
+                                                      P.n_src, P.tot_part, P.tot_done, d_total);
+    else
+        k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.sitem_own, P.n_sitem, P.sitem_ll, P.n_sitem, P.kl,
+                                                      P.n_src, P.tot_part, P.tot_done, d_total);
     return cudaGetLastError();
 }
 

@@ -94,14 +94,16 @@ def test_autotuned_variants_agree(cel):
     _, o_g, _ = orc.derivs(prob.theta)
     P = cel.Problem(prob)
     for ppt in (1, 2, 3, 4, 5, 6, 7):
-        for cap in (0, 3):
-            P.set_tuning(ppt, ppt, cap)
+        for cap, sep in ((0, 0), (3, 1)):
+            P.set_tuning(ppt, ppt, cap, sep)
             tot, loc, g = P.elbo_grad(prob.theta, precision=cel.FP32)
-            assert rel(tot, o_tot) <= 1e-5 and rel_l2(g, o_g) <= 1e-4, (ppt, cap)
-    c, a, cap = P.autotune(prob.theta)
-    assert c in range(1, 8) and a in range(1, 8) and cap in (0, 8, 7, 6, 5, 4, 3)
+            assert rel(tot, o_tot) <= 1e-5 and rel_l2(g, o_g) <= 1e-4, (ppt, cap, sep)
+    c, a, cap, sep = P.autotune(prob.theta)
+    assert c in range(1, 8) and a in range(1, 8) and cap in (0, 8, 7, 6, 5, 4, 3) and sep in (0, 1)
     with pytest.raises(cel.CelesteError):
         P.set_tuning(2, 2, 9)
+    with pytest.raises(cel.CelesteError):
+        P.set_tuning(2, 2, 0, 2)
     P.close()
 
 
