@@ -239,27 +239,35 @@ __device__ bool block_chol(const double* B, double lam, double* L, int n, int* f
     return true;
 }
 
-// forward (L y = b) and backward (L^T x = y) substitution by one thread
-__device__ void chol_solve(const double* L, const double* b, double* x, int n) {
-    double y[TRN];
-    for (int i = 0; i < n; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
-        y[i] = s / L[i * n + i];
+// Warp-level triangular solves (every lane of the calling warp calls them): lane l holds
+// rows l and l + 32 of the right-hand side; one column of L per step (column-oriented
+// substitution), the solved entry broadcast by shuffle.  invd[k] = 1 / L[k][k].
+__device__ void warp_fwd(const double* L, const double* invd, const double* b, double* y, int n) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    double r0 = lane < n ? b[lane] : 0.0, r1 = lane + 32 < n ? b[lane + 32] : 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
+        const double yk = rk * invd[k];
+        if (lane == (k & 31)) y[k] = yk;
+        if (lane > k && lane < n) r0 -= L[lane * n + k] * yk;
+        if (lane + 32 > k && lane + 32 < n) r1 -= L[(lane + 32) * n + k] * yk;
     }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
-        x[i] = s / L[i * n + i];
-    }
+    __syncwarp();
 }
 
-__device__ void fwd_solve(const double* L, const double* b, double* y, int n) {
-    for (int i = 0; i < n; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
-        y[i] = s / L[i * n + i];
+__device__ void warp_bwd(const double* L, const double* invd, const double* y, double* x, int n) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    double r0 = lane < n ? y[lane] : 0.0, r1 = lane + 32 < n ? y[lane + 32] : 0.0;
+    for (int k = n - 1; k >= 0; --k) {
+        const double rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
+        const double xk = rk * invd[k];
+        if (lane == (k & 31)) x[k] = xk;
+        if (lane < k) r0 -= L[k * n + lane] * xk;
+        if (lane + 32 < k) r1 -= L[k * n + lane + 32] * xk;
     }
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(TR_THREADS)
@@ -356,25 +364,29 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         Ht[idx] = s;
     }
     __syncthreads();
-    // convergence checks
-    if (tid == 0) {
-        double gmax = 0.0;
-        bool fin = isfinite(f_in[b]);
-        for (int a = 0; a < TRN; ++a) {
-            gmax = fmax(gmax, fabs(gt[a]));
-            fin = fin && isfinite(gt[a]);
+    // convergence checks (every thread a share of the entries)
+    {
+        bool bad = false;
+        for (int i = tid; i < TRN * TRN; i += blockDim.x) bad = bad || !isfinite(Ht[i]);
+        bool gbig = false;
+        if (tid < TRN) {
+            bad = bad || !isfinite(gt[tid]);
+            gbig = !(fabs(gt[tid]) <= o.grad_tol);
         }
-        for (int a = 0; a < TRN * TRN && fin; ++a) fin = isfinite(Ht[a]);
-        done = 0;
-        if (!fin) {
-            S.status = ST_NONFINITE;
-            done = 1;
-        } else if (gmax <= o.grad_tol) {
-            S.status = ST_CONVERGED;
-            done = 1;
+        const int any_bad = __syncthreads_or(bad || (tid == 0 && !isfinite(f_in[b])));
+        const int any_big = __syncthreads_or(gbig);
+        if (tid == 0) {
+            done = 0;
+            if (any_bad) {
+                S.status = ST_NONFINITE;
+                done = 1;
+            } else if (!any_big) {
+                S.status = ST_CONVERGED;
+                done = 1;
+            }
+            S.f = f_in[b];
+            S.kl = kl_in[b];
         }
-        S.f = f_in[b];
-        S.kl = kl_in[b];
     }
     __syncthreads();
     if (done) {
@@ -389,12 +401,19 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     for (int i = tid; i < TRN; i += blockDim.x) cvec[i] = -gt[i];
     __syncthreads();
     const double Delta = S.delta;
+    // |c|, the largest absolute row sum of B and its smallest diagonal entry: one row per
+    // thread, then combined in row order
+    __shared__ double rs[TRN], invd[TRN];
+    if (tid < TRN) {
+        double r = 0.0;
+        for (int j = 0; j < TRN; ++j) r += fabs(Ht[tid * TRN + j]);
+        rs[tid] = r;
+    }
+    __syncthreads();
     double cn = 0.0, bnorm = 0.0, bdmin = 1e300;
     for (int i = 0; i < TRN; ++i) {
         cn += cvec[i] * cvec[i];
-        double r = 0.0;
-        for (int j = 0; j < TRN; ++j) r += fabs(Ht[i * TRN + j]);
-        bnorm = fmax(bnorm, r);
+        bnorm = fmax(bnorm, rs[i]);
         bdmin = fmin(bdmin, Ht[i * TRN + i]);
     }
     cn = sqrt(cn);
@@ -407,14 +426,19 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     bool ok = block_chol(Ht, 0.0, L, TRN, &flag);
     bool solved = false;
     if (ok) {
-        if (tid == 0) {
-            chol_solve(L, cvec, p, TRN);
-            double s = 0.0;
-            for (int i = 0; i < TRN; ++i) {
-                p[i] = -p[i];
-                s += p[i] * p[i];
+        if (tid < TRN) invd[tid] = 1.0 / L[tid * TRN + tid];
+        __syncthreads();
+        if (tid < 32) {
+            warp_fwd(L, invd, cvec, w, TRN);
+            warp_bwd(L, invd, w, p, TRN);
+            if (tid == 0) {
+                double s = 0.0;
+                for (int i = 0; i < TRN; ++i) {
+                    p[i] = -p[i];
+                    s += p[i] * p[i];
+                }
+                pn_s = sqrt(s);
             }
-            pn_s = sqrt(s);
         }
         __syncthreads();
         if (pn_s <= Delta) solved = true;
@@ -425,54 +449,77 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         if (ok) lamL = fmax(lamL, 0.0);
         for (int it = 0; it < 200; ++it) {
             const bool pd = block_chol(Ht, lam, L, TRN, &flag);
-            if (tid == 0) {
-                double nl;
+            if (pd && tid < TRN) invd[tid] = 1.0 / L[tid * TRN + tid];
+            __syncthreads();
+            if (tid < 32) {
+                double nl = 0.0;
                 if (!pd) {
                     lamL = fmax(lamL, lam);
                     nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
-                    done = 0;
+                    if (tid == 0) done = 0;
                 } else {
-                    chol_solve(L, cvec, p, TRN);
+                    // p = -(B + lam I)^-1 c, then w = L^-1 p for Newton's step on 1/|p|
+                    warp_fwd(L, invd, cvec, w, TRN);
+                    warp_bwd(L, invd, w, p, TRN);
                     double s = 0.0;
-                    for (int i = 0; i < TRN; ++i) {
-                        p[i] = -p[i];
-                        s += p[i] * p[i];
-                    }
+                    for (int i = 0; i < TRN; ++i) s += p[i] * p[i];
                     const double pn = sqrt(s);
-                    pn_s = pn;
+                    __syncwarp();
+                    if (tid == 0) {
+                        for (int i = 0; i < TRN; ++i) p[i] = -p[i];
+                        pn_s = pn;
+                    }
+                    __syncwarp();
+                    int dn;
                     if (fabs(pn - Delta) <= 1e-12 * Delta) {
-                        done = 1;
+                        dn = 1;
                     } else {
                         if (pn < Delta) lamU = lam;
                         else lamL = lam;
-                        fwd_solve(L, p, w, TRN);
+                        warp_fwd(L, invd, p, w, TRN);
                         double wn = 0.0;
                         for (int i = 0; i < TRN; ++i) wn += w[i] * w[i];
                         nl = lam + (pn * pn / wn) * (pn - Delta) / Delta;
                         if (!(nl > lamL && nl < lamU))
                             nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
-                        done = (lamU - lamL <= 1e-15 * fmax(1.0, lamU)) ? 2 : 0;
+                        dn = (lamU - lamL <= 1e-15 * fmax(1.0, lamU)) ? 2 : 0;
                     }
+                    if (tid == 0) done = dn;
                 }
-                if (!done) lam_s = nl;
+                if (tid == 0 && !done) lam_s = nl;
             }
             __syncthreads();
             if (done) break;
             lam = lam_s;
+            // every thread follows warp 0's bracket (warp 0 updated its own copies)
+            if (tid == 0) { rs[0] = lamL; rs[1] = lamU; }
+            __syncthreads();
+            lamL = rs[0];
+            lamU = rs[1];
+            __syncthreads();
         }
         // hard case: |p| < Delta with lambda pinned at -lambda_min: add tau z, z from
         // inverse iteration with the last factorisation
         if (done == 2 && pn_s < Delta) {
-            if (tid == 0) {
-                double z[TRN], zn = 0.0;
-                for (int i = 0; i < TRN; ++i) z[i] = 1.0 + 0.01 * i;
+            __shared__ double zs[TRN], ys[TRN];
+            if (tid < 32) {
+                for (int i = tid; i < TRN; i += 32) zs[i] = 1.0 + 0.01 * i;
+                __syncwarp();
                 for (int r = 0; r < 6; ++r) {
-                    chol_solve(L, z, w, TRN);
-                    zn = 0.0;
+                    warp_fwd(L, invd, zs, ys, TRN);
+                    warp_bwd(L, invd, ys, w, TRN);
+                    double zn = 0.0;
                     for (int i = 0; i < TRN; ++i) zn += w[i] * w[i];
                     zn = sqrt(zn);
-                    for (int i = 0; i < TRN; ++i) z[i] = w[i] / zn;
+                    __syncwarp();
+                    for (int i = tid; i < TRN; i += 32) zs[i] = w[i] / zn;
+                    __syncwarp();
                 }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double z[TRN];
+                for (int i = 0; i < TRN; ++i) z[i] = zs[i];
                 double pz = 0.0, pp = 0.0;
                 for (int i = 0; i < TRN; ++i) {
                     pz += p[i] * z[i];
@@ -496,14 +543,17 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
             __syncthreads();
         }
     }
-    // predicted gain of the maximisation: g.p + p.H p / 2 = -(c.p + p.B p / 2)
+    // predicted gain of the maximisation: g.p + p.H p / 2 = -(c.p + p.B p / 2); the rows
+    // of B p one per thread, the sum in row order
+    if (tid < TRN) {
+        double s = 0.0;
+        for (int j = 0; j < TRN; ++j) s += Ht[tid * TRN + j] * p[j];
+        rs[tid] = s;
+    }
+    __syncthreads();
     if (tid == 0) {
         double pred = 0.0;
-        for (int i = 0; i < TRN; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < TRN; ++j) s += Ht[i * TRN + j] * p[j];
-            pred -= cvec[i] * p[i] + 0.5 * p[i] * s;
-        }
+        for (int i = 0; i < TRN; ++i) pred -= cvec[i] * p[i] + 0.5 * p[i] * rs[i];
         S.pred = pred;
         S.pnorm = pn_s;
         if (pred <= o.pred_tol_rel * (1.0 + fabs(S.f))) {
