@@ -485,8 +485,8 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                         c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx] == 1;
         }
     }
-    // the split item set: per source, per patch, the singly covered pixels (fused pass)
-    // then the multiply covered ones, each list cut into items of <= CHUNK pixels
+    // the split item set: per source, per patch, the singly covered pixels (fused pass,
+    // items of <= FUSED_CHUNK pixels) then the multiply covered ones (items of <= CHUNK)
     std::vector<WorkItem> sitems;
     std::vector<int32_t> spix, sitem_off(1, 0), sidx_single, sidx_multi;
     spix.reserve((size_t)n_sp);
@@ -500,9 +500,10 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                 for (int q = 0; q < g.w * g.h; ++q)
                     if ((f[q] != 0) == (pass == 0)) spix.push_back(q);
                 const int cnt = (int)spix.size() - first;
-                for (int o = 0; o < cnt; o += CHUNK) {
+                const int ch = pass == 0 ? FUSED_CHUNK : CHUNK;
+                for (int o = 0; o < cnt; o += ch) {
                     (pass == 0 ? sidx_single : sidx_multi).push_back((int32_t)sitems.size());
-                    sitems.push_back({p, first + o, std::min(CHUNK, cnt - o), s});
+                    sitems.push_back({p, first + o, std::min(ch, cnt - o), s});
                 }
                 if (pass == 0) sp_single += cnt;
             }

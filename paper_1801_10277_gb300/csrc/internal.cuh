@@ -47,6 +47,7 @@ constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
 
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)
+constexpr int FUSED_CHUNK = 256;   // pixels per split item of singly covered pixels (fused pass; 512 measured slower)
 constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
 
 struct ImgMeta {

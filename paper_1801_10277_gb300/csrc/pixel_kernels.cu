@@ -52,21 +52,24 @@ __device__ __forceinline__ R warp_sum(R v) {
 // in warp order.  Thread i < NV returns the CTA total of value i.
 template <class R, int NV>
 __device__ __forceinline__ void cta_sum(const R (&v)[NV], double* out) {
-    // sums within the CTA stay in R (a fixed tree over <= 256 pixels); one conversion
-    // per value: an FP64 warp instruction costs the narrow FP64 pipe ~16 cycles
+    // warp sums in R (a fixed tree over <= 32 threads' pixels), then FP64 across the
+    // warps in warp order
     __shared__ R red[32][NV > 0 ? NV : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
+    R ws[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        R s = warp_sum(v[i]);
-        if (lane == 0) red[warp][i] = s;
-    }
+    for (int i = 0; i < NV; ++i) ws[i] = warp_sum(v[i]);
+    __syncthreads();   // a previous call with the same NV may still be reading red
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[warp][i] = ws[i];
     __syncthreads();
     if (threadIdx.x < NV) {
-        R s = 0;
-        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = (double)s;
+        // across warps in FP64 (so no FP32 sum runs over more than one warp's pixels)
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
+        out[threadIdx.x] = s;
     }
 }
 
@@ -92,6 +95,37 @@ __device__ __forceinline__ void load_table(R* sT, const R* gT, int n) {
 
 __device__ __forceinline__ float lg2(float x) { return log2f(x); }
 __device__ __forceinline__ double lg2(double x) { return log2(x); }
+
+// Per-pixel FP32 quantities with every rounding written out (no contraction left to the
+// compiler), so that every kernel that forms them -- the value-only and the gradient
+// variants, the fused pass and the gather / adjoint passes -- gets the same bits.
+//   f_i = iota E[l_i] g_i,  E_s = a0 f0 + a1 f1,
+//   Var_s = a0 f0^2 em0 + a1 f1^2 em1 + a0 (1 - a0) f0^2 + a1 (1 - a1) f1^2 - 2 a0 a1 f0 f1
+//   (em_i = E[l_i^2] / E[l_i]^2 - 1)
+__device__ __forceinline__ void pixel_ev(float iota, float a0, float a1, float el0, float el1,
+                                         float em0, float em1, float G0, float G1, float& f0,
+                                         float& f1, float& es, float& vs) {
+    f0 = __fmul_rn(__fmul_rn(iota, el0), G0);
+    f1 = __fmul_rn(__fmul_rn(iota, el1), G1);
+    es = __fadd_rn(__fmul_rn(a0, f0), __fmul_rn(a1, f1));
+    const float f00 = __fmul_rn(f0, f0), f11 = __fmul_rn(f1, f1);
+    float v = __fmul_rn(__fmul_rn(a0, f00), em0);
+    v = __fadd_rn(v, __fmul_rn(__fmul_rn(a1, f11), em1));
+    v = __fadd_rn(v, __fmul_rn(__fmul_rn(a0, __fsub_rn(1.f, a0)), f00));
+    v = __fadd_rn(v, __fmul_rn(__fmul_rn(a1, __fsub_rn(1.f, a1)), f11));
+    vs = __fsub_rn(v, __fmul_rn(__fmul_rn(2.f, __fmul_rn(a0, a1)), __fmul_rn(f0, f1)));
+}
+// ll = x (log E - Var / (2 E^2)) - E and its weights c_E = x (1/E + Var/E^3) - 1,
+// c_V = -x / (2 E^2)
+__device__ __forceinline__ float pixel_ll(float x, float E, float V) {
+    const float iE = __fdiv_rn(1.f, E), iE2 = __fmul_rn(iE, iE);
+    return __fsub_rn(__fmul_rn(x, __fsub_rn(lg(E), __fmul_rn(__fmul_rn(0.5f, V), iE2))), E);
+}
+__device__ __forceinline__ void pixel_weights(float x, float E, float V, float& cE, float& cV) {
+    const float iE = __fdiv_rn(1.f, E), iE2 = __fmul_rn(iE, iE);
+    cE = __fsub_rn(__fmul_rn(x, __fadd_rn(iE, __fmul_rn(V, __fmul_rn(iE2, iE)))), 1.f);
+    cV = __fmul_rn(__fmul_rn(-0.5f, x), iE2);
+}
 __device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 __device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
@@ -750,7 +784,7 @@ struct GatherArgs {
     const int32_t* pix;
 };
 
-template <int MODE, int NPAIR, int SRC = SRC_MAPS>
+template <int MODE, int NPAIR, int SRC = SRC_MAPS, int CH = CHUNK>
 __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, const PatchGeo& g,
                                                 const ImgMeta& im, int nprof, const float2* sT2,
                                                 const float* __restrict__ pixels,
@@ -765,7 +799,7 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                                                 const int32_t* __restrict__ pix = nullptr) {
     constexpr bool FUSED = SRC == SRC_OWN;
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
-    constexpr int NT = CHUNK / (2 * NPAIR);
+    constexpr int NT = CH / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
     const int npsf = im.npsf;
     float v[NV];
@@ -826,12 +860,10 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                 E = emap[m];
                 V = vmap[m];
             }
-            const float iE = 1.f / E;
-            const float ll = x * (lg(E) - 0.5f * V * iE * iE) - E;
+            const float ll = pixel_ll(x, E, V);
             if (ok[p]) v[0] += ll;
             if (own) vown += ll;
-            cE[p] = x * (iE + V * iE * iE * iE) - 1.f;
-            cV[p] = -0.5f * x * iE * iE;
+            pixel_weights(x, E, V, cE[p], cV[p]);
         }
     }
     if constexpr (FUSED && MODE == MODE_LL) {
@@ -860,11 +892,11 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
             ld2(S + 2, s2, s3);
             const float2 s7 = S[7];
 #pragma unroll
-            for (int r = 0; r < NPAIR; ++r) {   // the gradient pass's rounding: n = c e, g += n
+            for (int r = 0; r < NPAIR; ++r) {
                 float2 a = __ffma2_rn(s2, dyy[r], s3);
                 a = __ffma2_rn(s1, dxy[r], a);
                 a = __ffma2_rn(s0, dxx[r], a);
-                g0[r] = __fadd2_rn(g0[r], __fmul2_rn(s7, ex2x2(a)));
+                g0[r] = __ffma2_rn(s7, ex2x2(a), g0[r]);   // as the gradient pass accumulates g
             }
             const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
             for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
@@ -877,25 +909,23 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                     float2 b = __ffma2_rn(c2, dyy[r], c3);
                     b = __ffma2_rn(c1, dxy[r], b);
                     b = __ffma2_rn(c0, dxx[r], b);
-                    g1[r] = __fadd2_rn(g1[r], __fmul2_rn(c7, ex2x2(b)));
+                    g1[r] = __ffma2_rn(c7, ex2x2(b), g1[r]);
                 }
             }
         }
         const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
         const float el0 = sT2[H_EL0].x, el1 = sT2[H_EL1].x;
-        const float em0 = sT2[H_EL20].x / (el0 * el0) - 1.f, em1 = sT2[H_EL21].x / (el1 * el1) - 1.f;
+        const float em0 = __fsub_rn(__fdiv_rn(sT2[H_EL20].x, __fmul_rn(el0, el0)), 1.f);
+        const float em1 = __fsub_rn(__fdiv_rn(sT2[H_EL21].x, __fmul_rn(el1, el1)), 1.f);
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             if (!ok[p]) continue;
             const int r = p >> 1;
             const float G0 = (p & 1) ? g0[r].y : g0[r].x, G1 = (p & 1) ? g1[r].y : g1[r].x;
-            const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
-            const float e = a0 * f0 + a1 * f1;
-            const float V = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
-                            a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
-            const float E = sky[p] + e;
-            const float iE = 1.f / E;
-            v[0] += xv[p] * (lg(E) - 0.5f * V * iE * iE) - E;
+            float f0, f1, e, V;
+            pixel_ev(iota, a0, a1, el0, el1, em0, em1, G0, G1, f0, f1, e, V);
+            const float E = __fadd_rn(sky[p], e);
+            v[0] += pixel_ll(xv[p], E, V);
             emap_out[mm[p]] = E;
             vmap_out[mm[p]] = V;
         }
@@ -934,10 +964,12 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                     float2 a = __ffma2_rn(s2, dyy[r], s3);
                     a = __ffma2_rn(s1, dxy[r], a);
                     a = __ffma2_rn(s0, dxx[r], a);
-                    const float2 n = __fmul2_rn(c, ex2x2(a));
+                    const float2 ea = ex2x2(a);
+                    const float2 n = __fmul2_rn(c, ea);
                     const float2 qx = __ffma2_rn(npxx, dx[r], __fmul2_rn(npxy, dy[r]));   // -(Pd)_x
                     const float2 qy = __ffma2_rn(npxy, dx[r], __fmul2_rn(npyy, dy[r]));   // -(Pd)_y
-                    g0[r] = __fadd2_rn(g0[r], n);
+                    // g as one fused multiply-add (the value-only pass forms it the same way)
+                    g0[r] = __ffma2_rn(c, ea, g0[r]);
                     gx0[r] = __ffma2_rn(n, qx, gx0[r]);
                     gy0[r] = __ffma2_rn(n, qy, gy0[r]);
                 }
@@ -960,7 +992,7 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
                     const float2 n = __fmul2_rn(c, e);
                     const float2 qx = __ffma2_rn(npxx, dx[r], __fmul2_rn(npxy, dy[r]));
                     const float2 qy = __ffma2_rn(npxy, dx[r], __fmul2_rn(npyy, dy[r]));
-                    g1[r] = __fadd2_rn(g1[r], n);
+                    g1[r] = __ffma2_rn(c, e, g1[r]);
                     gx1[r] = __ffma2_rn(n, qx, gx1[r]);
                     gy1[r] = __ffma2_rn(n, qy, gy1[r]);
                     de1[r] = __ffma2_rn(dc, e, de1[r]);
@@ -986,20 +1018,21 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
             const float DE = hi ? de1[r].y : de1[r].x;
             const float SXX = hi ? sxx[r].y : sxx[r].x, SXY = hi ? sxy[r].y : sxy[r].x,
                         SYY = hi ? syy[r].y : syy[r].x;
-            const float f0 = iota * el0 * G0, f1 = iota * el1 * G1;
-            const float Es = a0 * f0 + a1 * f1;
+            float f0, f1, Es, Vs;
             if constexpr (FUSED) {
                 // this pixel's E and Var are the item's own: form them, the ll and its weights
-                const float em0 = el20 / (el0 * el0) - 1.f, em1 = el21 / (el1 * el1) - 1.f;
-                const float V = a0 * f0 * f0 * em0 + a1 * f1 * f1 * em1 + a0 * (1.f - a0) * f0 * f0 +
-                                a1 * (1.f - a1) * f1 * f1 - 2.f * a0 * a1 * f0 * f1;
-                const float E = sky[p] + Es;
-                const float iE = 1.f / E;
-                v[0] += xv[p] * (lg(E) - 0.5f * V * iE * iE) - E;
-                cE[p] = xv[p] * (iE + V * iE * iE * iE) - 1.f;
-                cV[p] = -0.5f * xv[p] * iE * iE;
+                const float em0 = __fsub_rn(__fdiv_rn(el20, __fmul_rn(el0, el0)), 1.f);
+                const float em1 = __fsub_rn(__fdiv_rn(el21, __fmul_rn(el1, el1)), 1.f);
+                pixel_ev(iota, a0, a1, el0, el1, em0, em1, G0, G1, f0, f1, Es, Vs);
+                const float E = __fadd_rn(sky[p], Es);
+                v[0] += pixel_ll(xv[p], E, Vs);
+                pixel_weights(xv[p], E, Vs, cE[p], cV[p]);
                 emap_out[mm[p]] = E;
-                vmap_out[mm[p]] = V;
+                vmap_out[mm[p]] = Vs;
+            } else {
+                f0 = __fmul_rn(__fmul_rn(iota, el0), G0);   // as pixel_ev forms them
+                f1 = __fmul_rn(__fmul_rn(iota, el1), G1);
+                Es = __fadd_rn(__fmul_rn(a0, f0), __fmul_rn(a1, f1));
             }
             const float w1 = cE[p] - 2.f * cV[p] * Es, w2 = cV[p];
             const float s0 = i2 * G0 * G0, s1 = i2 * G1 * G1;
@@ -1147,7 +1180,7 @@ struct KlArgs {
 };
 
 template <int MODE, int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x2(const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(FUSED_CHUNK / (2 * NPAIR), CEL_FUSED_MINB * CHUNK / FUSED_CHUNK) k_fused_x2(const WorkItem* __restrict__ items,
                                                                 const int32_t* __restrict__ idx,
                                                                 const PatchGeo* __restrict__ geo,
                                                                 const ImgMeta* __restrict__ img, int nprof,
@@ -1160,7 +1193,7 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x
                                                                 double* __restrict__ item_ll,
                                                                 const int32_t* __restrict__ pix,
                                                                 KlArgs kl) {
-    constexpr int WARPS = CHUNK / (2 * NPAIR) / 32;
+    constexpr int WARPS = FUSED_CHUNK / (2 * NPAIR) / 32;
     if ((int)blockIdx.x < kl.blocks) {
         __shared__ double kth[WARPS][NP], kg[WARPS][NP];
         __shared__ float kthr[WARPS][NP];
@@ -1182,8 +1215,9 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR), CEL_FUSED_MINB) k_fused_x
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR, SRC_OWN>(item, it, g, im, nprof, sT2, pixels, nullptr, nullptr, part,
-                                          sky_map, emap, vmap, item_ll, nullptr, pix);
+    adjoint_x2_item<MODE, NPAIR, SRC_OWN, FUSED_CHUNK>(item, it, g, im, nprof, sT2, pixels, nullptr,
+                                                       nullptr, part, sky_map, emap, vmap, item_ll,
+                                                       nullptr, pix);
 }
 
 // ---- persistent CTAs with a work queue (tuning codes 6, 7)
@@ -1472,7 +1506,7 @@ static int cap_padding(const void* kernel, int threads, int cap) {
 
 template <int NPAIR>
 static void fused_x2(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta) {
-    constexpr int NT = CHUNK / (2 * NPAIR);
+    constexpr int NT = FUSED_CHUNK / (2 * NPAIR);
     constexpr int WARPS = NT / 32;
     KlArgs kl{d_theta, P.model, P.n_src, 0, P.kl, P.kl_grad, P.status};
     if (d_theta && P.kl_grad) kl.blocks = (P.n_src + WARPS - 1) / WARPS;
@@ -1494,10 +1528,10 @@ static void fused_x2(const DevProblem& P, int mode, cudaStream_t st, const doubl
 // the padding of every fused kernel for caps 1 .. 8, found outside any stream capture
 void prime_fused_caps() {
     for (int cap = 1; cap <= 8; ++cap) {
-        cap_padding((const void*)k_fused_x2<MODE_LL, 1>, CHUNK / 2, cap);
-        cap_padding((const void*)k_fused_x2<MODE_GRAD, 1>, CHUNK / 2, cap);
-        cap_padding((const void*)k_fused_x2<MODE_LL, 2>, CHUNK / 4, cap);
-        cap_padding((const void*)k_fused_x2<MODE_GRAD, 2>, CHUNK / 4, cap);
+        cap_padding((const void*)k_fused_x2<MODE_LL, 1>, FUSED_CHUNK / 2, cap);
+        cap_padding((const void*)k_fused_x2<MODE_GRAD, 1>, FUSED_CHUNK / 2, cap);
+        cap_padding((const void*)k_fused_x2<MODE_LL, 2>, FUSED_CHUNK / 4, cap);
+        cap_padding((const void*)k_fused_x2<MODE_GRAD, 2>, FUSED_CHUNK / 4, cap);
     }
 }
 

@@ -19,7 +19,7 @@ def test_autograd_matches_elbo_grad():
         tot, loc, g = P.elbo_grad(prob.theta, precision=prec)
         th = torch.tensor(prob.theta, dtype=torch.float64, device="cuda", requires_grad=True)
         out = autograd.elbo(th, P, prec)
-        assert out.item() == tot
+        assert out.item() == tot, prec
         (2.0 * out).backward()
         np.testing.assert_array_equal(th.grad.cpu().numpy(), 2.0 * g)
         # an evaluation between forward and backward does not corrupt the gradient
