@@ -16,7 +16,10 @@
 //   k_batch_dll          per-pixel change of the log-likelihood (stable difference form)
 //   k_tr_accept          actual / predicted gain, radius update, accept or reject
 // The iteration is captured once per colour as a CUDA graph and replayed; the host
-// reads one counter (sources still iterating) per replay.
+// reads one counter (sources still iterating) per replay.  A per-source mask
+// (k_mark_active, after the step and after the acceptance) lets every pixel kernel skip
+// the items of a source that has stopped iterating, so a replay costs in proportion to
+// the sources still active.
 #include <math.h>
 #include <string.h>
 
@@ -135,11 +138,13 @@ template <class R>
 __global__ void k_batch_maps(const WorkItem* __restrict__ bitems, const PatchGeo* __restrict__ bgeo,
                              const ImgMeta* __restrict__ img, const R* __restrict__ eo,
                              const R* __restrict__ vo, const R* __restrict__ se,
-                             const R* __restrict__ sv, R* __restrict__ emap, R* __restrict__ vmap) {
+                             const R* __restrict__ sv, R* __restrict__ emap, R* __restrict__ vmap,
+                             const int32_t* __restrict__ src_active) {
     const WorkItem it = bitems[blockIdx.x];
     const int t = threadIdx.x;
     if (t >= it.n) return;
     const PatchGeo g = bgeo[it.patch];
+    if (!src_active[g.src]) return;   // a converged source's maps do not change
     const ImgMeta& im = img[g.img];
     const int q = it.q0 + t;
     const int yy = q / g.w, xx = q - yy * g.w;
@@ -157,10 +162,11 @@ __global__ void k_batch_dll(const WorkItem* __restrict__ bitems, const PatchGeo*
                             const R* __restrict__ eo, const R* __restrict__ vo,
                             const R* __restrict__ se, const R* __restrict__ sv,
                             const R* __restrict__ ce, const R* __restrict__ cv,
-                            double* __restrict__ dll) {
+                            double* __restrict__ dll, const int32_t* __restrict__ src_active) {
     __shared__ double red[CHUNK / 32];
     const WorkItem it = bitems[blockIdx.x];
     const int t = threadIdx.x;
+    if (!src_active[bgeo[it.patch].src]) return;   // no candidate for a converged source
     R v = 0;
     if (t < it.n) {
         const PatchGeo g = bgeo[it.patch];
@@ -625,6 +631,12 @@ __global__ void k_scatter_theta(int nb, const int32_t* __restrict__ bsrc,
     if (i < nb * NP) theta[(size_t)NP * bsrc[i / NP] + i % NP] = bth[i];
 }
 
+// per batch source: 1 while its Newton iterations continue (its pixel work is skipped after)
+__global__ void k_mark_active(int nb, const TrState* __restrict__ st, int32_t* __restrict__ act) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) act[b] = st[b].status == ST_ACTIVE ? 1 : 0;
+}
+
 __global__ void k_init_state(int nb, TrState* st, double delta0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -747,7 +759,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
     // device buffers for the largest batch
     DevBuf mem;
     const size_t rs = sizeof(double);   // per-pixel batch buffers serve both precisions
-    int32_t *d_bsrc, *d_bpo, *d_active;
+    int32_t *d_bsrc, *d_bpo, *d_active, *d_srcact;
     PatchGeo* d_bgeo;
     WorkItem* d_bitems;
     double *d_bth, *d_bthc, *d_bt, *d_btc, *d_f, *d_g, *d_h, *d_kl, *d_part, *d_dll, *d_tbl64;
@@ -757,6 +769,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
     FIT_CUDA(mem.alloc(&d_bsrc, maxB));
     FIT_CUDA(mem.alloc(&d_bpo, maxB + 1));
     FIT_CUDA(mem.alloc(&d_active, 1));
+    FIT_CUDA(mem.alloc(&d_srcact, maxB));
     FIT_CUDA(mem.alloc(&d_bgeo, maxP));
     FIT_CUDA(mem.alloc(&d_bitems, maxI));
     FIT_CUDA(mem.alloc(&d_bth, maxB * NP));
@@ -828,6 +841,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             k_gather_theta<<<(nb * NP + 255) / 256, 256, 0, st>>>(nb, d_bsrc, pr->d_theta, d_bth);
             k_to_free<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bth, d_bt);
             k_init_state<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, opts->delta0);
+            k_mark_active<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, d_srcact);
             FIT_CUDA(cudaGetLastError());
             // batch views of the problem
             DevProblem Pb = P;
@@ -848,6 +862,8 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             Pb.single = nullptr;    // batch buffers keep every E_s / Var_s
             Pb.item_ll = nullptr;
             Pb.status = nullptr;
+            // a source that stopped iterating keeps its theta: its pixel work is skipped
+            Pb.src_active = d_srcact;
             DevProblem Pc = Pb;
             Pc.spE = d_ce;
             Pc.spE2 = d_cv;
@@ -866,16 +882,20 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                 if (prec == CELESTE_FP64)
                     k_batch_maps<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, (const double*)d_eo,
                                                                (const double*)d_vo, (const double*)d_se,
-                                                               (const double*)d_sv, (double*)P.emap, (double*)P.vmap);
+                                                               (const double*)d_sv, (double*)P.emap, (double*)P.vmap,
+                                                               d_srcact);
                 else
                     k_batch_maps<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, (const float*)d_eo,
                                                               (const float*)d_vo, (const float*)d_se,
-                                                              (const float*)d_sv, (float*)P.emap, (float*)P.vmap);
+                                                              (const float*)d_sv, (float*)P.emap, (float*)P.vmap,
+                                                              d_srcact);
             }
             chk(launch_hess_pixels(Pb, prec, st));
             chk(launch_finalize_hess(Pb, d_bth, d_f, d_g, d_h, st));
             k_tr_step<<<nb, TR_THREADS, 0, st>>>(nb, d_bth, d_bt, d_f, d_g, d_h, d_kl, d_bthc, d_btc,
                                                  d_st, *opts, d_active);
+            // only sources with a candidate evaluate it
+            k_mark_active<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, d_srcact);
             chk(launch_prep(Pc, d_bthc, prec, st));
             chk(launch_contrib(Pc, prec, st));
             if (nI > 0) {
@@ -883,15 +903,18 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                     k_batch_dll<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, P.pixels,
                                                               (const double*)d_eo, (const double*)d_vo,
                                                               (const double*)d_se, (const double*)d_sv,
-                                                              (const double*)d_ce, (const double*)d_cv, d_dll);
+                                                              (const double*)d_ce, (const double*)d_cv, d_dll,
+                                                              d_srcact);
                 else
                     k_batch_dll<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.img, P.pixels,
                                                              (const float*)d_eo, (const float*)d_vo,
                                                              (const float*)d_se, (const float*)d_sv,
-                                                             (const float*)d_ce, (const float*)d_cv, d_dll);
+                                                             (const float*)d_ce, (const float*)d_cv, d_dll,
+                                                             d_srcact);
             }
             k_tr_accept<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bpo, d_bgeo, d_dll, P.model, d_bth, d_bt,
                                                           d_bthc, d_btc, d_st, *opts);
+            k_mark_active<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, d_srcact);
             chk(cudaGetLastError());
             chk(cudaMemcpyAsync(h_active, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             cudaError_t ee = cudaStreamEndCapture(st, &graph);

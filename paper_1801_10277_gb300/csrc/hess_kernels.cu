@@ -52,11 +52,13 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                                                 const R* __restrict__ tbl,
                                                 const R* __restrict__ emap,
                                                 const R* __restrict__ vmap,
-                                                double* __restrict__ part) {
+                                                double* __restrict__ part,
+                                                const int32_t* __restrict__ src_active) {
     __shared__ R sT[TBL_STRIDE];
     __shared__ R red[CHUNK / 32][HV];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
+    if (src_active && !src_active[g.src]) return;
     const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
     {
@@ -360,9 +362,9 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 const ModelDev* __restrict__ md, const double* __restrict__ part,
                 double* __restrict__ kl_out, double* __restrict__ local_out,
                 double* __restrict__ grad_out, double* __restrict__ hess_out,
-                int32_t* __restrict__ status) {
+                int32_t* __restrict__ status, const int32_t* __restrict__ src_active) {
     const int s = blockIdx.x;
-    if (s >= n_src) return;
+    if (s >= n_src || (src_active && !src_active[s])) return;
     const double* th = theta + (size_t)NP * s;
     if (status && (int)threadIdx.x < NP) theta_domain_check(threadIdx.x, th[threadIdx.x], status);
     __shared__ double Hy[NY][NY];
@@ -504,11 +506,11 @@ cudaError_t launch_hess_pixels(const DevProblem& P, int precision, cudaStream_t 
     if (precision == CELESTE_FP64)
         k_hess<double><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
                                                    P.tbl64, (const double*)P.emap,
-                                                   (const double*)P.vmap, P.item_part);
+                                                   (const double*)P.vmap, P.item_part, P.src_active);
     else
         k_hess<float><<<P.n_item, CHUNK, 0, st>>>(P.items, P.geo, P.img, P.nprof, P.pixels,
                                                   P.tbl32, (const float*)P.emap,
-                                                  (const float*)P.vmap, P.item_part);
+                                                  (const float*)P.vmap, P.item_part, P.src_active);
     return cudaGetLastError();
 }
 
@@ -517,7 +519,7 @@ cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, dou
     if (P.n_src == 0) return cudaSuccess;
     k_finalize_hess<<<P.n_src, FH_THREADS, 0, st>>>(P.n_src, d_theta, P.geo, P.patch_off, P.img,
                                                     P.model, P.item_part, P.kl, d_local, d_grad,
-                                                    d_hess, P.status);
+                                                    d_hess, P.status, P.src_active);
     return cudaGetLastError();
 }
 

@@ -203,6 +203,8 @@ struct DevProblem {
     double* sitem_ll;            // ll of a singly covered item (0 for the others)
     double* sitem_own;           // ll of the multiply covered pixels an item owns (the first
                                  // covering patch owns a pixel; 0 for singly covered items)
+    const int32_t* src_active;   // per source: 0 = skip its work (the fit's converged batch
+                                 // sources); nullable = every source works
     int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
                              // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;

@@ -158,9 +158,10 @@ __global__ void __launch_bounds__(PREP_THREADS)
 k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
        const int32_t* __restrict__ patch_off, const ImgMeta* __restrict__ img,
        const ModelDev* __restrict__ md, int n_src, int nprof, R* __restrict__ tbl,
-       double* __restrict__ kl_out, double* __restrict__ klg_out, int32_t* __restrict__ status) {
+       double* __restrict__ kl_out, double* __restrict__ klg_out, int32_t* __restrict__ status,
+       const int32_t* __restrict__ src_active) {
     const int s = blockIdx.x;
-    if (s >= n_src) return;
+    if (s >= n_src || (src_active && !src_active[s])) return;
     const int p0 = patch_off[s], np = patch_off[s + 1] - p0;
     __shared__ double th[NP];
     __shared__ R thr[NP];
@@ -325,11 +326,13 @@ __global__ void __launch_bounds__(CHUNK / PPT) k_contrib(const WorkItem* __restr
                                                          const float* __restrict__ pixels,
                                                          const float* __restrict__ sky_map,
                                                          R* __restrict__ emap, R* __restrict__ vmap,
-                                                         double* __restrict__ item_ll) {
+                                                         double* __restrict__ item_ll,
+                                                         const int32_t* __restrict__ src_active) {
     __shared__ R sT[TBL_STRIDE];
     const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
+    if (src_active && !src_active[g.src]) return;
     const ImgMeta& im = img[g.img];
     const int npsf = im.npsf;
     load_table(sT, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + npsf * nprof * GAL_STRIDE);
@@ -1095,11 +1098,13 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_x2(const WorkIt
                                                                   const float* __restrict__ sky_map,
                                                                   float* __restrict__ emap,
                                                                   float* __restrict__ vmap,
-                                                                  double* __restrict__ item_ll) {
+                                                                  double* __restrict__ item_ll,
+                                                                  const int32_t* __restrict__ src_active) {
     __shared__ __align__(16) float2 sT2[TBL_STRIDE];
     const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
+    if (src_active && !src_active[g.src]) return;
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
     contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, single, pixels, sky_map, emap,
@@ -1337,6 +1342,7 @@ __device__ __forceinline__ void run_items_persistent(const WorkItem* __restrict_
 
 template <int NPAIR>
 struct ContribBody {
+    const int32_t* src_active;
     int nprof;
     float* spE;
     float* spV;
@@ -1348,6 +1354,7 @@ struct ContribBody {
     double* item_ll;
     __device__ void operator()(int item, const WorkItem& it, const PatchGeo& g, const ImgMeta& im,
                                const float2* sT2) const {
+        if (src_active && !src_active[g.src]) return;   // uniform over the CTA
         contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, single, pixels, sky_map, emap,
                                vmap, item_ll);
     }
@@ -1426,13 +1433,13 @@ template <int NPAIR>
 static void contrib_x2(const DevProblem& P, ItemSet S, cudaStream_t st) {
     k_contrib_x2<NPAIR><<<S.n, CHUNK / (2 * NPAIR), 0, st>>>(
         P.items, S.idx, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2, P.single,
-        P.pixels, P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll);
+        P.pixels, P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll, P.src_active);
 }
 
 template <int NPAIR>
 static void contrib_pq(const DevProblem& P, ItemSet S, cudaStream_t st) {
     constexpr int NT = CHUNK / (2 * NPAIR);
-    const ContribBody<NPAIR> body{P.nprof, (float*)P.spE, (float*)P.spE2, P.single, P.pixels,
+    const ContribBody<NPAIR> body{P.src_active, P.nprof, (float*)P.spE, (float*)P.spE2, P.single, P.pixels,
                                   P.sky_map, (float*)P.emap, (float*)P.vmap, P.item_ll};
     const int grid = persistent_grid((const void*)k_contrib_pq<NPAIR>, NT, S.n);
     k_contrib_pq<NPAIR><<<grid, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, S.n, P.tbl32,
@@ -1581,10 +1588,12 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
     const int grid = P.n_src;
     if (precision == CELESTE_FP64)
         k_prep<double><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                      P.n_src, P.nprof, P.tbl64, P.kl, klg, P.status);
+                                                      P.n_src, P.nprof, P.tbl64, P.kl, klg, P.status,
+                                                      P.src_active);
     else
         k_prep<float><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
-                                                     P.n_src, P.nprof, P.tbl32, P.kl, klg, P.status);
+                                                     P.n_src, P.nprof, P.tbl32, P.kl, klg, P.status,
+                                                     P.src_active);
     return cudaGetLastError();
 }
 
@@ -1599,7 +1608,7 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st, 
         k_contrib<double, 1><<<S.n, CHUNK, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.tbl64,
                                                     (double*)P.spE, (double*)P.spE2, P.single,
                                                     P.pixels, P.sky_map, (double*)P.emap,
-                                                    (double*)P.vmap, P.item_ll);
+                                                    (double*)P.vmap, P.item_ll, P.src_active);
     else
         switch (ppt_contrib(P)) {
 #define CEL_CONTRIB32(N)                                                                          \
@@ -1607,7 +1616,8 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st, 
         k_contrib<float, N><<<S.n, CHUNK / N, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof,       \
                                                        P.tbl32, (float*)P.spE, (float*)P.spE2,      \
                                                        P.single, P.pixels, P.sky_map,              \
-                                                       (float*)P.emap, (float*)P.vmap, P.item_ll); \
+                                                       (float*)P.emap, (float*)P.vmap, P.item_ll,  \
+                                                       P.src_active);                              \
         break;
             CEL_CONTRIB32(1)
             CEL_CONTRIB32(2)
