@@ -216,6 +216,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--hess-steps", type=int, default=20)
     ap.add_argument("--no-fit", action="store_true")
+    ap.add_argument("--no-schedules", action="store_true",
+                    help="skip the colour vs Cyclades convergence-per-sweep leg")
+    ap.add_argument("--schedule-sweeps", type=int, default=4)
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
                          "4 sweep field; the JSON line names it")
@@ -388,6 +391,37 @@ def main():
                "converged": int((fst == 0).sum()),
                "options": "FP32 pixels, FP64 refinement, <= 3 sweeps, <= 50 iterations per source"}
 
+    # convergence per sweep of the two conflict-free schedules (Section IV-D): greedy
+    # colouring vs Cyclades samples (sweep k's order drawn in the library from seed k);
+    # one sweep per call from the previous sweep's result, FP32 pixels, no polish; the
+    # ELBO after each sweep in FP64, outside the timed calls
+    schedules = None
+    if not args.no_fit and not args.no_schedules:
+        schedules = {}
+        for name, kw in (("colour", {}),
+                         ("cyclades_64", dict(schedule="cyclades", sample_size=64)),
+                         ("cyclades_all", dict(schedule="cyclades", sample_size=prob.n_src))):
+            th = prob.theta.copy()
+            elbos, secs_l, iters_l = [], [], []
+            for k in range(args.schedule_sweeps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                th, iters, _, _ = P.fit(th, precision=cel.FP32, refine_fp64=0, max_sweeps=1,
+                                        seed=k, **kw)
+                torch.cuda.synchronize()
+                secs_l.append(time.perf_counter() - t0)
+                iters_l.append(int(iters.sum()))
+                elbos.append(P.elbo(th, precision=cel.FP64)[0])
+            entry = {"elbo_after_sweep": elbos, "seconds_per_sweep": secs_l,
+                     "newton_iterations_per_sweep": iters_l}
+            if kw:   # batches per sweep, mean over four random orders
+                rng = np.random.default_rng(0)
+                entry["batches_per_sweep"] = float(np.mean([cel.cyclades_batches(
+                    prob.nbr_offsets, prob.nbrs, rng.permutation(prob.n_src).astype(np.int32),
+                    kw["sample_size"])[2] for _ in range(4)]))
+            schedules[name] = entry
+        schedules["elbo_start"] = P.elbo(prob.theta, precision=cel.FP64)[0]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, reps, secs = oracle_rate(prob)
@@ -410,7 +444,7 @@ def main():
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "hessian": hessian, "fit": fit,
+            "hessian": hessian, "fit": fit, "fit_schedules": schedules,
             "gpu_launches": int(round(launches_per_step * args.steps)),
         }
         print(json.dumps(line), flush=True)

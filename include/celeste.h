@@ -181,25 +181,62 @@ typedef struct {
     int32_t refine_fp64;       /* with CELESTE_FP32_ACC64: after the FP32 sweeps converge, polish with
                                   FP64 sweeps (Newton needs one or two steps from there), so poorly
                                   constrained parameters are not left at FP32 rounding noise */
+    int32_t schedule;          /* CELESTE_SCHED_COLOUR (default) or CELESTE_SCHED_CYCLADES */
+    int32_t sample_size;       /* Cyclades: sources per random sample, >= 1 (default 64) */
+    uint64_t seed;             /* Cyclades with order == NULL: sweep g visits the moving sources
+                                  (ascending ids) shuffled by Fisher-Yates with SplitMix64
+                                  draws keyed by (seed, g) */
+    const int32_t* order;      /* Cyclades, nullable: [max_sweeps][n_moving] host array; sweep g
+                                  (counted over both precision phases) uses row g mod max_sweeps,
+                                  each row a permutation of the moving sources */
 } celeste_fit_options;
+
+/* Conflict-free update schedules of the block-coordinate fit (Section IV-D). */
+enum { CELESTE_SCHED_COLOUR = 0, CELESTE_SCHED_CYCLADES = 1 };
 
 /* Fill opts with the defaults documented above. */
 void celeste_fit_options_default(celeste_fit_options* opts);
 
 /*
- * Block-coordinate trust-region Newton fit (Section IV-D).  Sources are greedily
- * coloured in ascending id over the neighbour graph; the colours are swept in order;
- * all sources of one colour (which never overlap) take their Newton iterations in
- * one batch with every other source fixed; E and Var are updated after accepted
- * steps.  theta_inout[n_src][44] (host) is read and overwritten.  which[n_which]
- * restricts the moving sources (NULL: all).  iters_out / status_out ([n_src],
- * nullable) receive Newton iterations and 0 converged / 1 iteration limit /
- * 2 non-finite.  The fit restarts from theta_inout, so it can be resumed.
+ * Block-coordinate trust-region Newton fit (Section IV-D).  Each sweep runs a sequence
+ * of batches; the sources of one batch never overlap and take their Newton iterations
+ * together with every other source fixed; E and Var are updated after each batch.
+ * Schedules:
+ *   CELESTE_SCHED_COLOUR: sources greedily coloured in ascending id over the
+ *     neighbour graph; one batch per colour, colours in order, the same every sweep.
+ *   CELESTE_SCHED_CYCLADES: the conflict-free sampling of Section IV-D (Pan et al.,
+ *     Cyclades): the sweep's order is cut into consecutive samples of sample_size
+ *     sources; each sample is split into the connected components of the neighbour
+ *     graph restricted to it; the sources of one component are updated one after
+ *     another in sample order, different components concurrently: batch r of a sample
+ *     holds the r-th source of every component that has one (celeste_cyclades_batches).
+ * theta_inout[n_src][44] (host) is read and overwritten.  which[n_which] restricts the
+ * moving sources (NULL: all).  iters_out / status_out ([n_src], nullable) receive
+ * Newton iterations and 0 converged / 1 iteration limit / 2 non-finite.  The fit
+ * restarts from theta_inout, so it can be resumed.  A Cyclades order row that is not a
+ * permutation of the moving sources, or sample_size < 1, is CELESTE_ERR_ARG.
  */
 celeste_status celeste_fit_sources(celeste_problem* prob, double* theta_inout,
                                    const int32_t* which, int32_t n_which,
                                    const celeste_fit_options* opts, int32_t* iters_out,
                                    int32_t* status_out, double* elbo_out);
+
+/*
+ * The Cyclades batches of one sweep (host logic, no device work, no CUDA context
+ * needed) over the neighbour graph nbr_offsets[n_src + 1] / nbrs (the CSR lists given
+ * to celeste_problem_create, symmetric): order[n_order] lists distinct source ids in
+ * [0, n_src); positions [k sample_size, (k+1) sample_size) form sample k.  On
+ * return batch_of[i] is the batch of order[i]: samples take consecutive batch ranges
+ * in order, and within a sample the r-th member (in order) of a connected component of
+ * the neighbour graph restricted to the sample goes to the sample's batch r.
+ * *n_batches = the number of batches.  comp_of (nullable, [n_order]) receives the
+ * position in order of the first member of order[i]'s component.  Errors:
+ * CELESTE_ERR_ARG (null pointers, n_src < 0, sample_size < 1, an id out of range or
+ * repeated, a neighbour id out of range).
+ */
+celeste_status celeste_cyclades_batches(const int32_t* nbr_offsets, const int32_t* nbrs, int32_t n_src,
+                                        const int32_t* order, int32_t n_order, int32_t sample_size,
+                                        int32_t* batch_of, int32_t* comp_of, int32_t* n_batches);
 
 /* Device-pointer variants: same semantics, pointers on the problem's device, work
  * enqueued on `stream` (a cudaStream_t; NULL = legacy default stream), no synchronisation.

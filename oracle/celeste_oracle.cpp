@@ -1168,15 +1168,59 @@ int oracle_colouring(const OProblem* P, int32_t* colour) {
     return maxc;
 }
 
+// Cyclades schedule (Section IV-D; Pan et al., "Cyclades"): positions [k B, (k+1) B)
+// of the order form sample k; the neighbour graph restricted to the sample splits into
+// connected components (breadth-first search from each unlabelled member in order, so
+// a component is labelled with the order position of its first member); the members
+// of one component are updated one after another in order and different components
+// side by side, i.e. the r-th member of every component forms the sample's r-th batch.
+// Samples take consecutive batch numbers.  Returns the number of batches.
+int oracle_cyclades_batches(const OProblem* P, const int32_t* order, int m, int B,
+                            int32_t* comp_of, int32_t* batch_of) {
+    int base = 0;
+    for (int k0 = 0; k0 < m; k0 += B) {
+        const int k1 = std::min(m, k0 + B);
+        std::vector<int> at(P->n_src, -1);   // order position of a sampled source
+        for (int i = k0; i < k1; ++i) at[order[i]] = i;
+        for (int i = k0; i < k1; ++i) comp_of[i] = -1;
+        for (int i = k0; i < k1; ++i) {
+            if (comp_of[i] >= 0) continue;
+            std::vector<int> queue{i};
+            comp_of[i] = i;
+            for (size_t q = 0; q < queue.size(); ++q) {
+                const int s = order[queue[q]];
+                for (int e = P->nbr_off[s]; e < P->nbr_off[s + 1]; ++e) {
+                    const int j = at[P->nbrs[e]];
+                    if (j >= 0 && comp_of[j] < 0) {
+                        comp_of[j] = i;
+                        queue.push_back(j);
+                    }
+                }
+            }
+        }
+        int rounds = 0;
+        for (int i = k0; i < k1; ++i) {
+            int r = 0;   // earlier members of the same component
+            for (int j = k0; j < i; ++j) r += comp_of[j] == comp_of[i];
+            batch_of[i] = base + r;
+            rounds = std::max(rounds, r + 1);
+        }
+        base += rounds;
+    }
+    return base;
+}
+
 // Block-coordinate fit: colour classes in order; every source of a class is fitted
 // by trust-region Newton with all other sources fixed; E and V are refreshed after
 // each class; sweeps repeat until the total ELBO changes by < sweep_tol relative.
-// `which` (null: all) restricts the sources that move.
+// `which` (null: all) restricts the sources that move.  With schedule 1 the batches of
+// sweep g are the Cyclades batches of order row g mod max_sweeps ([max_sweeps][n_moving],
+// each row a permutation of the moving sources) with samples of sample_size.
 int oracle_fit(const OProblem* P, double* theta, const int32_t* which, int n_which,
                int max_iter, double grad_tol, double pred_tol_rel, double delta0,
                double delta_max, double eta, double f_noise_rel, int max_sweeps,
                double sweep_tol, int32_t* iters_out, int32_t* status_out, double* elbo_out,
-               int32_t* sweeps_out) {
+               int32_t* sweeps_out, int schedule, int sample_size, const int32_t* order) {
     for (int s = 0; s < P->n_src; ++s)
         if (!theta_valid(theta + (size_t)NP * s) || !theta_in_box(theta + (size_t)NP * s))
             return -1;
@@ -1194,14 +1238,27 @@ int oracle_fit(const OProblem* P, double* theta, const int32_t* which, int n_whi
     }
     double prev;
     oracle_elbo(P, theta, &prev, nullptr, nullptr, nullptr);
+    int n_moving = 0;
+    for (int s = 0; s < P->n_src; ++s) n_moving += moves[s];
     int sw = 0;
     for (; sw < max_sweeps; ++sw) {
-        for (int c = 0; c < nc; ++c) {
+        // this sweep's batches: colour classes, or the Cyclades batches of its order row
+        std::vector<std::vector<int>> batches;
+        if (schedule == 1) {
+            const int32_t* row = order + (size_t)sw * n_moving;
+            std::vector<int32_t> comp(n_moving), bat(n_moving);
+            const int nb = oracle_cyclades_batches(P, row, n_moving, sample_size, comp.data(), bat.data());
+            batches.resize(nb);
+            for (int i = 0; i < n_moving; ++i) batches[bat[i]].push_back(row[i]);
+        } else {
+            batches.resize(nc);
+            for (int s = 0; s < P->n_src; ++s)
+                if (moves[s]) batches[colour[s]].push_back(s);
+        }
+        for (size_t c = 0; c < batches.size(); ++c) {
             std::vector<PatchVals> pv;
             build_patch_values(*P, theta, pv);
-            std::vector<int> members;
-            for (int s = 0; s < P->n_src; ++s)
-                if (colour[s] == c && moves[s]) members.push_back(s);
+            const std::vector<int>& members = batches[c];
 #pragma omp parallel for schedule(dynamic, 1)
             for (int k = 0; k < (int)members.size(); ++k) {
                 int s = members[k];

@@ -171,22 +171,40 @@ class Oracle:
         nc = self.L.oracle_colouring(C.byref(self.p), _ptr(col))
         return col, nc
 
+    def cyclades_batches(self, order, sample_size):
+        """(batch_of, comp_of, n_batches) of one order under the Cyclades schedule."""
+        od = np.ascontiguousarray(order, np.int32)
+        b = np.zeros(len(od), np.int32)
+        c = np.zeros(len(od), np.int32)
+        nb = self.L.oracle_cyclades_batches(C.byref(self.p), _ptr(od), C.c_int(len(od)),
+                                            C.c_int(sample_size), _ptr(c), _ptr(b))
+        return b, c, nb
+
     def fit(self, theta, which=None, max_iter=50, grad_tol=1e-8, pred_tol_rel=1e-12,
             delta0=1.0, delta_max=1e3, eta=1e-4, f_noise_rel=1e-13, max_sweeps=20,
-            sweep_tol=1e-8):
+            sweep_tol=1e-8, order=None, sample_size=64):
+        """Block-coordinate fit; with `order` ([max_sweeps][n_moving] permutations of the
+        moving sources) the Cyclades schedule with samples of `sample_size`, else the
+        colour schedule."""
         th = self._th(theta).copy()
         w = None if which is None else np.ascontiguousarray(which, np.int32)
         it = np.zeros(th.shape[0], np.int32)
         st = np.zeros(th.shape[0], np.int32)
         el = C.c_double()
         sw = C.c_int32()
+        od = None
+        if order is not None:
+            od = np.ascontiguousarray(order, np.int32)
+            n_moving = th.shape[0] if w is None else len(w)
+            assert od.shape == (max_sweeps, n_moving)
         rc = self.L.oracle_fit(C.byref(self.p), _ptr(th), _ptr(w),
                                C.c_int(0 if w is None else len(w)), C.c_int(max_iter),
                                C.c_double(grad_tol), C.c_double(pred_tol_rel),
                                C.c_double(delta0), C.c_double(delta_max), C.c_double(eta),
                                C.c_double(f_noise_rel), C.c_int(max_sweeps),
                                C.c_double(sweep_tol), _ptr(it), _ptr(st), C.byref(el),
-                               C.byref(sw))
+                               C.byref(sw), C.c_int(0 if order is None else 1),
+                               C.c_int(sample_size), _ptr(od))
         if rc != 0:
             raise ValueError(f"oracle_fit failed: {rc}")
         return th, it, st, el.value, sw.value

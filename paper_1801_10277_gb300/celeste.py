@@ -18,6 +18,8 @@ NPARAM = 44
 NFREE = 41
 FP64 = 0
 FP32 = 1          # FP32 per-pixel arithmetic, FP64 accumulation
+SCHED_COLOUR = 0    # fit schedule: one batch per colour of a greedy colouring
+SCHED_CYCLADES = 1  # fit schedule: connected components of random samples
 
 OK, ERR_ARG, ERR_NOT_PD, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 
@@ -50,7 +52,8 @@ class celeste_fit_options(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("grad_tol", C.c_double), ("pred_tol_rel", C.c_double),
                 ("delta0", C.c_double), ("delta_max", C.c_double), ("eta", C.c_double),
                 ("f_noise_rel", C.c_double), ("precision", C.c_int32), ("max_sweeps", C.c_int32),
-                ("sweep_tol", C.c_double), ("refine_fp64", C.c_int32)]
+                ("sweep_tol", C.c_double), ("refine_fp64", C.c_int32), ("schedule", C.c_int32),
+                ("sample_size", C.c_int32), ("seed", C.c_uint64), ("order", C.c_void_p)]
 
 
 _lib = None
@@ -62,7 +65,7 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
            "celeste_profile_enable", "celeste_profile_read",
            "celeste_patch_elbo_grad_noalloc", "celeste_grad_device", "celeste_autotune",
-           "celeste_set_tuning"]
+           "celeste_set_tuning", "celeste_cyclades_batches"]
 
 
 def lib_path():
@@ -134,6 +137,22 @@ def _check(st):
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def cyclades_batches(nbr_offsets, nbrs, order, sample_size):
+    """Batch of each position of `order`, and the order position of the first member of
+    its component, under the Cyclades schedule over the neighbour graph (CSR); returns
+    (batch_of, comp_of, n_batches).  Host logic: no CUDA device needed."""
+    L = load()
+    no = np.ascontiguousarray(nbr_offsets, np.int32)
+    nb_ = np.ascontiguousarray(nbrs, np.int32)
+    order = np.ascontiguousarray(order, np.int32)
+    b = np.zeros(len(order), np.int32)
+    c = np.zeros(len(order), np.int32)
+    nb = C.c_int32()
+    _check(L.celeste_cyclades_batches(_p(no), _p(nb_), len(no) - 1, _p(order), len(order),
+                                      int(sample_size), _p(b), _p(c), C.byref(nb)))
+    return b, c, nb.value
 
 
 def fit_options(**kw):
@@ -253,10 +272,17 @@ class Problem:
         it = np.zeros(self.n_src, np.int32)
         st = np.zeros(self.n_src, np.int32)
         el = C.c_double()
+        order = opts.pop("order", None)
+        if isinstance(opts.get("schedule"), str):
+            opts["schedule"] = {"colour": SCHED_COLOUR, "cyclades": SCHED_CYCLADES}[opts["schedule"]]
         o = fit_options(**opts)
+        if order is not None:
+            order = np.ascontiguousarray(order, np.int32)
+            o.order = order.ctypes.data
         _check(self.L.celeste_fit_sources(self.h, _p(th), _p(w), 0 if w is None else len(w),
                                           C.byref(o), _p(it), _p(st), C.byref(el)))
         return th, it, st, el.value
+
 
     # ---- device-pointer calls (torch tensors on the problem's device)
     @staticmethod

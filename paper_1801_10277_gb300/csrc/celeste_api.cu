@@ -741,6 +741,10 @@ celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, con
     if (o.max_iter < 1 || o.max_sweeps < 1 || !(o.delta0 > 0) || !(o.delta_max >= o.delta0))
         return fail(CELESTE_ERR_ARG, "bad fit options");
     if (which && n_which < 0) return fail(CELESTE_ERR_ARG, "n_which < 0");
+    if (o.schedule != CELESTE_SCHED_COLOUR && o.schedule != CELESTE_SCHED_CYCLADES)
+        return fail(CELESTE_ERR_ARG, "schedule must be CELESTE_SCHED_COLOUR or CELESTE_SCHED_CYCLADES");
+    if (o.schedule == CELESTE_SCHED_CYCLADES && o.sample_size < 1)
+        return fail(CELESTE_ERR_ARG, "Cyclades sample_size must be >= 1");
     celeste_status s = check_theta_host(theta_inout, pr->P.n_src);
     if (s) return s;
     for (int i = 0; i < pr->P.n_src; ++i) {

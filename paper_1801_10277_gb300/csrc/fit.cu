@@ -21,9 +21,11 @@
 // the items of a source that has stopped iterating, so a replay costs in proportion to
 // the sources still active.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "internal.cuh"
@@ -695,6 +697,69 @@ Batch make_batch(const celeste_problem* pr, const std::vector<int32_t>& members)
     return B;
 }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output for counter c is the
+// finaliser applied to seed + (c + 1) * golden gamma.
+uint64_t splitmix64(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Sweep g's visiting order when the caller gives none: Fisher-Yates over the moving
+// sources in ascending id, draw i of sweep g keyed by counter (g << 32) + i.
+void shuffled_order(const std::vector<int32_t>& moving, uint64_t seed, int g, std::vector<int32_t>& out) {
+    out = moving;
+    for (int i = (int)out.size() - 1; i > 0; --i) {
+        const uint64_t r = splitmix64(seed, ((uint64_t)(uint32_t)g << 32) + (uint64_t)i);
+        std::swap(out[i], out[(size_t)(r % (uint64_t)(i + 1))]);
+    }
+}
+
+int uf_find(std::vector<int>& up, int i) {
+    while (up[i] != i) {
+        up[i] = up[up[i]];
+        i = up[i];
+    }
+    return i;
+}
+
+// Cyclades batches of one order (documented with celeste_cyclades_batches).  pos[s] is
+// scratch of size n_src, -1 on entry and on return.  Union-find over the sample's
+// internal edges; a component's root is its earliest member, so ranks follow order.
+int cyclades_batches(const int32_t* nbr_off, const int32_t* nbrs, const int32_t* order, int m, int B,
+                     std::vector<int>& pos, int32_t* batch_of, int32_t* comp_of) {
+    std::vector<int> up, cnt;
+    int base = 0;
+    for (int k0 = 0; k0 < m; k0 += B) {
+        const int k1 = std::min(m, k0 + B);
+        const int L = k1 - k0;
+        for (int i = 0; i < L; ++i) pos[order[k0 + i]] = i;
+        up.resize(L);
+        for (int i = 0; i < L; ++i) up[i] = i;
+        for (int i = 0; i < L; ++i) {
+            const int s = order[k0 + i];
+            for (int e = nbr_off[s]; e < nbr_off[s + 1]; ++e) {
+                const int j = pos[nbrs[e]];
+                if (j < 0) continue;
+                const int a = uf_find(up, i), b = uf_find(up, j);
+                if (a != b) up[std::max(a, b)] = std::min(a, b);   // keep the earliest member
+            }
+        }
+        cnt.assign(L, 0);
+        int rounds = 0;
+        for (int i = 0; i < L; ++i) {
+            const int root = uf_find(up, i);
+            batch_of[k0 + i] = base + cnt[root];
+            if (comp_of) comp_of[k0 + i] = k0 + root;
+            rounds = std::max(rounds, ++cnt[root]);
+        }
+        for (int i = 0; i < L; ++i) pos[order[k0 + i]] = -1;
+        base += rounds;
+    }
+    return base;
+}
+
 }  // namespace
 
 }  // namespace cel
@@ -720,20 +785,6 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
         cudaError_t e_ = (x);                                \
         if (e_ != cudaSuccess) return cuda_err(e_, #x);      \
     } while (0)
-    // greedy colouring in ascending id over the neighbour graph
-    std::vector<int32_t> colour(n, 0);
-    int ncol = 0;
-    for (int s = 0; s < n; ++s) {
-        std::vector<char> used(ncol + 2, 0);
-        for (int e = pr->nbr_off[s]; e < pr->nbr_off[s + 1]; ++e) {
-            const int o = pr->nbrs[e];
-            if (o < s && colour[o] <= ncol) used[colour[o]] = 1;
-        }
-        int c = 0;
-        while (used[c]) ++c;
-        colour[s] = c;
-        ncol = std::max(ncol, c + 1);
-    }
     std::vector<char> moves(n, which ? 0 : 1);
     if (which)
         for (int k = 0; k < n_which; ++k) {
@@ -743,19 +794,102 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             }
             moves[which[k]] = 1;
         }
-    std::vector<Batch> batches(ncol);
+    std::vector<int32_t> moving;
+    for (int s = 0; s < n; ++s)
+        if (moves[s]) moving.push_back(s);
+    const int m = (int)moving.size();
+    const bool cyclades = opts->schedule == CELESTE_SCHED_CYCLADES;
+    // colour schedule: greedy colouring in ascending id over the neighbour graph, one
+    // batch per colour, built once
+    std::vector<Batch> colour_batches;
+    if (!cyclades) {
+        std::vector<int32_t> colour(n, 0);
+        int ncol = 0;
+        for (int s = 0; s < n; ++s) {
+            std::vector<char> used(ncol + 2, 0);
+            for (int e = pr->nbr_off[s]; e < pr->nbr_off[s + 1]; ++e) {
+                const int o = pr->nbrs[e];
+                if (o < s && colour[o] <= ncol) used[colour[o]] = 1;
+            }
+            int c = 0;
+            while (used[c]) ++c;
+            colour[s] = c;
+            ncol = std::max(ncol, c + 1);
+        }
+        std::vector<std::vector<int32_t>> members(ncol);
+        for (int s : moving) members[colour[s]].push_back(s);
+        for (int c = 0; c < ncol; ++c) colour_batches.push_back(make_batch(pr, members[c]));
+    } else if (opts->order) {
+        // every row must be a permutation of the moving sources
+        std::vector<int> seen(n, -1);
+        for (int r = 0; r < opts->max_sweeps; ++r)
+            for (int i = 0; i < m; ++i) {
+                const int s = opts->order[(size_t)r * m + i];
+                if (s < 0 || s >= n || !moves[s] || seen[s] == r) {
+                    char buf[96];
+                    snprintf(buf, sizeof buf, "order row %d is not a permutation of the moving sources", r);
+                    set_last_error(buf);
+                    return CELESTE_ERR_ARG;
+                }
+                seen[s] = r;
+            }
+    }
+    // device buffers for the largest batch: a colour, or (Cyclades: at most one source
+    // per component of a sample) the sample_size moving sources with the most work
     size_t maxB = 1, maxP = 1, maxI = 1;
     int64_t maxSp = 1;
-    for (int c = 0; c < ncol; ++c) {
-        std::vector<int32_t> mem;
-        for (int s = 0; s < n; ++s)
-            if (colour[s] == c && moves[s]) mem.push_back(s);
-        batches[c] = make_batch(pr, mem);
-        maxB = std::max(maxB, mem.size());
-        maxP = std::max(maxP, batches[c].geo.size());
-        maxI = std::max(maxI, batches[c].items.size());
-        maxSp = std::max(maxSp, batches[c].n_sp);
+    if (!cyclades) {
+        for (const Batch& B : colour_batches) {
+            maxB = std::max(maxB, B.src.size());
+            maxP = std::max(maxP, B.geo.size());
+            maxI = std::max(maxI, B.items.size());
+            maxSp = std::max(maxSp, B.n_sp);
+        }
+    } else {
+        std::vector<int64_t> np_, ni_, nsp_;
+        for (int s : moving) {
+            int64_t a = 0, b = 0, c = 0;
+            for (int p = pr->patch_off[s]; p < pr->patch_off[s + 1]; ++p) {
+                const int64_t npx = (int64_t)pr->geo[p].w * pr->geo[p].h;
+                ++a;
+                b += (npx + CHUNK - 1) / CHUNK;
+                c += npx;
+            }
+            np_.push_back(a);
+            ni_.push_back(b);
+            nsp_.push_back(c);
+        }
+        const size_t top = std::min<size_t>((size_t)opts->sample_size, moving.size());
+        auto top_sum = [&](std::vector<int64_t>& v) {
+            std::sort(v.begin(), v.end(), std::greater<int64_t>());
+            int64_t t = 0;
+            for (size_t i = 0; i < top; ++i) t += v[i];
+            return t;
+        };
+        maxB = std::max<size_t>(1, top);
+        maxP = std::max<size_t>(1, (size_t)top_sum(np_));
+        maxI = std::max<size_t>(1, (size_t)top_sum(ni_));
+        maxSp = std::max<int64_t>(1, top_sum(nsp_));
     }
+    // the batches of sweep g (counted over both precision phases)
+    std::vector<int> pos(n, -1);
+    std::vector<int32_t> ord, bof;
+    auto sweep_batches = [&](int g, std::vector<Batch>& out) {
+        if (!cyclades) {
+            out = colour_batches;
+            return;
+        }
+        if (opts->order) ord.assign(opts->order + (size_t)(g % opts->max_sweeps) * m,
+                                    opts->order + (size_t)(g % opts->max_sweeps + 1) * m);
+        else shuffled_order(moving, opts->seed, g, ord);
+        bof.resize(m);
+        const int nbt = cyclades_batches(pr->nbr_off.data(), pr->nbrs.data(), ord.data(), m,
+                                         opts->sample_size, pos, bof.data(), nullptr);
+        std::vector<std::vector<int32_t>> members(nbt);
+        for (int i = 0; i < m; ++i) members[bof[i]].push_back(ord[i]);
+        out.clear();
+        for (int b = 0; b < nbt; ++b) out.push_back(make_batch(pr, members[b]));
+    };
     // device buffers for the largest batch
     DevBuf mem;
     const size_t rs = sizeof(double);   // per-pixel batch buffers serve both precisions
@@ -808,6 +942,8 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
     std::vector<TrState> hst(maxB);
     // phase 0 in the requested precision; with FP32 and refine_fp64, phase 1 polishes in FP64
     const int nphase = (opts->precision == CELESTE_FP32_ACC64 && opts->refine_fp64) ? 2 : 1;
+    std::vector<Batch> batches;
+    int g_sweep = 0;
     for (int phase = 0; phase < nphase; ++phase) {
     prec = (phase == 0) ? opts->precision : CELESTE_FP64;
     if (phase == 1) {
@@ -815,8 +951,9 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
         if (s2) return s2;
     }
     int sw = 0;
-    for (; sw < opts->max_sweeps; ++sw) {
-        for (int c = 0; c < ncol; ++c) {
+    for (; sw < opts->max_sweeps; ++sw, ++g_sweep) {
+        sweep_batches(g_sweep, batches);
+        for (size_t c = 0; c < batches.size(); ++c) {
             const Batch& B = batches[c];
             const int nb = (int)B.src.size();
             if (nb == 0) continue;
@@ -955,6 +1092,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
         prev = cur;
         if (rel < opts->sweep_tol) {
             ++sw;
+            ++g_sweep;
             break;
         }
     }
@@ -980,6 +1118,49 @@ void celeste_fit_options_default(celeste_fit_options* o) {
     o->max_sweeps = 20;
     o->sweep_tol = 1e-8;
     o->refine_fp64 = 1;
+    o->schedule = CELESTE_SCHED_COLOUR;
+    o->sample_size = 64;
+    o->seed = 0;
+    o->order = nullptr;
+}
+
+celeste_status celeste_cyclades_batches(const int32_t* nbr_off, const int32_t* nbrs, int32_t n,
+                                        const int32_t* order, int32_t n_order, int32_t sample_size,
+                                        int32_t* batch_of, int32_t* comp_of, int32_t* n_batches) {
+    if (!nbr_off || !n_batches || n < 0 || n_order < 0 || (n_order > 0 && (!order || !batch_of)) ||
+        sample_size < 1) {
+        set_last_error("celeste_cyclades_batches: null pointer, n_src or n_order < 0, or sample_size < 1");
+        return CELESTE_ERR_ARG;
+    }
+    if (nbr_off[0] != 0 || (nbr_off[n] > 0 && !nbrs)) {
+        set_last_error("celeste_cyclades_batches: bad neighbour offsets");
+        return CELESTE_ERR_ARG;
+    }
+    for (int s = 0; s < n; ++s) {
+        if (nbr_off[s + 1] < nbr_off[s]) {
+            set_last_error("celeste_cyclades_batches: neighbour offsets decrease");
+            return CELESTE_ERR_ARG;
+        }
+    }
+    for (int e = 0; e < nbr_off[n]; ++e)
+        if (nbrs[e] < 0 || nbrs[e] >= n) {
+            set_last_error("celeste_cyclades_batches: neighbour id out of range");
+            return CELESTE_ERR_ARG;
+        }
+    std::vector<int> pos(n, -1);
+    for (int i = 0; i < n_order; ++i) {
+        const int s = order[i];
+        if (s < 0 || s >= n || pos[s] >= 0) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "celeste_cyclades_batches: order[%d] = %d is out of range or repeated", i, s);
+            set_last_error(buf);
+            return CELESTE_ERR_ARG;
+        }
+        pos[s] = i;
+    }
+    for (int i = 0; i < n_order; ++i) pos[order[i]] = -1;
+    *n_batches = cyclades_batches(nbr_off, nbrs, order, n_order, sample_size, pos, batch_of, comp_of);
+    return CELESTE_OK;
 }
 
 }  // extern "C"

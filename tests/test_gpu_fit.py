@@ -86,3 +86,102 @@ def test_fit_rejects_parameters_outside_the_box(cel):
         P.fit(bad)
     assert e.value.status == cel.ERR_ARG
     P.close()
+
+
+def _orders(rng, moving, sweeps):
+    return np.stack([rng.permutation(moving) for _ in range(sweeps)]).astype(np.int32)
+
+
+def _compare_sweeps(cel, prob, order, sample_size, which=None):
+    """The Cyclades schedule on given sweep orders, every sweep run (no early stop), on
+    both sides: sources that overlap follow one path, so after a fixed number of sweeps
+    the two fits agree to the per-source Newton tolerance (the joint optimum itself is
+    approached along flat ridges where a sweep tolerance stops each side elsewhere)."""
+    orc = Oracle(prob)
+    ns = order.shape[0]
+    moving = np.arange(prob.n_src) if which is None else np.asarray(which)
+    P = cel.Problem(prob)
+    # FP64: ns sweeps.  FP32: ns FP32 sweeps polished by ns FP64 sweeps on the same order
+    # rows, against ns + ns oracle sweeps on those rows.
+    for prec, tpos, tflux, tel in ((cel.FP64, 1e-6, 1e-8, 1e-10), (cel.FP32, 1e-3, 1e-4, 1e-5)):
+        reps = 1 if prec == cel.FP64 else 2
+        o_th, _, _, o_el, o_sw = orc.fit(prob.theta, which=which, max_sweeps=reps * ns,
+                                         sweep_tol=0.0, order=np.tile(order, (reps, 1)),
+                                         sample_size=sample_size)
+        assert o_sw == reps * ns
+        th, it, st, el = P.fit(prob.theta, which=which, precision=prec, refine_fp64=1,
+                               max_sweeps=ns, sweep_tol=0.0, schedule="cyclades", order=order,
+                               sample_size=sample_size)
+        for s in moving:
+            assert np.abs(th[s, 0:2] - o_th[s, 0:2]).max() <= tpos, (prec, s, th[s, :2], o_th[s, :2])
+            assert abs(rflux(th[s]) / rflux(o_th[s]) - 1) <= tflux, (prec, s)
+        assert abs(el - o_el) <= tel * abs(o_el), (prec, el, o_el)
+    P.close()
+
+
+def test_fit_cyclades_tiny(cel):
+    """Two overlapping sources, random sweep orders, samples of two."""
+    prob = synth.config(0)
+    _compare_sweeps(cel, prob, _orders(np.random.default_rng(21), np.arange(2), 3), 2)
+
+
+def connected_cluster(prob, k, start=0):
+    """k sources connected in the neighbour graph (breadth-first from `start`)."""
+    seen, queue = [start], [start]
+    while queue and len(seen) < k:
+        s = queue.pop(0)
+        for o in prob.nbrs[prob.nbr_offsets[s]:prob.nbr_offsets[s + 1]].tolist():
+            if o not in seen and len(seen) < k:
+                seen.append(o)
+                queue.append(o)
+    return np.array(sorted(seen), np.int32)
+
+
+def test_fit_cyclades_crowded_cluster(cel):
+    """Five linked sources of the crowded region moving, the rest fixed; samples of
+    three, so both components and serialised members occur."""
+    prob = synth.config(2)
+    which = connected_cluster(prob, 5)
+    assert len(which) == 5
+    _compare_sweeps(cel, prob, _orders(np.random.default_rng(22), which, 2), 3, which=which)
+
+
+def test_fit_cyclades_is_serially_equivalent(cel):
+    """Cyclades' guarantee: for one order the result is that of updating the sources one
+    at a time in that order, whatever the sample size (bit for bit here: a source's fit
+    reads the same neighbour values and sums in the same order)."""
+    prob = synth.config(2)
+    which = connected_cluster(prob, 12, start=5)
+    order = _orders(np.random.default_rng(23), which, 2)
+    P = cel.Problem(prob)
+    for prec in (cel.FP64, cel.FP32):
+        res = [P.fit(prob.theta, which=which, precision=prec, refine_fp64=0, max_sweeps=2,
+                     sweep_tol=0.0, schedule="cyclades", order=order, sample_size=B)
+               for B in (1, 3, 12)]
+        for th, it, st, el in res[1:]:
+            np.testing.assert_array_equal(th, res[0][0])
+            np.testing.assert_array_equal(it, res[0][1])
+            assert el == res[0][3]
+    P.close()
+
+
+def test_fit_cyclades_generated_orders(cel):
+    """Orders drawn inside the library from a seed: reproducible, ELBO raised, and
+    order rows that are not permutations of the moving set are errors."""
+    prob = synth.config(2)
+    which = connected_cluster(prob, 12, start=5)
+    P = cel.Problem(prob)
+    start = P.elbo(prob.theta, precision=cel.FP64)[0]
+    kw = dict(which=which, precision=cel.FP64, max_sweeps=3, schedule="cyclades", sample_size=4)
+    th1, it1, st1, el1 = P.fit(prob.theta, seed=11, **kw)
+    th2, it2, st2, el2 = P.fit(prob.theta, seed=11, **kw)
+    np.testing.assert_array_equal(th1, th2)
+    assert el1 == el2 and el1 > start
+    bad = np.tile(which, (3, 1))
+    bad[1, 0] = bad[1, 1]
+    with pytest.raises(cel.CelesteError) as e:
+        P.fit(prob.theta, order=bad, **kw)
+    assert e.value.status == cel.ERR_ARG
+    with pytest.raises(cel.CelesteError):
+        P.fit(prob.theta, which=which, schedule="cyclades", sample_size=0)
+    P.close()
