@@ -206,6 +206,34 @@ def reference_arm(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def model_image_fit(cel, prob, P, seed=7):
+    import copy
+    truth = prob.truth.copy()
+    star = truth[:, synth.I_A] >= 0.5
+    truth[:, synth.I_A] = np.where(star, 0.995, 0.005)
+    truth[:, synth.I_A + 1] = 1.0 - truth[:, synth.I_A]
+    E, _ = P.render(truth)
+    rng = np.random.default_rng(seed)
+    pm = copy.copy(prob)
+    pm.images = [copy.copy(im) for im in prob.images]
+    for im, e in zip(pm.images, E):
+        im.pixels = rng.poisson(e).astype(np.float32)
+    Pm = cel.Problem(pm)
+    t0 = time.perf_counter()
+    th_fit, iters, fst, _ = Pm.fit(prob.theta, precision=cel.FP32, max_sweeps=3)
+    secs = time.perf_counter() - t0
+    cat_true = Pm.catalog(truth)
+    cat_fit = Pm.catalog(th_fit)
+    bright = np.exp(truth[:, synth.I_R1]) >= 10.0   # r flux >= 10 nmgy
+    out = {"start": Pm.catalog_score(Pm.catalog(prob.theta), cat_true),
+           "fitted": Pm.catalog_score(cat_fit, cat_true),
+           "fitted_bright": Pm.catalog_score(cat_fit[bright], cat_true[bright]),
+           "seconds": secs, "converged": int((fst == 0).sum()),
+           "data": f"Poisson counts around the model's expected image at the truth (seed {seed})"}
+    Pm.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,6 +418,30 @@ def main():
                "elbo_start": el_start, "elbo_end": el_fit,
                "converged": int((fst == 0).sum()),
                "options": "FP32 pixels, FP64 refinement, <= 3 sweeps, <= 50 iterations per source"}
+        # fit quality against the generator's truth (Table II's error summary; the images
+        # are isotropic blobs, so galaxy shape truth is not in the pixels)
+        cat_true = P.catalog(prob.truth)
+        fit["quality"] = {"start": P.catalog_score(P.catalog(prob.theta), cat_true),
+                          "fitted": P.catalog_score(P.catalog(th_fit), cat_true)}
+        # the same fit on images drawn from the model itself: Poisson counts around the
+        # expected image at the truth (types as q(star) = 0.995 / 0.005)
+        fit["quality_model_images"] = model_image_fit(cel, prob, P)
+
+    # catalog rows with posterior uncertainty for every source (one kernel)
+    d_th = torch.tensor(prob.theta, dtype=torch.float64, device="cuda")
+    d_cat = torch.empty(prob.n_src, cel.CAT_NFIELD, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        P.catalog_device(d_th, d_cat)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(100):
+        P.catalog_device(d_th, d_cat)
+    ev1.record()
+    torch.cuda.synchronize()
+    cat_ms = ev0.elapsed_time(ev1) / 100
+    catalog = {"sources_per_s": prob.n_src / (cat_ms / 1000.0), "ms_per_call": cat_ms,
+               "fields": cel.CAT_NFIELD}
 
     # convergence per sweep of the two conflict-free schedules (Section IV-D): greedy
     # colouring vs Cyclades samples (sweep k's order drawn in the library from seed k);
@@ -444,7 +496,7 @@ def main():
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "hessian": hessian, "fit": fit, "fit_schedules": schedules,
+            "hessian": hessian, "fit": fit, "fit_schedules": schedules, "catalog": catalog,
             "gpu_launches": int(round(launches_per_step * args.steps)),
         }
         print(json.dumps(line), flush=True)

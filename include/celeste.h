@@ -334,6 +334,89 @@ celeste_status celeste_patch_elbo_grad_noalloc(const celeste_image* im, const ce
                                                int32_t precision, double* d_elbo_total,
                                                double* d_elbo_local, double* d_grad, void* stream);
 
+/*
+ * Catalog with posterior uncertainty (Section VIII: besides point estimates the
+ * variational posterior gives the probability of each type and the uncertainty of
+ * brightness and colours).  One row of CELESTE_CAT_NFIELD doubles per source, from
+ * theta alone:
+ *   CAT_U0, CAT_U1        position u (world coordinates)
+ *   CAT_PSTAR             q(star) = a_star;  CAT_IS_STAR = 1 if a_star >= 0.5 else 0
+ *   per type t (CAT_STAR + k, CAT_GAL + k): under q, log l_b | t is Gaussian with mean
+ *   r1_t + beta_b . c1_t and variance r2_t + sum_j beta_bj^2 c2_tj (log-normal
+ *   brightness, colours as adjacent-band log ratios), so the magnitude
+ *   m_b = 22.5 - 2.5 log10(l_b [nmgy]) is Gaussian:
+ *     k = CAT_RMAG, CAT_RMAG_SD     r-band magnitude mean and standard deviation
+ *     k = CAT_RFLUX, CAT_RFLUX_SD   r-band flux E[l_r | t] and its standard deviation (nmgy)
+ *     k = CAT_COLOR + j, CAT_COLOR_SD + j   magnitude colours m_j - m_{j+1}
+ *                                   (u-g, g-r, r-i, i-z): 2.5 / ln 10 * c1_tj, sd from c2_tj
+ *     k = CAT_MAG + b, CAT_MAG_SD + b       magnitude in band b (u g r i z)
+ *   CAT_RFLUX_MIX, CAT_RFLUX_MIX_SD   r-band flux mean and sd with the type marginalised
+ *                                     (weights a_star, a_gal, which sum to 1 in the model)
+ *   CAT_EDEV, CAT_AXIS, CAT_ANGLE_DEG (in [0, 180)), CAT_SCALE (world units)
+ */
+enum {
+    CELESTE_CAT_U0 = 0, CELESTE_CAT_U1 = 1, CELESTE_CAT_PSTAR = 2, CELESTE_CAT_IS_STAR = 3,
+    CELESTE_CAT_STAR = 4, CELESTE_CAT_GAL = 26, CELESTE_CAT_TYPE_NFIELD = 22,
+    /* offsets within a type block */
+    CELESTE_CAT_RMAG = 0, CELESTE_CAT_RMAG_SD = 1, CELESTE_CAT_RFLUX = 2, CELESTE_CAT_RFLUX_SD = 3,
+    CELESTE_CAT_COLOR = 4, CELESTE_CAT_COLOR_SD = 8, CELESTE_CAT_MAG = 12, CELESTE_CAT_MAG_SD = 17,
+    /* after both type blocks */
+    CELESTE_CAT_RFLUX_MIX = 48, CELESTE_CAT_RFLUX_MIX_SD = 49, CELESTE_CAT_EDEV = 50,
+    CELESTE_CAT_AXIS = 51, CELESTE_CAT_ANGLE_DEG = 52, CELESTE_CAT_SCALE = 53,
+    CELESTE_CAT_NFIELD = 54
+};
+
+/* catalog[n_src][CELESTE_CAT_NFIELD] (host) from theta[n_src][44] (host); one kernel
+ * thread per source.  Errors: CELESTE_ERR_ARG (null pointers, theta outside the
+ * parameter domain: r2, c2 <= 0 or non-finite entries), CELESTE_ERR_CUDA. */
+celeste_status celeste_catalog(celeste_problem* prob, const double* theta, double* catalog);
+/* Same with device pointers, enqueued on `stream`, no synchronisation; domain errors
+ * are reported through celeste_device_status(). */
+celeste_status celeste_catalog_device(celeste_problem* prob, const double* d_theta,
+                                      double* d_catalog, void* stream);
+
+/*
+ * Fit quality against a known truth, the error summary of Table II: from an estimated
+ * and a true catalog ([n][CELESTE_CAT_NFIELD] each, host) of the same sources, the
+ * types taken from each catalog's CAT_IS_STAR and brightness / colours from each
+ * catalog's own classified type:
+ *   SCORE_POSITION      mean distance between positions (world units)
+ *   SCORE_MISSED_GAL    fraction of true galaxies classified as stars
+ *   SCORE_MISSED_STAR   fraction of true stars classified as galaxies
+ *   SCORE_BRIGHTNESS    mean |r-band magnitude error|
+ *   SCORE_COLOR + j     mean |colour error| for u-g, g-r, r-i, i-z (magnitudes)
+ *   SCORE_PROFILE, SCORE_AXIS, SCORE_SCALE, SCORE_ANGLE_DEG   mean |e_dev|, |axis
+ *                       ratio|, |scale| and angle (degrees, modulo 180) errors over
+ *                       the true galaxies
+ *   SCORE_N_GAL, SCORE_N_STAR   counts of true galaxies and stars
+ * Means over an empty set are 0.  One CTA with a fixed-order FP64 reduction, so the
+ * result does not depend on timing.  Errors: CELESTE_ERR_ARG, CELESTE_ERR_CUDA.
+ */
+enum {
+    CELESTE_SCORE_POSITION = 0, CELESTE_SCORE_MISSED_GAL = 1, CELESTE_SCORE_MISSED_STAR = 2,
+    CELESTE_SCORE_BRIGHTNESS = 3, CELESTE_SCORE_COLOR = 4, CELESTE_SCORE_PROFILE = 8,
+    CELESTE_SCORE_AXIS = 9, CELESTE_SCORE_SCALE = 10, CELESTE_SCORE_ANGLE_DEG = 11,
+    CELESTE_SCORE_N_GAL = 12, CELESTE_SCORE_N_STAR = 13, CELESTE_SCORE_NFIELD = 14
+};
+celeste_status celeste_catalog_score(celeste_problem* prob, const double* cat_est,
+                                     const double* cat_true, int32_t n, double* score);
+
+/*
+ * The model's expected image and its variance under q (Section III: E[F] and Var[F]
+ * per pixel, sources independent): e[m] = sky_m + sum over the patches covering pixel m
+ * of the source's E[F_s], v[m] = sum of Var[F_s] (0 outside every patch), FP64, for
+ * every pixel of every image, images concatenated in creation order, each row-major
+ * ([sum_n height_n * width_n]).  Used to draw data from the model itself (e.g. Poisson
+ * counts around e).  The evaluation overwrites the problem's per-source scratch, so it
+ * must not fall between celeste_elbo_device and celeste_grad_device.  Host pointers;
+ * v nullable.  Errors as celeste_elbo.
+ */
+celeste_status celeste_render(celeste_problem* prob, const double* theta, double* e, double* v);
+/* Same with device pointers on `stream` (e and v: [sum_n height_n * width_n] doubles, v
+ * nullable), no synchronisation; domain errors via celeste_device_status(). */
+celeste_status celeste_render_device(celeste_problem* prob, const double* d_theta, double* d_e,
+                                     double* d_v, void* stream);
+
 /* Thread-local message describing the calling thread's last error. */
 const char* celeste_last_error(void);
 

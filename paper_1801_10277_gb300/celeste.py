@@ -65,7 +65,22 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_hess_device", "celeste_device_status", "celeste_last_error",
            "celeste_profile_enable", "celeste_profile_read",
            "celeste_patch_elbo_grad_noalloc", "celeste_grad_device", "celeste_autotune",
-           "celeste_set_tuning", "celeste_cyclades_batches"]
+           "celeste_set_tuning", "celeste_cyclades_batches", "celeste_catalog",
+           "celeste_catalog_device", "celeste_catalog_score", "celeste_render",
+           "celeste_render_device"]
+
+# catalog row layout (CELESTE_CAT_*): position, type, per-type brightness / colours with
+# their posterior standard deviations, the type-marginal r flux, galaxy shape
+_COL = ("ug", "gr", "ri", "iz")
+_TYPE_FIELDS = (["rmag", "rmag_sd", "rflux", "rflux_sd"] + [f"color_{c}" for c in _COL]
+                + [f"color_{c}_sd" for c in _COL] + [f"mag_{b}" for b in "ugriz"]
+                + [f"mag_{b}_sd" for b in "ugriz"])
+CAT_FIELDS = (["u0", "u1", "p_star", "is_star"] + [f"star_{f}" for f in _TYPE_FIELDS]
+              + [f"gal_{f}" for f in _TYPE_FIELDS]
+              + ["rflux_mix", "rflux_mix_sd", "e_dev", "e_axis", "angle_deg", "scale"])
+CAT_NFIELD = len(CAT_FIELDS)
+SCORE_FIELDS = ["position", "missed_gal", "missed_star", "brightness"] + \
+    [f"color_{c}" for c in _COL] + ["profile", "axis", "scale", "angle_deg", "n_gal", "n_star"]
 
 
 def lib_path():
@@ -114,6 +129,16 @@ def load(build_if_missing=False):
     L.celeste_autotune.restype = i32
     L.celeste_set_tuning.argtypes = [vp, i32, i32, i32, i32]
     L.celeste_set_tuning.restype = i32
+    L.celeste_cyclades_batches.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp, vp]
+    L.celeste_cyclades_batches.restype = i32
+    L.celeste_catalog.argtypes = [vp, vp, vp]
+    L.celeste_catalog_device.argtypes = [vp, vp, vp, vp]
+    L.celeste_catalog_score.argtypes = [vp, vp, vp, i32, vp]
+    L.celeste_render.argtypes = [vp, vp, vp, vp]
+    L.celeste_render_device.argtypes = [vp, vp, vp, vp, vp]
+    for f in ("celeste_catalog", "celeste_catalog_device", "celeste_catalog_score", "celeste_render",
+              "celeste_render_device"):
+        getattr(L, f).restype = i32
     L.celeste_device_status.argtypes = [vp]
     L.celeste_device_status.restype = i32
     L.celeste_profile_enable.argtypes = [vp, i32]
@@ -169,6 +194,7 @@ class Problem:
     def __init__(self, prob):
         L = load()
         self.n_src = int(prob.theta.shape[0])
+        self.shapes = [tuple(im.pixels.shape) for im in prob.images]
         keep = []
         imgs = (celeste_image * len(prob.images))()
         for i, im in enumerate(prob.images):
@@ -283,6 +309,41 @@ class Problem:
                                           C.byref(o), _p(it), _p(st), C.byref(el)))
         return th, it, st, el.value
 
+
+    def render(self, theta):
+        """The model's expected image E[F] and variance Var[F] at theta, one [H][W] array
+        per image (FP64)."""
+        th = self._theta(theta)
+        npx = sum(h * w for h, w in self.shapes)
+        e = np.zeros(npx, np.float64)
+        v = np.zeros(npx, np.float64)
+        _check(self.L.celeste_render(self.h, _p(th), _p(e), _p(v)))
+        out_e, out_v, off = [], [], 0
+        for h, w in self.shapes:
+            out_e.append(e[off:off + h * w].reshape(h, w))
+            out_v.append(v[off:off + h * w].reshape(h, w))
+            off += h * w
+        return out_e, out_v
+
+    def catalog(self, theta):
+        """Catalog rows [n_src][CAT_NFIELD] (columns named by CAT_FIELDS)."""
+        th = self._theta(theta)
+        out = np.zeros((self.n_src, CAT_NFIELD), np.float64)
+        _check(self.L.celeste_catalog(self.h, _p(th), _p(out)))
+        return out
+
+    def catalog_score(self, cat_est, cat_true):
+        """Table II style error summary of cat_est against cat_true: dict by SCORE_FIELDS."""
+        e = np.ascontiguousarray(cat_est, np.float64)
+        t = np.ascontiguousarray(cat_true, np.float64)
+        assert e.shape == t.shape and e.shape[1:] == (CAT_NFIELD,)
+        out = np.zeros(len(SCORE_FIELDS), np.float64)
+        _check(self.L.celeste_catalog_score(self.h, _p(e), _p(t), e.shape[0], _p(out)))
+        return dict(zip(SCORE_FIELDS, out.tolist()))
+
+    def catalog_device(self, d_theta, d_cat):
+        _check(self.L.celeste_catalog_device(self.h, self._dp(d_theta), self._dp(d_cat),
+                                             self._stream()))
 
     # ---- device-pointer calls (torch tensors on the problem's device)
     @staticmethod

@@ -952,6 +952,113 @@ celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int3
     return CELESTE_OK;
 }
 
+celeste_status celeste_catalog_device(celeste_problem* pr, const double* d_theta, double* d_cat,
+                                      void* stream) {
+    if (!pr || (pr->P.n_src > 0 && (!d_theta || !d_cat))) return fail(CELESTE_ERR_ARG, "null problem or pointer");
+    CEL_CUDA(cudaSetDevice(pr->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    pr->last_stream = st;
+    CEL_CUDA(cudaMemsetAsync(pr->P.status, 0, sizeof(int32_t), st));
+    CEL_CUDA(launch_catalog(pr->P.n_src, d_theta, d_cat, pr->P.status, st));
+    return CELESTE_OK;
+}
+
+celeste_status celeste_catalog(celeste_problem* pr, const double* theta, double* cat) {
+    if (!pr || !theta || !cat) return fail(CELESTE_ERR_ARG, "null problem or pointer");
+    const int n = pr->P.n_src;
+    for (int s = 0; s < n; ++s) {
+        const double* th = theta + (size_t)NP * s;
+        for (int i = 0; i < NP; ++i)
+            if (!isfinite(th[i])) return fail(CELESTE_ERR_ARG, "theta[%d][%d] is not finite", s, i);
+        for (int t = 0; t < 2; ++t) {
+            if (!(th[P_R2 + t] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: r2 <= 0", s);
+            for (int j = 0; j < 4; ++j)
+                if (!(th[P_C2 + 4 * t + j] > 0)) return fail(CELESTE_ERR_ARG, "theta[%d]: c2 <= 0", s);
+        }
+    }
+    celeste_status s = ensure_out(pr);   // n * (1 + 44 + 44^2) doubles: room for the rows
+    if (s) return s;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice, pr->stream));
+    s = celeste_catalog_device(pr, pr->d_theta, pr->d_out, pr->stream);
+    if (s) return s;
+    CEL_CUDA(cudaMemcpyAsync(cat, pr->d_out, sizeof(double) * CELESTE_CAT_NFIELD * n, cudaMemcpyDeviceToHost,
+                             pr->stream));
+    CEL_CUDA(cudaStreamSynchronize(pr->stream));
+    return CELESTE_OK;
+}
+
+celeste_status celeste_catalog_score(celeste_problem* pr, const double* est, const double* tru, int32_t n,
+                                     double* score) {
+    if (!pr || !score || n < 0 || (n > 0 && (!est || !tru))) return fail(CELESTE_ERR_ARG, "null pointer or n < 0");
+    CEL_CUDA(cudaSetDevice(pr->device));
+    const size_t rows = (size_t)CELESTE_CAT_NFIELD * n;
+    const size_t need = 2 * rows + CELESTE_SCORE_NFIELD;
+    if (pr->scr_cap < need) {
+        void* p;
+        celeste_status s = dalloc(pr, &p, need * sizeof(double));
+        if (s) return s;
+        pr->d_scr = (double*)p;
+        pr->scr_cap = need;
+    }
+    double* d_est = pr->d_scr;
+    double* d_tru = d_est + rows;
+    double* d_score = d_tru + rows;
+    if (n > 0) {
+        CEL_CUDA(cudaMemcpyAsync(d_est, est, sizeof(double) * rows, cudaMemcpyHostToDevice, pr->stream));
+        CEL_CUDA(cudaMemcpyAsync(d_tru, tru, sizeof(double) * rows, cudaMemcpyHostToDevice, pr->stream));
+    }
+    CEL_CUDA(launch_score(n, d_est, d_tru, d_score, pr->stream));
+    CEL_CUDA(cudaMemcpyAsync(score, d_score, sizeof(double) * CELESTE_SCORE_NFIELD, cudaMemcpyDeviceToHost,
+                             pr->stream));
+    CEL_CUDA(cudaStreamSynchronize(pr->stream));
+    pr->last_stream = pr->stream;
+    return CELESTE_OK;
+}
+
+celeste_status celeste_render_device(celeste_problem* pr, const double* d_theta, double* d_e, double* d_v,
+                                     void* stream) {
+    if (!pr || !d_theta || !d_e) return fail(CELESTE_ERR_ARG, "null problem, theta or E image");
+    CEL_CUDA(cudaSetDevice(pr->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    pr->last_stream = st;
+    // the FP64 evaluation's map passes with the caller's images as the maps: k_contrib
+    // writes the singly covered pixels, k_gather the multiply covered ones
+    DevProblem R = pr->P;
+    R.emap = d_e;
+    R.vmap = d_v ? d_v : pr->P.vmap;
+    CEL_CUDA(cudaMemsetAsync(R.status, 0, sizeof(int32_t), st));
+    CEL_CUDA(launch_fill_sky(R, d_e, (double*)R.vmap, st));
+    CEL_CUDA(launch_prep(R, d_theta, CELESTE_FP64, st));
+    CEL_CUDA(launch_contrib(R, CELESTE_FP64, st));
+    CEL_CUDA(launch_gather(R, CELESTE_FP64, st));
+    return CELESTE_OK;
+}
+
+celeste_status celeste_render(celeste_problem* pr, const double* theta, double* e, double* v) {
+    if (!pr || !theta || !e) return fail(CELESTE_ERR_ARG, "null problem, theta or E image");
+    celeste_status s = check_theta_host(theta, pr->P.n_src);
+    if (s) return s;
+    CEL_CUDA(cudaSetDevice(pr->device));
+    const size_t npx = (size_t)pr->P.n_px;
+    const size_t need = 2 * npx;
+    if (pr->scr_cap < need) {
+        void* p;
+        s = dalloc(pr, &p, need * sizeof(double));
+        if (s) return s;
+        pr->d_scr = (double*)p;
+        pr->scr_cap = need;
+    }
+    CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * pr->P.n_src, cudaMemcpyHostToDevice,
+                             pr->stream));
+    s = celeste_render_device(pr, pr->d_theta, pr->d_scr, pr->d_scr + npx, pr->stream);
+    if (s) return s;
+    CEL_CUDA(cudaMemcpyAsync(e, pr->d_scr, sizeof(double) * npx, cudaMemcpyDeviceToHost, pr->stream));
+    if (v) CEL_CUDA(cudaMemcpyAsync(v, pr->d_scr + npx, sizeof(double) * npx, cudaMemcpyDeviceToHost, pr->stream));
+    CEL_CUDA(cudaStreamSynchronize(pr->stream));
+    return celeste_device_status(pr);
+}
+
 celeste_status celeste_device_status(celeste_problem* pr) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
     CEL_CUDA(cudaSetDevice(pr->device));

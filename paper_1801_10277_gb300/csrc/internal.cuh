@@ -252,4 +252,10 @@ cudaError_t launch_finalize(const DevProblem& P, const double* d_theta, int prec
                             double* d_total, double* d_local, double* d_grad, double* d_hess,
                             cudaStream_t st);
 
+// catalog rows (one thread per source) and the Table II error summary (one CTA)
+cudaError_t launch_catalog(int n, const double* d_theta, double* d_cat, int32_t* d_status, cudaStream_t st);
+cudaError_t launch_score(int n, const double* d_est, const double* d_true, double* d_score, cudaStream_t st);
+// E = sky and Var = 0 over every pixel of every image (FP64, concatenated image layout)
+cudaError_t launch_fill_sky(const DevProblem& P, double* d_e, double* d_v, cudaStream_t st);
+
 }  // namespace cel

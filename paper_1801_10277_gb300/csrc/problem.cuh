@@ -44,6 +44,8 @@ struct celeste_problem {
     double* d_theta = nullptr;
     double* d_out = nullptr;     // total(1) | local(n_src) | grad(n_src*44) | hess(n_src*44*44)
     size_t out_cap = 0;
+    double* d_scr = nullptr;     // catalog / score scratch, grown on demand
+    size_t scr_cap = 0;
     // per-kernel CUDA-event timing (celeste_profile_*)
     bool profile = false;
     struct Rec { std::string name; cudaEvent_t a, b; };
