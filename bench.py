@@ -247,9 +247,9 @@ def main():
     ap.add_argument("--no-schedules", action="store_true",
                     help="skip the colour vs Cyclades convergence-per-sweep leg")
     ap.add_argument("--schedule-sweeps", type=int, default=4)
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4],
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
-                         "4 sweep field; the JSON line names it")
+                         "4 sweep field, 5 deep stack (480 images per source); the JSON line names it")
     ap.add_argument("--tuning", default=None,
                     help="contrib,adjoint,fused_cap,gather_sep codes to use instead of autotuning (e.g. 2,1,0,0)")
     args = ap.parse_args()

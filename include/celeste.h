@@ -123,6 +123,20 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                                       const int32_t* patch_offsets, const celeste_patch* patches,
                                       const int32_t* nbr_offsets, const int32_t* nbrs,
                                       celeste_problem** out);
+/*
+ * The same with a world -> pixel map per patch (multi-epoch data whose images carry a
+ * non-linear WCS: the caller linearises each image's map at the patch's source,
+ * pixel = A_p u + t_p near the source, Section III's image metadata Lambda_n evaluated
+ * per source).  patch_wcs[n_patches][6] in celeste_image.wcs layout, or NULL (every
+ * patch uses its image's wcs).  Position and galaxy shape of the source in that patch
+ * use its map; everything else is as in celeste_problem_create.  Errors as there, plus
+ * CELESTE_ERR_ARG for a non-finite or singular patch map.
+ */
+celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_img,
+                                         const celeste_model* model, int32_t n_src,
+                                         const int32_t* patch_offsets, const celeste_patch* patches,
+                                         const double* patch_wcs, const int32_t* nbr_offsets,
+                                         const int32_t* nbrs, celeste_problem** out);
 void celeste_problem_destroy(celeste_problem* prob);
 
 /* Number of (source, active pixel) pairs: the unit of the cost accounting (Section VI-B). */
@@ -220,6 +234,38 @@ celeste_status celeste_fit_sources(celeste_problem* prob, double* theta_inout,
                                    const int32_t* which, int32_t n_which,
                                    const celeste_fit_options* opts, int32_t* iters_out,
                                    int32_t* status_out, double* elbo_out);
+
+/*
+ * Region tasks (Section IV-A; host logic, no device work).  The sources' positions
+ * pos[n][2] (world coordinates) and expected work work[n] >= 0 (e.g. each source's
+ * active pixel count, or its bright pixels from an existing catalog) cut the bounding
+ * box of the positions recursively into regions of work <= max_work (or a single
+ * source): each cut runs across the longer side of a region's box, at the weighted
+ * median (sources sorted by that coordinate, ties by index; the first prefix whose work
+ * reaches half the region's goes to the lower side; the cut lies halfway between the
+ * two sources it separates); the leaves, depth first, lower side first, are tasks
+ * 0 .. n_tasks - 1.  task_of[s] = the task whose region holds pos[s] - shift (shift
+ * NULL = (0, 0)): the first stage with no shift, the second with the same regions
+ * shifted by a fixed amount.  Errors: CELESTE_ERR_ARG (null pointers, n < 0,
+ * max_work <= 0, non-finite positions, shift or work, negative work).
+ */
+celeste_status celeste_make_tasks(const double* pos, const double* work, int32_t n, double max_work,
+                                  const double* shift, int32_t* task_of, int32_t* n_tasks);
+
+/*
+ * One stage of region tasks: every task (the sources s with task_of[s] == k, k >= 0;
+ * -1 = the source stays fixed) is fitted as celeste_fit_sources would with `which` =
+ * its sources, starting from theta_inout with every other source held at its starting
+ * value, as tasks running side by side on separate nodes see each other; the tasks'
+ * results are then merged into theta_inout.  iters_out / status_out ([n_src],
+ * nullable) as celeste_fit_sources (0 for fixed sources); elbo_out (nullable) = the
+ * total ELBO of the merged parameters (FP64 when FP32 sweeps are polished, else in the
+ * fit's precision).  Errors as celeste_fit_sources; task ids below -1 are
+ * CELESTE_ERR_ARG.
+ */
+celeste_status celeste_fit_tasks(celeste_problem* prob, double* theta_inout, const int32_t* task_of,
+                                 const celeste_fit_options* opts, int32_t* iters_out,
+                                 int32_t* status_out, double* elbo_out);
 
 /*
  * The Cyclades batches of one sweep (host logic, no device work, no CUDA context

@@ -252,7 +252,15 @@ struct OProblem {
     const int32_t* patches;    // [P][5]: image, x0, y0, w, h
     const int32_t* nbr_off;    // [n_src + 1]
     const int32_t* nbrs;
+    // per patch, the image's world -> pixel map linearised at the source ([P][6], same
+    // layout as OImage::wcs); null: every patch uses its image's affine wcs
+    const double* patch_wcs;
 };
+
+// the affine world -> pixel map a patch's source is drawn with
+inline const double* patch_map(const OProblem& P, int p) {
+    return P.patch_wcs ? P.patch_wcs + 6 * (size_t)p : P.imgs[P.patches[5 * p]].wcs;
+}
 
 // parameter indices (constrained layout)
 constexpr int IU = 0, IEDEV = 2, IAXIS = 3, IANGLE = 4, ISCALE = 5;
@@ -291,10 +299,9 @@ struct Shape {
 };
 
 template <class T>
-inline Shape<T> make_shape(const OImage& im, const T& u0, const T& u1, const T& edev,
+inline Shape<T> make_shape(const double* A, const T& u0, const T& u1, const T& edev,
                            const T& rho, const T& phi, const T& sigma) {
     Shape<T> s;
-    const double* A = im.wcs;
     s.mux = A[0] * u0 + A[1] * u1 + A[4];
     s.muy = A[2] * u0 + A[3] * u1 + A[5];
     // world-frame galaxy covariance: sigma^2 R(phi) diag(1, rho^2) R(phi)^T
@@ -487,7 +494,7 @@ void source_patch_values(const OProblem& P, const double* th, int p, PatchVals& 
     const OImage& im = P.imgs[pt[0]];
     int x0 = pt[1], y0 = pt[2], w = pt[3], h = pt[4];
     double iota = 1.0 / im.calib;
-    Shape<double> sh = make_shape<double>(im, th[IU], th[IU + 1], th[IEDEV], th[IAXIS],
+    Shape<double> sh = make_shape<double>(patch_map(P, p), th[IU], th[IU + 1], th[IEDEV], th[IAXIS],
                                           th[IANGLE], th[ISCALE]);
     double El[2], El2[2];
     for (int i = 0; i < 2; ++i) brightness<double>(th, im.band, i, El[i], El2[i]);
@@ -611,7 +618,7 @@ void local_derivs(const OProblem& P, const std::vector<PatchVals>& pv, const dou
         J6 sv[6];
         for (int i = 0; i < 6; ++i) sv[i] = jvar<6, H>(th[i], i);
         int slot6[6] = {0, 1, 2, 3, 4, 5};
-        Shape<J6> sh = make_shape<J6>(im, sv[0], sv[1], sv[2], sv[3], sv[4], sv[5]);
+        Shape<J6> sh = make_shape<J6>(patch_map(P, p), sv[0], sv[1], sv[2], sv[3], sv[4], sv[5]);
         J20 El[2], El2[2];
         for (int i = 0; i < 2; ++i) brightness<J20>(t, im.band, i, El[i], El2[i]);
         std::vector<Acc> gl(n), hl(H ? n * n : 0);
@@ -1024,7 +1031,7 @@ int oracle_patch_values(const OProblem* P, const double* theta, int p, double* e
 int oracle_profiles(const OProblem* P, const double* th, int n, int npts, const double* px,
                     const double* py, double* gstar, double* ggal) {
     const OImage& im = P->imgs[n];
-    Shape<double> sh = make_shape<double>(im, th[IU], th[IU + 1], th[IEDEV], th[IAXIS],
+    Shape<double> sh = make_shape<double>(im.wcs, th[IU], th[IU + 1], th[IEDEV], th[IAXIS],
                                           th[IANGLE], th[ISCALE]);
     for (int i = 0; i < npts; ++i) profiles<double>(*P, im, sh, px[i], py[i], gstar[i], ggal[i]);
     return 0;

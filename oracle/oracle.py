@@ -45,7 +45,7 @@ class OProblem(C.Structure):
                 ("prior_star", C.c_double), ("prior_r", C.c_void_p),
                 ("n_comp", C.c_int32), ("prior_c", C.c_void_p),
                 ("n_src", C.c_int32), ("patch_off", C.c_void_p), ("patches", C.c_void_p),
-                ("nbr_off", C.c_void_p), ("nbrs", C.c_void_p)]
+                ("nbr_off", C.c_void_p), ("nbrs", C.c_void_p), ("patch_wcs", C.c_void_p)]
 
 
 def lib():
@@ -103,6 +103,11 @@ class Oracle:
         p.n_src = prob.theta.shape[0]
         for k in ("patch_off", "patches", "nbr_off", "nbrs"):
             setattr(p, k, _ptr(arrs[k]))
+        pw = getattr(prob, "patch_wcs", None)
+        if pw is not None:
+            arrs["patch_wcs"] = np.ascontiguousarray(pw, np.float64).reshape(-1, 6)
+            assert arrs["patch_wcs"].shape[0] == arrs["patches"].shape[0]
+            p.patch_wcs = _ptr(arrs["patch_wcs"])
         self.p = p
         self.L = lib()
 

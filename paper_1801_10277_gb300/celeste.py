@@ -58,7 +58,8 @@ class celeste_fit_options(C.Structure):
 
 _lib = None
 
-EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_pixels",
+EXPORTS = ["celeste_problem_create", "celeste_problem_create_ex", "celeste_problem_destroy",
+           "celeste_source_pixels",
            "celeste_problem_stats",
            "celeste_elbo", "celeste_elbo_grad", "celeste_hess", "celeste_fit_options_default",
            "celeste_fit_sources", "celeste_elbo_device", "celeste_elbo_grad_device",
@@ -67,7 +68,7 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_destroy", "celeste_source_
            "celeste_patch_elbo_grad_noalloc", "celeste_grad_device", "celeste_autotune",
            "celeste_set_tuning", "celeste_cyclades_batches", "celeste_catalog",
            "celeste_catalog_device", "celeste_catalog_score", "celeste_render",
-           "celeste_render_device"]
+           "celeste_render_device", "celeste_make_tasks", "celeste_fit_tasks"]
 
 # catalog row layout (CELESTE_CAT_*): position, type, per-type brightness / colours with
 # their posterior standard deviations, the type-marginal r flux, galaxy shape
@@ -103,6 +104,9 @@ def load(build_if_missing=False):
     L.celeste_problem_create.argtypes = [C.POINTER(celeste_image), i32, C.POINTER(celeste_model), i32,
                                          vp, C.POINTER(celeste_patch), vp, vp, C.POINTER(vp)]
     L.celeste_problem_create.restype = i32
+    L.celeste_problem_create_ex.argtypes = [C.POINTER(celeste_image), i32, C.POINTER(celeste_model), i32,
+                                            vp, C.POINTER(celeste_patch), vp, vp, vp, C.POINTER(vp)]
+    L.celeste_problem_create_ex.restype = i32
     L.celeste_problem_destroy.argtypes = [vp]
     L.celeste_problem_destroy.restype = None
     L.celeste_source_pixels.argtypes = [vp]
@@ -134,6 +138,10 @@ def load(build_if_missing=False):
     L.celeste_catalog.argtypes = [vp, vp, vp]
     L.celeste_catalog_device.argtypes = [vp, vp, vp, vp]
     L.celeste_catalog_score.argtypes = [vp, vp, vp, i32, vp]
+    L.celeste_make_tasks.argtypes = [vp, vp, i32, C.c_double, vp, vp, vp]
+    L.celeste_make_tasks.restype = i32
+    L.celeste_fit_tasks.argtypes = [vp, vp, vp, C.POINTER(celeste_fit_options), vp, vp, vp]
+    L.celeste_fit_tasks.restype = i32
     L.celeste_render.argtypes = [vp, vp, vp, vp]
     L.celeste_render_device.argtypes = [vp, vp, vp, vp, vp]
     for f in ("celeste_catalog", "celeste_catalog_device", "celeste_catalog_score", "celeste_render",
@@ -180,6 +188,20 @@ def cyclades_batches(nbr_offsets, nbrs, order, sample_size):
     return b, c, nb.value
 
 
+def make_tasks(pos, work, max_work, shift=None):
+    """Region tasks of one stage: (task of every source, number of tasks).  Host logic:
+    no CUDA device needed."""
+    L = load()
+    pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 2)
+    work = np.ascontiguousarray(work, np.float64)
+    out = np.zeros(pos.shape[0], np.int32)
+    sh = None if shift is None else np.ascontiguousarray(shift, np.float64)
+    nt = C.c_int32()
+    _check(L.celeste_make_tasks(_p(pos), _p(work), pos.shape[0], float(max_work), _p(sh), _p(out),
+                                C.byref(nt)))
+    return out, nt.value
+
+
 def fit_options(**kw):
     o = celeste_fit_options()
     load().celeste_fit_options_default(C.byref(o))
@@ -224,8 +246,15 @@ class Problem:
         nb = np.ascontiguousarray(prob.nbrs, np.int32)
         keep += [po, no, nb]
         h = C.c_void_p()
-        st = L.celeste_problem_create(imgs, len(prob.images), C.byref(m), self.n_src, _p(po),
-                                      patches, _p(no), _p(nb) if nb.size else None, C.byref(h))
+        pw = getattr(prob, "patch_wcs", None)   # per-patch linearised maps (optional)
+        if pw is not None:
+            pw = np.ascontiguousarray(pw, np.float64).reshape(-1, 6)
+            if pw.shape[0] != pa.shape[0]:
+                raise ValueError("patch_wcs must hold one map per patch")
+            keep.append(pw)
+        st = L.celeste_problem_create_ex(imgs, len(prob.images), C.byref(m), self.n_src, _p(po),
+                                         patches, _p(pw), _p(no), _p(nb) if nb.size else None,
+                                         C.byref(h))
         _check(st)
         self.h = h
         self.L = L
@@ -309,6 +338,18 @@ class Problem:
                                           C.byref(o), _p(it), _p(st), C.byref(el)))
         return th, it, st, el.value
 
+
+    def fit_tasks(self, theta, task_of, **opts):
+        """One stage of region tasks (celeste_fit_tasks): (theta, iters, status, elbo)."""
+        self.generation += 1
+        th = self._theta(theta).copy()
+        t = np.ascontiguousarray(task_of, np.int32)
+        it = np.zeros(self.n_src, np.int32)
+        st = np.zeros(self.n_src, np.int32)
+        el = C.c_double()
+        o = fit_options(**opts)
+        _check(self.L.celeste_fit_tasks(self.h, _p(th), _p(t), C.byref(o), _p(it), _p(st), C.byref(el)))
+        return th, it, st, el.value
 
     def render(self, theta):
         """The model's expected image E[F] and variance Var[F] at theta, one [H][W] array

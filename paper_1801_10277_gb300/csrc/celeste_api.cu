@@ -355,6 +355,15 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
                                       const int32_t* patch_offsets, const celeste_patch* patches,
                                       const int32_t* nbr_offsets, const int32_t* nbrs,
                                       celeste_problem** out) {
+    return celeste_problem_create_ex(imgs, n_img, model, n_src, patch_offsets, patches, nullptr,
+                                     nbr_offsets, nbrs, out);
+}
+
+celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_img,
+                                         const celeste_model* model, int32_t n_src,
+                                         const int32_t* patch_offsets, const celeste_patch* patches,
+                                         const double* patch_wcs, const int32_t* nbr_offsets,
+                                         const int32_t* nbrs, celeste_problem** out) {
     if (!out) return fail(CELESTE_ERR_ARG, "out is null");
     *out = nullptr;
     if (n_img <= 0 || !imgs) return fail(CELESTE_ERR_ARG, "need at least one image");
@@ -553,6 +562,31 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
             if (nbrs[e] < 0 || nbrs[e] >= n_src || nbrs[e] == s) return fail(CELESTE_ERR_ARG, "bad neighbour of source %d", s);
     }
 
+    // Per-patch world -> pixel maps (each image's map linearised at the patch's source):
+    // a patch whose map differs from its image's points at a copy of the image record
+    // carrying that map (appended after the images, sharing their pixels, sky, PSF and
+    // tile grid).  Every kernel reads a patch's map from img[geo.img], so nothing else
+    // changes; the tiles and the coverage flags above keep the real image ids.
+    if (patch_wcs) {
+        for (int p = 0; p < n_patch; ++p) {
+            const double* w = patch_wcs + 6 * (size_t)p;
+            for (int k = 0; k < 6; ++k)
+                if (!isfinite(w[k])) return fail(CELESTE_ERR_ARG, "patch %d: wcs not finite", p);
+            if (w[0] * w[3] - w[1] * w[2] == 0) return fail(CELESTE_ERR_ARG, "patch %d: singular wcs", p);
+            const ImgMeta& base = im[geo[p].img];
+            if (w[0] == base.A[0] && w[1] == base.A[1] && w[2] == base.A[2] && w[3] == base.A[3] &&
+                w[4] == base.t[0] && w[5] == base.t[1])
+                continue;
+            ImgMeta V = base;
+            for (int k = 0; k < 4; ++k) V.A[k] = w[k];
+            V.t[0] = w[4];
+            V.t[1] = w[5];
+            fill_float_copies(V);
+            geo[p].img = (int)im.size();
+            im.push_back(V);
+        }
+    }
+
     celeste_problem* pr = new (std::nothrow) celeste_problem();
     if (!pr) return fail(CELESTE_ERR_NOMEM, "host allocation failed");
     auto bail = [&](celeste_status st) { celeste_problem_destroy(pr); return st; };
@@ -580,6 +614,9 @@ celeste_status celeste_problem_create(const celeste_image* imgs, int32_t n_img,
     P.n_img = n_img; P.n_src = n_src; P.n_patch = n_patch; P.n_item = (int)items.size();
     P.n_tile = (int)tiles.size(); P.npsf_max = npsf_max; P.nprof = model->n_exp + model->n_dev;
     P.n_px = n_px; P.n_sp = n_sp;
+    P.max_src_patches = 0;
+    for (int s = 0; s < n_src; ++s)
+        P.max_src_patches = std::max(P.max_src_patches, patch_offsets[s + 1] - patch_offsets[s]);
     celeste_status st;
     // pixels (and optional sky maps) concatenated
     {

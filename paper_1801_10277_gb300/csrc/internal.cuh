@@ -163,6 +163,7 @@ struct DevProblem {
     int32_t gather_sep;                   // split path: 0 gather inside the adjoint of the multiply
                                           // covered items, 1 tile-major k_gather then the adjoint
     int64_t n_px, n_sp;
+    int32_t max_src_patches;              // most patches of one source (k_prep's grid)
     const ImgMeta* img;
     const float* pixels;
     const float* sky_map;

@@ -163,6 +163,9 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
     const int s = blockIdx.x;
     if (s >= n_src || (src_active && !src_active[s])) return;
     const int p0 = patch_off[s], np = patch_off[s + 1] - p0;
+    // blockIdx.y picks the rounds of PREP_THREADS / PREP_HDR patches this CTA builds (a
+    // source seen in hundreds of images spreads over several CTAs); the KL is y = 0's
+    if (blockIdx.y > 0 && (int)blockIdx.y * (PREP_THREADS / PREP_HDR) >= np) return;
     __shared__ double th[NP];
     __shared__ R thr[NP];
     __shared__ R gsh[PREP_THREADS / PREP_HDR][4];   // gxx gxy gyy e_dev per patch of a round
@@ -173,7 +176,7 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
         thr[t] = (R)v;   // the parameters converted once per source
     }
     __syncthreads();
-    const bool kl_here = klg_out && (t >> 5) == PREP_KL_WARP;
+    const bool kl_here = klg_out && (t >> 5) == PREP_KL_WARP && blockIdx.y == 0;
     __shared__ double kg[NP];
     if (np == 0) {
         if (kl_here) prep_kl<R>(s, th, thr, md, kl_out, klg_out, status, kg);
@@ -181,7 +184,7 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
     }
     const int per_k = 1 + nprof;
     // patches in rounds of PREP_THREADS / PREP_HDR
-    for (int r0 = 0; r0 < np; r0 += PREP_THREADS / PREP_HDR) {
+    for (int r0 = blockIdx.y * (PREP_THREADS / PREP_HDR); r0 < np; r0 += gridDim.y * (PREP_THREADS / PREP_HDR)) {
         const int pi = r0 + t / PREP_HDR, role = t % PREP_HDR;
         if (pi < np) {
             const PatchGeo g = geo[p0 + pi];
@@ -1585,7 +1588,8 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
                         cudaStream_t st, bool with_kl) {
     double* klg = with_kl ? P.kl_grad : nullptr;
     if (P.n_src == 0 || (P.n_patch == 0 && !klg)) return cudaSuccess;
-    const int grid = P.n_src;
+    const int per_cta = PREP_THREADS / PREP_HDR;
+    const dim3 grid(P.n_src, std::max(1, std::min(64, (P.max_src_patches + per_cta - 1) / per_cta)));
     if (precision == CELESTE_FP64)
         k_prep<double><<<grid, PREP_THREADS, 0, st>>>(d_theta, P.geo, P.patch_off, P.img, P.model,
                                                       P.n_src, P.nprof, P.tbl64, P.kl, klg, P.status,

@@ -60,6 +60,10 @@ class Image:
     wcs: np.ndarray               # [6]: A00 A01 A10 A11 t0 t1; pixel = A u + t
     psf: np.ndarray               # [K][6]: alpha, xi_x, xi_y, Sxx, Sxy, Syy
     sky_map: np.ndarray | None = None   # optional [H][W] float32 sky counts
+    # optional smooth distortion added to the affine map (a stand-in for a survey WCS):
+    # (cx, cy, L, d1, d2, d3, d4), pixel = A u + t + (d1 x^2 + d2 x y, d3 y^2 + d4 x y)
+    # with x = (u0 - cx) / L, y = (u1 - cy) / L
+    warp: tuple | None = None
 
     @property
     def height(self):
@@ -86,6 +90,7 @@ class Problem:
     nbrs: np.ndarray              # [E] int32
     name: str = ""
     meta: dict = field(default_factory=dict)
+    patch_wcs: np.ndarray | None = None   # optional [P][6]: each patch's map, linearised at its source
 
     @property
     def n_src(self):
@@ -200,6 +205,28 @@ def pixel_position(wcs, u):
     return A @ np.asarray(u) + np.array(wcs[4:6])
 
 
+def pixel_position_full(im, u):
+    """The image's full world -> pixel map (affine part plus its distortion)."""
+    p = pixel_position(im.wcs, u)
+    if im.warp is not None:
+        cx, cy, L, d1, d2, d3, d4 = im.warp
+        x, y = (u[0] - cx) / L, (u[1] - cy) / L
+        p = p + np.array([d1 * x * x + d2 * x * y, d3 * y * y + d4 * x * y])
+    return p
+
+
+def linearised_wcs(im, u0):
+    """The image's map linearised at u0: pixel ~ J (u - u0) + p(u0) = J u + t, in the
+    wcs layout (J00 J01 J10 J11 t0 t1)."""
+    J = np.array(im.wcs[:4], np.float64).reshape(2, 2).copy()
+    if im.warp is not None:
+        cx, cy, L, d1, d2, d3, d4 = im.warp
+        x, y = (u0[0] - cx) / L, (u0[1] - cy) / L
+        J += np.array([[2 * d1 * x + d2 * y, d2 * x], [d4 * y, 2 * d3 * y + d4 * x]]) / L
+    t = pixel_position_full(im, u0) - J @ np.asarray(u0, np.float64)
+    return np.array([J[0, 0], J[0, 1], J[1, 0], J[1, 1], t[0], t[1]])
+
+
 def render_blobs(rng, images, truth, is_gal):
     """Poisson counts: sky + one isotropic Gaussian blob per (source, image)."""
     for im in images:
@@ -210,7 +237,7 @@ def render_blobs(rng, images, truth, is_gal):
             lf = band_log_flux(truth[s, I_R1], truth[s, I_C1:I_C1 + 4])[im.band]
             cnt = iota * math.exp(lf)
             v = _blob_var(im.psf, bool(is_gal[s]), truth[s, I_SCALE])
-            px, py = pixel_position(im.wcs, truth[s, 0:2])
+            px, py = pixel_position_full(im, truth[s, 0:2])
             rad = int(math.ceil(5 * math.sqrt(v)))
             x0, x1 = max(0, int(px) - rad), min(W, int(px) + rad + 1)
             y0, y1 = max(0, int(py) - rad), min(H, int(py) + rad + 1)
@@ -245,7 +272,7 @@ def make_patches(images, theta, is_gal):
     for s in range(theta.shape[0]):
         w = patch_width(images[ref], theta[s], bool(is_gal[s]))
         for n, im in enumerate(images):
-            px, py = pixel_position(im.wcs, theta[s, 0:2])
+            px, py = pixel_position_full(im, theta[s, 0:2])
             cx, cy = int(round(px)), int(round(py))
             x0, y0 = cx - w // 2, cy - w // 2
             x1, y1 = x0 + w, y0 + w
@@ -304,10 +331,16 @@ def _finish(rng, name, images, truth, is_gal, theta, meta=None):
     render_blobs(rng, images, truth, is_gal)
     po, pa = make_patches(images, theta, is_gal)
     no, nb = make_neighbours(truth.shape[0], po, pa)
+    pw = None
+    if any(im.warp is not None for im in images):
+        # each patch's map linearised at its source's starting (catalog) position
+        owner = np.repeat(np.arange(truth.shape[0]), np.diff(po))
+        pw = np.stack([linearised_wcs(images[int(pa[p, 0])], theta[owner[p], 0:2])
+                       for p in range(pa.shape[0])]) if len(pa) else np.zeros((0, 6))
     return Problem(images=images, exp_mix=exp_mix, dev_mix=dev_mix, prior_star=prior_star,
                    prior_r=prior_r, prior_c=prior_c, theta=theta, truth=truth,
                    patch_offsets=po, patches=pa, nbr_offsets=no, nbrs=nb, name=name,
-                   meta=meta or {})
+                   meta=meta or {}, patch_wcs=pw)
 
 
 def tiny_two_source(seed=2026, H=48, W=48):
@@ -393,10 +426,36 @@ def multi_epoch(seed=2029, n_src=20000, n_fields=8, H=1489, W=2048, stride=400):
                    is_gal, theta)
 
 
+def deep_stack(seed=2031, n_src=100, n_epochs=96, H=400, W=400, field_size=384):
+    """A deeply imaged patch of sky (like the repeatedly scanned stripe): 96 epochs x 5
+    bands = 480 images of 400 x 400 px, each with its own pointing offset (+-8 px),
+    rotation (1e-2 rad), scale (3e-3), PSF, sky U(100, 200), calibration
+    U(0.004, 0.006) and a smooth quadratic distortion of up to ~1 px; 100 sources, so
+    every source has 480 patches, each with its image's map linearised at the source."""
+    rng = np.random.default_rng(seed)
+    images = []
+    c = field_size / 2.0
+    for e in range(n_epochs):
+        A = (1.0 + rng.normal(0, 3e-3)) * _rot(rng.normal(0, 1e-2))
+        off = np.array([W / 2.0, H / 2.0]) + rng.uniform(-8, 8, size=2)
+        t = off - A @ np.array([c, c])           # the field centre lands near the image centre
+        wcs = np.array([A[0, 0], A[0, 1], A[1, 0], A[1, 1], t[0], t[1]])
+        warp = (c, c, c, *rng.normal(0, 0.3, size=4))
+        for b in range(NBANDS):
+            images.append(Image(band=b, pixels=np.zeros((H, W), np.float32),
+                                sky=rng.uniform(100, 200), calib=rng.uniform(0.004, 0.006),
+                                wcs=wcs.copy(), psf=draw_psf(rng), warp=warp))
+    truth, is_gal = draw_truth(rng, n_src)
+    truth[:, 0:2] = rng.uniform(12, field_size - 12, size=(n_src, 2))
+    theta = perturb_start(rng, truth, is_gal)
+    return _finish(rng, f"deepstack_{n_src}src_{n_epochs}x5x{W}x{H}", images, truth, is_gal, theta)
+
+
 def config(idx, seed=None, **kw):
-    """The five workloads by index: 0 tiny two-source, 1 one field of 500 sources,
+    """The workloads by index: 0 tiny two-source, 1 one field of 500 sources,
     2 crowded 64-source region, 3 multi-epoch 20k sources, 4 is built per field by
-    ``many_fields`` (200k sources over 64 fields) and sampled."""
+    ``many_fields`` (200k sources over 64 fields) and sampled, 5 deep stack (480
+    images per source, distorted maps linearised per source)."""
     base = 2026 + idx if seed is None else seed
     if idx == 0:
         return tiny_two_source(base, **kw)
@@ -408,6 +467,8 @@ def config(idx, seed=None, **kw):
         return multi_epoch(base, **kw)
     if idx == 4:
         return many_fields_sample(base, **kw)
+    if idx == 5:
+        return deep_stack(base, **kw)
     raise ValueError(idx)
 
 
@@ -430,8 +491,10 @@ def subset(prob, idx):
     rows = []
     nb_off = [0]
     nb = []
+    keep_p = []
     for s in idx:
         rows.extend(prob.patches[prob.patch_offsets[s]:prob.patch_offsets[s + 1]].tolist())
+        keep_p.extend(range(prob.patch_offsets[s], prob.patch_offsets[s + 1]))
         offs.append(len(rows))
         for o in prob.nbrs[prob.nbr_offsets[s]:prob.nbr_offsets[s + 1]]:
             if remap[o] >= 0:
@@ -443,4 +506,5 @@ def subset(prob, idx):
                    patch_offsets=np.array(offs, np.int32),
                    patches=np.array(rows, np.int32).reshape(-1, 5),
                    nbr_offsets=np.array(nb_off, np.int32), nbrs=np.array(nb, np.int32),
-                   name=f"{prob.name}_subset{len(idx)}", meta=dict(prob.meta))
+                   name=f"{prob.name}_subset{len(idx)}", meta=dict(prob.meta),
+                   patch_wcs=None if prob.patch_wcs is None else prob.patch_wcs[keep_p].copy())
