@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--no-schedules", action="store_true",
                     help="skip the colour vs Cyclades convergence-per-sweep leg")
     ap.add_argument("--schedule-sweeps", type=int, default=4)
+    ap.add_argument("--no-tasks", action="store_true", help="skip the region-task leg")
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
                          "4 sweep field, 5 deep stack (480 images per source); the JSON line names it")
@@ -474,6 +475,37 @@ def main():
             schedules[name] = entry
         schedules["elbo_start"] = P.elbo(prob.theta, precision=cel.FP64)[0]
 
+    # region tasks (Section IV-A) on one GPU: one global fit against one and two stages of
+    # tasks (regions of about 1/16 of the work; the second stage shifted by half a
+    # region), FP32 sweeps polished in FP64; total ELBO after each and host wall time
+    tasks = None
+    if not args.no_fit and not args.no_tasks:
+        npx = np.zeros(prob.n_src)
+        np.add.at(npx, np.repeat(np.arange(prob.n_src), np.diff(prob.patch_offsets)),
+                  prob.patches[:, 3].astype(np.float64) * prob.patches[:, 4])
+        pos = prob.theta[:, 0:2]
+        t1, n1 = cel.make_tasks(pos, npx, npx.sum() / 16)
+        span = pos.max(axis=0) - pos.min(axis=0)
+        shift = 0.5 * span / 4.0   # about half a region of a 4 x 4 cut
+        t2, n2 = cel.make_tasks(pos, npx, npx.sum() / 16, shift)
+        kw = dict(precision=cel.FP32, max_sweeps=3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, el_g = P.fit(prob.theta, **kw)
+        torch.cuda.synchronize()
+        sec_g = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        th1, _, _, el_1 = P.fit_tasks(prob.theta, t1, **kw)
+        sec_1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, _, _, el_2 = P.fit_tasks(th1, t2, **kw)
+        sec_2 = time.perf_counter() - t0
+        tasks = {"tasks_per_stage": [n1, n2], "shift": shift.tolist(),
+                 "elbo_start": P.elbo(prob.theta, precision=cel.FP64)[0],
+                 "global_fit": {"elbo": el_g, "seconds": sec_g},
+                 "stage1": {"elbo": el_1, "seconds": sec_1},
+                 "stage2": {"elbo": el_2, "seconds": sec_2}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, reps, secs = oracle_rate(prob)
@@ -496,7 +528,7 @@ def main():
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "hessian": hessian, "fit": fit, "fit_schedules": schedules, "catalog": catalog,
+            "hessian": hessian, "fit": fit, "fit_schedules": schedules, "catalog": catalog, "tasks": tasks,
             "gpu_launches": int(round(launches_per_step * args.steps)),
         }
         print(json.dumps(line), flush=True)
