@@ -215,10 +215,17 @@ struct TrState {
     int32_t iters;
     int32_t cand;   // a candidate was produced this iteration
     int32_t pad;
+    double lam;     // multiplier of the last boundary step (warm start of the next), 0 inside
 };
 
-// Cholesky of (B + lam I) into L (lower, row-major n x n); returns success to all threads
-__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag) {
+// Cholesky of (B + lam I) into L (lower, row-major n x n); returns success to all threads.
+// Right-looking, two barriers per column: thread 0 takes the pivot's square root and its
+// reciprocal (one FP64 rsqrt per column; the FP64 pipe runs a warp instruction at the
+// same cost however few lanes are active, so per-element divisions are avoided), then
+// every thread updates its share of the trailing lower triangle from the still unscaled
+// column, L_ij -= L_ik L_jk / d_k, and scales the column left by the previous step.
+// The packed triangle index gives every warp instruction useful lanes.
+__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag, double* rcp) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < n * n; i += nt) {
         const int r = i / n, c = i - r * n;
@@ -229,21 +236,35 @@ __device__ bool block_chol(const double* B, double lam, double* L, int n, int* f
     for (int k = 0; k < n; ++k) {
         if (tid == 0) {
             const double d = L[k * n + k];
-            if (!(d > 0.0) || !isfinite(d)) *flag = 0;
-            else L[k * n + k] = sqrt(d);
+            if (!(d > 0.0) || !isfinite(d)) {
+                *flag = 0;
+            } else {
+                const double r = rsqrt(d);
+                L[k * n + k] = d * r;   // sqrt(d)
+                rcp[k] = r;             // 1 / sqrt(d)
+                rcp[n + k] = r * r;     // 1 / d
+            }
         }
+        // the previous column's scaling (its entries are not read in this step)
+        if (k > 0)
+            for (int i = k + tid; i < n; i += nt) L[i * n + k - 1] *= rcp[k - 1];
         __syncthreads();
         if (!*flag) return false;
-        const double dk = L[k * n + k];
-        for (int i = k + 1 + tid; i < n; i += nt) L[i * n + k] /= dk;
-        __syncthreads();
+        const double inv_d = rcp[n + k];
         const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += nt) {
-            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            if (j <= i) L[i * n + j] -= L[i * n + k] * L[j * n + k];
+        const int cnt = m * (m + 1) / 2;
+        for (int idx = tid; idx < cnt; idx += nt) {
+            // (a, b) with 0 <= b <= a < m from the packed index a (a + 1) / 2 + b
+            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > idx) --a;
+            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+            const int b = idx - a * (a + 1) / 2;
+            const int i = k + 1 + a, j = k + 1 + b;
+            L[i * n + j] -= L[i * n + k] * L[j * n + k] * inv_d;
         }
         __syncthreads();
     }
+    // column j was scaled in step j + 1 <= n - 1; the last column is its pivot alone
     return true;
 }
 
@@ -431,10 +452,11 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     for (int i = tid; i < TRN; i += blockDim.x) p[i] = 0.0;   // a zero step if nothing factors
     if (tid == 0) pn_s = 0.0;
     __syncthreads();
-    bool ok = block_chol(Ht, 0.0, L, TRN, &flag);
+    __shared__ double rcp[2 * TRN];
+    bool ok = block_chol(Ht, 0.0, L, TRN, &flag, rcp);
     bool solved = false;
     if (ok) {
-        if (tid < TRN) invd[tid] = 1.0 / L[tid * TRN + tid];
+        if (tid < TRN) invd[tid] = rcp[tid];
         __syncthreads();
         if (tid < 32) {
             warp_fwd(L, invd, cvec, w, TRN);
@@ -454,10 +476,13 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     }
     if (!solved) {
         lam = fmax(lamL, fmax(1e-3 * lamU, sqrt(fmax(lamL, 1e-300) * lamU)));
+        // the previous iteration's multiplier, when still inside the bracket, is usually
+        // close: the Hessian and the radius change little between Newton iterations
+        if (S.lam > lamL && S.lam < lamU) lam = S.lam;
         if (ok) lamL = fmax(lamL, 0.0);
         for (int it = 0; it < 200; ++it) {
-            const bool pd = block_chol(Ht, lam, L, TRN, &flag);
-            if (pd && tid < TRN) invd[tid] = 1.0 / L[tid * TRN + tid];
+            const bool pd = block_chol(Ht, lam, L, TRN, &flag, rcp);
+            if (pd && tid < TRN) invd[tid] = rcp[tid];
             __syncthreads();
             if (tid < 32) {
                 double nl = 0.0;
@@ -479,7 +504,10 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
                     }
                     __syncwarp();
                     int dn;
-                    if (fabs(pn - Delta) <= 1e-12 * Delta) {
+                    // |p| within 1e-6 of the radius: the step's model value is then
+                    // within ~1e-6 of the subproblem's optimum, far below what the
+                    // ratio test resolves; the bracket stops at 1e-10 relative
+                    if (fabs(pn - Delta) <= 1e-6 * Delta) {
                         dn = 1;
                     } else {
                         if (pn < Delta) lamU = lam;
@@ -490,7 +518,7 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
                         nl = lam + (pn * pn / wn) * (pn - Delta) / Delta;
                         if (!(nl > lamL && nl < lamU))
                             nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
-                        dn = (lamU - lamL <= 1e-15 * fmax(1.0, lamU)) ? 2 : 0;
+                        dn = (lamU - lamL <= 1e-10 * fmax(1.0, lamU)) ? 2 : 0;
                     }
                     if (tid == 0) done = dn;
                 }
@@ -564,6 +592,7 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         for (int i = 0; i < TRN; ++i) pred -= cvec[i] * p[i] + 0.5 * p[i] * rs[i];
         S.pred = pred;
         S.pnorm = pn_s;
+        S.lam = solved ? 0.0 : lam;
         if (pred <= o.pred_tol_rel * (1.0 + fabs(S.f))) {
             S.status = ST_CONVERGED;
             S.cand = 0;

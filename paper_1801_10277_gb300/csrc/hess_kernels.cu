@@ -292,69 +292,102 @@ __device__ void shape_hessian(const double* A, const double* th, double d2G[3][3
         }
 }
 
-// full KL Hessian (44 x 44, row-major) into H (zeroed by the caller); one thread
-__device__ void kl_hessian(const ModelDev& md, const double* th, double* H) {
-    for (int i = 0; i < 2; ++i) {
-        const double a = th[P_A + i];
+// Full KL Hessian (44 x 44, row-major) added into H (zeroed by the caller), by one warp
+// (every lane calls it).  Lanes 8 i + d (i < 2, d < 8) hold the terms of type i's
+// colour-prior component d, which touch disjoint entries (the k_d rows); the sums over
+// components are shuffled within each group of eight, and lane 8 i then writes the
+// type's a / r / c entries.  Every entry is written by exactly one lane.
+__device__ void kl_hessian_warp(const ModelDev& md, const double* th, double* H) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int i = (lane >> 3) & 1, d = lane & 7;
+    auto add = [&](int p, int q, double v) {
+        H[p * NP + q] += v;
+        if (p != q) H[q * NP + p] += v;
+    };
+    double c1[4], c2[4], ic2[4], slog = 0.0;
+    for (int j = 0; j < 4; ++j) {
+        c1[j] = th[P_C1 + 4 * i + j];
+        c2[j] = th[P_C2 + 4 * i + j];
+    }
+    double sc1[4] = {0, 0, 0, 0}, sc2[4] = {0, 0, 0, 0}, Pk[16], ks = 0.0;
+    for (int j = 0; j < 16; ++j) Pk[j] = 0.0;
+    const double a = th[P_A + i];
+    if (lane < 16) {
+        for (int j = 0; j < 4; ++j) {
+            slog += log(c2[j]);
+            ic2[j] = 1.0 / c2[j];
+        }
+        const double k = th[P_K + NCOMP * i + d];
+        const double* Pm = md.prior_P[i][d];
+        const double* mu = md.prior_mu[i][d];
+        double diff[4], Pd[4], quad = 0.0, tr = 0.0;
+        for (int j = 0; j < 4; ++j) diff[j] = c1[j] - mu[j];
+        for (int j = 0; j < 4; ++j) {
+            double sj = 0.0;
+            for (int l = 0; l < 4; ++l) sj += Pm[4 * j + l] * diff[l];
+            Pd[j] = sj;
+            quad += diff[j] * sj;
+            tr += Pm[5 * j] * c2[j];
+        }
+        const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
+        const int ik = P_K + NCOMP * i + d;
+        add(P_A + i, ik, log(k / md.prior_w[i][d]) + 1.0 + klc);
+        add(ik, ik, a / k);
+        for (int j = 0; j < 4; ++j) {
+            add(ik, P_C1 + 4 * i + j, a * Pd[j]);
+            add(ik, P_C2 + 4 * i + j, a * 0.5 * (Pm[5 * j] - ic2[j]));
+            sc1[j] = k * Pd[j];
+            sc2[j] = 0.5 * k * (Pm[5 * j] - ic2[j]);
+        }
+        for (int j = 0; j < 16; ++j) Pk[j] = k * Pm[j];
+        ks = k;
+    }
+    for (int o = 1; o < 8; o <<= 1) {
+        ks += __shfl_xor_sync(full, ks, o);
+        for (int j = 0; j < 4; ++j) {
+            sc1[j] += __shfl_xor_sync(full, sc1[j], o);
+            sc2[j] += __shfl_xor_sync(full, sc2[j], o);
+        }
+        for (int j = 0; j < 16; ++j) Pk[j] += __shfl_xor_sync(full, Pk[j], o);
+    }
+    if (lane < 16 && d == 0) {
         const double r1 = th[P_R1 + i], r2 = th[P_R2 + i];
         const double pm = md.prior_r[i][0], pv = md.prior_r[i][1];
         const int ia = P_A + i, ir1 = P_R1 + i, ir2 = P_R2 + i;
-        auto add = [&](int p, int q, double v) {
-            H[p * NP + q] += v;
-            if (p != q) H[q * NP + p] += v;
-        };
         add(ia, ia, 1.0 / a);
         add(ia, ir1, (r1 - pm) / pv);
         add(ia, ir2, 0.5 * (1.0 / pv - 1.0 / r2));
         add(ir1, ir1, a / pv);
         add(ir2, ir2, a * 0.5 / (r2 * r2));
-        double c1[4], c2[4], slog = 0.0;
         for (int j = 0; j < 4; ++j) {
-            c1[j] = th[P_C1 + 4 * i + j];
-            c2[j] = th[P_C2 + 4 * i + j];
-            slog += log(c2[j]);
-        }
-        double dc1[4] = {0, 0, 0, 0}, dc2[4] = {0, 0, 0, 0};
-        double Pk[16];
-        for (int j = 0; j < 16; ++j) Pk[j] = 0.0;
-        double ksum = 0.0;
-        for (int d = 0; d < NCOMP; ++d) {
-            const double k = th[P_K + NCOMP * i + d];
-            const double* Pm = md.prior_P[i][d];
-            const double* mu = md.prior_mu[i][d];
-            double diff[4], Pd[4], quad = 0.0, tr = 0.0;
-            for (int j = 0; j < 4; ++j) diff[j] = c1[j] - mu[j];
-            for (int j = 0; j < 4; ++j) {
-                double s = 0.0;
-                for (int l = 0; l < 4; ++l) s += Pm[4 * j + l] * diff[l];
-                Pd[j] = s;
-                quad += diff[j] * s;
-                tr += Pm[5 * j] * c2[j];
-            }
-            const double klc = 0.5 * (tr + quad - 4.0 + md.prior_logdet[i][d] - slog);
-            const int ik = P_K + NCOMP * i + d;
-            add(ia, ik, log(k / md.prior_w[i][d]) + 1.0 + klc);
-            add(ik, ik, a / k);
-            for (int j = 0; j < 4; ++j) {
-                add(ik, P_C1 + 4 * i + j, a * Pd[j]);
-                add(ik, P_C2 + 4 * i + j, a * 0.5 * (Pm[5 * j] - 1.0 / c2[j]));
-                dc1[j] += k * Pd[j];
-                dc2[j] += 0.5 * k * (Pm[5 * j] - 1.0 / c2[j]);
-            }
-            for (int j = 0; j < 16; ++j) Pk[j] += k * Pm[j];
-            ksum += k;
-        }
-        for (int j = 0; j < 4; ++j) {
-            add(ia, P_C1 + 4 * i + j, dc1[j]);
-            add(ia, P_C2 + 4 * i + j, dc2[j]);
-            add(P_C2 + 4 * i + j, P_C2 + 4 * i + j, a * 0.5 * ksum / (c2[j] * c2[j]));
+            add(ia, P_C1 + 4 * i + j, sc1[j]);
+            add(ia, P_C2 + 4 * i + j, sc2[j]);
+            add(P_C2 + 4 * i + j, P_C2 + 4 * i + j, a * 0.5 * ks * ic2[j] * ic2[j]);
             for (int l = j; l < 4; ++l) add(P_C1 + 4 * i + j, P_C1 + 4 * i + l, a * Pk[4 * j + l]);
         }
     }
+    __syncwarp();
 }
 
 constexpr int FH_THREADS = 256;
 constexpr int FH_PER = (NP * NP + FH_THREADS - 1) / FH_THREADS;
+
+// d(m + v/2) / d theta_j (second = false) or d(2m + 2v) / d theta_j (second = true) of
+// type ty in band `band`, where log l | ty ~ N(m, v), m = r1 + beta . c1, v = r2 + beta^2 . c2
+__device__ __forceinline__ double bright_d(int band, int ty, int j, bool second) {
+    if (j == P_R1 + ty) return second ? 2.0 : 1.0;
+    if (j == P_R2 + ty) return second ? 2.0 : 0.5;
+    if (j >= P_C1 + 4 * ty && j < P_C1 + 4 * ty + 4) {
+        const double b = color_beta(band, j - P_C1 - 4 * ty);
+        return second ? 2.0 * b : b;
+    }
+    if (j >= P_C2 + 4 * ty && j < P_C2 + 4 * ty + 4) {
+        const double b = color_beta(band, j - P_C2 - 4 * ty);
+        return second ? 2.0 * b * b : 0.5 * b * b;
+    }
+    return 0.0;
+}
 
 __global__ void __launch_bounds__(FH_THREADS)
 k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
@@ -365,25 +398,37 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 int32_t* __restrict__ status, const int32_t* __restrict__ src_active) {
     const int s = blockIdx.x;
     if (s >= n_src || (src_active && !src_active[s])) return;
-    const double* th = theta + (size_t)NP * s;
-    if (status && (int)threadIdx.x < NP) theta_domain_check(threadIdx.x, th[threadIdx.x], status);
+    __shared__ double th[NP];
     __shared__ double Hy[NY][NY];
     __shared__ double Gy[NY + 1];
     __shared__ int nzn[NP];
     __shared__ int nzy[NP][3];
     __shared__ double nzv[NP][3];
-    __shared__ double dvec[2][NP], evec[2][NP];   // d(m + v/2), d(2m + 2v) per type
+    __shared__ double bmom[5][2][2];              // E[l_b | i], E[l_b^2 | i] per band and type
+    __shared__ double dG[3][3], d2G[3][3][3];     // the patch map's shape derivatives
     __shared__ double wd[2], we[2];
     __shared__ double S2[3][3];
     __shared__ double klH[NP * NP];
     __shared__ double klg[NP];
     __shared__ double klv;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t < NP) {
+        th[t] = theta[(size_t)NP * s + t];
+        if (status) theta_domain_check(t, th[t], status);
+    }
     for (int i = t; i < NP * NP; i += blockDim.x) klH[i] = 0.0;
     __syncthreads();
-    if (t == 0) {
-        klv = kl_value_grad(*md, th, klg);
-        kl_hessian(*md, th, klH);
+    // the KL (warp 0: value and gradient; warp 1: Hessian) and the band moments of the
+    // five bands (warp 2), each lane-parallel: the FP64 pipe costs a warp instruction
+    // the same however few of its lanes are active
+    if (warp == 0) {
+        const double v = kl_warp<double>(*md, th, th, klg);
+        if (lane == 0) klv = v;
+    } else if (warp == 1) {
+        kl_hessian_warp(*md, th, klH);
+    } else if (warp == 2 && lane < 10) {
+        const int b = lane >> 1, i = lane & 1;
+        band_moments(th, b, i, bmom[b][i][0], bmom[b][i][1]);
     }
     double acc[FH_PER];
 #pragma unroll
@@ -393,6 +438,7 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         __syncthreads();
         const PatchGeo g = geo[p];
         const ImgMeta& im = img[g.img];
+        const double* A = im.A;
         if (t < 1 + NY + NYH) {
             double v = 0.0;
             for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
@@ -406,71 +452,49 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 Hy[a][b] = v;
                 Hy[b][a] = v;
             }
-        }
-        if (t == 0) {
-            // sparse Jacobian dy/dtheta, column by column (theta index)
-            for (int i = 0; i < NP; ++i) nzn[i] = 0;
-            auto put = [&](int i, int y, double val) {
-                const int n = nzn[i]++;
-                nzy[i][n] = y;
-                nzv[i][n] = val;
-            };
-            put(P_A, Y_A0, 1.0);
-            put(P_A + 1, Y_A1, 1.0);
-            const double* A = im.A;
-            put(0, Y_MX, A[0]);
-            put(0, Y_MY, A[2]);
-            put(1, Y_MX, A[1]);
-            put(1, Y_MY, A[3]);
-            put(P_EDEV, Y_EDEV, 1.0);
-            double dG[3][3];
+        } else if (t == 128) {
             shape_jacobian(A, th, dG);
-            for (int q = 0; q < 3; ++q) {
-                put(P_AXIS + q, Y_GXX, dG[q][0]);
-                put(P_AXIS + q, Y_GXY, dG[q][1]);
-                put(P_AXIS + q, Y_GYY, dG[q][2]);
-            }
-            for (int i = 0; i < 2; ++i) {
-                double el, el2;
-                band_moments(th, im.band, i, el, el2);
-                const int yl = i == 0 ? Y_EL0 : Y_EL1, yl2 = i == 0 ? Y_EL20 : Y_EL21;
-                for (int j = 0; j < NP; ++j) dvec[i][j] = evec[i][j] = 0.0;
-                dvec[i][P_R1 + i] = 1.0;
-                dvec[i][P_R2 + i] = 0.5;
-                evec[i][P_R1 + i] = 2.0;
-                evec[i][P_R2 + i] = 2.0;
-                for (int j = 0; j < 4; ++j) {
-                    const double b = color_beta(im.band, j);
-                    dvec[i][P_C1 + 4 * i + j] = b;
-                    dvec[i][P_C2 + 4 * i + j] = 0.5 * b * b;
-                    evec[i][P_C1 + 4 * i + j] = 2.0 * b;
-                    evec[i][P_C2 + 4 * i + j] = 2.0 * b * b;
-                }
-                for (int j = 0; j < NP; ++j) {
-                    if (dvec[i][j] != 0.0) put(j, yl, el * dvec[i][j]);
-                    if (evec[i][j] != 0.0) put(j, yl2, el2 * evec[i][j]);
-                }
-                wd[i] = el;
-                we[i] = el2;
-            }
+        } else if (t == 160) {
+            shape_hessian(A, th, d2G);
         }
         __syncthreads();
-        if (t == 0) {
-            // weights of the second-derivative terms sum_y Gy d2y
-            double d2G[3][3][3];
-            shape_hessian(im.A, th, d2G);
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b)
-                    S2[a][b] = Gy[Y_GXX] * d2G[a][b][0] + Gy[Y_GXY] * d2G[a][b][1] +
-                               Gy[Y_GYY] * d2G[a][b][2];
-            wd[0] *= Gy[Y_EL0];
-            wd[1] *= Gy[Y_EL1];
-            we[0] *= Gy[Y_EL20];
-            we[1] *= Gy[Y_EL21];
+        if (t < NP) {
+            // column t of the sparse Jacobian dy / dtheta for this patch
+            const int j = t;
+            int n = 0;
+            auto put = [&](int y, double val) {
+                nzy[j][n] = y;
+                nzv[j][n] = val;
+                ++n;
+            };
+            if (j == 0) { put(Y_MX, A[0]); put(Y_MY, A[2]); }
+            else if (j == 1) { put(Y_MX, A[1]); put(Y_MY, A[3]); }
+            else if (j == P_EDEV) put(Y_EDEV, 1.0);
+            else if (j >= P_AXIS && j <= P_SCALE) {
+                const int q = j - P_AXIS;
+                put(Y_GXX, dG[q][0]);
+                put(Y_GXY, dG[q][1]);
+                put(Y_GYY, dG[q][2]);
+            } else if (j == P_A || j == P_A + 1) put(j == P_A ? Y_A0 : Y_A1, 1.0);
+            else if (j < P_A) {
+                const int i = (j < P_C1) ? ((j - P_R1) & 1) : (((j - (j >= P_C2 ? P_C2 : P_C1)) >> 2) & 1);
+                const double dv = bright_d(im.band, i, j, false), ev = bright_d(im.band, i, j, true);
+                if (dv != 0.0) put(i == 0 ? Y_EL0 : Y_EL1, bmom[im.band][i][0] * dv);
+                if (ev != 0.0) put(i == 0 ? Y_EL20 : Y_EL21, bmom[im.band][i][1] * ev);
+            }
+            nzn[j] = n;
+        } else if (t >= 64 && t < 73) {
+            const int a = (t - 64) / 3, b = (t - 64) % 3;
+            S2[a][b] = Gy[Y_GXX] * d2G[a][b][0] + Gy[Y_GXY] * d2G[a][b][1] + Gy[Y_GYY] * d2G[a][b][2];
+        } else if (t >= 96 && t < 98) {
+            const int i = t - 96;
+            wd[i] = bmom[im.band][i][0] * Gy[i == 0 ? Y_EL0 : Y_EL1];
+            we[i] = bmom[im.band][i][1] * Gy[i == 0 ? Y_EL20 : Y_EL21];
         }
         __syncthreads();
         if (t < NP)
             for (int n = 0; n < nzn[t]; ++n) gacc += nzv[t][n] * Gy[nzy[t][n]];
+        const int band = im.band;
 #pragma unroll
         for (int k = 0; k < FH_PER; ++k) {
             const int idx = t + k * FH_THREADS;
@@ -480,8 +504,13 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
             for (int a = 0; a < nzn[i]; ++a)
                 for (int b = 0; b < nzn[j]; ++b)
                     h += nzv[i][a] * Hy[nzy[i][a]][nzy[j][b]] * nzv[j][b];
-            for (int ty = 0; ty < 2; ++ty)
-                h += wd[ty] * dvec[ty][i] * dvec[ty][j] + we[ty] * evec[ty][i] * evec[ty][j];
+            // second derivatives of log E[l] and log E[l^2] (linear in the brightness
+            // parameters, so only their products appear): w (dm)(dm)'
+            for (int ty = 0; ty < 2; ++ty) {
+                const double di = bright_d(band, ty, i, false), dj = bright_d(band, ty, j, false);
+                const double ei = bright_d(band, ty, i, true), ej = bright_d(band, ty, j, true);
+                h += wd[ty] * di * dj + we[ty] * ei * ej;
+            }
             if (i >= P_AXIS && i <= P_SCALE && j >= P_AXIS && j <= P_SCALE)
                 h += S2[i - P_AXIS][j - P_AXIS];
             acc[k] += h;
