@@ -248,6 +248,8 @@ def main():
                     help="skip the colour vs Cyclades convergence-per-sweep leg")
     ap.add_argument("--schedule-sweeps", type=int, default=4)
     ap.add_argument("--no-tasks", action="store_true", help="skip the region-task leg")
+    ap.add_argument("--fit-only", action="store_true",
+                    help="time the Newton fit of the workload alone (FP32 sweeps, FP64 polish)")
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
                          "4 sweep field, 5 deep stack (480 images per source); the JSON line names it")
@@ -273,6 +275,19 @@ def main():
         P.set_tuning(*tuning)
     else:
         tuning = P.autotune(prob.theta)
+    if args.fit_only:
+        # the Newton fit alone (the profiling command for the fit's kernels)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, fst, el = P.fit(prob.theta, precision=cel.FP32, max_sweeps=3)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"metric": "Newton iterations/s", "value": float(iters.sum()) / secs,
+                              "unit": "iterations/s", "seconds": secs, "newton_iterations": int(iters.sum()),
+                              "converged": int((fst == 0).sum()), "elbo": el,
+                              "config": {"workload": prob.name, "sources": prob.n_src}}), flush=True)
+        return
     dev = torch.device("cuda", local_rank)
     theta = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
     tot = torch.zeros(1, dtype=torch.float64, device=dev)
