@@ -161,6 +161,9 @@ int32_t celeste_problem_stats(const celeste_problem* prob, int64_t* out, int32_t
  *     its own patch pixels (neighbours' light included in E and Var) minus its KL.
  * Errors: CELESTE_ERR_ARG for parameters outside their domain (r2, c2, e_scale <= 0,
  * a or k outside (0,1), e_axis outside (0,1], e_dev outside [0,1]); CELESTE_ERR_NONFINITE.
+ * The domain is checked on the device during the evaluation and read back with the
+ * results (with several violations either code may be reported); on an error the
+ * outputs hold the evaluation at the invalid parameters and must not be used.
  */
 celeste_status celeste_elbo(celeste_problem* prob, const double* theta, int32_t precision,
                             double* elbo_total, double* elbo_per_source);
@@ -462,6 +465,16 @@ celeste_status celeste_render(celeste_problem* prob, const double* theta, double
  * nullable), no synchronisation; domain errors via celeste_device_status(). */
 celeste_status celeste_render_device(celeste_problem* prob, const double* d_theta, double* d_e,
                                      double* d_v, void* stream);
+
+/*
+ * Self-test of failure detection without a fault: one kernel waits, through the same
+ * bounded wait the persistent work-queue kernels use (a poll and ~1 s clock limit), on a
+ * shared-memory mbarrier that nothing arrives on.  Returns CELESTE_ERR_TIMEOUT when the
+ * wait gave up and reported it through a status word (the expected outcome, after about
+ * a second; the context stays usable), CELESTE_OK if the barrier completed (a defect),
+ * CELESTE_ERR_CUDA on a launch error.  Runs on the current device.
+ */
+celeste_status celeste_selftest_bounded_wait(void);
 
 /* Thread-local message describing the calling thread's last error. */
 const char* celeste_last_error(void);

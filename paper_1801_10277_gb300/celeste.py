@@ -68,7 +68,8 @@ EXPORTS = ["celeste_problem_create", "celeste_problem_create_ex", "celeste_probl
            "celeste_patch_elbo_grad_noalloc", "celeste_grad_device", "celeste_autotune",
            "celeste_set_tuning", "celeste_cyclades_batches", "celeste_catalog",
            "celeste_catalog_device", "celeste_catalog_score", "celeste_render",
-           "celeste_render_device", "celeste_make_tasks", "celeste_fit_tasks"]
+           "celeste_render_device", "celeste_make_tasks", "celeste_fit_tasks",
+           "celeste_selftest_bounded_wait"]
 
 # catalog row layout (CELESTE_CAT_*): position, type, per-type brightness / colours with
 # their posterior standard deviations, the type-marginal r flux, galaxy shape
@@ -138,6 +139,8 @@ def load(build_if_missing=False):
     L.celeste_catalog.argtypes = [vp, vp, vp]
     L.celeste_catalog_device.argtypes = [vp, vp, vp, vp]
     L.celeste_catalog_score.argtypes = [vp, vp, vp, i32, vp]
+    L.celeste_selftest_bounded_wait.argtypes = []
+    L.celeste_selftest_bounded_wait.restype = i32
     L.celeste_make_tasks.argtypes = [vp, vp, i32, C.c_double, vp, vp, vp]
     L.celeste_make_tasks.restype = i32
     L.celeste_fit_tasks.argtypes = [vp, vp, vp, C.POINTER(celeste_fit_options), vp, vp, vp]
@@ -186,6 +189,11 @@ def cyclades_batches(nbr_offsets, nbrs, order, sample_size):
     _check(L.celeste_cyclades_batches(_p(no), _p(nb_), len(no) - 1, _p(order), len(order),
                                       int(sample_size), _p(b), _p(c), C.byref(nb)))
     return b, c, nb.value
+
+
+def selftest_bounded_wait():
+    """Status of the bounded-wait self-test (ERR_TIMEOUT expected; see celeste.h)."""
+    return int(load().celeste_selftest_bounded_wait())
 
 
 def make_tasks(pos, work, max_work, shift=None):

@@ -286,9 +286,9 @@ celeste_status run_cached(celeste_problem* pr, const double* d_theta, int precis
 celeste_status run_host(celeste_problem* pr, const double* theta, int precision, int mode,
                         double* total, double* local, double* grad, double* hess) {
     if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
-    celeste_status s = check_theta_host(theta, pr->P.n_src);
-    if (s) return s;
-    s = ensure_out(pr);
+    // the parameter domain is checked on the device by the evaluation itself (every
+    // entry of every source, the same rules as the host check), read back with the results
+    celeste_status s = ensure_out(pr);
     if (s) return s;
     const int n = pr->P.n_src;
     double* o_total = pr->d_out;
@@ -300,7 +300,7 @@ celeste_status run_host(celeste_problem* pr, const double* theta, int precision,
                              pr->stream));
     s = run_cached(pr, pr->d_theta, precision, mode, o_total, o_local,
                    mode >= MODE_GRAD ? o_grad : nullptr, mode >= MODE_HESS ? o_hess : nullptr,
-                   pr->stream, false);
+                   pr->stream, true);
     if (s) return s;
     if (total) CEL_CUDA(cudaMemcpyAsync(total, o_total, sizeof(double), cudaMemcpyDeviceToHost, pr->stream));
     if (local) CEL_CUDA(cudaMemcpyAsync(local, o_local, sizeof(double) * n, cudaMemcpyDeviceToHost, pr->stream));
@@ -308,7 +308,11 @@ celeste_status run_host(celeste_problem* pr, const double* theta, int precision,
         CEL_CUDA(cudaMemcpyAsync(grad, o_grad, sizeof(double) * n * NP, cudaMemcpyDeviceToHost, pr->stream));
     if (hess && mode >= MODE_HESS)
         CEL_CUDA(cudaMemcpyAsync(hess, o_hess, sizeof(double) * n * NP * NP, cudaMemcpyDeviceToHost, pr->stream));
+    CEL_CUDA(cudaMemcpyAsync(pr->h_status, pr->P.status, sizeof(int32_t), cudaMemcpyDeviceToHost, pr->stream));
     CEL_CUDA(cudaStreamSynchronize(pr->stream));
+    if (*pr->h_status != 0)
+        return fail(*pr->h_status, "theta outside the parameter domain (status %d from the device check)",
+                    *pr->h_status);
     if (total && !isfinite(*total)) return fail(CELESTE_ERR_NONFINITE, "ELBO is not finite");
     return CELESTE_OK;
 }
@@ -347,6 +351,7 @@ void celeste_problem_destroy(celeste_problem* pr) {
     for (cudaEvent_t e : {pr->ev_prep, pr->ev_fused, pr->ev_gather, pr->ev_join})
         if (e) cudaEventDestroy(e);
     if (pr->stream) cudaStreamDestroy(pr->stream);
+    if (pr->h_status) cudaFreeHost(pr->h_status);
     delete pr;
 }
 
@@ -604,6 +609,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
                 return bail(fail(CELESTE_ERR_CUDA, "cudaEventCreate failed"));
     }
     pr->last_stream = pr->stream;
+    if (cudaMallocHost((void**)&pr->h_status, sizeof(int32_t)) != cudaSuccess)
+        return bail(fail(CELESTE_ERR_NOMEM, "pinned host allocation failed"));
     pr->patch_off.assign(patch_offsets, patch_offsets + n_src + 1);
     pr->nbr_off.assign(nbr_offsets, nbr_offsets + n_src + 1);
     pr->nbrs.assign(nbrs ? nbrs : nbr_offsets, nbrs ? nbrs + n_edge : nbr_offsets);

@@ -44,6 +44,7 @@ struct celeste_problem {
     double* d_theta = nullptr;
     double* d_out = nullptr;     // total(1) | local(n_src) | grad(n_src*44) | hess(n_src*44*44)
     size_t out_cap = 0;
+    int32_t* h_status = nullptr; // pinned copy of the device status word (host-pointer calls)
     double* d_scr = nullptr;     // catalog / score scratch, grown on demand
     size_t scr_cap = 0;
     // per-kernel CUDA-event timing (celeste_profile_*)
