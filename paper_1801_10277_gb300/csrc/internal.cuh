@@ -259,4 +259,11 @@ cudaError_t launch_score(int n, const double* d_est, const double* d_true, doubl
 // E = sky and Var = 0 over every pixel of every image (FP64, concatenated image layout)
 cudaError_t launch_fill_sky(const DevProblem& P, double* d_e, double* d_v, cudaStream_t st);
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor in the stream is
+// still running; pdl_wait() blocks until that predecessor has completed and its writes are
+// visible (a no-op for an ordinary launch), pdl_trigger() lets the dependent start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace cel

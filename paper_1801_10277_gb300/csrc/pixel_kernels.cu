@@ -160,6 +160,7 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
        const ModelDev* __restrict__ md, int n_src, int nprof, R* __restrict__ tbl,
        double* __restrict__ kl_out, double* __restrict__ klg_out, int32_t* __restrict__ status,
        const int32_t* __restrict__ src_active) {
+    pdl_trigger();   // the map pass may be scheduled; it waits for the tables
     const int s = blockIdx.x;
     if (s >= n_src || (src_active && !src_active[s])) return;
     const int p0 = patch_off[s], np = patch_off[s + 1] - p0;
@@ -1146,10 +1147,12 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_split(const Wor
                                                                      float* __restrict__ spE,
                                                                      float* __restrict__ spV) {
     __shared__ __align__(16) float2 sT2[TBL_STRIDE];
+    pdl_trigger();   // the gather + adjoint may be scheduled; it waits for this grid
     const int item = idx[blockIdx.x];
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
+    pdl_wait();      // the tables come from k_prep
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
     contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, nullptr, nullptr, nullptr, nullptr,
                            nullptr, nullptr, pix);
@@ -1169,6 +1172,7 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_gadjoint_x2(const WorkI
     const WorkItem it = items[item];
     const PatchGeo g = ga.geo[it.patch];
     const ImgMeta& im = img[g.img];
+    pdl_wait();      // E_s / Var_s of the covering patches come from k_contrib_split
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
     adjoint_x2_item<MODE, NPAIR, SRC_GATHER>(item, it, g, im, nprof, sT2, pixels, ga.emap, ga.vmap, part,
                                              nullptr, nullptr, nullptr, nullptr, &ga, ga.pix);
@@ -1545,24 +1549,47 @@ void prime_fused_caps() {
     }
 }
 
+static cudaLaunchConfig_t pdl_config(int grid, int block, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    return cfg;
+}
+
 template <int NPAIR>
-static void gadjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
+static cudaError_t gadjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     const GatherArgs ga{P.single, P.tile_grid, P.tiles, P.tile_list, P.geo, (const float*)P.spE,
                         (const float*)P.spE2, P.sky_map, (float*)P.emap, (float*)P.vmap, P.sitem_own,
                         P.spix};
+    cudaLaunchConfig_t cfg = pdl_config(P.n_smulti, NT, st);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
     if (mode == MODE_LL)
-        k_gadjoint_x2<MODE_LL, NPAIR><<<P.n_smulti, NT, 0, st>>>(P.sitems, P.sidx_multi, P.img, P.nprof,
-                                                                P.pixels, P.tbl32, P.spart, ga);
-    else
-        k_gadjoint_x2<MODE_GRAD, NPAIR><<<P.n_smulti, NT, 0, st>>>(P.sitems, P.sidx_multi, P.img, P.nprof,
-                                                                  P.pixels, P.tbl32, P.spart, ga);
+        return cudaLaunchKernelEx(&cfg, k_gadjoint_x2<MODE_LL, NPAIR>, P.sitems, P.sidx_multi, P.img, P.nprof,
+                                  (const float*)P.pixels, (const float*)P.tbl32, P.spart, ga);
+    return cudaLaunchKernelEx(&cfg, k_gadjoint_x2<MODE_GRAD, NPAIR>, P.sitems, P.sidx_multi, P.img, P.nprof,
+                              (const float*)P.pixels, (const float*)P.tbl32, P.spart, ga);
 }
 
+// the map pass of the multiply covered items, launched as a programmatic dependent of
+// k_prep (its CTAs start while the tables are being built and wait for them)
 template <int NPAIR>
-static void contrib_split(const DevProblem& P, cudaStream_t st) {
-    k_contrib_split<NPAIR><<<P.n_smulti, CHUNK / (2 * NPAIR), 0, st>>>(
-        P.sitems, P.sidx_multi, P.spix, P.geo, P.img, P.nprof, P.tbl32, (float*)P.spE, (float*)P.spE2);
+static cudaError_t contrib_split(const DevProblem& P, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = pdl_config(P.n_smulti, CHUNK / (2 * NPAIR), st);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_contrib_split<NPAIR>, (const WorkItem*)P.sitems, (const int32_t*)P.sidx_multi,
+                       (const int32_t*)P.spix, (const PatchGeo*)P.geo, (const ImgMeta*)P.img, P.nprof,
+                       (const float*)P.tbl32, (float*)P.spE, (float*)P.spE2);
 }
 
 // Occupancy queries of the persistent kernels, made once on the current device outside
@@ -1651,18 +1678,16 @@ cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const d
 cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st) {
     if (P.n_smulti == 0) return cudaSuccess;
     const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7) contrib_split<2>(P, st);
-    else contrib_split<1>(P, st);
-    return cudaGetLastError();
+    const cudaError_t e = (code == 5 || code == 7) ? contrib_split<2>(P, st) : contrib_split<1>(P, st);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // gather + adjoint over the split items of multiply covered pixels
 cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st) {
     if (P.n_smulti == 0) return cudaSuccess;
     const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7) gadjoint_x2<2>(P, mode, st);
-    else gadjoint_x2<1>(P, mode, st);
-    return cudaGetLastError();
+    const cudaError_t e = (code == 5 || code == 7) ? gadjoint_x2<2>(P, mode, st) : gadjoint_x2<1>(P, mode, st);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // the adjoint over P.idx_mixed from the maps, with the kernel launch_gather_adjoint uses
