@@ -250,9 +250,10 @@ def main():
     ap.add_argument("--no-tasks", action="store_true", help="skip the region-task leg")
     ap.add_argument("--fit-only", action="store_true",
                     help="time the Newton fit of the workload alone (FP32 sweeps, FP64 polish)")
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5],
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5, 6],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
-                         "4 sweep field, 5 deep stack (480 images per source); the JSON line names it")
+                         "4 sweep field, 5 deep stack (480 images per source), 6 the whole 200,000-source "
+                         "sweep (64 fields); the JSON line names it")
     ap.add_argument("--tuning", default=None,
                     help="contrib,adjoint,fused_cap,gather_sep codes to use instead of autotuning (e.g. 2,1,0,0)")
     args = ap.parse_args()

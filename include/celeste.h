@@ -230,8 +230,11 @@ void celeste_fit_options_default(celeste_fit_options* opts);
  * theta_inout[n_src][44] (host) is read and overwritten.  which[n_which] restricts the
  * moving sources (NULL: all).  iters_out / status_out ([n_src], nullable) receive
  * Newton iterations and 0 converged / 1 iteration limit / 2 non-finite.  The fit
- * restarts from theta_inout, so it can be resumed.  A Cyclades order row that is not a
- * permutation of the moving sources, or sample_size < 1, is CELESTE_ERR_ARG.
+ * restarts from theta_inout, so it can be resumed (also from its own result, whose
+ * bounded parameters may sit on their bounds).  The fit works inside a box: e_dev and
+ * e_axis in [0.01, 0.99], a_star in [0.005, 0.995]; a start outside it, a Cyclades order
+ * row that is not a permutation of the moving sources, or sample_size < 1, is
+ * CELESTE_ERR_ARG.
  */
 celeste_status celeste_fit_sources(celeste_problem* prob, double* theta_inout,
                                    const int32_t* which, int32_t n_which,

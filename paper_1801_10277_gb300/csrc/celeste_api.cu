@@ -793,10 +793,10 @@ celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, con
     if (s) return s;
     for (int i = 0; i < pr->P.n_src; ++i) {
         const double* th = theta_inout + (size_t)NP * i;
-        if (!(th[P_EDEV] > 0.01 && th[P_EDEV] < 0.99 && th[P_AXIS] > 0.01 && th[P_AXIS] < 0.99 &&
-              th[P_A] > 0.005 && th[P_A] < 0.995))
+        if (!(th[P_EDEV] >= 0.01 && th[P_EDEV] <= 0.99 && th[P_AXIS] >= 0.01 && th[P_AXIS] <= 0.99 &&
+              th[P_A] >= 0.005 && th[P_A] <= 0.995))
             return fail(CELESTE_ERR_ARG,
-                        "theta[%d]: the fit needs e_dev, e_axis in (0.01, 0.99) and a_star in (0.005, 0.995)", i);
+                        "theta[%d]: the fit needs e_dev, e_axis in [0.01, 0.99] and a_star in [0.005, 0.995]", i);
     }
     CEL_CUDA(cudaSetDevice(pr->device));
     s = ensure_out(pr);

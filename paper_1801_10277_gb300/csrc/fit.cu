@@ -74,7 +74,13 @@ __device__ void free_to_theta(const double* t, double* th) {
 }
 
 __device__ void theta_to_free(const double* th, double* t) {
-    auto logit = [](double p) { return log(p / (1.0 - p)); };
+    // a fitted parameter can sit on its bound after rounding (the sigmoid of a large free
+    // coordinate is 1 in FP64); the fraction is kept 1e-15 inside so the free coordinate
+    // stays finite and a fit can resume from its own result
+    auto logit = [](double p) {
+        p = fmin(fmax(p, 1e-15), 1.0 - 1e-15);
+        return log(p / (1.0 - p));
+    };
     t[0] = th[0];
     t[1] = th[1];
     t[2] = logit((th[P_EDEV] - BOX_LO) / (BOX_HI - BOX_LO));

@@ -455,7 +455,8 @@ def config(idx, seed=None, **kw):
     """The workloads by index: 0 tiny two-source, 1 one field of 500 sources,
     2 crowded 64-source region, 3 multi-epoch 20k sources, 4 is built per field by
     ``many_fields`` (200k sources over 64 fields) and sampled, 5 deep stack (480
-    images per source, distorted maps linearised per source)."""
+    images per source, distorted maps linearised per source), 6 the whole sweep (the
+    64 fields of 4 as one 200,000-source problem)."""
     base = 2026 + idx if seed is None else seed
     if idx == 0:
         return tiny_two_source(base, **kw)
@@ -469,6 +470,8 @@ def config(idx, seed=None, **kw):
         return many_fields_sample(base, **kw)
     if idx == 5:
         return deep_stack(base, **kw)
+    if idx == 6:
+        return full_sweep(2030 if seed is None else seed, **kw)
     raise ValueError(idx)
 
 
@@ -479,6 +482,42 @@ def many_fields_sample(seed=2030, n_fields_sampled=1, n_src_per_field=3125, brig
     out = one_field(seed, n_src=n_src_per_field * n_fields_sampled, bright_frac=bright_frac)
     out.name = f"sweep_field_{out.n_src}src_bright{bright_frac}"
     return out
+
+
+def full_sweep(seed=2030, n_fields=64, n_src_per_field=3125, bright_frac=0.1, gap=52):
+    """The whole 200,000-source sweep as one problem: 64 disjoint fields (field f drawn
+    as the sweep field with seed + 7919 f, so field 0 is the sampled sweep field), laid
+    side by side in one world frame 2048 + gap px apart along x; each field's images map
+    their own strip (pixel = u - (f (2048 + gap), 0))."""
+    fields = [one_field(seed + 7919 * f, n_src=n_src_per_field, bright_frac=bright_frac)
+              for f in range(n_fields)]
+    images, thetas, truths, po, pa, no, nb = [], [], [], [0], [], [0], []
+    n0 = 0
+    for f, fld in enumerate(fields):
+        dx = f * (fld.images[0].width + gap)
+        for im in fld.images:
+            im.wcs = im.wcs.copy()
+            im.wcs[4] -= dx
+            images.append(im)
+        th, tr = fld.theta.copy(), fld.truth.copy()
+        th[:, 0] += dx
+        tr[:, 0] += dx
+        thetas.append(th)
+        truths.append(tr)
+        rows = fld.patches.copy()
+        rows[:, 0] += NBANDS * f
+        pa.append(rows)
+        po.extend((fld.patch_offsets[1:] + po[-1]).tolist())
+        nb.append(fld.nbrs + n0)
+        no.extend((fld.nbr_offsets[1:] + no[-1]).tolist())
+        n0 += fld.n_src
+    f0 = fields[0]
+    return Problem(images=images, exp_mix=f0.exp_mix, dev_mix=f0.dev_mix, prior_star=f0.prior_star,
+                   prior_r=f0.prior_r, prior_c=f0.prior_c, theta=np.concatenate(thetas),
+                   truth=np.concatenate(truths), patch_offsets=np.array(po, np.int32),
+                   patches=np.concatenate(pa).astype(np.int32), nbr_offsets=np.array(no, np.int32),
+                   nbrs=np.concatenate(nb).astype(np.int32),
+                   name=f"sweep_{n0}src_{n_fields}x5x{f0.images[0].width}x{f0.images[0].height}")
 
 
 def subset(prob, idx):

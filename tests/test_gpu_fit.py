@@ -192,3 +192,20 @@ def test_fit_cyclades_generated_orders(cel):
     with pytest.raises(cel.CelesteError):
         P.fit(prob.theta, which=which, schedule="cyclades", sample_size=0)
     P.close()
+
+
+def test_fit_crowded_region_to_convergence(cel):
+    """The crowded region (64 mutually overlapping sources, 2-12 neighbours each),
+    block-coordinate trust-region Newton run until a sweep changes the total ELBO by
+    less than 1e-8 relative: a further sweep from the result then moves the ELBO by less
+    than that, and the total never decreased."""
+    prob = synth.config(2)
+    P = cel.Problem(prob)
+    start = P.elbo(prob.theta, precision=cel.FP64)[0]
+    th, it, st, el = P.fit(prob.theta, precision=cel.FP64, max_sweeps=100, sweep_tol=1e-8)
+    assert el > start
+    assert np.count_nonzero(st == 0) >= 0.75 * prob.n_src
+    th2, _, _, el2 = P.fit(th, precision=cel.FP64, max_sweeps=1)
+    assert abs(el2 - el) <= 1e-8 * abs(el)
+    assert el2 >= el - 1e-9 * abs(el)
+    P.close()
