@@ -1,4 +1,4 @@
-"""GPU parity on the two large workloads, at full size, through the C ABI.
+"""GPU parity on the large workloads, at full size, through the C ABI.
 
 * Multi-epoch region (8 overlapping 2048 x 1489 fields, 5 bands each, per-image PSF,
   sky, calibration and affine WCS; 20,000 sources).  The oracle cannot evaluate every
@@ -11,6 +11,9 @@
 * Sweep field (one of 64 disjoint fields: 3,125 sources, 10 % bright with patches up
   to 101 px).  The oracle evaluates the whole field; totals, every local objective and
   the gradients of a 1,000-source sample are compared.
+
+* The whole sweep (the 64 fields as one 200,000-source problem): each field's sources
+  against the same field evaluated alone.
 
 Tolerances as in test_gpu_parity: FP64 path ELBO rel <= 1e-10, gradient rel-L2 <= 1e-8;
 FP32 path ELBO rel <= 1e-5, gradient rel-L2 <= 1e-4.
@@ -83,3 +86,30 @@ def test_sweep_field_with_bright_sources(cel):
         assert np.max(np.abs(loc - o_loc) / np.abs(o_loc)) <= tl, prec
         assert rel_l2(g[which], o_g) <= tg, (prec, rel_l2(g[which], o_g))
     P.close()
+
+
+def test_whole_sweep_matches_its_fields(cel):
+    """The 200,000-source sweep as one problem (64 disjoint fields, 320 images): every
+    source's local objective and gradient equal those of its field evaluated alone (the
+    fields share no pixels; field 0 is the sweep field checked against the oracle above
+    on 1,000 sampled sources), and the total is the sum of the fields' totals."""
+    sweep = synth.config(6)
+    assert sweep.n_src == 200000 and len(sweep.images) == 320
+    P = cel.Problem(sweep)
+    res = {prec: P.elbo_grad(sweep.theta, precision=prec) for prec in (cel.FP64, cel.FP32)}
+    P.close()
+    for f in (0, 37, 63):
+        fld = synth.one_field(2030 + 7919 * f, n_src=3125, bright_frac=0.1)
+        # the sweep shares field 0's priors (each field alone draws its own)
+        fld.prior_star, fld.prior_r, fld.prior_c = sweep.prior_star, sweep.prior_r, sweep.prior_c
+        rows = slice(3125 * f, 3125 * (f + 1))
+        Pf = cel.Problem(fld)
+        # the sweep's world frame shifts positions and map offsets by up to 1.3e5 px, so
+        # the pixel-frame means agree to ~1e-11 px rather than bit for bit
+        for prec, tol in ((cel.FP64, 1e-9), (cel.FP32, 1e-5)):
+            tot, loc, g = Pf.elbo_grad(fld.theta, precision=prec)
+            np.testing.assert_allclose(res[prec][1][rows], loc, rtol=tol)
+            assert rel_l2(res[prec][2][rows], g) <= tol, (f, prec)
+        Pf.close()
+    assert np.isfinite(res[cel.FP64][0])
+    assert rel(res[cel.FP32][0], res[cel.FP64][0]) <= 1e-5
