@@ -320,7 +320,9 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
  * next item's table prefetched by bulk asynchronous copy), reps launches each with CUDA
  * events on the problem's stream, at theta (host).  The adjoint's code also picks the
  * pair count of the fused map + adjoint pass (four pixels per thread for codes 5, 7).
- * Then, with those kernels, it times whole FP32 value + gradient evaluations for the
+ * Then, with those kernels, it times whole FP32 value + gradient evaluations (through the
+ * captured CUDA graph the calls replay, whose nodes keep the critical chain's high and the
+ * fused pass's low stream priority) for the
  * schedule of the multiply covered pixels (gather_sep 0: each covering patch's adjoint
  * gathers E and Var itself; 1: one tile-major gather, then the adjoint from the maps --
  * better when many patches overlap) and for caps of 0 (none), 8, 7, .., 3 resident CTAs

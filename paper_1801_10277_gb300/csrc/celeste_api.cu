@@ -269,7 +269,7 @@ celeste_status run_cached(celeste_problem* pr, const double* d_theta, int precis
             if (rs != CELESTE_OK) return rs;
             return cuda_fail(ce != cudaSuccess ? ce : ee, "evaluation capture");
         }
-        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
         if (pr->graphs.size() >= MAX_GRAPHS) {
@@ -601,8 +601,10 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     {
         int least = 0, greatest = 0;   // numerically greatest = lowest priority
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        // graphs are captured with the critical chain on the highest-priority stream and the
+        // fused pass on the lowest, and instantiated to keep those per-node priorities
         if (cudaStreamCreateWithPriority(&pr->side, cudaStreamNonBlocking, least) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&pr->capture, cudaStreamNonBlocking) != cudaSuccess)
+            cudaStreamCreateWithPriority(&pr->capture, cudaStreamNonBlocking, greatest) != cudaSuccess)
             return bail(fail(CELESTE_ERR_CUDA, "cudaStreamCreate failed"));
         for (cudaEvent_t* e : {&pr->ev_prep, &pr->ev_fused, &pr->ev_gather, &pr->ev_join})
             if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
@@ -943,19 +945,23 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     int pick_cap = 0, pick_sep = 0;
     if (e == cudaSuccess && fused && ensure_out(pr) == CELESTE_OK) {
         // (sep, cap) pairs: the gather inside the adjoint or tile-major, then the cap
-        const int combos[9][2] = {{0, 0}, {1, 0}, {0, 8}, {0, 7}, {0, 6}, {0, 5}, {0, 4}, {0, 3}, {1, 6}};
+        // timed as the calls run them: through the captured graph, whose nodes keep the
+        // chain's and the fused pass's stream priorities
+        constexpr int NC = 12;
+        const int combos[NC][2] = {{0, 0}, {1, 0}, {0, 8}, {1, 8}, {0, 7}, {0, 6}, {1, 6},
+                                   {0, 5}, {0, 4}, {1, 4}, {0, 3}, {1, 3}};
         float best = 1e30f;
         double* o = pr->d_out;
-        for (int ci = 0; ci < 9 && e == cudaSuccess; ++ci) {
+        for (int ci = 0; ci < NC && e == cudaSuccess; ++ci) {
             P.gather_sep = combos[ci][0];
             P.fused_cap = combos[ci][1];
-            celeste_status rs = run(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1,
-                                    o + 1 + P.n_src, nullptr, st);
+            celeste_status rs = run_cached(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1,
+                                           o + 1 + P.n_src, nullptr, st, false);
             float t = 0.f;
             if (rs == CELESTE_OK) e = cudaEventRecord(a, st);
             for (int r = 0; r < 2 * reps && rs == CELESTE_OK && e == cudaSuccess; ++r)
-                rs = run(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1, o + 1 + P.n_src,
-                         nullptr, st);
+                rs = run_cached(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1, o + 1 + P.n_src,
+                                nullptr, st, false);
             if (rs != CELESTE_OK) e = cudaErrorUnknown;
             if (e == cudaSuccess) e = cudaEventRecord(b, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(b);
