@@ -371,7 +371,6 @@ __device__ void kl_hessian_warp(const ModelDev& md, const double* th, double* H)
 }
 
 constexpr int FH_THREADS = 256;
-constexpr int FH_PER = (NP * NP + FH_THREADS - 1) / FH_THREADS;
 
 // d(m + v/2) / d theta_j (second = false) or d(2m + 2v) / d theta_j (second = true) of
 // type ty in band `band`, where log l | ty ~ N(m, v), m = r1 + beta . c1, v = r2 + beta^2 . c2
@@ -409,6 +408,9 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
     __shared__ double wd[2], we[2];
     __shared__ double S2[3][3];
     __shared__ double klH[NP * NP];
+    __shared__ double Hacc[NP * NP];              // the pixel part of the 44 x 44 Hessian
+    __shared__ double bd[2][2][NP];               // bright_d(band, type, j, second) of this patch
+    __shared__ int act[NP], nact;                 // parameters this patch touches
     __shared__ double klg[NP];
     __shared__ double klv;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -416,7 +418,10 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         th[t] = theta[(size_t)NP * s + t];
         if (status) theta_domain_check(t, th[t], status);
     }
-    for (int i = t; i < NP * NP; i += blockDim.x) klH[i] = 0.0;
+    for (int i = t; i < NP * NP; i += blockDim.x) {
+        klH[i] = 0.0;
+        Hacc[i] = 0.0;
+    }
     __syncthreads();
     // the KL (warp 0: value and gradient; warp 1: Hessian) and the band moments of the
     // five bands (warp 2), each lane-parallel: the FP64 pipe costs a warp instruction
@@ -430,9 +435,6 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         const int b = lane >> 1, i = lane & 1;
         band_moments(th, b, i, bmom[b][i][0], bmom[b][i][1]);
     }
-    double acc[FH_PER];
-#pragma unroll
-    for (int k = 0; k < FH_PER; ++k) acc[k] = 0.0;
     double gacc = 0.0, lacc = 0.0;
     for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
         __syncthreads();
@@ -483,6 +485,10 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 if (ev != 0.0) put(i == 0 ? Y_EL20 : Y_EL21, bmom[im.band][i][1] * ev);
             }
             nzn[j] = n;
+            for (int ty = 0; ty < 2; ++ty) {
+                bd[ty][0][j] = bright_d(im.band, ty, j, false);
+                bd[ty][1][j] = bright_d(im.band, ty, j, true);
+            }
         } else if (t >= 64 && t < 73) {
             const int a = (t - 64) / 3, b = (t - 64) % 3;
             S2[a][b] = Gy[Y_GXX] * d2G[a][b][0] + Gy[Y_GXY] * d2G[a][b][1] + Gy[Y_GYY] * d2G[a][b][2];
@@ -494,35 +500,40 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         __syncthreads();
         if (t < NP)
             for (int n = 0; n < nzn[t]; ++n) gacc += nzv[t][n] * Gy[nzy[t][n]];
-        const int band = im.band;
-#pragma unroll
-        for (int k = 0; k < FH_PER; ++k) {
-            const int idx = t + k * FH_THREADS;
-            if (idx >= NP * NP) break;
-            const int i = idx / NP, j = idx - i * NP;
+        if (t == 0) {
+            // the parameters with a nonzero Jacobian column: the only rows and columns this
+            // patch adds to (every brightness and shape term lies among them)
+            int c = 0;
+            for (int j = 0; j < NP; ++j)
+                if (nzn[j] > 0) act[c++] = j;
+            nact = c;
+        }
+        __syncthreads();
+        // the upper triangle of the active block, each entry (and its mirror) by one thread
+        const int na = nact, npair = na * (na + 1) / 2;
+        for (int q = t; q < npair; q += blockDim.x) {
+            int a = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > q) --a;
+            while ((a + 1) * (a + 2) / 2 <= q) ++a;
+            const int b = q - a * (a + 1) / 2;   // b <= a
+            const int i = act[a], j = act[b];
             double h = 0.0;
-            for (int a = 0; a < nzn[i]; ++a)
-                for (int b = 0; b < nzn[j]; ++b)
-                    h += nzv[i][a] * Hy[nzy[i][a]][nzy[j][b]] * nzv[j][b];
+            for (int u = 0; u < nzn[i]; ++u)
+                for (int v = 0; v < nzn[j]; ++v)
+                    h += nzv[i][u] * Hy[nzy[i][u]][nzy[j][v]] * nzv[j][v];
             // second derivatives of log E[l] and log E[l^2] (linear in the brightness
             // parameters, so only their products appear): w (dm)(dm)'
-            for (int ty = 0; ty < 2; ++ty) {
-                const double di = bright_d(band, ty, i, false), dj = bright_d(band, ty, j, false);
-                const double ei = bright_d(band, ty, i, true), ej = bright_d(band, ty, j, true);
-                h += wd[ty] * di * dj + we[ty] * ei * ej;
-            }
+            for (int ty = 0; ty < 2; ++ty)
+                h += wd[ty] * bd[ty][0][i] * bd[ty][0][j] + we[ty] * bd[ty][1][i] * bd[ty][1][j];
             if (i >= P_AXIS && i <= P_SCALE && j >= P_AXIS && j <= P_SCALE)
                 h += S2[i - P_AXIS][j - P_AXIS];
-            acc[k] += h;
+            Hacc[i * NP + j] += h;
+            if (i != j) Hacc[j * NP + i] += h;
         }
     }
     __syncthreads();
     double* Ho = hess_out + (size_t)NP * NP * s;
-#pragma unroll
-    for (int k = 0; k < FH_PER; ++k) {
-        const int idx = t + k * FH_THREADS;
-        if (idx < NP * NP) Ho[idx] = acc[k] - klH[idx];
-    }
+    for (int idx = t; idx < NP * NP; idx += blockDim.x) Ho[idx] = Hacc[idx] - klH[idx];
     if (t < NP && grad_out) grad_out[(size_t)NP * s + t] = gacc - klg[t];
     if (t == 0) {
         kl_out[s] = klv;
