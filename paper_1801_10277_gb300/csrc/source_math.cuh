@@ -147,10 +147,10 @@ template <> __device__ __forceinline__ double rcpp<double>(double x) { return 1.
 
 // The KL and its gradient (closed forms of kl_value_grad) computed by one warp; every
 // lane must call it.  th: the 44 parameters (FP64), thr: the same in R (shared).
-//   round 1 (FP64 range, one logarithm / reciprocal per lane): lanes 0..15 log(k_id /
+//   phase one (FP64 range, one logarithm / reciprocal per lane): lanes 0..15 log(k_id /
 //     w_id), 16..23 log c2 and 1/c2, 24..25 log(a_i / Phi_i), 26..27 log(pv_i / r2_i) and
 //     1/r2_i;
-//   round 2 (lanes 0..15, lane = 8 i + d: type i, colour-prior component d): the 4 x 4
+//   phase two (lanes 0..15, lane = 8 i + d: type i, colour-prior component d): the 4 x 4
 //     algebra of component d in R, then sums over the eight components in R of
 //     k_d (log k_d/w_d + KL_d), k_d P_d (c1 - mu_d), k_d diag P_d and k_d;
 //   outputs: lanes 8 i + j (j < 4) the c1 / c2 entries of colour j, lanes 8 i + 4..6 the
@@ -182,7 +182,7 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, const R* 
     // log det of q's colour covariance: sum of the four log c2 of type i
     R slog = 0;
     for (int j = 0; j < 4; ++j) slog += (R)__shfl_sync(full, lv, 16 + 4 * i + j);
-    // round 2
+    // phase two
     R term = 0, ks = 0, kP[4] = {0, 0, 0, 0}, kD[4] = {0, 0, 0, 0};
     if (lane < 16) {
         const R k = thr[P_K + NCOMP * i + d];

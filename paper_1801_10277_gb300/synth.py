@@ -60,7 +60,7 @@ class Image:
     wcs: np.ndarray               # [6]: A00 A01 A10 A11 t0 t1; pixel = A u + t
     psf: np.ndarray               # [K][6]: alpha, xi_x, xi_y, Sxx, Sxy, Syy
     sky_map: np.ndarray | None = None   # optional [H][W] float32 sky counts
-    # optional smooth distortion added to the affine map (a stand-in for a survey WCS):
+    # optional smooth distortion added to the affine map (a stand-in for a sky survey's WCS):
     # (cx, cy, L, d1, d2, d3, d4), pixel = A u + t + (d1 x^2 + d2 x y, d3 y^2 + d4 x y)
     # with x = (u0 - cx) / L, y = (u1 - cy) / L
     warp: tuple | None = None
