@@ -305,6 +305,15 @@ __device__ void warp_bwd(const double* L, const double* invd, const double* y, d
     __syncwarp();
 }
 
+// Sum over the 32 lanes of a warp (every lane gets it).  The FP64 pipe charges a warp
+// instruction whatever the active lanes, so a vector of 41 is summed lane-parallel (two
+// entries a lane) and reduced in five steps rather than looped on one lane.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(TR_THREADS)
 k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ tfree,
           const double* __restrict__ f_in, const double* __restrict__ g_in,
@@ -445,13 +454,28 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         rs[tid] = r;
     }
     __syncthreads();
-    double cn = 0.0, bnorm = 0.0, bdmin = 1e300;
-    for (int i = 0; i < TRN; ++i) {
-        cn += cvec[i] * cvec[i];
-        bnorm = fmax(bnorm, rs[i]);
-        bdmin = fmin(bdmin, Ht[i * TRN + i]);
+    __shared__ double bnd[3];
+    if (tid < 32) {
+        double c2 = 0.0, bn = 0.0, bd = 1e300;
+        for (int i = tid; i < TRN; i += 32) {
+            c2 += cvec[i] * cvec[i];
+            bn = fmax(bn, rs[i]);
+            bd = fmin(bd, Ht[i * TRN + i]);
+        }
+        c2 = warp_sum_d(c2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bn = fmax(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+            bd = fmin(bd, __shfl_xor_sync(0xffffffffu, bd, o));
+        }
+        if (tid == 0) {
+            bnd[0] = c2;
+            bnd[1] = bn;
+            bnd[2] = bd;
+        }
     }
-    cn = sqrt(cn);
+    __syncthreads();
+    const double cn = sqrt(bnd[0]), bnorm = bnd[1], bdmin = bnd[2];
     double lamL = fmax(0.0, fmax(-bdmin, cn / Delta - bnorm));
     double lamU = cn / Delta + bnorm;
     double lam = 0.0;
@@ -467,14 +491,13 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         if (tid < 32) {
             warp_fwd(L, invd, cvec, w, TRN);
             warp_bwd(L, invd, w, p, TRN);
-            if (tid == 0) {
-                double s = 0.0;
-                for (int i = 0; i < TRN; ++i) {
-                    p[i] = -p[i];
-                    s += p[i] * p[i];
-                }
-                pn_s = sqrt(s);
+            double s = 0.0;
+            for (int i = tid; i < TRN; i += 32) {
+                p[i] = -p[i];
+                s += p[i] * p[i];
             }
+            s = warp_sum_d(s);
+            if (tid == 0) pn_s = sqrt(s);
         }
         __syncthreads();
         if (pn_s <= Delta) solved = true;
@@ -501,13 +524,12 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
                     warp_fwd(L, invd, cvec, w, TRN);
                     warp_bwd(L, invd, w, p, TRN);
                     double s = 0.0;
-                    for (int i = 0; i < TRN; ++i) s += p[i] * p[i];
-                    const double pn = sqrt(s);
-                    __syncwarp();
-                    if (tid == 0) {
-                        for (int i = 0; i < TRN; ++i) p[i] = -p[i];
-                        pn_s = pn;
+                    for (int i = tid; i < TRN; i += 32) {
+                        p[i] = -p[i];
+                        s += p[i] * p[i];
                     }
+                    const double pn = sqrt(warp_sum_d(s));
+                    if (tid == 0) pn_s = pn;
                     __syncwarp();
                     int dn;
                     // |p| within 1e-6 of the radius: the step's model value is then
@@ -520,7 +542,8 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
                         else lamL = lam;
                         warp_fwd(L, invd, p, w, TRN);
                         double wn = 0.0;
-                        for (int i = 0; i < TRN; ++i) wn += w[i] * w[i];
+                        for (int i = tid; i < TRN; i += 32) wn += w[i] * w[i];
+                        wn = warp_sum_d(wn);
                         nl = lam + (pn * pn / wn) * (pn - Delta) / Delta;
                         if (!(nl > lamL && nl < lamU))
                             nl = fmax(sqrt(fmax(lamL, 1e-300) * lamU), lamL + 0.01 * (lamU - lamL));
@@ -593,9 +616,12 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         rs[tid] = s;
     }
     __syncthreads();
+    double pred = 0.0;
+    if (tid < 32) {
+        for (int i = tid; i < TRN; i += 32) pred -= cvec[i] * p[i] + 0.5 * p[i] * rs[i];
+        pred = warp_sum_d(pred);
+    }
     if (tid == 0) {
-        double pred = 0.0;
-        for (int i = 0; i < TRN; ++i) pred -= cvec[i] * p[i] + 0.5 * p[i] * rs[i];
         S.pred = pred;
         S.pnorm = pn_s;
         S.lam = solved ? 0.0 : lam;
