@@ -648,38 +648,50 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     }
 }
 
-// ratio of actual to predicted gain, radius update, acceptance (one thread per source)
-__global__ void k_tr_accept(int nb, const int32_t* __restrict__ bpatch_off,
-                            const PatchGeo* __restrict__ bgeo, const double* __restrict__ dll,
-                            const ModelDev* __restrict__ md, double* __restrict__ theta,
-                            double* __restrict__ tfree, const double* __restrict__ theta_c,
-                            const double* __restrict__ tfree_c, TrState* __restrict__ st,
-                            celeste_fit_options o) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// ratio of actual to predicted gain, radius update, acceptance: one warp per source (the
+// candidate's KL lane-parallel in FP64, the log-likelihood change summed over the
+// source's items by the lanes), so the FP64 work spreads over every SM
+__global__ void __launch_bounds__(32)
+k_tr_accept(int nb, const int32_t* __restrict__ bpatch_off, const PatchGeo* __restrict__ bgeo,
+            const double* __restrict__ dll, const ModelDev* __restrict__ md, double* __restrict__ theta,
+            double* __restrict__ tfree, const double* __restrict__ theta_c,
+            const double* __restrict__ tfree_c, TrState* __restrict__ st, celeste_fit_options o) {
+    const int b = blockIdx.x;
     if (b >= nb) return;
-    TrState S = st[b];
+    const int lane = threadIdx.x;
+    __shared__ TrState S;
+    __shared__ double thc[NP], kg[NP];
+    __shared__ int accept;
+    if (lane == 0) S = st[b];
+    __syncwarp();
     if (S.status != ST_ACTIVE || !S.cand) return;
-    const double* thc = theta_c + (size_t)NP * b;
+    for (int i = lane; i < NP; i += 32) thc[i] = theta_c[(size_t)NP * b + i];
+    __syncwarp();
     double d = 0.0;
     for (int p = bpatch_off[b]; p < bpatch_off[b + 1]; ++p) {
         const PatchGeo g = bgeo[p];
-        for (int it = g.item0; it < g.item0 + g.nitem; ++it) d += dll[it];
+        for (int it = g.item0 + lane; it < g.item0 + g.nitem; it += 32) d += dll[it];
     }
-    const double klc = kl_value_grad(*md, thc, nullptr);
-    const double df = d - (klc - S.kl);
-    const double scale = 1.0 + fabs(S.f);
-    double rho = (S.pred <= o.f_noise_rel * scale) ? 1.0 : df / S.pred;
-    if (!isfinite(df)) rho = -1.0;
-    if (rho < 0.25) S.delta = 0.25 * S.delta;
-    else if (rho > 0.75 && S.pnorm >= (1.0 - 1e-9) * S.delta) S.delta = fmin(2.0 * S.delta, o.delta_max);
-    if (rho > o.eta) {
-        for (int i = 0; i < NP; ++i) theta[(size_t)NP * b + i] = thc[i];
-        for (int i = 0; i < NT; ++i) tfree[(size_t)NT * b + i] = tfree_c[(size_t)NT * b + i];
+    d = warp_sum_d(d);
+    const double klc = kl_warp<double>(*md, thc, thc, kg);
+    if (lane == 0) {
+        const double df = d - (klc - S.kl);
+        const double scale = 1.0 + fabs(S.f);
+        double rho = (S.pred <= o.f_noise_rel * scale) ? 1.0 : df / S.pred;
+        if (!isfinite(df)) rho = -1.0;
+        if (rho < 0.25) S.delta = 0.25 * S.delta;
+        else if (rho > 0.75 && S.pnorm >= (1.0 - 1e-9) * S.delta) S.delta = fmin(2.0 * S.delta, o.delta_max);
+        accept = rho > o.eta;
+        S.iters += 1;
+        if (S.iters >= o.max_iter) S.status = ST_MAXITER;
+        S.cand = 0;
+        st[b] = S;
     }
-    S.iters += 1;
-    if (S.iters >= o.max_iter) S.status = ST_MAXITER;
-    S.cand = 0;
-    st[b] = S;
+    __syncwarp();
+    if (accept) {
+        for (int i = lane; i < NP; i += 32) theta[(size_t)NP * b + i] = thc[i];
+        for (int i = lane; i < NT; i += 32) tfree[(size_t)NT * b + i] = tfree_c[(size_t)NT * b + i];
+    }
 }
 
 __global__ void k_gather_theta(int nb, const int32_t* __restrict__ bsrc,
@@ -1110,8 +1122,8 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                                                              (const float*)d_ce, (const float*)d_cv, d_dll,
                                                              d_srcact);
             }
-            k_tr_accept<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bpo, d_bgeo, d_dll, P.model, d_bth, d_bt,
-                                                          d_bthc, d_btc, d_st, *opts);
+            k_tr_accept<<<nb, 32, 0, st>>>(nb, d_bpo, d_bgeo, d_dll, P.model, d_bth, d_bt, d_bthc, d_btc,
+                                           d_st, *opts);
             k_mark_active<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, d_srcact);
             chk(cudaGetLastError());
             chk(cudaMemcpyAsync(h_active, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
