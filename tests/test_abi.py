@@ -42,3 +42,39 @@ def test_header_constants_match_binding():
     assert "CELESTE_FP64 = 0" in src and celeste.FP64 == 0
     assert "CELESTE_FP32_ACC64 = 1" in src and celeste.FP32 == 1
     assert "CELESTE_NPARAM = 44" in src and celeste.NPARAM == 44
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every public struct of include/celeste.h has, as compiled by the host C compiler,
+    the size and field offsets that the ctypes binding assumes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_1801_10277_gb300 import celeste
+    structs = [celeste.celeste_image, celeste.celeste_model, celeste.celeste_patch,
+               celeste.celeste_fit_options]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "celeste.h"',
+             'int main(void) {']
+    for s in structs:
+        n = s.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f in s._fields_:
+            lines.append(f'printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = {}
+    for line in out.splitlines():
+        n, field, v = line.split()
+        seen[(n, field)] = int(v)
+    for s in structs:
+        n = s.__name__
+        assert seen[(n, "size")] == ctypes.sizeof(s), n
+        for f in s._fields_:
+            assert seen[(n, f[0])] == getattr(s, f[0]).offset, (n, f[0])
