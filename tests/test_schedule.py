@@ -211,3 +211,43 @@ def test_oracle_cyclades_fit_is_serially_equivalent(crowded):
     b = orc.fit(crowded.theta, which=which, order=order, sample_size=2, max_sweeps=1)
     np.testing.assert_array_equal(a[0], b[0])
     assert a[3] == b[3]
+
+
+def _geometric_graph(n, side, radius, seed):
+    """Sources at uniform positions in a side x side box; two conflict when closer than
+    radius (the shape of a patch-overlap graph of equal-sized patches)."""
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0, side, (n, 2))
+    cell = np.floor(p / radius).astype(np.int64)
+    buckets = {}
+    for i, c in enumerate(map(tuple, cell)):
+        buckets.setdefault(c, []).append(i)
+    edges = []
+    for (cx, cy), members in buckets.items():
+        near = [j for dx in (-1, 0, 1) for dy in (-1, 0, 1) for j in buckets.get((cx + dx, cy + dy), [])]
+        for i in members:
+            for j in near:
+                if j > i and np.sum((p[i] - p[j]) ** 2) < radius * radius:
+                    edges.append((i, j))
+    return _Graph(n, edges)
+
+
+@pytest.mark.parametrize("B", [7, 256, 5000])
+def test_library_scheduler_on_a_large_random_graph(B):
+    """6,000 sources, about five conflicts each: the library's batches equal the oracle's
+    and, checked against networkx, are the connected components of each sample in rounds,
+    every batch conflict-free."""
+    from paper_1801_10277_gb300 import celeste
+    g = _geometric_graph(6000, 1000.0, 16.3, 7)
+    deg = np.diff(g.nbr_offsets)
+    assert 3.5 < deg.mean() < 6.5
+    orc = Oracle(g)
+    order = np.random.default_rng(B).permutation(g.n_src).astype(np.int32)
+    lb, lc, lnb = celeste.cyclades_batches(g.nbr_offsets, g.nbrs, order, B)
+    ob, oc, onb = orc.cyclades_batches(order, B)
+    assert lnb == onb
+    np.testing.assert_array_equal(lb, ob)
+    np.testing.assert_array_equal(lc, oc)
+    _check_schedule(g, order, B, lb, lc, lnb)
+    if B == 5000:
+        assert lnb > 5   # samples large enough for long components: several rounds
