@@ -1,0 +1,63 @@
+"""Host logic of bench.py that needs no GPU: the clock-sample summary that decides
+whether a timed run is kept, and the reference arm's JSON line (the FP64 oracle on the
+host cores)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _clocks(out):
+    import bench
+    c = bench.Clocks(0)
+    c.out = out
+    return c.summary()
+
+
+def test_clock_summary_median_max_and_reasons():
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = _clocks("\n".join(rows) + "\n")
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    hot = rows + ["0, 1500, 2070, 1400.0, 0x48, Active, Active, Not Active, Active"]
+    s = _clocks("\n".join(hot))
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples():
+    assert _clocks("")["reasons"] == ["unsampled"]
+    # a malformed line (too few fields) is not a sample
+    assert _clocks("0, 2070\n")["reasons"] == ["unsampled"]
+    # an unreadable clock field is skipped, the row still counts for its reasons
+    s = _clocks("0, [N/A], [N/A], 0, 0x0, Not Active, Not Active, Active, Not Active\n")
+    assert s["sm_mhz"] is None and s["reasons"] == ["sw_thermal_slowdown"]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` prints one JSON line whose value, e2e and
+    cpu_baseline agree, in the metric and unit of the GPU arm."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "ELBO+grad source-pixel evals/s"
+    assert d["unit"] == "source-pixel evals/s" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["dtype"] == "f64"
+    assert d["value"] > 0
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "field_500src_5x2048x1489"
+    assert d["config"]["source_pixels"] == 1001730
+    sp = d["ms_per_step"] / 1000.0 * d["value"]
+    assert 1 <= sp <= d["config"]["source_pixels"] * 1.000001
