@@ -78,3 +78,61 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert seen[(n, "size")] == ctypes.sizeof(s), n
         for f in s._fields_:
             assert seen[(n, f[0])] == getattr(s, f[0]).offset, (n, f[0])
+
+
+def _header_enums(tmp_path, names):
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ['#include <stdio.h>', '#include "celeste.h"', 'int main(void) {']
+    lines += [f'printf("{n} %lld\\n", (long long){n});' for n in names]
+    lines += ['return 0;', '}']
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "enums"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+
+
+def test_header_enums_match_binding(tmp_path):
+    """Status codes, schedules, sizes and the catalog / score column layouts: the values
+    the header's enums take when compiled equal the binding's constants and the column
+    positions of its field-name lists."""
+    from paper_1801_10277_gb300 import celeste as c
+    status = {"OK": c.OK, "ERR_ARG": c.ERR_ARG, "ERR_NOT_PD": c.ERR_NOT_PD,
+              "ERR_NONFINITE": c.ERR_NONFINITE, "ERR_CUDA": c.ERR_CUDA,
+              "ERR_TIMEOUT": c.ERR_TIMEOUT, "ERR_NOMEM": c.ERR_NOMEM,
+              "SCHED_COLOUR": c.SCHED_COLOUR, "SCHED_CYCLADES": c.SCHED_CYCLADES,
+              "NPARAM": c.NPARAM, "CAT_NFIELD": c.CAT_NFIELD,
+              "SCORE_NFIELD": len(c.SCORE_FIELDS)}
+    cat = {"CAT_U0": "u0", "CAT_U1": "u1", "CAT_PSTAR": "p_star", "CAT_IS_STAR": "is_star",
+           "CAT_RFLUX_MIX": "rflux_mix", "CAT_RFLUX_MIX_SD": "rflux_mix_sd",
+           "CAT_EDEV": "e_dev", "CAT_AXIS": "e_axis", "CAT_ANGLE_DEG": "angle_deg",
+           "CAT_SCALE": "scale"}
+    within = {"CAT_RMAG": "rmag", "CAT_RMAG_SD": "rmag_sd", "CAT_RFLUX": "rflux",
+              "CAT_RFLUX_SD": "rflux_sd", "CAT_COLOR": "color_ug", "CAT_COLOR_SD": "color_ug_sd",
+              "CAT_MAG": "mag_u", "CAT_MAG_SD": "mag_u_sd"}
+    score = {"SCORE_POSITION": "position", "SCORE_MISSED_GAL": "missed_gal",
+             "SCORE_MISSED_STAR": "missed_star", "SCORE_BRIGHTNESS": "brightness",
+             "SCORE_COLOR": "color_ug", "SCORE_PROFILE": "profile", "SCORE_AXIS": "axis",
+             "SCORE_SCALE": "scale", "SCORE_ANGLE_DEG": "angle_deg", "SCORE_N_GAL": "n_gal",
+             "SCORE_N_STAR": "n_star"}
+    names = list(status) + list(cat) + list(within) + list(score) + \
+        ["CAT_STAR", "CAT_GAL", "CAT_TYPE_NFIELD"]
+    v = _header_enums(tmp_path, ["CELESTE_" + n for n in names])
+    h = {k[len("CELESTE_"):]: x for k, x in v.items()}
+    for n, want in status.items():
+        assert h[n] == want, n
+    for n, field in cat.items():
+        assert c.CAT_FIELDS[h[n]] == field, n
+    assert c.CAT_FIELDS[h["CAT_STAR"]] == "star_rmag" and c.CAT_FIELDS[h["CAT_GAL"]] == "gal_rmag"
+    assert h["CAT_GAL"] - h["CAT_STAR"] == h["CAT_TYPE_NFIELD"]
+    for n, field in within.items():
+        assert c.CAT_FIELDS[h["CAT_STAR"] + h[n]] == "star_" + field, n
+        assert c.CAT_FIELDS[h["CAT_GAL"] + h[n]] == "gal_" + field, n
+    for n, field in score.items():
+        assert c.SCORE_FIELDS[h[n]] == field, n
