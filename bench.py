@@ -336,7 +336,15 @@ def main():
         step(cel.FP32)
     torch.cuda.synchronize()
     prof = P.profile_read()
+    # the same stages serialised on one stream: the shares a serialised launch list shows
+    P.profile(True, serial=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step(cel.FP32)
+    torch.cuda.synchronize()
+    prof_serial = P.profile_read()
     P.profile(False)
+    tot_serial = sum(v[0] for v in prof_serial.values())
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
     kernel_us = {k: 1000.0 * v[0] / max(1, v[1]) for k, v in prof.items()}
     tot_ms = sum(v[0] for v in prof.values())
@@ -364,6 +372,8 @@ def main():
                 "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
                 "kernel_us": kernel_us, "kernel_tflops": achieved_k,
                 "kernel_share": {k: v[0] / tot_ms for k, v in prof.items()},
+                "kernel_us_serialised": {k: 1000.0 * v[0] / max(1, v[1]) for k, v in prof_serial.items()},
+                "kernel_share_serialised": {k: v[0] / tot_serial for k, v in prof_serial.items()},
                 "work_split": split}
 
     # Hessian (value + gradient + per-source 44 x 44 Hessian), FP32 and FP64 pixel paths

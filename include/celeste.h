@@ -344,7 +344,13 @@ celeste_status celeste_device_status(celeste_problem* prob);
 /*
  * Per-kernel timing (tracing aid).  With profiling on, every stage launch of the
  * calls above (prep, contrib, gather, adjoint / ll_sum / hess_adjoint, finalize) is
- * bracketed by CUDA events on its launch stream.  celeste_profile_read waits for the
+ * bracketed by CUDA events on its launch stream.  on = 1: the stages run as in a
+ * normal call (the FP32 value / gradient path's fused pass and total on a second
+ * stream, concurrently with the others), so a stage's time includes waiting for SM
+ * slots that the concurrent stages hold; on = 2: every stage runs on the calling
+ * stream, one after another, so the times add up to a serialised evaluation (results
+ * identical to the concurrent order's); on = 0: off; anything else is CELESTE_ERR_ARG.
+ * celeste_profile_read waits for the
  * recorded events, writes up to max_kernels entries (names[k*32 .. k*32+31]
  * NUL-terminated, total milliseconds, launch count), resets the accumulators and
  * returns the number of distinct stages (negative status on error).

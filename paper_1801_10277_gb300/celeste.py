@@ -440,8 +440,10 @@ class Problem:
     def set_tuning(self, ppt_contrib, ppt_adjoint, fused_cap=0, gather_sep=0):
         _check(self.L.celeste_set_tuning(self.h, ppt_contrib, ppt_adjoint, fused_cap, gather_sep))
 
-    def profile(self, on=True):
-        _check(self.L.celeste_profile_enable(self.h, 1 if on else 0))
+    def profile(self, on=True, serial=False):
+        """Per-stage CUDA-event timing; serial=True runs every stage on the calling
+        stream, one after another."""
+        _check(self.L.celeste_profile_enable(self.h, (2 if serial else 1) if on else 0))
 
     def profile_read(self):
         """{stage: (total ms, launches)} since the last read."""

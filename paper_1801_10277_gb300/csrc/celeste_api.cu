@@ -190,7 +190,7 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
         // st:   prep (tables) -> map pass (other items) -> gather + adjoint (other items)
         //       -> finalize (after the fused pass)
         // side: fused pass + KL (after prep) -> total (after the gather + adjoint pass)
-        cudaStream_t sd = pr->side;
+        cudaStream_t sd = pr->profile_serial ? st : pr->side;
         CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st, false); }));
         CEL_CUDA(cudaEventRecord(pr->ev_prep, st));
         CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_prep, 0));
@@ -809,7 +809,9 @@ celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, con
 
 celeste_status celeste_profile_enable(celeste_problem* pr, int32_t on) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
+    if (on < 0 || on > 2) return fail(CELESTE_ERR_ARG, "profiling mode must be 0, 1 or 2");
     pr->profile = on != 0;
+    pr->profile_serial = on == 2;
     return CELESTE_OK;
 }
 

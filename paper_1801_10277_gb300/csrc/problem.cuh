@@ -49,6 +49,7 @@ struct celeste_problem {
     size_t scr_cap = 0;
     // per-kernel CUDA-event timing (celeste_profile_*)
     bool profile = false;
+    bool profile_serial = false;   // every stage on the calling stream, one after another
     struct Rec { std::string name; cudaEvent_t a, b; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
