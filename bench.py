@@ -133,20 +133,28 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
-def oracle_rate(prob, min_seconds=10.0, max_reps=200):
-    """FP64 CPU oracle ELBO + gradient over the whole field, repeated until
-    min_seconds of work; returns (source-pixel evals/s, cores, reps, seconds)."""
-    from oracle.oracle import Oracle, num_threads
-    orc = Oracle(prob)
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        orc.elbo(prob.theta)
-        orc.derivs(prob.theta)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    return prob.source_pixels() * reps / el, num_threads(), reps, el
+def oracle_rate(prob, min_seconds=10.0, max_reps=200, threads=None):
+    """FP64 CPU oracle ELBO + gradient over the whole of prob, repeated until
+    min_seconds of work, on all host cores or on `threads` of them; returns
+    (source-pixel evals/s, cores, reps, seconds)."""
+    from oracle.oracle import Oracle, num_threads, set_threads
+    prev = num_threads()
+    if threads:
+        set_threads(threads)
+    try:
+        cores = num_threads()
+        orc = Oracle(prob)
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            orc.elbo(prob.theta)
+            orc.derivs(prob.theta)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or reps >= max_reps:
+                break
+    finally:
+        set_threads(prev)
+    return prob.source_pixels() * reps / el, cores, reps, el
 
 
 def reference_sample(prob, steps, warmup, budget_s=120.0):
@@ -538,6 +546,12 @@ def main():
         cpu = {"value": rate, "unit": "source-pixel evals/s", "cores": cores, "kind": "oracle",
                "sample": f"whole field ({n_sp} source-pixels) ELBO + gradient x {reps} "
                          f"({secs:.1f} s)"}
+        # the same on one core, on every 10th source of the field
+        sub = synth.subset(prob, np.arange(0, prob.n_src, 10)) if prob.n_src >= 100 else prob
+        rate1, _, reps1, secs1 = oracle_rate(sub, min_seconds=5.0, threads=1)
+        cpu["one_core"] = {"value": rate1, "unit": "source-pixel evals/s", "cores": 1,
+                           "sample": f"every 10th source ({sub.source_pixels()} source-pixels) "
+                                     f"ELBO + gradient x {reps1} ({secs1:.1f} s)"}
     if rank == 0:
         line = {
             "metric": "ELBO+grad source-pixel evals/s", "value": value,

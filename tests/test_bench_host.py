@@ -61,3 +61,16 @@ def test_reference_arm_line():
     assert d["config"]["source_pixels"] == 1001730
     sp = d["ms_per_step"] / 1000.0 * d["value"]
     assert 1 <= sp <= d["config"]["source_pixels"] * 1.000001
+
+
+def test_oracle_rate_on_one_core_restores_the_thread_count():
+    import bench
+    from oracle.oracle import num_threads
+    from paper_1801_10277_gb300 import synth
+    prob = synth.config(0)
+    before = num_threads()
+    rate, cores, reps, secs = bench.oracle_rate(prob, min_seconds=0.2, threads=1)
+    assert cores == 1 and reps >= 1 and rate > 0
+    assert num_threads() == before
+    rate_all, cores_all, _, _ = bench.oracle_rate(prob, min_seconds=0.2)
+    assert cores_all == before and rate_all > 0
