@@ -36,6 +36,20 @@ SM_COUNT = 152
 # an entry is removed whenever its kernel changes after the capture.
 DRAM_BYTES_PER_LAUNCH = {"fused": 21.01e6, "gather_adjoint": 3.82e6, "contrib": 1.78e6}
 FP32_LANES = 128
+XU_LANES = 16   # MUFU ex2 results per SM per clock
+SM_MHZ_MAX = 2070.0
+
+
+def step_bound(npsf, n_exp, n_dev, value):
+    """The whole step's plain-ALU bound in source-pixel evals/s: the FP32 pipe at its
+    peak doing the fused pass's algorithmic FLOP for every source-pixel, or the ex2 unit
+    doing its exps (one per mixture component), whichever is slower; and value's
+    fraction of it."""
+    fp32 = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / fused_flops_per_source_pixel(npsf, n_exp, n_dev)
+    xu = SM_COUNT * XU_LANES * SM_MHZ_MAX * 1e6 / (npsf * (1 + n_exp + n_dev))
+    bound = min(fp32, xu)
+    return {"bound": "alu", "evals_per_s_fp32_pipe": fp32, "evals_per_s_ex2": xu,
+            "evals_per_s_bound": bound, "value": value, "frac": value / bound}
 
 
 def adjoint_flops_per_source_pixel(npsf, n_exp, n_dev):
@@ -380,6 +394,7 @@ def main():
                 "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
                 "kernel_us": kernel_us, "kernel_tflops": achieved_k,
                 "kernel_share": {k: v[0] / tot_ms for k, v in prof.items()},
+                "step": step_bound(npsf, ne, nd, value / ws),   # per GPU
                 "kernel_us_serialised": {k: 1000.0 * v[0] / max(1, v[1]) for k, v in prof_serial.items()},
                 "kernel_share_serialised": {k: v[0] / tot_serial for k, v in prof_serial.items()},
                 "work_split": split}

@@ -74,3 +74,16 @@ def test_oracle_rate_on_one_core_restores_the_thread_count():
     assert num_threads() == before
     rate_all, cores_all, _, _ = bench.oracle_rate(prob, min_seconds=0.2)
     assert cores_all == before and rate_all > 0
+
+
+def test_step_bound_of_the_one_field_model():
+    """3 PSF components x (1 star + 6 exp + 8 dev) = 45 mixture components per
+    source-pixel: the FP32 pipe at 152 SMs x 128 lanes x 2 x 2.07 GHz over the fused
+    pass's 1,541 FLOP binds before the ex2 unit at 152 x 16 x 2.07 GHz over 45 exps."""
+    import bench
+    assert bench.fused_flops_per_source_pixel(3, 6, 8) == 1541
+    b = bench.step_bound(3, 6, 8, 1.0e10)
+    assert abs(b["evals_per_s_fp32_pipe"] - 152 * 128 * 2 * 2.07e9 / 1541) < 1.0
+    assert abs(b["evals_per_s_ex2"] - 152 * 16 * 2.07e9 / 45) < 1.0
+    assert b["evals_per_s_bound"] == b["evals_per_s_fp32_pipe"]
+    assert abs(b["frac"] - 1.0e10 / b["evals_per_s_bound"]) < 1e-15
