@@ -613,3 +613,45 @@ def test_oracle_matches_its_stored_values():
     assert abs(tot - ref["elbo_total"]) <= 1e-12 * abs(ref["elbo_total"])
     assert np.allclose(loc, ref["elbo_local"], rtol=1e-12, atol=0)
     assert np.allclose(g, ref["grad"], rtol=1e-10, atol=1e-10)
+
+
+def test_brute_force_three_by_three_star():
+    """A star on 3 x 3 images with every term written out by hand: the Gaussian PSF
+    at integer pixel centres, band brightness moments from the colour definition
+    (log l_{j+1} = log l_j + c_j, walked out from the r band), E[F] and Var[F] of
+    Section III's rate, and the expected log-likelihood x (log E - Var / (2 E^2)) - E
+    summed over the pixels; the oracle's total ELBO plus its KL must equal the sum."""
+    sig, ux, uy = 0.9, 1.2, 0.9
+    th = H.star_theta(ux, uy, flux=30.0, r2=0.05, c2=0.02, a_star=1 - 1e-13)
+    th[synth.I_A], th[synth.I_A + 1] = 1 - 1e-13, 1e-13
+    p = H.problem(th, H=3, W=3, psfs=[H.psf_single(sig)] * 5, sky=150.0)
+    o = Oracle(p)
+    tot, loc = o.elbo(th[None])
+    kl = o.kl(th[None])[0]
+    r1, r2 = th[synth.I_R1], th[synth.I_R2]
+    c1 = th[synth.I_C1:synth.I_C1 + 4]
+    c2 = th[synth.I_C2:synth.I_C2 + 4]
+    # log-brightness mean and variance per band u g r i z, from r outwards
+    mean = [0.0] * 5
+    var = [0.0] * 5
+    mean[2], var[2] = r1, r2
+    for b in (1, 0):                      # l_b = l_{b+1} / exp(c_b)
+        mean[b], var[b] = mean[b + 1] - c1[b], var[b + 1] + c2[b]
+    for b in (3, 4):                      # l_b = l_{b-1} exp(c_{b-1})
+        mean[b], var[b] = mean[b - 1] + c1[b - 1], var[b - 1] + c2[b - 1]
+    iota = 1.0 / 0.005
+    a = th[synth.I_A]
+    want = 0.0
+    for im in p.images:
+        b = im.band
+        El = math.exp(mean[b] + var[b] / 2)
+        El2 = math.exp(2 * mean[b] + 2 * var[b])
+        for row in range(3):
+            for col in range(3):
+                g = math.exp(-((col - ux) ** 2 + (row - uy) ** 2) / (2 * sig * sig)) / (2 * math.pi * sig * sig)
+                E = 150.0 + a * iota * El * g
+                V = a * iota * iota * El2 * g * g - (a * iota * El * g) ** 2
+                x = float(im.pixels[row, col])
+                want += x * (math.log(E) - V / (2 * E * E)) - E
+    assert abs((tot + kl) - want) <= 1e-11 * abs(want)
+    assert abs((loc[0] + kl) - want) <= 1e-11 * abs(want)
