@@ -655,3 +655,38 @@ def test_brute_force_three_by_three_star():
                 want += x * (math.log(E) - V / (2 * E * E)) - E
     assert abs((tot + kl) - want) <= 1e-11 * abs(want)
     assert abs((loc[0] + kl) - want) <= 1e-11 * abs(want)
+
+
+def test_flux_stationarity_condition_of_an_isolated_star():
+    """With vanishing brightness variances and a certain type the ELBO is the Poisson
+    log-likelihood sum x log F - F minus the KL, so its derivative in the log flux r1
+    is sum (x / F - 1) iota E[l] g minus the KL's, and the KL's is
+    a_star (r1 - prior mean) / prior variance (Gaussian KL in the mean): the oracle's
+    gradient entry against that closed form at two fluxes."""
+    sig, ux, uy = 1.1, 6.3, 5.8
+    for flux in (25.0, 60.0):
+        th = H.star_theta(ux, uy, flux=flux, r2=1e-12, c2=1e-12, a_star=1 - 1e-13)
+        th[synth.I_A], th[synth.I_A + 1] = 1 - 1e-13, 1e-13
+        p = H.problem(th, H=13, W=13, psfs=[H.psf_single(sig)] * 5, sky=150.0, seed=4)
+        o = Oracle(p)
+        _, g, _ = o.derivs(th[None])
+        c1 = th[synth.I_C1:synth.I_C1 + 4]
+        logl = [0.0] * 5
+        logl[2] = th[synth.I_R1]
+        logl[1] = logl[2] - c1[1]
+        logl[0] = logl[1] - c1[0]
+        logl[3] = logl[2] + c1[2]
+        logl[4] = logl[3] + c1[3]
+        iota = 1.0 / 0.005
+        dll = 0.0
+        for im in p.images:
+            El = math.exp(logl[im.band])
+            for row in range(13):
+                for col in range(13):
+                    gp = math.exp(-((col - ux) ** 2 + (row - uy) ** 2) / (2 * sig * sig)) / (2 * math.pi * sig * sig)
+                    F = 150.0 + iota * El * gp
+                    dll += (float(im.pixels[row, col]) / F - 1.0) * iota * El * gp
+        mean_p, var_p = p.prior_r[0][0], p.prior_r[0][1]
+        dkl = th[synth.I_A] * (th[synth.I_R1] - mean_p) / var_p
+        want = dll - dkl
+        assert abs(g[0, synth.I_R1] - want) <= 1e-8 * max(1.0, abs(dll))
