@@ -215,11 +215,12 @@ def reference_arm(args, rank, ws):
             f"gradient evaluation per step")
     line = {
         "impl": "reference", "metric": "ELBO+grad source-pixel evals/s", "value": val,
-        "unit": "source-pixel evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": "source-pixel evals/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": prob.name, "sources": prob.n_src,
-                   "source_pixels": prob.source_pixels(), "sample": desc},
+                   "source_pixels": prob.source_pixels(), "sample": desc,
+                   "hardware": "host cores of rank 0; no GPU"},
         "cpu_baseline": {"value": val, "unit": "source-pixel evals/s", "cores": num_threads(),
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": val, "unit": "source-pixel evals/s", "h2d_bytes_per_step": 0,
@@ -279,10 +280,11 @@ def main():
     ap.add_argument("--tuning", default=None,
                     help="contrib,adjoint,fused_cap,gather_sep codes to use instead of autotuning (e.g. 2,1,0,0)")
     args = ap.parse_args()
-    rank, ws, dist = dist_init()
     if args.impl == "reference":
-        reference_arm(args, rank, ws)
+        # rank 0 alone times the oracle; no process group is needed for that
+        reference_arm(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
         return
+    rank, ws, dist = dist_init()
     import torch
     from paper_1801_10277_gb300 import celeste as cel
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

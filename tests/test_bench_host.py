@@ -87,3 +87,21 @@ def test_step_bound_of_the_one_field_model():
     assert abs(b["evals_per_s_ex2"] - 152 * 16 * 2.07e9 / 45) < 1.0
     assert b["evals_per_s_bound"] == b["evals_per_s_fp32_pipe"]
     assert abs(b["frac"] - 1.0e10 / b["evals_per_s_bound"]) < 1e-15
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the driver launches it for N > 1 (torchrun, two ranks), the reference
+    arm prints one JSON line, from rank 0, and every rank exits 0."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1", "--master-port",
+                        str(port), "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
