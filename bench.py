@@ -13,6 +13,15 @@ log-likelihood, adjoint, chain rule + KL, total), i.e. one source-pixel evaluati
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank evaluates its own field (weak scaling, no collective
 on the data path); timing is the max over ranks.
+
+Besides the step (`value`, `e2e`, `fp64_path`) the JSON line carries: `roofline` (the
+dominant pixel kernel's achieved FLOP rate against the FP32 peak derived from unit
+counts and clock, its measured DRAM bytes per launch, every stage's CUDA-event time as
+the call runs them and serialised on one stream, and `step`: the whole step against
+its plain-ALU bound); `cpu_baseline` (the FP64 oracle on all host cores and on one);
+`hessian`, `fit`, `fit_schedules`, `catalog` and `tasks` legs; `clocks` sampled during
+the timed region; `gpu_launches`.  `--impl reference` times the oracle instead (rank 0
+only) on a bounded sample of the same field.
 """
 import argparse
 import json
