@@ -40,49 +40,49 @@ from paper_1801_10277_gb300 import synth  # noqa: E402
 
 FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
-# DRAM bytes (read + write) per launch of each pixel kernel on the one-field workload, from
-# one ncu capture (profiles/k_fused_x2_field_500src.md, profiles/step_kernels_field_500src.md);
-# an entry is removed whenever its kernel changes after the capture.
-DRAM_BYTES_PER_LAUNCH = {"fused": 21.01e6, "gather_adjoint": 3.82e6, "contrib": 1.78e6}
+# DRAM bytes (read + write) per launch of the item kernel on the one-field workload, from one
+# ncu capture (profiles/); emptied whenever the kernel changes after the capture.
+DRAM_BYTES_PER_LAUNCH = {}
 FP32_LANES = 128
 XU_LANES = 16   # MUFU ex2 results per SM per clock
 SM_MHZ_MAX = 2070.0
 
 
-def step_bound(npsf, n_exp, n_dev, value):
+def step_bound(npsf, n_exp, n_dev, value, other_per_sp=0.0):
     """The whole step's plain-ALU bound in source-pixel evals/s: the FP32 pipe at its
-    peak doing the fused pass's algorithmic FLOP for every source-pixel, or the ex2 unit
-    doing its exps (one per mixture component), whichever is slower; and value's
+    peak doing the item kernel's algorithmic FLOP for every source-pixel (and the other
+    sources' values at multiply covered pixels, other_per_sp per source-pixel), or the
+    ex2 unit doing its exps (one per mixture component), whichever is slower; and value's
     fraction of it."""
-    fp32 = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / fused_flops_per_source_pixel(npsf, n_exp, n_dev)
-    xu = SM_COUNT * XU_LANES * SM_MHZ_MAX * 1e6 / (npsf * (1 + n_exp + n_dev))
+    per_sp = items_flops_per_source_pixel(npsf, n_exp, n_dev) + other_per_sp * other_eval_flops(npsf, n_exp, n_dev)
+    fp32 = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / per_sp
+    xu = SM_COUNT * XU_LANES * SM_MHZ_MAX * 1e6 / (npsf * (1 + n_exp + n_dev) * (1 + other_per_sp))
     bound = min(fp32, xu)
     return {"bound": "alu", "evals_per_s_fp32_pipe": fp32, "evals_per_s_ex2": xu,
-            "evals_per_s_bound": bound, "value": value, "frac": value / bound}
+            "evals_per_s_bound": bound, "value": value, "frac": value / bound,
+            "flop_per_source_pixel": per_sp}
 
 
-def adjoint_flops_per_source_pixel(npsf, n_exp, n_dev):
-    """Algorithmic FP32 operations (FMA = 2) of the adjoint per source-pixel, counted from
-    the formulas it evaluates: per PSF component the offset and its products (5), the
-    star component (exponent 6, weight 1, P d 6, three sums 5) and each galaxy
-    component (exponent 6, weight 1, P d 6, sums g/gx/gy 5, e_dev 2, nu weight 1, three
-    covariance sums 12); per pixel the likelihood weights and the 12 y-gradients (55)."""
+def items_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """Algorithmic FP32 operations (FMA = 2) of the item kernel per source-pixel of the
+    item's own patch (value + gradient), counted from the formulas it evaluates in the
+    frame whitening each PSF component: per PSF component the offset, whitened
+    coordinates and their squares (11), the star component (exponent 2, value 2, mean
+    derivative 11), each galaxy component (exponent 4, value 1, the two mean and three
+    shape sums 14) and the map back through T (41); per pixel the profile value and
+    e_dev derivative (4), E_s and Var_s (27), E (1), the likelihood (8), its two weights
+    (9) and the 12 y-gradients (65)."""
     nprof = n_exp + n_dev
-    return npsf * (5 + 18 + nprof * 33) + 55
+    return npsf * (67 + 19 * nprof) + 114
 
 
-def contrib_flops_per_source_pixel(npsf, n_exp, n_dev):
-    """The map pass per source-pixel: offsets and products (5), star component (exponent 6,
-    weighted sum 2), each galaxy component (exponent 6, weighted sum 2); per pixel E_s,
-    Var_s (30)."""
+def other_eval_flops(npsf, n_exp, n_dev):
+    """FP32 operations of one other covering source's E and Var at a multiply covered
+    pixel: per PSF component the coordinates (11), star exponent and value (4), each
+    galaxy component's exponent and value (5), the component's sums (6); then the profile
+    value (3), E_s and Var_s (27) and the two additions (2)."""
     nprof = n_exp + n_dev
-    return npsf * (5 + 8 + nprof * 8) + 30
-
-
-def fused_flops_per_source_pixel(npsf, n_exp, n_dev):
-    """The fused map + adjoint pass: the adjoint's work plus, per pixel, E = sky + E_s and
-    Var_s (16), the likelihood (8) and its two weights (7)."""
-    return adjoint_flops_per_source_pixel(npsf, n_exp, n_dev) + 31
+    return npsf * (21 + 5 * nprof) + 32
 
 
 class Clocks:
@@ -92,12 +92,24 @@ class Clocks:
         self.idx = idx
         self.p = None
 
-    def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def once(self):
+        """One sample, taken immediately (a short timed region may end between the
+        periodic samples)."""
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+            r = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            return r.stdout if r.returncode == 0 else ""
+        except Exception:
+            return ""
+
+    def __enter__(self):
+        self.first = self.once()
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
@@ -112,6 +124,7 @@ class Clocks:
                 self.out, _ = self.p.communicate(timeout=5)
             except Exception:
                 self.p.kill()
+        self.out = (self.first or "") + (self.out or "") + self.once()
 
     def summary(self):
         rows = []
@@ -287,7 +300,7 @@ def main():
                          "4 sweep field, 5 deep stack (480 images per source), 6 the whole 200,000-source "
                          "sweep (64 fields); the JSON line names it")
     ap.add_argument("--tuning", default=None,
-                    help="contrib,adjoint,fused_cap,gather_sep codes to use instead of autotuning (e.g. 2,1,0,0)")
+                    help="contrib,items codes to use instead of autotuning (e.g. 2,3)")
     args = ap.parse_args()
     if args.impl == "reference":
         # rank 0 alone times the oracle; no process group is needed for that
@@ -384,28 +397,25 @@ def main():
     npsf = prob.images[0].psf.shape[0]
     ne, nd = prob.exp_mix.shape[0], prob.dev_mix.shape[0]
     split = P.stats()
-    sp_fused = split["fused_source_pixels"] if "fused" in prof else 0
-    rest = n_sp - sp_fused
-    work = {   # algorithmic FP32 FLOP per launch of each pixel kernel (stage names)
-        "fused": fused_flops_per_source_pixel(npsf, ne, nd) * sp_fused,
-        "gather_adjoint": adjoint_flops_per_source_pixel(npsf, ne, nd) * rest,
-        "adjoint": adjoint_flops_per_source_pixel(npsf, ne, nd) * rest,
-        "contrib": contrib_flops_per_source_pixel(npsf, ne, nd) * rest,
-    }
-    achieved_k = {k: work[k] / (kernel_us[k] * 1e-6) / 1e12
-                  for k in work if kernel_us.get(k, 0) > 0 and work[k] > 0}
-    dom = max(achieved_k, key=lambda k: prof[k][0])     # the pixel kernel with the most time
+    # algorithmic FP32 FLOP of one launch of the item kernel: every source-pixel of its own
+    # patch, plus the other covering sources' E and Var at multiply covered pixels
+    work = {"items": items_flops_per_source_pixel(npsf, ne, nd) * n_sp
+                     + other_eval_flops(npsf, ne, nd) * split["other_evals"]}
+    achieved_k = {k: work[k] / (kernel_us[k] * 1e-6) / 1e12 for k in work if kernel_us.get(k, 0) > 0}
+    dom = "items"
     clocks = clk.summary()
     peak_fp32 = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
     achieved = achieved_k[dom]
     traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if args.workload == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32, "traffic": traffic, "kernel": f"{dom} (FP32)",
+                "frac": achieved / peak_fp32, "traffic": traffic, "kernel": "items (FP32 value + gradient)",
                 "flop_per_launch": work[dom],
+                "flop_per_source_pixel": items_flops_per_source_pixel(npsf, ne, nd),
+                "other_evals": split["other_evals"], "flop_per_other_eval": other_eval_flops(npsf, ne, nd),
                 "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
                 "kernel_us": kernel_us, "kernel_tflops": achieved_k,
                 "kernel_share": {k: v[0] / tot_ms for k, v in prof.items()},
-                "step": step_bound(npsf, ne, nd, value / ws),   # per GPU
+                "step": step_bound(npsf, ne, nd, value / ws, split["other_evals"] / n_sp),   # per GPU
                 "kernel_us_serialised": {k: 1000.0 * v[0] / max(1, v[1]) for k, v in prof_serial.items()},
                 "kernel_share_serialised": {k: v[0] / tot_serial for k, v in prof_serial.items()},
                 "work_split": split}
@@ -589,7 +599,7 @@ def main():
                        "image": "x".join(str(v) for v in prob.images[0].pixels.shape[::-1]),
                        "precision": "fp32 pixels, fp64 accumulation",
                        "l2": "flushed between steps (256 MiB write)",
-                       "tuning": dict(zip(("contrib", "adjoint", "fused_cap", "gather_sep"), tuning)),
+                       "tuning": dict(zip(("contrib", "items"), tuning)),
                        "parallelism": f"replica{ws}" if ws > 1 else "single"},
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
                           "speedup_fp32_over_fp64": value / value64},

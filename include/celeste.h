@@ -146,10 +146,12 @@ int64_t celeste_source_pixels(const celeste_problem* prob);
  * Work decomposition of a problem (host read, no GPU work), for cost accounting:
  * out[0] sources, [1] patches, [2] work items (<= 256 pixels of one patch each),
  * [3] work items of singly covered pixels in the FP32 value / gradient path (each patch's
- * pixels that no other patch covers, in items of <= 256; they take the fused map +
- * adjoint pass), [4] singly covered source-pixels, [5] 16 x 16 tiles covered by two or
- * more patches (the gather's cells), [6] source-pixels in all.  Writes min(n, 7) entries;
- * returns the number written, or CELESTE_ERR_ARG for a null problem / out.
+ * pixels that no other patch covers, in items of <= 1024), [4] singly covered
+ * source-pixels, [5] 16 x 16 tiles covered by two or more patches (the gather's cells),
+ * [6] source-pixels in all, [7] (source-pixel, other covering patch) pairs: the other
+ * sources' E and Var the FP32 value / gradient path evaluates at multiply covered pixels.
+ * Writes min(n, 8) entries; returns the number written, or CELESTE_ERR_ARG for a null
+ * problem / out.
  */
 int32_t celeste_problem_stats(const celeste_problem* prob, int64_t* out, int32_t n);
 
@@ -313,29 +315,22 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
                                    double* d_elbo_per_source, double* d_grad, void* stream);
 
 /*
- * Autotuner: times the FP32 contrib and adjoint kernels of this problem with 1, 2 and 4
- * pixels per thread (CTAs of 256, 128, 64 threads over the same 256-pixel work items)
- * and with two or four pixels per thread in packed FP32x2 instructions (codes 3, 5;
- * codes 6, 7: the same as persistent CTAs taking items from a work queue, with the
- * next item's table prefetched by bulk asynchronous copy), reps launches each with CUDA
- * events on the problem's stream, at theta (host).  The adjoint's code also picks the
- * pair count of the fused map + adjoint pass (four pixels per thread for codes 5, 7).
- * Then, with those kernels, it times whole FP32 value + gradient evaluations (through the
- * captured CUDA graph the calls replay, whose nodes keep the critical chain's high and the
- * fused pass's low stream priority) for the
- * schedule of the multiply covered pixels (gather_sep 0: each covering patch's adjoint
- * gathers E and Var itself; 1: one tile-major gather, then the adjoint from the maps --
- * better when many patches overlap) and for caps of 0 (none), 8, 7, .., 3 resident CTAs
- * per SM on the fused pass, which runs beside that chain and must leave it room.  The
- * choices are kept for later FP32 calls and returned (nullable outputs);
- * celeste_set_tuning restores them (codes 1 .. 7, 0 = built-in default 2; cap 0 .. 8;
- * gather_sep 0 or 1; anything else is CELESTE_ERR_ARG).
+ * Autotuner, at theta (host), with CUDA events on the problem's stream.
+ *   contrib_code: the FP32 map-pass kernel of the Hessian and fit paths, timed over reps
+ *     launches: 1, 2, 4 pixels per thread (CTAs of 256, 128, 64 threads over the same
+ *     256-pixel work items), 3, 5 two or four pixels per thread in packed FP32x2
+ *     instructions, 6, 7 the same as persistent CTAs taking items from a work queue.
+ *   items_code: the register budget of the FP32 value / gradient item kernel (codes
+ *     1 .. 5: at most 128, 96, 80, 72, 64 registers per thread, i.e. 4 .. 8 CTAs of 128
+ *     threads per SM), timed on whole FP32 value + gradient evaluations as the calls run
+ *     them (the captured CUDA graph).
+ * The choices are kept for later FP32 calls and returned (nullable outputs);
+ * celeste_set_tuning restores them (contrib 0 .. 7, items 0 .. 5; 0 = the built-in
+ * defaults 2 and 3; anything else is CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap,
-                                int32_t* gather_sep);
-celeste_status celeste_set_tuning(celeste_problem* prob, int32_t ppt_contrib, int32_t ppt_adjoint,
-                                  int32_t fused_cap, int32_t gather_sep);
+                                int32_t* contrib_code, int32_t* items_code);
+celeste_status celeste_set_tuning(celeste_problem* prob, int32_t contrib_code, int32_t items_code);
 
 /* Status word written by the device-side checks of the last _device call (host read;
  * synchronises the problem's last stream).  CELESTE_OK or a negative status. */

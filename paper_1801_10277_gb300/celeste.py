@@ -130,9 +130,9 @@ def load(build_if_missing=False):
         getattr(L, f).restype = i32
     L.celeste_grad_device.argtypes = [vp, vp, i32, vp, vp, vp]
     L.celeste_grad_device.restype = i32
-    L.celeste_autotune.argtypes = [vp, vp, i32, vp, vp, vp, vp]
+    L.celeste_autotune.argtypes = [vp, vp, i32, vp, vp]
     L.celeste_autotune.restype = i32
-    L.celeste_set_tuning.argtypes = [vp, i32, i32, i32, i32]
+    L.celeste_set_tuning.argtypes = [vp, i32, i32]
     L.celeste_set_tuning.restype = i32
     L.celeste_cyclades_batches.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp, vp]
     L.celeste_cyclades_batches.restype = i32
@@ -284,11 +284,11 @@ class Problem:
         return int(self.L.celeste_source_pixels(self.h))
 
     STAT_KEYS = ("sources", "patches", "items", "fused_items", "fused_source_pixels", "tiles",
-                 "source_pixels")
+                 "source_pixels", "other_evals")
 
     def stats(self):
         """Work decomposition: {sources, patches, items, fused_items, fused_source_pixels,
-        tiles, source_pixels}."""
+        tiles, source_pixels, other_evals}."""
         out = np.zeros(len(self.STAT_KEYS), np.int64)
         n = self.L.celeste_problem_stats(self.h, _p(out), len(out))
         if n < 0:
@@ -429,16 +429,15 @@ class Problem:
                                           self._dp(d_grad), self._dp(d_hess), self._stream()))
 
     def autotune(self, theta, reps=5):
-        """Pick the fastest FP32 kernel variants and schedule; returns (contrib code,
-        adjoint code, fused-pass CTA cap, gather_sep)."""
+        """Pick the fastest FP32 kernel variants; returns (contrib code, items code)."""
         self.generation += 1
-        out = [C.c_int32() for _ in range(4)]
+        out = [C.c_int32() for _ in range(2)]
         _check(self.L.celeste_autotune(self.h, _p(self._theta(theta)), reps,
                                        *(C.byref(o) for o in out)))
         return tuple(o.value for o in out)
 
-    def set_tuning(self, ppt_contrib, ppt_adjoint, fused_cap=0, gather_sep=0):
-        _check(self.L.celeste_set_tuning(self.h, ppt_contrib, ppt_adjoint, fused_cap, gather_sep))
+    def set_tuning(self, contrib_code, items_code=0):
+        _check(self.L.celeste_set_tuning(self.h, contrib_code, items_code))
 
     def profile(self, on=True, serial=False):
         """Per-stage CUDA-event timing; serial=True runs every stage on the calling

@@ -187,33 +187,9 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     // interleave.
     const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.sitems;
     if (fused) {
-        // st:   prep (tables) -> map pass (other items) -> gather + adjoint (other items)
-        //       -> finalize (after the fused pass)
-        // side: fused pass + KL (after prep) -> total (after the gather + adjoint pass)
-        cudaStream_t sd = pr->profile_serial ? st : pr->side;
-        CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st, false); }));
-        CEL_CUDA(cudaEventRecord(pr->ev_prep, st));
-        CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_prep, 0));
-        CEL_CUDA(timed(pr, "fused", sd, [&] { return launch_fused(P, mode, sd, d_theta); }));
-        CEL_CUDA(cudaEventRecord(pr->ev_fused, sd));
-        CEL_CUDA(timed(pr, "contrib", st, [&] { return launch_contrib_split(P, st); }));
-        if (P.gather_sep) {
-            CEL_CUDA(timed(pr, "gather", st, [&] { return launch_gather(P, precision, st); }));
-            CEL_CUDA(timed(pr, mode == MODE_LL ? "ll_sum" : "adjoint", st,
-                           [&] { return launch_adjoint_mixed_maps(P, mode, st); }));
-        } else {
-            CEL_CUDA(timed(pr, mode == MODE_LL ? "gather_ll" : "gather_adjoint", st,
-                           [&] { return launch_gather_adjoint(P, mode, st); }));
-        }
-        if (d_total) {
-            CEL_CUDA(cudaEventRecord(pr->ev_gather, st));
-            CEL_CUDA(cudaStreamWaitEvent(sd, pr->ev_gather, 0));
-            CEL_CUDA(timed(pr, "total", sd, [&] { return launch_total_items(P, d_total, sd); }));
-        }
-        CEL_CUDA(cudaEventRecord(pr->ev_join, sd));
-        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_fused, 0));
-        CEL_CUDA(timed(pr, "finalize", st, [&] { return launch_finalize_split(P, mode, d_local, d_grad, st); }));
-        CEL_CUDA(cudaStreamWaitEvent(st, pr->ev_join, 0));
+        // tables -> items (+ KL) -> per-source epilogue and total; each a programmatic
+        // dependent launch of its predecessor
+        CEL_CUDA(timed(pr, "items", st, [&] { return launch_items(P, mode, st, d_theta, d_local, d_grad, d_total); }));
         return CELESTE_OK;
     }
     CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
@@ -249,7 +225,7 @@ celeste_status run_cached(celeste_problem* pr, const double* d_theta, int precis
         if (reset_status) CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
         return run(pr, d_theta, precision, mode, d_total, d_local, d_grad, d_hess, st);
     }
-    celeste_problem::GraphKey key{precision, mode, P.tune_contrib, P.tune_adjoint, P.fused_cap | (P.gather_sep << 8),
+    celeste_problem::GraphKey key{precision, mode, P.tune_contrib, P.tune_adjoint, P.tune_items,
                                   {d_theta, d_total, d_local, d_grad, d_hess}};
     if (!reset_status) key.mode |= 0x100;
     cudaGraphExec_t exec = nullptr;
@@ -328,8 +304,9 @@ int64_t celeste_source_pixels(const celeste_problem* pr) { return pr ? pr->P.n_s
 int32_t celeste_problem_stats(const celeste_problem* pr, int64_t* out, int32_t n) {
     if (!pr || !out) return fail(CELESTE_ERR_ARG, "null problem or output");
     const DevProblem& P = pr->P;
-    const int64_t v[7] = {P.n_src, P.n_patch, P.n_item, P.n_ssingle, pr->sp_single, P.n_tile, P.n_sp};
-    const int m = n < 7 ? (n > 0 ? n : 0) : 7;
+    const int64_t v[8] = {P.n_src, P.n_patch, P.n_item, (int64_t)P.n_sitem - P.n_smulti, pr->sp_single, P.n_tile, P.n_sp,
+                          pr->other_evals};
+    const int m = n < 8 ? (n > 0 ? n : 0) : 8;
     for (int i = 0; i < m; ++i) out[i] = v[i];
     return m;
 }
@@ -466,6 +443,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
             const ImgMeta& M = im[c.image];
             if (c.w <= 0 || c.h <= 0 || c.x0 < 0 || c.y0 < 0 || c.x0 + c.w > M.W || c.y0 + c.h > M.H)
                 return fail(CELESTE_ERR_ARG, "patch %d lies outside image %d", p, c.image);
+            if (c.w > 32767 || c.h > 32767)
+                return fail(CELESTE_ERR_ARG, "patch %d: sides above 32767 pixels are not supported", p);
             PatchGeo& g = geo[p];
             g.img = c.image; g.x0 = c.x0; g.y0 = c.y0; g.w = c.w; g.h = c.h; g.src = s;
             g.sp_off = n_sp;
@@ -502,7 +481,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     // the split item set: per source, per patch, the singly covered pixels (fused pass,
     // items of <= FUSED_CHUNK pixels) then the multiply covered ones (items of <= CHUNK)
     std::vector<WorkItem> sitems;
-    std::vector<int32_t> spix, sitem_off(1, 0), sidx_single, sidx_multi;
+    std::vector<int32_t> spix, sitem_off(1, 0), spatch_off(1, 0);
+    int n_smulti = 0;
     spix.reserve((size_t)n_sp);
     int64_t sp_single = 0;
     for (int s = 0; s < n_src; ++s) {
@@ -512,15 +492,16 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
             for (int pass = 0; pass < 2; ++pass) {
                 const int first = (int)spix.size();
                 for (int q = 0; q < g.w * g.h; ++q)
-                    if ((f[q] != 0) == (pass == 0)) spix.push_back(q);
+                    if ((f[q] != 0) == (pass == 0)) spix.push_back(((q / g.w) << 16) | (q % g.w));
                 const int cnt = (int)spix.size() - first;
                 const int ch = pass == 0 ? FUSED_CHUNK : CHUNK;
                 for (int o = 0; o < cnt; o += ch) {
-                    (pass == 0 ? sidx_single : sidx_multi).push_back((int32_t)sitems.size());
                     sitems.push_back({p, first + o, std::min(ch, cnt - o), s});
+                    if (pass == 1) ++n_smulti;
                 }
                 if (pass == 0) sp_single += cnt;
             }
+            spatch_off.push_back((int32_t)sitems.size());
         }
         sitem_off.push_back((int32_t)sitems.size());
     }
@@ -556,6 +537,81 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
                     tiles.push_back(t);
                 }
         }
+    }
+    // the item kernel's lists: per split item the other patches covering any of its pixels
+    // (ascending patch id = ascending source id within an image), and the launch order
+    // (items with other covering patches first, most covering patches first)
+    std::vector<int32_t> zc_off(1, 0), zc_list, zorder;
+    int64_t other_evals = 0;   // (pixel, other covering patch) pairs the item kernel evaluates
+    {
+        std::vector<int32_t> cand;
+        for (size_t i = 0; i < sitems.size(); ++i) {
+            const WorkItem& it = sitems[i];
+            const PatchGeo& g = geo[it.patch];
+            const ImgMeta& M = im[g.img];
+            cand.clear();
+            for (int l = 0; l < it.n; ++l) {
+                const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
+                if (single[(size_t)g.sp_off + (size_t)yy * g.w + xx]) continue;
+                const int gx = g.x0 + xx, gy = g.y0 + yy;
+                const int tid = tile_grid[M.tg_off + (size_t)(gy / TILE) * M.tgw + gx / TILE];
+                if (tid < 0) continue;
+                const Tile& tl = tiles[tid];
+                for (int e = 0; e < tl.list_n; ++e) {
+                    const int pe = tile_list[tl.list_off + e];
+                    if (pe == it.patch) continue;
+                    const PatchGeo& G = geo[pe];
+                    if (gx >= G.x0 && gx < G.x0 + G.w && gy >= G.y0 && gy < G.y0 + G.h) {
+                        cand.push_back(pe);
+                        ++other_evals;
+                    }
+                }
+            }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            zc_list.insert(zc_list.end(), cand.begin(), cand.end());
+            zc_off.push_back((int32_t)zc_list.size());
+        }
+        // the most expensive items first (pixels, each other covering patch adding about a
+        // third of a pixel's cost), so the last CTAs to start are short ones
+        auto cost = [&](int32_t i) { return (double)sitems[i].n * (1.0 + 0.35 * (zc_off[i + 1] - zc_off[i])); };
+        for (size_t i = 0; i < sitems.size(); ++i) zorder.push_back((int32_t)i);
+        std::stable_sort(zorder.begin(), zorder.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+    }
+    // flat item records in launch order, candidate records, and the items' pixels gathered
+    // in item order (counts and sky), so that an item needs one record load before its data
+    std::vector<ZItem> zitems;
+    std::vector<ZCand> zcands;
+    std::vector<float2> zxs(spix.size());
+    for (size_t j = 0, i = 0; i < sitems.size(); ++i) {
+        const WorkItem& it = sitems[i];
+        const PatchGeo& g = geo[it.patch];
+        const ImgMeta& M = im[g.img];
+        const float* px = imgs[g.img].pixels;
+        const float* sm = imgs[g.img].sky_map;
+        for (int l = 0; l < it.n; ++l, ++j) {
+            const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
+            const size_t m = (size_t)(g.y0 + yy) * M.W + (g.x0 + xx);
+            zxs[it.q0 + l] = make_float2(px[m], sm ? sm[m] : (float)M.sky);
+        }
+    }
+    for (const int32_t i : zorder) {
+        const WorkItem& it = sitems[i];
+        const PatchGeo& g = geo[it.patch];
+        ZItem z{};
+        z.patch = it.patch;
+        z.n = it.n;
+        z.out = i;
+        z.src = g.src;
+        z.pix = it.q0;
+        z.c0 = (int32_t)zcands.size();
+        const int nc = zc_off[i + 1] - zc_off[i];
+        z.nc_npsf = nc | (im[g.img].npsf << 24);
+        for (int e = zc_off[i]; e < zc_off[i + 1]; ++e) {
+            const PatchGeo& G = geo[zc_list[e]];
+            zcands.push_back(ZCand{zc_list[e], G.x0 - g.x0, G.y0 - g.y0, G.w, G.h, G.src, im[G.img].npsf, 0});
+        }
+        zitems.push_back(z);
     }
     // neighbours
     if (nbr_offsets[0] != 0) return fail(CELESTE_ERR_ARG, "nbr_offsets[0] must be 0");
@@ -622,6 +678,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     DevProblem& P = pr->P;
     P.n_img = n_img; P.n_src = n_src; P.n_patch = n_patch; P.n_item = (int)items.size();
     P.n_tile = (int)tiles.size(); P.npsf_max = npsf_max; P.nprof = model->n_exp + model->n_dev;
+    P.model_npe = (model->n_exp + 1) / 2;
+    P.model_npd = (model->n_dev + 1) / 2;
     P.n_px = n_px; P.n_sp = n_sp;
     P.max_src_patches = 0;
     for (int s = 0; s < n_src; ++s)
@@ -659,20 +717,38 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     P.single = d_single;
     if (!sitems.empty()) {
         WorkItem* d_sit = nullptr;
-        int32_t *d_spix = nullptr, *d_soff = nullptr, *d_ss = nullptr, *d_sm = nullptr;
+        int32_t *d_spix = nullptr, *d_soff = nullptr, *d_spo = nullptr;
         if ((st = dupload(pr, &d_sit, sitems.data(), sitems.size()))) return bail(st);
         if ((st = dupload(pr, &d_spix, spix.data(), spix.size()))) return bail(st);
         if ((st = dupload(pr, &d_soff, sitem_off.data(), sitem_off.size()))) return bail(st);
-        if ((st = dupload(pr, &d_ss, sidx_single.data(), sidx_single.size()))) return bail(st);
-        if ((st = dupload(pr, &d_sm, sidx_multi.data(), sidx_multi.size()))) return bail(st);
-        P.sitems = d_sit; P.spix = d_spix; P.sitem_off = d_soff;
-        P.sidx_single = d_ss; P.sidx_multi = d_sm;
+        if ((st = dupload(pr, &d_spo, spatch_off.data(), spatch_off.size()))) return bail(st);
+        P.sitems = d_sit; P.spix = d_spix; P.sitem_off = d_soff; P.spatch_off = d_spo;
+        ZItem* d_zi = nullptr;
+        ZCand* d_zc = nullptr;
+        float2* d_zxs = nullptr;
+        if ((st = dupload(pr, &d_zi, zitems.data(), zitems.size()))) return bail(st);
+        if ((st = dupload(pr, &d_zc, zcands.data(), zcands.size()))) return bail(st);
+        if ((st = dupload(pr, &d_zxs, zxs.data(), zxs.size()))) return bail(st);
+        P.zitems = d_zi; P.zcands = d_zc; P.zxy = d_spix; P.zxs = d_zxs;
         P.n_sitem = (int)sitems.size();
-        P.n_ssingle = (int)sidx_single.size();
-        P.n_smulti = (int)sidx_multi.size();
+        P.n_smulti = n_smulti;
         void* q;
-        if ((st = dalloc(pr, &q, sizeof(double) * NPART * (size_t)P.n_sitem))) return bail(st);
+        if ((st = dalloc(pr, &q, sizeof(double) * NZPART * (size_t)P.n_sitem))) return bail(st);
         P.spart = (double*)q;
+        const int n_grp = (n_src + ZF_GROUP - 1) / ZF_GROUP;
+        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)n_grp))) return bail(st);
+        P.zf_grp_total = (double*)q;
+        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_grp + 1)))) return bail(st);
+        P.zf_done = (int32_t*)q;
+        if (cudaMemset(P.zf_done, 0, sizeof(int32_t) * ((size_t)n_grp + 1)) != cudaSuccess)
+            return bail(fail(CELESTE_ERR_CUDA, "memset"));
+        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_src + 1)))) return bail(st);
+        P.zsrc_done = (int32_t*)q;
+        if (cudaMemset(P.zsrc_done, 0, sizeof(int32_t) * ((size_t)n_src + 1)) != cudaSuccess)
+            return bail(fail(CELESTE_ERR_CUDA, "memset"));
+        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_patch + 1)))) return bail(st);
+        P.zready = (int32_t*)q;
+
         if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
         P.sitem_ll = (double*)q;
         if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
@@ -682,6 +758,7 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
             return bail(fail(CELESTE_ERR_CUDA, "memset"));
     }
     pr->sp_single = sp_single;
+    pr->other_evals = other_evals;
     if ((st = dupload(pr, &d_po, patch_offsets, (size_t)n_src + 1))) return bail(st);
     if ((st = dupload(pr, &d_md, &md, 1))) return bail(st);
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
@@ -692,6 +769,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     P.tbl64 = (double*)p;
     if ((st = dalloc(pr, &p, sizeof(float) * TBL_STRIDE * (size_t)n_patch))) return bail(st);
     P.tbl32 = (float*)p;
+    if ((st = dalloc(pr, &p, sizeof(float) * ZFULL_FLOATS * (size_t)n_patch))) return bail(st);
+    P.ztbl = (float*)p;
     if ((st = dalloc(pr, &P.spE, sizeof(double) * (size_t)n_sp))) return bail(st);
     if ((st = dalloc(pr, &P.spE2, sizeof(double) * (size_t)n_sp))) return bail(st);
     if ((st = dalloc(pr, &P.emap, sizeof(double) * (size_t)n_px))) return bail(st);
@@ -720,7 +799,6 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     if ((st = dalloc(pr, &p, 2 * sizeof(int32_t)))) return bail(st);
     P.queue = (int32_t*)p;
     prime_persistent_grids();
-    prime_fused_caps();
     if (cudaMemset(P.queue, 0, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.status = (int32_t*)p;
@@ -861,17 +939,15 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     pr->last_stream = st;
     const DevProblem& P = pr->P;
     CEL_CUDA(cudaMemsetAsync(P.status, 0, sizeof(int32_t), st));
-    // the mixture tables and the E / Var maps of the preceding celeste_elbo_device call
-    // are reused; the mixture terms themselves are recomputed by the adjoint.  In FP32 the
-    // same kernels as celeste_elbo_grad run (the fused pass over the singly covered items,
-    // whose maps it rewrites with the same values, and the adjoint over the others), so
-    // the gradient is bit-identical to the one-call gradient.
+    // FP64: the mixture tables and the E / Var maps of the preceding celeste_elbo_device
+    // call are reused; the mixture terms themselves are recomputed by the adjoint.  FP32:
+    // the item kernel of celeste_elbo_grad runs again (it recomputes its tables, E and Var
+    // from theta; the KL of the preceding forward call is reused), so the gradient is
+    // bit-identical to the one-call gradient.
     const bool fused = precision == CELESTE_FP32_ACC64 && P.sitems;
     if (fused) {
-        CEL_CUDA(timed(pr, "fused", st, [&] { return launch_fused(P, MODE_GRAD, st); }));
-        CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint_mixed_maps(P, MODE_GRAD, st); }));
-        CEL_CUDA(timed(pr, "finalize", st, [&] {
-            return launch_finalize_split(P, MODE_GRAD, d_elbo_per_source, d_grad, st);
+        CEL_CUDA(timed(pr, "items", st, [&] {
+            return launch_items(P, MODE_GRAD, st, d_theta, d_elbo_per_source, d_grad, nullptr);
         }));
         return CELESTE_OK;
     }
@@ -884,8 +960,7 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
 }
 
 celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_t reps,
-                                int32_t* ppt_contrib, int32_t* ppt_adjoint, int32_t* fused_cap,
-                                int32_t* gather_sep) {
+                                int32_t* contrib_code, int32_t* items_code) {
     if (!pr || !theta) return fail(CELESTE_ERR_ARG, "null problem or theta");
     celeste_status s = check_theta_host(theta, pr->P.n_src);
     if (s) return s;
@@ -893,70 +968,41 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     CEL_CUDA(cudaSetDevice(pr->device));
     cudaStream_t st = pr->stream;
     DevProblem& P = pr->P;
+    s = ensure_out(pr);
+    if (s) return s;
     CEL_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * P.n_src,
                              cudaMemcpyHostToDevice, st));
     CEL_CUDA(launch_prep(P, pr->d_theta, CELESTE_FP32_ACC64, st));
     cudaEvent_t a, b;
     CEL_CUDA(cudaEventCreate(&a));
     CEL_CUDA(cudaEventCreate(&b));
-    // 1, 2, 4 pixels per thread; 3, 5: two and four pixels per thread in packed FP32x2;
-    // 6, 7: the packed kernels as persistent CTAs on a work queue
-    const int cands[7] = {1, 2, 4, 3, 5, 6, 7};
-    float best_c = 1e30f, best_a = 1e30f;
-    int pick_c = 2, pick_a = 2;
     cudaError_t e = cudaSuccess;
-    // with the fused pass (FP32 value + gradient) contrib runs over the mixed items and
-    // the adjoint stage is the fused kernel plus the adjoint over the mixed items
-    // (the split item set's kernels follow the adjoint code's pair count)
-    const bool fused = P.sitems != nullptr;
-    const int32_t* rest = nullptr;
-    const int n_rest = -1;
-    auto adjoint_stage = [&]() {
-        if (!fused) return launch_adjoint(P, CELESTE_FP32_ACC64, MODE_GRAD, st);
-        cudaError_t r = launch_fused(P, MODE_GRAD, st);
-        if (r == cudaSuccess) r = launch_contrib_split(P, st);
-        if (r == cudaSuccess) r = launch_gather_adjoint(P, MODE_GRAD, st);
-        return r;
-    };
+    // the FP32 map pass of the Hessian and fit paths: 1, 2, 4 pixels per thread; 3, 5: two
+    // and four pixels per thread in packed FP32x2; 6, 7: the packed kernels as persistent
+    // CTAs on a work queue
+    const int cands[7] = {1, 2, 4, 3, 5, 6, 7};
+    float best_c = 1e30f;
+    int pick_c = 2;
     for (int ci = 0; ci < 7 && e == cudaSuccess; ++ci) {
-        P.tune_contrib = P.tune_adjoint = cands[ci];
-        // warm once, then time reps launches of each stage
-        if (fused) e = launch_fused(P, MODE_GRAD, st);
-        if (e == cudaSuccess) e = launch_contrib(P, CELESTE_FP32_ACC64, st, rest, n_rest);
-        if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
-        if (e == cudaSuccess) e = adjoint_stage();
-        float tc = 0.f, ta = 0.f;
+        P.tune_contrib = cands[ci];
+        float tc = 0.f;
+        e = launch_contrib(P, CELESTE_FP32_ACC64, st);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_contrib(P, CELESTE_FP32_ACC64, st, rest, n_rest);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_contrib(P, CELESTE_FP32_ACC64, st);
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&tc, a, b);
-        if (e == cudaSuccess) e = launch_gather(P, CELESTE_FP32_ACC64, st);
-        if (e == cudaSuccess) e = cudaEventRecord(a, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = adjoint_stage();
-        if (e == cudaSuccess) e = cudaEventRecord(b, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ta, a, b);
         if (e == cudaSuccess && tc < best_c) { best_c = tc; pick_c = cands[ci]; }
-        if (e == cudaSuccess && ta < best_a) { best_a = ta; pick_a = cands[ci]; }
     }
     P.tune_contrib = pick_c;
-    P.tune_adjoint = pick_a;
-    // the fused pass's CTA cap per SM, timed on whole value + gradient evaluations (it
-    // trades the fused pass's own speed against room for the concurrent chain)
-    int pick_cap = 0, pick_sep = 0;
-    if (e == cudaSuccess && fused && ensure_out(pr) == CELESTE_OK) {
-        // (sep, cap) pairs: the gather inside the adjoint or tile-major, then the cap
-        // timed as the calls run them: through the captured graph, whose nodes keep the
-        // chain's and the fused pass's stream priorities
-        constexpr int NC = 12;
-        const int combos[NC][2] = {{0, 0}, {1, 0}, {0, 8}, {1, 8}, {0, 7}, {0, 6}, {1, 6},
-                                   {0, 5}, {0, 4}, {1, 4}, {0, 3}, {1, 3}};
+    // the item kernel's register budget (codes 1 .. 5), timed on whole value + gradient
+    // evaluations as the calls run them (the captured graph)
+    int pick_i = 3;
+    if (P.sitems) {
         float best = 1e30f;
         double* o = pr->d_out;
-        for (int ci = 0; ci < NC && e == cudaSuccess; ++ci) {
-            P.gather_sep = combos[ci][0];
-            P.fused_cap = combos[ci][1];
+        for (int code = 1; code <= 5 && e == cudaSuccess; ++code) {
+            P.tune_items = code;
             celeste_status rs = run_cached(pr, pr->d_theta, CELESTE_FP32_ACC64, MODE_GRAD, o, o + 1,
                                            o + 1 + P.n_src, nullptr, st, false);
             float t = 0.f;
@@ -970,37 +1016,29 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
             if (e == cudaSuccess && t < best) {
                 best = t;
-                pick_sep = combos[ci][0];
-                pick_cap = combos[ci][1];
+                pick_i = code;
             }
         }
     }
-    P.fused_cap = pick_cap;
-    P.gather_sep = pick_sep;
+    P.tune_items = pick_i;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
-    if (ppt_contrib) *ppt_contrib = pick_c;
-    if (ppt_adjoint) *ppt_adjoint = pick_a;
-    if (fused_cap) *fused_cap = pick_cap;
-    if (gather_sep) *gather_sep = pick_sep;
+    if (contrib_code) *contrib_code = pick_c;
+    if (items_code) *items_code = pick_i;
     return CELESTE_OK;
 }
 
-celeste_status celeste_set_tuning(celeste_problem* pr, int32_t ppt_contrib, int32_t ppt_adjoint,
-                                  int32_t fused_cap, int32_t gather_sep) {
+celeste_status celeste_set_tuning(celeste_problem* pr, int32_t contrib_code, int32_t items_code) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");
-    if (fused_cap < 0 || fused_cap > 8) return fail(CELESTE_ERR_ARG, "fused_cap must be 0 .. 8");
-    if (gather_sep != 0 && gather_sep != 1) return fail(CELESTE_ERR_ARG, "gather_sep must be 0 or 1");
-    auto okp = [](int v) { return v >= 0 && v <= 7; };
-    if (!okp(ppt_contrib) || !okp(ppt_adjoint))
+    if (contrib_code < 0 || contrib_code > 7)
         return fail(CELESTE_ERR_ARG,
-                    "tuning codes: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 "
+                    "contrib code: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 "
                     "pixels), 6 / 7 the same as persistent CTAs on a work queue");
-    pr->P.tune_contrib = ppt_contrib;
-    pr->P.tune_adjoint = ppt_adjoint;
-    pr->P.fused_cap = fused_cap;
-    pr->P.gather_sep = gather_sep;
+    if (items_code < 0 || items_code > 5)
+        return fail(CELESTE_ERR_ARG, "items code: 0 default, 1 .. 5 the item kernel's register budget");
+    pr->P.tune_contrib = contrib_code;
+    pr->P.tune_items = items_code;
     return CELESTE_OK;
 }
 

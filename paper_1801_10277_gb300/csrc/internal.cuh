@@ -32,6 +32,10 @@ constexpr int NYH = NY * (NY + 1) / 2;   // packed upper triangle of the y-Hessi
 // [1..NY] gradient wrt y, [1+NY ..) packed y-Hessian.
 constexpr int PART_LL = 0, PART_G = 1, PART_H = 1 + NY, PART_TH = 1;
 constexpr int NPART = 1 + NY + NYH;
+// Split-item partial record of the FP32 value / gradient path (doubles): [0] ll,
+// [1..NY] d ll / d y; the chain rule runs once per patch in the per-source epilogue.
+constexpr int NZPART = 1 + NY;
+constexpr int ZF_GROUP = 128;   // sources per first-level group of the total
 
 // Mixture table of one (source, patch), in units of the pixel precision R:
 //   header [0..7]: a0 a1 E[l|star] E[l^2|star] E[l|gal] E[l^2|gal] iota 0
@@ -46,8 +50,11 @@ constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_
 constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
 
+// floats of one patch's whitened-frame table (item_kernels.cu): header 32, per PSF
+// component 20 + 20 per pair of profile components (each group padded to even)
+constexpr int ZFULL_FLOATS = 32 + MAXPSF * (20 + ((MAXPROF + 2) / 2) * 20);
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)
-constexpr int FUSED_CHUNK = 256;   // pixels per split item of singly covered pixels (fused pass; 512 measured slower)
+constexpr int FUSED_CHUNK = 1024;  // pixels per split item of singly covered pixels (one CTA of the item kernel)
 constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
 
 struct ImgMeta {
@@ -60,6 +67,16 @@ struct ImgMeta {
     double psf[MAXPSF][6];
     float psf_f[MAXPSF][6];  // the same in FP32 (conversions run on the narrow FP64 pipe)
     float A_f[4];
+    // whitened-frame constants of PSF component k (item_kernels.cu), from FP64 on the host:
+    //   psf_li:  L^-1 = [[li0, 0], [li1, li2]] with Sigma_k = L L^T (Cholesky)
+    //   psf_cs:  log2|alpha_k| - log2(2 pi) - log2(det Sigma_k) / 2 (-inf for alpha_k = 0)
+    //   psf_sg:  sign of alpha_k (+1 for alpha_k = 0)
+    //   psf_dm:  (det A / sqrt(det Sigma_k))^2, so det(L^-1 G L^-T) = psf_dm sigma^4 rho^2
+    float psf_li[MAXPSF][3];
+    float psf_cs[MAXPSF];
+    float psf_sg[MAXPSF];
+    float psf_dm[MAXPSF];
+    float sky_f;
 };
 
 struct PatchGeo {
@@ -70,6 +87,21 @@ struct PatchGeo {
 
 struct WorkItem {
     int32_t patch, q0, n, src;
+};
+
+// A split item of the FP32 item kernel, in launch order: its patch (table index), pixel
+// count, partial index (the split item), source, first entry of its gathered pixels, and
+// the other patches covering its pixels (zcands[c0 .. c0 + nc)); npsf of its image.
+struct ZItem {
+    int32_t patch, n, out, src;
+    int64_t pix;
+    int32_t c0, nc_npsf;     // nc | npsf << 24
+};
+
+// Another patch covering pixels of a multiply covered item: its table index, its origin
+// relative to the item's patch origin, size, source and PSF component count.
+struct ZCand {
+    int32_t patch, dx, dy, w, h, src, npsf, pad;
 };
 
 struct Tile {
@@ -97,6 +129,7 @@ struct ModelDev {
     float prior_mu_f[2][NCOMP][4];
     float prior_P_f[2][NCOMP][16];
     float prior_logdet_f[2][NCOMP];
+    float prof_lw_f[MAXPROF];         // log2 of the profile weights (-inf for a zero weight)
 };
 
 // FP32 copies of the model / image constants, filled once on the host
@@ -110,6 +143,7 @@ inline void fill_float_copies(ModelDev& m) {
     for (int j = 0; j < MAXPROF; ++j) {
         m.prof_w_f[j] = (float)m.prof_w[j];
         m.prof_nu_f[j] = (float)m.prof_nu[j];
+        m.prof_lw_f[j] = (float)std::log2(m.prof_w[j]);
     }
     m.prior_star_f = (float)m.prior_star;
     for (int i = 0; i < 2; ++i) {
@@ -126,6 +160,24 @@ inline void fill_float_copies(ImgMeta& im) {
     for (int k = 0; k < MAXPSF; ++k)
         for (int c = 0; c < 6; ++c) im.psf_f[k][c] = (float)im.psf[k][c];
     for (int k = 0; k < 4; ++k) im.A_f[k] = (float)im.A[k];
+    im.sky_f = (float)im.sky;
+    const double detA = im.A[0] * im.A[3] - im.A[1] * im.A[2];
+    for (int k = 0; k < MAXPSF; ++k) {
+        im.psf_li[k][0] = im.psf_li[k][1] = im.psf_li[k][2] = 0.f;
+        im.psf_cs[k] = -INFINITY;
+        im.psf_sg[k] = 1.f;
+        im.psf_dm[k] = 0.f;
+        if (k >= im.npsf) continue;
+        const double* ps = im.psf[k];
+        const double l11 = std::sqrt(ps[3]), l21 = ps[4] / l11, l22 = std::sqrt(ps[5] - l21 * l21);
+        const double det = ps[3] * ps[5] - ps[4] * ps[4];
+        im.psf_li[k][0] = (float)(1.0 / l11);
+        im.psf_li[k][1] = (float)(-l21 / (l11 * l22));
+        im.psf_li[k][2] = (float)(1.0 / l22);
+        im.psf_cs[k] = (float)(std::log2(std::fabs(ps[0])) - 2.6514961294723187 /* log2(2 pi) */ - 0.5 * std::log2(det));
+        im.psf_sg[k] = ps[0] < 0 ? -1.f : 1.f;
+        im.psf_dm[k] = (float)(detA * detA / det);
+    }
 }
 
 // precision-selected views of those constants
@@ -158,10 +210,8 @@ enum Mode : int { MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
 struct DevProblem {
     int32_t n_img, n_src, n_patch, n_item, n_tile, npsf_max, nprof;
-    int32_t tune_contrib, tune_adjoint;   // FP32 pixels per thread (0 = default)
-    int32_t fused_cap;                    // resident CTAs per SM of the fused pass (0 = no cap)
-    int32_t gather_sep;                   // split path: 0 gather inside the adjoint of the multiply
-                                          // covered items, 1 tile-major k_gather then the adjoint
+    int32_t tune_contrib, tune_adjoint;   // FP32 map-pass / adjoint kernel codes of the Hessian, fit
+                                          // and allocation-free paths (0 = default)
     int64_t n_px, n_sp;
     int32_t max_src_patches;              // most patches of one source (k_prep's grid)
     const ImgMeta* img;
@@ -191,21 +241,33 @@ struct DevProblem {
     double* tot_part;        // [64] k_total slice sums
     int32_t* tot_done;       // k_total completion counter, 0 between launches
     // The split item set of the FP32 value / gradient path: each patch's pixels split into
-    // the singly covered ones and the others, each list cut into items of <= CHUNK pixels
-    // (WorkItem.q0 indexes spix, which holds patch-relative pixel indices); a source's
-    // split items are contiguous (sitem_off).  Nullable (no split set: sitems null).
+    // the singly covered ones (items of <= FUSED_CHUNK pixels) and the others
+    // (items of <= CHUNK pixels, one CTA each); WorkItem.q0 indexes spix, which holds
+    // patch-relative pixel indices; a source's split items are contiguous (sitem_off).
+    // Nullable (no split set: sitems null).
     const WorkItem* sitems;
     const int32_t* spix;
     const int32_t* sitem_off;    // [n_src + 1]
-    const int32_t* sidx_single;  // split items of singly covered pixels (fused pass)
-    const int32_t* sidx_multi;   // split items of multiply covered pixels (map pass, gather + adjoint)
-    int n_sitem, n_ssingle, n_smulti;
-    double* spart;               // [n_sitem][NPART] partials of the split items
+    int n_sitem, n_smulti;       // all split items; those of multiply covered pixels
+    const int32_t* spatch_off;   // [n_patch + 1] split items of each patch (contiguous)
+    double* spart;               // [n_sitem][NZPART] partials of the split items: ll, d ll / d y
+    double* zf_grp_total;        // per group of ZF_GROUP sources: their share of the total
+    int32_t* zf_done;            // [groups + 1] completion counters, 0 between launches
     double* sitem_ll;            // ll of a singly covered item (0 for the others)
     double* sitem_own;           // ll of the multiply covered pixels an item owns (the first
                                  // covering patch owns a pixel; 0 for singly covered items)
     const int32_t* src_active;   // per source: 0 = skip its work (the fit's converged batch
                                  // sources); nullable = every source works
+    // the FP32 value / gradient item kernel (item_kernels.cu)
+    float* ztbl;                 // [n_patch][ZFULL] whitened-frame tables (FP32)
+    int32_t* zready;             // [n_patch] table ready flags (reset before each launch)
+    int32_t* zsrc_done;          // [n_src] arrivals of each source's items and KL warp, 0 between launches
+    const ZItem* zitems;         // [n_sitem] in launch order (multiply covered items first)
+    const ZCand* zcands;
+    const int32_t* zxy;          // per split-item pixel (spix order): (row << 16) | column in the patch
+    const float2* zxs;           // per split-item pixel: (counts, sky)
+    int32_t tune_items;          // item kernel variant: 1 one pixel per thread, else two
+    int32_t model_npe, model_npd;   // exp / dev profile components in pairs (rounded up)
     int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
                              // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;
@@ -220,7 +282,6 @@ celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const 
                                                           double*, double*));
 
 void prime_persistent_grids();
-void prime_fused_caps();
 // total = tile ll sums + item ll sums - KL (after the gather and every item ll)
 cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st);
 // tables (and, with_kl, the KL value / gradient and the domain check) of every source
@@ -229,22 +290,12 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
 // contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);
-// FP32 map pass + adjoint in one kernel over the split items of singly covered pixels
-// (mode MODE_LL or MODE_GRAD);
-// with d_theta, the same launch also computes the KL (value, gradient, domain check)
-cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta = nullptr);
-// FP32 map pass over the split items of multiply covered pixels (E_s, Var_s)
-cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st);
-// FP32 gather + adjoint in one kernel over the same items (after their map pass)
-cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st);
-// FP32 adjoint over the same items from the maps (same kernel body as the gather + adjoint)
-cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, int mode, cudaStream_t st);
-// per-source epilogue over the split item set (FP32 value / gradient path)
-cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local, double* d_grad,
-                                  cudaStream_t st);
-// total over the split items' sums: sitem_own + sitem_ll - KL (gather_sep: the tile sums
-// of k_gather instead of sitem_own)
-cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st);
+// The FP32 value (MODE_LL) or value + gradient (MODE_GRAD) evaluation in one launch
+// (item_kernels.cu): the patches' whitened-frame tables, the KL value / gradient and the
+// domain check of theta, every split item, and the per-source epilogue (local objective,
+// gradient; each nullable) and the total (nullable)
+cudaError_t launch_items(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta, double* d_local,
+                         double* d_grad, double* d_total);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);

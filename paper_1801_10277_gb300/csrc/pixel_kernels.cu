@@ -663,8 +663,7 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
                                                 const float* __restrict__ pixels,
                                                 const float* __restrict__ sky_map,
                                                 float* __restrict__ emap, float* __restrict__ vmap,
-                                                double* __restrict__ item_ll,
-                                                const int32_t* __restrict__ pix = nullptr) {
+                                                double* __restrict__ item_ll) {
     constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
     const int npsf = im.npsf;
@@ -675,8 +674,7 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
         ok[p] = l < it.n;
-        const int qi = it.q0 + (ok[p] ? l : 0);
-        const int q = pix ? pix[qi] : qi;   // patch-relative pixel (split items list them)
+        const int q = it.q0 + (ok[p] ? l : 0);
         qs[p] = q;
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
@@ -760,53 +758,16 @@ __device__ __forceinline__ void contrib_x2_item(int item, const WorkItem& it, co
     }
 }
 
-// FUSED: an item whose every pixel only its own patch covers.  E = sky + E_s and
-// Var = Var_s are then known from the item's own mixture sums, so the map pass and the
-// adjoint pass become one: the mixture is evaluated once, E and Var are formed after
-// the component loop (and written to the maps, which a later backward-only call reads),
-// and the item's ll goes to item_ll as well as to its partials.  Otherwise E and Var
-// come from the maps k_contrib / k_gather wrote.
-// Where an item's E and Var come from:
-//   SRC_MAPS   the maps (k_contrib / k_gather wrote them);
-//   SRC_OWN    the item's own mixture sums (every pixel singly covered; see FUSED);
-//   SRC_GATHER singly covered pixels from the maps (k_contrib wrote them), the others
-//              gathered here from the E_s, Var_s of the patches covering the pixel's 16 x 16
-//              cell, in the cell list's (ascending source) order -- the same sums k_gather
-//              forms.  The first covering patch owns the pixel: its item writes the maps and
-//              counts the pixel's ll for the total (item_own).
-constexpr int SRC_MAPS = 0, SRC_OWN = 1, SRC_GATHER = 2;
-
-struct GatherArgs {
-    const uint8_t* single;
-    const int32_t* tile_grid;
-    const Tile* tiles;
-    const int32_t* tile_list;
-    const PatchGeo* geo;
-    const float* spE;
-    const float* spV;
-    const float* sky_map;
-    float* emap;
-    float* vmap;
-    double* item_own;
-    const int32_t* pix;
-};
-
-template <int MODE, int NPAIR, int SRC = SRC_MAPS, int CH = CHUNK>
+// The adjoint of one item from the maps (k_contrib / k_gather wrote E and Var).
+template <int MODE, int NPAIR>
 __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, const PatchGeo& g,
                                                 const ImgMeta& im, int nprof, const float2* sT2,
                                                 const float* __restrict__ pixels,
                                                 const float* __restrict__ emap,
                                                 const float* __restrict__ vmap,
-                                                double* __restrict__ part,
-                                                const float* __restrict__ sky_map = nullptr,
-                                                float* __restrict__ emap_out = nullptr,
-                                                float* __restrict__ vmap_out = nullptr,
-                                                double* __restrict__ item_ll = nullptr,
-                                                const GatherArgs* ga = nullptr,
-                                                const int32_t* __restrict__ pix = nullptr) {
-    constexpr bool FUSED = SRC == SRC_OWN;
+                                                double* __restrict__ part) {
     constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
-    constexpr int NT = CH / (2 * NPAIR);
+    constexpr int NT = CHUNK / (2 * NPAIR);
     constexpr int PPT = 2 * NPAIR;
     const int npsf = im.npsf;
     float v[NV];
@@ -816,126 +777,20 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
     // pixel p of this thread: t + p * NT; pair r holds pixels 2r, 2r + 1
     int xs[PPT], ys[PPT];
     bool ok[PPT];
-    float cE[PPT], cV[PPT], xv[PPT], sky[PPT];
-    int64_t mm[PPT];
-    float vown = 0.f;   // SRC_GATHER: ll of the multiply covered pixels this item owns
+    float cE[PPT], cV[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int l = t + p * NT;
         ok[p] = l < it.n;
-        const int qi = it.q0 + (ok[p] ? l : 0);
-        const int q = pix ? pix[qi] : qi;   // patch-relative pixel (split items list them)
+        const int q = it.q0 + (ok[p] ? l : 0);
         ys[p] = q / g.w;
         xs[p] = q - ys[p] * g.w;
         const int64_t m = im.px_off + (int64_t)(g.y0 + ys[p]) * im.W + (g.x0 + xs[p]);
         const float x = pixels[m];
-        if constexpr (FUSED) {
-            mm[p] = m;
-            xv[p] = x;
-            sky[p] = im.has_sky_map ? sky_map[m] : (float)im.sky;
-        } else {
-            float E, V;
-            bool own = false;
-            if constexpr (SRC == SRC_GATHER) {
-                if (ga->single[g.sp_off + q]) {
-                    E = emap[m];
-                    V = vmap[m];
-                } else {
-                    const int gx = g.x0 + xs[p], gy = g.y0 + ys[p];
-                    const Tile tl = ga->tiles[ga->tile_grid[im.tg_off + (int64_t)(gy / TILE) * im.tgw + gx / TILE]];
-                    E = im.has_sky_map ? ga->sky_map[m] : (float)im.sky;
-                    V = 0.f;
-                    int first = -1;
-                    for (int e = 0; e < tl.list_n; ++e) {
-                        const int pe = ga->tile_list[tl.list_off + e];
-                        const PatchGeo G = ga->geo[pe];
-                        const int xx = gx - G.x0, yy = gy - G.y0;
-                        if (xx >= 0 && xx < G.w && yy >= 0 && yy < G.h) {
-                            const int64_t qq = G.sp_off + (int64_t)yy * G.w + xx;
-                            E += ga->spE[qq];
-                            V += ga->spV[qq];
-                            if (first < 0) first = pe;
-                        }
-                    }
-                    own = ok[p] && first == it.patch;
-                    if (own) {
-                        ga->emap[m] = E;
-                        ga->vmap[m] = V;
-                    }
-                }
-            } else {
-                E = emap[m];
-                V = vmap[m];
-            }
-            const float ll = pixel_ll(x, E, V);
-            if (ok[p]) v[0] += ll;
-            if (own) vown += ll;
-            pixel_weights(x, E, V, cE[p], cV[p]);
-        }
-    }
-    if constexpr (FUSED && MODE == MODE_LL) {
-        // value only: the mixture sums, then E, Var and ll per pixel
-        float2 X[NPAIR], Y[NPAIR], g0[NPAIR], g1[NPAIR];
-#pragma unroll
-        for (int r = 0; r < NPAIR; ++r) {
-            X[r] = make_float2((float)xs[2 * r], (float)xs[2 * r + 1]);
-            Y[r] = make_float2((float)ys[2 * r], (float)ys[2 * r + 1]);
-            g0[r] = g1[r] = f2(0.f);
-        }
-        for (int k = 0; k < npsf; ++k) {
-            float2 nmx, nmy;
-            ld2(sT2 + T_MEAN + 2 * k, nmx, nmy);
-            float2 dxx[NPAIR], dxy[NPAIR], dyy[NPAIR];
-#pragma unroll
-            for (int r = 0; r < NPAIR; ++r) {
-                const float2 dx = __fadd2_rn(X[r], nmx), dy = __fadd2_rn(Y[r], nmy);
-                dxx[r] = __fmul2_rn(dx, dx);
-                dxy[r] = __fmul2_rn(dx, dy);
-                dyy[r] = __fmul2_rn(dy, dy);
-            }
-            const float2* S = sT2 + T_STAR + k * STAR_STRIDE;
-            float2 s0, s1, s2, s3;
-            ld2(S, s0, s1);
-            ld2(S + 2, s2, s3);
-            const float2 s7 = S[7];
-#pragma unroll
-            for (int r = 0; r < NPAIR; ++r) {
-                float2 a = __ffma2_rn(s2, dyy[r], s3);
-                a = __ffma2_rn(s1, dxy[r], a);
-                a = __ffma2_rn(s0, dxx[r], a);
-                g0[r] = __ffma2_rn(s7, ex2x2(a), g0[r]);   // as the gradient pass accumulates g
-            }
-            const float2* G = sT2 + T_GAL + k * nprof * GAL_STRIDE;
-            for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
-                float2 c0, c1, c2, c3;
-                ld2(G, c0, c1);
-                ld2(G + 2, c2, c3);
-                const float2 c7 = G[7];
-#pragma unroll
-                for (int r = 0; r < NPAIR; ++r) {
-                    float2 b = __ffma2_rn(c2, dyy[r], c3);
-                    b = __ffma2_rn(c1, dxy[r], b);
-                    b = __ffma2_rn(c0, dxx[r], b);
-                    g1[r] = __ffma2_rn(c7, ex2x2(b), g1[r]);
-                }
-            }
-        }
-        const float iota = sT2[H_IOTA].x, a0 = sT2[H_A0].x, a1 = sT2[H_A1].x;
-        const float el0 = sT2[H_EL0].x, el1 = sT2[H_EL1].x;
-        const float em0 = __fsub_rn(__fdiv_rn(sT2[H_EL20].x, __fmul_rn(el0, el0)), 1.f);
-        const float em1 = __fsub_rn(__fdiv_rn(sT2[H_EL21].x, __fmul_rn(el1, el1)), 1.f);
-#pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            if (!ok[p]) continue;
-            const int r = p >> 1;
-            const float G0 = (p & 1) ? g0[r].y : g0[r].x, G1 = (p & 1) ? g1[r].y : g1[r].x;
-            float f0, f1, e, V;
-            pixel_ev(iota, a0, a1, el0, el1, em0, em1, G0, G1, f0, f1, e, V);
-            const float E = __fadd_rn(sky[p], e);
-            v[0] += pixel_ll(xv[p], E, V);
-            emap_out[mm[p]] = E;
-            vmap_out[mm[p]] = V;
-        }
+        const float E = emap[m], V = vmap[m];
+        const float ll = pixel_ll(x, E, V);
+        if (ok[p]) v[0] += ll;
+        pixel_weights(x, E, V, cE[p], cV[p]);
     }
     if constexpr (MODE >= MODE_GRAD) {
         float2 X[NPAIR], Y[NPAIR];
@@ -1025,22 +880,9 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
             const float DE = hi ? de1[r].y : de1[r].x;
             const float SXX = hi ? sxx[r].y : sxx[r].x, SXY = hi ? sxy[r].y : sxy[r].x,
                         SYY = hi ? syy[r].y : syy[r].x;
-            float f0, f1, Es, Vs;
-            if constexpr (FUSED) {
-                // this pixel's E and Var are the item's own: form them, the ll and its weights
-                const float em0 = __fsub_rn(__fdiv_rn(el20, __fmul_rn(el0, el0)), 1.f);
-                const float em1 = __fsub_rn(__fdiv_rn(el21, __fmul_rn(el1, el1)), 1.f);
-                pixel_ev(iota, a0, a1, el0, el1, em0, em1, G0, G1, f0, f1, Es, Vs);
-                const float E = __fadd_rn(sky[p], Es);
-                v[0] += pixel_ll(xv[p], E, Vs);
-                pixel_weights(xv[p], E, Vs, cE[p], cV[p]);
-                emap_out[mm[p]] = E;
-                vmap_out[mm[p]] = Vs;
-            } else {
-                f0 = __fmul_rn(__fmul_rn(iota, el0), G0);   // as pixel_ev forms them
-                f1 = __fmul_rn(__fmul_rn(iota, el1), G1);
-                Es = __fadd_rn(__fmul_rn(a0, f0), __fmul_rn(a1, f1));
-            }
+            const float f0 = __fmul_rn(__fmul_rn(iota, el0), G0);   // as pixel_ev forms them
+            const float f1 = __fmul_rn(__fmul_rn(iota, el1), G1);
+            const float Es = __fadd_rn(__fmul_rn(a0, f0), __fmul_rn(a1, f1));
             const float w1 = cE[p] - 2.f * cV[p] * Es, w2 = cV[p];
             const float s0 = i2 * G0 * G0, s1 = i2 * G1 * G1;
             v[1 + Y_A0] += w1 * f0 + w2 * el20 * s0;
@@ -1061,18 +903,9 @@ __device__ __forceinline__ void adjoint_x2_item(int item, const WorkItem& it, co
     }
     __shared__ double tot[NV];
     cta_sum<float, NV>(v, tot);
-    if constexpr (SRC == SRC_GATHER) {
-        float vo[1] = {vown};
-        double to[1];
-        cta_sum<float, 1>(vo, to);
-        if (threadIdx.x == 0) ga->item_own[item] = to[0];
-    }
     __syncthreads();
     double* out = part + (size_t)item * NPART;
-    if (threadIdx.x == 0) {
-        out[PART_LL] = tot[0];
-        if constexpr (FUSED) item_ll[item] = tot[0];
-    }
+    if (threadIdx.x == 0) out[PART_LL] = tot[0];
     if constexpr (MODE >= MODE_GRAD) {
         for (int j = threadIdx.x; j < NP; j += blockDim.x) {
             const float el[2] = {sT2[H_EL0].x, sT2[H_EL1].x}, el2[2] = {sT2[H_EL20].x, sT2[H_EL21].x};
@@ -1124,112 +957,14 @@ __global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_adjoint_x2(const WorkIt
                                                                   const float* __restrict__ tbl,
                                                                   const float* __restrict__ emap,
                                                                   const float* __restrict__ vmap,
-                                                                  double* __restrict__ part,
-                                                                  const int32_t* __restrict__ pix) {
+                                                                  double* __restrict__ part) {
     __shared__ __align__(16) float2 sT2[TBL_STRIDE];
     const int item = idx ? idx[blockIdx.x] : (int)blockIdx.x;
     const WorkItem it = items[item];
     const PatchGeo g = geo[it.patch];
     const ImgMeta& im = img[g.img];
     load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part, nullptr, nullptr,
-                                 nullptr, nullptr, nullptr, pix);
-}
-
-// map pass over split items of multiply covered pixels: E_s, Var_s for the gather
-template <int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_contrib_split(const WorkItem* __restrict__ items,
-                                                                     const int32_t* __restrict__ idx,
-                                                                     const int32_t* __restrict__ pix,
-                                                                     const PatchGeo* __restrict__ geo,
-                                                                     const ImgMeta* __restrict__ img, int nprof,
-                                                                     const float* __restrict__ tbl,
-                                                                     float* __restrict__ spE,
-                                                                     float* __restrict__ spV) {
-    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    pdl_trigger();   // the gather + adjoint may be scheduled; it waits for this grid
-    const int item = idx[blockIdx.x];
-    const WorkItem it = items[item];
-    const PatchGeo g = geo[it.patch];
-    const ImgMeta& im = img[g.img];
-    pdl_wait();      // the tables come from k_prep
-    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    contrib_x2_item<NPAIR>(item, it, g, im, nprof, sT2, spE, spV, nullptr, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, pix);
-}
-
-// gather + adjoint in one, for the items listed in idx (some pixel covered twice or more)
-template <int MODE, int NPAIR>
-__global__ void __launch_bounds__(CHUNK / (2 * NPAIR)) k_gadjoint_x2(const WorkItem* __restrict__ items,
-                                                                   const int32_t* __restrict__ idx,
-                                                                   const ImgMeta* __restrict__ img, int nprof,
-                                                                   const float* __restrict__ pixels,
-                                                                   const float* __restrict__ tbl,
-                                                                   double* __restrict__ part,
-                                                                   GatherArgs ga) {
-    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    const int item = idx[blockIdx.x];
-    const WorkItem it = items[item];
-    const PatchGeo g = ga.geo[it.patch];
-    const ImgMeta& im = img[g.img];
-    pdl_wait();      // E_s / Var_s of the covering patches come from k_contrib_split
-    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR, SRC_GATHER>(item, it, g, im, nprof, sT2, pixels, ga.emap, ga.vmap, part,
-                                             nullptr, nullptr, nullptr, nullptr, &ga, ga.pix);
-}
-
-// map pass + adjoint in one, for the items listed in idx (every pixel singly covered).
-// With kl.klg set, the first kl.blocks CTAs instead compute the KL (one warp per source,
-// value, gradient, domain check): the KL is needed only by the epilogue and the total,
-// which follow this kernel on the side stream, so it leaves k_prep's critical path.
-struct KlArgs {
-    const double* theta;
-    const ModelDev* md;
-    int n_src, blocks;
-    double* kl;
-    double* klg;
-    int32_t* status;
-};
-
-template <int MODE, int NPAIR>
-__global__ void __launch_bounds__(FUSED_CHUNK / (2 * NPAIR), CEL_FUSED_MINB * CHUNK / FUSED_CHUNK) k_fused_x2(const WorkItem* __restrict__ items,
-                                                                const int32_t* __restrict__ idx,
-                                                                const PatchGeo* __restrict__ geo,
-                                                                const ImgMeta* __restrict__ img, int nprof,
-                                                                const float* __restrict__ pixels,
-                                                                const float* __restrict__ sky_map,
-                                                                const float* __restrict__ tbl,
-                                                                float* __restrict__ emap,
-                                                                float* __restrict__ vmap,
-                                                                double* __restrict__ part,
-                                                                double* __restrict__ item_ll,
-                                                                const int32_t* __restrict__ pix,
-                                                                KlArgs kl) {
-    constexpr int WARPS = FUSED_CHUNK / (2 * NPAIR) / 32;
-    if ((int)blockIdx.x < kl.blocks) {
-        __shared__ double kth[WARPS][NP], kg[WARPS][NP];
-        __shared__ float kthr[WARPS][NP];
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int s = (int)blockIdx.x * WARPS + w;
-        if (s >= kl.n_src) return;   // whole warps leave; no block barrier in this branch
-        for (int i = lane; i < NP; i += 32) {
-            const double v = kl.theta[(size_t)NP * s + i];
-            kth[w][i] = v;
-            kthr[w][i] = (float)v;
-        }
-        __syncwarp();
-        prep_kl<float>(s, kth[w], kthr[w], kl.md, kl.kl, kl.klg, kl.status, kg[w]);
-        return;
-    }
-    __shared__ __align__(16) float2 sT2[TBL_STRIDE];
-    const int item = idx[blockIdx.x - kl.blocks];
-    const WorkItem it = items[item];
-    const PatchGeo g = geo[it.patch];
-    const ImgMeta& im = img[g.img];
-    load_table_x2(sT2, tbl + (size_t)it.patch * TBL_STRIDE, T_GAL + im.npsf * nprof * GAL_STRIDE);
-    adjoint_x2_item<MODE, NPAIR, SRC_OWN, FUSED_CHUNK>(item, it, g, im, nprof, sT2, pixels, nullptr,
-                                                       nullptr, part, sky_map, emap, vmap, item_ll,
-                                                       nullptr, pix);
+    adjoint_x2_item<MODE, NPAIR>(item, it, g, im, nprof, sT2, pixels, emap, vmap, part);
 }
 
 // ---- persistent CTAs with a work queue (tuning codes 6, 7)
@@ -1459,11 +1194,11 @@ static void adjoint_x2(const DevProblem& P, int mode, ItemSet S, cudaStream_t st
     if (mode == MODE_LL)
         k_adjoint_x2<MODE_LL, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
                                                         P.tbl32, (const float*)P.emap,
-                                                        (const float*)P.vmap, P.item_part, nullptr);
+                                                        (const float*)P.vmap, P.item_part);
     else
         k_adjoint_x2<MODE_GRAD, NPAIR><<<S.n, NT, 0, st>>>(P.items, S.idx, P.geo, P.img, P.nprof, P.pixels,
                                                           P.tbl32, (const float*)P.emap,
-                                                          (const float*)P.vmap, P.item_part, nullptr);
+                                                          (const float*)P.vmap, P.item_part);
 }
 
 template <int MODE, int NPAIR>
@@ -1481,115 +1216,6 @@ template <int NPAIR>
 static void adjoint_pq(const DevProblem& P, int mode, ItemSet S, cudaStream_t st) {
     if (mode == MODE_LL) adjoint_pq_mode<MODE_LL, NPAIR>(P, S, st);
     else adjoint_pq_mode<MODE_GRAD, NPAIR>(P, S, st);
-}
-
-// Dynamic shared memory (unused by the kernel) that holds a kernel to at most `cap`
-// resident CTAs per SM, so that the fused pass running beside the map / gather / adjoint
-// chain leaves SM slots for that chain; 0 = no cap.  Found with the occupancy API and
-// cached per (kernel, cap, device).
-static int cap_padding(const void* kernel, int threads, int cap) {
-    if (cap <= 0) return 0;
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, int>, int> cache;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        auto f = cache.find({kernel, cap, dev});
-        if (f != cache.end()) return f->second;
-    }
-    int smem_blk = 0;
-    cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, kernel);
-    const int room = smem_blk - (int)fa.sharedSizeBytes;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, room > 0 ? room : 0);
-    int pad = 0;
-    for (int bytes = 0; bytes <= room; bytes += 1024) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, bytes) != cudaSuccess) break;
-        if (per_sm <= cap) {
-            pad = bytes;
-            break;
-        }
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    cache[{kernel, cap, dev}] = pad;
-    return pad;
-}
-
-template <int NPAIR>
-static void fused_x2(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta) {
-    constexpr int NT = FUSED_CHUNK / (2 * NPAIR);
-    constexpr int WARPS = NT / 32;
-    KlArgs kl{d_theta, P.model, P.n_src, 0, P.kl, P.kl_grad, P.status};
-    if (d_theta && P.kl_grad) kl.blocks = (P.n_src + WARPS - 1) / WARPS;
-    const int grid = P.n_ssingle + kl.blocks;
-    if (grid == 0) return;
-    if (mode == MODE_LL) {
-        const int pad = cap_padding((const void*)k_fused_x2<MODE_LL, NPAIR>, NT, P.fused_cap);
-        k_fused_x2<MODE_LL, NPAIR><<<grid, NT, pad, st>>>(
-            P.sitems, P.sidx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.spart, P.sitem_ll, P.spix, kl);
-    } else {
-        const int pad = cap_padding((const void*)k_fused_x2<MODE_GRAD, NPAIR>, NT, P.fused_cap);
-        k_fused_x2<MODE_GRAD, NPAIR><<<grid, NT, pad, st>>>(
-            P.sitems, P.sidx_single, P.geo, P.img, P.nprof, P.pixels, P.sky_map, P.tbl32,
-            (float*)P.emap, (float*)P.vmap, P.spart, P.sitem_ll, P.spix, kl);
-    }
-}
-
-// the padding of every fused kernel for caps 1 .. 8, found outside any stream capture
-void prime_fused_caps() {
-    for (int cap = 1; cap <= 8; ++cap) {
-        cap_padding((const void*)k_fused_x2<MODE_LL, 1>, FUSED_CHUNK / 2, cap);
-        cap_padding((const void*)k_fused_x2<MODE_GRAD, 1>, FUSED_CHUNK / 2, cap);
-        cap_padding((const void*)k_fused_x2<MODE_LL, 2>, FUSED_CHUNK / 4, cap);
-        cap_padding((const void*)k_fused_x2<MODE_GRAD, 2>, FUSED_CHUNK / 4, cap);
-    }
-}
-
-static cudaLaunchConfig_t pdl_config(int grid, int block, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    return cfg;
-}
-
-template <int NPAIR>
-static cudaError_t gadjoint_x2(const DevProblem& P, int mode, cudaStream_t st) {
-    constexpr int NT = CHUNK / (2 * NPAIR);
-    const GatherArgs ga{P.single, P.tile_grid, P.tiles, P.tile_list, P.geo, (const float*)P.spE,
-                        (const float*)P.spE2, P.sky_map, (float*)P.emap, (float*)P.vmap, P.sitem_own,
-                        P.spix};
-    cudaLaunchConfig_t cfg = pdl_config(P.n_smulti, NT, st);
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    if (mode == MODE_LL)
-        return cudaLaunchKernelEx(&cfg, k_gadjoint_x2<MODE_LL, NPAIR>, P.sitems, P.sidx_multi, P.img, P.nprof,
-                                  (const float*)P.pixels, (const float*)P.tbl32, P.spart, ga);
-    return cudaLaunchKernelEx(&cfg, k_gadjoint_x2<MODE_GRAD, NPAIR>, P.sitems, P.sidx_multi, P.img, P.nprof,
-                              (const float*)P.pixels, (const float*)P.tbl32, P.spart, ga);
-}
-
-// the map pass of the multiply covered items, launched as a programmatic dependent of
-// k_prep (its CTAs start while the tables are being built and wait for them)
-template <int NPAIR>
-static cudaError_t contrib_split(const DevProblem& P, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = pdl_config(P.n_smulti, CHUNK / (2 * NPAIR), st);
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_contrib_split<NPAIR>, (const WorkItem*)P.sitems, (const int32_t*)P.sidx_multi,
-                       (const int32_t*)P.spix, (const PatchGeo*)P.geo, (const ImgMeta*)P.img, P.nprof,
-                       (const float*)P.tbl32, (float*)P.spE, (float*)P.spE2);
 }
 
 // Occupancy queries of the persistent kernels, made once on the current device outside
@@ -1660,56 +1286,6 @@ cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st, 
             case 7: if (P.queue) contrib_pq<2>(P, S, st); else contrib_x2<2>(P, S, st); break;
             default: return cudaErrorInvalidValue;
         }
-    return cudaGetLastError();
-}
-
-// The fused map + adjoint pass over the items whose pixels only their own patch covers
-// (FP32; the packed kernel with the adjoint's pair count: two pixels per thread unless
-// the adjoint is tuned to four).
-cudaError_t launch_fused(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta) {
-    const int code = ppt_adjoint(P);
-    if (code == 5 || code == 7) fused_x2<2>(P, mode, st, d_theta);
-    else fused_x2<1>(P, mode, st, d_theta);
-    return cudaGetLastError();
-}
-
-// map pass over the split items of multiply covered pixels (FP32, packed pairs as
-// launch_fused picks them)
-cudaError_t launch_contrib_split(const DevProblem& P, cudaStream_t st) {
-    if (P.n_smulti == 0) return cudaSuccess;
-    const int code = ppt_adjoint(P);
-    const cudaError_t e = (code == 5 || code == 7) ? contrib_split<2>(P, st) : contrib_split<1>(P, st);
-    return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-// gather + adjoint over the split items of multiply covered pixels
-cudaError_t launch_gather_adjoint(const DevProblem& P, int mode, cudaStream_t st) {
-    if (P.n_smulti == 0) return cudaSuccess;
-    const int code = ppt_adjoint(P);
-    const cudaError_t e = (code == 5 || code == 7) ? gadjoint_x2<2>(P, mode, st) : gadjoint_x2<1>(P, mode, st);
-    return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-// the adjoint over P.idx_mixed from the maps, with the kernel launch_gather_adjoint uses
-// (a backward-only call then reproduces the one-call gradient bit for bit)
-template <int MODE, int NPAIR>
-static void adjoint_split_maps(const DevProblem& P, cudaStream_t st) {
-    k_adjoint_x2<MODE, NPAIR><<<P.n_smulti, CHUNK / (2 * NPAIR), 0, st>>>(
-        P.sitems, P.sidx_multi, P.geo, P.img, P.nprof, P.pixels, P.tbl32, (const float*)P.emap,
-        (const float*)P.vmap, P.spart, P.spix);
-}
-
-cudaError_t launch_adjoint_mixed_maps(const DevProblem& P, int mode, cudaStream_t st) {
-    if (P.n_smulti == 0) return cudaSuccess;
-    const int code = ppt_adjoint(P);
-    const bool two = code == 5 || code == 7;
-    if (mode == MODE_LL) {
-        if (two) adjoint_split_maps<MODE_LL, 2>(P, st);
-        else adjoint_split_maps<MODE_LL, 1>(P, st);
-    } else {
-        if (two) adjoint_split_maps<MODE_GRAD, 2>(P, st);
-        else adjoint_split_maps<MODE_GRAD, 1>(P, st);
-    }
     return cudaGetLastError();
 }
 

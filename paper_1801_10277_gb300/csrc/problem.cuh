@@ -38,7 +38,8 @@ struct celeste_problem {
     std::vector<int32_t> patch_off, nbr_off, nbrs;
     std::vector<PatchGeo> geo;
     std::vector<ImgMeta> imgs;
-    int64_t sp_single = 0;               // source-pixels of the fused-pass items
+    int64_t sp_single = 0;               // singly covered source-pixels
+    int64_t other_evals = 0;             // (pixel, other covering patch) pairs of the item kernel
     // device buffers owned by the problem
     std::vector<void*> owned;
     double* d_theta = nullptr;

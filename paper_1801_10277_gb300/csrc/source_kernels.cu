@@ -34,27 +34,6 @@ k_total(const double* __restrict__ tile_ll, int n_tile, const double* __restrict
 cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, double* d_local,
                                  double* d_grad, double* d_hess, cudaStream_t st);
 
-// per-source epilogue over the split item set (no total: launch_total_items gives it)
-cudaError_t launch_finalize_split(const DevProblem& P, int mode, double* d_local, double* d_grad,
-                                  cudaStream_t st) {
-    if (P.n_src == 0) return cudaSuccess;
-    k_finalize<<<P.n_src, FZ_THREADS, 0, st>>>(P.n_src, mode, P.geo, P.patch_off, P.sitem_off, P.spart,
-                                               nullptr, nullptr, 0, P.kl, P.kl_grad, d_local, d_grad,
-                                               P.src_total, P.done, nullptr);
-    return cudaGetLastError();
-}
-
-// total = sitem_own + sitem_ll - KL: the split items' sums (fixed order)
-cudaError_t launch_total_items(const DevProblem& P, double* d_total, cudaStream_t st) {
-    if (P.gather_sep)
-        k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.tile_ll, P.n_tile, P.sitem_ll, P.n_sitem, P.kl,
-                                                      P.n_src, P.tot_part, P.tot_done, d_total);
-    else
-        k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.sitem_own, P.n_sitem, P.sitem_ll, P.n_sitem, P.kl,
-                                                      P.n_src, P.tot_part, P.tot_done, d_total);
-    return cudaGetLastError();
-}
-
 // total = tile ll sums + item ll sums - KL (fixed order, TOTAL_CTAS slices)
 cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st) {
     k_total<<<TOTAL_CTAS, TOTAL_THREADS, 0, st>>>(P.tile_ll, P.n_tile, P.item_ll,

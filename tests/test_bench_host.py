@@ -78,15 +78,20 @@ def test_oracle_rate_on_one_core_restores_the_thread_count():
 
 def test_step_bound_of_the_one_field_model():
     """3 PSF components x (1 star + 6 exp + 8 dev) = 45 mixture components per
-    source-pixel: the FP32 pipe at 152 SMs x 128 lanes x 2 x 2.07 GHz over the fused
-    pass's 1,541 FLOP binds before the ex2 unit at 152 x 16 x 2.07 GHz over 45 exps."""
+    source-pixel: the FP32 pipe at 152 SMs x 128 lanes x 2 x 2.07 GHz over the item
+    kernel's 3 (67 + 19 x 14) + 114 = 1,113 FLOP binds before the ex2 unit at 152 x 16 x
+    2.07 GHz over 45 exps; the other covering sources' values add 3 (21 + 5 x 14) + 32 =
+    305 FLOP and 45 exps per (pixel, other source)."""
     import bench
-    assert bench.fused_flops_per_source_pixel(3, 6, 8) == 1541
+    assert bench.items_flops_per_source_pixel(3, 6, 8) == 1113
+    assert bench.other_eval_flops(3, 6, 8) == 305
     b = bench.step_bound(3, 6, 8, 1.0e10)
-    assert abs(b["evals_per_s_fp32_pipe"] - 152 * 128 * 2 * 2.07e9 / 1541) < 1.0
+    assert abs(b["evals_per_s_fp32_pipe"] - 152 * 128 * 2 * 2.07e9 / 1113) < 1.0
     assert abs(b["evals_per_s_ex2"] - 152 * 16 * 2.07e9 / 45) < 1.0
     assert b["evals_per_s_bound"] == b["evals_per_s_fp32_pipe"]
     assert abs(b["frac"] - 1.0e10 / b["evals_per_s_bound"]) < 1e-15
+    b2 = bench.step_bound(3, 6, 8, 1.0e10, 0.1)
+    assert abs(b2["flop_per_source_pixel"] - (1113 + 0.1 * 305)) < 1e-9
 
 
 def test_reference_arm_under_torchrun_prints_once():

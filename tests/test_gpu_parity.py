@@ -86,24 +86,28 @@ def test_edge_cases(cel):
 
 
 def test_autotuned_variants_agree(cel):
-    """Every pixels-per-thread variant the autotuner may pick gives the oracle's answer
-    within the FP32 tolerances, and the tuner returns one of them."""
+    """Every register budget of the item kernel gives the oracle's value and gradient, and
+    every map-pass kernel code the oracle's gradient through the Hessian path, within the
+    FP32 tolerances; the tuner returns one of them."""
     prob = synth.config(2)
     orc = Oracle(prob)
     o_tot, _ = orc.elbo(prob.theta)
     _, o_g, _ = orc.derivs(prob.theta)
     P = cel.Problem(prob)
-    for ppt in (1, 2, 3, 4, 5, 6, 7):
-        for cap, sep in ((0, 0), (3, 1)):
-            P.set_tuning(ppt, ppt, cap, sep)
-            tot, loc, g = P.elbo_grad(prob.theta, precision=cel.FP32)
-            assert rel(tot, o_tot) <= 1e-5 and rel_l2(g, o_g) <= 1e-4, (ppt, cap, sep)
-    c, a, cap, sep = P.autotune(prob.theta)
-    assert c in range(1, 8) and a in range(1, 8) and cap in (0, 8, 7, 6, 5, 4, 3) and sep in (0, 1)
+    for code in (1, 2, 3, 4, 5):
+        P.set_tuning(2, code)
+        tot, loc, g = P.elbo_grad(prob.theta, precision=cel.FP32)
+        assert rel(tot, o_tot) <= 1e-5 and rel_l2(g, o_g) <= 1e-4, code
+    for code in (1, 2, 3, 4, 5, 6, 7):
+        P.set_tuning(code, 0)
+        _, g, _ = P.hess(prob.theta, precision=cel.FP32)
+        assert rel_l2(g, o_g) <= 1e-4, code
+    c, i = P.autotune(prob.theta)
+    assert c in range(1, 8) and i in range(1, 6)
     with pytest.raises(cel.CelesteError):
-        P.set_tuning(2, 2, 9)
+        P.set_tuning(2, 6)
     with pytest.raises(cel.CelesteError):
-        P.set_tuning(2, 2, 0, 2)
+        P.set_tuning(8, 0)
     P.close()
 
 

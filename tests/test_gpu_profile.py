@@ -34,7 +34,7 @@ def test_profiled_runs_match_and_report_the_stages(cel, cfg):
         np.testing.assert_array_equal(got[1], ref[1])
         np.testing.assert_array_equal(got[2], ref[2])
     assert set(stages[False]) == set(stages[True])
-    assert {"prep", "finalize"} <= set(stages[True])
+    assert {"items"} <= set(stages[True])
     for v in stages[True].values():
         assert v[0] > 0 and v[1] >= 1
     with pytest.raises(cel.CelesteError) as e:
