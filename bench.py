@@ -408,7 +408,9 @@ def main():
     achieved = achieved_k[dom]
     traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if args.workload == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp32, "traffic": traffic, "kernel": "items (FP32 value + gradient)",
+                "frac": achieved / peak_fp32, "traffic": traffic,
+                "kernel": "items: k_items, the FP32 value + gradient pass over every item (the tables "
+                          "and KL terms, and the per-source epilogues, are the stages 'tables' and 'finish')",
                 "flop_per_launch": work[dom],
                 "flop_per_source_pixel": items_flops_per_source_pixel(npsf, ne, nd),
                 "other_evals": split["other_evals"], "flop_per_other_eval": other_eval_flops(npsf, ne, nd),

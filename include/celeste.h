@@ -320,13 +320,14 @@ celeste_status celeste_grad_device(celeste_problem* prob, const double* d_theta,
  *     launches: 1, 2, 4 pixels per thread (CTAs of 256, 128, 64 threads over the same
  *     256-pixel work items), 3, 5 two or four pixels per thread in packed FP32x2
  *     instructions, 6, 7 the same as persistent CTAs taking items from a work queue.
- *   items_code: the register budget of the FP32 value / gradient item kernel (codes
- *     1 .. 5: at most 128, 96, 80, 72, 64 registers per thread, i.e. 4 .. 8 CTAs of 128
- *     threads per SM), timed on whole FP32 value + gradient evaluations as the calls run
- *     them (the captured CUDA graph).
+ *   items_code: the variant of the persistent FP32 value / gradient item kernel (CTAs
+ *     of four compute warps and one producer warp), as (pixels per thread, CTAs per SM,
+ *     unroll of the loop over profile-component pairs): 1 (2, 2, 7), 2 (3, 2, 3),
+ *     3 (2, 3, 2), 4 (3, 2, 7), 5 (3, 2, 2); timed on whole FP32 value + gradient
+ *     evaluations as the calls run them (the captured CUDA graph).
  * The choices are kept for later FP32 calls and returned (nullable outputs);
  * celeste_set_tuning restores them (contrib 0 .. 7, items 0 .. 5; 0 = the built-in
- * defaults 2 and 3; anything else is CELESTE_ERR_ARG).
+ * defaults 2 and 1; anything else is CELESTE_ERR_ARG).
  */
 celeste_status celeste_autotune(celeste_problem* prob, const double* theta, int32_t reps,
                                 int32_t* contrib_code, int32_t* items_code);
@@ -347,7 +348,7 @@ celeste_status celeste_device_status(celeste_problem* prob);
  * identical to the concurrent order's); on = 0: off; anything else is CELESTE_ERR_ARG.
  * celeste_profile_read waits for the
  * recorded events, writes up to max_kernels entries (names[k*32 .. k*32+31]
- * NUL-terminated, total milliseconds, launch count), resets the accumulators and
+ * NUL-terminated, total milliseconds, kernel launches), resets the accumulators and
  * returns the number of distinct stages (negative status on error).
  */
 celeste_status celeste_profile_enable(celeste_problem* prob, int32_t on);

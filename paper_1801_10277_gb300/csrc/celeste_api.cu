@@ -128,15 +128,16 @@ cudaEvent_t take_event(celeste_problem* pr) {
     return e;
 }
 
-// Run a launcher; with profiling on, bracket it with events on the launch stream.
+// Run a launcher of n_kernels kernels; with profiling on, bracket it with events on the
+// launch stream.
 template <class F>
-cudaError_t timed(celeste_problem* pr, const char* name, cudaStream_t st, F&& f) {
+cudaError_t timed(celeste_problem* pr, const char* name, cudaStream_t st, F&& f, int n_kernels = 1) {
     if (!pr->profile) return f();
     cudaEvent_t a = take_event(pr), b = take_event(pr);
     cudaEventRecord(a, st);
     cudaError_t e = f();
     cudaEventRecord(b, st);
-    pr->pending.push_back({name, a, b});
+    pr->pending.push_back({name, a, b, n_kernels});
     return e;
 }
 
@@ -179,17 +180,17 @@ celeste_status run(celeste_problem* pr, const double* d_theta, int precision, in
     CEL_CUDA(cudaSetDevice(pr->device));
     pr->last_stream = st;
     const DevProblem& P = pr->P;
-    // FP32 value / gradient: items whose pixels only their own patch covers take the fused
-    // map + adjoint pass on the side stream, concurrently with the critical path on st
-    // (map pass over the other items -> their gather + adjoint -> per-source epilogue);
-    // the total (per-item ll sums - KL) follows on the side stream.  The two streams write
-    // disjoint pixels and items, so the results do not depend on how the kernels
-    // interleave.
-    const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.sitems;
+    // FP32 value / gradient: the item kernels (item_kernels.cu) -- tables and KL terms,
+    // the items (a programmatic dependent of the tables), the per-source epilogues and
+    // the total (a programmatic dependent of the items); timed as three stages when
+    // profiling.  FP64 and the Hessian: the map / gather / adjoint pipeline below.
+    const bool fused = precision == CELESTE_FP32_ACC64 && mode != MODE_HESS && P.ztasks;
     if (fused) {
-        // tables -> items (+ KL) -> per-source epilogue and total; each a programmatic
-        // dependent launch of its predecessor
-        CEL_CUDA(timed(pr, "items", st, [&] { return launch_items(P, mode, st, d_theta, d_local, d_grad, d_total); }));
+        static const char* const names[3] = {"tables", "items", "finish"};
+        for (int stage = 0; stage < 3; ++stage)
+            CEL_CUDA(timed(pr, names[stage], st, [&] {
+                return launch_items_stage(P, stage, mode, st, d_theta, d_local, d_grad, d_total);
+            }));
         return CELESTE_OK;
     }
     CEL_CUDA(timed(pr, "prep", st, [&] { return launch_prep(P, d_theta, precision, st); }));
@@ -478,10 +479,15 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
                         c[(size_t)(g.y0 + yy) * im[g.img].W + g.x0 + xx] == 1;
         }
     }
-    // the split item set: per source, per patch, the singly covered pixels (fused pass,
-    // items of <= FUSED_CHUNK pixels) then the multiply covered ones (items of <= CHUNK)
-    std::vector<WorkItem> sitems;
-    std::vector<int32_t> spix, sitem_off(1, 0), spatch_off(1, 0);
+    // The FP32 value / gradient kernel's items: per source, per patch, the patch's pixels
+    // with the multiply covered ones first (row-major), then the singly covered ones, cut
+    // into ceil(n / ZIMAX) items of near-equal size.
+    struct SItem {
+        int32_t patch, src, n, nm;
+        int64_t q0;   // first pixel (spix)
+    };
+    std::vector<SItem> sitems;
+    std::vector<int32_t> spix, sitem_off(1, 0);
     int n_smulti = 0;
     spix.reserve((size_t)n_sp);
     int64_t sp_single = 0;
@@ -489,19 +495,22 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
         for (int p = patch_offsets[s]; p < patch_offsets[s + 1]; ++p) {
             const PatchGeo& g = geo[p];
             const uint8_t* f = single.data() + g.sp_off;
-            for (int pass = 0; pass < 2; ++pass) {
-                const int first = (int)spix.size();
-                for (int q = 0; q < g.w * g.h; ++q)
-                    if ((f[q] != 0) == (pass == 0)) spix.push_back(((q / g.w) << 16) | (q % g.w));
-                const int cnt = (int)spix.size() - first;
-                const int ch = pass == 0 ? FUSED_CHUNK : CHUNK;
-                for (int o = 0; o < cnt; o += ch) {
-                    sitems.push_back({p, first + o, std::min(ch, cnt - o), s});
-                    if (pass == 1) ++n_smulti;
-                }
-                if (pass == 0) sp_single += cnt;
+            const int64_t first = (int64_t)spix.size();
+            const int npx = g.w * g.h;
+            for (int q = 0; q < npx; ++q)
+                if (!f[q]) spix.push_back(((q / g.w) << 16) | (q % g.w));
+            const int nm_all = (int)((int64_t)spix.size() - first);
+            for (int q = 0; q < npx; ++q)
+                if (f[q]) spix.push_back(((q / g.w) << 16) | (q % g.w));
+            sp_single += npx - nm_all;
+            const int k = (npx + ZIMAX - 1) / ZIMAX, base = npx / k, rem = npx % k;
+            for (int j = 0, o = 0; j < k; ++j) {
+                const int n = base + (j < rem ? 1 : 0);
+                const int nm = std::max(0, std::min(n, nm_all - o));
+                sitems.push_back({p, s, n, nm, first + o});
+                if (nm > 0) ++n_smulti;
+                o += n;
             }
-            spatch_off.push_back((int32_t)sitems.size());
         }
         sitem_off.push_back((int32_t)sitems.size());
     }
@@ -538,80 +547,108 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
                 }
         }
     }
-    // the item kernel's lists: per split item the other patches covering any of its pixels
-    // (ascending patch id = ascending source id within an image), and the launch order
-    // (items with other covering patches first, most covering patches first)
+    // Per item, the other patches covering any of its multiply covered pixels (ascending
+    // patch id = ascending source id within an image) and its cost: its pixels plus about
+    // a third of a pixel per (64-pixel warp chunk, other patch touching the chunk).
     std::vector<int32_t> zc_off(1, 0), zc_list, zorder;
     int64_t other_evals = 0;   // (pixel, other covering patch) pairs the item kernel evaluates
+    std::vector<double> zcost(sitems.size());
     {
-        std::vector<int32_t> cand;
+        std::vector<int32_t> cand, chunk;
         for (size_t i = 0; i < sitems.size(); ++i) {
-            const WorkItem& it = sitems[i];
+            const SItem& it = sitems[i];
             const PatchGeo& g = geo[it.patch];
             const ImgMeta& M = im[g.img];
             cand.clear();
-            for (int l = 0; l < it.n; ++l) {
-                const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
-                if (single[(size_t)g.sp_off + (size_t)yy * g.w + xx]) continue;
-                const int gx = g.x0 + xx, gy = g.y0 + yy;
-                const int tid = tile_grid[M.tg_off + (size_t)(gy / TILE) * M.tgw + gx / TILE];
-                if (tid < 0) continue;
-                const Tile& tl = tiles[tid];
-                for (int e = 0; e < tl.list_n; ++e) {
-                    const int pe = tile_list[tl.list_off + e];
-                    if (pe == it.patch) continue;
-                    const PatchGeo& G = geo[pe];
-                    if (gx >= G.x0 && gx < G.x0 + G.w && gy >= G.y0 && gy < G.y0 + G.h) {
-                        cand.push_back(pe);
-                        ++other_evals;
+            double extra = 0.0;
+            for (int c0 = 0; c0 < it.nm; c0 += 64) {
+                chunk.clear();
+                for (int l = c0; l < std::min(it.nm, c0 + 64); ++l) {
+                    const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
+                    const int gx = g.x0 + xx, gy = g.y0 + yy;
+                    const int tid = tile_grid[M.tg_off + (size_t)(gy / TILE) * M.tgw + gx / TILE];
+                    if (tid < 0) continue;
+                    const Tile& tl = tiles[tid];
+                    for (int e = 0; e < tl.list_n; ++e) {
+                        const int pe = tile_list[tl.list_off + e];
+                        if (pe == it.patch) continue;
+                        const PatchGeo& G = geo[pe];
+                        if (gx >= G.x0 && gx < G.x0 + G.w && gy >= G.y0 && gy < G.y0 + G.h) {
+                            chunk.push_back(pe);
+                            ++other_evals;
+                        }
                     }
                 }
+                std::sort(chunk.begin(), chunk.end());
+                chunk.erase(std::unique(chunk.begin(), chunk.end()), chunk.end());
+                extra += 64.0 * (double)chunk.size();
+                cand.insert(cand.end(), chunk.begin(), chunk.end());
             }
             std::sort(cand.begin(), cand.end());
             cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
             zc_list.insert(zc_list.end(), cand.begin(), cand.end());
             zc_off.push_back((int32_t)zc_list.size());
+            zcost[i] = (double)it.n + 0.3 * extra;
         }
-        // the most expensive items first (pixels, each other covering patch adding about a
-        // third of a pixel's cost), so the last CTAs to start are short ones
-        auto cost = [&](int32_t i) { return (double)sitems[i].n * (1.0 + 0.35 * (zc_off[i + 1] - zc_off[i])); };
+        // the most expensive items first, so the last items taken are short ones
         for (size_t i = 0; i < sitems.size(); ++i) zorder.push_back((int32_t)i);
-        std::stable_sort(zorder.begin(), zorder.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+        std::stable_sort(zorder.begin(), zorder.end(), [&](int32_t a, int32_t b) { return zcost[a] > zcost[b]; });
     }
-    // flat item records in launch order, candidate records, and the items' pixels gathered
-    // in item order (counts and sky), so that an item needs one record load before its data
-    std::vector<ZItem> zitems;
+    // The work queue: the items in cost order, each with the patches of its first ZMAXC
+    // candidates; and the order in which the table kernel builds the patches' tables (by
+    // the first item that reads each).
+    std::vector<ZTask> ztasks;
     std::vector<ZCand> zcands;
-    std::vector<float2> zxs(spix.size());
-    for (size_t j = 0, i = 0; i < sitems.size(); ++i) {
-        const WorkItem& it = sitems[i];
-        const PatchGeo& g = geo[it.patch];
-        const ImgMeta& M = im[g.img];
-        const float* px = imgs[g.img].pixels;
-        const float* sm = imgs[g.img].sky_map;
-        for (int l = 0; l < it.n; ++l, ++j) {
-            const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
-            const size_t m = (size_t)(g.y0 + yy) * M.W + (g.x0 + xx);
-            zxs[it.q0 + l] = make_float2(px[m], sm ? sm[m] : (float)M.sky);
+    std::vector<int32_t> ztorder;   // the table kernel's order of the patches
+    std::vector<float4> zpx(spix.size());
+    {
+        const int n_it = (int)sitems.size();
+        const int64_t never = INT64_MAX / 4;
+        std::vector<int64_t> pneed((size_t)n_patch, never);
+        for (int j = 0; j < n_it; ++j) {
+            const int i = zorder[j];
+            const SItem& it = sitems[i];
+            pneed[it.patch] = std::min<int64_t>(pneed[it.patch], j);
+            for (int e = zc_off[i]; e < zc_off[i + 1]; ++e)
+                pneed[zc_list[e]] = std::min<int64_t>(pneed[zc_list[e]], j);
         }
-    }
-    for (const int32_t i : zorder) {
-        const WorkItem& it = sitems[i];
-        const PatchGeo& g = geo[it.patch];
-        ZItem z{};
-        z.patch = it.patch;
-        z.n = it.n;
-        z.out = i;
-        z.src = g.src;
-        z.pix = it.q0;
-        z.c0 = (int32_t)zcands.size();
-        const int nc = zc_off[i + 1] - zc_off[i];
-        z.nc_npsf = nc | (im[g.img].npsf << 24);
-        for (int e = zc_off[i]; e < zc_off[i + 1]; ++e) {
-            const PatchGeo& G = geo[zc_list[e]];
-            zcands.push_back(ZCand{zc_list[e], G.x0 - g.x0, G.y0 - g.y0, G.w, G.h, G.src, im[G.img].npsf, 0});
+        for (int p = 0; p < n_patch; ++p) ztorder.push_back(p);
+        std::stable_sort(ztorder.begin(), ztorder.end(), [&](int32_t a, int32_t b) { return pneed[a] < pneed[b]; });
+        for (int j = 0; j < n_it; ++j) {
+            ZTask t{};
+            t.kind = ZT_ITEM;
+            t.index = j;
+            for (int e = 0; e < ZMAXC; ++e) t.cand[e] = -1;
+            const int i = zorder[j];
+            const SItem& it = sitems[i];
+            const PatchGeo& g = geo[it.patch];
+            const int nc = zc_off[i + 1] - zc_off[i];
+            t.item.patch = it.patch;
+            t.item.n_nm = it.n | (it.nm << 16);
+            t.item.out = i;
+            t.item.src = it.src;
+            t.item.pix = it.q0;
+            t.item.c0 = (int32_t)zcands.size();
+            t.item.nc_npsf = nc | (im[g.img].npsf << 24);
+            for (int e = zc_off[i]; e < zc_off[i + 1]; ++e) {
+                const PatchGeo& G = geo[zc_list[e]];
+                if (e - zc_off[i] < ZMAXC) t.cand[e - zc_off[i]] = zc_list[e];
+                zcands.push_back(ZCand{zc_list[e], G.x0 - g.x0, G.y0 - g.y0, G.w, G.h, G.src, im[G.img].npsf, 0});
+            }
+            ztasks.push_back(t);
         }
-        zitems.push_back(z);
+        // pixel records in item order: (column, row in the patch, counts, sky)
+        for (const SItem& it : sitems) {
+            const PatchGeo& g = geo[it.patch];
+            const ImgMeta& M = im[g.img];
+            const float* px = imgs[g.img].pixels;
+            const float* sm = imgs[g.img].sky_map;
+            for (int l = 0; l < it.n; ++l) {
+                const int xx = spix[it.q0 + l] & 0xffff, yy = spix[it.q0 + l] >> 16;
+                const size_t m = (size_t)(g.y0 + yy) * M.W + (g.x0 + xx);
+                zpx[it.q0 + l] = make_float4((float)xx, (float)yy, px[m], sm ? sm[m] : (float)M.sky);
+            }
+        }
     }
     // neighbours
     if (nbr_offsets[0] != 0) return fail(CELESTE_ERR_ARG, "nbr_offsets[0] must be 0");
@@ -678,8 +715,8 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     DevProblem& P = pr->P;
     P.n_img = n_img; P.n_src = n_src; P.n_patch = n_patch; P.n_item = (int)items.size();
     P.n_tile = (int)tiles.size(); P.npsf_max = npsf_max; P.nprof = model->n_exp + model->n_dev;
-    P.model_npe = (model->n_exp + 1) / 2;
-    P.model_npd = (model->n_dev + 1) / 2;
+    P.model_ne = model->n_exp;
+    P.model_nd = model->n_dev;
     P.n_px = n_px; P.n_sp = n_sp;
     P.max_src_patches = 0;
     for (int s = 0; s < n_src; ++s)
@@ -716,24 +753,30 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     if ((st = dupload(pr, &d_single, single.data(), single.size()))) return bail(st);
     P.single = d_single;
     if (!sitems.empty()) {
-        WorkItem* d_sit = nullptr;
-        int32_t *d_spix = nullptr, *d_soff = nullptr, *d_spo = nullptr;
-        if ((st = dupload(pr, &d_sit, sitems.data(), sitems.size()))) return bail(st);
-        if ((st = dupload(pr, &d_spix, spix.data(), spix.size()))) return bail(st);
-        if ((st = dupload(pr, &d_soff, sitem_off.data(), sitem_off.size()))) return bail(st);
-        if ((st = dupload(pr, &d_spo, spatch_off.data(), spatch_off.size()))) return bail(st);
-        P.sitems = d_sit; P.spix = d_spix; P.sitem_off = d_soff; P.spatch_off = d_spo;
-        ZItem* d_zi = nullptr;
+        int32_t* d_soff = nullptr;
+        ZBuild* d_tord = nullptr;
+        ZTask* d_zt = nullptr;
         ZCand* d_zc = nullptr;
-        float2* d_zxs = nullptr;
-        if ((st = dupload(pr, &d_zi, zitems.data(), zitems.size()))) return bail(st);
-        if ((st = dupload(pr, &d_zc, zcands.data(), zcands.size()))) return bail(st);
-        if ((st = dupload(pr, &d_zxs, zxs.data(), zxs.size()))) return bail(st);
-        P.zitems = d_zi; P.zcands = d_zc; P.zxy = d_spix; P.zxs = d_zxs;
+        float4* d_zpx = nullptr;
+        if ((st = dupload(pr, &d_soff, sitem_off.data(), sitem_off.size()))) return bail(st);
+        // build records from the final patch geometry (a patch with its own linearised map
+        // refers to the image copy that carries it)
+        std::vector<ZBuild> zb;
+        for (const int32_t p : ztorder) zb.push_back(ZBuild{p, geo[p].img, geo[p].src, geo[p].x0, geo[p].y0, {0, 0, 0}});
+        if ((st = dupload(pr, &d_tord, zb.data(), zb.size()))) return bail(st);
+        if ((st = dupload(pr, &d_zt, ztasks.data(), ztasks.size()))) return bail(st);
+        if (!zcands.empty() && (st = dupload(pr, &d_zc, zcands.data(), zcands.size()))) return bail(st);
+        if ((st = dupload(pr, &d_zpx, zpx.data(), zpx.size()))) return bail(st);
+        P.sitem_off = d_soff;
+        P.ztorder = d_tord;
+        P.ztasks = d_zt;
+        P.n_task = (int32_t)ztasks.size();
+        P.zcands = d_zc;
+        P.zpx = d_zpx;
         P.n_sitem = (int)sitems.size();
         P.n_smulti = n_smulti;
         void* q;
-        if ((st = dalloc(pr, &q, sizeof(double) * NZPART * (size_t)P.n_sitem))) return bail(st);
+        if ((st = dalloc(pr, &q, sizeof(double) * ZPCOLS * (size_t)P.n_sitem))) return bail(st);
         P.spart = (double*)q;
         const int n_grp = (n_src + ZF_GROUP - 1) / ZF_GROUP;
         if ((st = dalloc(pr, &q, sizeof(double) * (size_t)n_grp))) return bail(st);
@@ -742,20 +785,10 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
         P.zf_done = (int32_t*)q;
         if (cudaMemset(P.zf_done, 0, sizeof(int32_t) * ((size_t)n_grp + 1)) != cudaSuccess)
             return bail(fail(CELESTE_ERR_CUDA, "memset"));
-        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_src + 1)))) return bail(st);
-        P.zsrc_done = (int32_t*)q;
-        if (cudaMemset(P.zsrc_done, 0, sizeof(int32_t) * ((size_t)n_src + 1)) != cudaSuccess)
-            return bail(fail(CELESTE_ERR_CUDA, "memset"));
-        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_patch + 1)))) return bail(st);
+        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_patch + 2)))) return bail(st);
         P.zready = (int32_t*)q;
-
-        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
-        P.sitem_ll = (double*)q;
-        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)P.n_sitem))) return bail(st);
-        P.sitem_own = (double*)q;
-        if (cudaMemset(P.sitem_ll, 0, sizeof(double) * P.n_sitem) != cudaSuccess ||
-            cudaMemset(P.sitem_own, 0, sizeof(double) * P.n_sitem) != cudaSuccess)
-            return bail(fail(CELESTE_ERR_CUDA, "memset"));
+        if ((st = dalloc(pr, &q, sizeof(float4) * NP * (size_t)n_patch))) return bail(st);
+        P.zchain = (float4*)q;
     }
     pr->sp_single = sp_single;
     pr->other_evals = other_evals;
@@ -799,6 +832,10 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     if ((st = dalloc(pr, &p, 2 * sizeof(int32_t)))) return bail(st);
     P.queue = (int32_t*)p;
     prime_persistent_grids();
+    {
+        const cudaError_t pe = prime_items_kernels();
+        if (pe != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "item kernel set-up: %s", cudaGetErrorString(pe)));
+    }
     if (cudaMemset(P.queue, 0, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(CELESTE_ERR_CUDA, "memset"));
     if ((st = dalloc(pr, &p, sizeof(int32_t)))) return bail(st);
     P.status = (int32_t*)p;
@@ -909,7 +946,7 @@ int32_t celeste_profile_read(celeste_problem* pr, int32_t max_kernels, char* nam
             pr->launches.push_back(0);
         }
         pr->ms[k] += t;
-        pr->launches[k] += 1;
+        pr->launches[k] += r.n_kernels;
         pr->pool.push_back(r.a);
         pr->pool.push_back(r.b);
     }
@@ -944,11 +981,13 @@ celeste_status celeste_grad_device(celeste_problem* pr, const double* d_theta, i
     // the item kernel of celeste_elbo_grad runs again (it recomputes its tables, E and Var
     // from theta; the KL of the preceding forward call is reused), so the gradient is
     // bit-identical to the one-call gradient.
-    const bool fused = precision == CELESTE_FP32_ACC64 && P.sitems;
+    const bool fused = precision == CELESTE_FP32_ACC64 && P.ztasks;
     if (fused) {
-        CEL_CUDA(timed(pr, "items", st, [&] {
-            return launch_items(P, MODE_GRAD, st, d_theta, d_elbo_per_source, d_grad, nullptr);
-        }));
+        static const char* const names[3] = {"tables", "items", "finish"};
+        for (int stage = 0; stage < 3; ++stage)
+            CEL_CUDA(timed(pr, names[stage], st, [&] {
+                return launch_items_stage(P, stage, MODE_GRAD, st, d_theta, d_elbo_per_source, d_grad, nullptr);
+            }));
         return CELESTE_OK;
     }
     CEL_CUDA(timed(pr, "adjoint", st, [&] { return launch_adjoint(P, precision, MODE_GRAD, st); }));
@@ -997,8 +1036,8 @@ celeste_status celeste_autotune(celeste_problem* pr, const double* theta, int32_
     P.tune_contrib = pick_c;
     // the item kernel's register budget (codes 1 .. 5), timed on whole value + gradient
     // evaluations as the calls run them (the captured graph)
-    int pick_i = 3;
-    if (P.sitems) {
+    int pick_i = 1;
+    if (P.ztasks) {
         float best = 1e30f;
         double* o = pr->d_out;
         for (int code = 1; code <= 5 && e == cudaSuccess; ++code) {

@@ -32,10 +32,11 @@ constexpr int NYH = NY * (NY + 1) / 2;   // packed upper triangle of the y-Hessi
 // [1..NY] gradient wrt y, [1+NY ..) packed y-Hessian.
 constexpr int PART_LL = 0, PART_G = 1, PART_H = 1 + NY, PART_TH = 1;
 constexpr int NPART = 1 + NY + NYH;
-// Split-item partial record of the FP32 value / gradient path (doubles): [0] ll,
-// [1..NY] d ll / d y; the chain rule runs once per patch in the per-source epilogue.
-constexpr int NZPART = 1 + NY;
-constexpr int ZF_GROUP = 128;   // sources per first-level group of the total
+// Per-item partial record of the FP32 value / gradient kernel (doubles): [0] ll of the
+// item's pixels, [1] ll of the pixels the item owns (its share of the total), [2 .. 2 + NP)
+// d ll / d theta of its source (the patch's chain rule applied per item).
+constexpr int ZPCOLS = 2 + NP;
+constexpr int ZF_GROUP = 1024;   // sources per first-level group of the total
 
 // Mixture table of one (source, patch), in units of the pixel precision R:
 //   header [0..7]: a0 a1 E[l|star] E[l^2|star] E[l|gal] E[l^2|gal] iota 0
@@ -50,11 +51,13 @@ constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_
 constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
 
-// floats of one patch's whitened-frame table (item_kernels.cu): header 32, per PSF
-// component 20 + 20 per pair of profile components (each group padded to even)
-constexpr int ZFULL_FLOATS = 32 + MAXPSF * (20 + ((MAXPROF + 2) / 2) * 20);
+// floats of one patch's whitened-frame table (item_kernels.cu): a value part (header 16,
+// per PSF component 8 + 8 per pair of profile components) and a gradient part (per PSF
+// component 12 + 12 per pair); each profile group padded to an even count
+constexpr int ZFULL_FLOATS = 16 + MAXPSF * (8 + ((MAXPROF + 2) / 2) * 8) + MAXPSF * (12 + ((MAXPROF + 2) / 2) * 12);
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)
-constexpr int FUSED_CHUNK = 1024;  // pixels per split item of singly covered pixels (one CTA of the item kernel)
+constexpr int ZIMAX = 512;   // pixels per item of the FP32 value / gradient kernel
+constexpr int ZMAXC = 4;     // other covering patches staged with such an item (more are read in place)
 constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
 
 struct ImgMeta {
@@ -89,19 +92,36 @@ struct WorkItem {
     int32_t patch, q0, n, src;
 };
 
-// A split item of the FP32 item kernel, in launch order: its patch (table index), pixel
-// count, partial index (the split item), source, first entry of its gathered pixels, and
-// the other patches covering its pixels (zcands[c0 .. c0 + nc)); npsf of its image.
+// One item of the FP32 value / gradient kernel: n <= ZIMAX consecutive pixel records of
+// one patch (from pix; the patch's multiply covered pixels come first, nm of them), its
+// partial record (out), source, the other patches covering any of its multiply covered
+// pixels (zcands[c0 .. c0 + nc), ascending patch id) and npsf of its image.
 struct ZItem {
-    int32_t patch, n, out, src;
+    int32_t patch, n_nm, out, src;   // n_nm = n | nm << 16
     int64_t pix;
-    int32_t c0, nc_npsf;     // nc | npsf << 24
+    int32_t c0, nc_npsf;             // nc | npsf << 24
+};
+
+// One entry of the FP32 value / gradient kernel's queue: an item (kind ZT_ITEM) with the
+// patches of its first ZMAXC candidates, so that one 64-byte load gives everything the
+// item's copies need; ZT_END marks the end of the queue.
+enum : int32_t { ZT_ITEM = 0, ZT_END = 3 };
+struct ZTask {
+    int32_t kind, index, pad0, pad1;
+    ZItem item;
+    int32_t cand[ZMAXC];
 };
 
 // Another patch covering pixels of a multiply covered item: its table index, its origin
 // relative to the item's patch origin, size, source and PSF component count.
 struct ZCand {
     int32_t patch, dx, dy, w, h, src, npsf, pad;
+};
+
+// What the table kernel needs of a patch to build its table: the patch, its image and
+// source, and its origin in the image.
+struct ZBuild {
+    int32_t patch, img, src, x0, y0, pad[3];
 };
 
 struct Tile {
@@ -240,34 +260,27 @@ struct DevProblem {
     int32_t* done;           // k_finalize completion counter, 0 between launches
     double* tot_part;        // [64] k_total slice sums
     int32_t* tot_done;       // k_total completion counter, 0 between launches
-    // The split item set of the FP32 value / gradient path: each patch's pixels split into
-    // the singly covered ones (items of <= FUSED_CHUNK pixels) and the others
-    // (items of <= CHUNK pixels, one CTA each); WorkItem.q0 indexes spix, which holds
-    // patch-relative pixel indices; a source's split items are contiguous (sitem_off).
-    // Nullable (no split set: sitems null).
-    const WorkItem* sitems;
-    const int32_t* spix;
+    // The FP32 value / gradient kernel's work (item_kernels.cu): a source's items are
+    // contiguous in partial order (sitem_off); ztasks null when there is none.
     const int32_t* sitem_off;    // [n_src + 1]
-    int n_sitem, n_smulti;       // all split items; those of multiply covered pixels
-    const int32_t* spatch_off;   // [n_patch + 1] split items of each patch (contiguous)
-    double* spart;               // [n_sitem][NZPART] partials of the split items: ll, d ll / d y
+    int n_sitem, n_smulti;       // items; those holding multiply covered pixels
+    double* spart;               // [n_sitem][ZPCOLS] per-item partials
     double* zf_grp_total;        // per group of ZF_GROUP sources: their share of the total
     int32_t* zf_done;            // [groups + 1] completion counters, 0 between launches
-    double* sitem_ll;            // ll of a singly covered item (0 for the others)
-    double* sitem_own;           // ll of the multiply covered pixels an item owns (the first
-                                 // covering patch owns a pixel; 0 for singly covered items)
     const int32_t* src_active;   // per source: 0 = skip its work (the fit's converged batch
                                  // sources); nullable = every source works
     // the FP32 value / gradient item kernel (item_kernels.cu)
-    float* ztbl;                 // [n_patch][ZFULL] whitened-frame tables (FP32)
-    int32_t* zready;             // [n_patch] table ready flags (reset before each launch)
-    int32_t* zsrc_done;          // [n_src] arrivals of each source's items and KL warp, 0 between launches
-    const ZItem* zitems;         // [n_sitem] in launch order (multiply covered items first)
+    const ZTask* ztasks;         // [n_task] the work queue
+    int32_t n_task;
+    const ZBuild* ztorder;       // [n_patch] the patches' build records, in the order the items first read them
     const ZCand* zcands;
-    const int32_t* zxy;          // per split-item pixel (spix order): (row << 16) | column in the patch
-    const float2* zxs;           // per split-item pixel: (counts, sky)
+    const float4* zpx;           // per item pixel: (column, row in the patch, counts, sky)
+    float* ztbl;                 // [n_patch][ZFULL_FLOATS] whitened-frame tables (FP32)
+    float4* zchain;              // [n_patch][NP] chain-rule records of the patches
+    int32_t* zready;             // [n_patch] table ready flags, then the queue counter and the
+                                 // count of built tables (reset before each launch)
     int32_t tune_items;          // item kernel variant: 1 one pixel per thread, else two
-    int32_t model_npe, model_npd;   // exp / dev profile components in pairs (rounded up)
+    int32_t model_ne, model_nd;     // exp / dev profile components of the model
     int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
                              // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;
@@ -282,6 +295,7 @@ celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const 
                                                           double*, double*));
 
 void prime_persistent_grids();
+cudaError_t prime_items_kernels();
 // total = tile ll sums + item ll sums - KL (after the gather and every item ll)
 cudaError_t launch_total(const DevProblem& P, double* d_total, cudaStream_t st);
 // tables (and, with_kl, the KL value / gradient and the domain check) of every source
@@ -290,12 +304,16 @@ cudaError_t launch_prep(const DevProblem& P, const double* d_theta, int precisio
 // contrib / adjoint over the items idx[0 .. n) (idx null: items 0 .. n; n < 0: all items)
 cudaError_t launch_contrib(const DevProblem& P, int precision, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);
-// The FP32 value (MODE_LL) or value + gradient (MODE_GRAD) evaluation in one launch
-// (item_kernels.cu): the patches' whitened-frame tables, the KL value / gradient and the
-// domain check of theta, every split item, and the per-source epilogue (local objective,
-// gradient; each nullable) and the total (nullable)
+// The FP32 value (MODE_LL) or value + gradient (MODE_GRAD) evaluation (item_kernels.cu):
+// the patches' whitened-frame tables, the KL value / gradient and the domain check of
+// theta, every item, the per-source epilogue (local objective, gradient; each nullable)
+// and the total (nullable); launch_items_stage below launches them one stage at a time
 cudaError_t launch_items(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta, double* d_local,
                          double* d_grad, double* d_total);
+// its three launches one at a time: stage 0 the tables and KL terms (after resetting the
+// ready flags), 1 the items, 2 the per-source epilogues and the total
+cudaError_t launch_items_stage(const DevProblem& P, int stage, int mode, cudaStream_t st, const double* d_theta,
+                               double* d_local, double* d_grad, double* d_total);
 cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st);
 cudaError_t launch_adjoint(const DevProblem& P, int precision, int mode, cudaStream_t st,
                            const int32_t* idx = nullptr, int n = -1);

@@ -1,6 +1,6 @@
-// FP32 value / gradient pass of the ELBO over the split work items, in the frame that
-// whitens each PSF component (Section III model; Section VI-B: the cost is proportional
-// to active pixel visits).
+// FP32 value / gradient pass of the ELBO over every source's active pixels, in the frame
+// that whitens each PSF component (Section III model; Section VI-B: the cost is
+// proportional to active pixel visits).
 //
 // Frame.  For PSF component k (covariance Sigma_k = L L^T) and the source's galaxy shape G
 // in the patch's pixel frame, let L^-1 G L^-T = Q D Q^T (D = diag(D1, D2) >= 0) and
@@ -13,26 +13,35 @@
 //   dN/dG        = nu_j N T^T (Lam z z^T Lam - Lam) T / 2
 // so per component only the sums over j of N times (1, l1, l2, nu (l1^2 z1^2 - l1),
 // nu l1 l2, nu (l2^2 z2^2 - l2)) are accumulated (ten FMA-pipe operations), and T maps
-// them back once per (pixel, k).  The star's component is the case nu = 0.  The same
-// quantities as the packed kernels of pixel_kernels.cu, rearranged: fewer operations
-// per component.
+// them back once per (pixel, k).  The star's component is the case nu = 0.  Packed FP32x2
+// arithmetic pairs two mixture components per instruction (coefficients of adjacent
+// components side by side in the table).
 //
-// Work.  k_ztab builds every patch's table (one warp per patch, in FP32 with the
-// position in FP64) and the KL of every source (one warp per source).  k_items then takes
-// one CTA per split item (<= 256 pixels of one patch): it copies its patch's table to
-// shared memory, evaluates the mixture and its derivatives at its pixels, and for pixels
-// that other patches also cover (multiply covered items) evaluates those patches' E_s,
-// Var_s too, from their tables, summing E = sky + sum_s E_s and Var = sum_s Var_s in
-// ascending source order (every covering item forms the same sum, bit for bit).  So the
-// value / gradient pass has no map buffers between kernels; a per-source epilogue
-// (k_finalize) and the total follow.  Packed FP32x2 arithmetic pairs two mixture
-// components in one instruction (coefficients of adjacent components side by side in
-// shared memory); FP64 only in the per-item sums.
+// Work.  Three launches.  k_tables builds every patch's table and chain-rule record (one
+// warp per patch, FP32 with the position in FP64), publishing each with a ready flag, and
+// every source's KL terms (one warp per source).  k_items, its programmatic dependent,
+// runs on persistent CTAs of four compute warps and a producer warp that take items from
+// a queue (a global counter over the items in decreasing cost): up to ZIMAX pixels of one
+// patch, the multiply covered ones first.  The producer waits for the tables an item
+// reads and copies its patch's table and chain-rule record, its pixel records and the
+// value records of up to ZMAXC other patches covering its pixels into a shared-memory
+// stage with bulk asynchronous copies (two stages, completing on mbarriers), while the
+// compute warps run the item in the other stage.  They evaluate the mixture and its
+// derivatives at the item's pixels; where other patches cover a pixel, E = sky + sum_s
+// E_s and Var = sum_s Var_s are summed over every covering source in ascending source
+// order (every covering item forms the same sum, bit for bit).  Per warp FP32 sums; the
+// last warp to finish adds the warps in FP64, applies the patch's chain rule dy/dtheta
+// and writes the item's record.  k_finish, k_items' programmatic dependent, runs every
+// source's epilogue (FP64 sums of its item records in order, minus the KL) once the items
+// are done; the last source of each group adds the group, the last group the total.
+// Every wait is bounded (~1 s), after which the kernel records CELESTE_ERR_TIMEOUT and
+// ends.
 #include <math.h>
 
 #include "internal.cuh"
 #include "source_math.cuh"
 #include "epilogue.cuh"
+#include "async_copy.cuh"
 
 namespace cel {
 
@@ -40,37 +49,76 @@ namespace {
 
 constexpr float HL = -0.72134752044448170368f;   // -log2(e) / 2
 
-// unroll factor of the component-pair loop of the gradient pass
-#ifndef CEL_PAIR_UNROLL
-#define CEL_PAIR_UNROLL 7
-#endif
-constexpr int PAIR_UNROLL = CEL_PAIR_UNROLL;
 
-// table layout (floats).  Full record (the item's own patch):
-//   header [0..31]: a0 a1 el0 el20 el1 el21 iota e_dev em0 em1 (1 - e_dev) band A[4]
-//                   dG[3][3] at 16..24 (d(Gxx, Gxy, Gyy) / d(e_axis, e_angle, e_scale))
-//   per PSF component k at ZH + k ZK:
+// Table layout (floats).  Value part (the prefix that another patch's items copy):
+//   header [0..15]: a0 a1 el0 el20 el1 el21 iota e_dev em0 em1 (1 - e_dev) band A[4]
+//   per PSF component k at VH + k VK:
 //     [0..3] -mean_x -mean_y c_star sign   [4..7] T11 T12 T21 T22
-//     [8..16] finishing coefficients of T^T W T (xx: T11^2, 2 T11 T21, T21^2; xy: T11 T12,
-//             T11 T22 + T21 T12, T21 T22; yy: T12^2, 2 T12 T22, T22^2)
-//     component pair q at 20 + 20 q, entries (component 2q, 2q+1) side by side:
-//       [A A B B] [C C U1 U1] [U2 U2 Wa Wa] [Wb Wb W12 W12] [Va Va Vb Vb]
-//       A, B = -log2(e)/2 (l1, l2); C = log2(|alpha_k| w_j) - log2(2 pi sqrt(det C_kj));
-//       U1, U2 = s (l1, l2); Wa, Wb = s nu (l1^2, -l1); W12 = s nu l1 l2; Va, Vb = s nu (l2^2, -l2)
-//       (s = sign(alpha_k) (1 - e_dev) for exp components, sign(alpha_k) e_dev for dev ones)
-//     exp components fill pairs 0 .. npe-1, dev components pairs npe .. npe+npd-1, each
-//     group padded to an even count with a component of weight zero (C = -1e30)
-// Value record (shared-memory copy of another patch covering some of the pixels): the
-// first 16 header floats, per k the first 8 floats, and per pair the first 8 floats
-// [A A B B] [C C U1 U1].
-constexpr int ZH = 32, ZKH = 20, ZPAIR = 20, ZMAXPAIR = (MAXPROF + 2) / 2;
-constexpr int ZK = ZKH + ZMAXPAIR * ZPAIR;
-constexpr int ZFULL = ZH + MAXPSF * ZK;
+//     profile component pair q at VKH + q VPAIR, the entries of components 2q and 2q + 1
+//     side by side (so that one 8-byte half of a 16-byte load is a packed FP32x2 operand):
+//       [A A B B] [C C U1 U1]
+// Gradient part, per PSF component k at VFULL + k GK:
+//     [0..8] finishing coefficients of T^T W T (xx: T11^2, 2 T11 T21, T21^2; xy: T11 T12,
+//            T11 T22 + T21 T12, T21 T22; yy: T12^2, 2 T12 T22, T22^2), [9..11] unused
+//     component pair q at GKH + q GPAIR: [U2 U2 Wa Wa] [Wb Wb W12 W12] [Va Va Vb Vb]
+//   A, B = -log2(e)/2 (l1, l2); C = log2(|alpha_k| w_j) - log2(2 pi sqrt(det C_kj));
+//   U1, U2 = s (l1, l2); Wa, Wb = s nu (l1^2, -l1); W12 = s nu l1 l2; Va, Vb = s nu (l2^2, -l2)
+//   (s = sign(alpha_k) (1 - e_dev) for exp components, sign(alpha_k) e_dev for dev ones);
+//   exp components fill pairs 0 .. npe-1, dev components pairs npe .. npe+npd-1, each
+//   group padded to an even count with a component of weight zero (C = -1e30).
+// Chain-rule record of a patch: per theta column j, (k0, k1, k2, y0 | y1 << 4 | y2 << 8):
+// d y_{y_e} / d theta_j = k_e (unused pairs y = 0, k = 0).
+constexpr int ZMAXPAIR = (MAXPROF + 2) / 2;
+constexpr int VH = 16, VKH = 8, VPAIR = 8, VK = VKH + ZMAXPAIR * VPAIR, VFULL = VH + MAXPSF * VK;
+constexpr int GKH = 12, GPAIR = 12, GK = GKH + ZMAXPAIR * GPAIR, GFULL = MAXPSF * GK;
+constexpr int ZFULL = VFULL + GFULL;
 static_assert(ZFULL == ZFULL_FLOATS, "table size");
-constexpr int VH = 16, VKH = 8, VPAIR = 8;
-constexpr int VK = VKH + ZMAXPAIR * VPAIR;
-constexpr int VFULL = VH + MAXPSF * VK;
-constexpr int ZMAXC = 8;    // other patches' value records staged at once
+static_assert(VFULL % 4 == 0 && ZFULL % 4 == 0, "tables are copied in 16-byte units");
+
+// CTA shape: four compute warps and the producer warp
+constexpr int NWC = 4;
+constexpr int NTC = 32 * NWC;
+constexpr int IT_THREADS = NTC + 32;
+
+// One shared-memory stage (bytes): the item's table, its patch's chain-rule record, its
+// pixel records, and its first ZMAXC candidates' records and value tables.
+constexpr int ST_TBL = 0;
+constexpr int ST_CHAIN = ST_TBL + ZFULL * 4;
+constexpr int ST_PX = ST_CHAIN + NP * 16;
+constexpr int ST_ZC = ST_PX + ZIMAX * 16;
+constexpr int ST_VREC = ST_ZC + ZMAXC * (int)sizeof(ZCand);
+constexpr int ST_BYTES = ST_VREC + ZMAXC * VFULL * 4;
+static_assert(ST_CHAIN % 16 == 0 && ST_PX % 16 == 0 && ST_ZC % 16 == 0 && ST_VREC % 16 == 0 && ST_BYTES % 16 == 0,
+              "bulk copies land on 16-byte boundaries");
+static_assert(sizeof(ZCand) == 32 && sizeof(ZTask) == 64, "record sizes");
+
+constexpr int PG_F = 10;                 // floats of a ProfileGrad
+constexpr int NSUM = 2 + NY;             // per-thread sums: ll, d ll / d y, owned ll
+constexpr int SCR_W = 880;               // per warp of the table kernel: KL arrays (2 x 44 doubles,
+                                         // 44 floats) or the table builder's 96 floats
+constexpr int RED_W = 16;                // floats per warp of an item's warp sums
+
+// the rest of the item kernel's shared memory (bytes), after the two stages
+template <int PX>
+struct Lay {
+    static constexpr int vs = 2 * ST_BYTES;                        // running sums [NSUM][NTC]
+    static constexpr int pg = vs + NSUM * NTC * 4;                 // stashed derivatives [PX PG_F][NTC]
+    static constexpr int red = pg + PX * PG_F * NTC * 4;           // [2][NWC][RED_W] warp sums
+    static constexpr int bar = red + 2 * NWC * RED_W * 4;          // full[2], reduced[2]
+    static constexpr int task = bar + 4 * 8;                       // [2] ZTask
+    static constexpr int cnt = task + 2 * (int)sizeof(ZTask);      // [2] warps done with the item
+    static constexpr int bytes = cnt + 16;
+    static_assert(task % 16 == 0 && bar % 8 == 0, "alignment");
+};
+
+// Registers per thread with MINB CTAs of IT_THREADS threads per SM: the SM's 64K
+// registers, and each of its four sub-partitions' 16K over the warps it holds (warps are
+// spread evenly), in multiples of 8.
+constexpr int regs_for(int minb) {
+    const int warps = minb * (IT_THREADS / 32), per_part = (warps + 3) / 4;
+    const int a = 65536 / (minb * IT_THREADS), b = 16384 / (per_part * 32);
+    return (a < b ? a : b) & ~7;
+}
 
 __device__ __forceinline__ float ex2f(float x) {
     float y;
@@ -84,25 +132,30 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 // ---------------------------------------------------------------------------------
 // table construction: one warp per patch, written to the table in global memory
 
-// One patch's table, built by one warp.  Every lane first converts a share of theta to
-// FP32 (FP64 -> FP32 conversions and FP64 arithmetic have ~70-cycle latencies on GB300's
-// narrow FP64 pipe, so each is done once); lane 0 forms the position in FP64 (relative to
-// the patch origin, so FP32 offsets stay exact).  Then, in parallel: lanes k < npsf build
-// PSF component k's frame, lanes npsf, npsf + 1 the brightness moments of each type, lane
-// npsf + 2 the weights, lane npsf + 3 the shape Jacobian; finally one lane per (PSF
-// component, component slot) the slot's coefficients.  sm: 64 floats of this warp's
-// shared memory.
-__device__ __forceinline__ void build_patch_table(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
-                                                  const ImgMeta* __restrict__ img, const ModelDev& md, int patch,
-                                                  float* __restrict__ ztbl, float* sm) {
+// One patch's table and chain-rule record, built by one warp.  Every lane first converts
+// a share of theta to FP32 (FP64 -> FP32 conversions and FP64 arithmetic have ~70-cycle
+// latencies on GB300's narrow FP64 pipe, so each is done once); lane 0 forms the position
+// in FP64 (relative to the patch origin, so FP32 offsets stay exact).  Then every lane
+// computes, and one lane each stores: PSF component k's frame (lanes k < npsf), the
+// brightness moments of each type (lanes npsf, npsf + 1), the weights (lane npsf + 2)
+// and the shape Jacobian (lane npsf + 3);
+// finally one lane per (PSF component, component slot) the slot's coefficients and one
+// lane per theta column its chain-rule pairs.  sm: 96 floats of this warp's shared memory.
+
+__device__ __forceinline__ void build_patch_table(const double* __restrict__ theta, const ZBuild& g,
+                                                  const ImgMeta* __restrict__ img, const ModelDev& md,
+                                                  float* __restrict__ ztbl, float4* __restrict__ zchain,
+                                                  float* sm) {
     const int lane = threadIdx.x & 31;
-    const PatchGeo g = geo[patch];
+    const int patch = g.patch;
     const ImgMeta& im = img[g.img];
     const double* th = theta + (size_t)NP * g.src;
     float* T = ztbl + (size_t)patch * ZFULL;
     float* thf = sm;        // [44] theta in FP32
     float* dscr = sm + 44;  // [8] D1, D2 per PSF component
     float* mu = sm + 52;    // [2] position relative to the patch origin
+    float* elv = sm + 56;   // [4] el0, el20, el1, el21
+    float* dgs = sm + 60;   // [9] dG
     // every global value this lane reads below, loaded together (one memory round trip)
     const int npsf = im.npsf, band = im.band;
     const float a0 = im.A_f[0], a1 = im.A_f[1], a2 = im.A_f[2], a3 = im.A_f[3];
@@ -120,13 +173,15 @@ __device__ __forceinline__ void build_patch_table(const double* __restrict__ the
     }
     __syncwarp();
     const float rho = thf[P_AXIS], phi = thf[P_ANGLE], sg = thf[P_SCALE], ed = thf[P_EDEV];
-    if (lane < npsf) {
-        const int k = lane;
-        // shape G = A W A^T in this patch's pixel frame, W = sigma^2 R(phi) diag(1, rho^2)
-        // R(phi)^T = ah I + bh (cos 2phi, sin 2phi; sin 2phi, -cos 2phi)
+    // Phase one, straight-line on every lane (the four parts are independent, so their
+    // latencies overlap instead of adding up); each lane stores only its own part.
+    float s2, c2;
+    sincosf(2.f * phi, &s2, &c2);
+    {
+        // PSF component kk's frame: shape G = A W A^T in this patch's pixel frame,
+        // W = sigma^2 R(phi) diag(1, rho^2), R(phi)^T = ah I + bh (cos 2phi, sin 2phi;
+        // sin 2phi, -cos 2phi)
         const float ah = 0.5f * sg * sg * (1.f + rho * rho), bh = 0.5f * sg * sg * (1.f - rho * rho);
-        float s2, c2;
-        sincosf(2.f * phi, &s2, &c2);
         const float wxx = ah + bh * c2, wxy = bh * s2, wyy = ah - bh * c2;
         const float gxx = a0 * a0 * wxx + 2.f * a0 * a1 * wxy + a1 * a1 * wyy;
         const float gxy = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
@@ -153,57 +208,66 @@ __device__ __forceinline__ void build_patch_table(const double* __restrict__ the
         d1 = fmaxf(d1, 0.f);
         d2 = fmaxf(d2, 0.f);
         const float t11 = cs * a - sn * b, t12 = -sn * c, t21 = sn * a + cs * b, t22 = cs * c;
-        float* K = T + ZH + k * ZK;
-        K[0] = -(mu[0] + ps1);
-        K[1] = -(mu[1] + ps2);
-        K[2] = csk;
-        K[3] = sgk;
-        K[4] = t11; K[5] = t12; K[6] = t21; K[7] = t22;
-        K[8] = t11 * t11; K[9] = 2.f * t11 * t21; K[10] = t21 * t21;
-        K[11] = t11 * t12; K[12] = t11 * t22 + t21 * t12; K[13] = t21 * t22;
-        K[14] = t12 * t12; K[15] = 2.f * t12 * t22; K[16] = t22 * t22;
-        K[17] = K[18] = K[19] = 0.f;
-        dscr[2 * k] = d1;
-        dscr[2 * k + 1] = d2;
-    } else if (lane < npsf + 2) {
+        if (lane < npsf) {
+            const int k = lane;
+            float4* K = reinterpret_cast<float4*>(T + VH + k * VK);
+            K[0] = make_float4(-(mu[0] + ps1), -(mu[1] + ps2), csk, sgk);
+            K[1] = make_float4(t11, t12, t21, t22);
+            float4* KG = reinterpret_cast<float4*>(T + VFULL + k * GK);
+            KG[0] = make_float4(t11 * t11, 2.f * t11 * t21, t21 * t21, t11 * t12);
+            KG[1] = make_float4(t11 * t22 + t21 * t12, t21 * t22, t12 * t12, 2.f * t12 * t22);
+            KG[2] = make_float4(t22 * t22, 0.f, 0.f, 0.f);
+            dscr[2 * k] = d1;
+            dscr[2 * k + 1] = d2;
+        }
+    }
+    {
         // brightness of type i in this band: log l ~ N(m, v); E[l] = e^{m+v/2},
         // E[l^2] = e^{2m+2v}, E[l^2] / E[l]^2 - 1 = e^v - 1
-        const int i = lane - npsf;
+        const int i = lane == npsf + 1 ? 1 : 0;
         float m = thf[P_R1 + i], v = thf[P_R2 + i];
+#pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float bb = band_beta<float>(band, j);
             m += bb * thf[P_C1 + 4 * i + j];
             v += bb * bb * thf[P_C2 + 4 * i + j];
         }
-        T[2 + 2 * i] = expf(m + 0.5f * v);
-        T[3 + 2 * i] = expf(2.f * m + 2.f * v);
-        T[8 + i] = expm1f(v);
-    } else if (lane == npsf + 2) {
+        const float el = expf(m + 0.5f * v), el2 = expf(2.f * m + 2.f * v), em = expm1f(v);
+        if (lane == npsf || lane == npsf + 1) {
+            T[2 + 2 * i] = el;
+            T[3 + 2 * i] = el2;
+            T[8 + i] = em;
+            elv[2 * i] = el;
+            elv[2 * i + 1] = el2;
+        }
+    }
+    if (lane == npsf + 2) {
         T[0] = thf[P_A];
         T[1] = thf[P_A + 1];
         T[6] = iota;
         T[7] = ed;
         T[10] = 1.f - ed;
-        T[11] = (float)band;   // the chain rule's band and image-frame map, for the epilogue
+        T[11] = (float)band;
         T[12] = a0; T[13] = a1; T[14] = a2; T[15] = a3;
-    } else if (lane == npsf + 3) {
+    }
+    {
         // dG = A dW A^T, dW = d(Wxx, Wxy, Wyy) / d(e_axis, e_angle, e_scale)
         const float bh = 0.5f * sg * sg * (1.f - rho * rho);
-        float s2, c2;
-        sincosf(2.f * phi, &s2, &c2);
         float dW[3][3];
         float da = sg * sg * rho, db = -sg * sg * rho;
         dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
         dW[1][0] = -2.f * bh * s2; dW[1][1] = 2.f * bh * c2; dW[1][2] = 2.f * bh * s2;
         da = sg * (1.f + rho * rho); db = sg * (1.f - rho * rho);
         dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
-        for (int q = 0; q < 3; ++q) {
-            const float ux = dW[q][0], uxy = dW[q][1], uy = dW[q][2];
-            T[16 + 3 * q + 0] = a0 * a0 * ux + 2.f * a0 * a1 * uxy + a1 * a1 * uy;
-            T[16 + 3 * q + 1] = a0 * a2 * ux + (a0 * a3 + a1 * a2) * uxy + a1 * a3 * uy;
-            T[16 + 3 * q + 2] = a2 * a2 * ux + 2.f * a2 * a3 * uxy + a3 * a3 * uy;
+        if (lane == npsf + 3) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float ux = dW[q][0], uxy = dW[q][1], uy = dW[q][2];
+                dgs[3 * q + 0] = a0 * a0 * ux + 2.f * a0 * a1 * uxy + a1 * a1 * uy;
+                dgs[3 * q + 1] = a0 * a2 * ux + (a0 * a3 + a1 * a2) * uxy + a1 * a3 * uy;
+                dgs[3 * q + 2] = a2 * a2 * ux + 2.f * a2 * a3 * uxy + a3 * a3 * uy;
+            }
         }
-        for (int q = 25; q < 32; ++q) T[q] = 0.f;
     }
     // the coefficients of each (PSF component k, component slot): lane r takes slots r,
     // r + 32, ..., whose constants are read before the wait for phase one
@@ -247,25 +311,39 @@ __device__ __forceinline__ void build_patch_table(const double* __restrict__ the
             C = scs[u] + slw[u] + 0.5f * (__log2f(l1) + __log2f(l2));
             U1 = sgn * l1;
             U2 = sgn * l2;
-            const float snu = sgn * nu;
-            Wa = snu * l1 * l1;
-            Wb = -snu * l1;
-            W12 = snu * l1 * l2;
-            Va = snu * l2 * l2;
-            Vb = -snu * l2;
+            const float snu_ = sgn * nu;
+            Wa = snu_ * l1 * l1;
+            Wb = -snu_ * l1;
+            W12 = snu_ * l1 * l2;
+            Va = snu_ * l2 * l2;
+            Vb = -snu_ * l2;
         }
-        float* pp = T + ZH + k * ZK + ZKH + q * ZPAIR + h;
-        pp[0] = A; pp[2] = B; pp[4] = C; pp[6] = U1; pp[8] = U2; pp[10] = Wa; pp[12] = Wb; pp[14] = W12;
-        pp[16] = Va; pp[18] = Vb;
+        float* pv = T + VH + k * VK + VKH + q * VPAIR + h;
+        pv[0] = A; pv[2] = B; pv[4] = C; pv[6] = U1;
+        float* pq = T + VFULL + k * GK + GKH + q * GPAIR + h;
+        pq[0] = U2; pq[2] = Wa; pq[4] = Wb; pq[6] = W12; pq[8] = Va; pq[10] = Vb;
+    }
+    // the chain-rule record: column j of dy/dtheta for this patch
+    const float Af[4] = {a0, a1, a2, a3};
+    const float el[2] = {elv[0], elv[2]}, el2[2] = {elv[1], elv[3]};
+    float dG[3][3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) dG[e / 3][e % 3] = dgs[e];
+    for (int j = lane; j < NP; j += 32) {
+        int y0, y1, y2;
+        float k0, k1, k2;
+        chain_column<float>(j, band, Af, el, el2, dG, &y0, &k0, &y1, &k1, &y2, &k2);
+        zchain[(size_t)patch * NP + j] = make_float4(k0, k1, k2, __int_as_float(y0 | (y1 << 4) | (y2 << 8)));
     }
 }
 
 // Ready flags of the tables (one int per patch, 0 before the launch): the building warp
-// publishes its table with a release (fence, then the flag); a reader acquires it, waiting
-// at most ~1 s of SM clock, after which it records CELESTE_ERR_TIMEOUT and goes on.
-__device__ __forceinline__ void publish_ready(int32_t* flag) {
-    __threadfence();
-    atomicExch(flag, 1);
+// publishes its table and chain record with a release (fence, then the flag) and counts
+// it in `built`; a reader acquires the flag, waiting at most ~1 s of SM clock (or less
+// once another wait has given up), after which it records CELESTE_ERR_TIMEOUT and goes on.
+__device__ __forceinline__ void publish_ready(int32_t* flag, int32_t* built) {
+    asm volatile("st.release.gpu.global.s32 [%0], 1;" ::"l"(flag) : "memory");
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(built) : "memory");
 }
 
 __device__ __forceinline__ int load_acquire(const int32_t* p) {
@@ -274,22 +352,60 @@ __device__ __forceinline__ int load_acquire(const int32_t* p) {
     return v;
 }
 
+__device__ __forceinline__ bool timed_out(const int32_t* status) {
+    return *reinterpret_cast<const volatile int32_t*>(status) == (int32_t)CELESTE_ERR_TIMEOUT;
+}
+
 __device__ __forceinline__ void wait_ready(const int32_t* flag, int32_t* status) {
     if (load_acquire(flag)) return;
     const long long t0 = clock64();
     for (int i = 0; i < (1 << 24); ++i) {
         __nanosleep(64);
         if (load_acquire(flag)) return;
-        if (clock64() - t0 > 2000000000LL) break;
+        if (timed_out(status) || clock64() - t0 > MBAR_MAX_CYCLES) break;
     }
     atomicExch(status, (int32_t)CELESTE_ERR_TIMEOUT);
 }
 
+// an mbarrier wait that also gives up once another wait of the launch has
+__device__ __forceinline__ bool mbar_wait_launch(uint64_t* bar, unsigned parity, int32_t* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (int i = 0; i < MBAR_MAX_POLLS; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && timed_out(status)) break;
+        if (clock64() - t0 > MBAR_MAX_CYCLES) break;
+    }
+    atomicExch(status, (int32_t)CELESTE_ERR_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive_plain(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// one bulk copy completing on bar (whose expected bytes were announced already)
+__device__ __forceinline__ void bulk_g2s_tx(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// order this thread's earlier (acquired) view of global memory before its async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------------
-// per-pixel evaluation
+// per-pixel evaluation: PX pixels per thread; a packed FP32x2 operation covers two
+// profile components of one pixel
 
 // E_s and Var_s of a source at a pixel from its profile sums (every rounding written out,
-// the same in every kernel of this file):
+// the same wherever a source's E_s is formed):
 //   f_i = iota E[l_i] g_i,  E_s = a0 f0 + a1 f1,
 //   Var_s = a0 f0^2 em0 + a1 f1^2 em1 + a0 (1 - a0) f0^2 + a1 (1 - a1) f1^2 - 2 a0 a1 f0 f1
 __device__ __forceinline__ void source_ev(const float* H, float G0, float G1, float& f0, float& f1,
@@ -306,17 +422,18 @@ __device__ __forceinline__ void source_ev(const float* H, float G0, float G1, fl
     vs = __fsub_rn(v, __fmul_rn(__fmul_rn(2.f, __fmul_rn(a0, a1)), __fmul_rn(f0, f1)));
 }
 
-// the profile sums g0 (star), g1 (galaxy) of one patch at PX pixels, value only
+// the profile sums g0 (star), g1 (galaxy) of one patch at PX pixels from its value part
+// (an item's own table or another patch's value record: the same layout)
 template <int PX, int NPE, int NPD>
-__device__ __forceinline__ void profile_value(const float* H, const float* Kbase, int kstride, int pstride,
-                                              int npsf, int npe_rt, int npd_rt, const float (&X)[PX],
-                                              const float (&Y)[PX], float (&G0)[PX], float (&G1)[PX]) {
+__device__ __forceinline__ void profile_value(const float* H, int npsf, int npe_rt, int npd_rt,
+                                              const float (&X)[PX], const float (&Y)[PX], float (&G0)[PX],
+                                              float (&G1)[PX]) {
     const int npe = NPE >= 0 ? NPE : npe_rt, npd = NPD >= 0 ? NPD : npd_rt;
     float ge[PX], gd[PX];
 #pragma unroll
     for (int p = 0; p < PX; ++p) G0[p] = ge[p] = gd[p] = 0.f;
     for (int k = 0; k < npsf; ++k) {
-        const float* K = Kbase + k * kstride;
+        const float* K = H + VH + k * VK;
         const float4 h0 = ld4(K), h1 = ld4(K + 4);
         float2 Z1[PX], Z2[PX], xe[PX], xd[PX];
 #pragma unroll
@@ -331,30 +448,22 @@ __device__ __forceinline__ void profile_value(const float* H, const float* Kbase
             Z2[p] = dup(q2);
             xe[p] = xd[p] = dup(0.f);
         }
-        const float* Q = K + (kstride == ZK ? ZKH : VKH);
-#pragma unroll
-        for (int q = 0; q < (NPE >= 0 ? NPE + NPD : 1); ++q) {
-            if (NPE < 0) break;
-            const float4 ab = ld4(Q + q * pstride), cc = ld4(Q + q * pstride + 4);
+        const float* Q = K + VKH;
+        auto pair = [&](int q, bool is_exp) {
+            const float4 ab = ld4(Q + q * VPAIR), cc = ld4(Q + q * VPAIR + 4);
             const float2 A = make_float2(ab.x, ab.y), B = make_float2(ab.z, ab.w), C = make_float2(cc.x, cc.y);
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
                 const float2 e = ex2x2(__ffma2_rn(A, Z1[p], __ffma2_rn(B, Z2[p], C)));
-                if (q < NPE) xe[p] = __fadd2_rn(xe[p], e);
+                if (is_exp) xe[p] = __fadd2_rn(xe[p], e);
                 else xd[p] = __fadd2_rn(xd[p], e);
             }
-        }
-        if (NPE < 0) {
-            for (int q = 0; q < npe + npd; ++q) {
-                const float4 ab = ld4(Q + q * pstride), cc = ld4(Q + q * pstride + 4);
-                const float2 A = make_float2(ab.x, ab.y), B = make_float2(ab.z, ab.w), C = make_float2(cc.x, cc.y);
+        };
+        if (NPE >= 0) {
 #pragma unroll
-                for (int p = 0; p < PX; ++p) {
-                    const float2 e = ex2x2(__ffma2_rn(A, Z1[p], __ffma2_rn(B, Z2[p], C)));
-                    if (q < npe) xe[p] = __fadd2_rn(xe[p], e);
-                    else xd[p] = __fadd2_rn(xd[p], e);
-                }
-            }
+            for (int q = 0; q < (NPE >= 0 ? NPE + NPD : 0); ++q) pair(q, q < NPE);
+        } else {
+            for (int q = 0; q < npe + npd; ++q) pair(q, q < npe);
         }
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
@@ -369,10 +478,12 @@ __device__ __forceinline__ void profile_value(const float* H, const float* Kbase
 struct ProfileGrad {
     float g0, gx0, gy0, g1, gx1, gy1, de, sxx, sxy, syy;
 };
+static_assert(sizeof(ProfileGrad) == PG_F * sizeof(float), "ProfileGrad layout");
 
 // the profile sums and their derivatives of the item's own patch at PX pixels; g0 and g1
-// are formed with exactly the operations of profile_value
-template <int PX, int NPE, int NPD>
+// are formed with exactly the operations of profile_value (UNR: unroll factor of the
+// loop over component pairs)
+template <int PX, int NPE, int NPD, int UNR>
 __device__ __forceinline__ void profile_grad(const float* H, int npsf, int npe_rt, int npd_rt,
                                              const float (&X)[PX], const float (&Y)[PX],
                                              ProfileGrad (&o)[PX]) {
@@ -384,7 +495,8 @@ __device__ __forceinline__ void profile_grad(const float* H, int npsf, int npe_r
         ge[p] = gd[p] = 0.f;
     }
     for (int k = 0; k < npsf; ++k) {
-        const float* K = H + ZH + k * ZK;
+        const float* K = H + VH + k * VK;
+        const float* KG = H + VFULL + k * GK;
         const float4 h0 = ld4(K), h1 = ld4(K + 4);
         float z1[PX], z2[PX];
         float2 Z1[PX], Z2[PX], xe[PX], xd[PX], u1[PX], u2[PX], w11[PX], w12[PX], w22[PX];
@@ -405,10 +517,12 @@ __device__ __forceinline__ void profile_grad(const float* H, int npsf, int npe_r
             Z2[p] = dup(q2);
             xe[p] = xd[p] = u1[p] = u2[p] = w11[p] = w12[p] = w22[p] = dup(0.f);
         }
-        const float* Q = K + ZKH;
+        const float* Q = K + VKH;
+        const float* QG = KG + GKH;
         auto pair = [&](int q, bool is_exp) {
-            const float* c = Q + q * ZPAIR;
-            const float4 c0 = ld4(c), c1 = ld4(c + 4), c2 = ld4(c + 8), c3 = ld4(c + 12), c4 = ld4(c + 16);
+            const float4 c0 = ld4(Q + q * VPAIR), c1 = ld4(Q + q * VPAIR + 4);
+            const float* cg = QG + q * GPAIR;
+            const float4 c2 = ld4(cg), c3 = ld4(cg + 4), c4 = ld4(cg + 8);
             const float2 A = make_float2(c0.x, c0.y), B = make_float2(c0.z, c0.w);
             const float2 C = make_float2(c1.x, c1.y), U1 = make_float2(c1.z, c1.w);
             const float2 U2 = make_float2(c2.x, c2.y), Wa = make_float2(c2.z, c2.w);
@@ -427,14 +541,14 @@ __device__ __forceinline__ void profile_grad(const float* H, int npsf, int npe_r
             }
         };
         if (NPE >= 0) {
-#pragma unroll (PAIR_UNROLL)
+#pragma unroll (UNR)
             for (int q = 0; q < (NPE >= 0 ? NPE + NPD : 0); ++q) pair(q, q < NPE);
         } else {
             for (int q = 0; q < npe + npd; ++q) pair(q, q < npe);
         }
         // finish component k: map the whitened sums back with T
-        const float4 f0 = ld4(K + 8), f1 = ld4(K + 12);
-        const float f8 = K[16];
+        const float4 f0 = ld4(KG), f1 = ld4(KG + 4);
+        const float f8 = KG[8];
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             ge[p] = __fmaf_rn(h0.w, __fadd_rn(xe[p].x, xe[p].y), ge[p]);
@@ -461,317 +575,28 @@ __device__ __forceinline__ void profile_grad(const float* H, int npsf, int npe_r
 // ll = x (log E - Var / (2 E^2)) - E and its weights c_E = x (1/E + Var/E^3) - 1,
 // c_V = -x / (2 E^2)
 __device__ __forceinline__ float pix_ll(float x, float E, float V) {
-    const float iE = __fdiv_rn(1.f, E), iE2 = __fmul_rn(iE, iE);
+    const float iE = __frcp_rn(E), iE2 = __fmul_rn(iE, iE);
     return __fsub_rn(__fmul_rn(x, __fsub_rn(logf(E), __fmul_rn(__fmul_rn(0.5f, V), iE2))), E);
 }
 __device__ __forceinline__ void pix_weights(float x, float E, float V, float& cE, float& cV) {
-    const float iE = __fdiv_rn(1.f, E), iE2 = __fmul_rn(iE, iE);
+    const float iE = __frcp_rn(E), iE2 = __fmul_rn(iE, iE);
     cE = __fsub_rn(__fmul_rn(x, __fadd_rn(iE, __fmul_rn(V, __fmul_rn(iE2, iE)))), 1.f);
     cV = __fmul_rn(__fmul_rn(-0.5f, x), iE2);
 }
 
-// Sum NV per-thread values over the CTA: FP32 within a warp, FP64 across warps in warp
-// order.  Thread i < NV receives the CTA total of value i in out[i] (shared).
-template <int NV, int NTH>
-__device__ __forceinline__ void block_sum(const float (&v)[NV], double* out) {
-    constexpr int NW = NTH / 32;
-    __shared__ float red[NW][NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float s = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp][i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) s += (double)red[w][threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
-
-struct ItemArgs {
-    const ZItem* items;        // launch order: the most expensive items first
-    const ZCand* cands;
-    const int32_t* xy;         // gathered pixels: (row << 16) | column in the patch
-    const float2* xs;          // gathered pixels: (counts, sky)
-    const ModelDev* md;
-    const double* theta;
-    float* ztbl;               // [patch][ZFULL] tables (built by the table CTAs)
-    int32_t* ready;            // [patch] table ready flags, 0 before the launch
-    const PatchGeo* geo_tab;   // patch geometry and image records for the table CTAs
-    const ImgMeta* img_tab;
-    double* part;              // [item][NZPART]
-    double* item_ll;           // ll of a singly covered item's pixels
-    double* item_own;          // ll of the multiply covered pixels the item owns
-    int n_order, n_multi;
-    int npe, npd;              // exp / dev component pairs
-    int n_patch, tab_blocks;   // table CTAs: the first tab_blocks of the launch
-    int kl_blocks, n_src;      // KL CTAs: the next kl_blocks
-    double* kl;
-    double* kl_grad;
-    int32_t* status;
-    // the per-source epilogue, run by the last of a source's items and KL warp to finish
-    int mode;
-    const int32_t* patch_off;
-    const int32_t* spatch_off;
-    const int32_t* sitem_off;
-    int32_t* src_done;         // [n_src] arrivals per source, 0 between launches
-    int32_t* grp_done;         // [groups + 1] finished sources per group, finished groups
-    double* src_total;
-    double* grp_total;
-    double* local_out;
-    double* grad_out;
-    double* total_out;
-};
-
-constexpr int IT_THREADS = 128;              // threads per CTA
-static_assert(CHUNK == 2 * IT_THREADS, "item sizes");
-// shared memory of a CTA (floats): four warp items' tables and sums, or a multiply covered
-// item's table, the other patches' value records and the stashed profile derivatives
-constexpr int PG_F = 10;   // floats of a ProfileGrad
-constexpr int VSUM_F = 16;   // floats per thread of the running per-thread sums (ll, d ll / d y, owned ll)
-constexpr int ZF_DBL_OUT = 1024;   // doubles of one epilogue warp's shared memory (at most)
-template <int PX>
-struct ItemSmem {
-    static constexpr int tables = ZFULL + ZMAXC * VFULL + IT_THREADS * PX * PG_F;
-    static constexpr int items = tables + IT_THREADS * VSUM_F;
-    // the KL CTAs: four warps' KL arrays and epilogue space
-    static constexpr int kl = 5 * (IT_THREADS / 32) * NP + 2 * (IT_THREADS / 32) * ZF_DBL_OUT;
-    static constexpr int floats = items > kl ? items : kl;
-};
-static_assert(sizeof(ProfileGrad) == PG_F * sizeof(float), "ProfileGrad layout");
-
-// ---------------------------------------------------------------------------------
-// Per-source epilogue, run by one warp: the last of the source's items and its KL warp to
-// finish (an arrival counter per source, released and acquired at gpu scope).  Per patch,
-// the [ll, d ll / d y] sums of its items (FP64 in item order: a batch of up to ZF_BATCH
-// patches has contiguous items, staged in chunks with coalesced L2 loads, lane c adding
-// column c, so one FP64 instruction serves every column -- GB300's FP64 pipe costs a whole
-// warp instruction however few lanes are active); then the chain rule dy/dtheta of each
-// patch from its table header (band, map, brightness moments, shape Jacobian), accumulated
-// per column over the source's patches in order; minus the KL.  The source's share of the
-// total (the ll of its singly covered items and of the multiply covered pixels its items
-// own, minus its KL) goes to src_total; the last source of each group of ZF_GROUP adds the
-// group's shares in order, the last group adds the group sums in order (fixed order at
-// every level), and the counters are reset for the next launch.
-
-constexpr int ZF_COLS = NZPART + 1;   // ll, d ll / d y, the item's share of the total
-constexpr int ZF_BATCH = 4;           // patches per batch
-constexpr int ZF_CHUNK = 24;          // item partials staged at once
-// shared memory of one epilogue warp (doubles): the batch's sums, a chunk of partials and
-// their total shares, the batch's headers and item ranges, chain coefficients and indices
-constexpr int ZF_YS = 0, ZF_SP = ZF_YS + ZF_BATCH * 32, ZF_SL = ZF_SP + ZF_CHUNK * NZPART,
-              ZF_HD = ZF_SL + ZF_CHUNK, ZF_CF = ZF_HD + ZF_BATCH * 10 + 8, ZF_CY = ZF_CF + ZF_BATCH * NP * 2,
-              ZF_DBL = ZF_CY + ZF_BATCH * NP / 2 + 2;
-
-__device__ __forceinline__ double warp_dsum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// one arrival of source s (the calling warp's writes -- and, after a block barrier, its
-// CTA's -- are done); true on the warp that arrived last
-__device__ __forceinline__ bool source_arrive(const ItemArgs& a, int s) {
-    const int lane = threadIdx.x & 31;
-    int last = 0;
-    if (lane == 0) {
-        const int target = a.sitem_off[s + 1] - a.sitem_off[s] + 1;   // items + the KL warp
-        __threadfence();
-        last = atomicAdd(a.src_done + s, 1) == target - 1;
-        if (last) __threadfence();
-    }
-    return __shfl_sync(0xffffffffu, last, 0) != 0;
-}
-
-__device__ void source_epilogue(const ItemArgs& a, int s, double* sm /* ZF_DBL doubles */) {
-    const int lane = threadIdx.x & 31, c = lane;
-    double* ys = sm + ZF_YS;
-    double* sp = sm + ZF_SP;
-    double* sl = sm + ZF_SL;
-    float* hd = reinterpret_cast<float*>(sm + ZF_HD);   // [ZF_BATCH][18]: 13 + band + A[4]
-    int* ir = reinterpret_cast<int*>(sm + ZF_HD + ZF_BATCH * 9);   // [ZF_BATCH + 1]
-    float* cf = reinterpret_cast<float*>(sm + ZF_CF);   // [ZF_BATCH * NP][4] chain coefficients
-    int* cy = reinterpret_cast<int*>(sm + ZF_CY);       // [ZF_BATCH * NP] their y indices
-    const int p0 = __ldcg(a.patch_off + s), p1 = __ldcg(a.patch_off + s + 1);
-    const bool grad = a.mode >= MODE_GRAD;
-    const double klv = __ldcg(a.kl + s);
-    const double klg0 = grad ? __ldcg(a.kl_grad + (size_t)NP * s + lane) : 0.0;
-    const double klg1 = grad && lane + 32 < NP ? __ldcg(a.kl_grad + (size_t)NP * s + 32 + lane) : 0.0;
-    double g0 = 0.0, g1 = 0.0, lls = 0.0, tot = 0.0;
-    for (int pb = p0; pb < p1; pb += ZF_BATCH) {
-        const int np = min(ZF_BATCH, p1 - pb);
-        if (lane <= np) ir[lane] = __ldcg(a.spatch_off + pb + lane);
-        if (grad && lane < np) {
-            const float* H = a.ztbl + (size_t)(pb + lane) * ZFULL;
-            float* h = hd + 18 * lane;
-            h[0] = __ldcg(H + 2); h[1] = __ldcg(H + 3); h[2] = __ldcg(H + 4); h[3] = __ldcg(H + 5);
-            for (int e = 0; e < 9; ++e) h[4 + e] = __ldcg(H + 16 + e);
-            for (int e = 0; e < 5; ++e) h[13 + e] = __ldcg(H + 11 + e);   // band, A[4]
-        }
-        __syncwarp();
-        // per-patch column sums in item order (the batch's items are contiguous)
-        // lane c (< 14) adds column c of the even items, lane 16 + c of the odd ones
-        const int ib = ir[0], ie = ir[np];
-        const int cc = c & 15, par = c >> 4;
-        int j = 0, jend = ir[1];
-        double acc = 0.0;
-        for (int cs = ib; cs < ie; cs += ZF_CHUNK) {
-            const int n = min(ZF_CHUNK, ie - cs);
-            for (int e = lane; e < n * NZPART; e += 32) sp[e] = __ldcg(a.part + (size_t)cs * NZPART + e);
-            for (int e = lane; e < n; e += 32) sl[e] = __ldcg(a.item_ll + cs + e) + __ldcg(a.item_own + cs + e);
-            __syncwarp();
-            if (cc < ZF_COLS && (grad || cc == 0 || cc == NZPART))
-                for (int k = 0; k < n; ++k) {
-                    while (cs + k >= jend) {   // the item starts a later patch of the batch
-                        ys[16 * (2 * j + par) + cc] = acc;
-                        acc = 0.0;
-                        ++j;
-                        jend = ir[j + 1];
-                    }
-                    if (((cs + k - ir[j]) & 1) == par) acc += cc < NZPART ? sp[k * NZPART + cc] : sl[k];
-                }
-            __syncwarp();
-        }
-        if (cc < ZF_COLS) {
-            for (; j < np; ++j) {   // the last patch with items
-                ys[16 * (2 * j + par) + cc] = acc;
-                acc = 0.0;
-            }
-        }
-        __syncwarp();
-        // even + odd halves, in that order
-        for (int r = lane; r < np * 16; r += 32) {
-            const int q = r >> 4, col = r & 15;
-            const double v = (col < ZF_COLS && (grad || col == 0 || col == NZPART))
-                                 ? ys[16 * (2 * q) + col] + ys[16 * (2 * q + 1) + col] : 0.0;
-            ys[16 * (2 * q) + col] = v;   // this lane's slot alone
-        }
-        __syncwarp();
-        for (int q = 0; q < np; ++q) {
-            lls += ys[32 * q];
-            tot += ys[32 * q + NZPART];
-        }
-        if (grad) {
-            // every (patch, column) pair's chain coefficients first (FP32, independent of the
-            // sums, so the conversions below overlap), then per column three dependent FP64
-            // FMAs per patch
-            for (int r = lane; r < np * NP; r += 32) {
-                const int q = r / NP, col = r - q * NP;
-                const float* h = hd + 18 * q;
-                const float el[2] = {h[0], h[2]}, el2[2] = {h[1], h[3]};
-                float dG[3][3];
-                for (int e = 0; e < 9; ++e) dG[e / 3][e % 3] = h[4 + e];
-                int y0, y1, y2;
-                float k0, k1, k2;
-                chain_column<float>(col, (int)h[13], h + 14, el, el2, dG, &y0, &k0, &y1, &k1, &y2, &k2);
-                cf[4 * r] = k0; cf[4 * r + 1] = k1; cf[4 * r + 2] = k2;
-                cy[r] = y0 | (y1 << 4) | (y2 << 8);
-            }
-            __syncwarp();
-            for (int q = 0; q < np; ++q) {
-                const double* Y = ys + 32 * q;
-                for (int half = 0; half < 2; ++half) {
-                    const int col = lane + 32 * half;
-                    if (col >= NP) break;
-                    const int r = q * NP + col, yy = cy[r];
-                    const double k0 = cf[4 * r], k1 = cf[4 * r + 1], k2 = cf[4 * r + 2];
-                    double& gg = half == 0 ? g0 : g1;
-                    gg = fma(k0, Y[1 + (yy & 15)], gg);
-                    gg = fma(k1, Y[1 + ((yy >> 4) & 15)], gg);
-                    gg = fma(k2, Y[1 + (yy >> 8)], gg);
-                }
-            }
-        }
-        __syncwarp();
-    }
-    if (lane == 0 && a.local_out) a.local_out[s] = lls - klv;
-    if (grad && a.grad_out) {
-        a.grad_out[(size_t)NP * s + lane] = g0 - klg0;
-        if (lane + 32 < NP) a.grad_out[(size_t)NP * s + 32 + lane] = g1 - klg1;
-    }
-    if (lane == 0) a.src_done[s] = 0;
-    if (!a.total_out) return;
-    const int grp = s / ZF_GROUP, n_grp = (a.n_src + ZF_GROUP - 1) / ZF_GROUP;
-    const int gb = grp * ZF_GROUP, gn = min(ZF_GROUP, a.n_src - gb);
-    int last = 0;
-    if (lane == 0) {
-        a.src_total[s] = tot - klv;
-        __threadfence();
-        last = atomicAdd(a.grp_done + grp, 1) == gn - 1;
-        if (last) __threadfence();
-    }
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    // the group's shares in order: lane l adds shares l, l + 32, ..., then a shuffle tree
-    double v = 0.0;
-    for (int i = lane; i < gn; i += 32) v += __ldcg(a.src_total + gb + i);
-    v = warp_dsum(v);
-    last = 0;
-    if (lane == 0) {
-        a.grp_total[grp] = v;
-        a.grp_done[grp] = 0;
-        __threadfence();
-        last = atomicAdd(a.grp_done + n_grp, 1) == n_grp - 1;
-        if (last) __threadfence();
-    }
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    v = 0.0;
-    for (int i = lane; i < n_grp; i += 32) v += __ldcg(a.grp_total + i);
-    v = warp_dsum(v);
-    if (lane == 0) {
-        *a.total_out = v;
-        a.grp_done[n_grp] = 0;
-    }
-}
-
-// this thread's pixels of an item (consecutive in the item's list, base = first index)
-template <int PX>
-__device__ __forceinline__ void item_pixels(const ItemArgs& a, const ZItem& it, int base, float (&X)[PX],
-                                            float (&Y)[PX], float (&xv)[PX], float (&sky)[PX], bool (&ok)[PX]) {
-#pragma unroll
-    for (int p = 0; p < PX; ++p) {
-        const int l = base + p;
-        ok[p] = l < it.n;
-        const int64_t j = it.pix + (ok[p] ? l : 0);
-        const int q = a.xy[j];   // (row << 16) | column in the patch
-        const float2 v = a.xs[j];
-        X[p] = (float)(q & 0xffff);
-        Y[p] = (float)(q >> 16);
-        xv[p] = v.x;
-        sky[p] = v.y;
-    }
-}
-
-// copy a patch's table (header and the used part of each PSF component) to shared memory,
-// threads `lane` of `nth`
-__device__ __forceinline__ void stage_table(const float* __restrict__ src_tbl, float* dst_tbl, int npsf,
-                                            int npair, int lane, int nth) {
-    const float4* src = reinterpret_cast<const float4*>(src_tbl);
-    float4* dst = reinterpret_cast<float4*>(dst_tbl);
-    const int per_k = (ZKH + npair * ZPAIR) / 4;
-    for (int i = lane; i < ZH / 4; i += nth) dst[i] = __ldcg(src + i);
-    for (int k = 0; k < npsf; ++k)
-        for (int i = lane; i < per_k; i += nth) dst[(ZH + k * ZK) / 4 + i] = __ldcg(src + (ZH + k * ZK) / 4 + i);
-}
-
 // the item's own source at this thread's pixels: E_s, Var_s, f_i and (gradient) the
 // profile sums with their derivatives
-template <int MODE, int PX, int NPE, int NPD>
+template <int MODE, int PX, int NPE, int NPD, int UNR>
 __device__ __forceinline__ void own_source(const float* H, int npsf, int npe, int npd, const float (&X)[PX],
                                            const float (&Y)[PX], float (&Es)[PX], float (&Vs)[PX],
                                            float (&f0)[PX], float (&f1)[PX], ProfileGrad (&pg)[PX]) {
     if constexpr (MODE == MODE_LL) {
         float G0[PX], G1[PX];
-        profile_value<PX, NPE, NPD>(H, H + ZH, ZK, ZPAIR, npsf, npe, npd, X, Y, G0, G1);
+        profile_value<PX, NPE, NPD>(H, npsf, npe, npd, X, Y, G0, G1);
 #pragma unroll
         for (int p = 0; p < PX; ++p) source_ev(H, G0[p], G1[p], f0[p], f1[p], Es[p], Vs[p]);
     } else {
-        profile_grad<PX, NPE, NPD>(H, npsf, npe, npd, X, Y, pg);
+        profile_grad<PX, NPE, NPD, UNR>(H, npsf, npe, npd, X, Y, pg);
 #pragma unroll
         for (int p = 0; p < PX; ++p) source_ev(H, pg[p].g0, pg[p].g1, f0[p], f1[p], Es[p], Vs[p]);
     }
@@ -809,136 +634,170 @@ __device__ __forceinline__ void pixel_terms(const float* H, float x, float E, fl
     }
 }
 
-// One singly covered item (<= FUSED_CHUNK pixels) on one CTA: no other source covers its
-// pixels, so E = sky + E_s and Var = Var_s come from the item's own mixture sums.  Warp w
-// takes the rounds of 32 PX pixels w, w + 4, ... (PX pixels per thread per round); the
-// thread's running sums wait in shared memory while the mixture is evaluated; FP32 sums
-// within a warp, FP64 across the warps in warp order.
-template <int MODE, int PX, int NPE, int NPD>
-__device__ __forceinline__ void single_item(const ItemArgs& a, const ZItem& it, float* sT, float* vs) {
-    constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
-    constexpr int NW = IT_THREADS / 32;
-    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const int npsf = it.nc_npsf >> 24, n = it.n;
-    float X[PX], Y[PX], xv[PX], sky[PX];
-    bool ok[PX];
-    item_pixels<PX>(a, it, w * 32 * PX + lane * PX, X, Y, xv, sky, ok);
-    if (t == 0) wait_ready(a.ready + it.patch, a.status);
-    __syncthreads();
-    stage_table(a.ztbl + (size_t)it.patch * ZFULL, sT, npsf, a.npe + a.npd, t, IT_THREADS);
+// ---------------------------------------------------------------------------------
+// launch arguments
+
+struct ItemArgs {
+    const ZTask* tasks;
+    int n_task;
+    const ZBuild* torder;      // the patches' build records, in the order the items first read them
+    const ZCand* cands;
+    const float4* px;          // pixel records (column, row in the patch, counts, sky)
+    const ModelDev* md;
+    const double* theta;
+    float* ztbl;               // [patch][ZFULL] tables
+    float4* zchain;            // [patch][NP] chain-rule records
+    int32_t* ready;            // [patch] table ready flags, then the queue counter and the
+                               // count of built tables; all 0 before the launch
+    const PatchGeo* geo_tab;
+    const ImgMeta* img_tab;
+    double* part;              // [item][ZPCOLS]
+    int ne, nd;                // exp / dev profile components
+    int n_patch, n_src;
+    double* kl;
+    double* kl_grad;
+    int32_t* status;
+    int mode;
+    const int32_t* sitem_off;
+    int32_t* grp_done;         // [0]: finished CTAs of the epilogue kernel, 0 between launches
+    double* src_total;         // [n_src] scratch of the total (per-CTA sums of the epilogue kernel)
+    double* local_out;
+    double* grad_out;
+    double* total_out;
+};
+
+// ---------------------------------------------------------------------------------
+// per-source epilogue and the total
+
+__device__ __forceinline__ double warp_dsum(double v) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) vs[i] = 0.f;
-    __syncthreads();
-    for (int r0 = w * 32 * PX; r0 < n; r0 += NW * 32 * PX) {
-        if (r0 != w * 32 * PX) item_pixels<PX>(a, it, r0 + lane * PX, X, Y, xv, sky, ok);
-        float Es[PX], Vs[PX], f0[PX], f1[PX];
-        ProfileGrad pg[PX];
-        own_source<MODE, PX, NPE, NPD>(sT, npsf, a.npe, a.npd, X, Y, Es, Vs, f0, f1, pg);
-        float v[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = vs[i];
-#pragma unroll
-        for (int p = 0; p < PX; ++p) {
-            if (!ok[p]) continue;
-            float ll;
-            pixel_terms<MODE, NV>(sT, xv[p], __fadd_rn(sky[p], Es[p]), Vs[p], Es[p], f0[p], f1[p], pg[p], v, ll);
-        }
-#pragma unroll
-        for (int i = 0; i < NV; ++i) vs[i] = v[i];
-    }
-    float v[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = vs[i];
-    __shared__ double tot[NV];
-    block_sum<NV, IT_THREADS>(v, tot);
-    double* out = a.part + (size_t)it.out * NZPART;
-    if (t < NV) out[t] = tot[t];
-    if (t == 0) {
-        a.item_ll[it.out] = tot[0];
-        a.item_own[it.out] = 0.0;
-    }
-    __syncthreads();
-    if (t >= 32) return;   // warp 0 arrives for the CTA (no block barrier after this)
-    if (source_arrive(a, it.src)) source_epilogue(a, it.src, reinterpret_cast<double*>(sT));
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// One multiply covered item (<= 256 pixels) on the whole CTA, PX pixels per thread per
-// round: E and Var sum the item's source and every other covering source in ascending
-// source order.
-template <int MODE, int PX, int NPE, int NPD>
-__device__ __forceinline__ void cta_item(const ItemArgs& a, const ZItem& it, float* sT, float* sVbase,
-                                         float* vs) {
-    constexpr int NTH = IT_THREADS;
-    constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;
-    __shared__ ZCand s_c[ZMAXC];
-    const int npsf = it.nc_npsf >> 24, nc = it.nc_npsf & 0xffffff;
-    const int npair = a.npe + a.npd;
-    const int t = threadIdx.x;
-    float X[PX], Y[PX], xv[PX], sky[PX];
-    bool ok[PX];
-    item_pixels<PX>(a, it, t * PX, X, Y, xv, sky, ok);
-    if (t == 0) wait_ready(a.ready + it.patch, a.status);
-    for (int ci = t; ci < nc; ci += NTH) wait_ready(a.ready + a.cands[it.c0 + ci].patch, a.status);
-    __syncthreads();
-    auto stage_others = [&](int cb, int cn) {
-        if (t < cn) s_c[t] = a.cands[it.c0 + cb + t];
-        // per record: 4 float4 of header, per k 2 float4 of header and 2 per pair
-        const int per_k = 2 + 2 * npair, per_rec = 4 + MAXPSF * per_k;
-        for (int i = t; i < cn * per_rec; i += NTH) {
-            const int ci = i / per_rec, r = i - ci * per_rec;
-            const float4* src = reinterpret_cast<const float4*>(a.ztbl + (size_t)a.cands[it.c0 + cb + ci].patch * ZFULL);
-            float4* dst = reinterpret_cast<float4*>(sVbase + ci * VFULL);
-            if (r < 4) {
-                dst[r] = __ldcg(src + r);
+// an arrival counter increment with release (this thread's, and what it has seen of its
+// CTA's, writes become visible first) and acquire (the other arrivals' writes become
+// visible to the caller) at gpu scope; returns the count before it
+__device__ __forceinline__ int arrive_acq_rel(int32_t* ctr) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    return old;
+}
+
+// One warp: the source's item records summed column by column in item order (FP64; lane
+// c adds columns c and c + 32, even and odd items in two sums added at the end), minus
+// the KL, into the local objective and gradient.  Returns (every lane) the source's share
+// of the total: the ll of the pixels its items own, minus its KL.
+__device__ double source_epilogue(const ItemArgs& a, int s) {
+    const int lane = threadIdx.x & 31;
+    const bool grad = a.mode >= MODE_GRAD;
+    const int ncol = grad ? ZPCOLS : 2;
+    const int i0 = __ldcg(a.sitem_off + s), i1 = __ldcg(a.sitem_off + s + 1);
+    const double klv = __ldcg(a.kl + s);
+    const int cA = lane, cB = lane + 32;
+    const double kA = (grad && cA >= 2) ? __ldcg(a.kl_grad + (size_t)NP * s + cA - 2) : 0.0;
+    const double kB = (grad && cB < ncol) ? __ldcg(a.kl_grad + (size_t)NP * s + cB - 2) : 0.0;
+    double eA = 0.0, oA = 0.0, eB = 0.0, oB = 0.0;
+    constexpr int WIN = 16;
+    for (int k0 = i0; k0 < i1; k0 += WIN) {
+        double vA[WIN], vB[WIN];
+#pragma unroll
+        for (int u = 0; u < WIN; ++u) {
+            const int k = k0 + u;
+            const double* r = a.part + (size_t)k * ZPCOLS;
+            vA[u] = (k < i1 && cA < ncol) ? __ldcg(r + cA) : 0.0;
+            vB[u] = (k < i1 && cB < ncol) ? __ldcg(r + cB) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < WIN; ++u) {
+            if (k0 + u >= i1) break;
+            if (u & 1) {
+                oA += vA[u];
+                oB += vB[u];
             } else {
-                const int k = (r - 4) / per_k, e = (r - 4) - k * per_k;
-                const int so = (ZH + k * ZK) / 4 + (e < 2 ? e : ZKH / 4 + ((e - 2) >> 1) * (ZPAIR / 4) + ((e - 2) & 1));
-                const int d = (VH + k * VK) / 4 + (e < 2 ? e : VKH / 4 + ((e - 2) >> 1) * (VPAIR / 4) + ((e - 2) & 1));
-                dst[d] = __ldcg(src + so);
+                eA += vA[u];
+                eB += vB[u];
             }
         }
-    };
-    stage_table(a.ztbl + (size_t)it.patch * ZFULL, sT, npsf, npair, t, NTH);
-    const int nc0 = nc < ZMAXC ? nc : ZMAXC;
-    if (nc0 > 0) stage_others(0, nc0);
-    __syncthreads();
-    // the profile derivatives wait in shared memory while the other sources are evaluated,
-    // and so do the thread's running sums
-    ProfileGrad* spg = reinterpret_cast<ProfileGrad*>(sVbase + ZMAXC * VFULL) + t * PX;
+    }
+    const double sA = eA + oA, sB = eB + oB;
+    if (lane == 0 && a.local_out) a.local_out[s] = sA - klv;   // column 0: ll
+    if (grad && a.grad_out) {
+        if (cA >= 2) a.grad_out[(size_t)NP * s + cA - 2] = sA - kA;
+        if (cB < ncol) a.grad_out[(size_t)NP * s + cB - 2] = sB - kB;
+    }
+    return __shfl_sync(0xffffffffu, sA, 1) - klv;   // column 1: owned ll
+}
+
+// ---------------------------------------------------------------------------------
+// tasks of the compute warps
+
+// One item on the four compute warps: warp w takes the chunks of 32 PX pixels w, w + 4,
+// ... (PX consecutive pixels per thread); the thread's running sums wait in shared memory
+// between chunks; a chunk that holds multiply covered pixels (warp-uniform) stashes its
+// derivatives in shared memory while the other covering patches are evaluated.  Each
+// warp leaves its FP32 sums (ll, d ll / d y, owned ll) in red (lane 0).
+template <int MODE, int PX, int NPE, int NPD, int UNR>
+__device__ __forceinline__ void item_compute(const ItemArgs& a, const ZItem& it, const uint8_t* stage,
+                                             float* vs, float* spg, float* red) {
+    constexpr int NV = (MODE == MODE_LL) ? 1 : 1 + NY;   // ll (+ d ll / d y)
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int n = it.n_nm & 0xffff, nm = it.n_nm >> 16;
+    const int npsf = it.nc_npsf >> 24, nc = it.nc_npsf & 0xffffff;
+    const int npe = (a.ne + 1) >> 1, npd = (a.nd + 1) >> 1;
+    const float* T = reinterpret_cast<const float*>(stage + ST_TBL);
+    const float4* pxr = reinterpret_cast<const float4*>(stage + ST_PX);
+    const ZCand* zc = reinterpret_cast<const ZCand*>(stage + ST_ZC);
+    const float* vrec = reinterpret_cast<const float*>(stage + ST_VREC);
 #pragma unroll
-    for (int i = 0; i <= NV; ++i) vs[i] = 0.f;
-    for (int r0 = 0; r0 < it.n; r0 += NTH * PX) {
-        if (r0 > 0) item_pixels<PX>(a, it, r0 + t * PX, X, Y, xv, sky, ok);
-        const bool warp_on = r0 + (t >> 5) * 32 * PX < it.n;   // idle warps skip the work
-        float Es[PX], Vs[PX], f0[PX], f1[PX];
-        if (warp_on) {
-            ProfileGrad pg[PX];
-            own_source<MODE, PX, NPE, NPD>(sT, npsf, a.npe, a.npd, X, Y, Es, Vs, f0, f1, pg);
-            if constexpr (MODE >= MODE_GRAD)
-#pragma unroll
-                for (int p = 0; p < PX; ++p) spg[p] = pg[p];
-        }
-        // E and Var over every covering source in ascending source order
-        float E[PX], V[PX];
-        bool owner[PX], added[PX];
+    for (int i = 0; i <= NV; ++i) vs[i * NTC] = 0.f;
+    for (int c0 = w * 32 * PX; c0 < n; c0 += NWC * 32 * PX) {
+        float X[PX], Y[PX], xv[PX], sky[PX];
+        bool ok[PX];
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
-            E[p] = sky[p];
-            V[p] = 0.f;
-            owner[p] = true;
-            added[p] = false;
+            const int l = c0 + lane * PX + p;
+            ok[p] = l < n;
+            const float4 r = pxr[ok[p] ? l : n - 1];
+            X[p] = r.x;
+            Y[p] = r.y;
+            xv[p] = r.z;
+            sky[p] = r.w;
         }
-        for (int cb = 0; cb < nc; cb += ZMAXC) {
-            const int cn = min(ZMAXC, nc - cb);
-            if (nc > ZMAXC && (cb > 0 || r0 > 0)) {
-                __syncthreads();   // every thread is done with the previous round's records
-                stage_others(cb, cn);
-                __syncthreads();
+        float Es[PX], Vs[PX], f0[PX], f1[PX];
+        ProfileGrad pg[PX];
+        own_source<MODE, PX, NPE, NPD, UNR>(T, npsf, npe, npd, X, Y, Es, Vs, f0, f1, pg);
+        float E[PX], V[PX];
+        bool owner[PX];
+        if (c0 < nm) {
+            // E and Var over every covering source in ascending source order; the item's
+            // own source enters at its place
+            if constexpr (MODE >= MODE_GRAD) {
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    const float* q = reinterpret_cast<const float*>(&pg[p]);
+#pragma unroll
+                    for (int f = 0; f < PG_F; ++f) spg[(p * PG_F + f) * NTC] = q[f];
+                }
             }
-            if (!warp_on) continue;
-            for (int ci = 0; ci < cn; ++ci) {
-                const float* R = sVbase + ci * VFULL;
-                const ZCand c = s_c[ci];
+            bool added = false;
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                E[p] = sky[p];
+                V[p] = 0.f;
+                owner[p] = true;
+            }
+            for (int ci = 0; ci < nc; ++ci) {
+                const ZCand c = ci < ZMAXC ? zc[ci] : a.cands[it.c0 + ci];
+                const float* R = ci < ZMAXC ? vrec + ci * VFULL : a.ztbl + (size_t)c.patch * ZFULL;
+                if (!added && c.src > it.src) {
+#pragma unroll
+                    for (int p = 0; p < PX; ++p) {
+                        E[p] = __fadd_rn(E[p], Es[p]);
+                        V[p] = __fadd_rn(V[p], Vs[p]);
+                    }
+                    added = true;
+                }
                 float Xc[PX], Yc[PX];
                 bool in[PX], any = false;
 #pragma unroll
@@ -948,17 +807,11 @@ __device__ __forceinline__ void cta_item(const ItemArgs& a, const ZItem& it, flo
                     Xc[p] = (float)xx;
                     Yc[p] = (float)yy;
                     any = any || in[p];
-                    // the item's own source enters the sum at its place in source order
-                    if (!added[p] && c.src > it.src) {
-                        E[p] = __fadd_rn(E[p], Es[p]);
-                        V[p] = __fadd_rn(V[p], Vs[p]);
-                        added[p] = true;
-                    }
                     if (in[p] && c.src < it.src) owner[p] = false;
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 float G0[PX], G1[PX];
-                profile_value<PX, NPE, NPD>(R, R + VH, VK, VPAIR, c.npsf, a.npe, a.npd, Xc, Yc, G0, G1);
+                profile_value<PX, NPE, NPD>(R, c.npsf, npe, npd, Xc, Yc, G0, G1);
 #pragma unroll
                 for (int p = 0; p < PX; ++p) {
                     float q0, q1, ec, vc;
@@ -969,171 +822,475 @@ __device__ __forceinline__ void cta_item(const ItemArgs& a, const ZItem& it, flo
                     }
                 }
             }
-        }
-        if (warp_on) {
-            float v[NV + 1];
+            if (!added)
 #pragma unroll
-            for (int i = 0; i <= NV; ++i) v[i] = vs[i];
-#pragma unroll
-            for (int p = 0; p < PX; ++p) {
-                if (!ok[p]) continue;
-                if (!added[p]) {
+                for (int p = 0; p < PX; ++p) {
                     E[p] = __fadd_rn(E[p], Es[p]);
                     V[p] = __fadd_rn(V[p], Vs[p]);
                 }
-                float vv[NV], ll;
+            if constexpr (MODE >= MODE_GRAD) {
 #pragma unroll
-                for (int i = 0; i < NV; ++i) vv[i] = v[i];
-                ProfileGrad q{};
-                if constexpr (MODE >= MODE_GRAD) q = spg[p];
-                pixel_terms<MODE, NV>(sT, xv[p], E[p], V[p], Es[p], f0[p], f1[p], q, vv, ll);
+                for (int p = 0; p < PX; ++p) {
+                    float* q = reinterpret_cast<float*>(&pg[p]);
 #pragma unroll
-                for (int i = 0; i < NV; ++i) v[i] = vv[i];
-                if (owner[p]) v[NV] += ll;
+                    for (int f = 0; f < PG_F; ++f) q[f] = spg[(p * PG_F + f) * NTC];
+                }
             }
+        } else {
 #pragma unroll
-            for (int i = 0; i <= NV; ++i) vs[i] = v[i];
+            for (int p = 0; p < PX; ++p) {
+                E[p] = __fadd_rn(sky[p], Es[p]);
+                V[p] = Vs[p];
+                owner[p] = true;
+            }
+        }
+        float v[NV + 1];
+#pragma unroll
+        for (int i = 0; i <= NV; ++i) v[i] = vs[i * NTC];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            if (!ok[p]) continue;
+            float vv[NV], ll;
+#pragma unroll
+            for (int i = 0; i < NV; ++i) vv[i] = v[i];
+            pixel_terms<MODE, NV>(T, xv[p], E[p], V[p], Es[p], f0[p], f1[p], pg[p], vv, ll);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = vv[i];
+            if (owner[p]) v[NV] += ll;
+        }
+#pragma unroll
+        for (int i = 0; i <= NV; ++i) vs[i * NTC] = v[i];
+    }
+    // the warp's sums (FP32 shuffle tree) to red
+#pragma unroll
+    for (int i = 0; i <= NV; ++i) {
+        float s = vs[i * NTC];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[i] = s;
+    }
+}
+
+// the KL value and gradient of source s on one warp (with the domain check of its theta)
+__device__ __forceinline__ void kl_task(const ItemArgs& a, int s, float* scr) {
+    const int lane = threadIdx.x & 31;
+    double* kth = reinterpret_cast<double*>(scr);
+    double* kg = kth + NP;
+    float* kthr = reinterpret_cast<float*>(kg + NP);
+    for (int i = lane; i < NP; i += 32) {
+        const double v = a.theta[(size_t)NP * s + i];
+        kth[i] = v;
+        kthr[i] = (float)v;
+        theta_domain_check(i, v, a.status);
+    }
+    __syncwarp();
+    const double v = kl_warp<float>(*a.md, kth, kthr, kg);
+    __syncwarp();
+    if (lane == 0) a.kl[s] = v;
+    for (int i = lane; i < NP; i += 32) a.kl_grad[(size_t)NP * s + i] = kg[i];
+}
+
+// After an item, on the last compute warp to finish it: the warps' sums added in warp
+// order (FP64), the patch's chain rule applied (column j of d ll / d theta =
+// sum_e k_e d ll / d y_{y_e}, FP64) and the item's record written.
+template <int MODE>
+__device__ __forceinline__ void finish_item(const ItemArgs& a, int out, const uint8_t* stage, const float* red) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NS = (MODE == MODE_LL) ? 2 : 2 + NY;   // ll, (d ll / d y), owned ll
+    double y = 0.0;
+    if (lane < NS)
+#pragma unroll
+        for (int w = 0; w < NWC; ++w) y += (double)red[w * RED_W + lane];
+    double* rec = a.part + (size_t)out * ZPCOLS;
+    if (lane == 0) rec[0] = y;
+    if (lane == NS - 1) rec[1] = y;
+    if constexpr (MODE >= MODE_GRAD) {
+        const float4* ch = reinterpret_cast<const float4*>(stage + ST_CHAIN);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            const float4 r = ch[c < NP ? c : 0];
+            const int yy = __float_as_int(r.w);
+            const double y0 = __shfl_sync(0xffffffffu, y, 1 + (yy & 15));
+            const double y1 = __shfl_sync(0xffffffffu, y, 1 + ((yy >> 4) & 15));
+            const double y2 = __shfl_sync(0xffffffffu, y, 1 + ((yy >> 8) & 15));
+            double g = (double)r.x * y0;
+            g = fma((double)r.y, y1, g);
+            g = fma((double)r.z, y2, g);
+            if (c < NP) rec[2 + c] = g;
         }
     }
-    float v[NV + 1];
-#pragma unroll
-    for (int i = 0; i <= NV; ++i) v[i] = vs[i];
-    __shared__ double tot[NV + 1];
-    block_sum<NV + 1, NTH>(v, tot);
-    double* out = a.part + (size_t)it.out * NZPART;
-    if (t < NV) out[t] = tot[t];
-    if (t == 0) {
-        a.item_ll[it.out] = 0.0;
-        a.item_own[it.out] = tot[NV];
+}
+
+// ---------------------------------------------------------------------------------
+// the producer warp
+
+// the 64-byte record of queue slot q, a quarter per lane 0 .. 3 (past the end: an end
+// marker)
+__device__ __forceinline__ int4 load_task(const ItemArgs& a, int q) {
+    const int lane = threadIdx.x & 31;
+    if (q >= a.n_task) return make_int4(ZT_END, 0, 0, 0);
+    return lane < 4 ? __ldcg(reinterpret_cast<const int4*>(a.tasks + q) + lane) : make_int4(0, 0, 0, 0);
+}
+
+// Put a task record (lanes 0 .. 3) in a stage and, for an item, wait for the tables it
+// reads and start the bulk copies of its data into the stage; the stage's full barrier
+// completes when they land (at once for the end marker).  Whole warp; lane 0 does the
+// waits and the copies.  all_built (lane 0): every table was seen built, so no flag need
+// be read.
+template <int MODE>
+__device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, uint64_t* full, bool& all_built) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 4) reinterpret_cast<int4*>(tk)[lane] = rec;
+    __syncwarp();
+    if (lane != 0) return;
+    if (tk->kind != ZT_ITEM) {
+        mbar_arrive_plain(full);
+        return;
+    }
+    const ZItem it = tk->item;
+    const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZMAXC ? nc : ZMAXC;
+    if (!all_built) {
+        if (load_acquire(a.ready + a.n_patch + 1) >= a.n_patch) {
+            all_built = true;
+        } else {
+            wait_ready(a.ready + it.patch, a.status);
+            for (int e = 0; e < nc0; ++e) wait_ready(a.ready + tk->cand[e], a.status);
+            for (int e = ZMAXC; e < nc; ++e) wait_ready(a.ready + a.cands[it.c0 + e].patch, a.status);
+        }
+    }
+    fence_proxy_async_global();
+    fence_proxy_async_smem();   // the stage was last read through the generic proxy
+    const unsigned tbl_bytes = MODE == MODE_LL ? VFULL * 4 : ZFULL * 4;
+    const unsigned chain_bytes = MODE == MODE_LL ? 0u : NP * 16;
+    const unsigned bytes =
+        tbl_bytes + chain_bytes + (unsigned)n * 16u + (unsigned)nc0 * (unsigned)(sizeof(ZCand) + VFULL * 4);
+    mbar_expect_arrive(full, bytes);
+    bulk_g2s_tx(stage + ST_TBL, a.ztbl + (size_t)it.patch * ZFULL, tbl_bytes, full);
+    if (chain_bytes) bulk_g2s_tx(stage + ST_CHAIN, a.zchain + (size_t)it.patch * NP, chain_bytes, full);
+    bulk_g2s_tx(stage + ST_PX, a.px + it.pix, (unsigned)n * 16u, full);
+    if (nc0 > 0) {
+        bulk_g2s_tx(stage + ST_ZC, a.cands + it.c0, (unsigned)nc0 * (unsigned)sizeof(ZCand), full);
+        for (int e = 0; e < nc0; ++e)
+            bulk_g2s_tx(stage + ST_VREC + e * VFULL * 4, a.ztbl + (size_t)tk->cand[e] * ZFULL, VFULL * 4, full);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// the kernels
+
+// Tables and KL terms: warp u < n_patch builds the table and chain-rule record of the
+// patch of torder[u] (the patches in the order the items first read them) and publishes it; warp
+// n_patch + s computes the KL of source s (with the domain check of its theta) and counts
+// as one of the source's arrivals.  The item kernel is launched as this kernel's
+// programmatic dependent and waits for each table's flag, not for this kernel.
+__global__ void __launch_bounds__(128) k_tables(ItemArgs a) {
+    __shared__ __align__(16) float scr[4][SCR_W / 4];
+    pdl_trigger();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = (int)blockIdx.x * 4 + w;
+    if (u < a.n_patch) {
+        const ZBuild g = a.torder[u];
+        build_patch_table(a.theta, g, a.img_tab, *a.md, a.ztbl, a.zchain, scr[w]);
+        __syncwarp();
+        if (lane == 0) publish_ready(a.ready + g.patch, a.ready + a.n_patch + 1);
+    } else if (u < a.n_patch + a.n_src) {
+        kl_task(a, u - a.n_patch, scr[w]);
+    }
+}
+
+// The per-source epilogues and the total, after every item: the item kernel's
+// programmatic dependent, waiting for it to finish.  A CTA takes FIN_W sources (a warp
+// each) and adds their shares of the total in warp order; the last CTA to finish adds the
+// CTA sums in order (its warps over contiguous ranges, lanes strided, then warp order)
+// and resets the counter for the next launch.
+constexpr int FIN_W = 8;
+__global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
+    __shared__ double sh[FIN_W];
+    __shared__ int s_last;
+    pdl_wait();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = (int)blockIdx.x * FIN_W + w;
+    const double share = s < a.n_src ? source_epilogue(a, s) : 0.0;
+    if (!a.total_out) return;
+    if (lane == 0) sh[w] = share;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c = 0.0;
+        for (int i = 0; i < FIN_W; ++i) c += sh[i];
+        a.src_total[blockIdx.x] = c;
+        s_last = arrive_acq_rel(a.grp_done) == (int)gridDim.x - 1;
     }
     __syncthreads();
-    if (t >= 32) return;   // warp 0 arrives for the CTA (no block barrier after this)
-    if (source_arrive(a, it.src)) source_epilogue(a, it.src, reinterpret_cast<double*>(sT));
+    if (!s_last) return;
+    const int n = (int)gridDim.x, per = (n + FIN_W - 1) / FIN_W;
+    const int b0 = w * per, b1 = min(n, b0 + per);
+    double acc = 0.0;
+    for (int c0 = b0; c0 < b1; c0 += 32 * 16) {
+        double x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int i = c0 + lane + 32 * u;
+            x[u] = i < b1 ? __ldcg(a.src_total + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc += x[u];
+    }
+    acc = warp_dsum(acc);
+    __syncthreads();   // every warp has read sh (above) before it is reused
+    if (lane == 0) sh[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < FIN_W; ++i) t += sh[i];
+        *a.total_out = t;
+        a.grp_done[0] = 0;
+    }
 }
 
-// The whole FP32 value / gradient evaluation in one launch: CTAs [0, tab_blocks) build the
-// patches' tables (one warp per patch) and publish them; the next kl_blocks CTAs compute
-// the KL (one warp per source, with the domain check of theta); then one CTA per item, the
-// most expensive first, each waiting for the tables it reads.  The last of each
-// source's items and KL warp to finish runs the source's epilogue.  Waits are only on CTAs
-// of lower index, which are dispatched first and wait on nothing.
-template <int MODE, int PX, int NPE, int NPD, int MINB>
-__global__ void __launch_bounds__(IT_THREADS, MINB) k_items(ItemArgs a) {
-    __shared__ __align__(16) float smem[ItemSmem<PX>::floats];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int W = IT_THREADS / 32;
-    if ((int)blockIdx.x < a.tab_blocks) {
-        const int patch = (int)blockIdx.x * W + w;
-        if (patch >= a.n_patch) return;   // whole warps leave; no block barrier in this branch
-        build_patch_table(a.theta, a.geo_tab, a.img_tab, *a.md, patch, a.ztbl, smem + 64 * w);
-        __syncwarp();
-        if (lane == 0) publish_ready(a.ready + patch);
+// The items, on persistent CTAs of four compute warps and a producer warp.  The producer
+// keeps the next two items in the two stages (item i + 2 goes to the stage of item i as
+// soon as the compute warps are done with it), one task record ahead in registers and
+// one queue slot claimed beyond that.  The last compute warp to finish an item writes its
+// record.
+template <int MODE, int PX, int NPE, int NPD, int MINB, int UNR>
+__global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_items(ItemArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    using L = Lay<PX>;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar);
+    uint64_t* reduced = full + 2;
+    ZTask* tasks = reinterpret_cast<ZTask*>(smem + L::task);
+    float* red = reinterpret_cast<float*>(smem + L::red);
+    int* cnt = reinterpret_cast<int*>(smem + L::cnt);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    pdl_trigger();   // the epilogue kernel may start (it waits for this grid to finish)
+    if (t == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&reduced[0], NTC);
+        mbar_init(&reduced[1], NTC);
+        mbar_init_fence();
+        cnt[0] = cnt[1] = 0;
+    }
+    __syncthreads();
+    int32_t* queue = a.ready + a.n_patch;
+    if (w == NWC) {
+        bool all_built = false;
+        int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(queue, 3);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        const int4 r0 = load_task(a, q0), r1 = load_task(a, q0 + 1);
+        int4 ra = load_task(a, q0 + 2);   // the record of the next item to prepare
+        prepare<MODE>(a, r0, smem, &tasks[0], &full[0], all_built);
+        prepare<MODE>(a, r1, smem + ST_BYTES, &tasks[1], &full[1], all_built);
+        int qb = 0;   // lane 0: the slot after that
+        if (lane == 0) qb = atomicAdd(queue, 1);
+        for (int i = 0;; ++i) {
+            const int b = i & 1;
+            __syncwarp();
+            if (tasks[b].kind == ZT_END) break;
+            if (!mbar_wait_launch(&reduced[b], (i >> 1) & 1, a.status)) break;
+            prepare<MODE>(a, ra, smem + b * ST_BYTES, &tasks[b], &full[b], all_built);
+            ra = load_task(a, __shfl_sync(0xffffffffu, qb, 0));
+            if (lane == 0) qb = atomicAdd(queue, 1);
+        }
+        // this grid completes only after the table kernel (and its KL terms) has, so the
+        // epilogue kernel that waits for this grid sees both
+        pdl_wait();
         return;
     }
-    const int kb = (int)blockIdx.x - a.tab_blocks;
-    if (kb < a.kl_blocks) {
-        double (*kth)[NP] = reinterpret_cast<double (*)[NP]>(smem);
-        double (*kg)[NP] = reinterpret_cast<double (*)[NP]>(smem + 2 * W * NP);
-        float (*kthr)[NP] = reinterpret_cast<float (*)[NP]>(smem + 4 * W * NP);
-        const int s = kb * W + w;
-        if (s >= a.n_src) return;   // whole warps leave; no block barrier in this branch
-        for (int i = lane; i < NP; i += 32) {
-            const double v = a.theta[(size_t)NP * s + i];
-            kth[w][i] = v;
-            kthr[w][i] = (float)v;
-            theta_domain_check(i, v, a.status);
+    // compute warps
+    float* vs = reinterpret_cast<float*>(smem + L::vs) + t;
+    float* spg = reinterpret_cast<float*>(smem + L::pg) + t;
+    for (int i = 0;; ++i) {
+        const int b = i & 1;
+        if (!mbar_wait_launch(&full[b], (i >> 1) & 1, a.status)) break;
+        if (tasks[b].kind == ZT_END) break;
+        const ZItem it = tasks[b].item;
+        const uint8_t* stage = smem + b * ST_BYTES;
+        float* rb = red + b * NWC * RED_W;
+        item_compute<MODE, PX, NPE, NPD, UNR>(a, it, stage, vs, spg, rb + w * RED_W);
+        // the last warp to finish adds the warps' sums and writes the item's record
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&cnt[b], 1) == NWC - 1;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+            __threadfence_block();
+            finish_item<MODE>(a, it.out, stage, rb);
+            if (lane == 0) cnt[b] = 0;
         }
         __syncwarp();
-        const double v = kl_warp<float>(*a.md, kth[w], kthr[w], kg[w]);
-        __syncwarp();
-        if (lane == 0) a.kl[s] = v;
-        for (int i = lane; i < NP; i += 32) a.kl_grad[(size_t)NP * s + i] = kg[w][i];
-        __syncwarp();
-        // the epilogue's shared memory lies beyond every warp's KL arrays
-        static_assert(ZF_DBL <= ZF_DBL_OUT, "epilogue shared memory");
-        if (source_arrive(a, s)) source_epilogue(a, s, reinterpret_cast<double*>(smem + 5 * W * NP) + w * ZF_DBL);
-        return;
+        mbar_arrive_plain(&reduced[b]);
     }
-    const ZItem it = a.items[kb - a.kl_blocks];
-    if ((it.nc_npsf & 0xffffff) > 0) {
-        cta_item<MODE, PX, NPE, NPD>(a, it, smem, smem + ZFULL, smem + ItemSmem<PX>::tables + threadIdx.x * VSUM_F);
-        return;
-    }
-    single_item<MODE, PX, NPE, NPD>(a, it, smem, smem + ItemSmem<PX>::tables + threadIdx.x * VSUM_F);
 }
 
-template <int MODE, int PX, int NPE, int NPD, int MINB>
-cudaError_t items_launch_k(const ItemArgs& a, cudaStream_t st) {
-    const int grid = a.tab_blocks + a.kl_blocks + a.n_order;
-    if (grid == 0) return cudaSuccess;
-    k_items<MODE, PX, NPE, NPD, MINB><<<grid, IT_THREADS, 0, st>>>(a);
-    return cudaGetLastError();
+// ---------------------------------------------------------------------------------
+// launch
+
+template <int MODE, int PX, int NPE, int NPD, int MINB, int UNR>
+struct ItemsKernel {
+    static int per_sm;   // resident CTAs per SM (0: not yet set up)
+    static cudaError_t setup() {
+        if (per_sm > 0) return cudaSuccess;
+        auto* fn = k_items<MODE, PX, NPE, NPD, MINB, UNR>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay<PX>::bytes);
+        if (e != cudaSuccess) return e;
+        int per = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, IT_THREADS, Lay<PX>::bytes);
+        if (e != cudaSuccess) return e;
+        per_sm = per > 0 ? per : 1;
+        return cudaSuccess;
+    }
+    // a programmatic dependent launch of the table kernel before it on st
+    static cudaError_t launch(const ItemArgs& a, int n_sm, cudaStream_t st) {
+        cudaError_t e = setup();
+        if (e != cudaSuccess) return e;
+        int grid = per_sm * n_sm;
+        if (grid > a.n_task) grid = a.n_task;
+        if (grid < 1) return cudaSuccess;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(IT_THREADS);
+        cfg.dynamicSmemBytes = Lay<PX>::bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_items<MODE, PX, NPE, NPD, MINB, UNR>, a);
+    }
+};
+template <int MODE, int PX, int NPE, int NPD, int MINB, int UNR>
+int ItemsKernel<MODE, PX, NPE, NPD, MINB, UNR>::per_sm = 0;
+
+// the model of the synthetic workloads and of the paper (6 exp + 8 dev profile
+// components: 3 + 4 pairs) gets its loops unrolled for those counts
+template <int MODE, int PX, int MINB, int UNR>
+cudaError_t items_launch_v(const ItemArgs& a, int n_sm, cudaStream_t st) {
+    if ((a.ne + 1) / 2 == 3 && (a.nd + 1) / 2 == 4) return ItemsKernel<MODE, PX, 3, 4, MINB, UNR>::launch(a, n_sm, st);
+    return ItemsKernel<MODE, PX, -1, -1, MINB, 1>::launch(a, n_sm, st);
 }
 
-// variant codes: 1, 2 two pixels per thread (at most 128 / 96 registers); 3, 4, 5 one pixel
-// per thread (at most 64 / 72 / 80 registers)
-template <int MODE, int PX, int MINB>
-cudaError_t items_launch_v(const ItemArgs& a, cudaStream_t st) {
-    if (a.npe == 3 && a.npd == 4) return items_launch_k<MODE, PX, 3, 4, MINB>(a, st);
-    return items_launch_k<MODE, PX, -1, -1, MINB>(a, st);
+#define CEL_ITEM_VARIANTS(X)   \
+    X(1, 2, 2, 7)              \
+    X(2, 3, 2, 3)              \
+    X(3, 2, 3, 2)              \
+    X(4, 3, 2, 7)              \
+    X(5, 3, 2, 2)
+// variant codes (code, pixels per thread, CTAs per SM, unroll of the component-pair loop):
+// 1 (2, 2, 7), 2 (3, 2, 3), 3 (2, 3, 2), 4 (3, 2, 7), 5 (3, 2, 2); two CTAs per SM leave
+// 168 registers per thread, three 128
+template <int MODE>
+cudaError_t items_launch(const ItemArgs& a, int code, int n_sm, cudaStream_t st) {
+    switch (code) {
+#define CEL_CASE(c, px, minb, unr) \
+    case c: return items_launch_v<MODE, px, minb, unr>(a, n_sm, st);
+        CEL_ITEM_VARIANTS(CEL_CASE)
+#undef CEL_CASE
+        default: return items_launch_v<MODE, 2, 2, 7>(a, n_sm, st);
+    }
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
 }
 
 template <int MODE>
-cudaError_t items_launch(const ItemArgs& a, int code, cudaStream_t st) {
-    switch (code) {
-        case 1: return items_launch_v<MODE, 2, 4>(a, st);
-        case 2: return items_launch_v<MODE, 2, 5>(a, st);
-        case 4: return items_launch_v<MODE, 1, 7>(a, st);
-        case 5: return items_launch_v<MODE, 1, 6>(a, st);
-        default: return items_launch_v<MODE, 1, 8>(a, st);
-    }
+cudaError_t items_setup_mode() {
+    cudaError_t e = cudaSuccess;
+#define CEL_SETUP(c, px, minb, unr)                                                    \
+    if (e == cudaSuccess) e = ItemsKernel<MODE, px, 3, 4, minb, unr>::setup();           \
+    if (e == cudaSuccess) e = ItemsKernel<MODE, px, -1, -1, minb, 1>::setup();
+    CEL_ITEM_VARIANTS(CEL_SETUP)
+#undef CEL_SETUP
+    return e;
 }
 
 }  // namespace
 
-cudaError_t launch_items(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta, double* d_local,
-                         double* d_grad, double* d_total) {
-    if (P.n_src == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(P.zready, 0, sizeof(int32_t) * (size_t)(P.n_patch > 0 ? P.n_patch : 1), st);
-    if (e != cudaSuccess) return e;
+// shared-memory limits and resident CTAs of every item-kernel variant, set once outside
+// any stream capture
+cudaError_t prime_items_kernels() {
+    cudaError_t e = items_setup_mode<MODE_LL>();
+    if (e == cudaSuccess) e = items_setup_mode<MODE_GRAD>();
+    return e;
+}
+
+cudaError_t launch_items_stage(const DevProblem& P, int stage, int mode, cudaStream_t st, const double* d_theta,
+                               double* d_local, double* d_grad, double* d_total) {
+    if (P.n_src == 0 || !P.ztasks) return cudaSuccess;
     ItemArgs a{};
-    a.items = P.zitems;
+    a.tasks = P.ztasks;
+    a.n_task = P.n_task;
+    a.torder = P.ztorder;
     a.cands = P.zcands;
-    a.xy = P.zxy;
-    a.xs = P.zxs;
+    a.px = P.zpx;
     a.md = P.model;
     a.theta = d_theta;
     a.ztbl = P.ztbl;
+    a.zchain = P.zchain;
     a.ready = P.zready;
     a.geo_tab = P.geo;
     a.img_tab = P.img;
     a.part = P.spart;
-    a.item_ll = P.sitem_ll;
-    a.item_own = P.sitem_own;
-    a.n_order = P.n_sitem;
-    a.n_multi = P.n_smulti;
-    a.npe = P.model_npe;
-    a.npd = P.model_npd;
+    a.ne = P.model_ne;
+    a.nd = P.model_nd;
     a.n_patch = P.n_patch;
-    a.tab_blocks = (P.n_patch + IT_THREADS / 32 - 1) / (IT_THREADS / 32);
     a.n_src = P.n_src;
-    a.kl_blocks = (P.n_src + IT_THREADS / 32 - 1) / (IT_THREADS / 32);
     a.kl = P.kl;
     a.kl_grad = P.kl_grad;
     a.status = P.status;
     a.mode = mode;
-    a.patch_off = P.patch_off;
-    a.spatch_off = P.spatch_off;
     a.sitem_off = P.sitem_off;
-    a.src_done = P.zsrc_done;
     a.grp_done = P.zf_done;
     a.src_total = P.src_total;
-    a.grp_total = P.zf_grp_total;
     a.local_out = d_local;
     a.grad_out = mode >= MODE_GRAD ? d_grad : nullptr;
     a.total_out = d_total;
-    if (mode == MODE_LL) return items_launch<MODE_LL>(a, P.tune_items, st);
-    return items_launch<MODE_GRAD>(a, P.tune_items, st);
+    if (stage == 0) {
+        // ready flags, the queue counter and the built-table count start at 0
+        cudaError_t e = cudaMemsetAsync(P.zready, 0, sizeof(int32_t) * ((size_t)P.n_patch + 2), st);
+        if (e != cudaSuccess) return e;
+        k_tables<<<(P.n_patch + P.n_src + 3) / 4, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (stage == 1) {
+        const int n_sm = sm_count();
+        return mode == MODE_LL ? items_launch<MODE_LL>(a, P.tune_items, n_sm, st)
+                               : items_launch<MODE_GRAD>(a, P.tune_items, n_sm, st);
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((P.n_src + FIN_W - 1) / FIN_W));
+    cfg.blockDim = dim3(32 * FIN_W);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_finish, a);
+}
+
+cudaError_t launch_items(const DevProblem& P, int mode, cudaStream_t st, const double* d_theta, double* d_local,
+                         double* d_grad, double* d_total) {
+    for (int stage = 0; stage < 3; ++stage) {
+        const cudaError_t e = launch_items_stage(P, stage, mode, st, d_theta, d_local, d_grad, d_total);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace cel

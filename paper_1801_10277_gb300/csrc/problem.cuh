@@ -51,7 +51,7 @@ struct celeste_problem {
     // per-kernel CUDA-event timing (celeste_profile_*)
     bool profile = false;
     bool profile_serial = false;   // every stage on the calling stream, one after another
-    struct Rec { std::string name; cudaEvent_t a, b; };
+    struct Rec { std::string name; cudaEvent_t a, b; int n_kernels; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
     std::vector<std::string> names;
