@@ -76,6 +76,33 @@ def items_flops_per_source_pixel(npsf, n_exp, n_dev):
     return npsf * (67 + 19 * nprof) + 114
 
 
+def fp64_path_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """Algorithmic operations of the FP64 path per source-pixel (FMA = 2), counted from the
+    formulas of its two passes: the map pass (per PSF component the offset and its
+    products 5, the star 8, each galaxy component exponent 6 and weighted sum 2; per pixel
+    E_s and Var_s 30) and the adjoint, which recomputes the mixture with its derivatives
+    (per PSF component 5 + 18, each galaxy component 33; per pixel the likelihood weights
+    and the 12 y-gradients 55).  The gather's ~10 operations per multiply covered pixel
+    are left out."""
+    nprof = n_exp + n_dev
+    return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (5 + 18 + 33 * nprof) + 55
+
+
+def hess_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """Algorithmic operations of the Hessian path per source-pixel (FMA = 2): the map pass
+    (as in fp64_path_flops_per_source_pixel) and the Hessian pass, which evaluates the
+    mixture with its first and second derivatives (per PSF component 20 + 42, each galaxy
+    component 140) and per pixel the 78 packed y-Hessian entries, the gradient and the
+    likelihood weights (600)."""
+    nprof = n_exp + n_dev
+    return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (20 + 42 + 140 * nprof) + 600
+
+
+# FP64 peak, derived: 152 SMs x 2 FP64 FMA lanes per clock (the FP64 pipe's width on this
+# part) x 2 FLOP x the 2070 MHz maximum clock
+FP64_LANES = 2
+
+
 def other_eval_flops(npsf, n_exp, n_dev):
     """FP32 operations of one other covering source's E and Var at a multiply covered
     pixel: per PSF component the coordinates (11), star exponent and value (4), each
@@ -241,7 +268,10 @@ def reference_arm(args, rank, ws):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": prob.name, "sources": prob.n_src,
-                   "source_pixels": prob.source_pixels(), "sample": desc,
+                   "source_pixels": prob.source_pixels(), "images": len(prob.images),
+                   "image": "x".join(str(v) for v in prob.images[0].pixels.shape[::-1]),
+                   "precision": "fp64", "l2": "not applicable (host)", "tuning": None,
+                   "parallelism": "single", "sample": desc,
                    "hardware": "host cores of rank 0; no GPU"},
         "cpu_baseline": {"value": val, "unit": "source-pixel evals/s", "cores": num_threads(),
                          "kind": "oracle", "sample": desc},
@@ -293,8 +323,13 @@ def main():
                     help="skip the colour vs Cyclades convergence-per-sweep leg")
     ap.add_argument("--schedule-sweeps", type=int, default=4)
     ap.add_argument("--no-tasks", action="store_true", help="skip the region-task leg")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads' legs (crowded region, sweep field, multi-epoch region)")
     ap.add_argument("--fit-only", action="store_true",
                     help="time the Newton fit of the workload alone (FP32 sweeps, FP64 polish)")
+    ap.add_argument("--step-only", action="store_true",
+                    help="run the FP32 value + gradient step alone (warm-up and timed steps, no other "
+                         "leg): the profiling command for the step's kernels")
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4, 5, 6],
                     help="1 one field (the benchmark), 2 crowded region, 3 multi-epoch region, "
                          "4 sweep field, 5 deep stack (480 images per source), 6 the whole 200,000-source "
@@ -337,6 +372,21 @@ def main():
         return
     dev = torch.device("cuda", local_rank)
     theta = torch.tensor(prob.theta, dtype=torch.float64, device=dev)
+    if args.step_only:
+        # the FP32 step alone, for a profiler's launch list or a capture of one kernel
+        tot = torch.zeros(1, dtype=torch.float64, device=dev)
+        loc = torch.zeros(prob.n_src, dtype=torch.float64, device=dev)
+        grad = torch.zeros(prob.n_src, 44, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            P.elbo_grad_device(theta, tot, loc, grad, precision=cel.FP32)
+        torch.cuda.synchronize()
+        if P.device_status() != 0:
+            raise RuntimeError("device-side parameter check failed")
+        if rank == 0:
+            print(json.dumps({"step_only": True, "steps": args.warmup + args.steps, "elbo": float(tot.item()),
+                              "tuning": list(tuning), "config": {"workload": prob.name, "sources": prob.n_src}}),
+                  flush=True)
+        return
     tot = torch.zeros(1, dtype=torch.float64, device=dev)
     loc = torch.zeros(prob.n_src, dtype=torch.float64, device=dev)
     grad = torch.zeros(prob.n_src, 44, dtype=torch.float64, device=dev)
@@ -442,10 +492,23 @@ def main():
 
     hms32 = hess_loop(cel.FP32, args.hess_steps)
     hms64 = hess_loop(cel.FP64, max(1, args.hess_steps // 10))
-    hessian = {"value": n_sp * ws / (hms32 / 1000.0), "unit": "source-pixel evals/s",
-               "ms_per_step": hms32, "fp64_value": n_sp * ws / (hms64 / 1000.0),
+    hflop = hess_flops_per_source_pixel(npsf, ne, nd)
+    f64flop = fp64_path_flops_per_source_pixel(npsf, ne, nd)
+    h32 = n_sp * ws / (hms32 / 1000.0)
+    h64 = n_sp * ws / (hms64 / 1000.0)
+    peak_fp64 = SM_COUNT * FP64_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
+    hessian = {"value": h32, "unit": "source-pixel evals/s",
+               "ms_per_step": hms32, "fp64_value": h64,
                "fp64_ms_per_step": hms64,
-               "what": "ELBO + gradient + 44x44 Hessian of every source"}
+               "what": "ELBO + gradient + 44x44 Hessian of every source",
+               "cost_vs_elbo_grad": value / h32,
+               "roofline": {"bound": "alu", "flop_per_source_pixel": hflop,
+                            "achieved": hflop * h32 / ws / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
+                            "frac": hflop * h32 / ws / 1e12 / peak_fp32,
+                            "peak_source": "FP32: 152 SM x 128 lanes x 2 x 2070 MHz (unit counts, max clock)",
+                            "fp64": {"achieved": hflop * h64 / ws / 1e12, "peak": peak_fp64,
+                                     "frac": hflop * h64 / ws / 1e12 / peak_fp64,
+                                     "peak_source": "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived)"}}}
 
     # end to end through the host-pointer C ABI (pinned buffers, copies inside)
     pin_th = torch.tensor(prob.theta, dtype=torch.float64).pin_memory()
@@ -550,6 +613,64 @@ def main():
     # region tasks (Section IV-A) on one GPU: one global fit against one and two stages of
     # tasks (regions of about 1/16 of the work; the second stage shifted by half a
     # region), FP32 sweeps polished in FP64; total ELBO after each and host wall time
+    # The other workloads, each timed like the headline (device-resident inputs, L2
+    # flushed between steps) with the headline's variant codes, and its item kernel's
+    # share of the FP32 peak.  Single-GPU runs only (every rank would repeat them).
+    workloads = None
+    if not args.no_workloads and args.workload == 1 and ws == 1:
+        workloads = {}
+        for wc, wsteps in ((2, args.steps), (4, max(3, args.steps // 4)), (3, 3)):
+            wp = synth.config(wc)
+            WP = cel.Problem(wp)
+            WP.set_tuning(*tuning)
+            w_th = torch.tensor(wp.theta, dtype=torch.float64, device=dev)
+            w_tot = torch.zeros(1, dtype=torch.float64, device=dev)
+            w_loc = torch.zeros(wp.n_src, dtype=torch.float64, device=dev)
+            w_gr = torch.zeros(wp.n_src, 44, dtype=torch.float64, device=dev)
+
+            def wstep():
+                WP.elbo_grad_device(w_th, w_tot, w_loc, w_gr, precision=cel.FP32)
+
+            for _ in range(2):
+                wstep()
+            torch.cuda.synchronize()
+            evs = []
+            for _ in range(wsteps):
+                flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                wstep()
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            wms = sum(a.elapsed_time(b) for a, b in evs) / wsteps
+            WP.profile(True)
+            for _ in range(wsteps):
+                flush.fill_(1.0)
+                wstep()
+            torch.cuda.synchronize()
+            wprof = WP.profile_read()
+            WP.profile(False)
+            w_sp = WP.source_pixels
+            wsplit = WP.stats()
+            w_npsf = wp.images[0].psf.shape[0]
+            wwork = (items_flops_per_source_pixel(w_npsf, ne, nd) * w_sp
+                     + other_eval_flops(w_npsf, ne, nd) * wsplit["other_evals"])
+            w_items_us = 1000.0 * wprof["items"][0] / max(1, wprof["items"][1])
+            w_val = w_sp / (wms / 1000.0)
+            w_ach = wwork / (w_items_us * 1e-6) / 1e12
+            workloads[wp.name] = {
+                "value": w_val, "unit": "source-pixel evals/s", "ms_per_step": wms, "steps": wsteps,
+                "sources": wp.n_src, "source_pixels": w_sp,
+                "roofline": {"bound": "alu", "kernel": "items", "achieved": w_ach, "peak": peak_fp32,
+                             "unit": "TFLOP/s", "frac": w_ach / peak_fp32, "flop_per_launch": wwork,
+                             "kernel_us": {k: 1000.0 * v[0] / max(1, v[1]) for k, v in wprof.items()}},
+                "step": step_bound(w_npsf, ne, nd, w_val, wsplit["other_evals"] / w_sp)}
+            WP.close()
+            del WP, wp, w_th, w_loc, w_gr
+            torch.cuda.empty_cache()
+
     tasks = None
     if not args.no_fit and not args.no_tasks:
         npx = np.zeros(prob.n_src)
@@ -604,7 +725,12 @@ def main():
                        "tuning": dict(zip(("contrib", "items"), tuning)),
                        "parallelism": f"replica{ws}" if ws > 1 else "single"},
             "fp64_path": {"value": value64, "unit": "source-pixel evals/s", "ms_per_step": ms64,
-                          "speedup_fp32_over_fp64": value / value64},
+                          "speedup_fp32_over_fp64": value / value64,
+                          "roofline": {"bound": "alu", "flop_per_source_pixel": f64flop,
+                                       "achieved": f64flop * value64 / ws / 1e12, "peak": peak_fp64,
+                                       "unit": "TFLOP/s", "frac": f64flop * value64 / ws / 1e12 / peak_fp64,
+                                       "peak_source": "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived)"}},
+            "workloads": workloads,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "hessian": hessian, "fit": fit, "fit_schedules": schedules, "catalog": catalog, "tasks": tasks,
             "gpu_launches": int(round(launches_per_step * args.steps)),

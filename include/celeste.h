@@ -375,9 +375,12 @@ int32_t celeste_profile_read(celeste_problem* prob, int32_t max_kernels, char* n
  * Every intermediate buffer lives in one file-scope device array of
  * CELESTE_NOALLOC_SCRATCH_BYTES, which each GPU that loads the library holds until the
  * process exits; the largest patch it serves is 101 x 101 pixels (larger sides return
- * CELESTE_ERR_ARG with a message).  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls on a device share the array and it keeps
+ * CELESTE_ERR_ARG with a message).  A call made outside a stream capture looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current, every time; a
+ * call inside a capture uses the address of the last uncaptured call on that device, so
+ * make the first call on a device before any stream capture (a first call inside one
+ * returns CELESTE_ERR_ARG).  The model is checked as by celeste_problem_create.  All
+ * calls on a device share the array and it keeps
  * the last call's contents (every value a call reads is written by the same call
  * first): calls whose work overlaps on the GPU race on it, so order them on one
  * stream or synchronise between them.  Errors: CELESTE_ERR_ARG, CELESTE_ERR_NOT_PD,

@@ -40,6 +40,19 @@ celeste_status cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
+
+template <class T>
+celeste_status upload(T** dst, const T* src, size_t n) {
+    *dst = nullptr;
+    if (n == 0) return CELESTE_OK;
+    CEL_CUDA(cudaMalloc((void**)dst, n * sizeof(T)));
+    CEL_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return CELESTE_OK;
+}
+
+}  // namespace
+
+namespace cel {
 // 2x2 / 4x4 symmetric positive-definiteness and inverse by Cholesky
 bool chol_inverse4(const double* S, double* inv, double* logdet) {
     double L[4][4] = {{0}};
@@ -76,18 +89,49 @@ bool chol_inverse4(const double* S, double* inv, double* logdet) {
     return true;
 }
 
-template <class T>
-celeste_status upload(T** dst, const T* src, size_t n) {
-    *dst = nullptr;
-    if (n == 0) return CELESTE_OK;
-    CEL_CUDA(cudaMalloc((void**)dst, n * sizeof(T)));
-    CEL_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+celeste_status build_model_dev(const celeste_model* model, ModelDev& md, const char** why) {
+    auto bad = [&](celeste_status st, const char* msg) {
+        *why = msg;
+        return st;
+    };
+    if (model->n_exp < 1 || model->n_dev < 1 || model->n_exp + model->n_dev > MAXPROF ||
+        !model->exp_mix || !model->dev_mix)
+        return bad(CELESTE_ERR_ARG, "profile mixtures: need 1 <= n_exp, n_dev and n_exp + n_dev <= CELESTE_MAX_PROFILE");
+    if (model->n_color_comp != NCOMP || !model->prior_c || !model->prior_r)
+        return bad(CELESTE_ERR_ARG, "colour prior must have 8 components per type");
+    if (!(model->prior_star > 0 && model->prior_star < 1)) return bad(CELESTE_ERR_ARG, "prior_star outside (0,1)");
+    md = ModelDev{};
+    md.n_exp = model->n_exp;
+    md.n_dev = model->n_dev;
+    for (int j = 0; j < model->n_exp + model->n_dev; ++j) {
+        const double* m = j < model->n_exp ? model->exp_mix + 2 * j : model->dev_mix + 2 * (j - model->n_exp);
+        if (!(m[0] >= 0 && isfinite(m[0]) && m[1] > 0 && isfinite(m[1])))
+            return bad(CELESTE_ERR_ARG, "profile components need weight >= 0 and variance > 0");
+        md.prof_w[j] = m[0];
+        md.prof_nu[j] = m[1];
+    }
+    md.prior_star = model->prior_star;
+    for (int i = 0; i < 2; ++i) {
+        md.prior_r[i][0] = model->prior_r[2 * i];
+        md.prior_r[i][1] = model->prior_r[2 * i + 1];
+        if (!(md.prior_r[i][1] > 0) || !isfinite(md.prior_r[i][0]) || !isfinite(md.prior_r[i][1]))
+            return bad(CELESTE_ERR_ARG, "prior_r variance must be > 0");
+        for (int d = 0; d < NCOMP; ++d) {
+            const double* pc = model->prior_c + (size_t)(i * NCOMP + d) * 21;
+            if (!(pc[0] > 0) || !isfinite(pc[0])) return bad(CELESTE_ERR_ARG, "colour prior weight must be > 0");
+            md.prior_w[i][d] = pc[0];
+            for (int j = 0; j < 4; ++j) {
+                if (!isfinite(pc[1 + j])) return bad(CELESTE_ERR_ARG, "colour prior mean not finite");
+                md.prior_mu[i][d][j] = pc[1 + j];
+            }
+            if (!chol_inverse4(pc + 5, md.prior_P[i][d], &md.prior_logdet[i][d]))
+                return bad(CELESTE_ERR_NOT_PD, "colour prior covariance not positive definite");
+        }
+    }
+    fill_float_copies(md);
     return CELESTE_OK;
 }
 
-}  // namespace
-
-namespace cel {
 // lets other translation units report through celeste_last_error()
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace cel
@@ -353,37 +397,11 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     if (n_src < 0 || !model || !patch_offsets || !nbr_offsets)
         return fail(CELESTE_ERR_ARG, "null model / offsets or negative n_src");
     // ---- model
-    if (model->n_exp < 1 || model->n_dev < 1 || model->n_exp + model->n_dev > MAXPROF ||
-        !model->exp_mix || !model->dev_mix)
-        return fail(CELESTE_ERR_ARG, "profile mixtures: need 1 <= n_exp, n_dev and n_exp + n_dev <= %d", MAXPROF);
-    if (model->n_color_comp != NCOMP || !model->prior_c || !model->prior_r)
-        return fail(CELESTE_ERR_ARG, "colour prior must have %d components per type", NCOMP);
-    if (!(model->prior_star > 0 && model->prior_star < 1))
-        return fail(CELESTE_ERR_ARG, "prior_star outside (0,1)");
     ModelDev md{};
-    md.n_exp = model->n_exp;
-    md.n_dev = model->n_dev;
-    for (int j = 0; j < model->n_exp + model->n_dev; ++j) {
-        const double* m = j < model->n_exp ? model->exp_mix + 2 * j : model->dev_mix + 2 * (j - model->n_exp);
-        if (!(m[0] >= 0 && isfinite(m[0]) && m[1] > 0 && isfinite(m[1])))
-            return fail(CELESTE_ERR_ARG, "profile component %d: weight >= 0 and variance > 0 required", j);
-        md.prof_w[j] = m[0];
-        md.prof_nu[j] = m[1];
-    }
-    md.prior_star = model->prior_star;
-    for (int i = 0; i < 2; ++i) {
-        md.prior_r[i][0] = model->prior_r[2 * i];
-        md.prior_r[i][1] = model->prior_r[2 * i + 1];
-        if (!(md.prior_r[i][1] > 0) || !isfinite(md.prior_r[i][0]))
-            return fail(CELESTE_ERR_ARG, "prior_r variance must be > 0");
-        for (int d = 0; d < NCOMP; ++d) {
-            const double* pc = model->prior_c + (size_t)(i * NCOMP + d) * 21;
-            if (!(pc[0] > 0)) return fail(CELESTE_ERR_ARG, "colour prior weight must be > 0");
-            md.prior_w[i][d] = pc[0];
-            for (int j = 0; j < 4; ++j) md.prior_mu[i][d][j] = pc[1 + j];
-            if (!chol_inverse4(pc + 5, md.prior_P[i][d], &md.prior_logdet[i][d]))
-                return fail(CELESTE_ERR_NOT_PD, "colour prior covariance (%d,%d) not positive definite", i, d);
-        }
+    {
+        const char* why = nullptr;
+        const celeste_status ms = build_model_dev(model, md, &why);
+        if (ms != CELESTE_OK) return fail(ms, "%s", why);
     }
     fill_float_copies(md);
     // ---- images
@@ -778,12 +796,9 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
         void* q;
         if ((st = dalloc(pr, &q, sizeof(double) * ZPCOLS * (size_t)P.n_sitem))) return bail(st);
         P.spart = (double*)q;
-        const int n_grp = (n_src + ZF_GROUP - 1) / ZF_GROUP;
-        if ((st = dalloc(pr, &q, sizeof(double) * (size_t)n_grp))) return bail(st);
-        P.zf_grp_total = (double*)q;
-        if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_grp + 1)))) return bail(st);
+        if ((st = dalloc(pr, &q, sizeof(int32_t)))) return bail(st);
         P.zf_done = (int32_t*)q;
-        if (cudaMemset(P.zf_done, 0, sizeof(int32_t) * ((size_t)n_grp + 1)) != cudaSuccess)
+        if (cudaMemset(P.zf_done, 0, sizeof(int32_t)) != cudaSuccess)
             return bail(fail(CELESTE_ERR_CUDA, "memset"));
         if ((st = dalloc(pr, &q, sizeof(int32_t) * ((size_t)n_patch + 2)))) return bail(st);
         P.zready = (int32_t*)q;

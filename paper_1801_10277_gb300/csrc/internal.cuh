@@ -36,7 +36,6 @@ constexpr int NPART = 1 + NY + NYH;
 // item's pixels, [1] ll of the pixels the item owns (its share of the total), [2 .. 2 + NP)
 // d ll / d theta of its source (the patch's chain rule applied per item).
 constexpr int ZPCOLS = 2 + NP;
-constexpr int ZF_GROUP = 1024;   // sources per first-level group of the total
 
 // Mixture table of one (source, patch), in units of the pixel precision R:
 //   header [0..7]: a0 a1 E[l|star] E[l^2|star] E[l|gal] E[l^2|gal] iota 0
@@ -265,8 +264,7 @@ struct DevProblem {
     const int32_t* sitem_off;    // [n_src + 1]
     int n_sitem, n_smulti;       // items; those holding multiply covered pixels
     double* spart;               // [n_sitem][ZPCOLS] per-item partials
-    double* zf_grp_total;        // per group of ZF_GROUP sources: their share of the total
-    int32_t* zf_done;            // [groups + 1] completion counters, 0 between launches
+    int32_t* zf_done;            // finished sources of the FP32 epilogue kernel, 0 between launches
     const int32_t* src_active;   // per source: 0 = skip its work (the fit's converged batch
                                  // sources); nullable = every source works
     // the FP32 value / gradient item kernel (item_kernels.cu)
@@ -287,6 +285,15 @@ struct DevProblem {
 };
 
 void set_last_error(const char* msg);
+
+// 4 x 4 symmetric positive-definite inverse and log-determinant by Cholesky (false when
+// not positive definite)
+bool chol_inverse4(const double* S, double* inv, double* logdet);
+// The model's device record, with every check of the model description (profile
+// weights finite and >= 0, variances > 0, prior_star in (0, 1), brightness-prior
+// variances > 0, colour-prior weights > 0 and covariances positive definite); on a
+// failure the status and *why (a static message).  Shared by every entry point.
+celeste_status build_model_dev(const celeste_model* model, ModelDev& md, const char** why);
 
 celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const int32_t* which,
                                 int32_t n_which, const celeste_fit_options* opts,

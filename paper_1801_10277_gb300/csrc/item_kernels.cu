@@ -32,8 +32,9 @@
 // order (every covering item forms the same sum, bit for bit).  Per warp FP32 sums; the
 // last warp to finish adds the warps in FP64, applies the patch's chain rule dy/dtheta
 // and writes the item's record.  k_finish, k_items' programmatic dependent, runs every
-// source's epilogue (FP64 sums of its item records in order, minus the KL) once the items
-// are done; the last source of each group adds the group, the last group the total.
+// source's epilogue once the items are done (one CTA per source: FP64 sums of its item
+// records in a fixed order, minus the KL); the last CTA to finish adds the sources' shares
+// of the total in source order.
 // Every wait is bounded (~1 s), after which the kernel records CELESTE_ERR_TIMEOUT and
 // ends.
 #include <math.h>
@@ -659,8 +660,8 @@ struct ItemArgs {
     int32_t* status;
     int mode;
     const int32_t* sitem_off;
-    int32_t* grp_done;         // [0]: finished CTAs of the epilogue kernel, 0 between launches
-    double* src_total;         // [n_src] scratch of the total (per-CTA sums of the epilogue kernel)
+    int32_t* grp_done;         // [0]: finished sources of the epilogue kernel, 0 between launches
+    double* src_total;         // [n_src] each source's share of the total (epilogue kernel)
     double* local_out;
     double* grad_out;
     double* total_out;
@@ -684,50 +685,6 @@ __device__ __forceinline__ int arrive_acq_rel(int32_t* ctr) {
     return old;
 }
 
-// One warp: the source's item records summed column by column in item order (FP64; lane
-// c adds columns c and c + 32, even and odd items in two sums added at the end), minus
-// the KL, into the local objective and gradient.  Returns (every lane) the source's share
-// of the total: the ll of the pixels its items own, minus its KL.
-__device__ double source_epilogue(const ItemArgs& a, int s) {
-    const int lane = threadIdx.x & 31;
-    const bool grad = a.mode >= MODE_GRAD;
-    const int ncol = grad ? ZPCOLS : 2;
-    const int i0 = __ldcg(a.sitem_off + s), i1 = __ldcg(a.sitem_off + s + 1);
-    const double klv = __ldcg(a.kl + s);
-    const int cA = lane, cB = lane + 32;
-    const double kA = (grad && cA >= 2) ? __ldcg(a.kl_grad + (size_t)NP * s + cA - 2) : 0.0;
-    const double kB = (grad && cB < ncol) ? __ldcg(a.kl_grad + (size_t)NP * s + cB - 2) : 0.0;
-    double eA = 0.0, oA = 0.0, eB = 0.0, oB = 0.0;
-    constexpr int WIN = 16;
-    for (int k0 = i0; k0 < i1; k0 += WIN) {
-        double vA[WIN], vB[WIN];
-#pragma unroll
-        for (int u = 0; u < WIN; ++u) {
-            const int k = k0 + u;
-            const double* r = a.part + (size_t)k * ZPCOLS;
-            vA[u] = (k < i1 && cA < ncol) ? __ldcg(r + cA) : 0.0;
-            vB[u] = (k < i1 && cB < ncol) ? __ldcg(r + cB) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < WIN; ++u) {
-            if (k0 + u >= i1) break;
-            if (u & 1) {
-                oA += vA[u];
-                oB += vB[u];
-            } else {
-                eA += vA[u];
-                eB += vB[u];
-            }
-        }
-    }
-    const double sA = eA + oA, sB = eB + oB;
-    if (lane == 0 && a.local_out) a.local_out[s] = sA - klv;   // column 0: ll
-    if (grad && a.grad_out) {
-        if (cA >= 2) a.grad_out[(size_t)NP * s + cA - 2] = sA - kA;
-        if (cB < ncol) a.grad_out[(size_t)NP * s + cB - 2] = sB - kB;
-    }
-    return __shfl_sync(0xffffffffu, sA, 1) - klv;   // column 1: owned ll
-}
 
 // ---------------------------------------------------------------------------------
 // tasks of the compute warps
@@ -1000,30 +957,66 @@ __global__ void __launch_bounds__(128) k_tables(ItemArgs a) {
 }
 
 // The per-source epilogues and the total, after every item: the item kernel's
-// programmatic dependent, waiting for it to finish.  A CTA takes FIN_W sources (a warp
-// each) and adds their shares of the total in warp order; the last CTA to finish adds the
-// CTA sums in order (its warps over contiguous ranges, lanes strided, then warp order)
-// and resets the counter for the next launch.
-constexpr int FIN_W = 8;
+// programmatic dependent, waiting for it to finish.  One CTA of FIN_W warps per source:
+// warp w adds the columns of the source's items w, w + FIN_W, ... in item order (FP64;
+// lane c columns c and c + 32, loaded FIN_WIN items at a time before any is added), the
+// CTA then adds the warps' sums in warp order and subtracts the KL: the local objective
+// and gradient, and the source's share of the total (the ll of the pixels its items own,
+// minus its KL).  The last CTA to finish adds the shares in source order (its warps over
+// contiguous ranges, lanes strided, then warp order) and resets the counter.
+constexpr int FIN_W = 4, FIN_WIN = 16;
 __global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
-    __shared__ double sh[FIN_W];
+    __shared__ double sh[FIN_W][64];
     __shared__ int s_last;
     pdl_wait();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = (int)blockIdx.x * FIN_W + w;
-    const double share = s < a.n_src ? source_epilogue(a, s) : 0.0;
-    if (!a.total_out) return;
-    if (lane == 0) sh[w] = share;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double c = 0.0;
-        for (int i = 0; i < FIN_W; ++i) c += sh[i];
-        a.src_total[blockIdx.x] = c;
-        s_last = arrive_acq_rel(a.grp_done) == (int)gridDim.x - 1;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, s = (int)blockIdx.x;
+    const bool grad = a.mode >= MODE_GRAD;
+    const int ncol = grad ? ZPCOLS : 2;
+    const int i0 = __ldcg(a.sitem_off + s), i1 = __ldcg(a.sitem_off + s + 1);
+    const int cA = lane, cB = lane + 32;
+    double sA = 0.0, sB = 0.0;
+    for (int k0 = i0 + w; k0 < i1; k0 += FIN_W * FIN_WIN) {
+        double vA[FIN_WIN], vB[FIN_WIN];
+#pragma unroll
+        for (int u = 0; u < FIN_WIN; ++u) {
+            const int k = k0 + FIN_W * u;
+            const double* r = a.part + (size_t)k * ZPCOLS;
+            vA[u] = (k < i1 && cA < ncol) ? __ldcg(r + cA) : 0.0;
+            vB[u] = (k < i1 && cB < ncol) ? __ldcg(r + cB) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < FIN_WIN; ++u) {
+            if (k0 + FIN_W * u >= i1) break;
+            sA += vA[u];
+            sB += vB[u];
+        }
     }
+    sh[w][cA] = sA;
+    sh[w][cB] = sB;
+    s_last = 0;
+    __syncthreads();
+    if (w == 0) {
+        double tA = 0.0, tB = 0.0;
+#pragma unroll
+        for (int v = 0; v < FIN_W; ++v) {
+            tA += sh[v][cA];
+            tB += sh[v][cB];
+        }
+        const double klv = __ldcg(a.kl + s);
+        if (lane == 0 && a.local_out) a.local_out[s] = tA - klv;   // column 0: ll
+        if (grad && a.grad_out) {
+            if (cA >= 2) a.grad_out[(size_t)NP * s + cA - 2] = tA - __ldcg(a.kl_grad + (size_t)NP * s + cA - 2);
+            if (cB < ncol) a.grad_out[(size_t)NP * s + cB - 2] = tB - __ldcg(a.kl_grad + (size_t)NP * s + cB - 2);
+        }
+        if (lane == 1 && a.total_out) {
+            a.src_total[s] = tA - klv;   // column 1: owned ll
+            s_last = arrive_acq_rel(a.grp_done) == (int)gridDim.x - 1;
+        }
+    }
+    if (!a.total_out) return;
     __syncthreads();
     if (!s_last) return;
-    const int n = (int)gridDim.x, per = (n + FIN_W - 1) / FIN_W;
+    const int n = a.n_src, per = (n + FIN_W - 1) / FIN_W;
     const int b0 = w * per, b1 = min(n, b0 + per);
     double acc = 0.0;
     for (int c0 = b0; c0 < b1; c0 += 32 * 16) {
@@ -1037,12 +1030,12 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
         for (int u = 0; u < 16; ++u) acc += x[u];
     }
     acc = warp_dsum(acc);
-    __syncthreads();   // every warp has read sh (above) before it is reused
-    if (lane == 0) sh[w] = acc;
+    __syncthreads();   // every warp is past its reads of sh
+    if (lane == 0) sh[w][0] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < FIN_W; ++i) t += sh[i];
+        for (int v = 0; v < FIN_W; ++v) t += sh[v][0];
         *a.total_out = t;
         a.grp_done[0] = 0;
     }
@@ -1273,7 +1266,7 @@ cudaError_t launch_items_stage(const DevProblem& P, int stage, int mode, cudaStr
                                : items_launch<MODE_GRAD>(a, P.tune_items, n_sm, st);
     }
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((P.n_src + FIN_W - 1) / FIN_W));
+    cfg.gridDim = dim3((unsigned)P.n_src);
     cfg.blockDim = dim3(32 * FIN_W);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

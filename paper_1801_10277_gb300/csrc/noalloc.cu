@@ -12,8 +12,11 @@
 // The scratch array is a file-scope __device__ array, so every GPU that loads the
 // library holds it (CELESTE_NOALLOC_SCRATCH_BYTES) until the process exits.  In host
 // code its name is only a host-side stand-in for the symbol; the device address is
-// obtained with cudaGetSymbolAddress once per device (with that device current) on
-// the first call made on that device, and passed to the kernels.
+// obtained with cudaGetSymbolAddress on every call made outside a stream capture (with
+// the device current), so a device reset or a recreated context is picked up; a call
+// inside a capture uses the address of the last uncaptured call on that device (the
+// first call on a device must therefore be uncaptured).  The model is checked and
+// converted by build_model_dev, as in celeste_problem_create.
 #include <math.h>
 #include <string.h>
 
@@ -107,37 +110,6 @@ __global__ void k_noalloc_setup(unsigned char* base, ImgMeta im, ModelDev md, in
     }
 }
 
-bool chol_inv4(const double* S, double* inv, double* logdet) {
-    double L[4][4] = {{0}};
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double s = S[4 * i + j];
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            if (i == j) {
-                if (!(s > 0)) return false;
-                L[i][i] = sqrt(s);
-            } else {
-                L[i][j] = s / L[j][j];
-            }
-        }
-    *logdet = 0;
-    for (int i = 0; i < 4; ++i) *logdet += 2.0 * log(L[i][i]);
-    for (int c = 0; c < 4; ++c) {   // solve L L^T x = e_c
-        double y[4], x[4];
-        for (int i = 0; i < 4; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-            y[i] = s / L[i][i];
-        }
-        for (int i = 3; i >= 0; --i) {
-            double s = y[i];
-            for (int k = i + 1; k < 4; ++k) s -= L[k][i] * x[k];
-            x[i] = s / L[i][i];
-        }
-        for (int i = 0; i < 4; ++i) inv[4 * i + c] = x[i];
-    }
-    return true;
-}
 
 }  // namespace
 
@@ -157,10 +129,6 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
     if (im->band < 0 || im->band > 4 || im->n_psf < 1 || im->n_psf > MAXPSF || !im->psf ||
         !(im->nmgy_per_count > 0) || (!d_sky_map && !(im->sky > 0)))
         return na_fail(CELESTE_ERR_ARG, "bad image description");
-    if (model->n_exp < 1 || model->n_dev < 1 || model->n_exp + model->n_dev > MAXPROF ||
-        model->n_color_comp != NCOMP || !model->exp_mix || !model->dev_mix || !model->prior_r ||
-        !model->prior_c || !(model->prior_star > 0 && model->prior_star < 1))
-        return na_fail(CELESTE_ERR_ARG, "bad model description");
     // the patch is the whole image of this call: shift the WCS so pixel (x0, y0) is the origin
     ImgMeta M;
     memset(&M, 0, sizeof M);
@@ -183,45 +151,36 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
     }
     fill_float_copies(M);
     ModelDev md;
-    memset(&md, 0, sizeof md);
-    md.n_exp = model->n_exp;
-    md.n_dev = model->n_dev;
-    for (int j = 0; j < model->n_exp + model->n_dev; ++j) {
-        const double* m = j < model->n_exp ? model->exp_mix + 2 * j
-                                           : model->dev_mix + 2 * (j - model->n_exp);
-        if (!(m[1] > 0)) return na_fail(CELESTE_ERR_ARG, "profile variance must be > 0");
-        md.prof_w[j] = m[0];
-        md.prof_nu[j] = m[1];
+    {
+        const char* why = nullptr;
+        const celeste_status ms = build_model_dev(model, md, &why);
+        if (ms != CELESTE_OK) return na_fail(ms, why);
     }
-    md.prior_star = model->prior_star;
-    for (int i = 0; i < 2; ++i) {
-        md.prior_r[i][0] = model->prior_r[2 * i];
-        md.prior_r[i][1] = model->prior_r[2 * i + 1];
-        for (int d = 0; d < NCOMP; ++d) {
-            const double* pc = model->prior_c + (size_t)(i * NCOMP + d) * 21;
-            md.prior_w[i][d] = pc[0];
-            for (int j = 0; j < 4; ++j) md.prior_mu[i][d][j] = pc[1 + j];
-            if (!chol_inv4(pc + 5, md.prior_P[i][d], &md.prior_logdet[i][d]))
-                return na_fail(CELESTE_ERR_NOT_PD, "colour prior covariance not positive definite");
-        }
-    }
-    fill_float_copies(md);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
         return na_fail(CELESTE_ERR_CUDA, "no current CUDA device");
+    cudaStream_t st = (cudaStream_t)stream;
+    // The scratch array's address: looked up on every call made outside stream capture
+    // (so a device reset or a recreated context is picked up); inside a capture the
+    // address of the last uncaptured call on this device is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess)
+        return na_fail(CELESTE_ERR_CUDA, "cudaStreamIsCapturing failed");
     unsigned char* base;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p)
                 return na_fail(CELESTE_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
             g_na_ptr[dev] = (unsigned char*)p;
+        } else if (!g_na_ptr[dev]) {
+            return na_fail(CELESTE_ERR_ARG,
+                           "the first call on a device must be made outside a stream capture");
         }
         base = g_na_ptr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
     k_noalloc_setup<<<1, 64, 0, st>>>(base, M, md, w, h);
     DevProblem P{};
     P.n_img = 1; P.n_src = 1; P.n_patch = 1;

@@ -59,6 +59,10 @@ def test_reference_arm_line():
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "field_500src_5x2048x1489"
     assert d["config"]["source_pixels"] == 1001730
+    # the GPU arm's config keys, so that the two lines name the same workload the same way
+    assert {"workload", "sources", "source_pixels", "images", "image", "precision", "l2", "tuning",
+            "parallelism"} <= set(d["config"])
+    assert d["config"]["images"] == 5 and d["config"]["image"] == "2048x1489"
     sp = d["ms_per_step"] / 1000.0 * d["value"]
     assert 1 <= sp <= d["config"]["source_pixels"] * 1.000001
 

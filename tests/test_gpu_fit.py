@@ -1,7 +1,10 @@
 """Block-coordinate trust-region Newton fits (Section IV-D) on the GPU against the
 oracle's fit from the same starts: positions within 1e-3 px and r-band expected
-fluxes within 1e-4 relative for sources both sides report converged, in both
-precisions."""
+fluxes within 1e-4 relative for every moving source, in both precisions.  A source's
+status (stopped by the gain test, or at the iteration cap) may differ between the two
+sides only as converged against capped: a source whose predicted gains hover at the
+stopping threshold can stop one iteration before the cap on one side and reach it on
+the other; neither side may report a non-finite objective."""
 import numpy as np
 import pytest
 
@@ -42,16 +45,27 @@ def _compare(cel, prob, which=None, max_sweeps=20, sweep_tol=1e-12):
         th, it, st, el = P.fit(prob.theta, which=which, precision=prec, max_sweeps=max_sweeps,
                                sweep_tol=sweep_tol)
         assert np.all(it[moving] <= 50 * max_sweeps * (2 if prec == cel.FP32 else 1))
-        both = [s for s in moving if st[s] == 0 and o_st[s] == 0]
-        assert len(both) >= 0.75 * len(moving), (prec, st[moving], o_st[moving])
-        for s in both:
+        # every moving source is compared
+        for s in moving:
             assert np.abs(th[s, 0:2] - o_th[s, 0:2]).max() <= 1e-3, (prec, s, th[s, :2], o_th[s, :2])
             assert abs(rflux(th[s]) / rflux(o_th[s]) - 1) <= 1e-4, (prec, s, th[s], o_th[s])
+        _check_status(prec == cel.FP64, moving, st, it, o_st, o_it)
         assert abs(el - o_el) <= (1e-8 if prec == cel.FP64 else 1e-5) * abs(o_el), (prec, el, o_el)
         # sources outside `which` never move
         still = np.setdiff1d(np.arange(prob.n_src), moving)
         np.testing.assert_array_equal(th[still], prob.theta[still])
     P.close()
+
+
+def _check_status(fp64, moving, st, it, o_st, o_it, o_index=None):
+    """Statuses of the moving sources: 0 converged, 1 at the iteration cap, 2 non-finite.
+    Prints every disagreement with both sides' iteration counts."""
+    o_index = moving if o_index is None else o_index
+    diff = [(int(s), int(st[s]), int(o_st[o]), int(it[s]), int(o_it[o]))
+            for s, o in zip(moving, o_index) if st[s] != o_st[o]]
+    print(f"{'FP64' if fp64 else 'FP32'}: status differs for (source, GPU, oracle, GPU iterations, "
+          f"oracle iterations) {diff}")
+    assert all(st[s] in (0, 1) for s in moving) and all(o_st[o] in (0, 1) for o in o_index)
 
 
 def test_fit_tiny_two_sources(cel):
@@ -74,6 +88,58 @@ def independent_set(prob, k):
 def test_fit_crowded_subset(cel):
     prob = synth.config(2)
     _compare(cel, prob, which=independent_set(prob, 8), max_sweeps=2)
+
+
+def closure_subset(prob, which):
+    """The sub-problem of `which` and their neighbours (every other source whose patches
+    overlap theirs, i.e. every source their pixels see), and the positions of `which` in
+    it."""
+    keep = set(int(s) for s in which)
+    for s in which:
+        keep |= set(prob.nbrs[prob.nbr_offsets[s]:prob.nbr_offsets[s + 1]].tolist())
+    keep = np.array(sorted(keep))
+    pos = np.searchsorted(keep, np.asarray(which))
+    return synth.subset(prob, keep), pos.astype(np.int32)
+
+
+def test_fit_field_sample(cel):
+    """32 sources of the one-field workload (500 sources over five 2048 x 1489 images), no
+    two overlapping: the GPU fits them in the whole field, the oracle in the sub-problem
+    of them and their neighbours.  Per-source positions and fluxes at the fit targets, in
+    both precisions."""
+    prob = synth.config(1)
+    which = independent_set(prob, 32)
+    assert len(which) == 32
+    sub, pos = closure_subset(prob, which)
+    o_th, o_it, o_st, _, _ = Oracle(sub).fit(sub.theta, which=pos, max_sweeps=2, sweep_tol=1e-12)
+    P = cel.Problem(prob)
+    for prec in (cel.FP64, cel.FP32):
+        th, it, st, _ = P.fit(prob.theta, which=which, precision=prec, max_sweeps=2, sweep_tol=1e-12)
+        for k, s in enumerate(which):
+            o = o_th[pos[k]]
+            assert np.abs(th[s, 0:2] - o[0:2]).max() <= 1e-3, (prec, s, th[s, :2], o[:2])
+            assert abs(rflux(th[s]) / rflux(o) - 1) <= 1e-4, (prec, s)
+        _check_status(prec == cel.FP64, which, st, it, o_st, o_it, pos)
+        still = np.setdiff1d(np.arange(prob.n_src), which)
+        np.testing.assert_array_equal(th[still], prob.theta[still])
+    P.close()
+
+
+def test_fit_fp32_sweeps_without_the_fp64_polish(cel):
+    """The FP32 fit's own result (refine_fp64 = 0: FP32 pixel sums throughout, FP64
+    accumulation) against the oracle's FP64 fit, on an independent set of the crowded
+    region, at the fit targets."""
+    prob = synth.config(2)
+    which = independent_set(prob, 8)
+    o_th, _, o_st, _, _ = Oracle(prob).fit(prob.theta, which=which, max_sweeps=2, sweep_tol=1e-12)
+    P = cel.Problem(prob)
+    th, it, st, _ = P.fit(prob.theta, which=which, precision=cel.FP32, refine_fp64=0, max_sweeps=2,
+                          sweep_tol=1e-12)
+    dpos = max(np.abs(th[s, 0:2] - o_th[s, 0:2]).max() for s in which)
+    dflux = max(abs(rflux(th[s]) / rflux(o_th[s]) - 1) for s in which)
+    print(f"FP32 without the FP64 polish: max position error {dpos:.3g} px, max flux error {dflux:.3g}")
+    assert dpos <= 1e-3 and dflux <= 1e-4, (dpos, dflux)
+    P.close()
 
 
 def test_fit_rejects_parameters_outside_the_box(cel):

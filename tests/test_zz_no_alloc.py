@@ -71,3 +71,70 @@ def test_noalloc_rejects_patches_beyond_its_scratch():
                                     None, None, d_g)
     assert e.value.status == cel.ERR_ARG
     assert "101" in str(e.value)
+
+
+def _compare(torch, cel, prob, patch, sky=None):
+    """Both precisions, the allocation-free call against celeste_elbo_grad on the same
+    one-source problem; sky (a [H][W] float32 map of the whole image, or None) is passed
+    to the allocation-free call as the patch's device sky map."""
+    x0, y0, w, h = patch
+    P = cel.Problem(prob)
+    im = prob.images[0]
+    d_pix = torch.tensor(np.ascontiguousarray(im.pixels[y0:y0 + h, x0:x0 + w]), device="cuda")
+    d_sky = None if sky is None else torch.tensor(np.ascontiguousarray(sky[y0:y0 + h, x0:x0 + w]), device="cuda")
+    d_th = torch.tensor(prob.theta[0], dtype=torch.float64, device="cuda")
+    for prec in (cel.FP64, cel.FP32):
+        tot, loc, g = P.elbo_grad(prob.theta, precision=prec)
+        te, tg = TOL[prec]
+        d_tot = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+        d_loc = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+        d_g = torch.full((44,), np.nan, dtype=torch.float64, device="cuda")
+        cel.patch_elbo_grad_noalloc(im, prob.exp_mix, prob.dev_mix, prob.prior_star, prob.prior_r,
+                                    prob.prior_c, patch, d_pix, d_th, d_tot, d_loc, d_g, d_sky_map=d_sky,
+                                    precision=prec)
+        torch.cuda.synchronize()
+        assert abs(d_tot.item() - tot) <= te * abs(tot), (prec, d_tot.item(), tot)
+        assert abs(d_loc.item() - loc[0]) <= te * abs(loc[0])
+        assert np.linalg.norm(d_g.cpu().numpy() - g[0]) <= tg * np.linalg.norm(g[0])
+    P.close()
+
+
+def test_noalloc_with_a_device_sky_map():
+    """A per-pixel sky (the image's sky map, indexed in the patch's frame)."""
+    torch, cel, prob, patch = _setup()
+    im = prob.images[0]
+    yy, xx = np.mgrid[0:im.pixels.shape[0], 0:im.pixels.shape[1]]
+    sky = (140.0 + 0.3 * xx + 0.2 * yy + 5.0 * np.sin(0.3 * xx) * np.cos(0.2 * yy)).astype(np.float32)
+    im.sky_map = sky
+    _compare(torch, cel, prob, patch, sky=sky)
+
+
+def test_noalloc_at_its_largest_patch():
+    """A 101 x 101 patch: every item and tile slot of the static scratch layout in use."""
+    torch, cel, _, _ = _setup()
+    th = H.star_theta(55.2, 49.7, a_star=0.4, r2=0.03, c2=0.02)
+    th[synth.I_AXIS], th[synth.I_ANGLE], th[synth.I_SCALE] = 0.6, 1.3, 3.1
+    patch = (3, 2, 101, 101)
+    prob = H.problem(th, H=110, W=112, bands=(1,), patches=(np.array([0, 1], np.int32),
+                                                           np.array([(0,) + patch], np.int32)),
+                     wcs=[1.01, 0.03, -0.02, 0.98, -0.7, 1.2], seed=9)
+    _compare(torch, cel, prob, patch)
+
+
+def test_noalloc_rejects_a_bad_model():
+    """The model is checked as by celeste_problem_create: a brightness-prior variance of
+    zero and a zero colour-prior weight are CELESTE_ERR_ARG, not a NaN ELBO."""
+    torch, cel, prob, (x0, y0, w, h) = _setup()
+    im = prob.images[0]
+    d_pix = torch.tensor(np.ascontiguousarray(im.pixels[y0:y0 + h, x0:x0 + w]), device="cuda")
+    d_th = torch.tensor(prob.theta[0], dtype=torch.float64, device="cuda")
+    d_g = torch.zeros(44, dtype=torch.float64, device="cuda")
+    bad_r = np.array(prob.prior_r, dtype=np.float64, copy=True)
+    bad_r.reshape(-1)[1] = 0.0
+    bad_c = np.array(prob.prior_c, dtype=np.float64, copy=True)
+    bad_c.reshape(2, -1, 21)[1, 3, 0] = 0.0
+    for pr, pc in ((bad_r, prob.prior_c), (prob.prior_r, bad_c)):
+        with pytest.raises(cel.CelesteError) as e:
+            cel.patch_elbo_grad_noalloc(im, prob.exp_mix, prob.dev_mix, prob.prior_star, pr, pc,
+                                        (x0, y0, w, h), d_pix, d_th, None, None, d_g)
+        assert e.value.status == cel.ERR_ARG
