@@ -41,8 +41,10 @@ from paper_1801_10277_gb300 import synth  # noqa: E402
 FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
 # DRAM bytes (read + write) per launch of the item kernel on the one-field workload, from one
-# ncu capture (profiles/); emptied whenever the kernel changes after the capture.
-DRAM_BYTES_PER_LAUNCH = {}
+# ncu capture (profiles/k_items_field_500src.md); emptied whenever the kernel changes after
+# the capture.
+DRAM_BYTES_PER_LAUNCH = {"items": 26233600}
+DRAM_BYTES_SOURCE = "ncu capture of one k_items launch, profiles/k_items_field_500src.md (imported, not measured here)"
 FP32_LANES = 128
 XU_LANES = 16   # MUFU ex2 results per SM per clock
 SM_MHZ_MAX = 2070.0
@@ -459,6 +461,7 @@ def main():
     traffic = DRAM_BYTES_PER_LAUNCH.get(dom) if args.workload == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                 "frac": achieved / peak_fp32, "traffic": traffic,
+                "traffic_source": DRAM_BYTES_SOURCE if traffic is not None else None,
                 "kernel": "items: k_items, the FP32 value + gradient pass over every item (the tables "
                           "and KL terms, and the per-source epilogues, are the stages 'tables' and 'finish')",
                 "flop_per_launch": work[dom],

@@ -144,10 +144,10 @@ int64_t celeste_source_pixels(const celeste_problem* prob);
 
 /*
  * Work decomposition of a problem (host read, no GPU work), for cost accounting:
- * out[0] sources, [1] patches, [2] work items (<= 256 pixels of one patch each),
- * [3] work items of singly covered pixels in the FP32 value / gradient path (each patch's
- * pixels that no other patch covers, in items of <= 1024), [4] singly covered
- * source-pixels, [5] 16 x 16 tiles covered by two or more patches (the gather's cells),
+ * out[0] sources, [1] patches, [2] work items of the FP64 and Hessian paths (<= 256
+ * pixels of one patch each), [3] items of the FP32 value / gradient path (<= 512 pixels
+ * of one patch each, fewer on a problem too small to give every resident CTA two),
+ * [4] singly covered source-pixels, [5] 16 x 16 tiles covered by two or more patches,
  * [6] source-pixels in all, [7] (source-pixel, other covering patch) pairs: the other
  * sources' E and Var the FP32 value / gradient path evaluates at multiply covered pixels.
  * Writes min(n, 8) entries; returns the number written, or CELESTE_ERR_ARG for a null

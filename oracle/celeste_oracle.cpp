@@ -699,10 +699,13 @@ double local_value(const OProblem& P, const std::vector<PatchVals>& pv, const do
 // Unconstrained coordinates t (41) -> constrained theta (44) for the trust region:
 //   u, angle, r1, c1: identity; scale, r2, c2: exp;
 //   e_dev, e_axis: 0.01 + 0.98 sigmoid;  a_star = 0.005 + 0.99 sigmoid, a_gal = 1 - a_star;
-//   k_i: softmax with the last component's logit fixed at 0 (7 free per type).
+//   k_i: softmax with the last component's logit fixed at 0 (7 free per type), plus
+//   K_LO = 1e-120: a weight whose softmax underflows keeps 1 / k and 1 / k^2 (the KL's
+//   derivatives in k) finite in FP64; for every weight above ~1e-104 the sum is the
+//   softmax itself, bit for bit.
 
 constexpr int NT = 41;
-constexpr double BOX_LO = BOX_LO_, BOX_HI = BOX_HI_, A_LO = A_LO_, A_HI = A_HI_;
+constexpr double BOX_LO = BOX_LO_, BOX_HI = BOX_HI_, A_LO = A_LO_, A_HI = A_HI_, K_LO = 1e-120;
 
 inline double sigm(double x) { return 1.0 / (1.0 + std::exp(-x)); }
 inline double logit(double p) { return std::log(p / (1.0 - p)); }
@@ -753,7 +756,7 @@ void from_free(const double* t, Jet<NT, H>* th) {
             den = den + e[d];
         }
         e[7] = jconst<NT, H>(1.0);
-        for (int d = 0; d < 8; ++d) th[IK + 8 * i + d] = e[d] / den;
+        for (int d = 0; d < 8; ++d) th[IK + 8 * i + d] = jconst<NT, H>(K_LO) + e[d] / den;
     }
 }
 

@@ -283,11 +283,11 @@ class Problem:
     def source_pixels(self):
         return int(self.L.celeste_source_pixels(self.h))
 
-    STAT_KEYS = ("sources", "patches", "items", "fused_items", "fused_source_pixels", "tiles",
+    STAT_KEYS = ("sources", "patches", "items", "fp32_items", "single_source_pixels", "tiles",
                  "source_pixels", "other_evals")
 
     def stats(self):
-        """Work decomposition: {sources, patches, items, fused_items, fused_source_pixels,
+        """Work decomposition: {sources, patches, items, fp32_items, single_source_pixels,
         tiles, source_pixels, other_evals}."""
         out = np.zeros(len(self.STAT_KEYS), np.int64)
         n = self.L.celeste_problem_stats(self.h, _p(out), len(out))

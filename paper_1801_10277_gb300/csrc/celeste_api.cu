@@ -349,7 +349,7 @@ int64_t celeste_source_pixels(const celeste_problem* pr) { return pr ? pr->P.n_s
 int32_t celeste_problem_stats(const celeste_problem* pr, int64_t* out, int32_t n) {
     if (!pr || !out) return fail(CELESTE_ERR_ARG, "null problem or output");
     const DevProblem& P = pr->P;
-    const int64_t v[8] = {P.n_src, P.n_patch, P.n_item, (int64_t)P.n_sitem - P.n_smulti, pr->sp_single, P.n_tile, P.n_sp,
+    const int64_t v[8] = {P.n_src, P.n_patch, P.n_item, (int64_t)P.n_sitem, pr->sp_single, P.n_tile, P.n_sp,
                           pr->other_evals};
     const int m = n < 8 ? (n > 0 ? n : 0) : 8;
     for (int i = 0; i < m; ++i) out[i] = v[i];
@@ -499,7 +499,18 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     }
     // The FP32 value / gradient kernel's items: per source, per patch, the patch's pixels
     // with the multiply covered ones first (row-major), then the singly covered ones, cut
-    // into ceil(n / ZIMAX) items of near-equal size.
+    // into ceil(n / cap) items of near-equal size.  cap = ZIMAX, or for a problem too small
+    // to give two items to each of the kernel's resident CTAs (two per SM), the pixel count
+    // that would, rounded up to 64 and at least 128.
+    int item_cap = ZIMAX;
+    {
+        int dev = 0, n_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
+            n_sm = 152;
+        const int64_t per = (n_sp + 4LL * n_sm - 1) / (4LL * n_sm);
+        item_cap = (int)std::min<int64_t>(ZIMAX, std::max<int64_t>(128, (per + 63) / 64 * 64));
+    }
     struct SItem {
         int32_t patch, src, n, nm;
         int64_t q0;   // first pixel (spix)
@@ -521,7 +532,7 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
             for (int q = 0; q < npx; ++q)
                 if (f[q]) spix.push_back(((q / g.w) << 16) | (q % g.w));
             sp_single += npx - nm_all;
-            const int k = (npx + ZIMAX - 1) / ZIMAX, base = npx / k, rem = npx % k;
+            const int k = (npx + item_cap - 1) / item_cap, base = npx / k, rem = npx % k;
             for (int j = 0, o = 0; j < k; ++j) {
                 const int n = base + (j < rem ? 1 : 0);
                 const int nm = std::max(0, std::min(n, nm_all - o));

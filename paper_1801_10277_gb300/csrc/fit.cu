@@ -39,13 +39,16 @@ cudaError_t launch_finalize_hess(const DevProblem& P, const double* d_theta, dou
 
 namespace {
 
-constexpr double BOX_LO = 0.01, BOX_HI = 0.99, A_LO = 0.005, A_HI = 0.995;
+// K_LO: added to every softmax weight, so that a weight whose softmax underflows keeps
+// 1 / k and 1 / k^2 (the KL's derivatives in k) finite in FP64 (above ~1e-104 the sum is
+// the softmax itself)
+constexpr double BOX_LO = 0.01, BOX_HI = 0.99, A_LO = 0.005, A_HI = 0.995, K_LO = 1e-120;
 enum : int { ST_ACTIVE = -1, ST_CONVERGED = 0, ST_MAXITER = 1, ST_NONFINITE = 2 };
 
 __device__ __forceinline__ double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 // theta(t): identity for u, angle, r1, c1; exp for scale, r2, c2; box sigmoids for
-// e_dev, e_axis and the star probability; softmax (last logit 0) for k.
+// e_dev, e_axis and the star probability; softmax (last logit 0) plus K_LO for k.
 __device__ void free_to_theta(const double* t, double* th) {
     th[0] = t[0];
     th[1] = t[1];
@@ -69,7 +72,7 @@ __device__ void free_to_theta(const double* t, double* th) {
         double ex[8], den = 0.0;
         for (int e = 0; e < 7; ++e) den += (ex[e] = exp(t[27 + 7 * i + e] - m));
         den += (ex[7] = exp(-m));
-        for (int d = 0; d < 8; ++d) th[P_K + 8 * i + d] = ex[d] / den;
+        for (int d = 0; d < 8; ++d) th[P_K + 8 * i + d] = K_LO + ex[d] / den;
     }
 }
 

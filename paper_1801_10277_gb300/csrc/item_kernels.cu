@@ -1044,7 +1044,8 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
 // The items, on persistent CTAs of four compute warps and a producer warp.  The producer
 // keeps the next two items in the two stages (item i + 2 goes to the stage of item i as
 // soon as the compute warps are done with it), one task record ahead in registers and
-// one queue slot claimed beyond that.  The last compute warp to finish an item writes its
+// one queue slot claimed beyond that.  CTA c's first two items are slots c and c + G
+// (G CTAs); later slots come from the queue counter.  The last compute warp to finish an item writes its
 // record.
 template <int MODE, int PX, int NPE, int NPD, int MINB, int UNR>
 __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_items(ItemArgs a) {
@@ -1069,15 +1070,18 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
     int32_t* queue = a.ready + a.n_patch;
     if (w == NWC) {
         bool all_built = false;
-        int q0 = 0;
-        if (lane == 0) q0 = atomicAdd(queue, 3);
-        q0 = __shfl_sync(0xffffffffu, q0, 0);
-        const int4 r0 = load_task(a, q0), r1 = load_task(a, q0 + 1);
-        int4 ra = load_task(a, q0 + 2);   // the record of the next item to prepare
+        // slots 0 .. 2 G - 1 (G CTAs) are dealt out, one per stage of every CTA, so that
+        // a queue of few items spreads over all CTAs; the rest are claimed one at a time
+        const int G = (int)gridDim.x, base = 2 * G;
+        int qa = 0;
+        if (lane == 0) qa = base + atomicAdd(queue, 1);
+        qa = __shfl_sync(0xffffffffu, qa, 0);
+        const int4 r0 = load_task(a, (int)blockIdx.x), r1 = load_task(a, (int)blockIdx.x + G);
+        int4 ra = load_task(a, qa);   // the record of the next item to prepare
         prepare<MODE>(a, r0, smem, &tasks[0], &full[0], all_built);
         prepare<MODE>(a, r1, smem + ST_BYTES, &tasks[1], &full[1], all_built);
         int qb = 0;   // lane 0: the slot after that
-        if (lane == 0) qb = atomicAdd(queue, 1);
+        if (lane == 0) qb = base + atomicAdd(queue, 1);
         for (int i = 0;; ++i) {
             const int b = i & 1;
             __syncwarp();
@@ -1085,7 +1089,7 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
             if (!mbar_wait_launch(&reduced[b], (i >> 1) & 1, a.status)) break;
             prepare<MODE>(a, ra, smem + b * ST_BYTES, &tasks[b], &full[b], all_built);
             ra = load_task(a, __shfl_sync(0xffffffffu, qb, 0));
-            if (lane == 0) qb = atomicAdd(queue, 1);
+            if (lane == 0) qb = base + atomicAdd(queue, 1);
         }
         // this grid completes only after the table kernel (and its KL terms) has, so the
         // epilogue kernel that waits for this grid sees both

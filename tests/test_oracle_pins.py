@@ -472,6 +472,30 @@ def test_unconstrained_map_round_trip_and_jacobian(cfg0):
         assert abs(back[synth.I_K + 8 * i:synth.I_K + 8 * i + 8].sum() - 1) < 1e-14
 
 
+def test_free_map_keeps_underflowing_weights_normal(cfg0):
+    """A colour-component logit far below the others (its softmax weight underflows):
+    the map keeps the weight at or above 1e-120, so the local objective's derivatives in
+    the 44 parameters and in the 41 free coordinates stay finite, and the free gradient
+    along that logit vanishes (d k / d t = k (1 - k) ~ 1e-120).  Away from underflow
+    the weights are the softmax itself."""
+    o = Oracle(cfg0)
+    s = 1
+    th = cfg0.theta.copy()
+    t = to_free(th[s])
+    ks = slice(synth.I_K, synth.I_K + 8)
+    ex = np.exp(np.append(t[27:34], 0.0))
+    np.testing.assert_allclose(from_free(t)[ks], ex / ex.sum(), rtol=1e-15, atol=0)
+    t[27 + 3] = -800.0   # exp(-800) is 0 in FP64
+    x = from_free(t)
+    assert np.all(x[ks] >= 1e-120) and x[synth.I_K + 3] < 1.01e-120
+    th[s] = x
+    _, g, h = o.derivs(th, which=[s], hess=True)
+    assert np.isfinite(g).all() and np.isfinite(h).all()
+    gt, ht = free_derivs(t, g[0], h[0])
+    assert np.isfinite(gt).all() and np.isfinite(ht).all()
+    assert abs(gt[27 + 3]) < 1e-100 * np.abs(gt).max()
+
+
 def test_free_derivatives_match_finite_differences(cfg0):
     """Gradient / Hessian in the 41 unconstrained coordinates (chain rule through the
     map) against central differences of ELBO_s(theta(t))."""
