@@ -70,7 +70,9 @@ enum {
     CELESTE_ERR_NONFINITE = -3,  /* NaN/Inf in inputs, or produced for some source */
     CELESTE_ERR_CUDA = -4,       /* a CUDA runtime call failed */
     CELESTE_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
-    CELESTE_ERR_NOMEM = -6       /* device allocation failed */
+    CELESTE_ERR_NOMEM = -6,      /* device allocation failed */
+    CELESTE_ERR_BOUNDS = -7      /* a device-side bounds check failed (libraries built with
+                                    CELESTE_CHECK_BOUNDS only; the access was skipped) */
 };
 
 enum { CELESTE_FP64 = 0, CELESTE_FP32_ACC64 = 1 };

@@ -1,5 +1,7 @@
 """Compile libceleste (CUDA, sm_103a) in-tree: one nvcc -c per translation unit in
-parallel, then one shared-library link.  Output: paper_1801_10277_gb300/_build/libceleste.so"""
+parallel, then one shared-library link.  Output: paper_1801_10277_gb300/_build/libceleste.so;
+with checked=True the same sources with -DCELESTE_CHECK_BOUNDS (device-side bounds checks
+that record CELESTE_ERR_BOUNDS instead of trapping) into _build_checked/libceleste.so."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -9,6 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libceleste.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libceleste.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -24,14 +28,17 @@ def _newest_input():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
+def build(force=False, verbose=False, extra=(), checked=False):
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if checked:
+        extra = (*extra, "-DCELESTE_CHECK_BOUNDS")
+    os.makedirs(out_dir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -46,15 +53,15 @@ def build(force=False, verbose=False, extra=()):
         for _, log in results:
             print(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force=True, verbose="-v" in sys.argv))
+    print(build(force=True, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

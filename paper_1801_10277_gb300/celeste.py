@@ -21,7 +21,7 @@ FP32 = 1          # FP32 per-pixel arithmetic, FP64 accumulation
 SCHED_COLOUR = 0    # fit schedule: one batch per colour of a greedy colouring
 SCHED_CYCLADES = 1  # fit schedule: connected components of random samples
 
-OK, ERR_ARG, ERR_NOT_PD, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_ARG, ERR_NOT_PD, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 
 
 class CelesteError(RuntimeError):
@@ -86,7 +86,9 @@ SCORE_FIELDS = ["position", "missed_gal", "missed_star", "brightness"] + \
 
 
 def lib_path():
-    return _build.LIB
+    """The library the binding loads: the checked build (device-side bounds checks) when
+    the environment sets CELESTE_CHECK_BOUNDS=1, else the normal build."""
+    return _build.LIB_CHECKED if os.environ.get("CELESTE_CHECK_BOUNDS") == "1" else _build.LIB
 
 
 def load(build_if_missing=False):
@@ -97,7 +99,7 @@ def load(build_if_missing=False):
     path = lib_path()
     if not os.path.exists(path):
         if build_if_missing:
-            _build.build()
+            _build.build(checked=path == _build.LIB_CHECKED)
         else:
             raise RuntimeError(f"libceleste is not built ({path}); run __graft_entry__.build()")
     L = C.CDLL(path)

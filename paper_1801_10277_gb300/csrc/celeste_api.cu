@@ -823,6 +823,10 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
     P.img = d_img; P.geo = d_geo; P.items = d_items; P.tiles = d_tiles; P.tile_list = d_tl;
     P.tile_grid = d_tg;
     P.patch_off = d_po; P.model = d_md;
+    P.n_img_rec = (int32_t)im.size();
+    P.n_zcand = (int32_t)zcands.size();
+    P.n_tile_list = (int64_t)tile_list.size();
+    P.n_tile_grid = (int64_t)tile_grid.size();
     void* p;
     if ((st = dalloc(pr, &p, sizeof(double) * TBL_STRIDE * (size_t)n_patch))) return bail(st);
     P.tbl64 = (double*)p;

@@ -49,31 +49,34 @@ __device__ __forceinline__ double sigm(double x) { return 1.0 / (1.0 + exp(-x));
 
 // theta(t): identity for u, angle, r1, c1; exp for scale, r2, c2; box sigmoids for
 // e_dev, e_axis and the star probability; softmax (last logit 0) plus K_LO for k.
-__device__ void free_to_theta(const double* t, double* th) {
-    th[0] = t[0];
-    th[1] = t[1];
-    th[P_EDEV] = BOX_LO + (BOX_HI - BOX_LO) * sigm(t[2]);
-    th[P_AXIS] = BOX_LO + (BOX_HI - BOX_LO) * sigm(t[3]);
-    th[P_ANGLE] = t[4];
-    th[P_SCALE] = exp(t[5]);
-    th[P_R1] = t[6];
-    th[P_R1 + 1] = t[7];
-    th[P_R2] = exp(t[8]);
-    th[P_R2 + 1] = exp(t[9]);
-    for (int j = 0; j < 8; ++j) {
-        th[P_C1 + j] = t[10 + j];
-        th[P_C2 + j] = exp(t[18 + j]);
+// One warp (every lane calls it): lane j < 28 writes parameter j, lanes 8 i + d (< 16)
+// the weight k_id.  Every exponential of the map is one lane's, so the warp runs two
+// FP64 exp sequences instead of thirty on one lane (the FP64 pipe charges a warp
+// instruction the same however few lanes are active); the softmax denominator is summed
+// in component order on every lane of its group.
+__device__ void free_to_theta_warp(const double* t, double* th) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    if (lane < 28) {
+        const int j = lane;
+        double v;
+        if (j == P_EDEV || j == P_AXIS) v = BOX_LO + (BOX_HI - BOX_LO) * sigm(t[j]);
+        else if (j == P_SCALE || j == P_R2 || j == P_R2 + 1 || (j >= P_C2 && j < P_C2 + 8)) v = exp(t[j]);
+        else if (j == P_A) v = A_LO + (A_HI - A_LO) * sigm(t[26]);
+        else if (j == P_A + 1) v = 1.0 - (A_LO + (A_HI - A_LO) * sigm(t[26]));
+        else v = t[j];
+        th[j] = v;
     }
-    th[P_A] = A_LO + (A_HI - A_LO) * sigm(t[26]);
-    th[P_A + 1] = 1.0 - th[P_A];
-    for (int i = 0; i < 2; ++i) {
+    const int i = (lane >> 3) & 1, d = lane & 7;
+    double ex = 0.0;
+    if (lane < 16) {
         double m = 0.0;
         for (int e = 0; e < 7; ++e) m = fmax(m, t[27 + 7 * i + e]);
-        double ex[8], den = 0.0;
-        for (int e = 0; e < 7; ++e) den += (ex[e] = exp(t[27 + 7 * i + e] - m));
-        den += (ex[7] = exp(-m));
-        for (int d = 0; d < 8; ++d) th[P_K + 8 * i + d] = K_LO + ex[d] / den;
+        ex = exp((d < 7 ? t[27 + 7 * i + d] : 0.0) - m);
     }
+    double den = 0.0;
+    for (int e = 0; e < 8; ++e) den += __shfl_sync(full, ex, 8 * i + e);
+    if (lane < 16) th[P_K + 8 * i + d] = K_LO + ex / den;
 }
 
 __device__ void theta_to_free(const double* th, double* t) {
@@ -114,7 +117,7 @@ __global__ void k_other(const WorkItem* __restrict__ bitems, const PatchGeo* __r
                         const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_list,
                         const int32_t* __restrict__ tile_grid, const float* __restrict__ sky_map,
                         const R* __restrict__ spE, const R* __restrict__ spV, R* __restrict__ eo,
-                        R* __restrict__ vo) {
+                        R* __restrict__ vo, CsrBounds cb) {
     const WorkItem it = bitems[blockIdx.x];
     const int t = threadIdx.x;
     if (t >= it.n) return;
@@ -123,14 +126,21 @@ __global__ void k_other(const WorkItem* __restrict__ bitems, const PatchGeo* __r
     const int q = it.q0 + t;
     const int yy = q / g.w, xx = q - yy * g.w;
     const int gx = g.x0 + xx, gy = g.y0 + yy;
+    if (!CEL_IN_BOUNDS(q < g.w * g.h && gx >= 0 && gx < im.W && gy >= 0 && gy < im.H, cb.status)) return;
     const int64_t m = im.px_off + (int64_t)gy * im.W + gx;
     R E = im.has_sky_map ? (R)sky_map[m] : (R)im.sky;
     R V = 0;
-    const int tid = tile_grid[im.tg_off + (int64_t)(gy / TILE) * im.tgw + gx / TILE];
-    if (tid >= 0) {
-        const Tile tl = tiles[tid];
+    const int64_t gi = im.tg_off + (int64_t)(gy / TILE) * im.tgw + gx / TILE;
+    const int tid = CEL_IN_BOUNDS(gi >= 0 && gi < cb.n_tile_grid, cb.status) ? tile_grid[gi] : -1;
+    if (tid >= 0 && CEL_IN_BOUNDS(tid < cb.n_tile, cb.status)) {
+        Tile tl = tiles[tid];
+        if (!CEL_IN_BOUNDS(tl.list_off >= 0 && tl.list_n >= 0 && (int64_t)tl.list_off + tl.list_n <= cb.n_tile_list,
+                           cb.status))
+            tl.list_n = 0;
         for (int e = 0; e < tl.list_n; ++e) {
-            const PatchGeo o = geo[tile_list[tl.list_off + e]];
+            const int pe = tile_list[tl.list_off + e];
+            if (!CEL_IN_BOUNDS(pe >= 0 && pe < cb.n_patch, cb.status)) continue;
+            const PatchGeo o = geo[pe];
             if (o.src == it.src) continue;
             const int ox = gx - o.x0, oy = gy - o.y0;
             if (ox >= 0 && ox < o.w && oy >= 0 && oy < o.h) {
@@ -642,13 +652,10 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     if (done) return;
     if (tid < TRN) tfree_c[(size_t)NT * b + tid] = tt[tid] + p[tid];
     __syncthreads();
-    if (tid == 0) {
-        double tc[TRN], thc[NP];
-        for (int i = 0; i < TRN; ++i) tc[i] = tt[i] + p[i];
-        free_to_theta(tc, thc);
-        for (int i = 0; i < NP; ++i) theta_c[(size_t)NP * b + i] = thc[i];
-        atomicAdd(active, 1);
-    }
+    if (tid < TRN) tt[tid] += p[tid];
+    __syncthreads();
+    if (tid < 32) free_to_theta_warp(tt, theta_c + (size_t)NP * b);
+    if (tid == 0) atomicAdd(active, 1);
 }
 
 // ratio of actual to predicted gain, radius update, acceptance: one warp per source (the
@@ -1045,11 +1052,13 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                 if (prec == CELESTE_FP64)
                     k_other<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
                                                          P.tile_grid, P.sky_map, (const double*)P.spE,
-                                                         (const double*)P.spE2, (double*)d_eo, (double*)d_vo);
+                                                         (const double*)P.spE2, (double*)d_eo, (double*)d_vo,
+                                                         csr_bounds(P));
                 else
                     k_other<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
                                                         P.tile_grid, P.sky_map, (const float*)P.spE,
-                                                        (const float*)P.spE2, (float*)d_eo, (float*)d_vo);
+                                                        (const float*)P.spE2, (float*)d_eo, (float*)d_vo,
+                                                        csr_bounds(P));
             }
             k_gather_theta<<<(nb * NP + 255) / 256, 256, 0, st>>>(nb, d_bsrc, pr->d_theta, d_bth);
             k_to_free<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bth, d_bt);

@@ -10,6 +10,20 @@
 
 namespace cel {
 
+// Device-side bounds checks, compiled in with -DCELESTE_CHECK_BOUNDS: an index outside its
+// buffer (a pixel outside its patch, a tile-list or candidate entry out of range, a table
+// or record offset past its array) records CELESTE_ERR_BOUNDS in the status word and the
+// access is skipped; nothing traps.  Without the flag every check is the constant true.
+#ifdef CELESTE_CHECK_BOUNDS
+__device__ __forceinline__ bool bound_ok(bool c, int32_t* status) {
+    if (!c) atomicExch(status, (int32_t)CELESTE_ERR_BOUNDS);
+    return c;
+}
+#define CEL_IN_BOUNDS(cond, status) ::cel::bound_ok((cond), (status))
+#else
+#define CEL_IN_BOUNDS(cond, status) true
+#endif
+
 constexpr int NP = CELESTE_NPARAM;      // 44 constrained parameters per source
 constexpr int NT = CELESTE_NFREE;       // 41 free parameters (trust-region coordinates)
 constexpr int MAXPSF = CELESTE_MAX_PSF;
@@ -282,7 +296,22 @@ struct DevProblem {
     int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
                              // launches (nullable: the persistent variants fall back to one CTA per item)
     int32_t* status;
+    // sizes the bounds checks compare against (CELESTE_CHECK_BOUNDS)
+    int32_t n_img_rec;           // image records (the images, then per-patch map copies)
+    int32_t n_zcand;             // candidate records of the FP32 items
+    int64_t n_tile_list;         // entries of tile_list
+    int64_t n_tile_grid;         // entries of tile_grid
 };
+
+// What the tile-list (CSR) bounds checks of k_gather and k_other compare against
+struct CsrBounds {
+    int32_t n_patch, n_tile;
+    int64_t n_tile_list, n_tile_grid;
+    int32_t* status;
+};
+inline CsrBounds csr_bounds(const DevProblem& P) {
+    return CsrBounds{P.n_patch, P.n_tile, P.n_tile_list, P.n_tile_grid, P.status};
+}
 
 void set_last_error(const char* msg);
 

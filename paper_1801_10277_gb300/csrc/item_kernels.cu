@@ -353,8 +353,15 @@ __device__ __forceinline__ int load_acquire(const int32_t* p) {
     return v;
 }
 
+// another wait of the launch gave up, or a bounds check failed: waits end at once
 __device__ __forceinline__ bool timed_out(const int32_t* status) {
-    return *reinterpret_cast<const volatile int32_t*>(status) == (int32_t)CELESTE_ERR_TIMEOUT;
+    const int32_t v = *reinterpret_cast<const volatile int32_t*>(status);
+    return v == (int32_t)CELESTE_ERR_TIMEOUT || v == (int32_t)CELESTE_ERR_BOUNDS;
+}
+
+// a wait that gave up records CELESTE_ERR_TIMEOUT unless an error is recorded already
+__device__ __forceinline__ void record_timeout(int32_t* status) {
+    atomicCAS(status, 0, (int32_t)CELESTE_ERR_TIMEOUT);
 }
 
 __device__ __forceinline__ void wait_ready(const int32_t* flag, int32_t* status) {
@@ -365,7 +372,7 @@ __device__ __forceinline__ void wait_ready(const int32_t* flag, int32_t* status)
         if (load_acquire(flag)) return;
         if (timed_out(status) || clock64() - t0 > MBAR_MAX_CYCLES) break;
     }
-    atomicExch(status, (int32_t)CELESTE_ERR_TIMEOUT);
+    record_timeout(status);
 }
 
 // an mbarrier wait that also gives up once another wait of the launch has
@@ -377,7 +384,7 @@ __device__ __forceinline__ bool mbar_wait_launch(uint64_t* bar, unsigned parity,
         if ((i & 63) == 63 && timed_out(status)) break;
         if (clock64() - t0 > MBAR_MAX_CYCLES) break;
     }
-    atomicExch(status, (int32_t)CELESTE_ERR_TIMEOUT);
+    record_timeout(status);
     return false;
 }
 
@@ -655,6 +662,8 @@ struct ItemArgs {
     double* part;              // [item][ZPCOLS]
     int ne, nd;                // exp / dev profile components
     int n_patch, n_src;
+    int64_t n_sp;              // pixel records (bounds checks)
+    int n_zcand, n_sitem, n_img_rec;
     double* kl;
     double* kl_grad;
     int32_t* status;
@@ -907,6 +916,25 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
     }
     const ZItem it = tk->item;
     const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZMAXC ? nc : ZMAXC;
+#ifdef CELESTE_CHECK_BOUNDS
+    {
+        // the record's offsets into the pixel records, candidates, tables and item records;
+        // a bad record ends this CTA's work (the status tells the caller)
+        const int nm = it.n_nm >> 16, npsf = it.nc_npsf >> 24;
+        bool ok = it.patch >= 0 && it.patch < a.n_patch && n >= 1 && n <= ZIMAX && nm <= n && it.pix >= 0 &&
+                  it.pix + n <= a.n_sp && it.c0 >= 0 && (int64_t)it.c0 + nc <= a.n_zcand && it.out >= 0 &&
+                  it.out < a.n_sitem && it.src >= 0 && it.src < a.n_src && npsf >= 1 && npsf <= MAXPSF;
+        for (int e = 0; ok && e < nc; ++e) {
+            const int pe = e < ZMAXC ? tk->cand[e] : a.cands[it.c0 + e].patch;
+            ok = pe >= 0 && pe < a.n_patch;
+        }
+        if (!CEL_IN_BOUNDS(ok, a.status)) {
+            tk->kind = ZT_END;
+            mbar_arrive_plain(full);
+            return;
+        }
+    }
+#endif
     if (!all_built) {
         if (load_acquire(a.ready + a.n_patch + 1) >= a.n_patch) {
             all_built = true;
@@ -948,6 +976,10 @@ __global__ void __launch_bounds__(128) k_tables(ItemArgs a) {
     const int u = (int)blockIdx.x * 4 + w;
     if (u < a.n_patch) {
         const ZBuild g = a.torder[u];
+        if (!CEL_IN_BOUNDS(g.patch >= 0 && g.patch < a.n_patch && g.img >= 0 && g.img < a.n_img_rec && g.src >= 0 &&
+                               g.src < a.n_src,
+                           a.status))
+            return;
         build_patch_table(a.theta, g, a.img_tab, *a.md, a.ztbl, a.zchain, scr[w]);
         __syncwarp();
         if (lane == 0) publish_ready(a.ready + g.patch, a.ready + a.n_patch + 1);
@@ -972,7 +1004,8 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, s = (int)blockIdx.x;
     const bool grad = a.mode >= MODE_GRAD;
     const int ncol = grad ? ZPCOLS : 2;
-    const int i0 = __ldcg(a.sitem_off + s), i1 = __ldcg(a.sitem_off + s + 1);
+    int i0 = __ldcg(a.sitem_off + s), i1 = __ldcg(a.sitem_off + s + 1);
+    if (!CEL_IN_BOUNDS(i0 >= 0 && i0 <= i1 && i1 <= a.n_sitem, a.status)) i0 = i1 = 0;
     const int cA = lane, cB = lane + 32;
     double sA = 0.0, sB = 0.0;
     for (int k0 = i0 + w; k0 < i1; k0 += FIN_W * FIN_WIN) {
@@ -1247,6 +1280,10 @@ cudaError_t launch_items_stage(const DevProblem& P, int stage, int mode, cudaStr
     a.nd = P.model_nd;
     a.n_patch = P.n_patch;
     a.n_src = P.n_src;
+    a.n_sp = P.n_sp;
+    a.n_zcand = P.n_zcand;
+    a.n_sitem = P.n_sitem;
+    a.n_img_rec = P.n_img_rec;
     a.kl = P.kl;
     a.kl_grad = P.kl_grad;
     a.status = P.status;

@@ -186,6 +186,8 @@ extern "C" celeste_status celeste_patch_elbo_grad_noalloc(
     P.n_img = 1; P.n_src = 1; P.n_patch = 1;
     P.n_item = (w * h + CHUNK - 1) / CHUNK;
     P.n_tile = ((w + TILE - 1) / TILE) * ((h + TILE - 1) / TILE);
+    P.n_tile_list = P.n_tile;   // tile i lists the patch at entry i
+    P.n_img_rec = 1;
     P.npsf_max = im->n_psf;
     P.nprof = model->n_exp + model->n_dev;
     P.n_px = (int64_t)w * h;

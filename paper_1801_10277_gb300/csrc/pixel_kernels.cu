@@ -427,18 +427,22 @@ __global__ void __launch_bounds__(TILE* TILE) k_gather(const Tile* __restrict__ 
                                                        const R* __restrict__ spV,
                                                        R* __restrict__ emap, R* __restrict__ vmap,
                                                        double* __restrict__ tile_ll,
-                                                       int min_cover) {
+                                                       int min_cover, CsrBounds cb) {
     const Tile tl = tiles[blockIdx.x];
     const ImgMeta& im = img[tl.img];
     const int gx = tl.x0 + (int)(threadIdx.x % TILE), gy = tl.y0 + (int)(threadIdx.x / TILE);
+    const bool list_ok = CEL_IN_BOUNDS(
+        tl.list_off >= 0 && tl.list_n >= 0 && (int64_t)tl.list_off + tl.list_n <= cb.n_tile_list, cb.status);
     R ll[1] = {0};
-    if (gx < im.W && gy < im.H) {
+    if (gx < im.W && gy < im.H && list_ok) {
         const int64_t m = im.px_off + (int64_t)gy * im.W + gx;
         R E = im.has_sky_map ? (R)sky_map[m] : (R)im.sky;
         R V = 0;
         int cov = 0;
         for (int e = 0; e < tl.list_n; ++e) {
-            const PatchGeo g = geo[tile_list[tl.list_off + e]];
+            const int pe = tile_list[tl.list_off + e];
+            if (!CEL_IN_BOUNDS(pe >= 0 && pe < cb.n_patch, cb.status)) continue;
+            const PatchGeo g = geo[pe];
             const int xx = gx - g.x0, yy = gy - g.y0;
             if (xx >= 0 && xx < g.w && yy >= 0 && yy < g.h) {
                 const int64_t q = g.sp_off + (int64_t)yy * g.w + xx;
@@ -1294,11 +1298,11 @@ cudaError_t launch_gather(const DevProblem& P, int precision, cudaStream_t st) {
     if (precision == CELESTE_FP64)
         k_gather<double><<<P.n_tile, TILE * TILE, 0, st>>>(
             P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const double*)P.spE,
-            (const double*)P.spE2, (double*)P.emap, (double*)P.vmap, P.tile_ll, P.single ? 2 : 1);
+            (const double*)P.spE2, (double*)P.emap, (double*)P.vmap, P.tile_ll, P.single ? 2 : 1, csr_bounds(P));
     else
         k_gather<float><<<P.n_tile, TILE * TILE, 0, st>>>(
             P.tiles, P.tile_list, P.geo, P.img, P.pixels, P.sky_map, (const float*)P.spE,
-            (const float*)P.spE2, (float*)P.emap, (float*)P.vmap, P.tile_ll, P.single ? 2 : 1);
+            (const float*)P.spE2, (float*)P.emap, (float*)P.vmap, P.tile_ll, P.single ? 2 : 1, csr_bounds(P));
     return cudaGetLastError();
 }
 

@@ -25,6 +25,29 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_checked_library_builds_and_exports_the_same_symbols():
+    """The build with CELESTE_CHECK_BOUNDS (device-side bounds checks that record
+    CELESTE_ERR_BOUNDS instead of trapping) compiles and exports every declared entry
+    point; the binding loads it when the environment sets CELESTE_CHECK_BOUNDS=1."""
+    from paper_1801_10277_gb300 import build, celeste
+    path = build.build(checked=True)
+    assert path == build.LIB_CHECKED and path != build.LIB
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    old = os.environ.get("CELESTE_CHECK_BOUNDS")
+    try:
+        os.environ["CELESTE_CHECK_BOUNDS"] = "1"
+        assert celeste.lib_path() == build.LIB_CHECKED
+        os.environ["CELESTE_CHECK_BOUNDS"] = "0"
+        assert celeste.lib_path() == build.LIB
+    finally:
+        if old is None:
+            os.environ.pop("CELESTE_CHECK_BOUNDS", None)
+        else:
+            os.environ["CELESTE_CHECK_BOUNDS"] = old
+
+
 def test_binding_declares_the_same_entry_points():
     from paper_1801_10277_gb300 import celeste
     assert set(celeste.EXPORTS) <= set(declared_functions())
@@ -105,7 +128,7 @@ def test_header_enums_match_binding(tmp_path):
     from paper_1801_10277_gb300 import celeste as c
     status = {"OK": c.OK, "ERR_ARG": c.ERR_ARG, "ERR_NOT_PD": c.ERR_NOT_PD,
               "ERR_NONFINITE": c.ERR_NONFINITE, "ERR_CUDA": c.ERR_CUDA,
-              "ERR_TIMEOUT": c.ERR_TIMEOUT, "ERR_NOMEM": c.ERR_NOMEM,
+              "ERR_TIMEOUT": c.ERR_TIMEOUT, "ERR_NOMEM": c.ERR_NOMEM, "ERR_BOUNDS": c.ERR_BOUNDS,
               "SCHED_COLOUR": c.SCHED_COLOUR, "SCHED_CYCLADES": c.SCHED_CYCLADES,
               "NPARAM": c.NPARAM, "CAT_NFIELD": c.CAT_NFIELD,
               "SCORE_NFIELD": len(c.SCORE_FIELDS)}
