@@ -557,6 +557,17 @@ def main():
                "elbo_start": el_start, "elbo_end": el_fit,
                "converged": int((fst == 0).sum()),
                "options": "FP32 pixels, FP64 refinement, <= 3 sweeps, <= 50 iterations per source"}
+        # the FP32 sweeps alone (no FP64 polish): the fit targets hold for them too
+        # (tests/test_gpu_fit.py), so this is the FP32 path's own fit time
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it32, fst32, el32 = P.fit(prob.theta, precision=cel.FP32, refine_fp64=0, max_sweeps=3)
+        torch.cuda.synchronize()
+        s32 = time.perf_counter() - t0
+        fit["fp32_only"] = {"seconds": s32, "newton_iterations": int(it32.sum()),
+                            "newton_iterations_per_s": float(it32.sum()) / s32,
+                            "converged": int((fst32 == 0).sum()), "elbo_end": el32,
+                            "options": "FP32 pixels, FP64 accumulation, no FP64 polish, <= 3 sweeps"}
         # fit quality against the generator's truth (Table II's error summary; the images
         # are isotropic blobs, so galaxy shape truth is not in the pixels)
         cat_true = P.catalog(prob.truth)

@@ -263,15 +263,19 @@ celeste_status celeste_make_tasks(const double* pos, const double* work, int32_t
                                   const double* shift, int32_t* task_of, int32_t* n_tasks);
 
 /*
- * One stage of region tasks: every task (the sources s with task_of[s] == k, k >= 0;
- * -1 = the source stays fixed) is fitted as celeste_fit_sources would with `which` =
- * its sources, starting from theta_inout with every other source held at its starting
- * value, as tasks running side by side on separate nodes see each other; the tasks'
- * results are then merged into theta_inout.  iters_out / status_out ([n_src],
- * nullable) as celeste_fit_sources (0 for fixed sources); elbo_out (nullable) = the
- * total ELBO of the merged parameters (FP64 when FP32 sweeps are polished, else in the
- * fit's precision).  Errors as celeste_fit_sources; task ids below -1 are
- * CELESTE_ERR_ARG.
+ * One stage of region tasks (Section IV-A): every task (the sources s with
+ * task_of[s] == k, k >= 0; -1 = the source stays fixed) is fitted as
+ * celeste_fit_sources would with `which` = its sources, starting from theta_inout with
+ * every other source held at its starting value, as tasks running side by side on
+ * separate nodes see each other; the tasks' results are merged into theta_inout.  The
+ * tasks run side by side on the device: one sweep schedule over all their sources, a
+ * source of another task contributing its stage-start E_s / Var_s, so each task's
+ * iterates equal those of its own fit.  Sweeps end for all tasks together: after
+ * max_sweeps, or once the merged parameters' total ELBO changes by less than
+ * sweep_tol (relative) in a sweep.  iters_out / status_out ([n_src], nullable) as
+ * celeste_fit_sources (0 for fixed sources); elbo_out (nullable) = the total ELBO of
+ * the merged parameters (FP64 when FP32 sweeps are polished, else in the fit's
+ * precision).  Errors as celeste_fit_sources; task ids below -1 are CELESTE_ERR_ARG.
  */
 celeste_status celeste_fit_tasks(celeste_problem* prob, double* theta_inout, const int32_t* task_of,
                                  const celeste_fit_options* opts, int32_t* iters_out,

@@ -923,6 +923,14 @@ celeste_status celeste_hess_device(celeste_problem* pr, const double* d_theta, i
 celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, const int32_t* which,
                                    int32_t n_which, const celeste_fit_options* opts,
                                    int32_t* iters_out, int32_t* status_out, double* elbo_out) {
+    return fit_sources_checked(pr, theta_inout, which, n_which, opts, iters_out, status_out, elbo_out, nullptr);
+}
+
+}  // extern "C"
+
+celeste_status cel::fit_sources_checked(celeste_problem* pr, double* theta_inout, const int32_t* which,
+                                        int32_t n_which, const celeste_fit_options* opts, int32_t* iters_out,
+                                        int32_t* status_out, double* elbo_out, const int32_t* task_of) {
     if (!pr || !theta_inout) return fail(CELESTE_ERR_ARG, "null problem or theta");
     celeste_fit_options o;
     if (opts) o = *opts;
@@ -949,8 +957,10 @@ celeste_status celeste_fit_sources(celeste_problem* pr, double* theta_inout, con
     s = ensure_out(pr);
     if (s) return s;
     return fit_sources_impl(pr, theta_inout, which, n_which, &o, iters_out, status_out, elbo_out,
-                            celeste_elbo);
+                            celeste_elbo, task_of);
 }
+
+extern "C" {
 
 celeste_status celeste_profile_enable(celeste_problem* pr, int32_t on) {
     if (!pr) return fail(CELESTE_ERR_ARG, "null problem");

@@ -111,13 +111,16 @@ __device__ void theta_to_free(const double* th, double* t) {
 
 // E_other, Var_other at every batch pixel: sky plus every other source covering it
 // (tile lists, ascending source order), from the current global E_s / Var_s buffers.
+// Region-task stages (task non-null): a covering source of another task than the batch
+// source's contributes its stage-start terms (spEs, spVs), as if it had not moved.
 template <class R>
 __global__ void k_other(const WorkItem* __restrict__ bitems, const PatchGeo* __restrict__ bgeo,
                         const PatchGeo* __restrict__ geo, const ImgMeta* __restrict__ img,
                         const Tile* __restrict__ tiles, const int32_t* __restrict__ tile_list,
                         const int32_t* __restrict__ tile_grid, const float* __restrict__ sky_map,
                         const R* __restrict__ spE, const R* __restrict__ spV, R* __restrict__ eo,
-                        R* __restrict__ vo, CsrBounds cb) {
+                        R* __restrict__ vo, CsrBounds cb, const int32_t* __restrict__ task,
+                        const R* __restrict__ spEs, const R* __restrict__ spVs) {
     const WorkItem it = bitems[blockIdx.x];
     const int t = threadIdx.x;
     if (t >= it.n) return;
@@ -145,8 +148,9 @@ __global__ void k_other(const WorkItem* __restrict__ bitems, const PatchGeo* __r
             const int ox = gx - o.x0, oy = gy - o.y0;
             if (ox >= 0 && ox < o.w && oy >= 0 && oy < o.h) {
                 const int64_t qq = o.sp_off + (int64_t)oy * o.w + ox;
-                E += spE[qq];
-                V += spV[qq];
+                const bool start = task && task[o.src] != task[it.src];
+                E += start ? spEs[qq] : spE[qq];
+                V += start ? spVs[qq] : spV[qq];
             }
         }
     }
@@ -223,6 +227,8 @@ __global__ void k_to_free(int nb, const double* __restrict__ th, double* __restr
 
 constexpr int TR_THREADS = 128;
 constexpr int TRN = NT;   // 41
+// k_tr_step's dynamic shared memory: the source's 44 x 44 Hessian and H T (44 x 41)
+constexpr size_t TR_DYN_BYTES = sizeof(double) * (NP * NP + NP * TRN);
 
 struct TrState {
     double delta;   // trust radius (free coordinates)
@@ -237,53 +243,65 @@ struct TrState {
     double lam;     // multiplier of the last boundary step (warm start of the next), 0 inside
 };
 
-// Cholesky of (B + lam I) into L (lower, row-major n x n); returns success to all threads.
-// Right-looking, two barriers per column: thread 0 takes the pivot's square root and its
-// reciprocal (one FP64 rsqrt per column; the FP64 pipe runs a warp instruction at the
-// same cost however few lanes are active, so per-element divisions are avoided), then
-// every thread updates its share of the trailing lower triangle from the still unscaled
-// column, L_ij -= L_ik L_jk / d_k, and scales the column left by the previous step.
-// The packed triangle index gives every warp instruction useful lanes.
-__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag, double* rcp) {
+// Packed lower-triangle order: entry idx = a (a + 1) / 2 + b, 0 <= b <= a, stored as
+// a << 8 | b.  A triangle of side m is the first m (m + 1) / 2 entries of a larger one.
+constexpr int PK_N = (TRN - 1) * TRN / 2;   // side 40: every trailing triangle of n = 41
+
+__device__ void packed_table(uint16_t* pk) {
+    for (int idx = threadIdx.x; idx < PK_N; idx += blockDim.x) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+        pk[idx] = (uint16_t)(a << 8 | (idx - a * (a + 1) / 2));
+    }
+}
+
+// Cholesky of (B + lam I) into L (lower, row-major n x n, n <= TRN); returns success to
+// all threads.  Right-looking, one barrier per column: step k updates the trailing
+// triangle from the still unscaled column k, L_ij -= L_ik L_jk / d_k (entries dealt out
+// in packed order, pk), and scales column k - 1, whose entries that step no longer
+// reads.  The thread that updates (k + 1, k + 1), the next pivot, takes its FP64 rsqrt
+// at once, so the pivot is ready at the barrier (the FP64 pipe charges a warp
+// instruction however few lanes are active, so one thread takes each pivot's square
+// root and reciprocal, and no element is divided).
+__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag, double* rcp,
+                           const uint16_t* pk) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    auto pivot = [&](int k, double d) {
+        if (!(d > 0.0) || !isfinite(d)) {
+            *flag = 0;
+        } else {
+            const double r = rsqrt(d);
+            rcp[k] = r;           // 1 / sqrt(d)
+            rcp[n + k] = r * r;   // 1 / d
+        }
+    };
     for (int i = tid; i < n * n; i += nt) {
         const int r = i / n, c = i - r * n;
         L[i] = (c <= r) ? B[i] + (r == c ? lam : 0.0) : 0.0;
     }
-    if (tid == 0) *flag = 1;
+    if (tid == 0) {
+        *flag = 1;
+        pivot(0, L[0]);   // this thread wrote L[0]
+    }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            const double d = L[k * n + k];
-            if (!(d > 0.0) || !isfinite(d)) {
-                *flag = 0;
-            } else {
-                const double r = rsqrt(d);
-                L[k * n + k] = d * r;   // sqrt(d)
-                rcp[k] = r;             // 1 / sqrt(d)
-                rcp[n + k] = r * r;     // 1 / d
-            }
-        }
-        // the previous column's scaling (its entries are not read in this step)
-        if (k > 0)
-            for (int i = k + tid; i < n; i += nt) L[i * n + k - 1] *= rcp[k - 1];
-        __syncthreads();
         if (!*flag) return false;
         const double inv_d = rcp[n + k];
         const int m = n - k - 1;
         const int cnt = m * (m + 1) / 2;
         for (int idx = tid; idx < cnt; idx += nt) {
-            // (a, b) with 0 <= b <= a < m from the packed index a (a + 1) / 2 + b
-            int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-            while (a * (a + 1) / 2 > idx) --a;
-            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-            const int b = idx - a * (a + 1) / 2;
-            const int i = k + 1 + a, j = k + 1 + b;
-            L[i * n + j] -= L[i * n + k] * L[j * n + k] * inv_d;
+            const int ab = pk[idx];
+            const int i = k + 1 + (ab >> 8), j = k + 1 + (ab & 255);
+            const double v = L[i * n + j] - L[i * n + k] * L[j * n + k] * inv_d;
+            L[i * n + j] = v;
+            if (idx == 0) pivot(k + 1, v);
         }
+        // column k - 1 (its diagonal becomes sqrt(d) = d / sqrt(d))
+        if (k > 0)
+            for (int i = k - 1 + tid; i < n; i += nt) L[i * n + k - 1] *= rcp[k - 1];
+        if (k == n - 1 && tid == nt - 1) L[k * n + k] *= rcp[k];
         __syncthreads();
     }
-    // column j was scaled in step j + 1 <= n - 1; the last column is its pivot alone
     return true;
 }
 
@@ -342,6 +360,10 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     __shared__ double tv[TRN][8];
     __shared__ int flag, done;
     __shared__ double lam_s, pn_s;
+    __shared__ uint16_t pk[PK_N];
+    extern __shared__ double tr_dyn[];
+    double* Hs = tr_dyn;             // [NP][NP] the source's Hessian
+    double* X = tr_dyn + NP * NP;    // [NP][TRN] H T
     const int tid = threadIdx.x;
     if (tid == 0) S = st[b];
     __syncthreads();
@@ -354,6 +376,11 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         g44[i] = g_in[(size_t)NP * b + i];
     }
     for (int i = tid; i < TRN; i += blockDim.x) tt[i] = tfree[(size_t)NT * b + i];
+    {
+        const double* H44 = h_in + (size_t)NP * NP * b;
+        for (int i = tid; i < NP * NP; i += blockDim.x) Hs[i] = H44[i];
+    }
+    packed_table(pk);
     __syncthreads();
     // columns of T = d theta / d t
     if (tid < TRN) {
@@ -390,13 +417,19 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         gt[a] = s;
     }
     __syncthreads();
-    // Ht = T' H T + sum_j g_j d2 theta_j / dt dt
-    const double* H44 = h_in + (size_t)NP * NP * b;
+    // Ht = T' H T + sum_j g_j d2 theta_j / dt dt, T' H T as two sparse products from
+    // shared memory: X = H T, then T' X
+    for (int idx = tid; idx < NP * TRN; idx += blockDim.x) {
+        const int r = idx / TRN, c = idx - r * TRN;
+        double x = 0.0;
+        for (int v = 0; v < tn[c]; ++v) x += Hs[r * NP + tj[c][v]] * tv[c][v];
+        X[idx] = x;
+    }
+    __syncthreads();
     for (int idx = tid; idx < TRN * TRN; idx += blockDim.x) {
         const int a = idx / TRN, c = idx % TRN;
         double s = 0.0;
-        for (int u = 0; u < tn[a]; ++u)
-            for (int v = 0; v < tn[c]; ++v) s += tv[a][u] * H44[tj[a][u] * NP + tj[c][v]] * tv[c][v];
+        for (int u = 0; u < tn[a]; ++u) s += tv[a][u] * X[tj[a][u] * TRN + c];
         if (a == c) {
             if (a == 2 || a == 3) {
                 const double sg = sigm(tt[a]);
@@ -496,7 +529,7 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
     if (tid == 0) pn_s = 0.0;
     __syncthreads();
     __shared__ double rcp[2 * TRN];
-    bool ok = block_chol(Ht, 0.0, L, TRN, &flag, rcp);
+    bool ok = block_chol(Ht, 0.0, L, TRN, &flag, rcp, pk);
     bool solved = false;
     if (ok) {
         if (tid < TRN) invd[tid] = rcp[tid];
@@ -523,7 +556,7 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         if (S.lam > lamL && S.lam < lamU) lam = S.lam;
         if (ok) lamL = fmax(lamL, 0.0);
         for (int it = 0; it < 200; ++it) {
-            const bool pd = block_chol(Ht, lam, L, TRN, &flag, rcp);
+            const bool pd = block_chol(Ht, lam, L, TRN, &flag, rcp, pk);
             if (pd && tid < TRN) invd[tid] = rcp[tid];
             __syncthreads();
             if (tid < 32) {
@@ -852,7 +885,8 @@ using namespace cel;
 celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const int32_t* which,
                                      int32_t n_which, const celeste_fit_options* opts,
                                      int32_t* iters_out, int32_t* status_out, double* elbo_out,
-                                     celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t, double*, double*)) {
+                                     celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t, double*, double*),
+                                     const int32_t* task_of) {
     const DevProblem& P = pr->P;
     const int n = P.n_src;
     int prec = opts->precision;
@@ -1015,6 +1049,20 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
         ~HostFree() { cudaFreeHost(p); }
     } hf{h_active};
 
+    // region-task stage: every source's task id, the stage-start parameters and, per
+    // precision phase, every source's E_s / Var_s at them
+    int32_t* d_task = nullptr;
+    double* d_th0 = nullptr;
+    unsigned char *d_se0 = nullptr, *d_sv0 = nullptr;
+    if (task_of) {
+        FIT_CUDA(mem.alloc(&d_task, n));
+        FIT_CUDA(mem.alloc(&d_th0, (size_t)n * NP));
+        FIT_CUDA(mem.alloc(&d_se0, (size_t)P.n_sp * rs));
+        FIT_CUDA(mem.alloc(&d_sv0, (size_t)P.n_sp * rs));
+        FIT_CUDA(cudaMemcpyAsync(d_task, task_of, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        FIT_CUDA(cudaMemcpyAsync(d_th0, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice, st));
+    }
+    FIT_CUDA(cudaFuncSetAttribute(k_tr_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_DYN_BYTES));
     FIT_CUDA(cudaMemcpyAsync(pr->d_theta, theta, sizeof(double) * NP * n, cudaMemcpyHostToDevice, st));
     std::vector<int32_t> iters(n, 0), status(n, ST_CONVERGED);
     double prev = 0.0;
@@ -1032,6 +1080,14 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
     if (phase == 1) {
         celeste_status s2 = elbo_fn(pr, theta, prec, &prev, nullptr);
         if (s2) return s2;
+    }
+    if (task_of) {
+        // the stage-start E_s / Var_s in this phase's precision
+        const size_t bytes = (size_t)P.n_sp * (prec == CELESTE_FP64 ? sizeof(double) : sizeof(float));
+        FIT_CUDA(launch_prep(P, d_th0, prec, st));
+        FIT_CUDA(launch_contrib(P, prec, st));
+        FIT_CUDA(cudaMemcpyAsync(d_se0, P.spE, bytes, cudaMemcpyDeviceToDevice, st));
+        FIT_CUDA(cudaMemcpyAsync(d_sv0, P.spE2, bytes, cudaMemcpyDeviceToDevice, st));
     }
     int sw = 0;
     for (; sw < opts->max_sweeps; ++sw, ++g_sweep) {
@@ -1053,12 +1109,14 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
                     k_other<double><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
                                                          P.tile_grid, P.sky_map, (const double*)P.spE,
                                                          (const double*)P.spE2, (double*)d_eo, (double*)d_vo,
-                                                         csr_bounds(P));
+                                                         csr_bounds(P), d_task, (const double*)d_se0,
+                                                         (const double*)d_sv0);
                 else
                     k_other<float><<<nI, CHUNK, 0, st>>>(d_bitems, d_bgeo, P.geo, P.img, P.tiles, P.tile_list,
                                                         P.tile_grid, P.sky_map, (const float*)P.spE,
                                                         (const float*)P.spE2, (float*)d_eo, (float*)d_vo,
-                                                        csr_bounds(P));
+                                                        csr_bounds(P), d_task, (const float*)d_se0,
+                                                        (const float*)d_sv0);
             }
             k_gather_theta<<<(nb * NP + 255) / 256, 256, 0, st>>>(nb, d_bsrc, pr->d_theta, d_bth);
             k_to_free<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_bth, d_bt);
@@ -1114,7 +1172,7 @@ celeste_status cel::fit_sources_impl(celeste_problem* pr, double* theta, const i
             }
             chk(launch_hess_pixels(Pb, prec, st));
             chk(launch_finalize_hess(Pb, d_bth, d_f, d_g, d_h, st));
-            k_tr_step<<<nb, TR_THREADS, 0, st>>>(nb, d_bth, d_bt, d_f, d_g, d_h, d_kl, d_bthc, d_btc,
+            k_tr_step<<<nb, TR_THREADS, TR_DYN_BYTES, st>>>(nb, d_bth, d_bt, d_f, d_g, d_h, d_kl, d_bthc, d_btc,
                                                  d_st, *opts, d_active);
             // only sources with a candidate evaluate it
             k_mark_active<<<(nb + 127) / 128, 128, 0, st>>>(nb, d_st, d_srcact);

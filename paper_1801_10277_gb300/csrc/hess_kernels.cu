@@ -413,7 +413,16 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
     __shared__ int act[NP], nact;                 // parameters this patch touches
     __shared__ double klg[NP];
     __shared__ double klv;
+    // packed upper-triangle order of the active block: q = a (a + 1) / 2 + b, b <= a,
+    // stored as a << 8 | b
+    constexpr int NPK = NP * (NP + 1) / 2;
+    __shared__ uint16_t pkq[NPK];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int q = t; q < NPK; q += blockDim.x) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= q) ++a;
+        pkq[q] = (uint16_t)(a << 8 | (q - a * (a + 1) / 2));
+    }
     if (t < NP) {
         th[t] = theta[(size_t)NP * s + t];
         if (status) theta_domain_check(t, th[t], status);
@@ -442,8 +451,17 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         const ImgMeta& im = img[g.img];
         const double* A = im.A;
         if (t < 1 + NY + NYH) {
+            // the patch's items in order, loaded eight at a time before any is added
             double v = 0.0;
-            for (int it = g.item0; it < g.item0 + g.nitem; ++it) v += part[(size_t)it * NPART + t];
+            const int i1 = g.item0 + g.nitem;
+            for (int i0 = g.item0; i0 < i1; i0 += 8) {
+                double x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = i0 + u < i1 ? part[(size_t)(i0 + u) * NPART + t] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < i1) v += x[u];
+            }
             if (t == 0) lacc += v;
             else if (t < 1 + NY) Gy[t - 1] = v;
             else {
@@ -500,22 +518,21 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
         __syncthreads();
         if (t < NP)
             for (int n = 0; n < nzn[t]; ++n) gacc += nzv[t][n] * Gy[nzy[t][n]];
-        if (t == 0) {
-            // the parameters with a nonzero Jacobian column: the only rows and columns this
-            // patch adds to (every brightness and shape term lies among them)
-            int c = 0;
-            for (int j = 0; j < NP; ++j)
-                if (nzn[j] > 0) act[c++] = j;
-            nact = c;
+        if (warp == 0) {
+            // the parameters with a nonzero Jacobian column, ascending: the only rows and
+            // columns this patch adds to (every brightness and shape term lies among them)
+            const unsigned b0 = __ballot_sync(0xffffffffu, nzn[lane] > 0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, lane + 32 < NP && nzn[lane + 32] > 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (b0 >> lane & 1u) act[__popc(b0 & below)] = lane;
+            if (b1 >> lane & 1u) act[__popc(b0) + __popc(b1 & below)] = lane + 32;
+            if (lane == 0) nact = __popc(b0) + __popc(b1);
         }
         __syncthreads();
         // the upper triangle of the active block, each entry (and its mirror) by one thread
         const int na = nact, npair = na * (na + 1) / 2;
         for (int q = t; q < npair; q += blockDim.x) {
-            int a = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-            while (a * (a + 1) / 2 > q) --a;
-            while ((a + 1) * (a + 2) / 2 <= q) ++a;
-            const int b = q - a * (a + 1) / 2;   // b <= a
+            const int a = pkq[q] >> 8, b = pkq[q] & 255;   // b <= a
             const int i = act[a], j = act[b];
             double h = 0.0;
             for (int u = 0; u < nzn[i]; ++u)

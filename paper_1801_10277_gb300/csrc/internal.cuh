@@ -324,11 +324,18 @@ bool chol_inverse4(const double* S, double* inv, double* logdet);
 // failure the status and *why (a static message).  Shared by every entry point.
 celeste_status build_model_dev(const celeste_model* model, ModelDev& md, const char** why);
 
+// task_of (host, one entry per source, nullable): a region-task stage, every task fitted
+// against the stage-start parameters of the sources outside it
 celeste_status fit_sources_impl(celeste_problem* pr, double* theta_inout, const int32_t* which,
                                 int32_t n_which, const celeste_fit_options* opts,
                                 int32_t* iters_out, int32_t* status_out, double* elbo_out,
                                 celeste_status (*elbo_fn)(celeste_problem*, const double*, int32_t,
-                                                          double*, double*));
+                                                          double*, double*),
+                                const int32_t* task_of = nullptr);
+// celeste_fit_sources with its argument checks, and the region-task stage mode above
+celeste_status fit_sources_checked(celeste_problem* pr, double* theta_inout, const int32_t* which,
+                                   int32_t n_which, const celeste_fit_options* opts, int32_t* iters_out,
+                                   int32_t* status_out, double* elbo_out, const int32_t* task_of);
 
 void prime_persistent_grids();
 cudaError_t prime_items_kernels();

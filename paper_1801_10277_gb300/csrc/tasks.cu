@@ -139,40 +139,36 @@ celeste_status celeste_fit_tasks(celeste_problem* pr, double* theta, const int32
         return CELESTE_ERR_ARG;
     }
     const int n = pr->P.n_src;
-    int n_tasks = 0;
+    std::vector<int32_t> members;
     for (int s = 0; s < n; ++s) {
         if (task_of[s] < -1) {
             set_last_error("celeste_fit_tasks: task ids must be >= -1");
             return CELESTE_ERR_ARG;
         }
-        n_tasks = std::max(n_tasks, task_of[s] + 1);
+        if (task_of[s] >= 0) members.push_back(s);
     }
-    std::vector<std::vector<int32_t>> members(n_tasks);
-    for (int s = 0; s < n; ++s)
-        if (task_of[s] >= 0) members[task_of[s]].push_back(s);
-    celeste_fit_options o;
-    if (opts) o = *opts;
-    else celeste_fit_options_default(&o);
-    const std::vector<double> start(theta, theta + (size_t)NP * n);
-    std::vector<double> work(start.size());
-    std::vector<int32_t> it(n), st(n);
     if (iters_out) memset(iters_out, 0, sizeof(int32_t) * n);
     if (status_out) memset(status_out, 0, sizeof(int32_t) * n);
-    for (int k = 0; k < n_tasks; ++k) {
-        if (members[k].empty()) continue;
-        work = start;   // every task starts from the stage's parameters
-        celeste_status e = celeste_fit_sources(pr, work.data(), members[k].data(), (int32_t)members[k].size(),
-                                               &o, it.data(), st.data(), nullptr);
-        if (e) return e;
-        for (int s : members[k]) {
-            memcpy(theta + (size_t)NP * s, work.data() + (size_t)NP * s, sizeof(double) * NP);
-            if (iters_out) iters_out[s] = it[s];
-            if (status_out) status_out[s] = st[s];
-        }
-    }
-    if (elbo_out) {
+    // Every task side by side in one fit over the union of the tasks' sources: the
+    // colour batches are those of the whole neighbour graph, so a batch mixes tasks
+    // without two of its sources overlapping, and each source sees the sources of other
+    // tasks at their stage-start terms.  A source's iterates are then those of its
+    // task's own fit from the stage start.
+    if (members.empty()) {
+        if (!elbo_out) return CELESTE_OK;
+        celeste_fit_options o;
+        if (opts) o = *opts;
+        else celeste_fit_options_default(&o);
         const int prec = (o.precision == CELESTE_FP32_ACC64 && o.refine_fp64) ? CELESTE_FP64 : o.precision;
         return celeste_elbo(pr, theta, prec, elbo_out, nullptr);
+    }
+    std::vector<int32_t> it(n), st(n);
+    const celeste_status e = cel::fit_sources_checked(pr, theta, members.data(), (int32_t)members.size(), opts,
+                                                      it.data(), st.data(), elbo_out, task_of);
+    if (e) return e;
+    for (int s : members) {
+        if (iters_out) iters_out[s] = it[s];
+        if (status_out) status_out[s] = st[s];
     }
     return CELESTE_OK;
 }

@@ -1,5 +1,6 @@
-"""Region task stages on the GPU (celeste_fit_tasks): the same as fitting each task
-from the stage's starting parameters and merging (bit for bit), and against the
+"""Region task stages on the GPU (celeste_fit_tasks, the tasks side by side in one
+sweep schedule): the same as fitting each task from the stage's starting parameters and
+merging (bit for bit, a fixed number of sweeps), in both precisions, and against the
 oracle's stage of task fits on the same tasks (FP64: positions 1e-3 px and fluxes 1e-4
 relative, the fit targets, and the total ELBO 1e-8)."""
 import numpy as np
@@ -31,12 +32,16 @@ def _crowded_tasks(cel, prob, parts=4, shift=None):
     return t
 
 
-def test_fit_tasks_is_per_task_fits_merged(cel):
+@pytest.mark.parametrize("fp32", [False, True])
+def test_fit_tasks_is_per_task_fits_merged(cel, fp32):
+    """Overlapping tasks of the crowded region (their border sources share pixels), the
+    stage against each task's own fit: FP64, and FP32 sweeps with the FP64 polish (the
+    stage-start terms are taken in each phase's precision)."""
     prob = synth.config(2)
     task_of = _crowded_tasks(cel, prob)
     task_of[::7] = -1   # a few sources stay fixed
     P = cel.Problem(prob)
-    kw = dict(precision=cel.FP64, max_sweeps=2, sweep_tol=0.0)
+    kw = dict(precision=cel.FP32 if fp32 else cel.FP64, max_sweeps=2, sweep_tol=0.0)
     th, it, st, el = P.fit_tasks(prob.theta, task_of, **kw)
     ref = prob.theta.copy()
     for k in range(task_of.max() + 1):
