@@ -243,41 +243,44 @@ struct TrState {
     double lam;     // multiplier of the last boundary step (warm start of the next), 0 inside
 };
 
-// Packed lower-triangle order: entry idx = a (a + 1) / 2 + b, 0 <= b <= a, stored as
-// a << 8 | b.  A triangle of side m is the first m (m + 1) / 2 entries of a larger one.
-constexpr int PK_N = (TRN - 1) * TRN / 2;   // side 40: every trailing triangle of n = 41
+// Packed lower-triangle order of side 40 (every trailing triangle of n = 41), copied
+// into shared memory by each CTA
+constexpr int PK_N = (TRN - 1) * TRN / 2;
+__device__ const PackedTriangle<TRN - 1> g_pk = packed_triangle<TRN - 1>();
 
 __device__ void packed_table(uint16_t* pk) {
-    for (int idx = threadIdx.x; idx < PK_N; idx += blockDim.x) {
-        int a = 0;
-        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-        pk[idx] = (uint16_t)(a << 8 | (idx - a * (a + 1) / 2));
-    }
+    for (int idx = threadIdx.x; idx < PK_N; idx += blockDim.x) pk[idx] = g_pk.v[idx];
 }
 
 // Cholesky of (B + lam I) into L (lower, row-major n x n, n <= TRN); returns success to
-// all threads.  Right-looking, one barrier per column: step k updates the trailing
-// triangle from the still unscaled column k, L_ij -= L_ik L_jk / d_k (entries dealt out
-// in packed order, pk), and scales column k - 1, whose entries that step no longer
-// reads.  The thread that updates (k + 1, k + 1), the next pivot, takes its FP64 rsqrt
-// at once, so the pivot is ready at the barrier (the FP64 pipe charges a warp
-// instruction however few lanes are active, so one thread takes each pivot's square
-// root and reciprocal, and no element is divided).
-__device__ bool block_chol(const double* B, double lam, double* L, int n, int* flag, double* rcp,
-                           const uint16_t* pk) {
+// all threads.  Right-looking, two barriers per column: step k scales column k by the
+// pivot's 1 / sqrt(d_k) (its diagonal becomes sqrt(d_k)), then updates the trailing
+// triangle with one FMA per entry, L_ij -= L_ik L_jk (entries dealt out in packed order,
+// pk).  The thread that updates (k + 1, k + 1), the next pivot, takes its FP64 rsqrt at
+// once, so the pivot is ready at the barrier.  On GB300's narrow FP64 pipe the
+// factorisation is bound by its FP64 instruction count (a warp instruction costs the
+// same however few lanes are active), so each pivot's square root and reciprocal come
+// from one thread and the update is a single FMA.
+// T = double, or float for the multiplier search (the same steps, FP32's reciprocal
+// square root).
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+template <class T>
+__device__ bool block_chol(const T* B, T lam, T* L, int n, int* flag, T* rcp, const uint16_t* pk) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    auto pivot = [&](int k, double d) {
-        if (!(d > 0.0) || !isfinite(d)) {
+    auto pivot = [&](int k, T d) {
+        if (!(d > (T)0) || !isfinite(d)) {
             *flag = 0;
         } else {
-            const double r = rsqrt(d);
+            const T r = rsqrt_t(d);
             rcp[k] = r;           // 1 / sqrt(d)
             rcp[n + k] = r * r;   // 1 / d
         }
     };
     for (int i = tid; i < n * n; i += nt) {
         const int r = i / n, c = i - r * n;
-        L[i] = (c <= r) ? B[i] + (r == c ? lam : 0.0) : 0.0;
+        L[i] = (c <= r) ? B[i] + (r == c ? lam : (T)0) : (T)0;
     }
     if (tid == 0) {
         *flag = 1;
@@ -286,20 +289,18 @@ __device__ bool block_chol(const double* B, double lam, double* L, int n, int* f
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (!*flag) return false;
-        const double inv_d = rcp[n + k];
+        const T r = rcp[k];
+        for (int i = k + tid; i < n; i += nt) L[i * n + k] *= r;
+        __syncthreads();
         const int m = n - k - 1;
         const int cnt = m * (m + 1) / 2;
         for (int idx = tid; idx < cnt; idx += nt) {
             const int ab = pk[idx];
             const int i = k + 1 + (ab >> 8), j = k + 1 + (ab & 255);
-            const double v = L[i * n + j] - L[i * n + k] * L[j * n + k] * inv_d;
+            const T v = fma(-L[i * n + k], L[j * n + k], L[i * n + j]);
             L[i * n + j] = v;
             if (idx == 0) pivot(k + 1, v);
         }
-        // column k - 1 (its diagonal becomes sqrt(d) = d / sqrt(d))
-        if (k > 0)
-            for (int i = k - 1 + tid; i < n; i += nt) L[i * n + k - 1] *= rcp[k - 1];
-        if (k == n - 1 && tid == nt - 1) L[k * n + k] *= rcp[k];
         __syncthreads();
     }
     return true;
@@ -307,14 +308,17 @@ __device__ bool block_chol(const double* B, double lam, double* L, int n, int* f
 
 // Warp-level triangular solves (every lane of the calling warp calls them): lane l holds
 // rows l and l + 32 of the right-hand side; one column of L per step (column-oriented
-// substitution), the solved entry broadcast by shuffle.  invd[k] = 1 / L[k][k].
-__device__ void warp_fwd(const double* L, const double* invd, const double* b, double* y, int n) {
+// substitution), the solved entry broadcast by shuffle.  invd[k] = 1 / L[k][k].  The
+// arrays must not overlap.
+template <class T>
+__device__ void warp_fwd(const T* __restrict__ L, const T* __restrict__ invd, const T* __restrict__ b,
+                         T* __restrict__ y, int n) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    double r0 = lane < n ? b[lane] : 0.0, r1 = lane + 32 < n ? b[lane + 32] : 0.0;
+    T r0 = lane < n ? b[lane] : (T)0, r1 = lane + 32 < n ? b[lane + 32] : (T)0;
     for (int k = 0; k < n; ++k) {
-        const double rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
-        const double yk = rk * invd[k];
+        const T rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
+        const T yk = rk * invd[k];
         if (lane == (k & 31)) y[k] = yk;
         if (lane > k && lane < n) r0 -= L[lane * n + k] * yk;
         if (lane + 32 > k && lane + 32 < n) r1 -= L[(lane + 32) * n + k] * yk;
@@ -322,13 +326,15 @@ __device__ void warp_fwd(const double* L, const double* invd, const double* b, d
     __syncwarp();
 }
 
-__device__ void warp_bwd(const double* L, const double* invd, const double* y, double* x, int n) {
+template <class T>
+__device__ void warp_bwd(const T* __restrict__ L, const T* __restrict__ invd, const T* __restrict__ y,
+                         T* __restrict__ x, int n) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    double r0 = lane < n ? y[lane] : 0.0, r1 = lane + 32 < n ? y[lane + 32] : 0.0;
+    T r0 = lane < n ? y[lane] : (T)0, r1 = lane + 32 < n ? y[lane + 32] : (T)0;
     for (int k = n - 1; k >= 0; --k) {
-        const double rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
-        const double xk = rk * invd[k];
+        const T rk = __shfl_sync(full, k < 32 ? r0 : r1, k & 31);
+        const T xk = rk * invd[k];
         if (lane == (k & 31)) x[k] = xk;
         if (lane < k) r0 -= L[k * n + lane] * xk;
         if (lane + 32 < k) r1 -= L[k * n + lane + 32] * xk;
@@ -340,6 +346,11 @@ __device__ void warp_bwd(const double* L, const double* invd, const double* y, d
 // instruction whatever the active lanes, so a vector of 41 is summed lane-parallel (two
 // entries a lane) and reduced in five steps rather than looped on one lane.
 __device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -555,6 +566,61 @@ k_tr_step(int nb, const double* __restrict__ theta, const double* __restrict__ t
         // close: the Hessian and the radius change little between Newton iterations
         if (S.lam > lamL && S.lam < lamU) lam = S.lam;
         if (ok) lamL = fmax(lamL, 0.0);
+        // The multiplier search in FP32 (a pipe 64 times the FP64 pipe's width): the same
+        // safeguarded Newton iteration on 1 / |p(lam)| - 1 / Delta, to |p| within 1e-4 of
+        // Delta (at most 16 factorisations); its multiplier starts the FP64 loop below,
+        // which then needs one or two.  The FP32 bracket is not kept: FP32 rounding can
+        // misjudge definiteness near the smallest eigenvalue.
+        {
+            float* B32 = reinterpret_cast<float*>(tr_dyn);   // H and H T are dead by now
+            float* L32 = B32 + TRN * TRN;
+            float* c32 = L32 + TRN * TRN;
+            float *y32 = c32 + TRN, *p32 = y32 + TRN, *w32 = p32 + TRN, *r32 = w32 + TRN;   // r32: 2 TRN
+            for (int i = tid; i < TRN * TRN; i += blockDim.x) B32[i] = (float)Ht[i];
+            for (int i = tid; i < TRN; i += blockDim.x) c32[i] = (float)cvec[i];
+            __syncthreads();
+            double l = lam, lo = lamL, hi = lamU;
+            for (int it = 0; it < 16; ++it) {
+                const bool pd = block_chol<float>(B32, (float)l, L32, TRN, &flag, r32, pk);
+                if (tid < 32) {
+                    double nl = l;
+                    int dn = 0;
+                    if (!pd) {
+                        lo = fmax(lo, l);
+                        nl = fmax(sqrt(fmax(lo, 1e-300) * hi), lo + 0.01 * (hi - lo));
+                    } else {
+                        warp_fwd<float>(L32, r32, c32, y32, TRN);
+                        warp_bwd<float>(L32, r32, y32, p32, TRN);
+                        float sp = 0.f;
+                        for (int i = tid; i < TRN; i += 32) sp += p32[i] * p32[i];
+                        const double pn = sqrt((double)warp_sum_f(sp));
+                        if (fabs(pn - Delta) <= 1e-4 * Delta) {
+                            dn = 1;
+                        } else {
+                            if (pn < Delta) hi = l;
+                            else lo = l;
+                            warp_fwd<float>(L32, r32, p32, w32, TRN);
+                            float sw = 0.f;
+                            for (int i = tid; i < TRN; i += 32) sw += w32[i] * w32[i];
+                            const double wn = (double)warp_sum_f(sw);
+                            nl = l + (pn * pn / wn) * (pn - Delta) / Delta;
+                            if (!(nl > lo && nl < hi)) nl = fmax(sqrt(fmax(lo, 1e-300) * hi), lo + 0.01 * (hi - lo));
+                            if (hi - lo <= 1e-6 * fmax(1.0, hi)) dn = 1;
+                        }
+                    }
+                    if (tid == 0) {
+                        done = dn;
+                        lam_s = nl;
+                    }
+                }
+                __syncthreads();
+                l = lam_s;
+                const int stop = done;
+                __syncthreads();   // every thread has read done and lam_s
+                if (stop) break;
+            }
+            if (l > lamL && l < lamU) lam = l;
+        }
         for (int it = 0; it < 200; ++it) {
             const bool pd = block_chol(Ht, lam, L, TRN, &flag, rcp, pk);
             if (pd && tid < TRN) invd[tid] = rcp[tid];

@@ -371,6 +371,8 @@ __device__ void kl_hessian_warp(const ModelDev& md, const double* th, double* H)
 }
 
 constexpr int FH_THREADS = 256;
+// packed order of the 44 x 44 upper triangle (a << 8 | b, b <= a)
+__device__ const PackedTriangle<NP> g_pkq = packed_triangle<NP>();
 
 // d(m + v/2) / d theta_j (second = false) or d(2m + 2v) / d theta_j (second = true) of
 // type ty in band `band`, where log l | ty ~ N(m, v), m = r1 + beta . c1, v = r2 + beta^2 . c2
@@ -418,11 +420,7 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
     constexpr int NPK = NP * (NP + 1) / 2;
     __shared__ uint16_t pkq[NPK];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int q = t; q < NPK; q += blockDim.x) {
-        int a = 0;
-        while ((a + 1) * (a + 2) / 2 <= q) ++a;
-        pkq[q] = (uint16_t)(a << 8 | (q - a * (a + 1) / 2));
-    }
+    for (int q = t; q < NPK; q += blockDim.x) pkq[q] = g_pkq.v[q];
     if (t < NP) {
         th[t] = theta[(size_t)NP * s + t];
         if (status) theta_domain_check(t, th[t], status);

@@ -303,6 +303,22 @@ struct DevProblem {
     int64_t n_tile_grid;         // entries of tile_grid
 };
 
+// Packed lower-triangle order of a side-N triangle, built at compile time: entry
+// idx = a (a + 1) / 2 + b (0 <= b <= a < N) holds a << 8 | b.  A triangle of side m < N
+// is the first m (m + 1) / 2 entries.
+template <int N>
+struct PackedTriangle {
+    uint16_t v[N * (N + 1) / 2];
+};
+template <int N>
+constexpr PackedTriangle<N> packed_triangle() {
+    PackedTriangle<N> t{};
+    int idx = 0;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b <= a; ++b) t.v[idx++] = (uint16_t)(a << 8 | b);
+    return t;
+}
+
 // What the tile-list (CSR) bounds checks of k_gather and k_other compare against
 struct CsrBounds {
     int32_t n_patch, n_tile;

@@ -30,8 +30,8 @@
 // derivatives at the item's pixels; where other patches cover a pixel, E = sky + sum_s
 // E_s and Var = sum_s Var_s are summed over every covering source in ascending source
 // order (every covering item forms the same sum, bit for bit).  Per warp FP32 sums; the
-// last warp to finish adds the warps in FP64, applies the patch's chain rule dy/dtheta
-// and writes the item's record.  k_finish, k_items' programmatic dependent, runs every
+// producer adds the warps in FP64, applies the patch's chain rule dy/dtheta and writes the
+// item's record.  k_finish, k_items' programmatic dependent, runs every
 // source's epilogue once the items are done (one CTA per source: FP64 sums of its item
 // records in a fixed order, minus the KL); the last CTA to finish adds the sources' shares
 // of the total in source order.
@@ -95,8 +95,8 @@ static_assert(sizeof(ZCand) == 32 && sizeof(ZTask) == 64, "record sizes");
 
 constexpr int PG_F = 10;                 // floats of a ProfileGrad
 constexpr int NSUM = 2 + NY;             // per-thread sums: ll, d ll / d y, owned ll
-constexpr int SCR_W = 880;               // per warp of the table kernel: KL arrays (2 x 44 doubles,
-                                         // 44 floats) or the table builder's 96 floats
+constexpr int SCR_W = 880;               // bytes per warp of the table kernel: KL arrays (2 x 44
+                                         // doubles, 44 floats) or the table builder's 96 floats
 constexpr int RED_W = 16;                // floats per warp of an item's warp sums
 
 // the rest of the item kernel's shared memory (bytes), after the two stages
@@ -107,8 +107,7 @@ struct Lay {
     static constexpr int red = pg + PX * PG_F * NTC * 4;           // [2][NWC][RED_W] warp sums
     static constexpr int bar = red + 2 * NWC * RED_W * 4;          // full[2], reduced[2]
     static constexpr int task = bar + 4 * 8;                       // [2] ZTask
-    static constexpr int cnt = task + 2 * (int)sizeof(ZTask);      // [2] warps done with the item
-    static constexpr int bytes = cnt + 16;
+    static constexpr int bytes = task + 2 * (int)sizeof(ZTask);
     static_assert(task % 16 == 0 && bar % 8 == 0, "alignment");
 };
 
@@ -856,7 +855,7 @@ __device__ __forceinline__ void kl_task(const ItemArgs& a, int s, float* scr) {
     for (int i = lane; i < NP; i += 32) a.kl_grad[(size_t)NP * s + i] = kg[i];
 }
 
-// After an item, on the last compute warp to finish it: the warps' sums added in warp
+// After an item, on the producer warp: the compute warps' sums added in warp
 // order (FP64), the patch's chain rule applied (column j of d ll / d theta =
 // sum_e k_e d ll / d y_{y_e}, FP64) and the item's record written.
 template <int MODE>
@@ -965,10 +964,10 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
 // the kernels
 
 // Tables and KL terms: warp u < n_patch builds the table and chain-rule record of the
-// patch of torder[u] (the patches in the order the items first read them) and publishes it; warp
-// n_patch + s computes the KL of source s (with the domain check of its theta) and counts
-// as one of the source's arrivals.  The item kernel is launched as this kernel's
-// programmatic dependent and waits for each table's flag, not for this kernel.
+// patch of torder[u] (the patches in the order the items first read them) and publishes
+// it; warp n_patch + s computes the KL terms of source s (with the domain check of its
+// theta).  The item kernel is launched as this kernel's programmatic dependent and waits
+// for each table's flag, not for this kernel.
 __global__ void __launch_bounds__(128) k_tables(ItemArgs a) {
     __shared__ __align__(16) float scr[4][SCR_W / 4];
     pdl_trigger();
@@ -1075,11 +1074,11 @@ __global__ void __launch_bounds__(32 * FIN_W) k_finish(ItemArgs a) {
 }
 
 // The items, on persistent CTAs of four compute warps and a producer warp.  The producer
-// keeps the next two items in the two stages (item i + 2 goes to the stage of item i as
-// soon as the compute warps are done with it), one task record ahead in registers and
-// one queue slot claimed beyond that.  CTA c's first two items are slots c and c + G
-// (G CTAs); later slots come from the queue counter.  The last compute warp to finish an item writes its
-// record.
+// keeps the next two items in the two stages: once the compute warps are done with item
+// i it writes item i's record (the warps' sums in FP64, the chain rule) and puts item
+// i + 2 in that stage; it holds one task record ahead in registers and one queue slot
+// claimed beyond that.  CTA c's first two items are slots c and c + G (G CTAs); later
+// slots come from the queue counter.
 template <int MODE, int PX, int NPE, int NPD, int MINB, int UNR>
 __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_items(ItemArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1088,7 +1087,6 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
     uint64_t* reduced = full + 2;
     ZTask* tasks = reinterpret_cast<ZTask*>(smem + L::task);
     float* red = reinterpret_cast<float*>(smem + L::red);
-    int* cnt = reinterpret_cast<int*>(smem + L::cnt);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     pdl_trigger();   // the epilogue kernel may start (it waits for this grid to finish)
     if (t == 0) {
@@ -1097,7 +1095,6 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
         mbar_init(&reduced[0], NTC);
         mbar_init(&reduced[1], NTC);
         mbar_init_fence();
-        cnt[0] = cnt[1] = 0;
     }
     __syncthreads();
     int32_t* queue = a.ready + a.n_patch;
@@ -1120,12 +1117,16 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
             __syncwarp();
             if (tasks[b].kind == ZT_END) break;
             if (!mbar_wait_launch(&reduced[b], (i >> 1) & 1, a.status)) break;
+            // item i is done: its record (FP64, off the compute warps), then item i + 2
+            finish_item<MODE>(a, tasks[b].item.out, smem + b * ST_BYTES, red + b * NWC * RED_W);
+            __syncwarp();
             prepare<MODE>(a, ra, smem + b * ST_BYTES, &tasks[b], &full[b], all_built);
             ra = load_task(a, __shfl_sync(0xffffffffu, qb, 0));
             if (lane == 0) qb = base + atomicAdd(queue, 1);
         }
         // this grid completes only after the table kernel (and its KL terms) has, so the
-        // epilogue kernel that waits for this grid sees both
+        // epilogue kernel that waits for this grid sees both, and the next evaluation's
+        // flag reset follows both
         pdl_wait();
         return;
     }
@@ -1140,18 +1141,7 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
         const uint8_t* stage = smem + b * ST_BYTES;
         float* rb = red + b * NWC * RED_W;
         item_compute<MODE, PX, NPE, NPD, UNR>(a, it, stage, vs, spg, rb + w * RED_W);
-        // the last warp to finish adds the warps' sums and writes the item's record
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) {
-            __threadfence_block();
-            last = atomicAdd(&cnt[b], 1) == NWC - 1;
-        }
-        if (__shfl_sync(0xffffffffu, last, 0)) {
-            __threadfence_block();
-            finish_item<MODE>(a, it.out, stage, rb);
-            if (lane == 0) cnt[b] = 0;
-        }
+        // the producer adds the warps' sums and writes the item's record
         __syncwarp();
         mbar_arrive_plain(&reduced[b]);
     }
