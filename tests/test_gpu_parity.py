@@ -133,6 +133,41 @@ def test_device_entry_points_match_host(cel):
     P.close()
 
 
+def test_page_locked_host_calls_match_pageable(cel):
+    """The host-pointer call with page-locked host buffers (as the bench's end-to-end leg
+    uses them): the same bits as with pageable buffers, the buffers re-read on every
+    call, and a domain error still reported."""
+    import ctypes as C
+    import torch
+    prob = synth.config(2)
+    P = cel.Problem(prob)
+    n = prob.n_src
+    th = torch.tensor(prob.theta, dtype=torch.float64).pin_memory()
+    tot = torch.zeros(1, dtype=torch.float64).pin_memory()
+    loc = torch.zeros(n, dtype=torch.float64).pin_memory()
+    g = torch.zeros(n, 44, dtype=torch.float64).pin_memory()
+
+    def call():
+        return P.L.celeste_elbo_grad(P.h, C.c_void_p(th.data_ptr()), cel.FP32, C.c_void_p(tot.data_ptr()),
+                                     C.c_void_p(loc.data_ptr()), C.c_void_p(g.data_ptr()))
+
+    for theta in (prob.theta, prob.theta * np.where(np.arange(44) == synth.I_R1, 1.01, 1.0)):
+        th.copy_(torch.from_numpy(theta))
+        for _ in range(2):
+            assert call() == 0
+            t0, l0, g0 = P.elbo_grad(theta, precision=cel.FP32)   # pageable buffers
+            assert tot.item() == t0
+            np.testing.assert_array_equal(loc.numpy(), l0)
+            np.testing.assert_array_equal(g.numpy(), g0)
+    bad = prob.theta.copy()
+    bad[1, synth.I_R2] = -1.0
+    th.copy_(torch.from_numpy(bad))
+    assert call() == cel.ERR_ARG
+    th.copy_(torch.from_numpy(prob.theta))
+    assert call() == 0
+    P.close()
+
+
 def test_invalid_parameters_are_errors_not_faults(cel):
     import torch
     prob = synth.config(0)
