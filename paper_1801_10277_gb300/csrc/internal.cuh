@@ -70,7 +70,9 @@ constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, 
 constexpr int ZFULL_FLOATS = 16 + MAXPSF * (8 + ((MAXPROF + 2) / 2) * 8) + MAXPSF * (12 + ((MAXPROF + 2) / 2) * 12);
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)
 constexpr int ZIMAX = 512;   // pixels per item of the FP32 value / gradient kernel
-constexpr int ZMAXC = 4;     // other covering patches staged with such an item (more are read in place)
+constexpr int ZMAXC = 4;     // other covering patches named inline in such an item's queue record
+constexpr int ZSTAGE = 12;   // other covering patches whose value records an item stages (more are
+                             // read in place)
 constexpr int TILE = 16;     // gather tiles are TILE x TILE pixels
 
 struct ImgMeta {

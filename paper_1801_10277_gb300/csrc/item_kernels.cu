@@ -24,7 +24,7 @@
 // a queue (a global counter over the items in decreasing cost): up to ZIMAX pixels of one
 // patch, the multiply covered ones first.  The producer waits for the tables an item
 // reads and copies its patch's table and chain-rule record, its pixel records and the
-// value records of up to ZMAXC other patches covering its pixels into a shared-memory
+// value records of up to ZSTAGE other patches covering its pixels into a shared-memory
 // stage with bulk asynchronous copies (two stages, completing on mbarriers), while the
 // compute warps run the item in the other stage.  They evaluate the mixture and its
 // derivatives at the item's pixels; where other patches cover a pixel, E = sky + sum_s
@@ -82,13 +82,13 @@ constexpr int NTC = 32 * NWC;
 constexpr int IT_THREADS = NTC + 32;
 
 // One shared-memory stage (bytes): the item's table, its patch's chain-rule record, its
-// pixel records, and its first ZMAXC candidates' records and value tables.
+// pixel records, and its first ZSTAGE candidates' records and value tables.
 constexpr int ST_TBL = 0;
 constexpr int ST_CHAIN = ST_TBL + ZFULL * 4;
 constexpr int ST_PX = ST_CHAIN + NP * 16;
 constexpr int ST_ZC = ST_PX + ZIMAX * 16;
-constexpr int ST_VREC = ST_ZC + ZMAXC * (int)sizeof(ZCand);
-constexpr int ST_BYTES = ST_VREC + ZMAXC * VFULL * 4;
+constexpr int ST_VREC = ST_ZC + ZSTAGE * (int)sizeof(ZCand);
+constexpr int ST_BYTES = ST_VREC + ZSTAGE * VFULL * 4;
 static_assert(ST_CHAIN % 16 == 0 && ST_PX % 16 == 0 && ST_ZC % 16 == 0 && ST_VREC % 16 == 0 && ST_BYTES % 16 == 0,
               "bulk copies land on 16-byte boundaries");
 static_assert(sizeof(ZCand) == 32 && sizeof(ZTask) == 64, "record sizes");
@@ -753,8 +753,8 @@ __device__ __forceinline__ void item_compute(const ItemArgs& a, const ZItem& it,
                 owner[p] = true;
             }
             for (int ci = 0; ci < nc; ++ci) {
-                const ZCand c = ci < ZMAXC ? zc[ci] : a.cands[it.c0 + ci];
-                const float* R = ci < ZMAXC ? vrec + ci * VFULL : a.ztbl + (size_t)c.patch * ZFULL;
+                const ZCand c = ci < ZSTAGE ? zc[ci] : a.cands[it.c0 + ci];
+                const float* R = ci < ZSTAGE ? vrec + ci * VFULL : a.ztbl + (size_t)c.patch * ZFULL;
                 if (!added && c.src > it.src) {
 #pragma unroll
                     for (int p = 0; p < PX; ++p) {
@@ -855,26 +855,50 @@ __device__ __forceinline__ void kl_task(const ItemArgs& a, int s, float* scr) {
     for (int i = lane; i < NP; i += 32) a.kl_grad[(size_t)NP * s + i] = kg[i];
 }
 
-// After an item, on the producer warp: the compute warps' sums added in warp
-// order (FP64), the patch's chain rule applied (column j of d ll / d theta =
-// sum_e k_e d ll / d y_{y_e}, FP64) and the item's record written.
+// After an item, on the producer warp: the compute warps' sums added in warp order
+// (FP64), the patch's chain rule applied (column j of d ll / d theta =
+// sum_e k_e d ll / d y_{y_e}, FP64) and the item's record written.  In two parts: what
+// the record needs from the item's stage and warp sums, read into registers (so that the
+// stage can take its next item at once), then the FP64 arithmetic and the stores.
+struct ItemSums {
+    float r[NWC];       // lane < NS: the warps' sums of column lane
+    float4 ch[2];       // the chain-rule columns lane, lane + 32
+};
+
 template <int MODE>
-__device__ __forceinline__ void finish_item(const ItemArgs& a, int out, const uint8_t* stage, const float* red) {
+__device__ __forceinline__ ItemSums finish_load(const uint8_t* stage, const float* red) {
     const int lane = threadIdx.x & 31;
     constexpr int NS = (MODE == MODE_LL) ? 2 : 2 + NY;   // ll, (d ll / d y), owned ll
-    double y = 0.0;
-    if (lane < NS)
+    ItemSums q;
 #pragma unroll
-        for (int w = 0; w < NWC; ++w) y += (double)red[w * RED_W + lane];
-    double* rec = a.part + (size_t)out * ZPCOLS;
-    if (lane == 0) rec[0] = y;
-    if (lane == NS - 1) rec[1] = y;
+    for (int w = 0; w < NWC; ++w) q.r[w] = lane < NS ? red[w * RED_W + lane] : 0.f;
     if constexpr (MODE >= MODE_GRAD) {
         const float4* ch = reinterpret_cast<const float4*>(stage + ST_CHAIN);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
-            const float4 r = ch[c < NP ? c : 0];
+            q.ch[h] = ch[c < NP ? c : 0];
+        }
+    }
+    return q;
+}
+
+template <int MODE>
+__device__ __forceinline__ void finish_store(const ItemArgs& a, int out, const ItemSums& q) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NS = (MODE == MODE_LL) ? 2 : 2 + NY;
+    double y = 0.0;
+    if (lane < NS)
+#pragma unroll
+        for (int w = 0; w < NWC; ++w) y += (double)q.r[w];
+    double* rec = a.part + (size_t)out * ZPCOLS;
+    if (lane == 0) rec[0] = y;
+    if (lane == NS - 1) rec[1] = y;
+    if constexpr (MODE >= MODE_GRAD) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            const float4 r = q.ch[h];
             const int yy = __float_as_int(r.w);
             const double y0 = __shfl_sync(0xffffffffu, y, 1 + (yy & 15));
             const double y1 = __shfl_sync(0xffffffffu, y, 1 + ((yy >> 4) & 15));
@@ -914,7 +938,9 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
         return;
     }
     const ZItem it = tk->item;
-    const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZMAXC ? nc : ZMAXC;
+    const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZSTAGE ? nc : ZSTAGE;
+    // candidate e's patch: named in the record for e < ZMAXC, else in the candidate list
+    auto cand_patch = [&](int e) { return e < ZMAXC ? tk->cand[e] : a.cands[it.c0 + e].patch; };
 #ifdef CELESTE_CHECK_BOUNDS
     {
         // the record's offsets into the pixel records, candidates, tables and item records;
@@ -924,7 +950,7 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
                   it.pix + n <= a.n_sp && it.c0 >= 0 && (int64_t)it.c0 + nc <= a.n_zcand && it.out >= 0 &&
                   it.out < a.n_sitem && it.src >= 0 && it.src < a.n_src && npsf >= 1 && npsf <= MAXPSF;
         for (int e = 0; ok && e < nc; ++e) {
-            const int pe = e < ZMAXC ? tk->cand[e] : a.cands[it.c0 + e].patch;
+            const int pe = cand_patch(e);
             ok = pe >= 0 && pe < a.n_patch;
         }
         if (!CEL_IN_BOUNDS(ok, a.status)) {
@@ -939,8 +965,7 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
             all_built = true;
         } else {
             wait_ready(a.ready + it.patch, a.status);
-            for (int e = 0; e < nc0; ++e) wait_ready(a.ready + tk->cand[e], a.status);
-            for (int e = ZMAXC; e < nc; ++e) wait_ready(a.ready + a.cands[it.c0 + e].patch, a.status);
+            for (int e = 0; e < nc; ++e) wait_ready(a.ready + cand_patch(e), a.status);
         }
     }
     fence_proxy_async_global();
@@ -956,7 +981,7 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
     if (nc0 > 0) {
         bulk_g2s_tx(stage + ST_ZC, a.cands + it.c0, (unsigned)nc0 * (unsigned)sizeof(ZCand), full);
         for (int e = 0; e < nc0; ++e)
-            bulk_g2s_tx(stage + ST_VREC + e * VFULL * 4, a.ztbl + (size_t)tk->cand[e] * ZFULL, VFULL * 4, full);
+            bulk_g2s_tx(stage + ST_VREC + e * VFULL * 4, a.ztbl + (size_t)cand_patch(e) * ZFULL, VFULL * 4, full);
     }
 }
 
@@ -1117,10 +1142,13 @@ __global__ void __launch_bounds__(IT_THREADS) __maxnreg__(regs_for(MINB)) k_item
             __syncwarp();
             if (tasks[b].kind == ZT_END) break;
             if (!mbar_wait_launch(&reduced[b], (i >> 1) & 1, a.status)) break;
-            // item i is done: its record (FP64, off the compute warps), then item i + 2
-            finish_item<MODE>(a, tasks[b].item.out, smem + b * ST_BYTES, red + b * NWC * RED_W);
+            // item i is done: what its record needs, read from the stage; item i + 2's
+            // copies into the stage; item i's record (FP64, off the compute warps)
+            const int out = tasks[b].item.out;
+            const ItemSums q = finish_load<MODE>(smem + b * ST_BYTES, red + b * NWC * RED_W);
             __syncwarp();
             prepare<MODE>(a, ra, smem + b * ST_BYTES, &tasks[b], &full[b], all_built);
+            finish_store<MODE>(a, out, q);
             ra = load_task(a, __shfl_sync(0xffffffffu, qb, 0));
             if (lane == 0) qb = base + atomicAdd(queue, 1);
         }
