@@ -924,23 +924,27 @@ __device__ __forceinline__ int4 load_task(const ItemArgs& a, int q) {
 
 // Put a task record (lanes 0 .. 3) in a stage and, for an item, wait for the tables it
 // reads and start the bulk copies of its data into the stage; the stage's full barrier
-// completes when they land (at once for the end marker).  Whole warp; lane 0 does the
-// waits and the copies.  all_built (lane 0): every table was seen built, so no flag need
-// be read.
+// completes when they land (at once for the end marker).  Whole warp, every lane one of
+// the item's patches (lane 0 its own, lane 1 + e candidate e), so that the patch ids,
+// the ready flags and the copies of the candidates' value records take one memory round
+// trip each instead of one per candidate.  all_built (every lane): every table was seen
+// built, so no flag need be read.
 template <int MODE>
 __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, uint64_t* full, bool& all_built) {
     const int lane = threadIdx.x & 31;
+    const unsigned fullmask = 0xffffffffu;
     if (lane < 4) reinterpret_cast<int4*>(tk)[lane] = rec;
     __syncwarp();
-    if (lane != 0) return;
     if (tk->kind != ZT_ITEM) {
-        mbar_arrive_plain(full);
+        if (lane == 0) mbar_arrive_plain(full);
         return;
     }
     const ZItem it = tk->item;
     const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZSTAGE ? nc : ZSTAGE;
     // candidate e's patch: named in the record for e < ZMAXC, else in the candidate list
     auto cand_patch = [&](int e) { return e < ZMAXC ? tk->cand[e] : a.cands[it.c0 + e].patch; };
+    // this lane's patch: 0 the item's own, 1 + e candidate e (staged ones: e < nc0 <= 31)
+    const int pl = lane == 0 ? it.patch : (lane - 1 < nc ? cand_patch(lane - 1) : -1);
 #ifdef CELESTE_CHECK_BOUNDS
     {
         // the record's offsets into the pixel records, candidates, tables and item records;
@@ -949,39 +953,49 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
         bool ok = it.patch >= 0 && it.patch < a.n_patch && n >= 1 && n <= ZIMAX && nm <= n && it.pix >= 0 &&
                   it.pix + n <= a.n_sp && it.c0 >= 0 && (int64_t)it.c0 + nc <= a.n_zcand && it.out >= 0 &&
                   it.out < a.n_sitem && it.src >= 0 && it.src < a.n_src && npsf >= 1 && npsf <= MAXPSF;
-        for (int e = 0; ok && e < nc; ++e) {
-            const int pe = cand_patch(e);
+        for (int j = lane; ok && j <= nc; j += 32) {
+            const int pe = j == 0 ? it.patch : cand_patch(j - 1);
             ok = pe >= 0 && pe < a.n_patch;
         }
-        if (!CEL_IN_BOUNDS(ok, a.status)) {
-            tk->kind = ZT_END;
-            mbar_arrive_plain(full);
+        ok = __all_sync(fullmask, ok);
+        if (!ok) {
+            if (lane == 0) {
+                CEL_IN_BOUNDS(false, a.status);
+                tk->kind = ZT_END;
+                mbar_arrive_plain(full);
+            }
             return;
         }
     }
 #endif
     if (!all_built) {
-        if (load_acquire(a.ready + a.n_patch + 1) >= a.n_patch) {
-            all_built = true;
-        } else {
-            wait_ready(a.ready + it.patch, a.status);
-            for (int e = 0; e < nc; ++e) wait_ready(a.ready + cand_patch(e), a.status);
-        }
+        // lane 0 reads the built counter while the lanes read the flags of their patches
+        bool built = false;
+        if (lane == 0) built = load_acquire(a.ready + a.n_patch + 1) >= a.n_patch;
+        else if (pl >= 0) wait_ready(a.ready + pl, a.status);
+        for (int j = lane + 32; j <= nc; j += 32) wait_ready(a.ready + cand_patch(j - 1), a.status);
+        if (lane == 0 && !built) wait_ready(a.ready + it.patch, a.status);
+        all_built = __shfl_sync(fullmask, built, 0);
     }
-    fence_proxy_async_global();
-    fence_proxy_async_smem();   // the stage was last read through the generic proxy
+    __syncwarp();
+    // lane 0 announces the bytes before any copy is issued
     const unsigned tbl_bytes = MODE == MODE_LL ? VFULL * 4 : ZFULL * 4;
     const unsigned chain_bytes = MODE == MODE_LL ? 0u : NP * 16;
-    const unsigned bytes =
-        tbl_bytes + chain_bytes + (unsigned)n * 16u + (unsigned)nc0 * (unsigned)(sizeof(ZCand) + VFULL * 4);
-    mbar_expect_arrive(full, bytes);
-    bulk_g2s_tx(stage + ST_TBL, a.ztbl + (size_t)it.patch * ZFULL, tbl_bytes, full);
-    if (chain_bytes) bulk_g2s_tx(stage + ST_CHAIN, a.zchain + (size_t)it.patch * NP, chain_bytes, full);
-    bulk_g2s_tx(stage + ST_PX, a.px + it.pix, (unsigned)n * 16u, full);
-    if (nc0 > 0) {
-        bulk_g2s_tx(stage + ST_ZC, a.cands + it.c0, (unsigned)nc0 * (unsigned)sizeof(ZCand), full);
-        for (int e = 0; e < nc0; ++e)
-            bulk_g2s_tx(stage + ST_VREC + e * VFULL * 4, a.ztbl + (size_t)cand_patch(e) * ZFULL, VFULL * 4, full);
+    if (lane == 0) {
+        const unsigned bytes =
+            tbl_bytes + chain_bytes + (unsigned)n * 16u + (unsigned)nc0 * (unsigned)(sizeof(ZCand) + VFULL * 4);
+        mbar_expect_arrive(full, bytes);
+    }
+    __syncwarp();
+    fence_proxy_async_global();
+    fence_proxy_async_smem();   // the stage was last read through the generic proxy
+    if (lane == 0) {
+        bulk_g2s_tx(stage + ST_TBL, a.ztbl + (size_t)it.patch * ZFULL, tbl_bytes, full);
+        if (chain_bytes) bulk_g2s_tx(stage + ST_CHAIN, a.zchain + (size_t)it.patch * NP, chain_bytes, full);
+        bulk_g2s_tx(stage + ST_PX, a.px + it.pix, (unsigned)n * 16u, full);
+        if (nc0 > 0) bulk_g2s_tx(stage + ST_ZC, a.cands + it.c0, (unsigned)nc0 * (unsigned)sizeof(ZCand), full);
+    } else if (lane - 1 < nc0) {
+        bulk_g2s_tx(stage + ST_VREC + (lane - 1) * VFULL * 4, a.ztbl + (size_t)pl * ZFULL, VFULL * 4, full);
     }
 }
 
