@@ -43,7 +43,7 @@ SM_COUNT = 152
 # DRAM bytes (read + write) per launch of the item kernel on the one-field workload, from one
 # ncu capture (profiles/k_items_field_500src.md); emptied whenever the kernel changes after
 # the capture.
-DRAM_BYTES_PER_LAUNCH = {"items": 26234368}
+DRAM_BYTES_PER_LAUNCH = {"items": 26240256}
 DRAM_BYTES_SOURCE = "ncu capture of one k_items launch, profiles/k_items_field_500src.md (imported, not measured here)"
 FP32_LANES = 128
 XU_LANES = 16   # MUFU ex2 results per SM per clock
