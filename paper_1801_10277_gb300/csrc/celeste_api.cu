@@ -791,7 +791,9 @@ celeste_status celeste_problem_create_ex(const celeste_image* imgs, int32_t n_im
         // build records from the final patch geometry (a patch with its own linearised map
         // refers to the image copy that carries it)
         std::vector<ZBuild> zb;
-        for (const int32_t p : ztorder) zb.push_back(ZBuild{p, geo[p].img, geo[p].src, geo[p].x0, geo[p].y0, {0, 0, 0}});
+        for (const int32_t p : ztorder)
+            zb.push_back(ZBuild{p, geo[p].img, geo[p].src, 0, im[geo[p].img].t[0] - (double)geo[p].x0,
+                                im[geo[p].img].t[1] - (double)geo[p].y0});
         if ((st = dupload(pr, &d_tord, zb.data(), zb.size()))) return bail(st);
         if ((st = dupload(pr, &d_zt, ztasks.data(), ztasks.size()))) return bail(st);
         if (!zcands.empty() && (st = dupload(pr, &d_zc, zcands.data(), zcands.size()))) return bail(st);

@@ -95,6 +95,7 @@ struct ImgMeta {
     float psf_sg[MAXPSF];
     float psf_dm[MAXPSF];
     float sky_f;
+    float iota_f;
 };
 
 struct PatchGeo {
@@ -136,7 +137,8 @@ struct ZCand {
 // What the table kernel needs of a patch to build its table: the patch, its image and
 // source, and its origin in the image.
 struct ZBuild {
-    int32_t patch, img, src, x0, y0, pad[3];
+    int32_t patch, img, src, pad;
+    double ox, oy;   // the image map's translation minus the patch origin (FP64, from the host)
 };
 
 struct Tile {
@@ -196,6 +198,7 @@ inline void fill_float_copies(ImgMeta& im) {
         for (int c = 0; c < 6; ++c) im.psf_f[k][c] = (float)im.psf[k][c];
     for (int k = 0; k < 4; ++k) im.A_f[k] = (float)im.A[k];
     im.sky_f = (float)im.sky;
+    im.iota_f = (float)im.iota;
     const double detA = im.A[0] * im.A[3] - im.A[1] * im.A[2];
     for (int k = 0; k < MAXPSF; ++k) {
         im.psf_li[k][0] = im.psf_li[k][1] = im.psf_li[k][2] = 0.f;

@@ -162,14 +162,14 @@ __device__ __forceinline__ void build_patch_table(const double* __restrict__ the
     const int kk = lane < npsf ? lane : 0;
     const float li0 = im.psf_li[kk][0], li1 = im.psf_li[kk][1], li2 = im.psf_li[kk][2], dmk = im.psf_dm[kk];
     const float ps1 = im.psf_f[kk][1], ps2 = im.psf_f[kk][2], csk = im.psf_cs[kk], sgk = im.psf_sg[kk];
-    const float iota = (float)im.iota;
+    const float iota = im.iota_f;
     const int n_exp = md.n_exp, n_dev = md.n_dev;
     thf[lane] = (float)th[lane];
     if (lane + 32 < NP) thf[lane + 32] = (float)th[lane + 32];
     if (lane == 0) {
         const double u0 = th[0], u1 = th[1];
-        mu[0] = (float)(im.A[0] * u0 + im.A[1] * u1 + im.t[0] - g.x0);
-        mu[1] = (float)(im.A[2] * u0 + im.A[3] * u1 + im.t[1] - g.y0);
+        mu[0] = (float)fma(im.A[0], u0, fma(im.A[1], u1, g.ox));
+        mu[1] = (float)fma(im.A[2], u0, fma(im.A[3], u1, g.oy));
     }
     __syncwarp();
     const float rho = thf[P_AXIS], phi = thf[P_ANGLE], sg = thf[P_SCALE], ed = thf[P_EDEV];

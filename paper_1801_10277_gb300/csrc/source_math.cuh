@@ -248,16 +248,22 @@ __device__ inline double kl_warp(const ModelDev& md, const double* th, const R* 
 // Domain of parameter j (celeste.h): every entry finite; e_dev in [0,1]; e_axis in
 // (0,1]; e_scale, r2, c2, k > 0; a in (0,1).  A violation sets the status word
 // (CELESTE_ERR_NONFINITE or CELESTE_ERR_ARG); nothing traps.
+// The comparisons run on the bit pattern (integer operations): for a finite double the
+// signed 64-bit pattern orders like the value when the value is >= +0, every negative
+// value has a negative pattern and -0 is the pattern's minimum (GB300's FP64 pipe is
+// narrow, and these checks run for every parameter of every source in every evaluation).
 __device__ inline void theta_domain_check(int j, double x, int32_t* status) {
-    bool ok;
-    if (!isfinite(x)) {
+    const long long b = __double_as_longlong(x);
+    constexpr long long ONE = 0x3FF0000000000000LL, NEG_ZERO = (long long)0x8000000000000000ULL;
+    if (((b >> 52) & 0x7FF) == 0x7FF) {   // Inf or NaN
         atomicExch(status, (int32_t)CELESTE_ERR_NONFINITE);
         return;
     }
-    if (j == P_EDEV) ok = x >= 0.0 && x <= 1.0;
-    else if (j == P_AXIS) ok = x > 0.0 && x <= 1.0;
-    else if (j == P_SCALE || (j >= P_R2 && j < P_C1) || (j >= P_C2 && j < P_A) || j >= P_K) ok = x > 0.0;
-    else if (j == P_A || j == P_A + 1) ok = x > 0.0 && x < 1.0;
+    bool ok;
+    if (j == P_EDEV) ok = (b >= 0 && b <= ONE) || b == NEG_ZERO;   // [0, 1]
+    else if (j == P_AXIS) ok = b > 0 && b <= ONE;                   // (0, 1]
+    else if (j == P_SCALE || (j >= P_R2 && j < P_C1) || (j >= P_C2 && j < P_A) || j >= P_K) ok = b > 0;   // > 0
+    else if (j == P_A || j == P_A + 1) ok = b > 0 && b < ONE;       // (0, 1)
     else ok = true;
     if (!ok) atomicExch(status, (int32_t)CELESTE_ERR_ARG);
 }
