@@ -4,24 +4,31 @@ SDSS-shaped field (5 bands x 2048 x 1489 px, 500 sources), FP32 per-pixel arithm
 with FP64 accumulation, next to the plain FP64 path, the end-to-end host-pointer call
 and the FP64 CPU oracle.
 
-One step = one ELBO + gradient evaluation of every source of the field (brightness
-moments and mixture tables, per-source E/Var contributions, E/Var maps and
-log-likelihood, adjoint, chain rule + KL, total), i.e. one source-pixel evaluation per
-(source, active pixel) pair.  Inputs are resident on the device; L2 is flushed
-(256 MiB write) between timed steps, outside the timed events.
+One step = one ELBO + gradient evaluation of every source of the field (the patch
+tables and KL terms, every item's mixture values and derivatives with its neighbours'
+E/Var at multiply covered pixels, log-likelihood, adjoint and chain rule, then the
+per-source epilogues and the total), i.e. one source-pixel evaluation per (source,
+active pixel) pair.  Inputs are resident on the device; L2 is flushed (256 MiB write)
+between timed steps, outside the timed events.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --step-only ...    the FP32 step alone (the profiling command)
+  python bench.py --fit-only ...     the Newton fit alone (the fit's profiling command)
+  python bench.py --workload N ...   another workload as the step (see --help)
 Multi-GPU (torchrun): every rank evaluates its own field (weak scaling, no collective
 on the data path); timing is the max over ranks.
 
-Besides the step (`value`, `e2e`, `fp64_path`) the JSON line carries: `roofline` (the
-dominant pixel kernel's achieved FLOP rate against the FP32 peak derived from unit
-counts and clock, its measured DRAM bytes per launch, every stage's CUDA-event time as
-the call runs them and serialised on one stream, and `step`: the whole step against
-its plain-ALU bound); `cpu_baseline` (the FP64 oracle on all host cores and on one);
-`hessian`, `fit`, `fit_schedules`, `catalog` and `tasks` legs; `clocks` sampled during
-the timed region; `gpu_launches`.  `--impl reference` times the oracle instead (rank 0
-only) on a bounded sample of the same field.
+Besides the step (`value`, `e2e`, `fp64_path` with its FP64 roofline) the JSON line
+carries: `roofline` (the item kernel's achieved FLOP rate against the FP32 peak derived
+from unit counts and clock, its DRAM bytes per launch imported from an ncu capture,
+every stage's CUDA-event time as the call runs them and serialised on one stream, and
+`step`: the whole step against its plain-ALU bound); `cpu_baseline` (the FP64 oracle on
+all host cores and on one); `hessian` (with its FLOP count, roofline and cost relative
+to ELBO + gradient), `fit` (with the FP32 sweeps alone, `fp32_only`, and fit quality),
+`fit_schedules`, `catalog`, `workloads` (the crowded region, the sweep field and the
+multi-epoch region) and `tasks` legs; `clocks` sampled around and during the timed
+region; `gpu_launches`.  `--impl reference` times the oracle instead (rank 0 only) on a
+bounded sample of the same field.
 """
 import argparse
 import json
