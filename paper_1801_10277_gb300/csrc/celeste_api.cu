@@ -1117,7 +1117,9 @@ celeste_status celeste_set_tuning(celeste_problem* pr, int32_t contrib_code, int
                     "contrib code: 0 default, 1 / 2 / 4 pixels per thread, 3 / 5 packed FP32x2 (2 / 4 "
                     "pixels), 6 / 7 the same as persistent CTAs on a work queue");
     if (items_code < 0 || items_code > 5)
-        return fail(CELESTE_ERR_ARG, "items code: 0 default, 1 .. 5 the item kernel's register budget");
+        return fail(CELESTE_ERR_ARG,
+                    "items code: 0 default, 1 .. 5 the item kernel's variant (pixels per thread, CTAs per SM, "
+                    "unroll)");
     pr->P.tune_contrib = contrib_code;
     pr->P.tune_items = items_code;
     return CELESTE_OK;

@@ -69,7 +69,7 @@ constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, 
 // component 12 + 12 per pair); each profile group padded to an even count
 constexpr int ZFULL_FLOATS = 16 + MAXPSF * (8 + ((MAXPROF + 2) / 2) * 8) + MAXPSF * (12 + ((MAXPROF + 2) / 2) * 12);
 constexpr int CHUNK = 256;   // pixels per work item (one CTA)
-constexpr int ZIMAX = 512;   // pixels per item of the FP32 value / gradient kernel
+constexpr int ZIMAX = 512;   // most pixels per item of the FP32 value / gradient kernel
 constexpr int ZMAXC = 4;     // other covering patches named inline in such an item's queue record
 constexpr int ZSTAGE = 12;   // other covering patches whose value records an item stages (more are
                              // read in place)
@@ -296,10 +296,12 @@ struct DevProblem {
     float4* zchain;              // [n_patch][NP] chain-rule records of the patches
     int32_t* zready;             // [n_patch] table ready flags, then the queue counter and the
                                  // count of built tables (reset before each launch)
-    int32_t tune_items;          // item kernel variant: 1 one pixel per thread, else two
+    int32_t tune_items;          // item kernel variant, 1 .. 5 (pixels per thread, CTAs per SM,
+                                 // unroll; item_kernels.cu); 0 = the default, 1
     int32_t model_ne, model_nd;     // exp / dev profile components of the model
-    int32_t* queue;          // [2] persistent-kernel work queue (next item, finished CTAs), 0 between
-                             // launches (nullable: the persistent variants fall back to one CTA per item)
+    int32_t* queue;          // [2] work queue of the FP64 / Hessian map pass's persistent variants
+                             // (next item, finished CTAs), 0 between launches (nullable: those
+                             // variants fall back to one CTA per item)
     int32_t* status;
     // sizes the bounds checks compare against (CELESTE_CHECK_BOUNDS)
     int32_t n_img_rec;           // image records (the images, then per-patch map copies)
