@@ -943,8 +943,6 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
     const int n = it.n_nm & 0xffff, nc = it.nc_npsf & 0xffffff, nc0 = nc < ZSTAGE ? nc : ZSTAGE;
     // candidate e's patch: named in the record for e < ZMAXC, else in the candidate list
     auto cand_patch = [&](int e) { return e < ZMAXC ? tk->cand[e] : a.cands[it.c0 + e].patch; };
-    // this lane's patch: 0 the item's own, 1 + e candidate e (staged ones: e < nc0 <= 31)
-    const int pl = lane == 0 ? it.patch : (lane - 1 < nc ? cand_patch(lane - 1) : -1);
 #ifdef CELESTE_CHECK_BOUNDS
     {
         // the record's offsets into the pixel records, candidates, tables and item records;
@@ -968,6 +966,8 @@ __device__ void prepare(const ItemArgs& a, int4 rec, uint8_t* stage, ZTask* tk, 
         }
     }
 #endif
+    // this lane's patch: 0 the item's own, 1 + e candidate e (staged ones: e < nc0 <= 31)
+    const int pl = lane == 0 ? it.patch : (lane - 1 < nc ? cand_patch(lane - 1) : -1);
     if (!all_built) {
         // lane 0 reads the built counter while the lanes read the flags of their patches
         bool built = false;
