@@ -168,6 +168,36 @@ def test_page_locked_host_calls_match_pageable(cel):
     P.close()
 
 
+def test_parameter_domain_boundaries(cel):
+    """The device's domain check at the edges of each interval (it compares the doubles'
+    bit patterns): e_dev in [0, 1] (-0 and 1 accepted), e_axis in (0, 1] (0 rejected, 1
+    accepted), a in (0, 1) (1 rejected), variances > 0 (the smallest subnormal accepted,
+    +0 rejected), Inf and NaN non-finite.  Checked through the device entry point, whose
+    status the host reads."""
+    import torch
+    prob = synth.config(0)
+    P = cel.Problem(prob)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cases = [(synth.I_EDEV, -0.0, cel.OK), (synth.I_EDEV, 1.0, cel.OK), (synth.I_EDEV, np.nextafter(1.0, 2.0), cel.ERR_ARG),
+             (synth.I_EDEV, -1e-300, cel.ERR_ARG), (synth.I_AXIS, 0.0, cel.ERR_ARG), (synth.I_AXIS, 1.0, cel.OK),
+             (synth.I_AXIS, 5e-324, cel.OK), (synth.I_R2, 5e-324, cel.OK), (synth.I_R2, 0.0, cel.ERR_ARG),
+             (synth.I_R2, -0.0, cel.ERR_ARG), (synth.I_R2, np.inf, cel.ERR_NONFINITE),
+             (synth.I_R1, -np.inf, cel.ERR_NONFINITE), (synth.I_R1, np.nan, cel.ERR_NONFINITE)]
+    for j, v, want in cases:
+        th = prob.theta.copy()
+        th[1, j] = v
+        P.elbo_device(torch.tensor(th, dtype=torch.float64, device="cuda"), dt)
+        torch.cuda.synchronize()
+        assert P.device_status() == want, (j, v, P.device_status(), want)
+    th = prob.theta.copy()
+    th[1, synth.I_A] = 1.0
+    th[1, synth.I_A + 1] = 0.0
+    P.elbo_device(torch.tensor(th, dtype=torch.float64, device="cuda"), dt)
+    torch.cuda.synchronize()
+    assert P.device_status() == cel.ERR_ARG
+    P.close()
+
+
 def test_invalid_parameters_are_errors_not_faults(cel):
     import torch
     prob = synth.config(0)
