@@ -34,7 +34,7 @@ struct celeste_problem {
     };
     std::vector<std::pair<GraphKey, cudaGraphExec_t>> graphs;
     cudaStream_t capture = nullptr;       // private stream the graphs are captured on
-    // host copies used by the fit driver and validation
+    // host copies used by the fit's host loop and validation
     std::vector<int32_t> patch_off, nbr_off, nbrs;
     std::vector<PatchGeo> geo;
     std::vector<ImgMeta> imgs;

@@ -99,7 +99,7 @@ def test_step_bound_of_the_one_field_model():
 
 
 def test_reference_arm_under_torchrun_prints_once():
-    """Launched as the driver launches it for N > 1 (torchrun, two ranks), the reference
+    """Launched as a multi-GPU run launches it (torchrun, two ranks), the reference
     arm prints one JSON line, from rank 0, and every rank exits 0."""
     import socket
     with socket.socket() as s:
