@@ -18,6 +18,8 @@
 //   d2logN/dC[E]dC[F] = -q'E P F q + tr(P E P F)/2,   d2N = N (dlogN dlogN' + d2logN).
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "source_math.cuh"
 
@@ -30,12 +32,7 @@ __device__ __forceinline__ double ex2h(double x) { return exp2(x); }
 __device__ __forceinline__ float lgh(float x) { return logf(x); }
 __device__ __forceinline__ double lgh(double x) { return log(x); }
 
-template <class R>
-__device__ __forceinline__ R warp_sum_h(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+constexpr double LOG2E_H = 1.4426950408889634;   // log2(e)
 
 // packed index of the symmetric 12 x 12 (a <= b not required)
 __device__ __forceinline__ int P2(int a, int b) { return a <= b ? yh_index(a, b) : yh_index(b, a); }
@@ -43,6 +40,254 @@ __device__ __forceinline__ int P2(int a, int b) { return a <= b ? yh_index(a, b)
 }  // namespace
 
 constexpr int HV = 1 + NY + NYH;   // values reduced per work item
+constexpr int HVP = 96;            // HV padded to three per lane
+static_assert(HV <= HVP && HVP == 3 * 32, "the reduce-scatter leaves three sums per lane");
+
+// Sums v over the warp's 32 lanes and leaves lane l holding the sums of entries
+// 3 l, 3 l + 1, 3 l + 2 in v[0..2].  Five halving steps: at the step on lane bit m the
+// two lanes that differ in m hold the same index range; the one with m set keeps the
+// upper half and adds its partner's upper half, the other keeps and adds the lower
+// half.  93 shuffles instead of 5 per entry.
+template <class R>
+__device__ __forceinline__ void warp_reduce_scatter(R (&v)[HVP], int lane) {
+#pragma unroll
+    for (int m = 16, n = HVP; m > 0; m >>= 1, n >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const R send = up ? v[i] : v[i + n / 2];
+            const R keep = up ? v[i + n / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+}
+
+// ---- The galaxy components in the frame that whitens PSF component k (FP32 path).
+// T_k maps a pixel offset d to z = T_k d with T_k Sigma_k T_k' = I and T_k G T_k' =
+// diag(g1, g2), so component j's precision is T_k' diag(lam1, lam2) T_k with
+// lam_a = 1 / (1 + nu_j g_a).  With r = lam z and E~ = T_k E T_k', every derivative of
+// N_kj over (mu, G) is N_kj times T_k' (a polynomial in z) T_k:
+//   d/dmu: r;   d/dG[E]: (nu/2)(r' E~ r - tr(lam E~));   d2/dmu2: r r' - lam;
+//   d2/dmu dG[E]: r d/dG[E] - nu lam E~ r;
+//   d2/dG[E] dG[F]: d/dG[E] d/dG[F] - nu^2 r' E~ lam F~ r + (nu^2/2) tr(lam E~ lam F~).
+// A pixel therefore needs, per k, 35 sums over j of N_kj (or of its e_dev derivative)
+// times a monomial in (nu, lam1, lam2); the z-polynomials and the maps back to the
+// pixel frame are applied once per (pixel, k) instead of once per component.
+// Sums (monomial lam1^(deg - i) lam2^i at offset i):
+constexpr int WS_N = 0,    // N
+              WS_L = 1,    // N lam            (deg 1)
+              WS_LL = 3,   // N lam lam        (deg 2)
+              WS_B = 6,    // N nu lam         (deg 1)
+              WS_A = 8,    // N nu lam lam     (deg 2)
+              WS_C = 11,   // N nu lam^3       (deg 3)
+              WS_D2 = 15,  // N nu^2 lam^2
+              WS_D3 = 18,  // N nu^2 lam^3
+              WS_D4 = 22,  // N nu^2 lam^4
+              WS_NE = 27,  // dN/de_dev
+              WS_LE = 28,  // dN/de_dev lam
+              WS_BE = 30,  // dN/de_dev nu lam
+              WS_AE = 32,  // dN/de_dev nu lam lam
+              NWS = 35;
+constexpr int WROW = 40;   // floats per (k, j): exponent coefficients of z1^2, z2^2, constant; 35 weights; pad
+constexpr int WFR = 16;    // floats per k: T (row-major), K (3 x 3), g1, g2, pad
+// K[e][p] = (T E_e T')_p for the pixel-frame shape directions E_e = (xx, xy + yx, yy)
+// and the whitened pairs p = (11, 12, 22)
+constexpr int WF_K = 4, WF_G = 13;
+
+__host__ __device__ __forceinline__ int wpa(int p) { return p == 2 ? 1 : 0; }
+__host__ __device__ __forceinline__ int wpb(int p) { return p == 0 ? 0 : 1; }
+__host__ __device__ __forceinline__ float wmult(int p) { return p == 1 ? 2.f : 1.f; }
+__host__ __device__ __forceinline__ float wdl(int a, int b) { return a == b ? 1.f : 0.f; }
+
+// T_k from the Cholesky factor of the component's precision and one Jacobi rotation, in
+// FP32 (a few threads per work item, before its pixels: FP64 square roots and divisions
+// there would hold every warp of the item at the barrier; host-callable for tests)
+__host__ __device__ void whiten_frame(const float* sT, int k, float* fr) {
+    const float* S = sT + T_STAR + k * STAR_STRIDE;
+    const float pxx = S[4], pxy = S[5], pyy = S[6];
+    const float gxx = sT[T_G], gxy = sT[T_G + 1], gyy = sT[T_G + 2];
+    // T0 = [[r11, r21], [0, r22]] with T0 Sigma T0' = I (r the lower factor of Sigma^-1)
+    const float r11 = sqrtf(pxx), r21 = pxy / r11, r22 = sqrtf(fmaxf(pyy - r21 * r21, 0.f));
+    const float u0 = r11 * gxx + r21 * gxy, u1 = r11 * gxy + r21 * gyy;
+    const float b11 = u0 * r11 + u1 * r21, b12 = u1 * r22, b22 = r22 * gyy * r22;
+    // Q = [[c, s], [-s, c]] with Q B Q' diagonal, B = T0 G T0' (the smaller rotation; an
+    // infinite tau gives t = 0)
+    float c = 1.f, s = 0.f;
+    if (b12 != 0.f) {
+        const float tau = (b22 - b11) / (2.f * b12);
+        const float t = tau == 0.f ? 1.f : -copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+        c = 1.f / sqrtf(1.f + t * t);
+        s = t * c;
+    }
+    const float T[2][2] = {{c * r11, c * r21 + s * r22}, {-s * r11, -s * r21 + c * r22}};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        fr[2 * a] = T[a][0];
+        fr[2 * a + 1] = T[a][1];
+        const float v0 = T[a][0] * gxx + T[a][1] * gxy, v1 = T[a][0] * gxy + T[a][1] * gyy;
+        fr[WF_G + a] = fmaxf(v0 * T[a][0] + v1 * T[a][1], 0.f);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int a = wpa(p), b = wpb(p);
+        fr[WF_K + 0 * 3 + p] = T[a][0] * T[b][0];
+        fr[WF_K + 1 * 3 + p] = T[a][0] * T[b][1] + T[a][1] * T[b][0];
+        fr[WF_K + 2 * 3 + p] = T[a][1] * T[b][1];
+    }
+    fr[15] = 0.f;
+}
+
+// the row of galaxy component (k, j): exponent in z and the 35 monomial weights
+__host__ __device__ void whiten_row(const float* G, const float* fr, float* row) {
+    const float nu = G[9], w = G[7], dw = G[8];
+    const float l1 = 1.f / (1.f + nu * fr[WF_G]), l2 = 1.f / (1.f + nu * fr[WF_G + 1]);
+    float p1[5], p2[5];
+    p1[0] = p2[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        p1[i] = p1[i - 1] * l1;
+        p2[i] = p2[i - 1] * l2;
+    }
+    auto mono = [&](int deg, int i) { return p1[deg - i] * p2[i]; };
+    const float wn = w * nu, wn2 = wn * nu, dwn = dw * nu;
+    row[0] = -0.5f * (float)LOG2E_H * l1;
+    row[1] = -0.5f * (float)LOG2E_H * l2;
+    row[2] = G[3];
+    float* c = row + 3;
+    c[WS_N] = w;
+    c[WS_NE] = dw;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        c[WS_L + i] = w * mono(1, i);
+        c[WS_B + i] = wn * mono(1, i);
+        c[WS_LE + i] = dw * mono(1, i);
+        c[WS_BE + i] = dwn * mono(1, i);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        c[WS_LL + i] = w * mono(2, i);
+        c[WS_A + i] = wn * mono(2, i);
+        c[WS_D2 + i] = wn2 * mono(2, i);
+        c[WS_AE + i] = dwn * mono(2, i);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        c[WS_C + i] = wn * mono(3, i);
+        c[WS_D3 + i] = wn2 * mono(3, i);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) c[WS_D4 + i] = wn2 * mono(4, i);
+    row[3 + NWS] = 0.f;
+    row[4 + NWS] = 0.f;
+}
+
+// adds PSF component k's galaxy terms at one pixel, from its 35 sums, to the pixel-frame
+// value, gradient (mx, my, Gxx, Gxy, Gyy), e_dev derivatives and packed 5 x 5 Hessian
+__host__ __device__ __forceinline__ void whitened_add(const float (&s)[NWS], float z1, float z2,
+                                             const float* fr, float& g1, float (&d1)[5],
+                                             float& de, float (&h1)[15], float (&he)[5]) {
+    const float z[2] = {z1, z2};
+    const float Z2[3] = {z1 * z1, z1 * z2, z2 * z2};
+    const float Z3[4] = {z1 * Z2[0], z1 * Z2[1], z1 * Z2[2], z2 * Z2[2]};
+    const float Z4[5] = {Z2[0] * Z2[0], Z2[0] * Z2[1], Z2[0] * Z2[2], Z2[1] * Z2[2], Z2[2] * Z2[2]};
+    float T[2][2], K[3][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        T[a][0] = fr[2 * a];
+        T[a][1] = fr[2 * a + 1];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) K[e][p] = fr[WF_K + 3 * e + p];
+    g1 += s[WS_N];
+    de += s[WS_NE];
+    // d/dmu = T' r-sums; d/dG[E] = K (W11, 2 W12, W22), W_ab = (z_a z_b A_ab - delta_ab B_a) / 2
+    const float gm[2] = {z1 * s[WS_L], z2 * s[WS_L + 1]};
+    const float ge[2] = {z1 * s[WS_LE], z2 * s[WS_LE + 1]};
+    float Wv[3], Wev[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int a = wpa(p), b = wpb(p);
+        Wv[p] = 0.5f * wmult(p) * (Z2[a + b] * s[WS_A + a + b] - wdl(a, b) * s[WS_B + a]);
+        Wev[p] = 0.5f * wmult(p) * (Z2[a + b] * s[WS_AE + a + b] - wdl(a, b) * s[WS_BE + a]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        d1[i] += T[0][i] * gm[0] + T[1][i] * gm[1];
+        he[i] += T[0][i] * ge[0] + T[1][i] * ge[1];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        d1[2 + e] += K[e][0] * Wv[0] + K[e][1] * Wv[1] + K[e][2] * Wv[2];
+        he[2 + e] += K[e][0] * Wev[0] + K[e][1] * Wev[1] + K[e][2] * Wev[2];
+    }
+    // (mu, mu) = T' X T, X_ab = z_a z_b LL_ab - delta_ab L_a
+    float XT[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float v = 0.f;
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+                v += (Z2[a + b] * s[WS_LL + a + b] - wdl(a, b) * s[WS_L + a]) * T[b][k];
+            XT[a][k] = v;
+        }
+    h1[0] += T[0][0] * XT[0][0] + T[1][0] * XT[1][0];
+    h1[1] += T[0][0] * XT[0][1] + T[1][0] * XT[1][1];
+    h1[5] += T[0][1] * XT[0][1] + T[1][1] * XT[1][1];
+    // (mu, G): T' (Yv K'), Y_{a,bc} = (z_a z_b z_c C_abc - delta_bc z_a A_ab - delta_ab z_c A_ac
+    //                                  - delta_ac z_b A_ab) / 2
+    float YK[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float Yv[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const int b = wpa(p), c = wpb(p);
+            Yv[p] = 0.5f * wmult(p) *
+                    (Z3[a + b + c] * s[WS_C + a + b + c] - wdl(b, c) * z[a] * s[WS_A + a + b] -
+                     wdl(a, b) * z[c] * s[WS_A + a + c] - wdl(a, c) * z[b] * s[WS_A + a + b]);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) YK[a][e] = K[e][0] * Yv[0] + K[e][1] * Yv[1] + K[e][2] * Yv[2];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        h1[2 + e] += T[0][0] * YK[0][e] + T[1][0] * YK[1][e];
+        h1[6 + e] += T[0][1] * YK[0][e] + T[1][1] * YK[1][e];
+    }
+    // (G, G) = K Vm K', Vm_pq = m_p m_q V_{ab,cd} (pairs p = ab, q = cd)
+    float KV[3][3];
+    {
+        float Vm[3][3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int a = wpa(p), b = wpb(p), c = wpa(q), d = wpb(q);
+                const float* D2 = s + WS_D2;
+                const float* D3 = s + WS_D3;
+                const float v =
+                    Z4[a + b + c + d] * s[WS_D4 + a + b + c + d] - wdl(c, d) * Z2[a + b] * D3[a + b + c] -
+                    wdl(a, b) * Z2[c + d] * D3[a + c + d] + wdl(a, b) * wdl(c, d) * D2[a + c] -
+                    wdl(b, c) * Z2[a + d] * D3[a + b + d] - wdl(a, c) * Z2[b + d] * D3[a + b + d] -
+                    wdl(b, d) * Z2[a + c] * D3[a + b + c] - wdl(a, d) * Z2[b + c] * D3[a + b + c] +
+                    (wdl(b, c) * wdl(a, d) + wdl(a, c) * wdl(b, d)) * D2[a + b];
+                Vm[p][q] = 0.25f * wmult(p) * wmult(q) * v;
+            }
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) KV[e][q] = K[e][0] * Vm[0][q] + K[e][1] * Vm[1][q] + K[e][2] * Vm[2][q];
+    }
+    int c = 9;
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int f = e; f < 3; ++f, ++c) h1[c] += KV[e][0] * K[f][0] + KV[e][1] * K[f][1] + KV[e][2] * K[f][2];
+}
 
 template <class R>
 __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ items,
@@ -54,8 +299,11 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                                                 const R* __restrict__ vmap,
                                                 double* __restrict__ part,
                                                 const int32_t* __restrict__ src_active) {
+    // FP32: the galaxy terms in the frame that whitens each PSF component
+    constexpr bool WHITE = std::is_same<R, float>::value;
     __shared__ R sT[TBL_STRIDE];
-    __shared__ R red[CHUNK / 32][HV];
+    __shared__ double red[CHUNK / 32][HV];
+    __shared__ __align__(16) float wsm[WHITE ? MAXPSF * WFR + MAXPSF * MAXPROF * WROW : 4];
     const WorkItem it = items[blockIdx.x];
     const PatchGeo g = geo[it.patch];
     if (src_active && !src_active[g.src]) return;
@@ -65,6 +313,13 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
         const R* gT = tbl + (size_t)it.patch * TBL_STRIDE;
         const int n = T_GAL + npsf * nprof * GAL_STRIDE;
         for (int i = threadIdx.x; i < n; i += blockDim.x) sT[i] = gT[i];
+        __syncthreads();
+    }
+    if constexpr (WHITE) {
+        if ((int)threadIdx.x < npsf) whiten_frame(sT, threadIdx.x, wsm + threadIdx.x * WFR);
+        __syncthreads();
+        for (int i = threadIdx.x; i < npsf * nprof; i += blockDim.x)
+            whiten_row(sT + T_GAL + i * GAL_STRIDE, wsm + (i / nprof) * WFR, wsm + MAXPSF * WFR + i * WROW);
         __syncthreads();
     }
     R out[HV];
@@ -102,6 +357,31 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                 h0[0] += n * (qx * qx - S[4]);
                 h0[1] += n * (qx * qy - S[5]);
                 h0[2] += n * (qy * qy - S[6]);
+            }
+            if constexpr (WHITE) {
+                const float* fr = wsm + k * WFR;
+                const float z1 = fr[0] * dx + fr[1] * dy, z2 = fr[2] * dx + fr[3] * dy;
+                const float z1s = z1 * z1, z2s = z2 * z2;
+                float sw[NWS];
+#pragma unroll
+                for (int m = 0; m < NWS; ++m) sw[m] = 0.f;
+                const float4* row = reinterpret_cast<const float4*>(wsm + MAXPSF * WFR + k * nprof * WROW);
+                for (int j = 0; j < nprof; ++j, row += WROW / 4) {
+                    float cw[WROW];
+#pragma unroll
+                    for (int u = 0; u < WROW / 4; ++u) {
+                        const float4 v = row[u];
+                        cw[4 * u] = v.x;
+                        cw[4 * u + 1] = v.y;
+                        cw[4 * u + 2] = v.z;
+                        cw[4 * u + 3] = v.w;
+                    }
+                    const float e = ex2h(fmaf(cw[0], z1s, fmaf(cw[1], z2s, cw[2])));
+#pragma unroll
+                    for (int m = 0; m < NWS; ++m) sw[m] = fmaf(e, cw[3 + m], sw[m]);
+                }
+                whitened_add(sw, z1, z2, fr, g1, d1, de, h1, he);
+                continue;
             }
             const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
             for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
@@ -241,18 +521,20 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                 H[yh_index(Y_MX + a, Y_MX + b)] += s;
             }
     }
-    // ---- CTA reduction: FP32 or FP64 within a warp, FP64 across warps
+    // ---- CTA reduction: in R within a warp (a reduce-scatter), FP64 across warps
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    R v[HVP];
 #pragma unroll
-    for (int i = 0; i < HV; ++i) {
-        const R s = warp_sum_h(out[i]);
-        if (lane == 0) red[warp][i] = s;
-    }
+    for (int i = 0; i < HVP; ++i) v[i] = i < HV ? out[i] : (R)0;
+    warp_reduce_scatter(v, lane);
+#pragma unroll
+    for (int u = 0; u < HVP / 32; ++u)
+        if (3 * lane + u < HV) red[warp][3 * lane + u] = (double)v[u];
     __syncthreads();
     for (int i = threadIdx.x; i < HV; i += blockDim.x) {
-        R s = 0;
+        double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][i];
-        part[(size_t)blockIdx.x * NPART + i] = (double)s;
+        part[(size_t)blockIdx.x * NPART + i] = s;
     }
 }
 
@@ -260,18 +542,30 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
 // per-source chain rule and KL Hessian
 
 
-// d2(Gxx, Gxy, Gyy)/d(s_a) d(s_b), s = (e_axis, e_angle, e_scale)
-__device__ void shape_hessian(const double* A, const double* th, double d2G[3][3][3]) {
+// The pixel-frame ellipse is G = A W A' with W = ah I + bh (cos 2phi, sin 2phi; sin 2phi,
+// -cos 2phi), ah = sigma^2 (1 + rho^2) / 2, bh = sigma^2 (1 - rho^2) / 2.  Its first and
+// second derivatives over s = (e_axis, e_angle, e_scale) are A (dW) A' and A (d2W) A':
+// dW and d2W depend on theta alone (computed once per source, by one thread), and each
+// patch maps them through its own A (one output per thread).
+__device__ void shape_w_derivs(const double* th, double dW[3][3], double d2W[3][3][3]) {
     const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
     const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
     double s2, c2;
     sincos(2.0 * phi, &s2, &c2);
-    const double bh_r = -sg * sg * rho, bh_s = sg * (1.0 - rho * rho);
+    // first derivatives (index order rho = 0, phi = 1, sigma = 2; W as xx, xy, yy)
+    {
+        const double da = sg * sg * rho, db = -sg * sg * rho;
+        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
+    }
+    dW[1][0] = -2.0 * bh * s2; dW[1][1] = 2.0 * bh * c2; dW[1][2] = 2.0 * bh * s2;
+    {
+        const double da = sg * (1.0 + rho * rho), db = sg * (1.0 - rho * rho);
+        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
+    }
     // second derivatives of ah, bh over (rho, sigma)
+    const double bh_r = -sg * sg * rho, bh_s = sg * (1.0 - rho * rho);
     const double ah_rr = sg * sg, ah_ss = 1.0 + rho * rho, ah_rs = 2.0 * sg * rho;
     const double bh_rr = -sg * sg, bh_ss = 1.0 - rho * rho, bh_rs = -2.0 * sg * rho;
-    // W = (ah + bh c2, bh s2, ah - bh c2); index order (rho=0, phi=1, sigma=2)
-    double d2W[3][3][3];
     auto set = [&](int a, int b, double xx, double xy, double yy) {
         d2W[a][b][0] = d2W[b][a][0] = xx;
         d2W[a][b][1] = d2W[b][a][1] = xy;
@@ -283,13 +577,14 @@ __device__ void shape_hessian(const double* A, const double* th, double d2G[3][3
     set(0, 1, -2.0 * bh_r * s2, 2.0 * bh_r * c2, 2.0 * bh_r * s2);
     set(2, 1, -2.0 * bh_s * s2, 2.0 * bh_s * c2, 2.0 * bh_s * s2);
     set(1, 1, -4.0 * bh * c2, -4.0 * bh * s2, 4.0 * bh * c2);
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            const double wxx = d2W[a][b][0], wxy = d2W[a][b][1], wyy = d2W[a][b][2];
-            d2G[a][b][0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
-            d2G[a][b][1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
-            d2G[a][b][2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
-        }
+}
+
+// component c (xx, xy, yy) of A w A' for a symmetric w = (wxx, wxy, wyy)
+__device__ __forceinline__ double a_transform(const double* A, const double* w, int c) {
+    const double wxx = w[0], wxy = w[1], wyy = w[2];
+    if (c == 0) return A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
+    if (c == 1) return A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
+    return A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
 }
 
 // Full KL Hessian (44 x 44, row-major) added into H (zeroed by the caller), by one warp
@@ -407,6 +702,7 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
     __shared__ double nzv[NP][3];
     __shared__ double bmom[5][2][2];              // E[l_b | i], E[l_b^2 | i] per band and type
     __shared__ double dG[3][3], d2G[3][3][3];     // the patch map's shape derivatives
+    __shared__ double dW[3][3], d2W[3][3][3];     // the same in the world frame (theta only)
     __shared__ double wd[2], we[2];
     __shared__ double S2[3][3];
     __shared__ double klH[NP * NP];
@@ -441,6 +737,8 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
     } else if (warp == 2 && lane < 10) {
         const int b = lane >> 1, i = lane & 1;
         band_moments(th, b, i, bmom[b][i][0], bmom[b][i][1]);
+    } else if (warp == 3 && lane == 0) {
+        shape_w_derivs(th, dW, d2W);
     }
     double gacc = 0.0, lacc = 0.0;
     for (int p = patch_off[s]; p < patch_off[s + 1]; ++p) {
@@ -470,10 +768,15 @@ k_finalize_hess(int n_src, const double* __restrict__ theta, const PatchGeo* __r
                 Hy[a][b] = v;
                 Hy[b][a] = v;
             }
-        } else if (t == 128) {
-            shape_jacobian(A, th, dG);
-        } else if (t == 160) {
-            shape_hessian(A, th, d2G);
+        } else if (t >= 128 && t < 128 + 9 + 27) {
+            // the patch's shape derivatives through its map, one output per thread
+            const int i = t - 128;
+            if (i < 9) {
+                dG[i / 3][i % 3] = a_transform(A, dW[i / 3], i % 3);
+            } else {
+                const int r = i - 9, a = r / 9, b = (r / 3) % 3, c = r % 3;
+                d2G[a][b][c] = a_transform(A, d2W[a][b], c);
+            }
         }
         __syncthreads();
         if (t < NP) {

@@ -56,10 +56,11 @@ constexpr int ZPCOLS = 2 + NP;
 //   means  [8..15]: pixel-frame mean of PSF component k (x, y)
 //   star   [16 + 8k]: qa qb qc qd pxx pxy pyy c
 //   dG     [48 + 3q + c]: d(Gxx, Gxy, Gyy)[c] / d(e_axis, e_angle, e_scale)[q] (chain rule)
+//   G      [57..59]: the galaxy covariance Gxx Gxy Gyy in the pixel frame
 //   galaxy [64 + 12 (k nprof + j)]: qa qb qc qd pxx pxy pyy c dc nu 0 0
 // Component density: c * exp2(qa dx^2 + qb dx dy + qc dy^2 + qd) with
 // (qa, qb, qc) = -log2(e) (Pxx/2, Pxy, Pyy/2) and qd = -log2(2 pi sqrt(det C)).
-constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_GAL = 64,
+constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_G = 57, T_GAL = 64,
               GAL_STRIDE = 12;
 constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;

@@ -217,6 +217,9 @@ k_prep(const double* __restrict__ theta, const PatchGeo* __restrict__ geo,
                 G[1] = a0 * a2 * wxx + (a0 * a3 + a1 * a2) * wxy + a1 * a3 * wyy;
                 G[2] = a2 * a2 * wxx + (R)2 * a2 * a3 * wxy + a3 * a3 * wyy;
                 G[3] = thr[P_EDEV];
+                T[T_G + 0] = G[0];
+                T[T_G + 1] = G[1];
+                T[T_G + 2] = G[2];
                 R dW[3][3];
                 R da = sg * sg * rho, db = -sg * sg * rho;
                 dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;

@@ -70,33 +70,6 @@ __device__ inline double kl_value_grad(const ModelDev& md, const double* th, dou
     return kl;
 }
 
-// d(Gxx, Gxy, Gyy)/d(e_axis, e_angle, e_scale), G = A W A^T in the image's pixel frame.
-__device__ inline void shape_jacobian(const double* A, const double* th, double dG[3][3]) {
-    const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
-    const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
-    double s2, c2;
-    sincos(2.0 * phi, &s2, &c2);
-    double dW[3][3];
-    // d/d rho: d ah = sg^2 rho, d bh = -sg^2 rho
-    {
-        const double da = sg * sg * rho, db = -sg * sg * rho;
-        dW[0][0] = da + db * c2; dW[0][1] = db * s2; dW[0][2] = da - db * c2;
-    }
-    // d/d phi
-    dW[1][0] = -2.0 * bh * s2; dW[1][1] = 2.0 * bh * c2; dW[1][2] = 2.0 * bh * s2;
-    // d/d sigma: d ah = sg (1 + rho^2), d bh = sg (1 - rho^2)
-    {
-        const double da = sg * (1.0 + rho * rho), db = sg * (1.0 - rho * rho);
-        dW[2][0] = da + db * c2; dW[2][1] = db * s2; dW[2][2] = da - db * c2;
-    }
-    for (int q = 0; q < 3; ++q) {
-        const double wxx = dW[q][0], wxy = dW[q][1], wyy = dW[q][2];
-        dG[q][0] = A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
-        dG[q][1] = A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
-        dG[q][2] = A[2] * A[2] * wxx + 2.0 * A[2] * A[3] * wxy + A[3] * A[3] * wyy;
-    }
-}
-
 __device__ inline void band_moments(const double* th, int band, int i, double& el, double& el2) {
     double m = th[P_R1 + i], v = th[P_R2 + i];
     for (int j = 0; j < 4; ++j) {
