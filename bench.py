@@ -23,8 +23,8 @@ carries: `roofline` (the item kernel's achieved FLOP rate against the FP32 peak 
 from unit counts and clock, its DRAM bytes per launch imported from an ncu capture,
 every stage's CUDA-event time as the call runs them and serialised on one stream, and
 `step`: the whole step against its plain-ALU bound); `cpu_baseline` (the FP64 oracle on
-all host cores and on one); `hessian` (with its FLOP count, roofline and cost relative
-to ELBO + gradient), `fit` (with the FP32 sweeps alone, `fp32_only`, and fit quality),
+all host cores and on one); `hessian` (with its FLOP count, roofline, cost relative
+to ELBO + gradient and the CUDA-event time of each of its stages), `fit` (with the FP32 sweeps alone, `fp32_only`, and fit quality),
 `fit_schedules`, `catalog`, `workloads` (the crowded region, the sweep field and the
 multi-epoch region) and `tasks` legs; `clocks` sampled around and during the timed
 region; `gpu_launches`.  `--impl reference` times the oracle instead (rank 0 only) on a
@@ -98,11 +98,23 @@ def fp64_path_flops_per_source_pixel(npsf, n_exp, n_dev):
 
 
 def hess_flops_per_source_pixel(npsf, n_exp, n_dev):
-    """Algorithmic operations of the Hessian path per source-pixel (FMA = 2): the map pass
-    (as in fp64_path_flops_per_source_pixel) and the Hessian pass, which evaluates the
-    mixture with its first and second derivatives (per PSF component 20 + 42, each galaxy
-    component 140) and per pixel the 78 packed y-Hessian entries, the gradient and the
+    """Algorithmic operations of the FP32 Hessian path per source-pixel (FMA = 2): the map
+    pass (as in fp64_path_flops_per_source_pixel) and the Hessian pass, which evaluates the
+    galaxy mixture in the frame whitening each PSF component.  Per PSF component: the
+    offset and its products (5), the star component with its first and second derivatives
+    (31), the whitened coordinates and their squares (8), each galaxy component's exponent
+    and value (5) and its 35 weighted sums (70), and the sums' map back to the pixel frame
+    (329: the z-monomials, the whitened gradient and Hessian blocks, their transforms
+    through T and K); per pixel the 78 packed y-Hessian entries, the gradient and the
     likelihood weights (600)."""
+    nprof = n_exp + n_dev
+    return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (5 + 31 + 8 + 329 + 75 * nprof) + 600
+
+
+def hess64_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """The same for the FP64 Hessian path, which evaluates the mixture's first and second
+    derivatives component by component in the pixel frame (per PSF component 20 + 42, each
+    galaxy component 140; per pixel 600)."""
     nprof = n_exp + n_dev
     return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (20 + 42 + 140 * nprof) + 600
 
@@ -502,7 +514,17 @@ def main():
 
     hms32 = hess_loop(cel.FP32, args.hess_steps)
     hms64 = hess_loop(cel.FP64, max(1, args.hess_steps // 10))
+    # the FP32 Hessian evaluation's stages (CUDA events on each stage's launch stream)
+    P.profile(True)
+    for _ in range(args.hess_steps):
+        flush.fill_(1.0)
+        P.hess_device(theta, loc, grad, hes, precision=cel.FP32)
+    torch.cuda.synchronize()
+    hprof = P.profile_read()
+    P.profile(False)
+    hstage_us = {k: 1000.0 * v[0] / max(1, v[1]) for k, v in hprof.items()}
     hflop = hess_flops_per_source_pixel(npsf, ne, nd)
+    h64flop = hess64_flops_per_source_pixel(npsf, ne, nd)
     f64flop = fp64_path_flops_per_source_pixel(npsf, ne, nd)
     h32 = n_sp * ws / (hms32 / 1000.0)
     h64 = n_sp * ws / (hms64 / 1000.0)
@@ -512,12 +534,14 @@ def main():
                "fp64_ms_per_step": hms64,
                "what": "ELBO + gradient + 44x44 Hessian of every source",
                "cost_vs_elbo_grad": value / h32,
+               "stage_us": hstage_us,
                "roofline": {"bound": "alu", "flop_per_source_pixel": hflop,
                             "achieved": hflop * h32 / ws / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
                             "frac": hflop * h32 / ws / 1e12 / peak_fp32,
                             "peak_source": "FP32: 152 SM x 128 lanes x 2 x 2070 MHz (unit counts, max clock)",
-                            "fp64": {"achieved": hflop * h64 / ws / 1e12, "peak": peak_fp64,
-                                     "frac": hflop * h64 / ws / 1e12 / peak_fp64,
+                            "fp64": {"flop_per_source_pixel": h64flop,
+                                     "achieved": h64flop * h64 / ws / 1e12, "peak": peak_fp64,
+                                     "frac": h64flop * h64 / ws / 1e12 / peak_fp64,
                                      "peak_source": "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived)"}}}
 
     # end to end through the host-pointer C ABI (pinned buffers, copies inside)
