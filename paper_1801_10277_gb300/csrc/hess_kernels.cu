@@ -546,8 +546,8 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
 // -cos 2phi), ah = sigma^2 (1 + rho^2) / 2, bh = sigma^2 (1 - rho^2) / 2.  Its first and
 // second derivatives over s = (e_axis, e_angle, e_scale) are A (dW) A' and A (d2W) A':
 // dW and d2W depend on theta alone (computed once per source, by one thread), and each
-// patch maps them through its own A (one output per thread).
-__device__ void shape_w_derivs(const double* th, double dW[3][3], double d2W[3][3][3]) {
+// patch maps them through its own A (one output per thread).  Host-callable for tests.
+__host__ __device__ void shape_w_derivs(const double* th, double dW[3][3], double d2W[3][3][3]) {
     const double rho = th[P_AXIS], phi = th[P_ANGLE], sg = th[P_SCALE];
     const double bh = 0.5 * sg * sg * (1.0 - rho * rho);
     double s2, c2;
@@ -580,7 +580,7 @@ __device__ void shape_w_derivs(const double* th, double dW[3][3], double d2W[3][
 }
 
 // component c (xx, xy, yy) of A w A' for a symmetric w = (wxx, wxy, wyy)
-__device__ __forceinline__ double a_transform(const double* A, const double* w, int c) {
+__host__ __device__ __forceinline__ double a_transform(const double* A, const double* w, int c) {
     const double wxx = w[0], wxy = w[1], wyy = w[2];
     if (c == 0) return A[0] * A[0] * wxx + 2.0 * A[0] * A[1] * wxy + A[1] * A[1] * wyy;
     if (c == 1) return A[0] * A[2] * wxx + (A[0] * A[3] + A[1] * A[2]) * wxy + A[1] * A[3] * wyy;
