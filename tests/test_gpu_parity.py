@@ -265,6 +265,15 @@ def test_hessian_crowded(cel):
     _check_hessian(cel, synth.config(2), which=np.arange(0, 64, 4).astype(np.int32))
 
 
+def test_hessian_one_field_full_size_sampled(cel):
+    """The benchmark's workload at full size (500 sources, 5 x 2048 x 1489): local
+    objectives, gradients and 44 x 44 Hessians of the seeded sample of 24 sources the
+    gradient test uses, both precisions."""
+    prob = synth.config(1)
+    which = np.sort(np.random.default_rng(7).choice(prob.n_src, 24, replace=False)).astype(np.int32)
+    _check_hessian(cel, prob, which=which)
+
+
 def test_hessian_edge_cases(cel):
     th = np.stack([H.star_theta(1.0, 2.0), H.star_theta(20.0, 21.0, a_star=0.3)])
     th[1, synth.I_AXIS] = 0.35
