@@ -23,8 +23,9 @@ carries: `roofline` (the item kernel's achieved FLOP rate against the FP32 peak 
 from unit counts and clock, its DRAM bytes per launch imported from an ncu capture,
 every stage's CUDA-event time as the call runs them and serialised on one stream, and
 `step`: the whole step against its plain-ALU bound); `cpu_baseline` (the FP64 oracle on
-all host cores and on one); `hessian` (with its FLOP count, roofline, cost relative
-to ELBO + gradient and the CUDA-event time of each of its stages), `fit` (with the FP32 sweeps alone, `fp32_only`, and fit quality),
+all host cores and on one); `hessian` (with its FLOP count, roofline, the Hessian
+pass's own roofline, cost relative to ELBO + gradient and the CUDA-event time of each
+of its stages), `fit` (with the FP32 sweeps alone, `fp32_only`, and fit quality),
 `fit_schedules`, `catalog`, `workloads` (the crowded region, the sweep field and the
 multi-epoch region) and `tasks` legs; `clocks` sampled around and during the timed
 region; `gpu_launches`.  `--impl reference` times the oracle instead (rank 0 only) on a
@@ -97,18 +98,24 @@ def fp64_path_flops_per_source_pixel(npsf, n_exp, n_dev):
     return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (5 + 18 + 33 * nprof) + 55
 
 
-def hess_flops_per_source_pixel(npsf, n_exp, n_dev):
-    """Algorithmic operations of the FP32 Hessian path per source-pixel (FMA = 2): the map
-    pass (as in fp64_path_flops_per_source_pixel) and the Hessian pass, which evaluates the
-    galaxy mixture in the frame whitening each PSF component.  Per PSF component: the
-    offset and its products (5), the star component with its first and second derivatives
-    (31), the whitened coordinates and their squares (8), each galaxy component's exponent
-    and value (5) and its 35 weighted sums (70), and the sums' map back to the pixel frame
-    (329: the z-monomials, the whitened gradient and Hessian blocks, their transforms
-    through T and K); per pixel the 78 packed y-Hessian entries, the gradient and the
-    likelihood weights (600)."""
+def hess_pass_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """Algorithmic operations of the FP32 Hessian pass (`k_hess<float>`) per source-pixel
+    (FMA = 2); it evaluates the galaxy mixture in the frame whitening each PSF component.
+    Per PSF component: the offset and its products (5), the star component with its first
+    and second derivatives (31), the whitened coordinates and their squares (8), each
+    galaxy component's exponent and value (5) and its 35 weighted sums (70), and the sums'
+    map back to the pixel frame (329: the z-monomials, the whitened gradient and Hessian
+    blocks, their transforms through T and K); per pixel the 78 packed y-Hessian entries,
+    the gradient and the likelihood weights (600)."""
     nprof = n_exp + n_dev
-    return npsf * (5 + 8 + 8 * nprof) + 30 + npsf * (5 + 31 + 8 + 329 + 75 * nprof) + 600
+    return npsf * (5 + 31 + 8 + 329 + 75 * nprof) + 600
+
+
+def hess_flops_per_source_pixel(npsf, n_exp, n_dev):
+    """The whole FP32 Hessian evaluation per source-pixel: the map pass (as in
+    fp64_path_flops_per_source_pixel) and the Hessian pass."""
+    nprof = n_exp + n_dev
+    return npsf * (5 + 8 + 8 * nprof) + 30 + hess_pass_flops_per_source_pixel(npsf, n_exp, n_dev)
 
 
 def hess64_flops_per_source_pixel(npsf, n_exp, n_dev):
@@ -122,6 +129,43 @@ def hess64_flops_per_source_pixel(npsf, n_exp, n_dev):
 # FP64 peak, derived: 152 SMs x 2 FP64 FMA lanes per clock (the FP64 pipe's width on this
 # part) x 2 FLOP x the 2070 MHz maximum clock
 FP64_LANES = 2
+
+
+def hessian_summary(n_sp, ws, npsf, n_exp, n_dev, ms32, ms64, stage_us, elbo_grad_value):
+    """The `hessian` leg of the JSON line from its measurements: ms32 / ms64 the FP32 and
+    FP64 evaluations' CUDA-event milliseconds, stage_us the FP32 evaluation's stages (µs
+    per launch), n_sp the source-pixels per rank, ws ranks.  `roofline` is the whole
+    evaluation against the FP32 peak (and the FP64 path against the FP64 peak);
+    `roofline.kernel` is the Hessian pass alone (its stage time), null if the stage is
+    missing."""
+    peak_fp32 = SM_COUNT * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
+    peak_fp64 = SM_COUNT * FP64_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
+    hflop = hess_flops_per_source_pixel(npsf, n_exp, n_dev)
+    h64flop = hess64_flops_per_source_pixel(npsf, n_exp, n_dev)
+    pflop = hess_pass_flops_per_source_pixel(npsf, n_exp, n_dev)
+    h32 = n_sp * ws / (ms32 / 1000.0)
+    h64 = n_sp * ws / (ms64 / 1000.0)
+    k_us = stage_us.get("hess_adjoint")
+    kernel = None
+    if k_us:
+        k_ach = pflop * n_sp / (k_us * 1e-6) / 1e12
+        kernel = {"name": "k_hess<float>", "us": k_us, "flop_per_source_pixel": pflop,
+                  "achieved": k_ach, "frac": k_ach / peak_fp32}
+    return {"value": h32, "unit": "source-pixel evals/s",
+            "ms_per_step": ms32, "fp64_value": h64,
+            "fp64_ms_per_step": ms64,
+            "what": "ELBO + gradient + 44x44 Hessian of every source",
+            "cost_vs_elbo_grad": elbo_grad_value / h32,
+            "stage_us": stage_us,
+            "roofline": {"bound": "alu", "flop_per_source_pixel": hflop,
+                         "achieved": hflop * h32 / ws / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": hflop * h32 / ws / 1e12 / peak_fp32,
+                         "peak_source": "FP32: 152 SM x 128 lanes x 2 x 2070 MHz (unit counts, max clock)",
+                         "kernel": kernel,
+                         "fp64": {"flop_per_source_pixel": h64flop,
+                                  "achieved": h64flop * h64 / ws / 1e12, "peak": peak_fp64,
+                                  "frac": h64flop * h64 / ws / 1e12 / peak_fp64,
+                                  "peak_source": "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived)"}}}
 
 
 def other_eval_flops(npsf, n_exp, n_dev):
@@ -523,26 +567,9 @@ def main():
     hprof = P.profile_read()
     P.profile(False)
     hstage_us = {k: 1000.0 * v[0] / max(1, v[1]) for k, v in hprof.items()}
-    hflop = hess_flops_per_source_pixel(npsf, ne, nd)
-    h64flop = hess64_flops_per_source_pixel(npsf, ne, nd)
+    hessian = hessian_summary(n_sp, ws, npsf, ne, nd, hms32, hms64, hstage_us, value)
     f64flop = fp64_path_flops_per_source_pixel(npsf, ne, nd)
-    h32 = n_sp * ws / (hms32 / 1000.0)
-    h64 = n_sp * ws / (hms64 / 1000.0)
     peak_fp64 = SM_COUNT * FP64_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
-    hessian = {"value": h32, "unit": "source-pixel evals/s",
-               "ms_per_step": hms32, "fp64_value": h64,
-               "fp64_ms_per_step": hms64,
-               "what": "ELBO + gradient + 44x44 Hessian of every source",
-               "cost_vs_elbo_grad": value / h32,
-               "stage_us": hstage_us,
-               "roofline": {"bound": "alu", "flop_per_source_pixel": hflop,
-                            "achieved": hflop * h32 / ws / 1e12, "peak": peak_fp32, "unit": "TFLOP/s",
-                            "frac": hflop * h32 / ws / 1e12 / peak_fp32,
-                            "peak_source": "FP32: 152 SM x 128 lanes x 2 x 2070 MHz (unit counts, max clock)",
-                            "fp64": {"flop_per_source_pixel": h64flop,
-                                     "achieved": h64flop * h64 / ws / 1e12, "peak": peak_fp64,
-                                     "frac": h64flop * h64 / ws / 1e12 / peak_fp64,
-                                     "peak_source": "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived)"}}}
 
     # end to end through the host-pointer C ABI (pinned buffers, copies inside)
     pin_th = torch.tensor(prob.theta, dtype=torch.float64).pin_memory()

@@ -1,6 +1,6 @@
 """Host logic of bench.py that needs no GPU: the clock-sample summary that decides
-whether a timed run is kept, and the reference arm's JSON line (the FP64 oracle on the
-host cores)."""
+whether a timed run is kept, the Hessian leg's summary from its timings, and the
+reference arm's JSON line (the FP64 oracle on the host cores)."""
 import json
 import os
 import subprocess
@@ -29,6 +29,33 @@ def test_clock_summary_median_max_and_reasons():
     hot = rows + ["0, 1500, 2070, 1400.0, 0x48, Active, Active, Not Active, Active"]
     s = _clocks("\n".join(hot))
     assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_hessian_summary_from_timings():
+    """The one-field workload's counts (3 PSF components, 8 + 6 profile components):
+    FLOP per source-pixel, rates, the evaluation's and the Hessian pass's fractions of
+    the FP32 peak, and no kernel entry when the pass's stage is missing."""
+    import bench
+    assert bench.hess_pass_flops_per_source_pixel(3, 8, 6) == 3 * (373 + 75 * 14) + 600
+    assert bench.hess_flops_per_source_pixel(3, 8, 6) == 3 * (13 + 8 * 14) + 30 + 4869
+    n_sp = 1_001_730
+    stages = {"prep": 16.0, "contrib": 29.0, "gather": 9.0, "hess_adjoint": 199.0, "finalize": 123.0}
+    h = bench.hessian_summary(n_sp, 1, 3, 8, 6, 0.373, 13.47, stages, 1.5e10)
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    assert abs(h["value"] - n_sp / 0.373e-3) < 1.0
+    assert abs(h["cost_vs_elbo_grad"] - 1.5e10 / h["value"]) < 1e-9
+    r = h["roofline"]
+    assert abs(r["achieved"] - 5274 * n_sp / 0.373e-3 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    k = r["kernel"]
+    assert k["name"] == "k_hess<float>" and k["flop_per_source_pixel"] == 4869
+    assert abs(k["achieved"] - 4869 * n_sp / 199e-6 / 1e12) < 1e-9 and 0.29 < k["frac"] < 0.31
+    assert abs(r["fp64"]["achieved"] - 7071 * n_sp / 13.47e-3 / 1e12) < 1e-9
+    # two replicas: the rate doubles, each kernel's own rate does not
+    h2 = bench.hessian_summary(n_sp, 2, 3, 8, 6, 0.373, 13.47, stages, 3.0e10)
+    assert abs(h2["value"] - 2 * h["value"]) < 1.0 and h2["roofline"]["kernel"]["achieved"] == k["achieved"]
+    assert abs(h2["roofline"]["frac"] - r["frac"]) < 1e-12
+    assert bench.hessian_summary(n_sp, 1, 3, 8, 6, 0.373, 13.47, {}, 1.5e10)["roofline"]["kernel"] is None
+    json.dumps(h)
 
 
 def test_clock_summary_without_samples():
