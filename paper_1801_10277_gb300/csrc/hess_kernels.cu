@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(CHUNK) k_hess(const WorkItem* __restrict__ ite
                 whitened_add(sw, z1, z2, fr, g1, d1, de, h1, he);
                 continue;
             }
+            // FP64: the galaxy components one by one in the pixel frame
             const R* G = sT + T_GAL + k * nprof * GAL_STRIDE;
             for (int j = 0; j < nprof; ++j, G += GAL_STRIDE) {
                 const R e = ex2h(G[0] * dxx + G[1] * dxy + G[2] * dyy + G[3]);
