@@ -93,6 +93,8 @@ constexpr int WFR = 16;    // floats per k: T (row-major), K (3 x 3), g1, g2, pa
 // K[e][p] = (T E_e T')_p for the pixel-frame shape directions E_e = (xx, xy + yx, yy)
 // and the whitened pairs p = (11, 12, 22)
 constexpr int WF_K = 4, WF_G = 13;
+static_assert(3 + NWS <= WROW && WROW % 4 == 0 && WFR % 4 == 0 && WF_G + 2 <= WFR,
+              "whitened rows are read as float4 from a 16-byte aligned array");
 
 __host__ __device__ __forceinline__ int wpa(int p) { return p == 2 ? 1 : 0; }
 __host__ __device__ __forceinline__ int wpb(int p) { return p == 0 ? 0 : 1; }

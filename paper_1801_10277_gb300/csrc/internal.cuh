@@ -63,6 +63,9 @@ constexpr int ZPCOLS = 2 + NP;
 constexpr int T_HDR = 0, T_MEAN = 8, T_STAR = 16, STAR_STRIDE = 8, T_DG = 48, T_G = 57, T_GAL = 64,
               GAL_STRIDE = 12;
 constexpr int TBL_STRIDE = T_GAL + MAXPSF * MAXPROF * GAL_STRIDE;   // 832
+static_assert(T_MEAN + 2 * MAXPSF <= T_STAR && T_STAR + MAXPSF * STAR_STRIDE <= T_DG &&
+                  T_DG + 9 <= T_G && T_G + 3 <= T_GAL,
+              "mixture-table fields overlap");
 constexpr int H_A0 = 0, H_A1 = 1, H_EL0 = 2, H_EL20 = 3, H_EL1 = 4, H_EL21 = 5, H_IOTA = 6;
 
 // floats of one patch's whitened-frame table (item_kernels.cu): a value part (header 16,
